@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the factored Levenberg-Marquardt LNCC iteration on GB300.
+
+Workload: brain-MRI-shaped synthetic pair 160x192x224 fp32 (30-label Voronoi
+phantom, bias field, noise; moving = SVF warp, max 8 voxels), LNCC window 5,
+gradient smoothing sigma 1, paper defaults (lambda0 0.006, mu+ 1.5,
+mu- 0.975), no rejection.  One step = one full-resolution LM iteration
+(trial field, loss + gradient evaluation, damping decision) replayed from a
+CUDA graph with all inputs resident in HBM.  The metric is
+Gvoxel-iterations / s (voxels x loss evaluations / s).
+
+Extra keys:
+  roofline     -- pass-1 evaluation against the measured HBM copy bandwidth
+  cpu_baseline -- the FP64 oracle on the host cores (bounded sample)
+  e2e          -- whole coarse-to-fine registration (levels 4/2/1 with
+                  200/100/50 iterations) through lm_register, host buffers
+                  copied in and the field copied out inside the timed region
+Multi-GPU (torchrun): one independent pair per rank (replicas, weak scaling).
+
+--impl reference runs the FP64 oracle (test infrastructure) on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SHAPE = (160, 192, 224)
+WORKLOAD = ("brain-MRI-shaped Voronoi pair 160x192x224 fp32, full-resolution "
+            "LM iterations, LNCC k=5, sigma_grad=1, lambda0=0.006, mu+=1.5, "
+            "mu-=0.975")
+METRIC = "Gvoxel-iters/s"
+# algorithmic HBM bytes per voxel of one pass-1 evaluation:
+# read F 4 + M 4 + u 12, write g 12 (fp32 images)
+EVAL_BYTES_PER_VOXEL = 32
+STEP_BYTES_PER_VOXEL = 36
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-i",
+                 str(self.index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(F, M, iters=3):
+    """The FP64 oracle, as it stands, on the host cores (OpenMP threads)."""
+    import numpy as np
+    import oracle
+    P = oracle.params()
+    t0 = time.perf_counter()
+    st = oracle.State(F, M, np.zeros((3,) + F.shape), P)
+    evals = 1
+    for _ in range(iters):
+        evals += oracle.lm_step(st)["evals"]
+    dt = time.perf_counter() - t0
+    V = F.size
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": V * evals / dt / 1e9, "unit": METRIC, "cores": cores,
+            "kind": "oracle",
+            "sample": f"FP64 C oracle (OpenMP), initial evaluation + {iters} "
+                      f"LM iterations of the full 160x192x224 pair, "
+                      f"{evals} evaluations in {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import synth
+    oracle.build()
+    F, M, _ = synth.voronoi_pair(SHAPE, seed=0)
+    # bounded sample: a 40-slice z-slab of the same pair per step
+    Fs, Ms = F[60:100].astype(np.float64), M[60:100].astype(np.float64)
+    P = oracle.params()
+    st = oracle.State(Fs, Ms, np.zeros((3,) + Fs.shape), P)
+    for _ in range(args.warmup):
+        oracle.lm_step(st)
+    evals = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        evals += oracle.lm_step(st)["evals"]
+    dt = time.perf_counter() - t0
+    V = Fs.size
+    value = V * evals / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "40-slice z-slab "
+                   "(40x192x224) of the pair, one LM iteration per step"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores,
+                         "kind": "oracle",
+                         "sample": "40x192x224 z-slab, one FP64 LM iteration "
+                                   "per step"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2603_19371_gb300 import build as _build
+    from paper_2603_19371_gb300 import lmreg as P
+    import synth
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    P.load()
+
+    F, M, _ = synth.voronoi_pair(SHAPE, seed=rank)
+    V = F.size
+    stream = torch.cuda.Stream()
+    params = P.lm_default_params()
+    with torch.cuda.stream(stream):
+        Ft = torch.from_numpy(F).cuda()
+        Mt = torch.from_numpy(M).cuda()
+        u = torch.zeros((3,) + SHAPE, device="cuda")
+    stream.synchronize()
+    ctx = P.lm_init(Ft, Mt, params, stream=stream)
+    P.lm_reset(ctx, u)
+    P.lm_iterate(ctx, u, args.warmup, info=False)
+    st0 = P.lm_get_state(ctx)
+
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.lm_iterate(ctx, u, args.steps, info=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    st1 = P.lm_get_state(ctx)
+    evals = st1.evals - st0.evals
+    launches = st1.kernel_launches - st0.kernel_launches
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        ev = torch.tensor([float(evals) * V], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(ev)
+        voxel_evals = float(ev.item())
+    else:
+        voxel_evals = float(evals) * V
+    value = voxel_evals / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (pass-1 evaluation), timed live
+    ms_eval, ms_step = P.lm_time_passes(ctx, u, 20)
+    peak, peak_kind = _peaks()
+    achieved = EVAL_BYTES_PER_VOXEL * V / (ms_eval / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "pass-1 evaluation",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": None,
+                "ms_eval": ms_eval, "ms_step": ms_step,
+                "step_achieved_gbs": STEP_BYTES_PER_VOXEL * V / (ms_step / 1e3) / 1e9,
+                "bytes_per_voxel_eval": EVAL_BYTES_PER_VOXEL}
+
+    # end to end: host buffers in, whole registration, field out
+    e2e = None
+    if not args.no_e2e:
+        levels = [(4, 200), (2, 100), (1, 50)]
+        Fh = torch.from_numpy(F).pin_memory()
+        Mh = torch.from_numpy(M).pin_memory()
+        uh = torch.empty((3,) + SHAPE).pin_memory()
+        with torch.cuda.stream(stream):
+            Fd = torch.empty_like(Ft)
+            Md = torch.empty_like(Mt)
+            ud = torch.zeros_like(u)
+            Fd.copy_(Fh, non_blocking=True)
+            Md.copy_(Mh, non_blocking=True)
+        stream.synchronize()
+        ctx2 = P.lm_init(Fd, Md, params, stream=stream)
+        P.lm_register(ctx2, levels, ud)            # warm-up (allocations)
+        n_e2e = max(1, min(args.steps, 3))
+        vox = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            with torch.cuda.stream(stream):
+                Fd.copy_(Fh, non_blocking=True)
+                Md.copy_(Mh, non_blocking=True)
+                ud.zero_()
+            rep = P.lm_register(ctx2, levels, ud)
+            with torch.cuda.stream(stream):
+                uh.copy_(ud, non_blocking=True)
+            stream.synchronize()
+            vox += rep.voxel_evals
+        dt = time.perf_counter() - t0
+        e2e = {"value": vox / dt / 1e9, "unit": METRIC,
+               "h2d_bytes_per_step": 2 * F.nbytes,
+               "d2h_bytes_per_step": int(uh.numel() * 4),
+               "ms_per_registration": dt / n_e2e * 1e3,
+               "what": "lm_register, levels 4/2/1 x 200/100/50 iterations, "
+                       "F and M copied in, u copied out per step"}
+        P.lm_destroy(ctx2)
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(F, M)
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "voxels": V,
+                   "l2": "no flush: per-iteration working set (F, M, u, "
+                         "trial u, two gradients: 385 MB) exceeds the "
+                         "129 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "evals": int(evals),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * lmreg.h -- C ABI of the GB300 (sm_103a) factored Levenberg-Marquardt
+ * registration library.
+ *
+ * The library minimises an LNCC image-similarity loss over a dense 3-D
+ * displacement field u, L(u) = L_sim(F, M o (Id + u)) (Section 1, Eq. 1 of
+ * Jena, Chaudhari, Gee, "Factored Levenberg-Marquardt for Diffeomorphic Image
+ * Registration"), with the per-voxel rank-1 damped step of Eq. tile1
+ * (Appendix A), the compositive update of Eq. compositive (Section 2.1), the
+ * damping rule of Eq. lambda-update and the rejection rule of Eq. rejection
+ * (Section 3.3), on a coarse-to-fine pyramid (Section 2.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Volumes are [D][H][W] (z, y, x) with x fastest, contiguous.
+ *  - A displacement field is float32 [3][D][H][W]: component 0 along x (W),
+ *    1 along y (H), 2 along z (D), in voxel units; u(p) names the sample
+ *    point p + u(p) in voxel index coordinates.
+ *  - All data pointers are DEVICE pointers unless a parameter says "host".
+ *    The caller owns every pointer it passes; the library never frees them
+ *    and keeps no pointer past the call unless stated (lm_init keeps the
+ *    fixed/moving image pointers for the context's lifetime).
+ *  - Calls are ordered on the CUDA stream given to lm_init.  Entry points
+ *    that fill a host struct synchronise that stream before returning.
+ *  - Every function returns LM_OK (0) or a negative LM_E* code; nothing
+ *    throws across the ABI.  lm_strerror() names a code, lm_last_error()
+ *    describes the last failure on the calling thread.
+ *  - The loss reported everywhere is r = 1 - LNCC in [0, 1] (the residual of
+ *    the squared-loss form (1 - LNCC)^2 of Section 2.2).
+ */
+#ifndef LMREG_H
+#define LMREG_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LM_API __attribute__((visibility("default")))
+#else
+#define LM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define LM_OK            0
+#define LM_EINVAL       -1  /* bad argument: null pointer, shape, parameter */
+#define LM_ENOMEM       -2  /* device or host allocation failed */
+#define LM_ECUDA        -3  /* a CUDA runtime call failed */
+#define LM_ENONFINITE   -4  /* a loss or gradient reduction was not finite */
+#define LM_ETIMEOUT     -5  /* a bounded device wait ran out */
+#define LM_EUNSUPPORTED -6  /* valid request this build does not handle */
+#define LM_ESTATE       -7  /* call out of order (e.g. lm_step before reset) */
+
+/* ---- image storage types ----------------------------------------------- */
+#define LM_F32  0  /* float32 images */
+#define LM_BF16 1  /* bfloat16 images, sampled and accumulated in float32 */
+
+/* An image volume. */
+typedef struct {
+    int D, H, W;        /* depth (z), height (y), width (x); each >= 1 */
+    int dtype;          /* LM_F32 or LM_BF16 */
+    const void *data;   /* device pointer to D*H*W elements, caller-owned */
+} lm_volume;
+
+/* Optimiser and loss parameters.  lm_default_params() fills the paper's
+ * defaults: lambda0 = 0.006, mu+ = 1.5, mu- = 0.975 (Section 3), rejection
+ * off with tau = 1 and 10 retries (Section 3.3). */
+typedef struct {
+    int    win;         /* LNCC box side k: odd, 3..9.                 [5] */
+    float  eps_nr;      /* LNCC numerator stabiliser, >= 0.         [1e-5] */
+    float  eps_dr;      /* LNCC denominator stabiliser, > 0.        [1e-5] */
+    float  sigma_grad;  /* Gaussian sigma on the gradient, 0..2.       [1] */
+    float  sigma_warp;  /* Gaussian sigma on the composed warp, 0..2.  [0] */
+    float  step;        /* epsilon of Eq. compositive, voxels, > 0.  [0.5] */
+    double lambda0;     /* initial damping, > 0.                   [0.006] */
+    double mu_inc;      /* damping increase factor mu+, > 1.         [1.5] */
+    double mu_dec;      /* damping decrease factor mu-, in (0, 1). [0.975] */
+    double lambda_max;  /* damping cap, >= lambda0, may be +inf.    [+inf] */
+    int    reject;      /* 1: Eq. rejection on.                         [0] */
+    double tau;         /* rejection tolerance ratio, >= 0.          [1.0] */
+    int    max_retries; /* retries after a rejection, 0..32.          [10] */
+} lm_params;
+
+/* Coarse-to-fine schedule: levels run in order, factor[l] in {1, 2, 4}
+ * (image size divided by factor[l], rounded down, at least 1),
+ * iters[l] >= 0 LM iterations at that level. */
+#define LM_MAX_LEVELS 4
+typedef struct {
+    int nlevels;
+    int factor[LM_MAX_LEVELS];
+    int iters[LM_MAX_LEVELS];
+} lm_schedule;
+
+/* Outcome of one LM iteration. */
+typedef struct {
+    double loss;        /* loss of the field after the iteration */
+    double loss_first;  /* loss of the first trial of the iteration */
+    double lambda;      /* damping after the iteration */
+    float  gmax;        /* max_p |g(p)| of the field after the iteration */
+    int    accepted;    /* 1 = a trial was accepted, 0 = discarded */
+    int    retries;     /* rejected trials before the outcome */
+    int    evals;       /* loss evaluations spent (retries + 1) */
+} lm_step_info;
+
+/* Optimiser scalars of a context (for inspection, teacher forcing and
+ * checkpoints).  has_prev = 0 means L_prev is not defined yet. */
+typedef struct {
+    double loss;        /* L_t */
+    double loss_prev;   /* L_{t-1} */
+    double lambda;
+    float  gmax;
+    int    has_prev;
+    int    iter;        /* iterations run since lm_reset */
+    int    evals;       /* loss evaluations since lm_reset */
+    long long kernel_launches; /* kernels this context enqueued since
+                                  lm_reset (read-only for lm_set_state) */
+} lm_state;
+
+/* Summary of a registration run. */
+typedef struct {
+    int    nlevels;
+    int    level_dims[LM_MAX_LEVELS][3];    /* D, H, W of each level */
+    int    level_iters[LM_MAX_LEVELS];
+    int    level_evals[LM_MAX_LEVELS];
+    int    level_accepted[LM_MAX_LEVELS];
+    double level_loss[LM_MAX_LEVELS];       /* loss at the end of the level */
+    double final_loss;
+    long long voxel_evals;                  /* sum over levels of V * evals */
+    double wall_ms;                         /* host wall time of the call */
+} lm_report;
+
+typedef struct lm_ctx lm_ctx;
+
+/* Fill *p with the defaults listed above.  LM_EINVAL if p is NULL. */
+LM_API int lm_default_params(lm_params *p);
+
+/* Create a context for one fixed/moving pair of equal shape and dtype.
+ * fixed, moving: image descriptors; their device data must stay valid and
+ *   unchanged for the context's lifetime.
+ * p: parameters (copied); NULL = defaults.
+ * cuda_stream: cudaStream_t to order all work on (NULL = default stream).
+ * The context allocates its own device scratch (about 40 bytes per voxel
+ * plus pyramid levels on first lm_register).  LM_EINVAL on bad shapes or
+ * parameters, LM_ENOMEM / LM_ECUDA on allocation failure. */
+LM_API int lm_init(lm_ctx **ctx, const lm_volume *fixed, const lm_volume *moving,
+            const lm_params *p, void *cuda_stream);
+
+/* Release the context and its scratch.  NULL is ignored. */
+LM_API void lm_destroy(lm_ctx *ctx);
+
+/* Evaluate the loss and its smoothed gradient at u (steps (a)-(c)) without
+ * touching the optimiser state.  u: device [3][D][H][W].  loss (host, may be
+ * NULL), g_out (device [3][D][H][W], may be NULL), gmax (host, may be NULL).
+ * Synchronises the stream.  LM_ENONFINITE if the loss is not finite. */
+LM_API int lm_eval(lm_ctx *ctx, const float *u, double *loss, float *g_out,
+            float *gmax);
+
+/* Start an LM run from the field u (device, in/out for later lm_step
+ * calls): evaluates L_0 and g_0 at u, sets lambda = lambda0 and clears the
+ * loss history.  Asynchronous. */
+LM_API int lm_reset(lm_ctx *ctx, float *u);
+
+/* One LM iteration (Section 2.2 / 3.3) on the field u passed to the last
+ * lm_reset: the trial u* = v + u o (Id + v) with v = step * du from
+ * Eq. tile1, its loss, and the damping / rejection decision.  On return u
+ * holds u_{t+1}.  info (host, may be NULL): filled after a stream
+ * synchronisation; NULL keeps the call asynchronous.  LM_ESTATE if u is not
+ * the pointer given to lm_reset. */
+LM_API int lm_step(lm_ctx *ctx, float *u, lm_step_info *info);
+
+/* n LM iterations as lm_step, replayed from a captured CUDA graph; info of
+ * the last iteration (host, may be NULL). */
+LM_API int lm_iterate(lm_ctx *ctx, float *u, int n, lm_step_info *info);
+
+/* Read / overwrite the optimiser scalars (synchronising).  lm_set_state
+ * keeps the context's field and gradient, replacing only the scalars. */
+LM_API int lm_get_state(lm_ctx *ctx, lm_state *out);
+LM_API int lm_set_state(lm_ctx *ctx, const lm_state *in);
+
+/* Whole coarse-to-fine registration (Section 2.1 pyramid).  u (device,
+ * full resolution [3][D][H][W]): in = initial field, out = result.  At each
+ * level F and M are Gaussian-blurred (sigma = factor/2) and resampled, the
+ * field is carried over with values scaled by the factor ratio, and lambda
+ * and the loss history restart.  rep (host, may be NULL) receives a
+ * summary.  Synchronises the stream. */
+LM_API int lm_register(lm_ctx *ctx, const lm_schedule *s, float *u, lm_report *rep);
+
+/* Checkpoint: the optimiser scalars and the context's gradient of the
+ * current field.  lm_state_save with buf NULL writes the needed size to
+ * *nbytes; otherwise buf (host) must hold *nbytes bytes.  lm_state_load
+ * restores a checkpoint taken from a context of the same shape; the field
+ * itself is the caller's u, which must be passed to lm_reset first. */
+LM_API int lm_state_save(lm_ctx *ctx, void *buf, size_t *nbytes);
+LM_API int lm_state_load(lm_ctx *ctx, const void *buf, size_t nbytes);
+
+/* Measurement aid: time the two passes of the iteration separately.  With
+ * the state of the last lm_reset / lm_step on u, launches the trial kernel
+ * (pass 2: Eq. tile1 + Eq. compositive) n times, then the evaluation kernels
+ * (pass 1: resampling, LNCC and its gradient, smoothing) n times, each run
+ * bracketed by CUDA events on the context's stream, and returns the mean
+ * milliseconds per launch in *ms_step and *ms_eval (host).  The optimiser
+ * state is not changed.  Synchronises the stream. */
+LM_API int lm_time_passes(lm_ctx *ctx, float *u, int n, double *ms_eval,
+                          double *ms_step);
+
+/* Static message for an LM_E* code. */
+LM_API const char *lm_strerror(int code);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+LM_API const char *lm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LMREG_H */

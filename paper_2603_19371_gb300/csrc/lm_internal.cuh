@@ -1,0 +1,106 @@
+// Internal definitions shared by the CUDA translation units of liblmreg.
+// Not part of the public ABI (include/lmreg.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "lmreg.h"
+
+namespace lmk {
+
+// Volume geometry: x fastest, V = nx * ny * nz.
+struct Geom {
+    int nx, ny, nz;
+    long long V;
+};
+
+// Optimiser state kept on the device so that an LM iteration (and its
+// rejected retries) runs without a host round trip.  u and g live in two
+// ping-pong slots each; cu / cg name the slot holding the current field and
+// its gradient, the trial goes to the other slot.
+struct DevState {
+    double L;          // L_t, loss of the current field
+    double L_prev;     // L_{t-1}
+    double L_trial;    // loss of the last evaluated trial
+    double L_first;    // loss of the first trial of the last iteration
+    double lambda;     // damping
+    float gmax;        // max |g| of the current gradient
+    float gmax_trial;  // max |g| of the last trial gradient
+    int has_prev;      // L_prev defined
+    int cu, cg;        // current slots
+    int retries;       // rejections in the current iteration
+    int done;          // current iteration finished (attempts > 0 skip)
+    int accepted;      // outcome of the last finished iteration
+    int status;        // sticky error bits (STATUS_*)
+    int iter;          // finished iterations since reset
+    int evals;         // loss evaluations since reset
+    int log_pos;       // next log slot
+};
+
+enum { STATUS_NONFINITE = 1 };
+
+// One record per finished iteration, written by the decision kernel.
+struct LogEntry {
+    double loss;
+    double lambda;
+    float gmax;
+    int accepted;
+    int retries;
+    int pad;
+};
+constexpr int LOG_CAP = 8192;
+
+// Result of an explicit (stateless) evaluation.
+struct EvalOut {
+    double L;
+    float gmax;
+    int status;
+};
+
+// Gaussian taps t_{-R..R}, R <= MAX_R.
+constexpr int MAX_R = 6;
+struct Taps {
+    int R;
+    float t[2 * MAX_R + 1];
+};
+
+// Where an evaluation reads its field and writes its gradient.
+enum EvalMode {
+    EVAL_EXPLICIT = 0,  // u = u_in, g -> g_out; result to EvalOut
+    EVAL_RESET = 1,     // u = slot 0, g -> slot 0; result initialises state
+    EVAL_TRIAL = 2,     // u = trial slot (1 - cu), g -> trial slot (1 - cg)
+};
+
+// Scalar LNCC / smoothing constants of one evaluation.
+struct LnccConsts {
+    int win;        // k
+    float eps_nr, eps_dr;
+    float shift;    // common intensity shift applied to F and J
+    float inv_k3;   // 1 / k^3
+    float inv_V;    // 1 / V
+    Taps gtaps;     // gradient smoothing taps
+};
+
+// Decision parameters (Eq. lambda-update, Eq. rejection), device copy.
+struct DecideConsts {
+    double lambda0, mu_inc, mu_dec, lambda_max, tau;
+    int reject, max_retries;
+};
+
+// Image element load as float.
+__device__ __forceinline__ float ld_img(const float* p, long long i) {
+    return __ldg(p + i);
+}
+__device__ __forceinline__ float ld_img(const __nv_bfloat16* p, long long i) {
+    return __bfloat162float(p[i]);
+}
+
+// Device-selected slot pointers.
+template <typename T>
+__device__ __forceinline__ T* slot(T* a, T* b, int which) {
+    return which ? b : a;
+}
+
+}  // namespace lmk

@@ -1,0 +1,288 @@
+"""Python binding of the C ABI in include/lmreg.h (argument marshalling only).
+
+Every computation runs in liblmreg.so's CUDA kernels; this module only turns
+torch tensors into device pointers and C structs into Python values.  If the
+library is missing the import of a function raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblmreg.so")
+
+LM_OK, LM_EINVAL, LM_ENOMEM, LM_ECUDA = 0, -1, -2, -3
+LM_ENONFINITE, LM_ETIMEOUT, LM_EUNSUPPORTED, LM_ESTATE = -4, -5, -6, -7
+LM_F32, LM_BF16 = 0, 1
+LM_MAX_LEVELS = 4
+
+
+class LMError(RuntimeError):
+    def __init__(self, code, fn, msg):
+        super().__init__(f"{fn} failed ({code}: {msg})")
+        self.code = code
+
+
+class Volume(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("data", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("win", ctypes.c_int), ("eps_nr", ctypes.c_float),
+                ("eps_dr", ctypes.c_float), ("sigma_grad", ctypes.c_float),
+                ("sigma_warp", ctypes.c_float), ("step", ctypes.c_float),
+                ("lambda0", ctypes.c_double), ("mu_inc", ctypes.c_double),
+                ("mu_dec", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("reject", ctypes.c_int), ("tau", ctypes.c_double),
+                ("max_retries", ctypes.c_int)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int),
+                ("factor", ctypes.c_int * LM_MAX_LEVELS),
+                ("iters", ctypes.c_int * LM_MAX_LEVELS)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_double), ("loss_first", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("gmax", ctypes.c_float),
+                ("accepted", ctypes.c_int), ("retries", ctypes.c_int),
+                ("evals", ctypes.c_int)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_double), ("loss_prev", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("gmax", ctypes.c_float),
+                ("has_prev", ctypes.c_int), ("iter", ctypes.c_int),
+                ("evals", ctypes.c_int), ("kernel_launches", ctypes.c_longlong)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int),
+                ("level_dims", (ctypes.c_int * 3) * LM_MAX_LEVELS),
+                ("level_iters", ctypes.c_int * LM_MAX_LEVELS),
+                ("level_evals", ctypes.c_int * LM_MAX_LEVELS),
+                ("level_accepted", ctypes.c_int * LM_MAX_LEVELS),
+                ("level_loss", ctypes.c_double * LM_MAX_LEVELS),
+                ("final_loss", ctypes.c_double),
+                ("voxel_evals", ctypes.c_longlong),
+                ("wall_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load liblmreg.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build()"
+                          " (the CUDA library has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    V, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "lm_default_params": [ctypes.POINTER(Params)],
+        "lm_init": [ctypes.POINTER(V), ctypes.POINTER(Volume),
+                    ctypes.POINTER(Volume), ctypes.POINTER(Params), V],
+        "lm_eval": [V, V, ctypes.POINTER(D), V, ctypes.POINTER(ctypes.c_float)],
+        "lm_reset": [V, V],
+        "lm_step": [V, V, ctypes.POINTER(StepInfo)],
+        "lm_iterate": [V, V, I, ctypes.POINTER(StepInfo)],
+        "lm_get_state": [V, ctypes.POINTER(State)],
+        "lm_set_state": [V, ctypes.POINTER(State)],
+        "lm_register": [V, ctypes.POINTER(Schedule), V,
+                        ctypes.POINTER(Report)],
+        "lm_state_save": [V, V, ctypes.POINTER(ctypes.c_size_t)],
+        "lm_state_load": [V, V, ctypes.c_size_t],
+        "lm_time_passes": [V, V, I, ctypes.POINTER(D), ctypes.POINTER(D)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = I
+    lib.lm_destroy.argtypes = [V]
+    lib.lm_destroy.restype = None
+    lib.lm_strerror.argtypes = [I]
+    lib.lm_strerror.restype = ctypes.c_char_p
+    lib.lm_last_error.argtypes = []
+    lib.lm_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc, fn):
+    if rc != LM_OK:
+        lib = load()
+        msg = lib.lm_last_error().decode() or lib.lm_strerror(rc).decode()
+        raise LMError(rc, fn, msg)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _volume(t):
+    import torch
+    if not t.is_cuda or not t.is_contiguous() or t.dim() != 3:
+        raise ValueError("images must be contiguous 3-D CUDA tensors")
+    if t.dtype == torch.float32:
+        dt = LM_F32
+    elif t.dtype == torch.bfloat16:
+        dt = LM_BF16
+    else:
+        raise ValueError("images must be float32 or bfloat16")
+    D, H, W = t.shape
+    return Volume(D, H, W, dt, t.data_ptr())
+
+
+def _field_ptr(u, shape=None):
+    import torch
+    if (not u.is_cuda or u.dtype != torch.float32 or not u.is_contiguous()
+            or u.dim() != 4 or u.shape[0] != 3):
+        raise ValueError("fields must be contiguous float32 CUDA tensors of "
+                         "shape (3, D, H, W)")
+    if shape is not None and tuple(u.shape[1:]) != tuple(shape):
+        raise ValueError(f"field shape {tuple(u.shape)} does not match the "
+                         f"images {tuple(shape)}")
+    return ctypes.c_void_p(u.data_ptr())
+
+
+class Context:
+    """Owns an lm_ctx handle and keeps its images alive."""
+
+    def __init__(self, handle, fixed, moving, stream):
+        self.handle = handle
+        self.fixed, self.moving = fixed, moving
+        self.shape = tuple(fixed.shape)
+        self.stream = stream
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.lm_destroy(h)
+
+
+def lm_default_params(**overrides) -> Params:
+    p = Params()
+    _check(load().lm_default_params(ctypes.byref(p)), "lm_default_params")
+    for k, v in overrides.items():
+        setattr(p, "lambda_max" if k == "lambda_max" else k,
+                math.inf if v is None and k == "lambda_max" else v)
+    return p
+
+
+def lm_init(fixed, moving, params: Params | None = None, stream=None):
+    lib = load()
+    vf, vm = _volume(fixed), _volume(moving)
+    h = ctypes.c_void_p()
+    p = ctypes.byref(params) if params is not None else None
+    _check(lib.lm_init(ctypes.byref(h), ctypes.byref(vf), ctypes.byref(vm), p,
+                       _stream_handle(stream)), "lm_init")
+    return Context(h, fixed, moving, stream)
+
+
+def lm_destroy(ctx: Context):
+    h, ctx.handle = ctx.handle, None
+    if h:
+        load().lm_destroy(h)
+
+
+def lm_eval(ctx: Context, u, g_out=None):
+    """Returns (loss, gmax); fills g_out (3, D, H, W) when given."""
+    L = ctypes.c_double()
+    gm = ctypes.c_float()
+    gp = _field_ptr(g_out, ctx.shape) if g_out is not None else None
+    _check(load().lm_eval(ctx.handle, _field_ptr(u, ctx.shape),
+                          ctypes.byref(L), gp, ctypes.byref(gm)), "lm_eval")
+    return L.value, gm.value
+
+
+def lm_reset(ctx: Context, u):
+    _check(load().lm_reset(ctx.handle, _field_ptr(u, ctx.shape)), "lm_reset")
+
+
+def lm_step(ctx: Context, u, info=True):
+    si = StepInfo() if info else None
+    _check(load().lm_step(ctx.handle, _field_ptr(u, ctx.shape),
+                          ctypes.byref(si) if si is not None else None),
+           "lm_step")
+    return si
+
+
+def lm_iterate(ctx: Context, u, n, info=True):
+    si = StepInfo() if info else None
+    _check(load().lm_iterate(ctx.handle, _field_ptr(u, ctx.shape), int(n),
+                             ctypes.byref(si) if si is not None else None),
+           "lm_iterate")
+    return si
+
+
+def lm_get_state(ctx: Context) -> State:
+    s = State()
+    _check(load().lm_get_state(ctx.handle, ctypes.byref(s)), "lm_get_state")
+    return s
+
+
+def lm_set_state(ctx: Context, s: State):
+    _check(load().lm_set_state(ctx.handle, ctypes.byref(s)), "lm_set_state")
+
+
+def lm_register(ctx: Context, levels, u) -> Report:
+    """levels: sequence of (factor, iters)."""
+    s = Schedule()
+    s.nlevels = len(levels)
+    for i, (f, it) in enumerate(levels):
+        s.factor[i] = int(f)
+        s.iters[i] = int(it)
+    r = Report()
+    _check(load().lm_register(ctx.handle, ctypes.byref(s),
+                              _field_ptr(u, ctx.shape), ctypes.byref(r)),
+           "lm_register")
+    return r
+
+
+def lm_state_save(ctx: Context) -> bytes:
+    n = ctypes.c_size_t()
+    _check(load().lm_state_save(ctx.handle, None, ctypes.byref(n)),
+           "lm_state_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().lm_state_save(ctx.handle, buf, ctypes.byref(n)),
+           "lm_state_save")
+    return buf.raw[:n.value]
+
+
+def lm_state_load(ctx: Context, data: bytes):
+    buf = ctypes.create_string_buffer(data, len(data))
+    _check(load().lm_state_load(ctx.handle, buf, len(data)), "lm_state_load")
+
+
+def lm_time_passes(ctx: Context, u, n):
+    """Mean ms per launch of (pass 1 evaluation, pass 2 trial)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().lm_time_passes(ctx.handle, _field_ptr(u, ctx.shape), int(n),
+                                 ctypes.byref(a), ctypes.byref(b)),
+           "lm_time_passes")
+    return a.value, b.value
+
+
+def lm_strerror(code: int) -> str:
+    return load().lm_strerror(int(code)).decode()
+
+
+def lm_last_error() -> str:
+    return load().lm_last_error().decode()
+
+
+#: every function declared in include/lmreg.h
+EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
+            "lm_reset", "lm_step", "lm_iterate", "lm_get_state",
+            "lm_set_state", "lm_register", "lm_state_save", "lm_state_load",
+            "lm_time_passes", "lm_strerror", "lm_last_error")

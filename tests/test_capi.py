@@ -1,0 +1,105 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol
+declared in include/lmreg.h, and validates arguments on the host before any
+CUDA call."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lmreg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_19371_gb300 import build, lmreg
+    build.build()
+    return lmreg.load()
+
+
+def _declared():
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"LM_API\s+[\w\s\*]*?\b(lm_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("lm_init", "lm_step", "lm_register", "lm_destroy",
+              "lm_strerror", "lm_state_save", "lm_state_load"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2603_19371_gb300 import lmreg
+    assert sorted(lmreg.EXPORTED) == _declared()
+
+
+def test_default_params_match_the_paper(lib):
+    from paper_2603_19371_gb300 import lmreg
+    p = lmreg.lm_default_params()
+    # Section 3: lambda0 = 0.006, mu+ = 1.5, mu- = 0.975; Section 3.3: tau 1,
+    # 10 retries, rejection off by default
+    assert p.lambda0 == pytest.approx(0.006)
+    assert p.mu_inc == 1.5 and p.mu_dec == pytest.approx(0.975)
+    assert p.reject == 0 and p.tau == 1.0 and p.max_retries == 10
+    assert math.isinf(p.lambda_max) and p.win == 5
+
+
+def test_strerror(lib):
+    from paper_2603_19371_gb300 import lmreg
+    assert lmreg.lm_strerror(0) == "ok"
+    assert "invalid" in lmreg.lm_strerror(-1)
+    assert lmreg.lm_strerror(-99) == "unknown error"
+
+
+def _init(lib, fixed, moving, params=None):
+    from paper_2603_19371_gb300 import lmreg
+    h = ctypes.c_void_p()
+    p = ctypes.byref(params) if params is not None else None
+    rc = lib.lm_init(ctypes.byref(h), ctypes.byref(fixed),
+                     ctypes.byref(moving), p, None)
+    return rc, lmreg.lm_last_error()
+
+
+def test_init_rejects_bad_arguments_on_host(lib):
+    from paper_2603_19371_gb300 import lmreg
+    V = lmreg.Volume
+    ok = V(4, 4, 4, lmreg.LM_F32, 0x1000)
+    rc, msg = _init(lib, V(0, 4, 4, lmreg.LM_F32, 0x1000), ok)
+    assert rc == lmreg.LM_EINVAL and "dimension" in msg
+    rc, msg = _init(lib, ok, V(4, 4, 5, lmreg.LM_F32, 0x1000))
+    assert rc == lmreg.LM_EINVAL and "shapes differ" in msg
+    rc, msg = _init(lib, ok, V(4, 4, 4, lmreg.LM_BF16, 0x1000))
+    assert rc == lmreg.LM_EINVAL and "dtypes differ" in msg
+    rc, msg = _init(lib, V(4, 4, 4, 7, 0x1000), ok)
+    assert rc == lmreg.LM_EINVAL and "dtype" in msg
+    rc, msg = _init(lib, V(4, 4, 4, lmreg.LM_F32, 0), ok)
+    assert rc == lmreg.LM_EINVAL and "NULL" in msg
+    for field, val, word in [("win", 4, "win"), ("win", 11, "win"),
+                             ("mu_inc", 1.0, "mu_inc"),
+                             ("mu_dec", 1.0, "mu_dec"),
+                             ("lambda0", 0.0, "lambda0"),
+                             ("sigma_grad", 3.0, "sigma"),
+                             ("step", float("nan"), "step"),
+                             ("max_retries", 99, "max_retries"),
+                             ("lambda_max", 1e-9, "lambda_max")]:
+        p = lmreg.lm_default_params()
+        setattr(p, field, val)
+        rc, msg = _init(lib, ok, ok, p)
+        assert rc == lmreg.LM_EINVAL and word in msg, (field, msg)
+
+
+def test_null_arguments(lib):
+    from paper_2603_19371_gb300 import lmreg
+    assert lib.lm_default_params(None) == lmreg.LM_EINVAL
+    assert lib.lm_step(None, None, None) == lmreg.LM_EINVAL
+    assert lib.lm_register(None, None, None, None) == lmreg.LM_EINVAL
+    lib.lm_destroy(None)

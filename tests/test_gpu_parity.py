@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars (per iteration, teacher-forced: both sides start from the GPU's FP32
+state): max |u_gpu - u_oracle| <= 1e-4 voxel, |L_gpu - L_oracle| / L_oracle
+<= 1e-5, the same accept / reject decision and damping.  The gradient itself
+is held to max |g_gpu - g_oracle| <= 1e-4 * gmax (it enters the step only
+through g / gmax).
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_U = 1e-4        # voxels
+TOL_L = 1e-5        # relative
+TOL_G = 1e-4        # relative to gmax
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_19371_gb300 import build, lmreg
+    build.build()
+    lmreg.load()
+    return lmreg
+
+
+def _t(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def _oracle_params(oracle, p):
+    return oracle.params(win=p.win, eps_nr=float(np.float32(p.eps_nr)),
+                         eps_dr=float(np.float32(p.eps_dr)),
+                         sigma_grad=float(p.sigma_grad),
+                         sigma_warp=float(p.sigma_warp), step=float(p.step),
+                         lambda0=p.lambda0, mu_inc=p.mu_inc, mu_dec=p.mu_dec,
+                         lambda_max=p.lambda_max, reject=p.reject, tau=p.tau,
+                         max_retries=p.max_retries)
+
+
+def _images(F, M, dtype):
+    """Device images and the exact values the oracle must see."""
+    import torch
+    if dtype == "bf16":
+        Ft, Mt = _t(F, torch.bfloat16), _t(M, torch.bfloat16)
+        return Ft, Mt, Ft.float().cpu().numpy(), Mt.float().cpu().numpy()
+    return _t(F), _t(M), F.astype(np.float64), M.astype(np.float64)
+
+
+def _eval_check(P, oracle_mod, F, M, u, params, dtype="f32"):
+    import torch
+    Ft, Mt, Fo, Mo = _images(F, M, dtype)
+    ctx = P.lm_init(Ft, Mt, params)
+    ut = _t(u.astype(np.float32))
+    g = torch.empty_like(ut)
+    L, gmax = P.lm_eval(ctx, ut, g)
+    ev = oracle_mod.evaluate(Fo, Mo, u.astype(np.float32).astype(np.float64),
+                             _oracle_params(oracle_mod, params))
+    assert abs(L - ev["L"]) <= TOL_L * abs(ev["L"]) + 1e-12, (L, ev["L"])
+    gg = g.cpu().numpy().astype(np.float64)
+    err = np.abs(gg - ev["g"]).max()
+    assert err <= TOL_G * ev["gmax"], (err, ev["gmax"])
+    assert abs(gmax - ev["gmax"]) <= 1e-4 * ev["gmax"]
+    P.lm_destroy(ctx)
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (13, 17, 29), (5, 7, 3),
+                                   (1, 1, 1), (2, 40, 3)])
+def test_eval_parity_shapes(P, oracle_mod, shape):
+    import synth
+    rng = np.random.default_rng(11)
+    if min(shape) >= 8:
+        F, M, _ = synth.blob_pair(shape, seed=3)
+    else:
+        F = rng.random(shape).astype(np.float32)
+        M = rng.random(shape).astype(np.float32)
+    u = synth.random_field(shape, seed=5, scale=1.7)
+    _eval_check(P, oracle_mod, F, M, u, P.lm_default_params())
+
+
+@pytest.mark.parametrize("win,sg", [(3, 0.0), (5, 1.0), (7, 1.5), (9, 2.0)])
+def test_eval_parity_windows(P, oracle_mod, win, sg):
+    import synth
+    F, M, _ = synth.blob_pair((24, 20, 28), seed=4)
+    u = synth.random_field((24, 20, 28), seed=6, scale=2.2)
+    _eval_check(P, oracle_mod, F, M, u,
+                P.lm_default_params(win=win, sigma_grad=sg))
+
+
+def test_eval_parity_bf16(P, oracle_mod):
+    import synth
+    F, M, _ = synth.blob_pair((32, 32, 32), seed=7)
+    u = synth.random_field((32, 32, 32), seed=8, scale=1.3)
+    _eval_check(P, oracle_mod, F, M, u, P.lm_default_params(), dtype="bf16")
+
+
+def test_identity_gives_zero_loss_and_step(P, oracle_mod):
+    import torch
+    import synth
+    F, _, _ = synth.blob_pair((24, 24, 24), seed=1)
+    Ft = _t(F)
+    ctx = P.lm_init(Ft, Ft.clone(), P.lm_default_params())
+    u = torch.zeros((3, 24, 24, 24), device="cuda")
+    L, gmax = P.lm_eval(ctx, u)
+    assert abs(L) < 1e-7
+    P.lm_reset(ctx, u)
+    info = P.lm_step(ctx, u)
+    assert info.accepted == 1
+    assert float(u.abs().max()) < 1e-6
+
+
+def _teacher_forced(P, oracle_mod, F, M, params, iters, dtype="f32",
+                    u0=None, use_iterate=False):
+    """Run the GPU iteration and check every step against the oracle."""
+    import torch
+    Ft, Mt, Fo, Mo = _images(F, M, dtype)
+    Po = _oracle_params(oracle_mod, params)
+    ctx = P.lm_init(Ft, Mt, params)
+    shape = F.shape
+    u = torch.zeros((3,) + shape, device="cuda") if u0 is None else _t(u0)
+    P.lm_reset(ctx, u)
+    near_ties = 0
+    decisions = []
+    for t in range(iters):
+        st = P.lm_get_state(ctx)
+        ut = u.cpu().numpy().astype(np.float64)
+        ev = oracle_mod.evaluate(Fo, Mo, ut, Po)
+        assert abs(st.loss - ev["L"]) <= TOL_L * ev["L"] + 1e-12, (t, st.loss,
+                                                                  ev["L"])
+        u1, _ = oracle_mod.trial(ut, ev["g"], ev["gmax"], ev["L"], st.lambda_,
+                                 Po)
+        L1 = oracle_mod.loss(Fo, Mo, u1, Po)
+        act, lam_o = oracle_mod.decide(L1, ev["L"], st.loss_prev, st.has_prev,
+                                       st.lambda_, 0, Po)
+        info = (P.lm_iterate(ctx, u, 1) if use_iterate
+                else P.lm_step(ctx, u))
+        assert abs(info.loss_first - L1) <= TOL_L * L1 + 1e-12, (t, info.loss_first, L1)
+        # decision of the first trial
+        margin = abs((L1 - ev["L"]) - (Po.tau * abs(ev["L"] - st.loss_prev)
+                                        if (Po.reject and st.has_prev) else 0.0))
+        tie = margin < 1e-6 * ev["L"]
+        first_rejected = info.retries > 0 or info.accepted == 0
+        if tie:
+            near_ties += 1
+        else:
+            assert first_rejected == (act != oracle_mod.ACCEPT), t
+        if info.retries == 0 and info.accepted == 1 and not tie:
+            assert info.lambda_ == pytest.approx(lam_o, rel=1e-12), t
+            du = np.abs(u.cpu().numpy().astype(np.float64) - u1).max()
+            assert du <= TOL_U, (t, du)
+        decisions.append((info.accepted, info.retries))
+    P.lm_destroy(ctx)
+    assert near_ties <= max(1, iters // 10)
+    return decisions
+
+
+def test_lm_step_parity_blobs(P, oracle_mod):
+    import synth
+    F, M, _ = synth.blob_pair((32, 32, 32), seed=0)
+    params = P.lm_default_params(lambda0=1.0)
+    _teacher_forced(P, oracle_mod, F, M, params, 12)
+
+
+def test_lm_iterate_parity_ragged(P, oracle_mod):
+    import synth
+    F, M, _ = synth.blob_pair((19, 23, 37), seed=2)
+    params = P.lm_default_params(lambda0=0.006, step=1.0)
+    _teacher_forced(P, oracle_mod, F, M, params, 8, use_iterate=True)
+
+
+def test_lm_step_parity_rejection(P, oracle_mod):
+    import synth
+    F, M, _ = synth.blob_pair((24, 24, 24), seed=9)
+    params = P.lm_default_params(lambda0=1e-3, step=3.0, reject=1, tau=1.0,
+                                 lambda_max=1.0, max_retries=4)
+    dec = _teacher_forced(P, oracle_mod, F, M, params, 10)
+    assert any(r > 0 for _, r in dec), dec
+
+
+def test_lm_step_parity_warp_smoothing(P, oracle_mod):
+    import synth
+    F, M, _ = synth.blob_pair((24, 24, 24), seed=10)
+    params = P.lm_default_params(lambda0=0.006, step=1.0, sigma_warp=1.0,
+                                 lambda_max=0.1)
+    _teacher_forced(P, oracle_mod, F, M, params, 6)
+
+
+def test_lm_step_parity_bf16(P, oracle_mod):
+    import synth
+    F, M, _ = synth.blob_pair((32, 32, 32), seed=12)
+    params = P.lm_default_params(lambda0=1.0)
+    _teacher_forced(P, oracle_mod, F, M, params, 6, dtype="bf16")
+
+
+def test_iterate_equals_repeated_steps_and_is_deterministic(P):
+    import torch
+    import synth
+    F, M, _ = synth.blob_pair((32, 32, 32), seed=13)
+    params = P.lm_default_params(lambda0=0.5)
+    outs = []
+    for mode in ("step", "iterate", "iterate"):
+        ctx = P.lm_init(_t(F), _t(M), params)
+        u = torch.zeros((3, 32, 32, 32), device="cuda")
+        P.lm_reset(ctx, u)
+        if mode == "step":
+            for _ in range(7):
+                P.lm_step(ctx, u, info=False)
+            info = P.lm_step(ctx, u)
+        else:
+            info = P.lm_iterate(ctx, u, 8)
+        outs.append((u.cpu().numpy(), info.loss, info.lambda_))
+        P.lm_destroy(ctx)
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[0], outs[0][0])
+        assert o[1] == outs[0][1] and o[2] == outs[0][2]
+
+
+def test_checkpoint_resume_is_bitwise(P):
+    import torch
+    import synth
+    F, M, _ = synth.blob_pair((24, 24, 24), seed=14)
+    params = P.lm_default_params(lambda0=0.3)
+    ctx = P.lm_init(_t(F), _t(M), params)
+    u = torch.zeros((3, 24, 24, 24), device="cuda")
+    P.lm_reset(ctx, u)
+    P.lm_iterate(ctx, u, 5)
+    blob = P.lm_state_save(ctx)
+    u_mid = u.clone()
+    P.lm_iterate(ctx, u, 5)
+    ref = u.cpu().numpy()
+    ref_state = P.lm_get_state(ctx)
+    ctx2 = P.lm_init(_t(F), _t(M), params)
+    u2 = u_mid.clone()
+    P.lm_reset(ctx2, u2)
+    P.lm_state_load(ctx2, blob)
+    P.lm_iterate(ctx2, u2, 5)
+    np.testing.assert_array_equal(u2.cpu().numpy(), ref)
+    s2 = P.lm_get_state(ctx2)
+    assert s2.loss == ref_state.loss and s2.lambda_ == ref_state.lambda_
+
+
+def test_nonfinite_field_is_reported(P):
+    import torch
+    import synth
+    F, M, _ = synth.blob_pair((16, 16, 16), seed=15)
+    ctx = P.lm_init(_t(F), _t(M), P.lm_default_params())
+    u = torch.zeros((3, 16, 16, 16), device="cuda")
+    u[1, 3, 4, 5] = float("nan")
+    with pytest.raises(P.LMError) as e:
+        P.lm_eval(ctx, u)
+    assert e.value.code == P.LM_ENONFINITE
+
+
+def test_step_out_of_order(P):
+    import torch
+    import synth
+    F, M, _ = synth.blob_pair((16, 16, 16), seed=16)
+    ctx = P.lm_init(_t(F), _t(M), P.lm_default_params())
+    u = torch.zeros((3, 16, 16, 16), device="cuda")
+    with pytest.raises(P.LMError) as e:
+        P.lm_step(ctx, u)
+    assert e.value.code == P.LM_ESTATE
+    P.lm_reset(ctx, u)
+    with pytest.raises(P.LMError) as e:
+        P.lm_step(ctx, u.clone())
+    assert e.value.code == P.LM_ESTATE
+
+
+def test_register_multilevel_tracks_oracle(P, oracle_mod):
+    import torch
+    import synth
+    shape = (40, 44, 48)
+    F, M, _ = synth.blob_pair(shape, seed=17, max_disp=2.0)
+    params = P.lm_default_params(lambda0=0.006, step=1.0)
+    ctx = P.lm_init(_t(F), _t(M), params)
+    u = torch.zeros((3,) + shape, device="cuda")
+    rep = P.lm_register(ctx, [(4, 6), (2, 4), (1, 3)], u)
+    uo, log, evals = oracle_mod.register(
+        F.astype(np.float64), M.astype(np.float64),
+        _oracle_params(oracle_mod, params), [4, 2, 1], [6, 4, 3])
+    assert rep.level_iters[0] == 6 and rep.level_iters[2] == 3
+    assert rep.level_dims[0][0] == 10 and rep.level_dims[1][2] == 24
+    assert rep.final_loss == pytest.approx(log[-1], rel=1e-3)
+    assert np.abs(u.cpu().numpy() - uo).max() < 1e-2
+
+
+def test_full_size_eval_and_step(P, oracle_mod):
+    """160x192x224 brain-shaped pair: loss, sampled gradients, one step."""
+    import torch
+    import synth
+    F, M, _ = synth.voronoi_pair((160, 192, 224), seed=0)
+    shape = F.shape
+    params = P.lm_default_params()
+    Po = _oracle_params(oracle_mod, params)
+    u0 = synth.random_field(shape, seed=3, scale=1.5)
+    ctx = P.lm_init(_t(F), _t(M), params)
+    u = _t(u0)
+    g = torch.empty_like(u)
+    L, gmax = P.lm_eval(ctx, u, g)
+    ev = oracle_mod.evaluate(F, M, u0.astype(np.float64), Po)
+    assert abs(L - ev["L"]) <= TOL_L * ev["L"], (L, ev["L"])
+    gg = g.cpu().numpy()
+    rng = np.random.default_rng(0)
+    idx = tuple(rng.integers(0, n, 4000) for n in shape)
+    for c in range(3):
+        err = np.abs(gg[c][idx] - ev["g"][c][idx]).max()
+        assert err <= TOL_G * ev["gmax"]
+    P.lm_reset(ctx, u)
+    st = P.lm_get_state(ctx)
+    info = P.lm_iterate(ctx, u, 1)
+    u1, _ = oracle_mod.trial(u0.astype(np.float64), ev["g"], ev["gmax"],
+                             ev["L"], st.lambda_, Po)
+    if info.accepted and info.retries == 0:
+        du = np.abs(u.cpu().numpy().astype(np.float64) - u1).max()
+        assert du <= TOL_U, du
