@@ -164,7 +164,11 @@ void or_box(int nx, int ny, int nz, int k, const double *X, double *S)
 /* and the partial derivatives of cc with respect to the three J-side  */
 /* window means:                                                       */
 /*   a = d cc / d S_FJ, b = d cc / d S_JJ, c = d cc / d S_J.           */
-/* The clamp on C has zero slope where S_JJ - mJ^2 < 0, so b = 0 there. */
+/* Reading: the clamps only guard against rounding (an exact window    */
+/* variance is never negative), so C's derivative is taken as 1, its   */
+/* value on C >= 0; b = -(A^2 + eps_nr) B / D^2 everywhere.  A slope of */
+/* 0 on the clamped side would let rounding decide a jump of b in      */
+/* windows where J is constant.                                        */
 /* ------------------------------------------------------------------ */
 void or_lncc_terms(int nx, int ny, int nz, int k, double eps_nr,
                    double eps_dr, const double *F, const double *J,
@@ -197,7 +201,7 @@ void or_lncc_terms(int nx, int ny, int nz, int k, double eps_nr,
         double D = B * C + eps_dr;
         double ccv = N / D;
         double av = 2.0 * A / D;
-        double bv = (Craw < 0) ? 0.0 : -N * B / (D * D);
+        double bv = -N * B / (D * D);
         double cv = -av * mF - 2.0 * bv * mJ;
         if (cc) cc[p] = ccv;
         if (a) a[p] = av;

@@ -166,7 +166,8 @@ __device__ __forceinline__ float block_max(float v) {
 // Window moments -> per-voxel (1 - cc) and backward coefficients.
 //   A = S_FJ - mF mJ, B = max(S_FF - mF^2, 0), C = max(S_JJ - mJ^2, 0)
 //   1 - cc = (B C - A^2 + eps_dr - eps_nr) / (B C + eps_dr)
-//   a = 2A/D, b = -(A^2 + eps_nr) B / D^2 (0 where the C clamp is active),
+//   a = 2A/D, b = -(A^2 + eps_nr) B / D^2 (the clamp on C only guards
+//   against rounding; its slope is taken as 1),
 //   c = -a mF - 2 b mJ  (in shifted coordinates)
 // Products are formed with explicit round-to-nearest multiplies so that
 // identical F and J windows give bitwise B == C == A and cc == 1.
@@ -192,7 +193,7 @@ __global__ void k_coef(const float* __restrict__ S, EvalIO io, Geom g,
         float rD = 1.f / D;
         one_m_cc = ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD;
         float a = 2.f * A * rD;
-        float b = (Craw < 0.f) ? 0.f : -N * B * rD * rD;
+        float b = -N * B * rD * rD;
         float cc = -a * mF - 2.f * b * mJ;
         abc[i] = a;
         abc[g.V + i] = b;

@@ -125,3 +125,18 @@ def test_smoothed_gradient_is_smoothed_raw_gradient(oracle_mod):
         np.testing.assert_allclose(ev["g"][i], want, rtol=1e-12, atol=1e-20)
     nrm = np.sqrt((ev["g"] ** 2).sum(0)).max()
     assert ev["gmax"] == pytest.approx(nrm, rel=1e-15)
+
+
+def test_clamp_slope_keeps_b_continuous(oracle_mod):
+    # Reading: max(C, 0) only guards against rounding, so b is the same
+    # expression on both sides of C = 0 and a constant J window gives the
+    # limit of nearly constant windows.
+    rng = np.random.default_rng(7)
+    F = rng.random((7, 7, 7))
+    J0 = np.full((7, 7, 7), 0.625)
+    J1 = J0 + 1e-9 * rng.standard_normal((7, 7, 7))
+    _, _, b0, _ = oracle_mod.lncc_terms(F, J0, 5, 1e-5, 1e-5)
+    _, _, b1, _ = oracle_mod.lncc_terms(F, J1, 5, 1e-5, 1e-5)
+    inner = (slice(2, 5),) * 3
+    np.testing.assert_allclose(b0[inner], b1[inner], rtol=1e-6)
+    assert np.all(b0[inner] < 0)
