@@ -201,14 +201,15 @@ def run_ours(args):
         torch.distributed.barrier()
     P.load()
 
-    F, M, _ = synth.voronoi_pair(SHAPE, seed=rank)
+    shape = tuple(args.shape) if args.shape else SHAPE
+    F, M, _ = synth.voronoi_pair(shape, seed=rank)
     V = F.size
     stream = torch.cuda.Stream()
     params = P.lm_default_params()
     with torch.cuda.stream(stream):
         Ft = torch.from_numpy(F).cuda()
         Mt = torch.from_numpy(M).cuda()
-        u = torch.zeros((3,) + SHAPE, device="cuda")
+        u = torch.zeros((3,) + shape, device="cuda")
     stream.synchronize()
     ctx = P.lm_init(Ft, Mt, params, stream=stream)
     P.lm_reset(ctx, u)
@@ -262,7 +263,7 @@ def run_ours(args):
         levels = [(4, 200), (2, 100), (1, 50)]
         Fh = torch.from_numpy(F).pin_memory()
         Mh = torch.from_numpy(M).pin_memory()
-        uh = torch.empty((3,) + SHAPE).pin_memory()
+        uh = torch.empty((3,) + shape).pin_memory()
         with torch.cuda.stream(stream):
             Fd = torch.empty_like(Ft)
             Md = torch.empty_like(Mt)
@@ -298,7 +299,7 @@ def run_ours(args):
     if rank != 0:
         return 0
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and shape == SHAPE:
         cpu = cpu_baseline(F, M)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
@@ -306,7 +307,9 @@ def run_ours(args):
         "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "voxels": V,
+        "config": {"workload": WORKLOAD if shape == SHAPE else
+                   WORKLOAD.replace("160x192x224", "x".join(map(str, shape))),
+                   "voxels": V,
                    "l2": "no flush: per-iteration working set (F, M, u, "
                          "trial u, two gradients: 385 MB) exceeds the "
                          "129 MB L2",
@@ -330,6 +333,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", type=int, nargs=3, default=None,
+                    metavar=("D", "H", "W"),
+                    help="other pair size (profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

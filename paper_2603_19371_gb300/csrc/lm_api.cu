@@ -2,6 +2,7 @@
 // context scratch, the ordering of the kernels of one LM iteration (with
 // its rejected retries unrolled so no host round trip is needed), CUDA
 // graph replay of iterations, the coarse-to-fine schedule, checkpoints.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -9,6 +10,10 @@
 #include <cstring>
 #include <vector>
 
+#include <cstdlib>
+#include <mutex>
+
+#include "lm_fused.cuh"
 #include "lm_kernels.cuh"
 #include "lm_pyramid.cuh"
 
@@ -125,6 +130,11 @@ struct lm_ctx {
     float* tmpA = nullptr;       // warp smoothing temporaries
     float* tmpB = nullptr;
     StagedScratch sc{};
+    bool staged = false;         // staged evaluation schedule (debug aid)
+    FusedPlan plan{};
+    float* shift = nullptr;      // per-item box-sum shifts (fused)
+    float* dldj = nullptr;       // dL/dJ between the fused kernels
+    float* gdiscard = nullptr;   // gradient sink for lm_eval without g_out
     Partials part{};
     DevState* st = nullptr;
     LogEntry* log = nullptr;
@@ -172,6 +182,9 @@ int dalloc(lm_ctx* c, T** out, size_t bytes) {
     return LM_OK;
 }
 
+int run_eval(lm_ctx* c, int mode, const float* u_in, float* g_out, float* u0,
+             int attempt, cudaStream_t s);
+
 EvalLaunch make_eval(lm_ctx* c, int mode, const float* u_in, float* g_out,
                      float* u0, int attempt) {
     EvalLaunch a;
@@ -192,6 +205,25 @@ EvalLaunch make_eval(lm_ctx* c, int mode, const float* u_in, float* g_out,
     a.part = c->part;
     a.sc = c->sc;
     return a;
+}
+
+// Pass 1 in the context's schedule; returns the number of kernels.
+int run_eval(lm_ctx* c, int mode, const float* u_in, float* g_out, float* u0,
+             int attempt, cudaStream_t s) {
+    EvalLaunch e = make_eval(c, mode, u_in, g_out, u0, attempt);
+    if (c->staged) return eval_staged(e, s);
+    FusedLaunch f;
+    f.g = e.g;
+    f.F = e.F;
+    f.M = e.M;
+    f.dtype = e.dtype;
+    f.io = e.io;
+    f.c = e.c;
+    f.plan = c->plan;
+    f.shift = c->shift;
+    f.dldj = c->dldj;
+    f.part = c->part;
+    return eval_fused(f, s);
 }
 
 FinLaunch make_fin(lm_ctx* c, int mode, int attempt) {
@@ -226,7 +258,7 @@ int enqueue_iteration(lm_ctx* c, float* u, cudaStream_t s) {
         sl.tmpA = c->tmpA;
         sl.tmpB = c->tmpB;
         n += step_compose(sl, s);
-        n += eval_staged(make_eval(c, EVAL_TRIAL, nullptr, nullptr, u, j), s);
+        n += run_eval(c, EVAL_TRIAL, nullptr, nullptr, u, j, s);
         n += finalize(make_fin(c, FIN_DECIDE, j), s);
     }
     return n;
@@ -363,26 +395,63 @@ int lm_init(lm_ctx** out, const lm_volume* fixed, const lm_volume* moving,
 
     const size_t V = (size_t)c->g.V;
     const size_t f4 = sizeof(float);
+    {
+        const char* e = getenv("LMREG_STAGED");
+        c->staged = e && e[0] == '1';
+    }
+    static std::once_flag setup_once;
+    static cudaError_t setup_err = cudaSuccess;
+    std::call_once(setup_once, [] { setup_err = fused_setup(); });
+    if (setup_err != cudaSuccess) {
+        lm_destroy(c);
+        return fail(LM_ECUDA, "kernel setup failed: %s",
+                    cudaGetErrorString(setup_err));
+    }
+    int num_sms = 0;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount,
+                               c->device) != cudaSuccess || num_sms < 1) {
+        cudaGetLastError();
+        num_sms = 148;
+    }
+    c->plan = fused_plan(c->g, num_sms);
     int nl, ng;
-    eval_staged_partials(c->g, &nl, &ng);
+    if (c->staged) {
+        eval_staged_partials(c->g, &nl, &ng);
+    } else {
+        nl = c->plan.e1_items;
+        ng = c->plan.e2_items;
+    }
+    int nl_alloc = std::max(nl, (int)std::min<long long>((c->g.V + 255) / 256, 1024));
     c->part.n_loss = nl;
     c->part.n_g2 = ng;
     if ((rc = dalloc(c, &c->u1, 3 * V * f4)) ||
         (rc = dalloc(c, &c->gs[0], 3 * V * f4)) ||
         (rc = dalloc(c, &c->gs[1], 3 * V * f4)) ||
-        (rc = dalloc(c, &c->sc.J, V * f4)) ||
-        (rc = dalloc(c, &c->sc.dJ, 3 * V * f4)) ||
-        (rc = dalloc(c, &c->sc.S, 5 * V * f4)) ||
-        (rc = dalloc(c, &c->sc.T, 5 * V * f4)) ||
-        (rc = dalloc(c, &c->sc.abc, 3 * V * f4)) ||
-        (rc = dalloc(c, &c->sc.graw, 3 * V * f4)) ||
-        (rc = dalloc(c, &c->part.loss, (size_t)nl * sizeof(double))) ||
+        (rc = dalloc(c, &c->gdiscard, 3 * V * f4)) ||
+        (rc = dalloc(c, &c->part.loss, (size_t)nl_alloc * sizeof(double))) ||
         (rc = dalloc(c, &c->part.g2max, (size_t)ng * sizeof(float))) ||
         (rc = dalloc(c, &c->st, sizeof(DevState))) ||
         (rc = dalloc(c, &c->log, LOG_CAP * sizeof(LogEntry))) ||
         (rc = dalloc(c, &c->eout, sizeof(EvalOut)))) {
         lm_destroy(c);
         return rc;
+    }
+    if (c->staged) {
+        if ((rc = dalloc(c, &c->sc.J, V * f4)) ||
+            (rc = dalloc(c, &c->sc.dJ, 3 * V * f4)) ||
+            (rc = dalloc(c, &c->sc.S, 5 * V * f4)) ||
+            (rc = dalloc(c, &c->sc.T, 5 * V * f4)) ||
+            (rc = dalloc(c, &c->sc.abc, 3 * V * f4)) ||
+            (rc = dalloc(c, &c->sc.graw, 3 * V * f4))) {
+            lm_destroy(c);
+            return rc;
+        }
+    } else {
+        if ((rc = dalloc(c, &c->dldj, V * f4)) ||
+            (rc = dalloc(c, &c->shift, (size_t)c->plan.e1_items * f4))) {
+            lm_destroy(c);
+            return rc;
+        }
     }
     if (c->wtaps.R > 0) {
         if ((rc = dalloc(c, &c->tmpA, 3 * V * f4)) ||
@@ -402,14 +471,16 @@ int lm_init(lm_ctx** out, const lm_volume* fixed, const lm_volume* moving,
         lm_destroy(c);
         return fail(LM_ECUDA, "cudaMemsetAsync failed");
     }
-    // Common shift of the box sums: the mean intensity of F.
-    float mean = 0.f;
-    if ((rc = lmk::image_mean(c->F, c->dtype, c->g.V, c->part.loss, &mean,
-                              c->stream)) != 0) {
-        lm_destroy(c);
-        return fail(LM_ECUDA, "image mean failed");
+    if (c->staged) {
+        // common shift of the staged box sums: the mean intensity of F
+        float mean = 0.f;
+        if ((rc = lmk::image_mean(c->F, c->dtype, c->g.V, c->part.loss,
+                                  &mean, c->stream)) != 0) {
+            lm_destroy(c);
+            return fail(LM_ECUDA, "image mean failed");
+        }
+        c->lc.shift = mean;
     }
-    c->lc.shift = mean;
     *out = c;
     return LM_OK;
 }
@@ -420,10 +491,10 @@ int lm_eval(lm_ctx* c, const float* u, double* loss, float* g_out,
     if (!is_device_ptr(u)) return fail(LM_EINVAL, "u is not a device pointer");
     if (g_out && !is_device_ptr(g_out))
         return fail(LM_EINVAL, "g_out is not a device pointer");
-    // without g_out the gradient lands in a scratch volume the last stage
-    // does not read
-    float* gdst = g_out ? g_out : c->sc.abc;
-    eval_staged(make_eval(c, EVAL_EXPLICIT, u, gdst, (float*)u, 0), c->stream);
+    float* gdst = g_out ? g_out : c->gdiscard;
+    if (!c->staged)
+        fused_tile_shift(c->F, c->dtype, c->g, c->plan, c->shift, c->stream);
+    run_eval(c, EVAL_EXPLICIT, u, gdst, (float*)u, 0, c->stream);
     finalize(make_fin(c, FIN_EXPLICIT, 0), c->stream);
     LM_CK(cudaGetLastError());
     LM_CK(cudaMemcpyAsync(c->h_eout, c->eout, sizeof(EvalOut),
@@ -439,8 +510,11 @@ int lm_eval(lm_ctx* c, const float* u, double* loss, float* g_out,
 int lm_reset(lm_ctx* c, float* u) {
     if (!c) return fail(LM_EINVAL, "ctx is NULL");
     if (!is_device_ptr(u)) return fail(LM_EINVAL, "u is not a device pointer");
-    c->launches = eval_staged(make_eval(c, EVAL_RESET, nullptr, nullptr, u, 0),
-                              c->stream);
+    c->launches = 0;
+    if (!c->staged)
+        c->launches += fused_tile_shift(c->F, c->dtype, c->g, c->plan,
+                                        c->shift, c->stream);
+    c->launches += run_eval(c, EVAL_RESET, nullptr, nullptr, u, 0, c->stream);
     c->launches += finalize(make_fin(c, FIN_RESET, 0), c->stream);
     LM_CK(cudaGetLastError());
     c->bound_u = u;
@@ -643,8 +717,7 @@ extern "C" int lm_time_passes(lm_ctx* c, float* u, int n, double* ms_eval,
     for (int i = 0; i < n; ++i) step_compose(sl, c->stream);
     LM_CK(cudaEventRecord(e1, c->stream));
     for (int i = 0; i < n; ++i)
-        eval_staged(make_eval(c, EVAL_TRIAL, nullptr, nullptr, u, 0),
-                    c->stream);
+        run_eval(c, EVAL_TRIAL, nullptr, nullptr, u, 0, c->stream);
     LM_CK(cudaEventRecord(e2, c->stream));
     LM_CK(cudaEventSynchronize(e2));
     float a = 0.f, b = 0.f;

@@ -55,7 +55,14 @@ def _images(F, M, dtype):
     return _t(F), _t(M), F.astype(np.float64), M.astype(np.float64)
 
 
-def _eval_check(P, oracle_mod, F, M, u, params, dtype="f32"):
+def _worst(err):
+    idx = np.unravel_index(int(np.argmax(err)), err.shape)
+    return f"max err {float(err[idx]):.3e} at {tuple(int(i) for i in idx)}"
+
+
+def _eval_check(P, oracle_mod, F, M, u, params, dtype="f32", atol_L=0.0):
+    """atol_L: absolute floor for cases whose exact loss is ~0 (the per-voxel
+    terms are FP32, unit roundoff 6e-8)."""
     import torch
     Ft, Mt, Fo, Mo = _images(F, M, dtype)
     ctx = P.lm_init(Ft, Mt, params)
@@ -64,17 +71,27 @@ def _eval_check(P, oracle_mod, F, M, u, params, dtype="f32"):
     L, gmax = P.lm_eval(ctx, ut, g)
     ev = oracle_mod.evaluate(Fo, Mo, u.astype(np.float32).astype(np.float64),
                              _oracle_params(oracle_mod, params))
-    assert abs(L - ev["L"]) <= TOL_L * abs(ev["L"]) + 1e-12, (L, ev["L"])
+    assert abs(L - ev["L"]) <= TOL_L * abs(ev["L"]) + atol_L, (L, ev["L"])
     gg = g.cpu().numpy().astype(np.float64)
-    err = np.abs(gg - ev["g"]).max()
-    assert err <= TOL_G * ev["gmax"], (err, ev["gmax"])
+    err = np.abs(gg - ev["g"])
+    assert err.max() <= TOL_G * ev["gmax"], (_worst(err), ev["gmax"])
     assert abs(gmax - ev["gmax"]) <= 1e-4 * ev["gmax"]
     P.lm_destroy(ctx)
+    return err.max() / max(ev["gmax"], 1e-300)
+
+
+@pytest.fixture(params=["fused", "staged"])
+def schedule(request, monkeypatch):
+    if request.param == "staged":
+        monkeypatch.setenv("LMREG_STAGED", "1")
+    else:
+        monkeypatch.delenv("LMREG_STAGED", raising=False)
+    return request.param
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (13, 17, 29), (5, 7, 3),
-                                   (1, 1, 1), (2, 40, 3)])
-def test_eval_parity_shapes(P, oracle_mod, shape):
+                                   (1, 1, 1), (2, 40, 3), (9, 70, 33)])
+def test_eval_parity_shapes(P, oracle_mod, shape, schedule):
     import synth
     rng = np.random.default_rng(11)
     if min(shape) >= 8:
@@ -83,7 +100,9 @@ def test_eval_parity_shapes(P, oracle_mod, shape):
         F = rng.random(shape).astype(np.float32)
         M = rng.random(shape).astype(np.float32)
     u = synth.random_field(shape, seed=5, scale=1.7)
-    _eval_check(P, oracle_mod, F, M, u, P.lm_default_params())
+    tiny = min(shape) < 8
+    _eval_check(P, oracle_mod, F, M, u, P.lm_default_params(),
+                atol_L=1e-7 if tiny else 0.0)
 
 
 @pytest.mark.parametrize("win,sg", [(3, 0.0), (5, 1.0), (7, 1.5), (9, 2.0)])
@@ -154,8 +173,8 @@ def _teacher_forced(P, oracle_mod, F, M, params, iters, dtype="f32",
             assert first_rejected == (act != oracle_mod.ACCEPT), t
         if info.retries == 0 and info.accepted == 1 and not tie:
             assert info.lambda_ == pytest.approx(lam_o, rel=1e-12), t
-            du = np.abs(u.cpu().numpy().astype(np.float64) - u1).max()
-            assert du <= TOL_U, (t, du)
+            err = np.abs(u.cpu().numpy().astype(np.float64) - u1)
+            assert err.max() <= TOL_U, (t, _worst(err), st.lambda_, ev["L"])
         decisions.append((info.accepted, info.retries))
     P.lm_destroy(ctx)
     assert near_ties <= max(1, iters // 10)
@@ -312,12 +331,12 @@ def test_full_size_eval_and_step(P, oracle_mod):
     idx = tuple(rng.integers(0, n, 4000) for n in shape)
     for c in range(3):
         err = np.abs(gg[c][idx] - ev["g"][c][idx]).max()
-        assert err <= TOL_G * ev["gmax"]
+        assert err <= TOL_G * ev["gmax"], (c, err, ev["gmax"])
     P.lm_reset(ctx, u)
     st = P.lm_get_state(ctx)
     info = P.lm_iterate(ctx, u, 1)
     u1, _ = oracle_mod.trial(u0.astype(np.float64), ev["g"], ev["gmax"],
                              ev["L"], st.lambda_, Po)
     if info.accepted and info.retries == 0:
-        du = np.abs(u.cpu().numpy().astype(np.float64) - u1).max()
-        assert du <= TOL_U, du
+        err = np.abs(u.cpu().numpy().astype(np.float64) - u1)
+        assert err.max() <= TOL_U, _worst(err)
