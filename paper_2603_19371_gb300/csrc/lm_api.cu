@@ -132,7 +132,8 @@ struct lm_ctx {
     StagedScratch sc{};
     bool staged = false;         // staged evaluation schedule (debug aid)
     FusedPlan plan{};
-    float* shift = nullptr;      // per-item box-sum shifts (fused)
+    QScale* qs = nullptr;        // fixed-point scale of the window moments
+    float2* mm_part = nullptr;   // image range partials
     float* dldj = nullptr;       // dL/dJ between the fused kernels
     float* gdiscard = nullptr;   // gradient sink for lm_eval without g_out
     Partials part{};
@@ -220,7 +221,7 @@ int run_eval(lm_ctx* c, int mode, const float* u_in, float* g_out, float* u0,
     f.io = e.io;
     f.c = e.c;
     f.plan = c->plan;
-    f.shift = c->shift;
+    f.qs = c->qs;
     f.dldj = c->dldj;
     f.part = c->part;
     return eval_fused(f, s);
@@ -413,13 +414,13 @@ int lm_init(lm_ctx** out, const lm_volume* fixed, const lm_volume* moving,
         cudaGetLastError();
         num_sms = 148;
     }
-    c->plan = fused_plan(c->g, num_sms);
+    c->plan = fused_plan(c->g, prm.win, num_sms);
     int nl, ng;
     if (c->staged) {
         eval_staged_partials(c->g, &nl, &ng);
     } else {
-        nl = c->plan.e1_items;
-        ng = c->plan.e2_items;
+        nl = c->plan.e1_ctas;
+        ng = c->plan.e2_ctas;
     }
     int nl_alloc = std::max(nl, (int)std::min<long long>((c->g.V + 255) / 256, 1024));
     c->part.n_loss = nl;
@@ -448,7 +449,9 @@ int lm_init(lm_ctx** out, const lm_volume* fixed, const lm_volume* moving,
         }
     } else {
         if ((rc = dalloc(c, &c->dldj, V * f4)) ||
-            (rc = dalloc(c, &c->shift, (size_t)c->plan.e1_items * f4))) {
+            (rc = dalloc(c, &c->qs, sizeof(QScale))) ||
+            (rc = dalloc(c, &c->mm_part,
+                         (size_t)c->plan.minmax_ctas * sizeof(float2)))) {
             lm_destroy(c);
             return rc;
         }
@@ -493,7 +496,8 @@ int lm_eval(lm_ctx* c, const float* u, double* loss, float* g_out,
         return fail(LM_EINVAL, "g_out is not a device pointer");
     float* gdst = g_out ? g_out : c->gdiscard;
     if (!c->staged)
-        fused_tile_shift(c->F, c->dtype, c->g, c->plan, c->shift, c->stream);
+        fused_qscale(c->F, c->M, c->dtype, c->g, c->plan, c->p.win,
+                     c->mm_part, c->qs, c->stream);
     run_eval(c, EVAL_EXPLICIT, u, gdst, (float*)u, 0, c->stream);
     finalize(make_fin(c, FIN_EXPLICIT, 0), c->stream);
     LM_CK(cudaGetLastError());
@@ -512,8 +516,8 @@ int lm_reset(lm_ctx* c, float* u) {
     if (!is_device_ptr(u)) return fail(LM_EINVAL, "u is not a device pointer");
     c->launches = 0;
     if (!c->staged)
-        c->launches += fused_tile_shift(c->F, c->dtype, c->g, c->plan,
-                                        c->shift, c->stream);
+        c->launches += fused_qscale(c->F, c->M, c->dtype, c->g, c->plan,
+                                    c->p.win, c->mm_part, c->qs, c->stream);
     c->launches += run_eval(c, EVAL_RESET, nullptr, nullptr, u, 0, c->stream);
     c->launches += finalize(make_fin(c, FIN_RESET, 0), c->stream);
     LM_CK(cudaGetLastError());

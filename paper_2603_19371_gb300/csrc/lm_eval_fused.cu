@@ -1,26 +1,27 @@
 // Pass 1 (loss and smoothed gradient, steps (a)-(c)) as two z-streaming
-// kernels.  Each CTA owns an x-y tile and a z-range and marches along z,
-// keeping the planes of every stage in shared memory; the separable box and
-// Gaussian filters run in x and y on those planes and in z on ring buffers
-// of the last k planes.
+// kernels.  Each CTA owns a column of the volume (an x-y tile) and a range
+// of z, marching along z with the planes of every stage in shared memory;
+// separable box and Gaussian filters run along x and y on the planes and
+// along z on ring buffers of the last k planes.
 //
-//  E1 (lncc): J = M(p + u) (trilinear, Section 2.1); window moments of the
-//     shifted F' = F - s, J' = J - s (box k^3, zero padding); per voxel
-//     (1 - cc) and the backward coefficients (a, b, c) of Section 2.2's
-//     squared-loss form; their box sums; and
+//  E1 (lncc): J = M(p + u) (trilinear, Section 2.1); the LNCC window
+//     moments (k^3 box, zero padding); per voxel (1 - cc) and the backward
+//     coefficients (a, b, c) of the squared-loss form (Section 2.2); their
+//     box sums; and
 //        dL/dJ(y) = -V^-1 [F'(y) Box(a) + 2 J'(y) Box(b) + Box(c)]
 //     written to HBM (4 bytes / voxel), plus the CTA's loss partial.
-//     Halo: 2w voxels of J around the tile (w around the moments).
-//  E2 (grad): dJ/du at the tile and an R-voxel halo, g_raw = dL/dJ * dJ/du,
+//  E2 (grad): dJ/du, g_raw = dL/dJ * dJ/du on the tile and an R halo,
 //     separable Gaussian (R = ceil(3 sigma)), g to HBM, CTA max |g|^2.
+//
+// Window moments are exact: F' = F - s and J' = J - s are rounded to fixed
+// point (Xq = round(X' * Q), |Xq| <= 2^qb) and the window sums of Xq and of
+// the products Xq*Yq are int64, so A, B, C come out of exact integer
+// differences k^3 S_XY - S_X S_Y; only their final conversion rounds.  The
+// variance cancellation that FP32 window sums suffer in flat regions is
+// gone.  Everything after the moments is FP32.
 //
 // HBM traffic per voxel: E1 reads F, M, u (20 B) and writes dL/dJ (4 B);
 // E2 reads dL/dJ, M, u (20 B) and writes g (12 B).  Halo re-reads hit L2.
-//
-// The shift s is one value per E1 work item (the mean of F over the item's
-// tile), so the window moments are formed from values near zero; moments,
-// cc and the gradient are exactly shift-invariant in exact arithmetic
-// because out-of-volume cells carry -s as well.
 #include <algorithm>
 
 #include "lm_fused.cuh"
@@ -28,8 +29,9 @@
 namespace lmk {
 namespace {
 
-constexpr int E1_TX = 32, E1_TY = 8, E1_NT = 256;
-constexpr int E2_TX = 32, E2_TY = 16, E2_NT = 256;
+constexpr int NT = 512;       // threads per CTA (both kernels)
+constexpr int PLANE_X = 32;   // E1 moment plane / E2 output tile width
+constexpr int PLANE_Y = 16;   // and height
 
 __device__ __forceinline__ float safe_floor(float v) {
     return fminf(fmaxf(floorf(v), -1048576.f), 1048576.f);
@@ -41,7 +43,7 @@ __device__ __forceinline__ void corners(const T* __restrict__ M,
                                         const float* __restrict__ u,
                                         const Geom& g, int x, int y, int z,
                                         long long i, float m[8], float f[3]) {
-    float d0 = u[i], d1 = u[g.V + i], d2 = u[2 * g.V + i];
+    float d0 = __ldg(u + i), d1 = __ldg(u + g.V + i), d2 = __ldg(u + 2 * g.V + i);
     float l0 = safe_floor(d0), l1 = safe_floor(d1), l2 = safe_floor(d2);
     f[0] = d0 - l0;
     f[1] = d1 - l1;
@@ -71,7 +73,7 @@ __device__ __forceinline__ void corners(const T* __restrict__ M,
     }
 }
 
-// J from the corners (m index = x + 2y + 4z).
+// J from the corners (corner index = x + 2y + 4z).
 __device__ __forceinline__ float interp(const float m[8], const float f[3]) {
     float a0 = m[0] + f[0] * (m[1] - m[0]);
     float a1 = m[2] + f[0] * (m[3] - m[2]);
@@ -98,302 +100,440 @@ __device__ __forceinline__ void interp_grad(const float m[8], const float f[3],
     d[2] = b1 - b0;
 }
 
+// Contiguous share of the (column, slice) work of CTA b out of n: the CTA
+// walks segments [col, z0, z1) covering work units [lo, hi).
+struct Share {
+    long long lo, hi;
+};
+__device__ __forceinline__ Share share_of(int b, int n, long long total) {
+    Share s;
+    s.lo = total * b / n;
+    s.hi = total * (b + 1) / n;
+    return s;
+}
+
+// ----------------------------------------------------------------------
+// E1
+// ----------------------------------------------------------------------
 template <int W>
-struct E1Smem {
+struct E1Cfg {
     static constexpr int K = 2 * W + 1;
-    static constexpr int GX = E1_TX + 4 * W, GY = E1_TY + 4 * W;
-    static constexpr int SX = E1_TX + 2 * W, SY = E1_TY + 2 * W;
-    static constexpr int P = 5 * GY * GX;            // products, gather plane
-    static constexpr int X = 5 * GY * SX;            // x-boxed
-    static constexpr int SR = K * 5 * SY * SX;       // xy-boxed ring
-    static constexpr int AB = 3 * SY * SX;           // a, b, c
-    static constexpr int AX = 3 * SY * E1_TX;        // x-boxed a, b, c
-    static constexpr int BR = K * 3 * E1_TY * E1_TX; // xy-boxed ring
-    static constexpr int JR = K * E1_TY * E1_TX;     // J' delay line
-    static constexpr int floats = P + X + SR + AB + AX + BR + JR;
+    static constexpr int SX = PLANE_X, SY = PLANE_Y;   // moment plane
+    static constexpr int TX = SX - 2 * W, TY = SY - 2 * W;  // output tile
+    static constexpr int GX = SX + 2 * W, GY = SY + 2 * W;  // gather plane
+    static constexpr int GXP = (GX + 3) / 4 * 4;            // padded stride
+    static constexpr int NXU = GY * (SX / 2);   // x-pass units (2 outputs)
+    static constexpr int NX2U = 3 * SY * (TX / 2);
+    // shared memory (bytes), 16-byte aligned sections
+    static constexpr int B_GQ = 2 * GY * GXP * 4;
+    static constexpr int B_X32 = 2 * GY * SX * 4;
+    static constexpr int B_X64 = 3 * GY * SX * 8;
+    static constexpr int B_ZR32 = K * 2 * NT * 4;
+    static constexpr int B_ZR64 = K * 3 * NT * 8;
+    static constexpr int B_AB = 3 * SY * SX * 4;
+    static constexpr int B_AX = 3 * SY * TX * 4;
+    static constexpr int bytes =
+        B_GQ + B_X32 + B_X64 + B_ZR32 + B_ZR64 + B_AB + B_AX;
 };
 
 template <int W, typename T>
-__global__ void __launch_bounds__(E1_NT)
+__global__ void __launch_bounds__(NT, 1)
     k_e1(const T* __restrict__ F, const T* __restrict__ M, EvalIO io, Geom g,
-         LnccConsts c, FusedPlan pl, const float* __restrict__ shift,
+         LnccConsts c, FusedPlan pl, const QScale* __restrict__ qs,
          float* __restrict__ dldj, double* __restrict__ loss_part) {
-    using S = E1Smem<W>;
-    constexpr int K = S::K, GX = S::GX, GY = S::GY, SX = S::SX, SY = S::SY;
-    constexpr int TX = E1_TX, TY = E1_TY;
-    extern __shared__ float sm[];
-    float* Pg = sm;
-    float* Sx = Pg + S::P;
-    float* Sr = Sx + S::X;
-    float* Ab = Sr + S::SR;
-    float* Ax = Ab + S::AB;
-    float* Br = Ax + S::AX;
-    float* Jr = Br + S::BR;
-    __shared__ double red[E1_NT / 32];
+    using C = E1Cfg<W>;
+    constexpr int K = C::K, SX = C::SX, SY = C::SY, TX = C::TX, TY = C::TY;
+    constexpr int GX = C::GX, GY = C::GY, GXP = C::GXP;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* GqF = (int*)smem;
+    int* GqJ = GqF + GY * GXP;
+    int* XF = (int*)(smem + C::B_GQ);
+    int* XJ = XF + GY * SX;
+    long long* XFF = (long long*)(smem + C::B_GQ + C::B_X32);
+    long long* XJJ = XFF + GY * SX;
+    long long* XFJ = XJJ + GY * SX;
+    int* ZR32 = (int*)(smem + C::B_GQ + C::B_X32 + C::B_X64);
+    long long* ZR64 =
+        (long long*)(smem + C::B_GQ + C::B_X32 + C::B_X64 + C::B_ZR32);
+    float* Ab = (float*)(smem + C::B_GQ + C::B_X32 + C::B_X64 + C::B_ZR32 +
+                         C::B_ZR64);
+    float* Ax = Ab + 3 * SY * SX;
+    __shared__ double red[NT / 32];
 
     if (eval_skip(io)) return;
-    const int item = blockIdx.x;
-    const int tx_ = item % pl.e1_tx;
-    const int rest = item / pl.e1_tx;
-    const int ty_ = rest % pl.e1_ty;
-    const int zi = rest / pl.e1_ty;
-    const int x0 = tx_ * TX, y0 = ty_ * TY;
-    const int z0 = zi * pl.e1_zc;
-    const int z1 = min(z0 + pl.e1_zc, g.nz);
-    const float sh = shift[item];
+    const int tid = threadIdx.x;
     const float* __restrict__ u = eval_u(io);
     const long long sxy = (long long)g.nx * g.ny;
-    const int tid = threadIdx.x;
-    double lacc = 0.0;
+    const float sh = qs->shift, Q = qs->Q, iQ = qs->invQ;
+    const int qlim = qs->qlim;
+    const int qpad = __float2int_rn(-sh * Q);
+    const long long k3 = (long long)K * K * K;
+    // exact moment differences are k^6 Q^2 times the moments
+    const float mscale = c.inv_k3 * c.inv_k3 * iQ * iQ;
+    const float m1scale = c.inv_k3 * iQ;
 
-    const int s_begin = z0 - 2 * W, s_end = z1 + 2 * W;
-    for (int s = s_begin, t = 0; s < s_end; ++s, ++t) {
-        // (1) gather plane: F', J' and the five products
-        const bool zin = s >= 0 && s < g.nz;
-        for (int idx = tid; idx < GX * GY; idx += E1_NT) {
-            int gy = idx / GX, gx = idx - gy * GX;
-            int x = x0 - 2 * W + gx, y = y0 - 2 * W + gy;
-            float fp = -sh, jp = -sh;
-            if (zin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
-                long long i = (long long)s * sxy + (long long)y * g.nx + x;
-                float m[8], f[3];
-                corners(M, u, g, x, y, s, i, m, f);
-                fp = ld_img(F, i) - sh;
-                jp = interp(m, f) - sh;
-            }
-            Pg[idx] = fp;
-            Pg[GY * GX + idx] = jp;
-            Pg[2 * GY * GX + idx] = fp * fp;
-            Pg[3 * GY * GX + idx] = jp * jp;
-            Pg[4 * GY * GX + idx] = fp * jp;
-            int ox = gx - 2 * W, oy = gy - 2 * W;
-            if (ox >= 0 && ox < TX && oy >= 0 && oy < TY)
-                Jr[(t % K) * TY * TX + oy * TX + ox] = jp;
+    // this thread's moment-plane point and output point
+    const int sx = tid & (SX - 1), sy = tid / SX;
+    const bool has_o = tid < TX * TY;
+    const int ox = has_o ? tid % TX : 0, oy = has_o ? tid / TX : 0;
+
+    double lacc = 0.0;
+    bool bad = false;
+    const long long total = (long long)pl.e1_cx * pl.e1_cy * g.nz;
+    const Share sh_ = share_of(blockIdx.x, gridDim.x, total);
+    long long w0 = sh_.lo;
+    while (w0 < sh_.hi) {
+        const long long col = w0 / g.nz;
+        const int z0 = (int)(w0 - col * g.nz);
+        const long long zl = z0 + (sh_.hi - w0);
+        const int z1 = zl < g.nz ? (int)zl : g.nz;
+        w0 += z1 - z0;
+        const int x0 = (int)(col % pl.e1_cx) * TX;
+        const int y0 = (int)(col / pl.e1_cx) * TY;
+
+        // ring and running sums restart for every segment
+        for (int k = 0; k < K; ++k) {
+            ZR32[(k * 2 + 0) * NT + tid] = 0;
+            ZR32[(k * 2 + 1) * NT + tid] = 0;
+            ZR64[(k * 3 + 0) * NT + tid] = 0;
+            ZR64[(k * 3 + 1) * NT + tid] = 0;
+            ZR64[(k * 3 + 2) * NT + tid] = 0;
         }
-        __syncthreads();
-        // (2) box along x
-        for (int idx = tid; idx < 5 * GY * SX; idx += E1_NT) {
-            int q = idx / (GY * SX);
-            int r2 = idx - q * (GY * SX);
-            int gy = r2 / SX, sx = r2 - gy * SX;
-            const float* row = Pg + q * GY * GX + gy * GX + sx;
-            float v = 0.f;
+        int runF = 0, runJ = 0;
+        long long runFF = 0, runJJ = 0, runFJ = 0;
+        float r2[3][K];
+        float dF[K], dJ[K];
 #pragma unroll
-            for (int o = 0; o < K; ++o) v += row[o];
-            Sx[idx] = v;
+        for (int k = 0; k < K; ++k) {
+            r2[0][k] = r2[1][k] = r2[2][k] = 0.f;
+            dF[k] = dJ[k] = 0.f;
         }
-        __syncthreads();
-        // (3) box along y into the ring; along z once the ring is full; the
-        //     moments give (1 - cc) and (a, b, c) at slice cz = s - W
-        const int cz = s - W;
-        const bool coef_valid = t >= 2 * W;
-        for (int idx = tid; idx < SY * SX; idx += E1_NT) {
-            int sy = idx / SX, sx = idx - sy * SX;
+        const int s_begin = z0 - 2 * W, s_end = z1 + 2 * W;
+        for (int base = s_begin; base < s_end; base += K) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const float* col = Sx + q * GY * SX + sy * SX + sx;
-                float v = 0.f;
-#pragma unroll
-                for (int o = 0; o < K; ++o) v += col[o * SX];
-                Sr[((t % K) * 5 + q) * SY * SX + idx] = v;
-            }
-            if (!coef_valid) continue;
-            float m5[5];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                float v = 0.f;
-#pragma unroll
-                for (int j = 0; j < K; ++j)
-                    v += Sr[(((t - 2 * W + j) % K) * 5 + q) * SY * SX + idx];
-                m5[q] = v * c.inv_k3;
-            }
-            int x = x0 - W + sx, y = y0 - W + sy;
-            float av = 0.f, bv = 0.f, cv = 0.f;
-            if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && cz >= 0 &&
-                cz < g.nz) {
-                float mF = m5[0], mJ = m5[1];
-                float A = __fmaf_rn(-mF, mJ, m5[4]);
-                float B = fmaxf(__fmaf_rn(-mF, mF, m5[2]), 0.f);
-                float C = fmaxf(__fmaf_rn(-mJ, mJ, m5[3]), 0.f);
-                float BC = __fmul_rn(B, C), AA = __fmul_rn(A, A);
-                float N = AA + c.eps_nr;
-                float D = BC + c.eps_dr;
-                float rD = 1.f / D;
-                av = 2.f * A * rD;
-                bv = -N * B * rD * rD;
-                cv = -av * mF - 2.f * bv * mJ;
-                if (sx >= W && sx < W + TX && sy >= W && sy < W + TY &&
-                    cz >= z0 && cz < z1)
-                    lacc += (double)(((BC - AA) + (c.eps_dr - c.eps_nr)) * rD);
-            }
-            Ab[idx] = av;
-            Ab[SY * SX + idx] = bv;
-            Ab[2 * SY * SX + idx] = cv;
-        }
-        __syncthreads();
-        if (coef_valid) {
-            // (4) box of (a, b, c) along x
-            for (int idx = tid; idx < 3 * SY * TX; idx += E1_NT) {
-                int q = idx / (SY * TX);
-                int r2 = idx - q * (SY * TX);
-                int sy = r2 / TX, tx = r2 - sy * TX;
-                const float* row = Ab + q * SY * SX + sy * SX + tx;
-                float v = 0.f;
-#pragma unroll
-                for (int o = 0; o < K; ++o) v += row[o];
-                Ax[idx] = v;
-            }
-            __syncthreads();
-            // (5) along y into the second ring, along z, then dL/dJ at
-            //     slice r = s - 2W
-            const int tc = t - 2 * W;
-            const bool out_valid = tc >= 2 * W;
-            const int r = cz - W;
-            for (int idx = tid; idx < TY * TX; idx += E1_NT) {
-                int ty = idx / TX, tx = idx - ty * TX;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const float* col = Ax + q * SY * TX + ty * TX + tx;
-                    float v = 0.f;
-#pragma unroll
-                    for (int o = 0; o < K; ++o) v += col[o * TX];
-                    Br[((tc % K) * 3 + q) * TY * TX + idx] = v;
+            for (int j = 0; j < K; ++j) {
+                const int s = base + j;
+                if (s >= s_end) break;
+                const int t = s - s_begin;
+                // (1) gather plane: quantised F', J'
+                const bool zin = s >= 0 && s < g.nz;
+                for (int idx = tid; idx < GX * GY; idx += NT) {
+                    int gy = idx / GX, gx = idx - gy * GX;
+                    int x = x0 - 2 * W + gx, y = y0 - 2 * W + gy;
+                    int fq = qpad, jq = qpad;
+                    if (zin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+                        long long i = (long long)s * sxy + (long long)y * g.nx + x;
+                        float m[8], f[3];
+                        corners(M, u, g, x, y, s, i, m, f);
+                        float fv = ld_img(F, i), jv = interp(m, f);
+                        if (!isfinite(fv) || !isfinite(jv)) bad = true;
+                        fq = min(max(__float2int_rn((fv - sh) * Q), -qlim), qlim);
+                        jq = min(max(__float2int_rn((jv - sh) * Q), -qlim), qlim);
+                    }
+                    GqF[gy * GXP + gx] = fq;
+                    GqJ[gy * GXP + gx] = jq;
                 }
-                if (!out_valid) continue;
-                float b3[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    float v = 0.f;
-#pragma unroll
-                    for (int j = 0; j < K; ++j)
-                        v += Br[(((tc - 2 * W + j) % K) * 3 + q) * TY * TX + idx];
-                    b3[q] = v;
+                __syncthreads();
+                // delay line of F', J' for this thread's output point
+                if (has_o) {
+                    int gi = (oy + 2 * W) * GXP + ox + 2 * W;
+                    dF[j] = (float)GqF[gi] * iQ;
+                    dJ[j] = (float)GqJ[gi] * iQ;
                 }
-                int x = x0 + tx, y = y0 + ty;
-                if (x < g.nx && y < g.ny) {
-                    long long i = (long long)r * sxy + (long long)y * g.nx + x;
-                    float fp = ld_img(F, i) - sh;
-                    float jp = Jr[((t - 2 * W) % K) * TY * TX + idx];
-                    dldj[i] = -c.inv_V *
-                              ((fp * b3[0] + 2.f * jp * b3[1] + b3[2]) * c.inv_k3);
+                // (2) window sums along x: two outputs per unit
+                for (int uidx = tid; uidx < C::NXU; uidx += NT) {
+                    int gy = uidx / (SX / 2);
+                    int p = uidx - gy * (SX / 2);
+                    const int* rf = GqF + gy * GXP + 2 * p;
+                    const int* rj = GqJ + gy * GXP + 2 * p;
+                    int vf[K + 1], vj[K + 1];
+#pragma unroll
+                    for (int o = 0; o < K + 1; ++o) {
+                        vf[o] = rf[o];
+                        vj[o] = rj[o];
+                    }
+                    int sf = 0, sj = 0;
+                    long long sff = 0, sjj = 0, sfj = 0;
+#pragma unroll
+                    for (int o = 0; o < K; ++o) {
+                        sf += vf[o];
+                        sj += vj[o];
+                        sff += (long long)vf[o] * vf[o];
+                        sjj += (long long)vj[o] * vj[o];
+                        sfj += (long long)vf[o] * vj[o];
+                    }
+                    int o1 = gy * SX + 2 * p;
+                    XF[o1] = sf;
+                    XJ[o1] = sj;
+                    XFF[o1] = sff;
+                    XJJ[o1] = sjj;
+                    XFJ[o1] = sfj;
+                    sf += vf[K] - vf[0];
+                    sj += vj[K] - vj[0];
+                    sff += (long long)vf[K] * vf[K] - (long long)vf[0] * vf[0];
+                    sjj += (long long)vj[K] * vj[K] - (long long)vj[0] * vj[0];
+                    sfj += (long long)vf[K] * vj[K] - (long long)vf[0] * vj[0];
+                    XF[o1 + 1] = sf;
+                    XJ[o1 + 1] = sj;
+                    XFF[o1 + 1] = sff;
+                    XJJ[o1 + 1] = sjj;
+                    XFJ[o1 + 1] = sfj;
                 }
+                __syncthreads();
+                // (3) along y, then the z running sums (exact) and, once K
+                //     slices are in, the moments at slice cz = s - W
+                {
+                    int yf = 0, yj = 0;
+                    long long yff = 0, yjj = 0, yfj = 0;
+#pragma unroll
+                    for (int o = 0; o < K; ++o) {
+                        int a = (sy + o) * SX + sx;
+                        yf += XF[a];
+                        yj += XJ[a];
+                        yff += XFF[a];
+                        yjj += XJJ[a];
+                        yfj += XFJ[a];
+                    }
+                    int* zr = ZR32 + j * 2 * NT + tid;
+                    long long* zr64 = ZR64 + j * 3 * NT + tid;
+                    runF += yf - zr[0];
+                    runJ += yj - zr[NT];
+                    runFF += yff - zr64[0];
+                    runJJ += yjj - zr64[NT];
+                    runFJ += yfj - zr64[2 * NT];
+                    zr[0] = yf;
+                    zr[NT] = yj;
+                    zr64[0] = yff;
+                    zr64[NT] = yjj;
+                    zr64[2 * NT] = yfj;
+                }
+                const int cz = s - W;
+                const bool coef_valid = t >= 2 * W;
+                if (coef_valid) {
+                    int x = x0 - W + sx, y = y0 - W + sy;
+                    float av = 0.f, bv = 0.f, cv = 0.f;
+                    if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && cz >= 0 &&
+                        cz < g.nz) {
+                        long long Ai = k3 * runFJ - (long long)runF * runJ;
+                        long long Bi = k3 * runFF - (long long)runF * runF;
+                        long long Ci = k3 * runJJ - (long long)runJ * runJ;
+                        float A = (float)Ai * mscale;
+                        float B = (float)Bi * mscale;
+                        float Cm = (float)Ci * mscale;
+                        float mF = (float)runF * m1scale;
+                        float mJ = (float)runJ * m1scale;
+                        float BC = __fmul_rn(B, Cm), AA = __fmul_rn(A, A);
+                        float N = AA + c.eps_nr;
+                        float D = BC + c.eps_dr;
+                        float rD = 1.f / D;
+                        av = 2.f * A * rD;
+                        bv = -N * B * rD * rD;
+                        cv = -av * mF - 2.f * bv * mJ;
+                        if (sx >= W && sx < W + TX && sy >= W && sy < W + TY &&
+                            cz >= z0 && cz < z1)
+                            lacc += (double)(((BC - AA) + (c.eps_dr - c.eps_nr)) *
+                                             rD);
+                    }
+                    Ab[sy * SX + sx] = av;
+                    Ab[SY * SX + sy * SX + sx] = bv;
+                    Ab[2 * SY * SX + sy * SX + sx] = cv;
+                }
+                __syncthreads();
+                if (coef_valid) {
+                    // (4) box of (a, b, c) along x: two outputs per unit
+                    for (int uidx = tid; uidx < C::NX2U; uidx += NT) {
+                        int row = uidx / (TX / 2);   // q * SY + sy
+                        int p = uidx - row * (TX / 2);
+                        const float* r = Ab + row * SX + 2 * p;
+                        float v[K + 1];
+#pragma unroll
+                        for (int o = 0; o < K + 1; ++o) v[o] = r[o];
+                        float s0 = 0.f;
+#pragma unroll
+                        for (int o = 0; o < K; ++o) s0 += v[o];
+                        float s1 = 0.f;
+#pragma unroll
+                        for (int o = 1; o < K + 1; ++o) s1 += v[o];
+                        Ax[row * TX + 2 * p] = s0;
+                        Ax[row * TX + 2 * p + 1] = s1;
+                    }
+                    __syncthreads();
+                    // (5) along y into the register ring, along z, dL/dJ at
+                    //     slice r = s - 2W
+                    if (has_o) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            float v = 0.f;
+#pragma unroll
+                            for (int o = 0; o < K; ++o)
+                                v += Ax[(q * SY + oy + o) * TX + ox];
+                            r2[q][j] = v;
+                        }
+                        const int r = cz - W;
+                        const int x = x0 + ox, y = y0 + oy;
+                        if (t >= 4 * W && x < g.nx && y < g.ny) {
+                            float b3[3];
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                float v = 0.f;
+#pragma unroll
+                                for (int i2 = 0; i2 < K; ++i2)
+                                    v += r2[q][(j + 1 + i2) % K];
+                                b3[q] = v;
+                            }
+                            const int jd = (j + 1) % K;
+                            long long i = (long long)r * sxy + (long long)y * g.nx + x;
+                            dldj[i] = -c.inv_V * ((dF[jd] * b3[0] +
+                                                   2.f * dJ[jd] * b3[1] + b3[2]) *
+                                                  c.inv_k3);
+                        }
+                    }
+                }
+                __syncthreads();
             }
         }
-        __syncthreads();
     }
-    // CTA loss partial, fixed-order FP64 reduction
+    if (bad) lacc = __longlong_as_double(0x7ff8000000000000LL);   // NaN
     for (int o = 16; o > 0; o >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, o);
     if ((tid & 31) == 0) red[tid >> 5] = lacc;
     __syncthreads();
     if (tid == 0) {
         double v = 0.0;
-        for (int w = 0; w < E1_NT / 32; ++w) v += red[w];
-        loss_part[item] = v;
+        for (int w = 0; w < NT / 32; ++w) v += red[w];
+        loss_part[blockIdx.x] = v;
     }
 }
 
+// ----------------------------------------------------------------------
+// E2
+// ----------------------------------------------------------------------
 template <int R>
-struct E2Smem {
+struct E2Cfg {
     static constexpr int KG = 2 * R + 1;
-    static constexpr int RX = E2_TX + 2 * R, RY = E2_TY + 2 * R;
-    static constexpr int GR = 3 * RY * RX;
-    static constexpr int GXs = 3 * RY * E2_TX;
-    static constexpr int GQ = KG * 3 * E2_TY * E2_TX;
-    static constexpr int floats = GR + GXs + GQ;
+    static constexpr int TX = PLANE_X, TY = PLANE_Y;
+    static constexpr int RX = TX + 2 * R, RY = TY + 2 * R;
+    static constexpr int RXP = (RX + 3) / 4 * 4;
+    static constexpr int NXU = 3 * RY * (TX / 4);   // x-pass units (4 outputs)
+    static constexpr int bytes = (3 * RY * RXP + 3 * RY * TX) * 4;
 };
 
 template <int R, typename T>
-__global__ void __launch_bounds__(E2_NT)
+__global__ void __launch_bounds__(NT, 2)
     k_e2(const T* __restrict__ M, EvalIO io, Geom g, Taps tp, FusedPlan pl,
          const float* __restrict__ dldj, float* __restrict__ g2_part) {
-    using S = E2Smem<R>;
-    constexpr int KG = S::KG, RX = S::RX, RY = S::RY;
-    constexpr int TX = E2_TX, TY = E2_TY;
-    extern __shared__ float sm[];
-    float* Gr = sm;
-    float* Gx = Gr + S::GR;
-    float* Gq = Gx + S::GXs;
-    __shared__ float red[E2_NT / 32];
+    using C = E2Cfg<R>;
+    constexpr int KG = C::KG, RX = C::RX, RY = C::RY, RXP = C::RXP;
+    constexpr int TX = C::TX, TY = C::TY;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* Gr = (float*)smem;            // [3][RY][RXP]
+    float* Gx = Gr + 3 * RY * RXP;       // [3][RY][TX]
+    __shared__ float red[NT / 32];
 
     if (eval_skip(io)) return;
-    const int item = blockIdx.x;
-    const int tx_ = item % pl.e2_tx;
-    const int rest = item / pl.e2_tx;
-    const int ty_ = rest % pl.e2_ty;
-    const int zi = rest / pl.e2_ty;
-    const int x0 = tx_ * TX, y0 = ty_ * TY;
-    const int z0 = zi * pl.e2_zc;
-    const int z1 = min(z0 + pl.e2_zc, g.nz);
+    const int tid = threadIdx.x;
     const float* __restrict__ u = eval_u(io);
     float* __restrict__ gout = eval_g(io);
     const long long sxy = (long long)g.nx * g.ny;
-    const int tid = threadIdx.x;
+    const int ox = tid & (TX - 1), oy = tid / TX;
+    float tt[KG];
+#pragma unroll
+    for (int j = 0; j < KG; ++j) tt[j] = tp.t[j];
     float m2 = 0.f;
 
-    for (int s = z0 - R, t = 0; s < z1 + R; ++s, ++t) {
-        const bool zin = s >= 0 && s < g.nz;
-        // (1) g_raw = dL/dJ * dJ/du on the tile and its R halo
-        for (int idx = tid; idx < RX * RY; idx += E2_NT) {
-            int ry = idx / RX, rx = idx - ry * RX;
-            int x = x0 - R + rx, y = y0 - R + ry;
-            float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-            if (zin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
-                long long i = (long long)s * sxy + (long long)y * g.nx + x;
-                float m[8], f[3], d[3];
-                corners(M, u, g, x, y, s, i, m, f);
-                interp_grad(m, f, d);
-                float dl = dldj[i];
-                g0 = dl * d[0];
-                g1 = dl * d[1];
-                g2 = dl * d[2];
+    const long long total = (long long)pl.e2_cx * pl.e2_cy * g.nz;
+    const Share sh_ = share_of(blockIdx.x, gridDim.x, total);
+    long long w0 = sh_.lo;
+    while (w0 < sh_.hi) {
+        const long long col = w0 / g.nz;
+        const int z0 = (int)(w0 - col * g.nz);
+        const long long zl = z0 + (sh_.hi - w0);
+        const int z1 = zl < g.nz ? (int)zl : g.nz;
+        w0 += z1 - z0;
+        const int x0 = (int)(col % pl.e2_cx) * TX;
+        const int y0 = (int)(col / pl.e2_cx) * TY;
+        float ring[3][KG];
+#pragma unroll
+        for (int k = 0; k < KG; ++k) ring[0][k] = ring[1][k] = ring[2][k] = 0.f;
+        const int s_begin = z0 - R, s_end = z1 + R;
+        for (int base = s_begin; base < s_end; base += KG) {
+#pragma unroll
+            for (int j = 0; j < KG; ++j) {
+                const int s = base + j;
+                if (s >= s_end) break;
+                const int t = s - s_begin;
+                // (1) g_raw on the tile and its R halo
+                const bool zin = s >= 0 && s < g.nz;
+                for (int idx = tid; idx < RX * RY; idx += NT) {
+                    int ry = idx / RX, rx = idx - ry * RX;
+                    int x = x0 - R + rx, y = y0 - R + ry;
+                    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+                    if (zin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+                        long long i = (long long)s * sxy + (long long)y * g.nx + x;
+                        float m[8], f[3], d[3];
+                        corners(M, u, g, x, y, s, i, m, f);
+                        interp_grad(m, f, d);
+                        float dl = __ldg(dldj + i);
+                        g0 = dl * d[0];
+                        g1 = dl * d[1];
+                        g2 = dl * d[2];
+                    }
+                    int o = ry * RXP + rx;
+                    Gr[o] = g0;
+                    Gr[RY * RXP + o] = g1;
+                    Gr[2 * RY * RXP + o] = g2;
+                }
+                __syncthreads();
+                // (2) Gaussian along x: four outputs per unit
+                for (int uidx = tid; uidx < C::NXU; uidx += NT) {
+                    int row = uidx / (TX / 4);   // q * RY + ry
+                    int p = uidx - row * (TX / 4);
+                    const float* rr = Gr + row * RXP + 4 * p;
+                    float v[4 + 2 * R];
+#pragma unroll
+                    for (int o = 0; o < 4 + 2 * R; ++o) v[o] = rr[o];
+                    float out[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float a = tt[R] * v[e + R];
+#pragma unroll
+                        for (int k = 1; k <= R; ++k)
+                            a += tt[R + k] * (v[e + R - k] + v[e + R + k]);
+                        out[e] = a;
+                    }
+                    *(float4*)(Gx + row * TX + 4 * p) =
+                        make_float4(out[0], out[1], out[2], out[3]);
+                }
+                __syncthreads();
+                // (3) along y into the register ring; along z at o = s - R
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float* col = Gx + (q * RY + oy) * TX + ox;
+                    float a = tt[R] * col[R * TX];
+#pragma unroll
+                    for (int k = 1; k <= R; ++k)
+                        a += tt[R + k] * (col[(R - k) * TX] + col[(R + k) * TX]);
+                    ring[q][j] = a;
+                }
+                const int x = x0 + ox, y = y0 + oy, o = s - R;
+                if (t >= 2 * R && x < g.nx && y < g.ny) {
+                    long long i = (long long)o * sxy + (long long)y * g.nx + x;
+                    float n2 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        // slice o - R + i2 sits in slot (j + 1 + i2) mod KG
+                        float a = tt[R] * ring[q][(j + 1 + R) % KG];
+#pragma unroll
+                        for (int k = 1; k <= R; ++k)
+                            a += tt[R + k] * (ring[q][(j + 1 + R - k) % KG] +
+                                              ring[q][(j + 1 + R + k) % KG]);
+                        gout[q * g.V + i] = a;
+                        n2 += a * a;
+                    }
+                    m2 = (n2 != n2) ? INFINITY : fmaxf(m2, n2);
+                }
+                __syncthreads();
             }
-            Gr[idx] = g0;
-            Gr[RY * RX + idx] = g1;
-            Gr[2 * RY * RX + idx] = g2;
         }
-        __syncthreads();
-        // (2) Gaussian along x
-        for (int idx = tid; idx < 3 * RY * TX; idx += E2_NT) {
-            int q = idx / (RY * TX);
-            int r2 = idx - q * (RY * TX);
-            int ry = r2 / TX, tx = r2 - ry * TX;
-            const float* row = Gr + q * RY * RX + ry * RX + tx;
-            float v = 0.f;
-#pragma unroll
-            for (int j = 0; j < KG; ++j) v += tp.t[j] * row[j];
-            Gx[idx] = v;
-        }
-        __syncthreads();
-        // (3) along y into the ring, along z at slice o = s - R
-        const int o = s - R;
-        const bool valid = t >= 2 * R;
-        for (int idx = tid; idx < TY * TX; idx += E2_NT) {
-            int ty = idx / TX, tx = idx - ty * TX;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float* col = Gx + q * RY * TX + ty * TX + tx;
-                float v = 0.f;
-#pragma unroll
-                for (int j = 0; j < KG; ++j) v += tp.t[j] * col[j * TX];
-                Gq[((t % KG) * 3 + q) * TY * TX + idx] = v;
-            }
-            if (!valid) continue;
-            int x = x0 + tx, y = y0 + ty;
-            if (x >= g.nx || y >= g.ny) continue;
-            long long i = (long long)o * sxy + (long long)y * g.nx + x;
-            float n2 = 0.f;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                float v = 0.f;
-#pragma unroll
-                for (int j = 0; j < KG; ++j)
-                    v += tp.t[j] * Gq[(((t - 2 * R + j) % KG) * 3 + q) * TY * TX + idx];
-                gout[q * g.V + i] = v;
-                n2 += v * v;
-            }
-            m2 = (n2 != n2) ? INFINITY : fmaxf(m2, n2);
-        }
-        __syncthreads();
     }
     for (int k = 16; k > 0; k >>= 1)
         m2 = fmaxf(m2, __shfl_down_sync(0xffffffffu, m2, k));
@@ -401,57 +541,76 @@ __global__ void __launch_bounds__(E2_NT)
     __syncthreads();
     if (tid == 0) {
         float v = 0.f;
-        for (int w = 0; w < E2_NT / 32; ++w) v = fmaxf(v, red[w]);
-        g2_part[item] = v;
+        for (int w = 0; w < NT / 32; ++w) v = fmaxf(v, red[w]);
+        g2_part[blockIdx.x] = v;
     }
 }
 
-// Per-item mean of F over the item's E1 tile (the box-sum shift).
+// ----------------------------------------------------------------------
+// Quantisation scale: shift s = (lo + hi) / 2 and Q = 2^qb / h with
+// h = (hi - lo) / 2, lo = min(0, F, M), hi = max(0, F, M) (0 is the padding
+// value and J is a convex combination of M values and 0).
+// ----------------------------------------------------------------------
 template <typename T>
-__global__ void k_tile_shift(const T* __restrict__ F, Geom g, FusedPlan pl,
-                             float* __restrict__ shift) {
-    __shared__ double red[256 / 32];
-    const int item = blockIdx.x;
-    const int tx_ = item % pl.e1_tx;
-    const int rest = item / pl.e1_tx;
-    const int ty_ = rest % pl.e1_ty;
-    const int zi = rest / pl.e1_ty;
-    const int x0 = tx_ * E1_TX, y0 = ty_ * E1_TY;
-    const int z0 = zi * pl.e1_zc, z1 = min(z0 + pl.e1_zc, g.nz);
-    const int nxl = min(E1_TX, g.nx - x0), nyl = min(E1_TY, g.ny - y0);
-    const long long n = (long long)nxl * nyl * (z1 - z0);
-    double s = 0.0;
-    for (long long k = threadIdx.x; k < n; k += blockDim.x) {
-        int x = (int)(k % nxl);
-        long long r = k / nxl;
-        int y = (int)(r % nyl);
-        int z = (int)(r / nyl);
-        s += (double)ld_img(F, ((long long)(z0 + z) * g.ny + (y0 + y)) * g.nx +
-                                   (x0 + x));
+__global__ void k_minmax(const T* __restrict__ F, const T* __restrict__ M,
+                         long long V, float2* __restrict__ part) {
+    __shared__ float smin[NT / 32], smax[NT / 32];
+    float lo = 0.f, hi = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V;
+         i += (long long)gridDim.x * blockDim.x) {
+        float a = ld_img(F, i), b = ld_img(M, i);
+        lo = fminf(lo, fminf(a, b));
+        hi = fmaxf(hi, fmaxf(a, b));
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smin[threadIdx.x >> 5] = lo;
+        smax[threadIdx.x >> 5] = hi;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double v = 0.0;
-        for (int w = 0; w < 256 / 32; ++w) v += red[w];
-        shift[item] = n > 0 ? (float)(v / (double)n) : 0.f;
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) {
+            lo = fminf(lo, smin[w]);
+            hi = fmaxf(hi, smax[w]);
+        }
+        part[blockIdx.x] = make_float2(smin[0] < lo ? smin[0] : lo,
+                                       smax[0] > hi ? smax[0] : hi);
     }
+}
+
+__global__ void k_qscale(const float2* __restrict__ part, int n, int qb,
+                         QScale* __restrict__ qs) {
+    if (threadIdx.x != 0) return;
+    float lo = 0.f, hi = 0.f;
+    for (int i = 0; i < n; ++i) {
+        lo = fminf(lo, part[i].x);
+        hi = fmaxf(hi, part[i].y);
+    }
+    double h = 0.5 * ((double)hi - (double)lo);
+    if (!(h > 1e-30)) h = 1.0;       // constant images: any scale is exact
+    double s = 0.5 * ((double)hi + (double)lo);
+    double lim = ldexp(1.0, qb);
+    qs->shift = (float)s;
+    // a little headroom so that rounding never leaves [-lim, lim]
+    qs->Q = (float)(lim / (h * (1.0 + 1e-6)));
+    qs->invQ = (float)(1.0 / (double)qs->Q);
+    qs->qlim = (int)lim;
 }
 
 template <int W, typename T>
 int launch_e1(const FusedLaunch& a, cudaStream_t s) {
-    size_t bytes = (size_t)E1Smem<W>::floats * sizeof(float);
-    k_e1<W, T><<<a.plan.e1_items, E1_NT, bytes, s>>>(
-        (const T*)a.F, (const T*)a.M, a.io, a.g, a.c, a.plan, a.shift, a.dldj,
+    k_e1<W, T><<<a.plan.e1_ctas, NT, E1Cfg<W>::bytes, s>>>(
+        (const T*)a.F, (const T*)a.M, a.io, a.g, a.c, a.plan, a.qs, a.dldj,
         a.part.loss);
     return 1;
 }
 
 template <int R, typename T>
 int launch_e2(const FusedLaunch& a, cudaStream_t s) {
-    size_t bytes = (size_t)E2Smem<R>::floats * sizeof(float);
-    k_e2<R, T><<<a.plan.e2_items, E2_NT, bytes, s>>>(
+    k_e2<R, T><<<a.plan.e2_ctas, NT, E2Cfg<R>::bytes, s>>>(
         (const T*)a.M, a.io, a.g, a.c.gtaps, a.plan, a.dldj, a.part.g2max);
     return 1;
 }
@@ -483,19 +642,18 @@ template <int W, typename T>
 cudaError_t attr_e1() {
     return cudaFuncSetAttribute(k_e1<W, T>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(E1Smem<W>::floats * sizeof(float)));
+                                E1Cfg<W>::bytes);
 }
 template <int R, typename T>
 cudaError_t attr_e2() {
     return cudaFuncSetAttribute(k_e2<R, T>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(E2Smem<R>::floats * sizeof(float)));
+                                E2Cfg<R>::bytes);
 }
 
 template <typename T>
 cudaError_t attrs_all() {
-    cudaError_t e = cudaSuccess;
-    cudaError_t r;
+    cudaError_t e = cudaSuccess, r;
     if ((r = attr_e1<1, T>()) != cudaSuccess) e = r;
     if ((r = attr_e1<2, T>()) != cudaSuccess) e = r;
     if ((r = attr_e1<3, T>()) != cudaSuccess) e = r;
@@ -514,25 +672,33 @@ int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
-FusedPlan fused_plan(const Geom& g, int num_sms) {
+// Quantisation bits per window: the largest qb with k^3 2^qb < 2^31 (int32
+// first-moment sums) and k^6 2^(2 qb) < 2^63 (int64 moment differences).
+int quant_bits(int win) {
+    switch (win) {
+        case 3: return 26;
+        case 5: return 24;
+        case 7: return 22;
+        default: return 21;
+    }
+}
+
+FusedPlan fused_plan(const Geom& g, int win, int num_sms) {
     FusedPlan p;
-    const int target = 4 * num_sms;
-    p.e1_tx = ceil_div(g.nx, E1_TX);
-    p.e1_ty = ceil_div(g.ny, E1_TY);
-    int cols1 = p.e1_tx * p.e1_ty;
-    int nzc1 = std::min(std::max(1, ceil_div(target, cols1)),
-                        std::max(1, ceil_div(g.nz, 8)));
-    p.e1_zc = ceil_div(g.nz, nzc1);
-    p.e1_tz = ceil_div(g.nz, p.e1_zc);
-    p.e1_items = cols1 * p.e1_tz;
-    p.e2_tx = ceil_div(g.nx, E2_TX);
-    p.e2_ty = ceil_div(g.ny, E2_TY);
-    int cols2 = p.e2_tx * p.e2_ty;
-    int nzc2 = std::min(std::max(1, ceil_div(target, cols2)),
-                        std::max(1, ceil_div(g.nz, 8)));
-    p.e2_zc = ceil_div(g.nz, nzc2);
-    p.e2_tz = ceil_div(g.nz, p.e2_zc);
-    p.e2_items = cols2 * p.e2_tz;
+    const int W = (win - 1) / 2;
+    const int tx1 = PLANE_X - 2 * W, ty1 = PLANE_Y - 2 * W;
+    p.e1_cx = ceil_div(g.nx, tx1);
+    p.e1_cy = ceil_div(g.ny, ty1);
+    long long w1 = (long long)p.e1_cx * p.e1_cy * g.nz;
+    // one CTA per SM (shared memory bound); fewer when there is less work
+    // than ~8 slices per CTA
+    p.e1_ctas = (int)std::max<long long>(1, std::min<long long>(num_sms, w1 / 8));
+    p.e2_cx = ceil_div(g.nx, PLANE_X);
+    p.e2_cy = ceil_div(g.ny, PLANE_Y);
+    long long w2 = (long long)p.e2_cx * p.e2_cy * g.nz;
+    p.e2_ctas =
+        (int)std::max<long long>(1, std::min<long long>(2LL * num_sms, w2 / 8));
+    p.minmax_ctas = num_sms;
     return p;
 }
 
@@ -542,15 +708,18 @@ cudaError_t fused_setup() {
     return e != cudaSuccess ? e : e2;
 }
 
-int fused_tile_shift(const void* F, int dtype, const Geom& g,
-                     const FusedPlan& pl, float* shift, cudaStream_t s) {
+int fused_qscale(const void* F, const void* M, int dtype, const Geom& g,
+                 const FusedPlan& pl, int win, float2* part, QScale* qs,
+                 cudaStream_t s) {
     if (dtype == LM_BF16)
-        k_tile_shift<<<pl.e1_items, 256, 0, s>>>((const __nv_bfloat16*)F, g,
-                                                  pl, shift);
+        k_minmax<<<pl.minmax_ctas, NT, 0, s>>>((const __nv_bfloat16*)F,
+                                               (const __nv_bfloat16*)M, g.V,
+                                               part);
     else
-        k_tile_shift<<<pl.e1_items, 256, 0, s>>>((const float*)F, g, pl,
-                                                  shift);
-    return 1;
+        k_minmax<<<pl.minmax_ctas, NT, 0, s>>>((const float*)F,
+                                               (const float*)M, g.V, part);
+    k_qscale<<<1, 32, 0, s>>>(part, pl.minmax_ctas, quant_bits(win), qs);
+    return 2;
 }
 
 int eval_fused(const FusedLaunch& a, cudaStream_t s) {

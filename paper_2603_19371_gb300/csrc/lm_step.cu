@@ -25,13 +25,20 @@ __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
     return attempt > 0 && st->done;
 }
 
-// One thread per voxel.  The trial goes to slot (1 - cu), or to dst when
-// the warp is smoothed afterwards.
-__global__ void k_step_compose(StepLaunch a, float* __restrict__ dst) {
+// Trial field, one voxel per thread.  A CTA owns a 32 x 8 x-y tile and a z
+// range; the planes z-1, z, z+1 of u (3 components, with a one-voxel x-y
+// halo, read at edge-clamped positions) sit in a shared-memory ring, so
+// the trilinear read of u at p + v comes from shared memory whenever
+// |v| < 1 along each axis and from global memory otherwise.  The trial goes
+// to slot (1 - cu), or to dst when the warp is smoothed afterwards.
+constexpr int ST_X = 32, ST_Y = 8, ST_HX = ST_X + 2, ST_HY = ST_Y + 2;
+constexpr int ST_PLANE = ST_HX * ST_HY;
+
+__global__ void __launch_bounds__(ST_X * ST_Y)
+    k_step_compose(StepLaunch a, float* __restrict__ dst, int zc) {
+    __shared__ float ring[3][3][ST_PLANE];   // [z slot][component][y][x]
     if (attempt_skip(a.st, a.attempt)) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const Geom& g = a.g;
-    if (i >= g.V) return;
+    const Geom g = a.g;
     const int cu = a.st->cu, cg = a.st->cg;
     const float* __restrict__ u = cu ? a.u1 : a.u0;
     float* __restrict__ out = dst ? dst : (cu ? a.u0 : a.u1);
@@ -40,45 +47,97 @@ __global__ void k_step_compose(StepLaunch a, float* __restrict__ dst) {
     const float lam = (float)a.st->lambda;
     const float gm = a.st->gmax;
     const float inv = gm > 0.f ? 1.f / gm : 0.f;
+    const float scale = -r * a.step;
 
-    float gh[3] = {gg[i] * inv, gg[g.V + i] * inv, gg[2 * g.V + i] * inv};
-    float n2 = gh[0] * gh[0] + gh[1] * gh[1] + gh[2] * gh[2];
-    float sc = -r / (n2 + lam) * a.step;
-    float v[3] = {gh[0] * sc, gh[1] * sc, gh[2] * sc};
+    const int tid = threadIdx.y * ST_X + threadIdx.x;
+    const int x0 = blockIdx.x * ST_X, y0 = blockIdx.y * ST_Y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, g.nz);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int sxy = g.nx * g.ny;
+    const float* U[3] = {u, u + g.V, u + 2 * g.V};
 
-    int x = (int)(i % g.nx);
-    long long rr = i / g.nx;
-    int y = (int)(rr % g.ny), z = (int)(rr / g.ny);
-    const int p[3] = {x, y, z};
-    const int n[3] = {g.nx, g.ny, g.nz};
-    int c0[3], c1[3];
-    float f[3];
-    for (int k = 0; k < 3; ++k) {
-        float fl = safe_floor(v[k]);
-        f[k] = v[k] - fl;
-        int c = p[k] + (int)fl;
-        c0[k] = min(max(c, 0), n[k] - 1);
-        c1[k] = min(max(c + 1, 0), n[k] - 1);
-    }
-    long long sy = g.nx, sz = (long long)g.nx * g.ny;
-    long long i000 = c0[2] * sz + c0[1] * sy + c0[0];
-    long long dx = c1[0] - c0[0], dy = (c1[1] - c0[1]) * sy,
-              dz = (c1[2] - c0[2]) * sz;
-    float wx1 = f[0], wx0 = 1.f - f[0];
-    float wy1 = f[1], wy0 = 1.f - f[1];
-    float wz1 = f[2], wz0 = 1.f - f[2];
+    auto load_plane = [&](int zp, int slot) {
+        int zc_ = min(max(zp, 0), g.nz - 1);
+        for (int k = tid; k < 3 * ST_PLANE; k += ST_X * ST_Y) {
+            int q = k / ST_PLANE, rem = k - q * ST_PLANE;
+            int hy = rem / ST_HX, hx = rem - hy * ST_HX;
+            int gx = min(max(x0 - 1 + hx, 0), g.nx - 1);
+            int gy = min(max(y0 - 1 + hy, 0), g.ny - 1);
+            ring[slot][q][rem] = __ldg(U[q] + zc_ * sxy + gy * g.nx + gx);
+        }
+    };
+    load_plane(z0 - 1, (z0 + 2) % 3);
+    load_plane(z0, z0 % 3);
+    for (int z = z0; z < z1; ++z) {
+        load_plane(z + 1, (z + 1) % 3);
+        __syncthreads();
+        if (x < g.nx && y < g.ny) {
+            const int i = z * sxy + y * g.nx + x;
+            float gh0 = __ldg(gg + i) * inv;
+            float gh1 = __ldg(gg + g.V + i) * inv;
+            float gh2 = __ldg(gg + 2 * g.V + i) * inv;
+            float n2 = gh0 * gh0 + gh1 * gh1 + gh2 * gh2;
+            float sc = scale / (n2 + lam);
+            float v[3] = {gh0 * sc, gh1 * sc, gh2 * sc};
+            float fl[3], f[3];
+            for (int k = 0; k < 3; ++k) {
+                fl[k] = safe_floor(v[k]);
+                f[k] = v[k] - fl[k];
+            }
+            const int cx = x + (int)fl[0], cy = y + (int)fl[1], cz = z + (int)fl[2];
+            const float wx1 = f[0], wx0 = 1.f - f[0];
+            const float wy1 = f[1], wy0 = 1.f - f[1];
+            const float wz1 = f[2], wz0 = 1.f - f[2];
+            float m[3][8];
+            if (cx >= x0 - 1 && cx + 1 <= x0 + ST_X && cy >= y0 - 1 &&
+                cy + 1 <= y0 + ST_Y && cz >= z - 1 && cz + 1 <= z + 1) {
+                const int hx = cx - (x0 - 1), hy = cy - (y0 - 1);
+                const int s0 = (cz + 3) % 3, s1 = (cz + 4) % 3;
+                const int o = hy * ST_HX + hx;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const float* U = u + q * g.V;
-        float m000 = U[i000], m100 = U[i000 + dx];
-        float m010 = U[i000 + dy], m110 = U[i000 + dy + dx];
-        float m001 = U[i000 + dz], m101 = U[i000 + dz + dx];
-        float m011 = U[i000 + dz + dy], m111 = U[i000 + dz + dy + dx];
-        float s = wz0 * (wy0 * (wx0 * m000 + wx1 * m100) +
-                         wy1 * (wx0 * m010 + wx1 * m110)) +
-                  wz1 * (wy0 * (wx0 * m001 + wx1 * m101) +
-                         wy1 * (wx0 * m011 + wx1 * m111));
-        out[q * g.V + i] = v[q] + s;
+                for (int q = 0; q < 3; ++q) {
+                    const float* p0 = ring[s0][q] + o;
+                    const float* p1 = ring[s1][q] + o;
+                    m[q][0] = p0[0];
+                    m[q][1] = p0[1];
+                    m[q][2] = p0[ST_HX];
+                    m[q][3] = p0[ST_HX + 1];
+                    m[q][4] = p1[0];
+                    m[q][5] = p1[1];
+                    m[q][6] = p1[ST_HX];
+                    m[q][7] = p1[ST_HX + 1];
+                }
+            } else {
+                const int ax = min(max(cx, 0), g.nx - 1), bx = min(max(cx + 1, 0), g.nx - 1);
+                const int ay = min(max(cy, 0), g.ny - 1), by = min(max(cy + 1, 0), g.ny - 1);
+                const int az = min(max(cz, 0), g.nz - 1), bz = min(max(cz + 1, 0), g.nz - 1);
+                const int o000 = az * sxy + ay * g.nx;
+                const int o010 = az * sxy + by * g.nx;
+                const int o001 = bz * sxy + ay * g.nx;
+                const int o011 = bz * sxy + by * g.nx;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    m[q][0] = __ldg(U[q] + o000 + ax);
+                    m[q][1] = __ldg(U[q] + o000 + bx);
+                    m[q][2] = __ldg(U[q] + o010 + ax);
+                    m[q][3] = __ldg(U[q] + o010 + bx);
+                    m[q][4] = __ldg(U[q] + o001 + ax);
+                    m[q][5] = __ldg(U[q] + o001 + bx);
+                    m[q][6] = __ldg(U[q] + o011 + ax);
+                    m[q][7] = __ldg(U[q] + o011 + bx);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float s = wz0 * (wy0 * (wx0 * m[q][0] + wx1 * m[q][1]) +
+                                 wy1 * (wx0 * m[q][2] + wx1 * m[q][3])) +
+                          wz1 * (wy0 * (wx0 * m[q][4] + wx1 * m[q][5]) +
+                                 wy1 * (wx0 * m[q][6] + wx1 * m[q][7]));
+                out[q * g.V + i] = v[q] + s;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -266,14 +325,22 @@ __global__ void k_flip_slot(DevState* st) { st->cu = 0; }
 
 int step_compose(const StepLaunch& a, cudaStream_t s) {
     unsigned nb = (unsigned)((a.g.V + TPB - 1) / TPB);
+    // z chunks so that the grid holds ~8 tiles per SM-slot of work
+    const int tx = (a.g.nx + ST_X - 1) / ST_X, ty = (a.g.ny + ST_Y - 1) / ST_Y;
+    const long long cols = (long long)tx * ty;
+    int nzc = (int)std::max<long long>(1, std::min<long long>(
+                                              a.g.nz, (2048 + cols - 1) / cols));
+    int zc = (a.g.nz + nzc - 1) / nzc;
+    nzc = (a.g.nz + zc - 1) / zc;
+    dim3 grid(tx, ty, nzc), block(ST_X, ST_Y);
     if (a.wtaps.R > 0) {
-        k_step_compose<<<nb, TPB, 0, s>>>(a, a.tmpA);
+        k_step_compose<<<grid, block, 0, s>>>(a, a.tmpA, zc);
         k_warp_gauss<<<nb, TPB, 0, s>>>(a.tmpA, a, 0, a.tmpB, 0);
         k_warp_gauss<<<nb, TPB, 0, s>>>(a.tmpB, a, 1, a.tmpA, 0);
         k_warp_gauss<<<nb, TPB, 0, s>>>(a.tmpA, a, 2, nullptr, 1);
         return 4;
     }
-    k_step_compose<<<nb, TPB, 0, s>>>(a, nullptr);
+    k_step_compose<<<grid, block, 0, s>>>(a, nullptr, zc);
     return 1;
 }
 
