@@ -205,6 +205,37 @@ LM_API int lm_state_load(lm_ctx *ctx, const void *buf, size_t nbytes);
 LM_API int lm_time_passes(lm_ctx *ctx, float *u, int n, double *ms_eval,
                           double *ms_step);
 
+/* ---- evaluation without allocation ------------------------------------ */
+/* The paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory while they evaluate (code inside another
+ * framework's memory pool or allocator hooks, real-time loops where the
+ * device synchronisation of cudaMalloc / cudaFree is not allowed, processes
+ * that gave their free memory to another component).
+ *
+ * Same result as lm_eval on a fresh context: the loss r = 1 - LNCC and its
+ * smoothed gradient at u, without a context and without any allocation.
+ * Its scratch is one static device array inside the library, sized for at
+ * most LM_NOALLOC_MAX_VOXELS voxels (about 8.4 MB, held by every GPU that
+ * loads the library until the process exits); larger volumes return
+ * LM_EINVAL.
+ *   fixed, moving: images as for lm_init; p: parameters (NULL = defaults;
+ *   only win, eps_nr, eps_dr and sigma_grad matter); u: device field
+ *   [3][D][H][W]; g_out: device [3][D][H][W] (written); loss_out: device
+ *   double (written; NaN if the loss or gradient is not finite; may be
+ *   NULL); gmax_out: device float (may be NULL); cuda_stream: the stream.
+ * Asynchronous on cuda_stream.  The first call on a device looks up the
+ * array's device address and prepares the kernels (no allocation); make
+ * that first call before any stream capture.  Every call shares the one
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * host threads without ordering) race and corrupt each other's results;
+ * order them on one stream.  The array keeps the last call's contents;
+ * every call overwrites all of the scratch it reads. */
+#define LM_NOALLOC_MAX_VOXELS (1 << 21)
+LM_API int lm_eval_noalloc(const lm_volume *fixed, const lm_volume *moving,
+                           const lm_params *p, const float *u, float *g_out,
+                           double *loss_out, float *gmax_out,
+                           void *cuda_stream);
+
 /* Static message for an LM_E* code. */
 LM_API const char *lm_strerror(int code);
 

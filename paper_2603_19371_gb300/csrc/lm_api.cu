@@ -39,6 +39,14 @@ int fail(int code, const char* fmt, ...) {
                         cudaGetErrorString(e_));                           \
     } while (0)
 
+}  // namespace
+
+void lmk::set_last_error(const char* msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+
+namespace {
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes at;

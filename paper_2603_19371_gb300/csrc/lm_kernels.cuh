@@ -98,6 +98,9 @@ struct FinLaunch {
 };
 int finalize(const FinLaunch& a, cudaStream_t s);
 
+// Replace the calling thread's lm_last_error() message.
+void set_last_error(const char* msg);
+
 // Copy the current field back into slot 0 when it sits in slot 1.
 int sync_back(const Geom& g, float* u0, float* u1, DevState* st,
               cudaStream_t s);

@@ -1,0 +1,217 @@
+// lm_eval_noalloc: the loss / gradient evaluation without any allocation.
+//
+// Some callers cannot allocate device memory at the time they evaluate:
+// code running inside another framework's memory pool or allocator hooks,
+// real-time loops that forbid cudaMalloc/cudaFree (both synchronise the
+// device), or a process that has handed all free memory to another
+// component.  For them this entry point takes only the caller's inputs and
+// outputs and keeps its scratch (dL/dJ between the two evaluation kernels,
+// per-CTA partials, the fixed-point scale and the reduced result) in one
+// file-scope static device array, sized for volumes up to
+// LM_NOALLOC_MAX_VOXELS voxels.  Every GPU that loads the library holds that
+// array until the process exits.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "lm_fused.cuh"
+#include "lm_kernels.cuh"
+
+namespace {
+
+// Scratch layout (bytes, each section 256-byte aligned):
+//   dL/dJ               LM_NOALLOC_MAX_VOXELS floats
+//   loss partials       MAX_CTAS doubles
+//   |g|^2 partials      MAX_CTAS floats
+//   image range parts   MAX_CTAS float2
+//   QScale, EvalOut
+constexpr size_t MAX_CTAS = 1024;
+constexpr size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+constexpr size_t OFF_DLDJ = 0;
+constexpr size_t OFF_LOSS =
+    OFF_DLDJ + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
+constexpr size_t OFF_G2 = OFF_LOSS + align256(MAX_CTAS * sizeof(double));
+constexpr size_t OFF_MM = OFF_G2 + align256(MAX_CTAS * sizeof(float));
+constexpr size_t OFF_QS = OFF_MM + align256(MAX_CTAS * sizeof(float2));
+constexpr size_t OFF_OUT = OFF_QS + align256(sizeof(lmk::QScale));
+constexpr size_t SCRATCH_BYTES = OFF_OUT + align256(sizeof(lmk::EvalOut));
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+unsigned char* g_scratch_ptr[MAX_DEVICES] = {};
+int g_num_sms[MAX_DEVICES] = {};
+
+// Failures are described through lm_last_error(), like every entry point.
+int fail(int code, const char* m) {
+    lmk::set_last_error(m);
+    return code;
+}
+
+// Once per device, with that device current: the device address of the
+// static array (host code only knows a host-side stand-in for the symbol),
+// the SM count, and the kernels' shared-memory opt-in.
+int setup_device(int dev, unsigned char** ptr, int* sms) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= MAX_DEVICES) return LM_EUNSUPPORTED;
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(LM_ECUDA, "cudaGetSymbolAddress of the scratch failed");
+        }
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                cudaSuccess ||
+            n < 1) {
+            cudaGetLastError();
+            return fail(LM_ECUDA, "cannot query the SM count");
+        }
+        if (lmk::fused_setup() != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LM_ECUDA, "kernel shared-memory set-up failed");
+        }
+        g_num_sms[dev] = n;
+        g_scratch_ptr[dev] = (unsigned char*)p;
+    }
+    *ptr = g_scratch_ptr[dev];
+    *sms = g_num_sms[dev];
+    return LM_OK;
+}
+
+// Copies the reduced scalars to the caller's device outputs.
+__global__ void k_noalloc_out(const lmk::EvalOut* __restrict__ o,
+                              double* __restrict__ loss,
+                              float* __restrict__ gmax) {
+    if (threadIdx.x != 0) return;
+    if (loss) *loss = o->status ? __longlong_as_double(0x7ff8000000000000LL)
+                                : o->L;
+    if (gmax) *gmax = o->gmax;
+}
+
+}  // namespace
+
+extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
+                               const lm_params* p, const float* u,
+                               float* g_out, double* loss_out,
+                               float* gmax_out, void* cuda_stream) {
+    lmk::set_last_error("");
+    if (!fixed || !moving || !u || !g_out)
+        return fail(LM_EINVAL, "fixed, moving, u and g_out must be non-NULL");
+    if (fixed->D != moving->D || fixed->H != moving->H ||
+        fixed->W != moving->W || fixed->dtype != moving->dtype)
+        return fail(LM_EINVAL, "fixed and moving differ in shape or dtype");
+    if (fixed->D < 1 || fixed->H < 1 || fixed->W < 1 || !fixed->data ||
+        !moving->data)
+        return fail(LM_EINVAL, "bad image descriptor");
+    if (fixed->dtype != LM_F32 && fixed->dtype != LM_BF16)
+        return fail(LM_EINVAL, "unknown dtype");
+    const long long V = (long long)fixed->D * fixed->H * fixed->W;
+    if (V > (long long)LM_NOALLOC_MAX_VOXELS)
+        return fail(LM_EINVAL,
+                    "volume exceeds LM_NOALLOC_MAX_VOXELS (2^21 voxels) of the "
+                    "static scratch");
+    lm_params prm;
+    if (p) {
+        prm = *p;
+    } else {
+        lm_default_params(&prm);
+    }
+    if (!(prm.win >= 3 && prm.win <= 9 && (prm.win & 1)) ||
+        !(prm.sigma_grad >= 0 && prm.sigma_grad <= 2) || !(prm.eps_dr > 0) ||
+        !(prm.eps_nr >= 0))
+        return fail(LM_EINVAL, "win, sigma_grad or eps out of range");
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LM_ECUDA, "no current device");
+    }
+    unsigned char* base = nullptr;
+    int sms = 0;
+    int rc = setup_device(dev, &base, &sms);
+    if (rc != LM_OK) return rc;
+
+    lmk::Geom g;
+    g.nx = fixed->W;
+    g.ny = fixed->H;
+    g.nz = fixed->D;
+    g.V = V;
+    lmk::FusedPlan plan = lmk::fused_plan(g, prm.win, sms);
+    if ((size_t)plan.e1_ctas > MAX_CTAS || (size_t)plan.e2_ctas > MAX_CTAS ||
+        (size_t)plan.minmax_ctas > MAX_CTAS)
+        return fail(LM_EUNSUPPORTED, "device has more SMs than the scratch covers");
+
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    float* dldj = (float*)(base + OFF_DLDJ);
+    double* loss_part = (double*)(base + OFF_LOSS);
+    float* g2_part = (float*)(base + OFF_G2);
+    float2* mm = (float2*)(base + OFF_MM);
+    lmk::QScale* qs = (lmk::QScale*)(base + OFF_QS);
+    lmk::EvalOut* out = (lmk::EvalOut*)(base + OFF_OUT);
+
+    lmk::LnccConsts lc{};
+    lc.win = prm.win;
+    lc.eps_nr = prm.eps_nr;
+    lc.eps_dr = prm.eps_dr;
+    lc.inv_k3 = (float)(1.0 / ((double)prm.win * prm.win * prm.win));
+    lc.inv_V = (float)(1.0 / (double)V);
+    // Gaussian taps, as in the context path
+    {
+        double sg = prm.sigma_grad;
+        lc.gtaps.R = 0;
+        lc.gtaps.t[0] = 1.f;
+        if (sg > 0) {
+            int R = (int)ceil(3.0 * sg);
+            double w[2 * lmk::MAX_R + 1], sum = 0;
+            for (int j = -R; j <= R; ++j) {
+                w[j + R] = exp(-(double)j * j / (2.0 * sg * sg));
+                sum += w[j + R];
+            }
+            lc.gtaps.R = R;
+            for (int j = 0; j <= 2 * R; ++j) lc.gtaps.t[j] = (float)(w[j] / sum);
+        }
+    }
+
+    lmk::fused_qscale(fixed->data, moving->data, fixed->dtype, g, plan, prm.win,
+                      mm, qs, s);
+    lmk::FusedLaunch f;
+    f.g = g;
+    f.F = fixed->data;
+    f.M = moving->data;
+    f.dtype = fixed->dtype;
+    f.io.u_in = u;
+    f.io.g_out = g_out;
+    f.io.u0 = const_cast<float*>(u);
+    f.io.u1 = nullptr;
+    f.io.g0 = nullptr;
+    f.io.g1 = nullptr;
+    f.io.st = nullptr;
+    f.io.mode = lmk::EVAL_EXPLICIT;
+    f.io.attempt = 0;
+    f.c = lc;
+    f.plan = plan;
+    f.qs = qs;
+    f.dldj = dldj;
+    f.part.loss = loss_part;
+    f.part.n_loss = plan.e1_ctas;
+    f.part.g2max = g2_part;
+    f.part.n_g2 = plan.e2_ctas;
+    lmk::eval_fused(f, s);
+    lmk::FinLaunch fl;
+    fl.part = f.part;
+    fl.st = nullptr;
+    fl.out = out;
+    fl.log = nullptr;
+    fl.d = lmk::DecideConsts{};
+    fl.inv_V = 1.0 / (double)V;
+    fl.mode = lmk::FIN_EXPLICIT;
+    fl.attempt = 0;
+    lmk::finalize(fl, s);
+    k_noalloc_out<<<1, 32, 0, s>>>(out, loss_out, gmax_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LM_ECUDA, cudaGetErrorString(e));
+    return LM_OK;
+}

@@ -17,6 +17,7 @@ LM_OK, LM_EINVAL, LM_ENOMEM, LM_ECUDA = 0, -1, -2, -3
 LM_ENONFINITE, LM_ETIMEOUT, LM_EUNSUPPORTED, LM_ESTATE = -4, -5, -6, -7
 LM_F32, LM_BF16 = 0, 1
 LM_MAX_LEVELS = 4
+LM_NOALLOC_MAX_VOXELS = 1 << 21
 
 
 class LMError(RuntimeError):
@@ -100,6 +101,8 @@ def load():
         "lm_state_save": [V, V, ctypes.POINTER(ctypes.c_size_t)],
         "lm_state_load": [V, V, ctypes.c_size_t],
         "lm_time_passes": [V, V, I, ctypes.POINTER(D), ctypes.POINTER(D)],
+        "lm_eval_noalloc": [ctypes.POINTER(Volume), ctypes.POINTER(Volume),
+                            ctypes.POINTER(Params), V, V, V, V, V],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -273,6 +276,20 @@ def lm_time_passes(ctx: Context, u, n):
     return a.value, b.value
 
 
+def lm_eval_noalloc(fixed, moving, u, g_out, loss_out=None, gmax_out=None,
+                    params: Params | None = None, stream=None):
+    """Evaluation without allocation (static scratch, at most
+    LM_NOALLOC_MAX_VOXELS voxels); outputs are device tensors."""
+    vf, vm = _volume(fixed), _volume(moving)
+    p = ctypes.byref(params) if params is not None else None
+    lp = ctypes.c_void_p(loss_out.data_ptr()) if loss_out is not None else None
+    gp = ctypes.c_void_p(gmax_out.data_ptr()) if gmax_out is not None else None
+    _check(load().lm_eval_noalloc(ctypes.byref(vf), ctypes.byref(vm), p,
+                                  _field_ptr(u, fixed.shape),
+                                  _field_ptr(g_out, fixed.shape), lp, gp,
+                                  _stream_handle(stream)), "lm_eval_noalloc")
+
+
 def lm_strerror(code: int) -> str:
     return load().lm_strerror(int(code)).decode()
 
@@ -285,4 +302,5 @@ def lm_last_error() -> str:
 EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_reset", "lm_step", "lm_iterate", "lm_get_state",
             "lm_set_state", "lm_register", "lm_state_save", "lm_state_load",
-            "lm_time_passes", "lm_strerror", "lm_last_error")
+            "lm_time_passes", "lm_eval_noalloc", "lm_strerror",
+            "lm_last_error")
