@@ -37,22 +37,22 @@ __device__ __forceinline__ float safe_floor(float v) {
     return fminf(fmaxf(floorf(v), -1048576.f), 1048576.f);
 }
 
-// Trilinear corners of M around p + u(p), zero outside the volume.
+// Trilinear corners of M around p + d (d = u(p) already loaded), zero
+// outside the volume.  Offsets are 32-bit (V < 2^31).
 template <typename T>
-__device__ __forceinline__ void corners(const T* __restrict__ M,
-                                        const float* __restrict__ u,
-                                        const Geom& g, int x, int y, int z,
-                                        long long i, float m[8], float f[3]) {
-    float d0 = __ldg(u + i), d1 = __ldg(u + g.V + i), d2 = __ldg(u + 2 * g.V + i);
+__device__ __forceinline__ void corners(const T* __restrict__ M, const Geom& g,
+                                        int x, int y, int z, float d0,
+                                        float d1, float d2, float m[8],
+                                        float f[3]) {
     float l0 = safe_floor(d0), l1 = safe_floor(d1), l2 = safe_floor(d2);
     f[0] = d0 - l0;
     f[1] = d1 - l1;
     f[2] = d2 - l2;
     int cx = x + (int)l0, cy = y + (int)l1, cz = z + (int)l2;
-    const long long sxy = (long long)g.nx * g.ny;
+    const int sxy = g.nx * g.ny;
     if (cx >= 0 && cx + 1 < g.nx && cy >= 0 && cy + 1 < g.ny && cz >= 0 &&
         cz + 1 < g.nz) {
-        long long b = (long long)cz * sxy + (long long)cy * g.nx + cx;
+        int b = cz * sxy + cy * g.nx + cx;
         m[0] = ld_img(M, b);
         m[1] = ld_img(M, b + 1);
         m[2] = ld_img(M, b + g.nx);
@@ -67,8 +67,7 @@ __device__ __forceinline__ void corners(const T* __restrict__ M,
             int qx = cx + (s & 1), qy = cy + ((s >> 1) & 1), qz = cz + (s >> 2);
             bool in = qx >= 0 && qx < g.nx && qy >= 0 && qy < g.ny && qz >= 0 &&
                       qz < g.nz;
-            m[s] = in ? ld_img(M, (long long)qz * sxy + (long long)qy * g.nx + qx)
-                      : 0.f;
+            m[s] = in ? ld_img(M, qz * sxy + qy * g.nx + qx) : 0.f;
         }
     }
 }
@@ -144,6 +143,9 @@ __global__ void __launch_bounds__(NT, 1)
     using C = E1Cfg<W>;
     constexpr int K = C::K, SX = C::SX, SY = C::SY, TX = C::TX, TY = C::TY;
     constexpr int GX = C::GX, GY = C::GY, GXP = C::GXP;
+    constexpr int NGS = (GX * GY + NT - 1) / NT;      // gather slots / thread
+    constexpr int NX2S = (C::NX2U + NT - 1) / NT;     // x-box-2 slots
+    static_assert(C::NXU <= NT, "one x-pass unit per thread");
     extern __shared__ __align__(16) unsigned char smem[];
     int* GqF = (int*)smem;
     int* GqJ = GqF + GY * GXP;
@@ -163,7 +165,9 @@ __global__ void __launch_bounds__(NT, 1)
     if (eval_skip(io)) return;
     const int tid = threadIdx.x;
     const float* __restrict__ u = eval_u(io);
-    const long long sxy = (long long)g.nx * g.ny;
+    const float* __restrict__ u1 = u + g.V;
+    const float* __restrict__ u2 = u + 2 * g.V;
+    const int sxy = g.nx * g.ny;
     const float sh = qs->shift, Q = qs->Q, iQ = qs->invQ;
     const int qlim = qs->qlim;
     const int qpad = __float2int_rn(-sh * Q);
@@ -172,10 +176,29 @@ __global__ void __launch_bounds__(NT, 1)
     const float mscale = c.inv_k3 * c.inv_k3 * iQ * iQ;
     const float m1scale = c.inv_k3 * iQ;
 
-    // this thread's moment-plane point and output point
+    // fixed per-thread work: gather slots, x-pass unit, moment point,
+    // x-box-2 slots and output point
+    int g_gx[NGS], g_gy[NGS], g_sm[NGS];
+#pragma unroll
+    for (int k = 0; k < NGS; ++k) {
+        int idx = tid + k * NT;
+        g_gy[k] = idx / GX;
+        g_gx[k] = idx - g_gy[k] * GX;
+        g_sm[k] = idx < GX * GY ? g_gy[k] * GXP + g_gx[k] : -1;
+    }
+    const bool has_xu = tid < C::NXU;
+    const int xu_gy = tid / (SX / 2), xu_p = tid - xu_gy * (SX / 2);
     const int sx = tid & (SX - 1), sy = tid / SX;
+    int x2_row[NX2S], x2_p[NX2S];
+#pragma unroll
+    for (int k = 0; k < NX2S; ++k) {
+        int uidx = tid + k * NT;
+        x2_row[k] = uidx < C::NX2U ? uidx / (TX / 2) : -1;
+        x2_p[k] = uidx - (uidx / (TX / 2)) * (TX / 2);
+    }
     const bool has_o = tid < TX * TY;
     const int ox = has_o ? tid % TX : 0, oy = has_o ? tid / TX : 0;
+    const int o_gi = (oy + 2 * W) * GXP + ox + 2 * W;
 
     double lacc = 0.0;
     bool bad = false;
@@ -190,8 +213,24 @@ __global__ void __launch_bounds__(NT, 1)
         w0 += z1 - z0;
         const int x0 = (int)(col % pl.e1_cx) * TX;
         const int y0 = (int)(col / pl.e1_cx) * TY;
+        // in-plane offsets of the gather slots (-1: outside the volume)
+        int g_off[NGS];
+#pragma unroll
+        for (int k = 0; k < NGS; ++k) {
+            int x = x0 - 2 * W + g_gx[k], y = y0 - 2 * W + g_gy[k];
+            g_off[k] = (g_sm[k] >= 0 && x >= 0 && x < g.nx && y >= 0 &&
+                        y < g.ny)
+                           ? y * g.nx + x
+                           : -1;
+        }
+        const bool s_in = x0 - W + sx < g.nx && y0 - W + sy < g.ny &&
+                          x0 - W + sx >= 0 && y0 - W + sy >= 0;
+        const bool s_out = sx >= W && sx < W + TX && sy >= W && sy < W + TY;
+        const bool o_in = has_o && x0 + ox < g.nx && y0 + oy < g.ny;
+        const int o_off = (y0 + oy) * g.nx + x0 + ox;
 
         // ring and running sums restart for every segment
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             ZR32[(k * 2 + 0) * NT + tid] = 0;
             ZR32[(k * 2 + 1) * NT + tid] = 0;
@@ -217,35 +256,50 @@ __global__ void __launch_bounds__(NT, 1)
                 const int t = s - s_begin;
                 // (1) gather plane: quantised F', J'
                 const bool zin = s >= 0 && s < g.nz;
-                for (int idx = tid; idx < GX * GY; idx += NT) {
-                    int gy = idx / GX, gx = idx - gy * GX;
-                    int x = x0 - 2 * W + gx, y = y0 - 2 * W + gy;
-                    int fq = qpad, jq = qpad;
-                    if (zin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
-                        long long i = (long long)s * sxy + (long long)y * g.nx + x;
-                        float m[8], f[3];
-                        corners(M, u, g, x, y, s, i, m, f);
-                        float fv = ld_img(F, i), jv = interp(m, f);
-                        if (!isfinite(fv) || !isfinite(jv)) bad = true;
-                        fq = min(max(__float2int_rn((fv - sh) * Q), -qlim), qlim);
-                        jq = min(max(__float2int_rn((jv - sh) * Q), -qlim), qlim);
+                {
+                    float d[NGS][3], fv[NGS];
+                    int i[NGS];
+#pragma unroll
+                    for (int k = 0; k < NGS; ++k) {
+                        i[k] = (zin && g_off[k] >= 0) ? s * sxy + g_off[k] : -1;
+                        if (i[k] >= 0) {
+                            d[k][0] = __ldg(u + i[k]);
+                            d[k][1] = __ldg(u1 + i[k]);
+                            d[k][2] = __ldg(u2 + i[k]);
+                            fv[k] = ld_img(F, i[k]);
+                        }
                     }
-                    GqF[gy * GXP + gx] = fq;
-                    GqJ[gy * GXP + gx] = jq;
+#pragma unroll
+                    for (int k = 0; k < NGS; ++k) {
+                        if (g_sm[k] < 0) continue;
+                        int fq = qpad, jq = qpad;
+                        if (i[k] >= 0) {
+                            float m[8], f[3];
+                            corners(M, g, x0 - 2 * W + g_gx[k],
+                                    y0 - 2 * W + g_gy[k], s, d[k][0], d[k][1],
+                                    d[k][2], m, f);
+                            float jv = interp(m, f);
+                            bad |= !(fabsf(jv) <= 3.0e38f) ||
+                                   !(fabsf(fv[k]) <= 3.0e38f);
+                            fq = min(max(__float2int_rn((fv[k] - sh) * Q), -qlim),
+                                     qlim);
+                            jq = min(max(__float2int_rn((jv - sh) * Q), -qlim),
+                                     qlim);
+                        }
+                        GqF[g_sm[k]] = fq;
+                        GqJ[g_sm[k]] = jq;
+                    }
                 }
                 __syncthreads();
                 // delay line of F', J' for this thread's output point
                 if (has_o) {
-                    int gi = (oy + 2 * W) * GXP + ox + 2 * W;
-                    dF[j] = (float)GqF[gi] * iQ;
-                    dJ[j] = (float)GqJ[gi] * iQ;
+                    dF[j] = (float)GqF[o_gi] * iQ;
+                    dJ[j] = (float)GqJ[o_gi] * iQ;
                 }
                 // (2) window sums along x: two outputs per unit
-                for (int uidx = tid; uidx < C::NXU; uidx += NT) {
-                    int gy = uidx / (SX / 2);
-                    int p = uidx - gy * (SX / 2);
-                    const int* rf = GqF + gy * GXP + 2 * p;
-                    const int* rj = GqJ + gy * GXP + 2 * p;
+                if (has_xu) {
+                    const int* rf = GqF + xu_gy * GXP + 2 * xu_p;
+                    const int* rj = GqJ + xu_gy * GXP + 2 * xu_p;
                     int vf[K + 1], vj[K + 1];
 #pragma unroll
                     for (int o = 0; o < K + 1; ++o) {
@@ -262,7 +316,7 @@ __global__ void __launch_bounds__(NT, 1)
                         sjj += (long long)vj[o] * vj[o];
                         sfj += (long long)vf[o] * vj[o];
                     }
-                    int o1 = gy * SX + 2 * p;
+                    int o1 = xu_gy * SX + 2 * xu_p;
                     XF[o1] = sf;
                     XJ[o1] = sj;
                     XFF[o1] = sff;
@@ -310,10 +364,8 @@ __global__ void __launch_bounds__(NT, 1)
                 const int cz = s - W;
                 const bool coef_valid = t >= 2 * W;
                 if (coef_valid) {
-                    int x = x0 - W + sx, y = y0 - W + sy;
                     float av = 0.f, bv = 0.f, cv = 0.f;
-                    if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && cz >= 0 &&
-                        cz < g.nz) {
+                    if (s_in && cz >= 0 && cz < g.nz) {
                         long long Ai = k3 * runFJ - (long long)runF * runJ;
                         long long Bi = k3 * runFF - (long long)runF * runF;
                         long long Ci = k3 * runJJ - (long long)runJ * runJ;
@@ -329,8 +381,7 @@ __global__ void __launch_bounds__(NT, 1)
                         av = 2.f * A * rD;
                         bv = -N * B * rD * rD;
                         cv = -av * mF - 2.f * bv * mJ;
-                        if (sx >= W && sx < W + TX && sy >= W && sy < W + TY &&
-                            cz >= z0 && cz < z1)
+                        if (s_out && cz >= z0 && cz < z1)
                             lacc += (double)(((BC - AA) + (c.eps_dr - c.eps_nr)) *
                                              rD);
                     }
@@ -341,21 +392,20 @@ __global__ void __launch_bounds__(NT, 1)
                 __syncthreads();
                 if (coef_valid) {
                     // (4) box of (a, b, c) along x: two outputs per unit
-                    for (int uidx = tid; uidx < C::NX2U; uidx += NT) {
-                        int row = uidx / (TX / 2);   // q * SY + sy
-                        int p = uidx - row * (TX / 2);
-                        const float* r = Ab + row * SX + 2 * p;
+#pragma unroll
+                    for (int k = 0; k < NX2S; ++k) {
+                        if (x2_row[k] < 0) continue;
+                        const float* r = Ab + x2_row[k] * SX + 2 * x2_p[k];
                         float v[K + 1];
 #pragma unroll
                         for (int o = 0; o < K + 1; ++o) v[o] = r[o];
-                        float s0 = 0.f;
+                        float s0 = 0.f, s1 = 0.f;
 #pragma unroll
                         for (int o = 0; o < K; ++o) s0 += v[o];
-                        float s1 = 0.f;
 #pragma unroll
                         for (int o = 1; o < K + 1; ++o) s1 += v[o];
-                        Ax[row * TX + 2 * p] = s0;
-                        Ax[row * TX + 2 * p + 1] = s1;
+                        float2* dst = (float2*)(Ax + x2_row[k] * TX + 2 * x2_p[k]);
+                        *dst = make_float2(s0, s1);
                     }
                     __syncthreads();
                     // (5) along y into the register ring, along z, dL/dJ at
@@ -370,8 +420,7 @@ __global__ void __launch_bounds__(NT, 1)
                             r2[q][j] = v;
                         }
                         const int r = cz - W;
-                        const int x = x0 + ox, y = y0 + oy;
-                        if (t >= 4 * W && x < g.nx && y < g.ny) {
+                        if (t >= 4 * W && o_in) {
                             float b3[3];
 #pragma unroll
                             for (int q = 0; q < 3; ++q) {
@@ -382,10 +431,10 @@ __global__ void __launch_bounds__(NT, 1)
                                 b3[q] = v;
                             }
                             const int jd = (j + 1) % K;
-                            long long i = (long long)r * sxy + (long long)y * g.nx + x;
-                            dldj[i] = -c.inv_V * ((dF[jd] * b3[0] +
-                                                   2.f * dJ[jd] * b3[1] + b3[2]) *
-                                                  c.inv_k3);
+                            dldj[r * sxy + o_off] =
+                                -c.inv_V * ((dF[jd] * b3[0] +
+                                             2.f * dJ[jd] * b3[1] + b3[2]) *
+                                            c.inv_k3);
                         }
                     }
                 }
@@ -424,6 +473,8 @@ __global__ void __launch_bounds__(NT, 2)
     using C = E2Cfg<R>;
     constexpr int KG = C::KG, RX = C::RX, RY = C::RY, RXP = C::RXP;
     constexpr int TX = C::TX, TY = C::TY;
+    constexpr int NRS = (RX * RY + NT - 1) / NT;    // halo-plane slots
+    constexpr int NXS = (C::NXU + NT - 1) / NT;     // x-pass slots
     extern __shared__ __align__(16) unsigned char smem[];
     float* Gr = (float*)smem;            // [3][RY][RXP]
     float* Gx = Gr + 3 * RY * RXP;       // [3][RY][TX]
@@ -432,12 +483,32 @@ __global__ void __launch_bounds__(NT, 2)
     if (eval_skip(io)) return;
     const int tid = threadIdx.x;
     const float* __restrict__ u = eval_u(io);
+    const float* __restrict__ u1 = u + g.V;
+    const float* __restrict__ u2 = u + 2 * g.V;
     float* __restrict__ gout = eval_g(io);
-    const long long sxy = (long long)g.nx * g.ny;
+    const int sxy = g.nx * g.ny;
     const int ox = tid & (TX - 1), oy = tid / TX;
-    float tt[KG];
+    // taps stay in the kernel-parameter constant bank (no registers)
+    const float* tt = tp.t;
+
+    // packed per-thread slots: halo-plane point (rx | ry << 16) and its
+    // shared-memory index; x-pass unit (smem offsets of input and output)
+    int r_xy[NRS], r_sm[NRS];
 #pragma unroll
-    for (int j = 0; j < KG; ++j) tt[j] = tp.t[j];
+    for (int k = 0; k < NRS; ++k) {
+        int idx = tid + k * NT;
+        int ry = idx / RX, rx = idx - ry * RX;
+        r_xy[k] = rx | (ry << 16);
+        r_sm[k] = idx < RX * RY ? ry * RXP + rx : -1;
+    }
+    int x_in[NXS], x_out[NXS];
+#pragma unroll
+    for (int k = 0; k < NXS; ++k) {
+        int uidx = tid + k * NT;
+        int row = uidx / (TX / 4), p = uidx - row * (TX / 4);
+        x_in[k] = uidx < C::NXU ? row * RXP + 4 * p : -1;
+        x_out[k] = row * TX + 4 * p;
+    }
     float m2 = 0.f;
 
     const long long total = (long long)pl.e2_cx * pl.e2_cy * g.nz;
@@ -451,6 +522,17 @@ __global__ void __launch_bounds__(NT, 2)
         w0 += z1 - z0;
         const int x0 = (int)(col % pl.e2_cx) * TX;
         const int y0 = (int)(col / pl.e2_cx) * TY;
+        int r_off[NRS];
+#pragma unroll
+        for (int k = 0; k < NRS; ++k) {
+            int x = x0 - R + (r_xy[k] & 0xffff), y = y0 - R + (r_xy[k] >> 16);
+            r_off[k] = (r_sm[k] >= 0 && x >= 0 && x < g.nx && y >= 0 &&
+                        y < g.ny)
+                           ? y * g.nx + x
+                           : -1;
+        }
+        const bool o_in = x0 + ox < g.nx && y0 + oy < g.ny;
+        const int o_off = (y0 + oy) * g.nx + x0 + ox;
         float ring[3][KG];
 #pragma unroll
         for (int k = 0; k < KG; ++k) ring[0][k] = ring[1][k] = ring[2][k] = 0.f;
@@ -463,31 +545,35 @@ __global__ void __launch_bounds__(NT, 2)
                 const int t = s - s_begin;
                 // (1) g_raw on the tile and its R halo
                 const bool zin = s >= 0 && s < g.nz;
-                for (int idx = tid; idx < RX * RY; idx += NT) {
-                    int ry = idx / RX, rx = idx - ry * RX;
-                    int x = x0 - R + rx, y = y0 - R + ry;
-                    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-                    if (zin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
-                        long long i = (long long)s * sxy + (long long)y * g.nx + x;
-                        float m[8], f[3], d[3];
-                        corners(M, u, g, x, y, s, i, m, f);
-                        interp_grad(m, f, d);
-                        float dl = __ldg(dldj + i);
-                        g0 = dl * d[0];
-                        g1 = dl * d[1];
-                        g2 = dl * d[2];
+                {
+#pragma unroll
+                    for (int k = 0; k < NRS; ++k) {
+                        if (r_sm[k] < 0) continue;
+                        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+                        if (zin && r_off[k] >= 0) {
+                            const int i = s * sxy + r_off[k];
+                            float m[8], f[3], dd[3];
+                            float dl = __ldg(dldj + i);
+                            corners(M, g, x0 - R + (r_xy[k] & 0xffff),
+                                    y0 - R + (r_xy[k] >> 16), s,
+                                    __ldg(u + i), __ldg(u1 + i), __ldg(u2 + i),
+                                    m, f);
+                            interp_grad(m, f, dd);
+                            g0 = dl * dd[0];
+                            g1 = dl * dd[1];
+                            g2 = dl * dd[2];
+                        }
+                        Gr[r_sm[k]] = g0;
+                        Gr[RY * RXP + r_sm[k]] = g1;
+                        Gr[2 * RY * RXP + r_sm[k]] = g2;
                     }
-                    int o = ry * RXP + rx;
-                    Gr[o] = g0;
-                    Gr[RY * RXP + o] = g1;
-                    Gr[2 * RY * RXP + o] = g2;
                 }
                 __syncthreads();
                 // (2) Gaussian along x: four outputs per unit
-                for (int uidx = tid; uidx < C::NXU; uidx += NT) {
-                    int row = uidx / (TX / 4);   // q * RY + ry
-                    int p = uidx - row * (TX / 4);
-                    const float* rr = Gr + row * RXP + 4 * p;
+#pragma unroll
+                for (int k = 0; k < NXS; ++k) {
+                    if (x_in[k] < 0) continue;
+                    const float* rr = Gr + x_in[k];
                     float v[4 + 2 * R];
 #pragma unroll
                     for (int o = 0; o < 4 + 2 * R; ++o) v[o] = rr[o];
@@ -496,11 +582,11 @@ __global__ void __launch_bounds__(NT, 2)
                     for (int e = 0; e < 4; ++e) {
                         float a = tt[R] * v[e + R];
 #pragma unroll
-                        for (int k = 1; k <= R; ++k)
-                            a += tt[R + k] * (v[e + R - k] + v[e + R + k]);
+                        for (int q = 1; q <= R; ++q)
+                            a += tt[R + q] * (v[e + R - q] + v[e + R + q]);
                         out[e] = a;
                     }
-                    *(float4*)(Gx + row * TX + 4 * p) =
+                    *(float4*)(Gx + x_out[k]) =
                         make_float4(out[0], out[1], out[2], out[3]);
                 }
                 __syncthreads();
@@ -514,9 +600,8 @@ __global__ void __launch_bounds__(NT, 2)
                         a += tt[R + k] * (col[(R - k) * TX] + col[(R + k) * TX]);
                     ring[q][j] = a;
                 }
-                const int x = x0 + ox, y = y0 + oy, o = s - R;
-                if (t >= 2 * R && x < g.nx && y < g.ny) {
-                    long long i = (long long)o * sxy + (long long)y * g.nx + x;
+                if (t >= 2 * R && o_in) {
+                    const int i = (s - R) * sxy + o_off;
                     float n2 = 0.f;
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {

@@ -57,15 +57,31 @@ __global__ void __launch_bounds__(ST_X * ST_Y)
     const int sxy = g.nx * g.ny;
     const float* U[3] = {u, u + g.V, u + 2 * g.V};
 
-    auto load_plane = [&](int zp, int slot) {
-        int zc_ = min(max(zp, 0), g.nz - 1);
-        for (int k = tid; k < 3 * ST_PLANE; k += ST_X * ST_Y) {
+    // Each thread loads fixed halo positions of every plane; their clamped
+    // in-plane offsets and smem slots are computed once.
+    constexpr int NLD = (3 * ST_PLANE + ST_X * ST_Y - 1) / (ST_X * ST_Y);
+    const float* ld_src[NLD];
+    int ld_dst[NLD];
+#pragma unroll
+    for (int r = 0; r < NLD; ++r) {
+        int k = tid + r * ST_X * ST_Y;
+        ld_dst[r] = -1;
+        ld_src[r] = u;
+        if (k < 3 * ST_PLANE) {
             int q = k / ST_PLANE, rem = k - q * ST_PLANE;
             int hy = rem / ST_HX, hx = rem - hy * ST_HX;
             int gx = min(max(x0 - 1 + hx, 0), g.nx - 1);
             int gy = min(max(y0 - 1 + hy, 0), g.ny - 1);
-            ring[slot][q][rem] = __ldg(U[q] + zc_ * sxy + gy * g.nx + gx);
+            ld_src[r] = u + q * g.V + gy * g.nx + gx;
+            ld_dst[r] = q * ST_PLANE + rem;
         }
+    }
+    auto load_plane = [&](int zp, int slot) {
+        const int zo = min(max(zp, 0), g.nz - 1) * sxy;
+        float* dst = &ring[slot][0][0];
+#pragma unroll
+        for (int r = 0; r < NLD; ++r)
+            if (ld_dst[r] >= 0) dst[ld_dst[r]] = __ldg(ld_src[r] + zo);
     };
     load_plane(z0 - 1, (z0 + 2) % 3);
     load_plane(z0, z0 % 3);
