@@ -205,6 +205,42 @@ LM_API int lm_state_load(lm_ctx *ctx, const void *buf, size_t nbytes);
 LM_API int lm_time_passes(lm_ctx *ctx, float *u, int n, double *ms_eval,
                           double *ms_step);
 
+/* ---- batches of pairs ------------------------------------------------- */
+/* A batch registers npairs independent pairs (shapes may differ, one dtype)
+ * with the same parameters.  Every pass of an iteration is one kernel launch
+ * over the work of all pairs (CTAs are shared among the pairs in proportion
+ * to their voxels), an iteration is one replay of a captured CUDA graph,
+ * and each pair keeps its own damping, loss history and rejection state on
+ * the device.  Arrays below have npairs entries. */
+typedef struct lm_batch lm_batch;
+
+/* fixed[i], moving[i]: image descriptors as for lm_init (data kept for the
+ * batch's lifetime).  LM_EINVAL on bad shapes, mixed dtypes or parameters. */
+LM_API int lm_batch_init(lm_batch **b, int npairs, const lm_volume *fixed,
+                         const lm_volume *moving, const lm_params *p,
+                         void *cuda_stream);
+LM_API void lm_batch_destroy(lm_batch *b);
+/* Loss (host doubles) and gmax (host floats, may be NULL) of each pair at
+ * u[i] (device fields); g_out (array of device pointers, may be NULL)
+ * receives the smoothed gradients.  Synchronises. */
+LM_API int lm_batch_eval(lm_batch *b, const float *const *u,
+                         float *const *g_out, double *loss, float *gmax);
+/* As lm_reset for every pair (u[i]: device fields, in/out). */
+LM_API int lm_batch_reset(lm_batch *b, float *const *u);
+/* n LM iterations of every pair (u as given to lm_batch_reset); infos
+ * (host, npairs entries, may be NULL) receive each pair's last outcome. */
+LM_API int lm_batch_iterate(lm_batch *b, float *const *u, int n,
+                            lm_step_info *infos);
+/* Coarse-to-fine registration of every pair (as lm_register); reps (host,
+ * npairs entries, may be NULL). */
+LM_API int lm_batch_register(lm_batch *b, const lm_schedule *s,
+                             float *const *u, lm_report *reps);
+/* One-shot form: create a batch, register, destroy. */
+LM_API int lm_register_batch(int npairs, const lm_volume *fixed,
+                             const lm_volume *moving, float *const *u,
+                             const lm_params *p, const lm_schedule *s,
+                             void *cuda_stream, lm_report *reps);
+
 /* ---- evaluation without allocation ------------------------------------ */
 /* The paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory while they evaluate (code inside another

@@ -1,19 +1,23 @@
 // Host runtime behind the C ABI of include/lmreg.h: argument validation,
-// context scratch, the ordering of the kernels of one LM iteration (with
-// its rejected retries unrolled so no host round trip is needed), CUDA
-// graph replay of iterations, the coarse-to-fine schedule, checkpoints.
+// device scratch, the ordering of the kernels of one LM iteration (rejected
+// retries unrolled so no host round trip is needed), CUDA graph replay of
+// iterations, the coarse-to-fine schedule, batches of pairs, checkpoints.
+//
+// A Core holds a batch of pairs: a device table of PairDesc entries, the
+// per-pair buffers and state, and the shared partial arrays.  The
+// single-pair context (lm_ctx) is a Core of one pair; lm_batch is a Core of
+// many.  All kernels of an iteration read the table at run time, so one
+// captured CUDA graph serves any caller field pointers.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <vector>
 
-#include <cstdlib>
-#include <mutex>
-
-#include "lm_fused.cuh"
 #include "lm_kernels.cuh"
 #include "lm_pyramid.cuh"
 
@@ -31,14 +35,6 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-#define LM_CK(call)                                                        \
-    do {                                                                   \
-        cudaError_t e_ = (call);                                           \
-        if (e_ != cudaSuccess)                                             \
-            return fail(LM_ECUDA, "%s failed: %s", #call,                  \
-                        cudaGetErrorString(e_));                           \
-    } while (0)
-
 }  // namespace
 
 void lmk::set_last_error(const char* msg) {
@@ -46,6 +42,14 @@ void lmk::set_last_error(const char* msg) {
 }
 
 namespace {
+
+#define LM_CK(call)                                                        \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess)                                             \
+            return fail(LM_ECUDA, "%s failed: %s", #call,                  \
+                        cudaGetErrorString(e_));                           \
+    } while (0)
 
 bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -117,168 +121,305 @@ int check_volume(const lm_volume* v, const char* name) {
     return LM_OK;
 }
 
-}  // namespace
+int check_pair(const lm_volume* f, const lm_volume* m) {
+    int rc;
+    if ((rc = check_volume(f, "fixed")) != LM_OK) return rc;
+    if ((rc = check_volume(m, "moving")) != LM_OK) return rc;
+    if (f->D != m->D || f->H != m->H || f->W != m->W)
+        return fail(LM_EINVAL, "fixed and moving shapes differ");
+    if (f->dtype != m->dtype)
+        return fail(LM_EINVAL, "fixed and moving dtypes differ");
+    return LM_OK;
+}
 
-struct lm_ctx {
-    Geom g{};
+// ---------------------------------------------------------------------
+// Core: a batch of pairs with its device scratch and state.
+// ---------------------------------------------------------------------
+struct Core {
+    int npairs = 0;
     int dtype = LM_F32;
-    const void* F = nullptr;
-    const void* M = nullptr;
     lm_params p{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int device = 0;
-    LnccConsts lc{};
-    DecideConsts dc{};
-    Taps wtaps{};
-
-    // device buffers
-    float* u1 = nullptr;         // field slot 1
-    float* gs[2] = {nullptr, nullptr};
-    float* tmpA = nullptr;       // warp smoothing temporaries
-    float* tmpB = nullptr;
-    StagedScratch sc{};
-    bool staged = false;         // staged evaluation schedule (debug aid)
-    FusedPlan plan{};
-    QScale* qs = nullptr;        // fixed-point scale of the window moments
-    float2* mm_part = nullptr;   // image range partials
-    float* dldj = nullptr;       // dL/dJ between the fused kernels
-    float* gdiscard = nullptr;   // gradient sink for lm_eval without g_out
-    Partials part{};
-    DevState* st = nullptr;
-    LogEntry* log = nullptr;
-    EvalOut* eout = nullptr;
+    std::vector<PairDesc> hpd;     // host copy of the table
+    PairDesc* dpd = nullptr;       // device table
+    Batch b{};
     std::vector<void*> allocs;
-
-    // pinned host mirrors
-    DevState* h_st = nullptr;
-    EvalOut* h_eout = nullptr;
-    LogEntry* h_log = nullptr;
-
-    float* bound_u = nullptr;
+    EvalOut* eout = nullptr;       // npairs
+    DevState* h_st = nullptr;      // pinned, npairs
+    EvalOut* h_eout = nullptr;     // pinned, npairs
+    LogEntry* h_log = nullptr;     // pinned, LOG_CAP
+    std::vector<float*> gsink;     // lm_eval gradient sinks (lazy)
     bool have_reset = false;
-
     cudaGraphExec_t gexec = nullptr;
-    float* graph_u = nullptr;
-    int graph_launches = 0;      // kernels per replay of gexec
-    long long launches = 0;      // kernels enqueued since lm_reset
+    int graph_launches = 0;
+    long long launches = 0;
 
-    // coarse levels for lm_register (factor -> context), built lazily
-    struct Level {
-        int factor = 0;
-        lm_ctx* ctx = nullptr;
-        void* Fl = nullptr;
-        void* Ml = nullptr;
-        float* ul = nullptr;
-    };
-    std::vector<Level> levels;
-    float* u_tmp = nullptr;      // full-res field staging for resampling
+    ~Core() {
+        if (stream) cudaStreamSynchronize(stream);
+        else cudaDeviceSynchronize();
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (void* q : allocs) cudaFree(q);
+        if (h_st) cudaFreeHost(h_st);
+        if (h_eout) cudaFreeHost(h_eout);
+        if (h_log) cudaFreeHost(h_log);
+    }
+
+    template <typename T>
+    int dalloc(T** out, size_t bytes) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LM_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes,
+                        cudaGetErrorString(e));
+        }
+        allocs.push_back(q);
+        *out = (T*)q;
+        return LM_OK;
+    }
+
+    // Host table -> device (pageable source: safe to modify on return).
+    int push_table() {
+        LM_CK(cudaMemcpyAsync(dpd, hpd.data(), npairs * sizeof(PairDesc),
+                              cudaMemcpyHostToDevice, stream));
+        return LM_OK;
+    }
+
+    int read_states() {
+        LM_CK(cudaMemcpyAsync(h_st, hpd[0].st, npairs * sizeof(DevState),
+                              cudaMemcpyDeviceToHost, stream));
+        LM_CK(cudaStreamSynchronize(stream));
+        for (int i = 0; i < npairs; ++i)
+            if (h_st[i].status & STATUS_NONFINITE)
+                return fail(LM_ENONFINITE,
+                            "loss or gradient is not finite (pair %d)", i);
+        return LM_OK;
+    }
+
+    // One LM iteration for every pair: attempts 0..max_retries when
+    // rejection is on (later attempts are no-ops once a pair is decided).
+    int enqueue_iteration(cudaStream_t s) {
+        int attempts = p.reject ? p.max_retries + 1 : 1;
+        int n = 0;
+        for (int j = 0; j < attempts; ++j) {
+            n += batch_step(b, j, s);
+            n += batch_eval(b, EVAL_TRIAL, j, s);
+            n += batch_finalize(b, FIN_DECIDE, j, nullptr, s);
+        }
+        return n;
+    }
+
+    int iterate(int n) {
+        if (n <= 0) return LM_OK;
+        if (!gexec) {
+            if (!cap_stream)
+                LM_CK(cudaStreamCreateWithFlags(&cap_stream,
+                                                cudaStreamNonBlocking));
+            cudaGraph_t graph;
+            LM_CK(cudaStreamBeginCapture(cap_stream,
+                                         cudaStreamCaptureModeThreadLocal));
+            graph_launches = enqueue_iteration(cap_stream);
+            cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+            if (e != cudaSuccess)
+                return fail(LM_ECUDA, "graph capture failed: %s",
+                            cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess)
+                return fail(LM_ECUDA, "graph instantiate failed: %s",
+                            cudaGetErrorString(e));
+        }
+        for (int i = 0; i < n; ++i) LM_CK(cudaGraphLaunch(gexec, stream));
+        launches += (long long)n * graph_launches;
+        launches += batch_sync_back(b, stream);
+        LM_CK(cudaGetLastError());
+        return LM_OK;
+    }
 };
 
-namespace {
+// Creates a Core for npairs pairs (all of one dtype).
+int core_create(std::unique_ptr<Core>& out, int npairs,
+                const lm_volume* fixed, const lm_volume* moving,
+                const lm_params* p, void* stream) {
+    if (npairs < 1) return fail(LM_EINVAL, "npairs must be >= 1");
+    if (!fixed || !moving) return fail(LM_EINVAL, "fixed / moving is NULL");
+    int rc;
+    for (int i = 0; i < npairs; ++i)
+        if ((rc = check_pair(&fixed[i], &moving[i])) != LM_OK) return rc;
+    for (int i = 1; i < npairs; ++i)
+        if (fixed[i].dtype != fixed[0].dtype)
+            return fail(LM_EINVAL, "all pairs of a batch share one dtype");
+    lm_params prm;
+    if (p) prm = *p;
+    else lm_default_params(&prm);
+    if ((rc = check_params(&prm)) != LM_OK) return rc;
+    for (int i = 0; i < npairs; ++i)
+        if (!is_device_ptr(fixed[i].data) || !is_device_ptr(moving[i].data))
+            return fail(LM_EINVAL, "image data of pair %d is not a device "
+                                   "pointer", i);
+    static std::once_flag setup_once;
+    static cudaError_t setup_err = cudaSuccess;
+    std::call_once(setup_once, [] { setup_err = fused_setup(); });
+    if (setup_err != cudaSuccess)
+        return fail(LM_ECUDA, "kernel setup failed: %s",
+                    cudaGetErrorString(setup_err));
 
-template <typename T>
-int dalloc(lm_ctx* c, T** out, size_t bytes) {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
+    auto c = std::make_unique<Core>();
+    c->npairs = npairs;
+    c->dtype = fixed[0].dtype;
+    c->p = prm;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    int num_sms = 0;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount,
+                               c->device) != cudaSuccess || num_sms < 1) {
         cudaGetLastError();
-        return fail(LM_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes,
-                    cudaGetErrorString(e));
+        num_sms = 148;
     }
-    c->allocs.push_back(p);
-    *out = (T*)p;
+    c->hpd.resize(npairs);
+    c->gsink.assign(npairs, nullptr);
+    for (int i = 0; i < npairs; ++i) {
+        PairDesc& d = c->hpd[i];
+        memset(&d, 0, sizeof(d));
+        d.g.nx = fixed[i].W;
+        d.g.ny = fixed[i].H;
+        d.g.nz = fixed[i].D;
+        d.g.V = (long long)fixed[i].W * fixed[i].H * fixed[i].D;
+        d.F = fixed[i].data;
+        d.M = moving[i].data;
+    }
+    BatchPlan plan = plan_batch(c->hpd.data(), npairs, prm.win, num_sms);
+    const size_t f4 = sizeof(float);
+    const bool smooth = prm.sigma_warp > 0;
+    // per-pair buffers
+    DevState* st = nullptr;
+    QScale* qs = nullptr;
+    LogEntry* lg = nullptr;
+    if ((rc = c->dalloc(&st, npairs * sizeof(DevState))) ||
+        (rc = c->dalloc(&qs, npairs * sizeof(QScale))) ||
+        (rc = c->dalloc(&lg, npairs * sizeof(LogEntry) * LOG_CAP)) ||
+        (rc = c->dalloc(&c->eout, npairs * sizeof(EvalOut))) ||
+        (rc = c->dalloc(&c->dpd, npairs * sizeof(PairDesc))) ||
+        (rc = c->dalloc(&c->b.part.loss, plan.e1_ctas * sizeof(double))) ||
+        (rc = c->dalloc(&c->b.part.g2max, plan.e2_ctas * sizeof(float))) ||
+        (rc = c->dalloc(&c->b.mm_part,
+                        (size_t)npairs * plan.mm_ctas * sizeof(float2))))
+        return rc;
+    for (int i = 0; i < npairs; ++i) {
+        PairDesc& d = c->hpd[i];
+        size_t V = (size_t)d.g.V;
+        if ((rc = c->dalloc(&d.u1, 3 * V * f4)) ||
+            (rc = c->dalloc(&d.g0, 3 * V * f4)) ||
+            (rc = c->dalloc(&d.g1, 3 * V * f4)) ||
+            (rc = c->dalloc(&d.dldj, V * f4)))
+            return rc;
+        if (smooth && ((rc = c->dalloc(&d.wtmpA, 3 * V * f4)) ||
+                       (rc = c->dalloc(&d.wtmpB, 3 * V * f4))))
+            return rc;
+        d.st = st + i;
+        d.qs = qs + i;
+        d.log = lg + (size_t)i * LOG_CAP;
+        d.u0 = nullptr;
+    }
+    if (cudaMallocHost(&c->h_st, npairs * sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost(&c->h_eout, npairs * sizeof(EvalOut)) != cudaSuccess ||
+        cudaMallocHost(&c->h_log, LOG_CAP * sizeof(LogEntry)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LM_ENOMEM, "pinned host allocation failed");
+    }
+    LM_CK(cudaMemsetAsync(st, 0, npairs * sizeof(DevState), c->stream));
+    c->b.pd = c->dpd;
+    c->b.npairs = npairs;
+    c->b.dtype = c->dtype;
+    c->b.plan = plan;
+    c->b.c.win = prm.win;
+    c->b.c.eps_nr = prm.eps_nr;
+    c->b.c.eps_dr = prm.eps_dr;
+    c->b.c.inv_k3 = (float)(1.0 / ((double)prm.win * prm.win * prm.win));
+    c->b.c.gtaps = make_taps(prm.sigma_grad);
+    c->b.d.lambda0 = prm.lambda0;
+    c->b.d.mu_inc = prm.mu_inc;
+    c->b.d.mu_dec = prm.mu_dec;
+    c->b.d.lambda_max = prm.lambda_max;
+    c->b.d.tau = prm.tau;
+    c->b.d.reject = prm.reject;
+    c->b.d.max_retries = prm.max_retries;
+    c->b.wtaps = make_taps(prm.sigma_warp);
+    c->b.step = prm.step;
+    if ((rc = c->push_table()) != LM_OK) return rc;
+    out = std::move(c);
     return LM_OK;
 }
 
-int run_eval(lm_ctx* c, int mode, const float* u_in, float* g_out, float* u0,
-             int attempt, cudaStream_t s);
-
-EvalLaunch make_eval(lm_ctx* c, int mode, const float* u_in, float* g_out,
-                     float* u0, int attempt) {
-    EvalLaunch a;
-    a.g = c->g;
-    a.F = c->F;
-    a.M = c->M;
-    a.dtype = c->dtype;
-    a.io.u_in = u_in;
-    a.io.g_out = g_out;
-    a.io.u0 = u0;
-    a.io.u1 = c->u1;
-    a.io.g0 = c->gs[0];
-    a.io.g1 = c->gs[1];
-    a.io.st = c->st;
-    a.io.mode = mode;
-    a.io.attempt = attempt;
-    a.c = c->lc;
-    a.part = c->part;
-    a.sc = c->sc;
-    return a;
-}
-
-// Pass 1 in the context's schedule; returns the number of kernels.
-int run_eval(lm_ctx* c, int mode, const float* u_in, float* g_out, float* u0,
-             int attempt, cudaStream_t s) {
-    EvalLaunch e = make_eval(c, mode, u_in, g_out, u0, attempt);
-    if (c->staged) return eval_staged(e, s);
-    FusedLaunch f;
-    f.g = e.g;
-    f.F = e.F;
-    f.M = e.M;
-    f.dtype = e.dtype;
-    f.io = e.io;
-    f.c = e.c;
-    f.plan = c->plan;
-    f.qs = c->qs;
-    f.dldj = c->dldj;
-    f.part = c->part;
-    return eval_fused(f, s);
-}
-
-FinLaunch make_fin(lm_ctx* c, int mode, int attempt) {
-    FinLaunch f;
-    f.part = c->part;
-    f.st = c->st;
-    f.out = c->eout;
-    f.log = c->log;
-    f.d = c->dc;
-    f.inv_V = 1.0 / (double)c->g.V;
-    f.mode = mode;
-    f.attempt = attempt;
-    return f;
-}
-
-// Enqueue one LM iteration on stream s: attempts 0..max_retries when
-// rejection is on (later attempts are no-ops once the iteration is done).
-int enqueue_iteration(lm_ctx* c, float* u, cudaStream_t s) {
-    int attempts = c->p.reject ? c->p.max_retries + 1 : 1;
-    int n = 0;
-    for (int j = 0; j < attempts; ++j) {
-        StepLaunch sl;
-        sl.g = c->g;
-        sl.u0 = u;
-        sl.u1 = c->u1;
-        sl.g0 = c->gs[0];
-        sl.g1 = c->gs[1];
-        sl.st = c->st;
-        sl.step = c->p.step;
-        sl.attempt = j;
-        sl.wtaps = c->wtaps;
-        sl.tmpA = c->tmpA;
-        sl.tmpB = c->tmpB;
-        n += step_compose(sl, s);
-        n += run_eval(c, EVAL_TRIAL, nullptr, nullptr, u, j, s);
-        n += finalize(make_fin(c, FIN_DECIDE, j), s);
+// Evaluation of explicit fields (no optimiser state change); losses and
+// gmax to host.  Without g_out a pair's gradient goes to a sink volume
+// allocated on first use.
+int core_eval(Core* c, const float* const* u, float* const* g_out,
+              double* loss, float* gmax) {
+    for (int i = 0; i < c->npairs; ++i) {
+        if (!is_device_ptr(u[i]))
+            return fail(LM_EINVAL, "u of pair %d is not a device pointer", i);
+        if (g_out && g_out[i] && !is_device_ptr(g_out[i]))
+            return fail(LM_EINVAL, "g_out of pair %d is not a device pointer",
+                        i);
     }
-    return n;
-}
-
-int read_state(lm_ctx* c) {
-    LM_CK(cudaMemcpyAsync(c->h_st, c->st, sizeof(DevState),
+    int rc;
+    for (int i = 0; i < c->npairs; ++i) {
+        if ((g_out && g_out[i]) || c->gsink[i]) continue;
+        if ((rc = c->dalloc(&c->gsink[i],
+                            3 * (size_t)c->hpd[i].g.V * sizeof(float))) != LM_OK)
+            return rc;
+    }
+    std::vector<PairDesc> save = c->hpd;
+    for (int i = 0; i < c->npairs; ++i) {
+        c->hpd[i].u_in = u[i];
+        c->hpd[i].g_out = (g_out && g_out[i]) ? g_out[i] : c->gsink[i];
+    }
+    rc = c->push_table();
+    if (rc != LM_OK) return rc;
+    batch_qscale(c->b, c->stream);
+    batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);
+    batch_finalize(c->b, FIN_EXPLICIT, 0, c->eout, c->stream);
+    LM_CK(cudaGetLastError());
+    LM_CK(cudaMemcpyAsync(c->h_eout, c->eout, c->npairs * sizeof(EvalOut),
                           cudaMemcpyDeviceToHost, c->stream));
     LM_CK(cudaStreamSynchronize(c->stream));
-    if (c->h_st->status & STATUS_NONFINITE)
-        return fail(LM_ENONFINITE, "loss or gradient is not finite");
+    c->hpd = save;
+    if ((rc = c->push_table()) != LM_OK) return rc;
+    for (int i = 0; i < c->npairs; ++i) {
+        if (loss) loss[i] = c->h_eout[i].L;
+        if (gmax) gmax[i] = c->h_eout[i].gmax;
+        if (c->h_eout[i].status & STATUS_NONFINITE)
+            return fail(LM_ENONFINITE,
+                        "loss or gradient is not finite (pair %d)", i);
+    }
+    return LM_OK;
+}
+
+int core_reset(Core* c, float* const* u) {
+    for (int i = 0; i < c->npairs; ++i)
+        if (!is_device_ptr(u[i]))
+            return fail(LM_EINVAL, "u of pair %d is not a device pointer", i);
+    for (int i = 0; i < c->npairs; ++i) c->hpd[i].u0 = u[i];
+    int rc = c->push_table();
+    if (rc != LM_OK) return rc;
+    c->launches = batch_qscale(c->b, c->stream);
+    c->launches += batch_eval(c->b, EVAL_RESET, 0, c->stream);
+    c->launches += batch_finalize(c->b, FIN_RESET, 0, nullptr, c->stream);
+    LM_CK(cudaGetLastError());
+    c->have_reset = true;
+    return LM_OK;
+}
+
+int core_check_bound(Core* c, float* const* u) {
+    if (!c->have_reset) return fail(LM_ESTATE, "lm_reset was not called");
+    for (int i = 0; i < c->npairs; ++i)
+        if (u[i] != c->hpd[i].u0)
+            return fail(LM_ESTATE,
+                        "u of pair %d is not the field passed to reset", i);
     return LM_OK;
 }
 
@@ -292,15 +433,43 @@ void fill_info(const DevState& s, lm_step_info* info) {
     info->evals = s.retries + 1;
 }
 
-int check_bound(lm_ctx* c, float* u) {
-    if (!c) return fail(LM_EINVAL, "ctx is NULL");
-    if (!c->have_reset) return fail(LM_ESTATE, "lm_reset was not called");
-    if (u != c->bound_u)
-        return fail(LM_ESTATE, "u is not the field passed to lm_reset");
-    return LM_OK;
+}  // namespace
+
+struct lm_ctx {
+    std::unique_ptr<Core> core;
+    // coarse levels for lm_register (factor -> context), built lazily
+    struct Level {
+        int factor = 0;
+        lm_ctx* ctx = nullptr;
+        void* Fl = nullptr;
+        void* Ml = nullptr;
+        float* ul = nullptr;
+    };
+    std::vector<Level> levels;
+    float* u_tmp = nullptr;      // full-res staging (3V floats)
+    ~lm_ctx();
+};
+
+struct lm_batch {
+    std::unique_ptr<Core> core;
+    struct Level {
+        int factor = 0;
+        lm_batch* b = nullptr;
+        std::vector<void*> Fl, Ml;
+        std::vector<float*> ul;
+    };
+    std::vector<Level> levels;
+    std::vector<float*> u_tmp;
+    ~lm_batch();
+};
+
+lm_ctx::~lm_ctx() {
+    for (auto& l : levels) lm_destroy(l.ctx);
 }
 
-}  // namespace
+lm_batch::~lm_batch() {
+    for (auto& l : levels) lm_batch_destroy(l.b);
+}
 
 extern "C" {
 
@@ -340,16 +509,7 @@ const char* lm_last_error(void) { return g_err; }
 
 void lm_destroy(lm_ctx* c) {
     if (!c) return;
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    else cudaDeviceSynchronize();
-    for (auto& l : c->levels) lm_destroy(l.ctx);
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    for (void* p : c->allocs) cudaFree(p);
-    if (c->h_st) cudaFreeHost(c->h_st);
-    if (c->h_eout) cudaFreeHost(c->h_eout);
-    if (c->h_log) cudaFreeHost(c->h_log);
-    delete c;
+    delete c;   // the Core's destructor synchronises and frees
 }
 
 int lm_init(lm_ctx** out, const lm_volume* fixed, const lm_volume* moving,
@@ -357,140 +517,11 @@ int lm_init(lm_ctx** out, const lm_volume* fixed, const lm_volume* moving,
     g_err[0] = 0;
     if (!out) return fail(LM_EINVAL, "ctx out-pointer is NULL");
     *out = nullptr;
-    int rc;
-    if ((rc = check_volume(fixed, "fixed")) != LM_OK) return rc;
-    if ((rc = check_volume(moving, "moving")) != LM_OK) return rc;
-    if (fixed->D != moving->D || fixed->H != moving->H ||
-        fixed->W != moving->W)
-        return fail(LM_EINVAL, "fixed and moving shapes differ");
-    if (fixed->dtype != moving->dtype)
-        return fail(LM_EINVAL, "fixed and moving dtypes differ");
-    lm_params prm;
-    if (p) prm = *p;
-    else lm_default_params(&prm);
-    if ((rc = check_params(&prm)) != LM_OK) return rc;
-    if (!is_device_ptr(fixed->data))
-        return fail(LM_EINVAL, "fixed data is not a device pointer");
-    if (!is_device_ptr(moving->data))
-        return fail(LM_EINVAL, "moving data is not a device pointer");
-
-    lm_ctx* c = new lm_ctx();
-    c->g.nx = fixed->W;
-    c->g.ny = fixed->H;
-    c->g.nz = fixed->D;
-    c->g.V = (long long)fixed->W * fixed->H * fixed->D;
-    c->dtype = fixed->dtype;
-    c->F = fixed->data;
-    c->M = moving->data;
-    c->p = prm;
-    c->stream = (cudaStream_t)cuda_stream;
-    cudaGetDevice(&c->device);
-
-    c->lc.win = prm.win;
-    c->lc.eps_nr = prm.eps_nr;
-    c->lc.eps_dr = prm.eps_dr;
-    c->lc.inv_k3 = (float)(1.0 / ((double)prm.win * prm.win * prm.win));
-    c->lc.inv_V = (float)(1.0 / (double)c->g.V);
-    c->lc.gtaps = make_taps(prm.sigma_grad);
-    c->lc.shift = 0.f;
-    c->wtaps = make_taps(prm.sigma_warp);
-    c->dc.lambda0 = prm.lambda0;
-    c->dc.mu_inc = prm.mu_inc;
-    c->dc.mu_dec = prm.mu_dec;
-    c->dc.lambda_max = prm.lambda_max;
-    c->dc.tau = prm.tau;
-    c->dc.reject = prm.reject;
-    c->dc.max_retries = prm.max_retries;
-
-    const size_t V = (size_t)c->g.V;
-    const size_t f4 = sizeof(float);
-    {
-        const char* e = getenv("LMREG_STAGED");
-        c->staged = e && e[0] == '1';
-    }
-    static std::once_flag setup_once;
-    static cudaError_t setup_err = cudaSuccess;
-    std::call_once(setup_once, [] { setup_err = fused_setup(); });
-    if (setup_err != cudaSuccess) {
-        lm_destroy(c);
-        return fail(LM_ECUDA, "kernel setup failed: %s",
-                    cudaGetErrorString(setup_err));
-    }
-    int num_sms = 0;
-    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount,
-                               c->device) != cudaSuccess || num_sms < 1) {
-        cudaGetLastError();
-        num_sms = 148;
-    }
-    c->plan = fused_plan(c->g, prm.win, num_sms);
-    int nl, ng;
-    if (c->staged) {
-        eval_staged_partials(c->g, &nl, &ng);
-    } else {
-        nl = c->plan.e1_ctas;
-        ng = c->plan.e2_ctas;
-    }
-    int nl_alloc = std::max(nl, (int)std::min<long long>((c->g.V + 255) / 256, 1024));
-    c->part.n_loss = nl;
-    c->part.n_g2 = ng;
-    if ((rc = dalloc(c, &c->u1, 3 * V * f4)) ||
-        (rc = dalloc(c, &c->gs[0], 3 * V * f4)) ||
-        (rc = dalloc(c, &c->gs[1], 3 * V * f4)) ||
-        (rc = dalloc(c, &c->gdiscard, 3 * V * f4)) ||
-        (rc = dalloc(c, &c->part.loss, (size_t)nl_alloc * sizeof(double))) ||
-        (rc = dalloc(c, &c->part.g2max, (size_t)ng * sizeof(float))) ||
-        (rc = dalloc(c, &c->st, sizeof(DevState))) ||
-        (rc = dalloc(c, &c->log, LOG_CAP * sizeof(LogEntry))) ||
-        (rc = dalloc(c, &c->eout, sizeof(EvalOut)))) {
-        lm_destroy(c);
+    auto c = new lm_ctx();
+    int rc = core_create(c->core, 1, fixed, moving, p, cuda_stream);
+    if (rc != LM_OK) {
+        delete c;
         return rc;
-    }
-    if (c->staged) {
-        if ((rc = dalloc(c, &c->sc.J, V * f4)) ||
-            (rc = dalloc(c, &c->sc.dJ, 3 * V * f4)) ||
-            (rc = dalloc(c, &c->sc.S, 5 * V * f4)) ||
-            (rc = dalloc(c, &c->sc.T, 5 * V * f4)) ||
-            (rc = dalloc(c, &c->sc.abc, 3 * V * f4)) ||
-            (rc = dalloc(c, &c->sc.graw, 3 * V * f4))) {
-            lm_destroy(c);
-            return rc;
-        }
-    } else {
-        if ((rc = dalloc(c, &c->dldj, V * f4)) ||
-            (rc = dalloc(c, &c->qs, sizeof(QScale))) ||
-            (rc = dalloc(c, &c->mm_part,
-                         (size_t)c->plan.minmax_ctas * sizeof(float2)))) {
-            lm_destroy(c);
-            return rc;
-        }
-    }
-    if (c->wtaps.R > 0) {
-        if ((rc = dalloc(c, &c->tmpA, 3 * V * f4)) ||
-            (rc = dalloc(c, &c->tmpB, 3 * V * f4))) {
-            lm_destroy(c);
-            return rc;
-        }
-    }
-    if (cudaMallocHost(&c->h_st, sizeof(DevState)) != cudaSuccess ||
-        cudaMallocHost(&c->h_eout, sizeof(EvalOut)) != cudaSuccess ||
-        cudaMallocHost(&c->h_log, LOG_CAP * sizeof(LogEntry)) != cudaSuccess) {
-        cudaGetLastError();
-        lm_destroy(c);
-        return fail(LM_ENOMEM, "pinned host allocation failed");
-    }
-    if (cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream) != cudaSuccess) {
-        lm_destroy(c);
-        return fail(LM_ECUDA, "cudaMemsetAsync failed");
-    }
-    if (c->staged) {
-        // common shift of the staged box sums: the mean intensity of F
-        float mean = 0.f;
-        if ((rc = lmk::image_mean(c->F, c->dtype, c->g.V, c->part.loss,
-                                  &mean, c->stream)) != 0) {
-            lm_destroy(c);
-            return fail(LM_ECUDA, "image mean failed");
-        }
-        c->lc.shift = mean;
     }
     *out = c;
     return LM_OK;
@@ -499,100 +530,51 @@ int lm_init(lm_ctx** out, const lm_volume* fixed, const lm_volume* moving,
 int lm_eval(lm_ctx* c, const float* u, double* loss, float* g_out,
             float* gmax) {
     if (!c) return fail(LM_EINVAL, "ctx is NULL");
-    if (!is_device_ptr(u)) return fail(LM_EINVAL, "u is not a device pointer");
-    if (g_out && !is_device_ptr(g_out))
-        return fail(LM_EINVAL, "g_out is not a device pointer");
-    float* gdst = g_out ? g_out : c->gdiscard;
-    if (!c->staged)
-        fused_qscale(c->F, c->M, c->dtype, c->g, c->plan, c->p.win,
-                     c->mm_part, c->qs, c->stream);
-    run_eval(c, EVAL_EXPLICIT, u, gdst, (float*)u, 0, c->stream);
-    finalize(make_fin(c, FIN_EXPLICIT, 0), c->stream);
-    LM_CK(cudaGetLastError());
-    LM_CK(cudaMemcpyAsync(c->h_eout, c->eout, sizeof(EvalOut),
-                          cudaMemcpyDeviceToHost, c->stream));
-    LM_CK(cudaStreamSynchronize(c->stream));
-    if (loss) *loss = c->h_eout->L;
-    if (gmax) *gmax = c->h_eout->gmax;
-    if (c->h_eout->status & STATUS_NONFINITE)
-        return fail(LM_ENONFINITE, "loss or gradient is not finite");
-    return LM_OK;
+    float* gs[1] = {g_out};
+    return core_eval(c->core.get(), &u, g_out ? gs : nullptr, loss, gmax);
 }
 
 int lm_reset(lm_ctx* c, float* u) {
     if (!c) return fail(LM_EINVAL, "ctx is NULL");
-    if (!is_device_ptr(u)) return fail(LM_EINVAL, "u is not a device pointer");
-    c->launches = 0;
-    if (!c->staged)
-        c->launches += fused_qscale(c->F, c->M, c->dtype, c->g, c->plan,
-                                    c->p.win, c->mm_part, c->qs, c->stream);
-    c->launches += run_eval(c, EVAL_RESET, nullptr, nullptr, u, 0, c->stream);
-    c->launches += finalize(make_fin(c, FIN_RESET, 0), c->stream);
-    LM_CK(cudaGetLastError());
-    c->bound_u = u;
-    c->have_reset = true;
-    return LM_OK;
+    return core_reset(c->core.get(), &u);
 }
 
 int lm_step(lm_ctx* c, float* u, lm_step_info* info) {
-    int rc = check_bound(c, u);
+    if (!c) return fail(LM_EINVAL, "ctx is NULL");
+    Core* k = c->core.get();
+    int rc = core_check_bound(k, &u);
     if (rc) return rc;
-    c->launches += enqueue_iteration(c, u, c->stream);
-    c->launches += sync_back(c->g, u, c->u1, c->st, c->stream);
+    k->launches += k->enqueue_iteration(k->stream);
+    k->launches += batch_sync_back(k->b, k->stream);
     LM_CK(cudaGetLastError());
     if (info) {
-        if ((rc = read_state(c)) != LM_OK) return rc;
-        fill_info(*c->h_st, info);
+        if ((rc = k->read_states()) != LM_OK) return rc;
+        fill_info(k->h_st[0], info);
     }
     return LM_OK;
 }
 
 int lm_iterate(lm_ctx* c, float* u, int n, lm_step_info* info) {
-    int rc = check_bound(c, u);
+    if (!c) return fail(LM_EINVAL, "ctx is NULL");
+    Core* k = c->core.get();
+    int rc = core_check_bound(k, &u);
     if (rc) return rc;
     if (n < 0) return fail(LM_EINVAL, "n must be >= 0");
-    if (n > 0) {
-        if (!c->gexec || c->graph_u != u) {
-            if (c->gexec) {
-                cudaGraphExecDestroy(c->gexec);
-                c->gexec = nullptr;
-            }
-            if (!c->cap_stream)
-                LM_CK(cudaStreamCreateWithFlags(&c->cap_stream,
-                                                cudaStreamNonBlocking));
-            cudaGraph_t graph;
-            LM_CK(cudaStreamBeginCapture(c->cap_stream,
-                                         cudaStreamCaptureModeThreadLocal));
-            c->graph_launches = enqueue_iteration(c, u, c->cap_stream);
-            cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-            if (e != cudaSuccess)
-                return fail(LM_ECUDA, "graph capture failed: %s",
-                            cudaGetErrorString(e));
-            e = cudaGraphInstantiate(&c->gexec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess)
-                return fail(LM_ECUDA, "graph instantiate failed: %s",
-                            cudaGetErrorString(e));
-            c->graph_u = u;
-        }
-        for (int i = 0; i < n; ++i) LM_CK(cudaGraphLaunch(c->gexec, c->stream));
-        c->launches += (long long)n * c->graph_launches;
-        c->launches += sync_back(c->g, u, c->u1, c->st, c->stream);
-        LM_CK(cudaGetLastError());
-    }
+    if ((rc = k->iterate(n)) != LM_OK) return rc;
     if (info) {
-        if ((rc = read_state(c)) != LM_OK) return rc;
-        fill_info(*c->h_st, info);
+        if ((rc = k->read_states()) != LM_OK) return rc;
+        fill_info(k->h_st[0], info);
     }
     return LM_OK;
 }
 
 int lm_get_state(lm_ctx* c, lm_state* out) {
     if (!c || !out) return fail(LM_EINVAL, "NULL argument");
-    LM_CK(cudaMemcpyAsync(c->h_st, c->st, sizeof(DevState),
-                          cudaMemcpyDeviceToHost, c->stream));
-    LM_CK(cudaStreamSynchronize(c->stream));
-    const DevState& s = *c->h_st;
+    Core* k = c->core.get();
+    LM_CK(cudaMemcpyAsync(k->h_st, k->hpd[0].st, sizeof(DevState),
+                          cudaMemcpyDeviceToHost, k->stream));
+    LM_CK(cudaStreamSynchronize(k->stream));
+    const DevState& s = k->h_st[0];
     out->loss = s.L;
     out->loss_prev = s.L_prev;
     out->lambda = s.lambda;
@@ -600,20 +582,21 @@ int lm_get_state(lm_ctx* c, lm_state* out) {
     out->has_prev = s.has_prev;
     out->iter = s.iter;
     out->evals = s.evals;
-    out->kernel_launches = c->launches;
+    out->kernel_launches = k->launches;
     return LM_OK;
 }
 
 int lm_set_state(lm_ctx* c, const lm_state* in) {
     if (!c || !in) return fail(LM_EINVAL, "NULL argument");
-    if (!c->have_reset) return fail(LM_ESTATE, "lm_reset was not called");
+    Core* k = c->core.get();
+    if (!k->have_reset) return fail(LM_ESTATE, "lm_reset was not called");
     if (!(in->lambda > 0) || !std::isfinite(in->lambda) ||
         !std::isfinite(in->loss) || !std::isfinite(in->loss_prev))
         return fail(LM_EINVAL, "state scalars must be finite, lambda > 0");
-    LM_CK(cudaMemcpyAsync(c->h_st, c->st, sizeof(DevState),
-                          cudaMemcpyDeviceToHost, c->stream));
-    LM_CK(cudaStreamSynchronize(c->stream));
-    DevState s = *c->h_st;
+    LM_CK(cudaMemcpyAsync(k->h_st, k->hpd[0].st, sizeof(DevState),
+                          cudaMemcpyDeviceToHost, k->stream));
+    LM_CK(cudaStreamSynchronize(k->stream));
+    DevState s = k->h_st[0];
     s.L = in->loss;
     s.L_prev = in->loss_prev;
     s.lambda = in->lambda;
@@ -621,10 +604,40 @@ int lm_set_state(lm_ctx* c, const lm_state* in) {
     s.has_prev = in->has_prev ? 1 : 0;
     s.iter = in->iter;
     s.evals = in->evals;
-    *c->h_st = s;
-    LM_CK(cudaMemcpyAsync(c->st, c->h_st, sizeof(DevState),
-                          cudaMemcpyHostToDevice, c->stream));
-    LM_CK(cudaStreamSynchronize(c->stream));
+    k->h_st[0] = s;
+    LM_CK(cudaMemcpyAsync(k->hpd[0].st, k->h_st, sizeof(DevState),
+                          cudaMemcpyHostToDevice, k->stream));
+    LM_CK(cudaStreamSynchronize(k->stream));
+    return LM_OK;
+}
+
+int lm_time_passes(lm_ctx* c, float* u, int n, double* ms_eval,
+                   double* ms_step) {
+    if (!c) return fail(LM_EINVAL, "ctx is NULL");
+    Core* k = c->core.get();
+    int rc = core_check_bound(k, &u);
+    if (rc) return rc;
+    if (n < 1 || !ms_eval || !ms_step)
+        return fail(LM_EINVAL, "n must be >= 1 and outputs non-NULL");
+    cudaEvent_t e0, e1, e2;
+    LM_CK(cudaEventCreate(&e0));
+    LM_CK(cudaEventCreate(&e1));
+    LM_CK(cudaEventCreate(&e2));
+    LM_CK(cudaEventRecord(e0, k->stream));
+    for (int i = 0; i < n; ++i) batch_step(k->b, 0, k->stream);
+    LM_CK(cudaEventRecord(e1, k->stream));
+    for (int i = 0; i < n; ++i) batch_eval(k->b, EVAL_TRIAL, 0, k->stream);
+    LM_CK(cudaEventRecord(e2, k->stream));
+    LM_CK(cudaEventSynchronize(e2));
+    float a = 0.f, bb = 0.f;
+    cudaEventElapsedTime(&a, e0, e1);
+    cudaEventElapsedTime(&bb, e1, e2);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    *ms_step = a / n;
+    *ms_eval = bb / n;
+    LM_CK(cudaGetLastError());
     return LM_OK;
 }
 
@@ -643,30 +656,33 @@ struct CkptHeader {
 
 extern "C" int lm_state_save(lm_ctx* c, void* buf, size_t* nbytes) {
     if (!c || !nbytes) return fail(LM_EINVAL, "NULL argument");
-    if (!c->have_reset) return fail(LM_ESTATE, "lm_reset was not called");
+    Core* k = c->core.get();
+    if (!k->have_reset) return fail(LM_ESTATE, "lm_reset was not called");
+    const PairDesc& d = k->hpd[0];
     size_t need = sizeof(CkptHeader) + sizeof(DevState) +
-                  3 * (size_t)c->g.V * sizeof(float);
+                  3 * (size_t)d.g.V * sizeof(float);
     if (!buf) {
         *nbytes = need;
         return LM_OK;
     }
     if (*nbytes < need) return fail(LM_EINVAL, "buffer too small");
     // make sure the field sits in the caller's slot
-    sync_back(c->g, c->bound_u, c->u1, c->st, c->stream);
-    LM_CK(cudaMemcpyAsync(c->h_st, c->st, sizeof(DevState),
-                          cudaMemcpyDeviceToHost, c->stream));
-    LM_CK(cudaStreamSynchronize(c->stream));
+    batch_sync_back(k->b, k->stream);
+    LM_CK(cudaMemcpyAsync(k->h_st, d.st, sizeof(DevState),
+                          cudaMemcpyDeviceToHost, k->stream));
+    LM_CK(cudaStreamSynchronize(k->stream));
     CkptHeader h;
     memcpy(h.magic, "LMREGCK1", 8);
-    h.nx = c->g.nx;
-    h.ny = c->g.ny;
-    h.nz = c->g.nz;
+    h.nx = d.g.nx;
+    h.ny = d.g.ny;
+    h.nz = d.g.nz;
     h.version = 1;
-    char* p = (char*)buf;
-    memcpy(p, &h, sizeof(h));
-    memcpy(p + sizeof(h), c->h_st, sizeof(DevState));
-    LM_CK(cudaMemcpy(p + sizeof(h) + sizeof(DevState), c->gs[c->h_st->cg],
-                     3 * (size_t)c->g.V * sizeof(float),
+    char* q = (char*)buf;
+    memcpy(q, &h, sizeof(h));
+    memcpy(q + sizeof(h), k->h_st, sizeof(DevState));
+    LM_CK(cudaMemcpy(q + sizeof(h) + sizeof(DevState),
+                     k->h_st[0].cg ? d.g1 : d.g0,
+                     3 * (size_t)d.g.V * sizeof(float),
                      cudaMemcpyDeviceToHost));
     *nbytes = need;
     return LM_OK;
@@ -674,80 +690,40 @@ extern "C" int lm_state_save(lm_ctx* c, void* buf, size_t* nbytes) {
 
 extern "C" int lm_state_load(lm_ctx* c, const void* buf, size_t nbytes) {
     if (!c || !buf) return fail(LM_EINVAL, "NULL argument");
-    if (!c->have_reset) return fail(LM_ESTATE, "lm_reset was not called");
+    Core* k = c->core.get();
+    if (!k->have_reset) return fail(LM_ESTATE, "lm_reset was not called");
+    const PairDesc& d = k->hpd[0];
     size_t need = sizeof(CkptHeader) + sizeof(DevState) +
-                  3 * (size_t)c->g.V * sizeof(float);
+                  3 * (size_t)d.g.V * sizeof(float);
     if (nbytes < need) return fail(LM_EINVAL, "checkpoint too small");
     CkptHeader h;
     memcpy(&h, buf, sizeof(h));
     if (memcmp(h.magic, "LMREGCK1", 8) != 0 || h.version != 1)
         return fail(LM_EINVAL, "not an lmreg checkpoint");
-    if (h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz)
+    if (h.nx != d.g.nx || h.ny != d.g.ny || h.nz != d.g.nz)
         return fail(LM_EINVAL, "checkpoint shape differs from the context");
     DevState s;
     memcpy(&s, (const char*)buf + sizeof(h), sizeof(DevState));
     s.cu = 0;       // the field is the caller's (slot 0)
     s.cg = 0;       // the gradient is restored into slot 0
     s.done = 0;
-    *c->h_st = s;
-    LM_CK(cudaMemcpyAsync(c->st, c->h_st, sizeof(DevState),
-                          cudaMemcpyHostToDevice, c->stream));
-    LM_CK(cudaMemcpyAsync(c->gs[0],
-                          (const char*)buf + sizeof(h) + sizeof(DevState),
-                          3 * (size_t)c->g.V * sizeof(float),
-                          cudaMemcpyHostToDevice, c->stream));
-    LM_CK(cudaStreamSynchronize(c->stream));
+    k->h_st[0] = s;
+    LM_CK(cudaMemcpyAsync(d.st, k->h_st, sizeof(DevState),
+                          cudaMemcpyHostToDevice, k->stream));
+    LM_CK(cudaMemcpyAsync(d.g0, (const char*)buf + sizeof(h) + sizeof(DevState),
+                          3 * (size_t)d.g.V * sizeof(float),
+                          cudaMemcpyHostToDevice, k->stream));
+    LM_CK(cudaStreamSynchronize(k->stream));
     return LM_OK;
 }
 
 // ---------------------------------------------------------------------
 // Coarse-to-fine registration.
 // ---------------------------------------------------------------------
-extern "C" int lm_time_passes(lm_ctx* c, float* u, int n, double* ms_eval,
-                              double* ms_step) {
-    int rc = check_bound(c, u);
-    if (rc) return rc;
-    if (n < 1 || !ms_eval || !ms_step)
-        return fail(LM_EINVAL, "n must be >= 1 and outputs non-NULL");
-    cudaEvent_t e0, e1, e2;
-    LM_CK(cudaEventCreate(&e0));
-    LM_CK(cudaEventCreate(&e1));
-    LM_CK(cudaEventCreate(&e2));
-    StepLaunch sl;
-    sl.g = c->g;
-    sl.u0 = u;
-    sl.u1 = c->u1;
-    sl.g0 = c->gs[0];
-    sl.g1 = c->gs[1];
-    sl.st = c->st;
-    sl.step = c->p.step;
-    sl.attempt = 0;
-    sl.wtaps = c->wtaps;
-    sl.tmpA = c->tmpA;
-    sl.tmpB = c->tmpB;
-    LM_CK(cudaEventRecord(e0, c->stream));
-    for (int i = 0; i < n; ++i) step_compose(sl, c->stream);
-    LM_CK(cudaEventRecord(e1, c->stream));
-    for (int i = 0; i < n; ++i)
-        run_eval(c, EVAL_TRIAL, nullptr, nullptr, u, 0, c->stream);
-    LM_CK(cudaEventRecord(e2, c->stream));
-    LM_CK(cudaEventSynchronize(e2));
-    float a = 0.f, b = 0.f;
-    cudaEventElapsedTime(&a, e0, e1);
-    cudaEventElapsedTime(&b, e1, e2);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
-    *ms_step = a / n;
-    *ms_eval = b / n;
-    LM_CK(cudaGetLastError());
-    return LM_OK;
-}
+namespace {
 
-extern "C" int lm_register(lm_ctx* c, const lm_schedule* s, float* u,
-                           lm_report* rep) {
-    if (!c || !s) return fail(LM_EINVAL, "NULL argument");
-    if (!is_device_ptr(u)) return fail(LM_EINVAL, "u is not a device pointer");
+int check_schedule(const lm_schedule* s) {
+    if (!s) return fail(LM_EINVAL, "schedule is NULL");
     if (s->nlevels < 1 || s->nlevels > LM_MAX_LEVELS)
         return fail(LM_EINVAL, "nlevels must be in [1, %d]", LM_MAX_LEVELS);
     for (int l = 0; l < s->nlevels; ++l) {
@@ -756,21 +732,56 @@ extern "C" int lm_register(lm_ctx* c, const lm_schedule* s, float* u,
             return fail(LM_EINVAL, "factor[%d] must be 1, 2 or 4", l);
         if (s->iters[l] < 0) return fail(LM_EINVAL, "iters[%d] < 0", l);
     }
+    return LM_OK;
+}
+
+// Per-level accounting from a Core's state and log after a level's run.
+int level_report(Core* k, int pair, lm_report* r, int l) {
+    const DevState& hs = k->h_st[pair];
+    const PairDesc& d = k->hpd[pair];
+    r->level_dims[l][0] = d.g.nz;
+    r->level_dims[l][1] = d.g.ny;
+    r->level_dims[l][2] = d.g.nx;
+    r->level_iters[l] = hs.iter;
+    r->level_evals[l] = hs.evals;
+    r->level_accepted[l] = 0;
+    int nlog = hs.log_pos < LOG_CAP ? hs.log_pos : LOG_CAP;
+    if (nlog > 0) {
+        LM_CK(cudaMemcpy(k->h_log, d.log, nlog * sizeof(LogEntry),
+                         cudaMemcpyDeviceToHost));
+        for (int i = 0; i < nlog; ++i)
+            r->level_accepted[l] += k->h_log[i].accepted;
+    }
+    r->level_loss[l] = hs.L;
+    r->voxel_evals += (long long)d.g.V * hs.evals;
+    return LM_OK;
+}
+
+}  // namespace
+
+extern "C" int lm_register(lm_ctx* c, const lm_schedule* s, float* u,
+                           lm_report* rep) {
+    if (!c) return fail(LM_EINVAL, "NULL argument");
+    int rc = check_schedule(s);
+    if (rc) return rc;
+    if (!is_device_ptr(u)) return fail(LM_EINVAL, "u is not a device pointer");
+    Core* top = c->core.get();
+    const PairDesc td = top->hpd[0];
+    const Geom G = td.g;
     auto t0 = std::chrono::steady_clock::now();
-    int rc;
-    const size_t V = (size_t)c->g.V;
     if (!c->u_tmp) {
-        if ((rc = dalloc(c, &c->u_tmp, 3 * V * sizeof(float))) != LM_OK)
+        if ((rc = top->dalloc(&c->u_tmp, 3 * (size_t)G.V * sizeof(float))) !=
+            LM_OK)
             return rc;
     }
     lm_report r;
     memset(&r, 0, sizeof(r));
     r.nlevels = s->nlevels;
-    // the field travels between levels in `cur` (dims cx, cy, cz, factor cf)
     float* cur = u;
-    int cx = c->g.nx, cy = c->g.ny, cz = c->g.nz, cf = 1;
+    Geom cg = G;
+    int cf = 1;
     for (int l = 0; l < s->nlevels; ++l) {
-        int f = s->factor[l];
+        const int f = s->factor[l];
         lm_ctx* lc = c;
         float* ul = u;
         if (f != 1) {
@@ -781,84 +792,246 @@ extern "C" int lm_register(lm_ctx* c, const lm_schedule* s, float* u,
                 lm_ctx::Level nl;
                 nl.factor = f;
                 int lx, ly, lz;
-                level_dims(c->g.nx, c->g.ny, c->g.nz, f, &lx, &ly, &lz);
+                level_dims(G.nx, G.ny, G.nz, f, &lx, &ly, &lz);
                 size_t Vl = (size_t)lx * ly * lz;
-                size_t es = c->dtype == LM_BF16 ? 2 : 4;
-                if ((rc = dalloc(c, &nl.Fl, Vl * es)) ||
-                    (rc = dalloc(c, &nl.Ml, Vl * es)) ||
-                    (rc = dalloc(c, &nl.ul, 3 * Vl * sizeof(float))))
+                size_t es = top->dtype == LM_BF16 ? 2 : 4;
+                if ((rc = top->dalloc(&nl.Fl, Vl * es)) ||
+                    (rc = top->dalloc(&nl.Ml, Vl * es)) ||
+                    (rc = top->dalloc(&nl.ul, 3 * Vl * sizeof(float))))
                     return rc;
-                // level images must exist before the level context reads
-                // their mean
-                if ((rc = downsample_image(c->F, c->dtype, c->g, f, nl.Fl,
-                                           c->u_tmp, c->stream)) ||
-                    (rc = downsample_image(c->M, c->dtype, c->g, f, nl.Ml,
-                                           c->u_tmp, c->stream)))
-                    return fail(LM_ECUDA, "downsample failed");
-                lm_volume vf = {lz, ly, lx, c->dtype, nl.Fl};
-                lm_volume vm = {lz, ly, lx, c->dtype, nl.Ml};
-                if ((rc = lm_init(&nl.ctx, &vf, &vm, &c->p, c->stream)))
+                lm_volume vf = {lz, ly, lx, top->dtype, nl.Fl};
+                lm_volume vm = {lz, ly, lx, top->dtype, nl.Ml};
+                if ((rc = lm_init(&nl.ctx, &vf, &vm, &top->p, top->stream)))
                     return rc;
                 c->levels.push_back(nl);
                 lv = &c->levels.back();
             }
-            else {
-                // the caller may have changed F or M since the last call
-                if ((rc = downsample_image(c->F, c->dtype, c->g, f, lv->Fl,
-                                           c->u_tmp, c->stream)) ||
-                    (rc = downsample_image(c->M, c->dtype, c->g, f, lv->Ml,
-                                           c->u_tmp, c->stream)))
-                    return fail(LM_ECUDA, "downsample failed");
-            }
+            // the caller may change F or M between calls: resample each time
+            if (downsample_image(td.F, top->dtype, G, f, lv->Fl, c->u_tmp,
+                                 top->stream) ||
+                downsample_image(td.M, top->dtype, G, f, lv->Ml, c->u_tmp,
+                                 top->stream))
+                return fail(LM_ECUDA, "downsample failed");
             lc = lv->ctx;
             ul = lv->ul;
         }
-        // carry the field from (cur, cf) into this level's buffer
+        const Geom lg = lc->core->hpd[0].g;
         if (ul != cur || cf != f) {
-            Geom ga{cx, cy, cz, (long long)cx * cy * cz};
             float* src = cur;
             if (ul == cur) {   // resample in place through the staging copy
-                LM_CK(cudaMemcpyAsync(c->u_tmp, cur, 3 * ga.V * sizeof(float),
-                                      cudaMemcpyDeviceToDevice, c->stream));
+                LM_CK(cudaMemcpyAsync(c->u_tmp, cur, 3 * cg.V * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, top->stream));
                 src = c->u_tmp;
             }
-            if ((rc = resample_field(src, ga, cf, ul, lc->g, f, c->stream)))
+            if (resample_field(src, cg, cf, ul, lg, f, top->stream))
                 return fail(LM_ECUDA, "field resampling failed");
         }
-        if ((rc = lm_reset(lc, ul)) != LM_OK) return rc;
-        lm_step_info info;
-        if ((rc = lm_iterate(lc, ul, s->iters[l], &info)) != LM_OK) return rc;
-        DevState hs = *lc->h_st;
-        r.level_dims[l][0] = lc->g.nz;
-        r.level_dims[l][1] = lc->g.ny;
-        r.level_dims[l][2] = lc->g.nx;
-        r.level_iters[l] = hs.iter;
-        r.level_evals[l] = hs.evals;
-        r.level_accepted[l] = 0;
-        int nlog = hs.log_pos < LOG_CAP ? hs.log_pos : LOG_CAP;
-        if (nlog > 0) {
-            LM_CK(cudaMemcpy(lc->h_log, lc->log, nlog * sizeof(LogEntry),
-                             cudaMemcpyDeviceToHost));
-            for (int i = 0; i < nlog; ++i)
-                r.level_accepted[l] += lc->h_log[i].accepted;
-        }
-        r.level_loss[l] = hs.L;
-        r.voxel_evals += (long long)lc->g.V * hs.evals;
+        Core* k = lc->core.get();
+        if ((rc = core_reset(k, &ul)) != LM_OK) return rc;
+        if ((rc = k->iterate(s->iters[l])) != LM_OK) return rc;
+        if ((rc = k->read_states()) != LM_OK) return rc;
+        if ((rc = level_report(k, 0, &r, l)) != LM_OK) return rc;
         cur = ul;
-        cx = lc->g.nx;
-        cy = lc->g.ny;
-        cz = lc->g.nz;
+        cg = lg;
         cf = f;
     }
     if (cur != u) {
-        Geom ga{cx, cy, cz, (long long)cx * cy * cz};
-        if ((rc = resample_field(cur, ga, cf, u, c->g, 1, c->stream)))
+        if (resample_field(cur, cg, cf, u, G, 1, top->stream))
             return fail(LM_ECUDA, "field resampling failed");
     }
-    LM_CK(cudaStreamSynchronize(c->stream));
+    LM_CK(cudaStreamSynchronize(top->stream));
     r.final_loss = r.level_loss[s->nlevels - 1];
     auto t1 = std::chrono::steady_clock::now();
     r.wall_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     if (rep) *rep = r;
     return LM_OK;
+}
+
+// ---------------------------------------------------------------------
+// Batches of pairs.
+// ---------------------------------------------------------------------
+extern "C" int lm_batch_init(lm_batch** out, int npairs,
+                             const lm_volume* fixed, const lm_volume* moving,
+                             const lm_params* p, void* cuda_stream) {
+    g_err[0] = 0;
+    if (!out) return fail(LM_EINVAL, "batch out-pointer is NULL");
+    *out = nullptr;
+    auto b = new lm_batch();
+    int rc = core_create(b->core, npairs, fixed, moving, p, cuda_stream);
+    if (rc != LM_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return LM_OK;
+}
+
+extern "C" void lm_batch_destroy(lm_batch* b) {
+    if (!b) return;
+    delete b;
+}
+
+extern "C" int lm_batch_eval(lm_batch* b, const float* const* u,
+                             float* const* g_out, double* loss,
+                             float* gmax) {
+    if (!b || !u) return fail(LM_EINVAL, "NULL argument");
+    return core_eval(b->core.get(), u, g_out, loss, gmax);
+}
+
+extern "C" int lm_batch_reset(lm_batch* b, float* const* u) {
+    if (!b || !u) return fail(LM_EINVAL, "NULL argument");
+    return core_reset(b->core.get(), u);
+}
+
+extern "C" int lm_batch_iterate(lm_batch* b, float* const* u, int n,
+                                lm_step_info* infos) {
+    if (!b || !u) return fail(LM_EINVAL, "NULL argument");
+    Core* k = b->core.get();
+    int rc = core_check_bound(k, u);
+    if (rc) return rc;
+    if (n < 0) return fail(LM_EINVAL, "n must be >= 0");
+    if ((rc = k->iterate(n)) != LM_OK) return rc;
+    if (infos) {
+        if ((rc = k->read_states()) != LM_OK) return rc;
+        for (int i = 0; i < k->npairs; ++i) fill_info(k->h_st[i], &infos[i]);
+    }
+    return LM_OK;
+}
+
+extern "C" int lm_batch_register(lm_batch* b, const lm_schedule* s,
+                                 float* const* u, lm_report* reps) {
+    if (!b || !u) return fail(LM_EINVAL, "NULL argument");
+    int rc = check_schedule(s);
+    if (rc) return rc;
+    Core* top = b->core.get();
+    const int n = top->npairs;
+    for (int i = 0; i < n; ++i)
+        if (!is_device_ptr(u[i]))
+            return fail(LM_EINVAL, "u of pair %d is not a device pointer", i);
+    auto t0 = std::chrono::steady_clock::now();
+    if (b->u_tmp.empty()) {
+        b->u_tmp.resize(n);
+        for (int i = 0; i < n; ++i)
+            if ((rc = top->dalloc(&b->u_tmp[i], 3 * (size_t)top->hpd[i].g.V *
+                                                    sizeof(float))) != LM_OK)
+                return rc;
+    }
+    std::vector<lm_report> r(n);
+    for (auto& x : r) {
+        memset(&x, 0, sizeof(x));
+        x.nlevels = s->nlevels;
+    }
+    std::vector<float*> cur(u, u + n);
+    std::vector<Geom> cg(n);
+    for (int i = 0; i < n; ++i) cg[i] = top->hpd[i].g;
+    int cf = 1;
+    for (int l = 0; l < s->nlevels; ++l) {
+        const int f = s->factor[l];
+        lm_batch* lb = b;
+        std::vector<float*> ul(u, u + n);
+        if (f != 1) {
+            lm_batch::Level* lv = nullptr;
+            for (auto& x : b->levels)
+                if (x.factor == f) lv = &x;
+            if (!lv) {
+                lm_batch::Level nl;
+                nl.factor = f;
+                std::vector<lm_volume> vf(n), vm(n);
+                size_t es = top->dtype == LM_BF16 ? 2 : 4;
+                nl.Fl.resize(n);
+                nl.Ml.resize(n);
+                nl.ul.resize(n);
+                for (int i = 0; i < n; ++i) {
+                    const Geom& G = top->hpd[i].g;
+                    int lx, ly, lz;
+                    level_dims(G.nx, G.ny, G.nz, f, &lx, &ly, &lz);
+                    size_t Vl = (size_t)lx * ly * lz;
+                    if ((rc = top->dalloc(&nl.Fl[i], Vl * es)) ||
+                        (rc = top->dalloc(&nl.Ml[i], Vl * es)) ||
+                        (rc = top->dalloc(&nl.ul[i], 3 * Vl * sizeof(float))))
+                        return rc;
+                    vf[i] = {lz, ly, lx, top->dtype, nl.Fl[i]};
+                    vm[i] = {lz, ly, lx, top->dtype, nl.Ml[i]};
+                }
+                // the level images must exist before the batch checks them
+                for (int i = 0; i < n; ++i) {
+                    const PairDesc& d = top->hpd[i];
+                    if (downsample_image(d.F, top->dtype, d.g, f, nl.Fl[i],
+                                         b->u_tmp[i], top->stream) ||
+                        downsample_image(d.M, top->dtype, d.g, f, nl.Ml[i],
+                                         b->u_tmp[i], top->stream))
+                        return fail(LM_ECUDA, "downsample failed");
+                }
+                if ((rc = lm_batch_init(&nl.b, n, vf.data(), vm.data(),
+                                        &top->p, top->stream)))
+                    return rc;
+                b->levels.push_back(nl);
+                lv = &b->levels.back();
+            } else {
+                for (int i = 0; i < n; ++i) {
+                    const PairDesc& d = top->hpd[i];
+                    if (downsample_image(d.F, top->dtype, d.g, f, lv->Fl[i],
+                                         b->u_tmp[i], top->stream) ||
+                        downsample_image(d.M, top->dtype, d.g, f, lv->Ml[i],
+                                         b->u_tmp[i], top->stream))
+                        return fail(LM_ECUDA, "downsample failed");
+                }
+            }
+            lb = lv->b;
+            ul = lv->ul;
+        }
+        Core* k = lb->core.get();
+        for (int i = 0; i < n; ++i) {
+            const Geom lg = k->hpd[i].g;
+            if (ul[i] != cur[i] || cf != f) {
+                float* src = cur[i];
+                if (ul[i] == cur[i]) {
+                    LM_CK(cudaMemcpyAsync(b->u_tmp[i], cur[i],
+                                          3 * cg[i].V * sizeof(float),
+                                          cudaMemcpyDeviceToDevice,
+                                          top->stream));
+                    src = b->u_tmp[i];
+                }
+                if (resample_field(src, cg[i], cf, ul[i], lg, f, top->stream))
+                    return fail(LM_ECUDA, "field resampling failed");
+            }
+        }
+        if ((rc = core_reset(k, ul.data())) != LM_OK) return rc;
+        if ((rc = k->iterate(s->iters[l])) != LM_OK) return rc;
+        if ((rc = k->read_states()) != LM_OK) return rc;
+        for (int i = 0; i < n; ++i)
+            if ((rc = level_report(k, i, &r[i], l)) != LM_OK) return rc;
+        for (int i = 0; i < n; ++i) {
+            cur[i] = ul[i];
+            cg[i] = k->hpd[i].g;
+        }
+        cf = f;
+    }
+    for (int i = 0; i < n; ++i)
+        if (cur[i] != u[i]) {
+            if (resample_field(cur[i], cg[i], cf, u[i], top->hpd[i].g, 1,
+                               top->stream))
+                return fail(LM_ECUDA, "field resampling failed");
+        }
+    LM_CK(cudaStreamSynchronize(top->stream));
+    auto t1 = std::chrono::steady_clock::now();
+    double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    for (int i = 0; i < n; ++i) {
+        r[i].final_loss = r[i].level_loss[s->nlevels - 1];
+        r[i].wall_ms = ms;
+        if (reps) reps[i] = r[i];
+    }
+    return LM_OK;
+}
+
+extern "C" int lm_register_batch(int npairs, const lm_volume* fixed,
+                                 const lm_volume* moving, float* const* u,
+                                 const lm_params* p, const lm_schedule* s,
+                                 void* cuda_stream, lm_report* reps) {
+    lm_batch* b = nullptr;
+    int rc = lm_batch_init(&b, npairs, fixed, moving, p, cuda_stream);
+    if (rc != LM_OK) return rc;
+    rc = lm_batch_register(b, s, u, reps);
+    lm_batch_destroy(b);
+    return rc;
 }

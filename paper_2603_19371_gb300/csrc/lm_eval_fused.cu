@@ -23,8 +23,9 @@
 // HBM traffic per voxel: E1 reads F, M, u (20 B) and writes dL/dJ (4 B);
 // E2 reads dL/dJ, M, u (20 B) and writes g (12 B).  Halo re-reads hit L2.
 #include <algorithm>
+#include <vector>
 
-#include "lm_fused.cuh"
+#include "lm_kernels.cuh"
 
 namespace lmk {
 namespace {
@@ -137,9 +138,8 @@ struct E1Cfg {
 
 template <int W, typename T>
 __global__ void __launch_bounds__(NT, 1)
-    k_e1(const T* __restrict__ F, const T* __restrict__ M, EvalIO io, Geom g,
-         LnccConsts c, FusedPlan pl, const QScale* __restrict__ qs,
-         float* __restrict__ dldj, double* __restrict__ loss_part) {
+    k_e1(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
+         LnccConsts c, double* __restrict__ loss_part) {
     using C = E1Cfg<W>;
     constexpr int K = C::K, SX = C::SX, SY = C::SY, TX = C::TX, TY = C::TY;
     constexpr int GX = C::GX, GY = C::GY, GXP = C::GXP;
@@ -162,9 +162,16 @@ __global__ void __launch_bounds__(NT, 1)
     float* Ax = Ab + 3 * SY * SX;
     __shared__ double red[NT / 32];
 
-    if (eval_skip(io)) return;
+    const PairDesc& P = pd[pair_of_block<1>(pd, npairs, blockIdx.x)];
+    if (trial_skip(P, mode, attempt)) return;
+    const Geom g = P.g;
+    const T* __restrict__ F = (const T*)P.F;
+    const T* __restrict__ M = (const T*)P.M;
+    float* __restrict__ dldj = P.dldj;
+    const QScale* __restrict__ qs = P.qs;
+    const float inv_V = (float)(1.0 / (double)g.V);
     const int tid = threadIdx.x;
-    const float* __restrict__ u = eval_u(io);
+    const float* __restrict__ u = eval_u(P, mode);
     const float* __restrict__ u1 = u + g.V;
     const float* __restrict__ u2 = u + 2 * g.V;
     const int sxy = g.nx * g.ny;
@@ -202,8 +209,9 @@ __global__ void __launch_bounds__(NT, 1)
 
     double lacc = 0.0;
     bool bad = false;
-    const long long total = (long long)pl.e1_cx * pl.e1_cy * g.nz;
-    const Share sh_ = share_of(blockIdx.x, gridDim.x, total);
+    const int e1_cx = P.e1_cx;
+    const long long total = (long long)P.e1_cx * P.e1_cy * g.nz;
+    const Share sh_ = share_of(blockIdx.x - P.e1_cta0, P.e1_ncta, total);
     long long w0 = sh_.lo;
     while (w0 < sh_.hi) {
         const long long col = w0 / g.nz;
@@ -211,8 +219,8 @@ __global__ void __launch_bounds__(NT, 1)
         const long long zl = z0 + (sh_.hi - w0);
         const int z1 = zl < g.nz ? (int)zl : g.nz;
         w0 += z1 - z0;
-        const int x0 = (int)(col % pl.e1_cx) * TX;
-        const int y0 = (int)(col / pl.e1_cx) * TY;
+        const int x0 = (int)(col % e1_cx) * TX;
+        const int y0 = (int)(col / e1_cx) * TY;
         // in-plane offsets of the gather slots (-1: outside the volume)
         int g_off[NGS];
 #pragma unroll
@@ -432,7 +440,7 @@ __global__ void __launch_bounds__(NT, 1)
                             }
                             const int jd = (j + 1) % K;
                             dldj[r * sxy + o_off] =
-                                -c.inv_V * ((dF[jd] * b3[0] +
+                                -inv_V * ((dF[jd] * b3[0] +
                                              2.f * dJ[jd] * b3[1] + b3[2]) *
                                             c.inv_k3);
                         }
@@ -468,8 +476,8 @@ struct E2Cfg {
 
 template <int R, typename T>
 __global__ void __launch_bounds__(NT, 2)
-    k_e2(const T* __restrict__ M, EvalIO io, Geom g, Taps tp, FusedPlan pl,
-         const float* __restrict__ dldj, float* __restrict__ g2_part) {
+    k_e2(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
+         Taps tp, float* __restrict__ g2_part) {
     using C = E2Cfg<R>;
     constexpr int KG = C::KG, RX = C::RX, RY = C::RY, RXP = C::RXP;
     constexpr int TX = C::TX, TY = C::TY;
@@ -480,12 +488,16 @@ __global__ void __launch_bounds__(NT, 2)
     float* Gx = Gr + 3 * RY * RXP;       // [3][RY][TX]
     __shared__ float red[NT / 32];
 
-    if (eval_skip(io)) return;
+    const PairDesc& P = pd[pair_of_block<2>(pd, npairs, blockIdx.x)];
+    if (trial_skip(P, mode, attempt)) return;
+    const Geom g = P.g;
+    const T* __restrict__ M = (const T*)P.M;
+    const float* __restrict__ dldj = P.dldj;
     const int tid = threadIdx.x;
-    const float* __restrict__ u = eval_u(io);
+    const float* __restrict__ u = eval_u(P, mode);
     const float* __restrict__ u1 = u + g.V;
     const float* __restrict__ u2 = u + 2 * g.V;
-    float* __restrict__ gout = eval_g(io);
+    float* __restrict__ gout = eval_g(P, mode);
     const int sxy = g.nx * g.ny;
     const int ox = tid & (TX - 1), oy = tid / TX;
     // taps stay in the kernel-parameter constant bank (no registers)
@@ -511,8 +523,9 @@ __global__ void __launch_bounds__(NT, 2)
     }
     float m2 = 0.f;
 
-    const long long total = (long long)pl.e2_cx * pl.e2_cy * g.nz;
-    const Share sh_ = share_of(blockIdx.x, gridDim.x, total);
+    const int e2_cx = P.e2_cx;
+    const long long total = (long long)P.e2_cx * P.e2_cy * g.nz;
+    const Share sh_ = share_of(blockIdx.x - P.e2_cta0, P.e2_ncta, total);
     long long w0 = sh_.lo;
     while (w0 < sh_.hi) {
         const long long col = w0 / g.nz;
@@ -520,8 +533,8 @@ __global__ void __launch_bounds__(NT, 2)
         const long long zl = z0 + (sh_.hi - w0);
         const int z1 = zl < g.nz ? (int)zl : g.nz;
         w0 += z1 - z0;
-        const int x0 = (int)(col % pl.e2_cx) * TX;
-        const int y0 = (int)(col / pl.e2_cx) * TY;
+        const int x0 = (int)(col % e2_cx) * TX;
+        const int y0 = (int)(col / e2_cx) * TY;
         int r_off[NRS];
 #pragma unroll
         for (int k = 0; k < NRS; ++k) {
@@ -632,14 +645,18 @@ __global__ void __launch_bounds__(NT, 2)
 }
 
 // ----------------------------------------------------------------------
-// Quantisation scale: shift s = (lo + hi) / 2 and Q = 2^qb / h with
+// Quantisation scale per pair: shift s = (lo + hi) / 2 and Q = 2^qb / h with
 // h = (hi - lo) / 2, lo = min(0, F, M), hi = max(0, F, M) (0 is the padding
 // value and J is a convex combination of M values and 0).
 // ----------------------------------------------------------------------
 template <typename T>
-__global__ void k_minmax(const T* __restrict__ F, const T* __restrict__ M,
-                         long long V, float2* __restrict__ part) {
+__global__ void k_minmax(const PairDesc* __restrict__ pd,
+                         float2* __restrict__ part) {
     __shared__ float smin[NT / 32], smax[NT / 32];
+    const PairDesc& P = pd[blockIdx.y];
+    const T* __restrict__ F = (const T*)P.F;
+    const T* __restrict__ M = (const T*)P.M;
+    const long long V = P.g.V;
     float lo = 0.f, hi = 0.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V;
          i += (long long)gridDim.x * blockDim.x) {
@@ -661,65 +678,66 @@ __global__ void k_minmax(const T* __restrict__ F, const T* __restrict__ M,
             lo = fminf(lo, smin[w]);
             hi = fmaxf(hi, smax[w]);
         }
-        part[blockIdx.x] = make_float2(smin[0] < lo ? smin[0] : lo,
-                                       smax[0] > hi ? smax[0] : hi);
+        part[blockIdx.y * gridDim.x + blockIdx.x] = make_float2(lo, hi);
     }
 }
 
-__global__ void k_qscale(const float2* __restrict__ part, int n, int qb,
-                         QScale* __restrict__ qs) {
+__global__ void k_qscale(const PairDesc* __restrict__ pd,
+                         const float2* __restrict__ part, int n, int qb) {
     if (threadIdx.x != 0) return;
+    const int p = blockIdx.x;
     float lo = 0.f, hi = 0.f;
     for (int i = 0; i < n; ++i) {
-        lo = fminf(lo, part[i].x);
-        hi = fmaxf(hi, part[i].y);
+        lo = fminf(lo, part[p * n + i].x);
+        hi = fmaxf(hi, part[p * n + i].y);
     }
     double h = 0.5 * ((double)hi - (double)lo);
     if (!(h > 1e-30)) h = 1.0;       // constant images: any scale is exact
-    double s = 0.5 * ((double)hi + (double)lo);
+    double sft = 0.5 * ((double)hi + (double)lo);
     double lim = ldexp(1.0, qb);
-    qs->shift = (float)s;
+    QScale* qs = pd[p].qs;
+    qs->shift = (float)sft;
     // a little headroom so that rounding never leaves [-lim, lim]
-    qs->Q = (float)(lim / (h * (1.0 + 1e-6)));
-    qs->invQ = (float)(1.0 / (double)qs->Q);
+    float Q = (float)(lim / (h * (1.0 + 1e-6)));
+    qs->Q = Q;
+    qs->invQ = (float)(1.0 / (double)Q);
     qs->qlim = (int)lim;
 }
 
 template <int W, typename T>
-int launch_e1(const FusedLaunch& a, cudaStream_t s) {
-    k_e1<W, T><<<a.plan.e1_ctas, NT, E1Cfg<W>::bytes, s>>>(
-        (const T*)a.F, (const T*)a.M, a.io, a.g, a.c, a.plan, a.qs, a.dldj,
-        a.part.loss);
+int launch_e1(const Batch& b, int mode, int attempt, cudaStream_t s) {
+    k_e1<W, T><<<b.plan.e1_ctas, NT, E1Cfg<W>::bytes, s>>>(
+        b.pd, b.npairs, mode, attempt, b.c, b.part.loss);
     return 1;
 }
 
 template <int R, typename T>
-int launch_e2(const FusedLaunch& a, cudaStream_t s) {
-    k_e2<R, T><<<a.plan.e2_ctas, NT, E2Cfg<R>::bytes, s>>>(
-        (const T*)a.M, a.io, a.g, a.c.gtaps, a.plan, a.dldj, a.part.g2max);
+int launch_e2(const Batch& b, int mode, int attempt, cudaStream_t s) {
+    k_e2<R, T><<<b.plan.e2_ctas, NT, E2Cfg<R>::bytes, s>>>(
+        b.pd, b.npairs, mode, attempt, b.c.gtaps, b.part.g2max);
     return 1;
 }
 
 template <typename T>
-int launch_e1_w(const FusedLaunch& a, cudaStream_t s) {
-    switch ((a.c.win - 1) / 2) {
-        case 1: return launch_e1<1, T>(a, s);
-        case 2: return launch_e1<2, T>(a, s);
-        case 3: return launch_e1<3, T>(a, s);
-        default: return launch_e1<4, T>(a, s);
+int launch_e1_w(const Batch& b, int mode, int attempt, cudaStream_t s) {
+    switch ((b.c.win - 1) / 2) {
+        case 1: return launch_e1<1, T>(b, mode, attempt, s);
+        case 2: return launch_e1<2, T>(b, mode, attempt, s);
+        case 3: return launch_e1<3, T>(b, mode, attempt, s);
+        default: return launch_e1<4, T>(b, mode, attempt, s);
     }
 }
 
 template <typename T>
-int launch_e2_r(const FusedLaunch& a, cudaStream_t s) {
-    switch (a.c.gtaps.R) {
-        case 0: return launch_e2<0, T>(a, s);
-        case 1: return launch_e2<1, T>(a, s);
-        case 2: return launch_e2<2, T>(a, s);
-        case 3: return launch_e2<3, T>(a, s);
-        case 4: return launch_e2<4, T>(a, s);
-        case 5: return launch_e2<5, T>(a, s);
-        default: return launch_e2<6, T>(a, s);
+int launch_e2_r(const Batch& b, int mode, int attempt, cudaStream_t s) {
+    switch (b.c.gtaps.R) {
+        case 0: return launch_e2<0, T>(b, mode, attempt, s);
+        case 1: return launch_e2<1, T>(b, mode, attempt, s);
+        case 2: return launch_e2<2, T>(b, mode, attempt, s);
+        case 3: return launch_e2<3, T>(b, mode, attempt, s);
+        case 4: return launch_e2<4, T>(b, mode, attempt, s);
+        case 5: return launch_e2<5, T>(b, mode, attempt, s);
+        default: return launch_e2<6, T>(b, mode, attempt, s);
     }
 }
 
@@ -753,7 +771,7 @@ cudaError_t attrs_all() {
     return e;
 }
 
-int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
 }  // namespace
 
@@ -768,23 +786,74 @@ int quant_bits(int win) {
     }
 }
 
-FusedPlan fused_plan(const Geom& g, int win, int num_sms) {
-    FusedPlan p;
+// CTA ranges per pair: a single pair takes the whole grid (one CTA per SM
+// for E1, two for E2); a batch shares a grid of several waves among its
+// pairs in proportion to their work, at least one CTA each, so that every
+// CTA works on one pair.
+static void split_ctas(const long long* work, int npairs, long long target,
+                       int* c0, int* n) {
+    long long tot = 0;
+    for (int p = 0; p < npairs; ++p) tot += work[p];
+    int acc = 0;
+    for (int p = 0; p < npairs; ++p) {
+        long long k = tot > 0 ? (target * work[p] + tot / 2) / tot : 1;
+        k = std::max<long long>(1, std::min<long long>(k, std::max<long long>(1, work[p] / 8)));
+        c0[p] = acc;
+        n[p] = (int)k;
+        acc += (int)k;
+    }
+}
+
+BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms) {
+    BatchPlan bp{};
     const int W = (win - 1) / 2;
     const int tx1 = PLANE_X - 2 * W, ty1 = PLANE_Y - 2 * W;
-    p.e1_cx = ceil_div(g.nx, tx1);
-    p.e1_cy = ceil_div(g.ny, ty1);
-    long long w1 = (long long)p.e1_cx * p.e1_cy * g.nz;
-    // one CTA per SM (shared memory bound); fewer when there is less work
-    // than ~8 slices per CTA
-    p.e1_ctas = (int)std::max<long long>(1, std::min<long long>(num_sms, w1 / 8));
-    p.e2_cx = ceil_div(g.nx, PLANE_X);
-    p.e2_cy = ceil_div(g.ny, PLANE_Y);
-    long long w2 = (long long)p.e2_cx * p.e2_cy * g.nz;
-    p.e2_ctas =
-        (int)std::max<long long>(1, std::min<long long>(2LL * num_sms, w2 / 8));
-    p.minmax_ctas = num_sms;
-    return p;
+    std::vector<long long> w1(npairs), w2(npairs);
+    std::vector<int> c0(npairs), n(npairs);
+    for (int p = 0; p < npairs; ++p) {
+        Geom& g = pd[p].g;
+        pd[p].e1_cx = (int)ceil_div(g.nx, tx1);
+        pd[p].e1_cy = (int)ceil_div(g.ny, ty1);
+        w1[p] = (long long)pd[p].e1_cx * pd[p].e1_cy * g.nz;
+        pd[p].e2_cx = (int)ceil_div(g.nx, PLANE_X);
+        pd[p].e2_cy = (int)ceil_div(g.ny, PLANE_Y);
+        w2[p] = (long long)pd[p].e2_cx * pd[p].e2_cy * g.nz;
+    }
+    const long long t1 = npairs == 1 ? num_sms : 4LL * num_sms;
+    const long long t2 = npairs == 1 ? 2LL * num_sms : 8LL * num_sms;
+    split_ctas(w1.data(), npairs, t1, c0.data(), n.data());
+    for (int p = 0; p < npairs; ++p) {
+        pd[p].e1_cta0 = c0[p];
+        pd[p].e1_ncta = n[p];
+    }
+    bp.e1_ctas = c0[npairs - 1] + n[npairs - 1];
+    split_ctas(w2.data(), npairs, t2, c0.data(), n.data());
+    for (int p = 0; p < npairs; ++p) {
+        pd[p].e2_cta0 = c0[p];
+        pd[p].e2_ncta = n[p];
+    }
+    bp.e2_ctas = c0[npairs - 1] + n[npairs - 1];
+    // step kernel: 32 x 8 tiles, z chunks with ~2048 tiles per pair
+    int blk = 0, lnb = 0;
+    for (int p = 0; p < npairs; ++p) {
+        Geom& g = pd[p].g;
+        pd[p].st_tx = (int)ceil_div(g.nx, 32);
+        pd[p].st_ty = (int)ceil_div(g.ny, 8);
+        long long cols = (long long)pd[p].st_tx * pd[p].st_ty;
+        long long nzc = std::max<long long>(
+            1, std::min<long long>(g.nz, ceil_div(2048, cols)));
+        pd[p].st_zc = (int)ceil_div(g.nz, nzc);
+        pd[p].st_nzc = (int)ceil_div(g.nz, pd[p].st_zc);
+        pd[p].st_blk0 = blk;
+        blk += pd[p].st_tx * pd[p].st_ty * pd[p].st_nzc;
+        pd[p].ln_blk0 = lnb;
+        pd[p].ln_nblk = (int)ceil_div(g.V, 256);
+        lnb += pd[p].ln_nblk;
+    }
+    bp.st_blocks = blk;
+    bp.ln_blocks = lnb;
+    bp.mm_ctas = std::max(2, num_sms / npairs);
+    return bp;
 }
 
 cudaError_t fused_setup() {
@@ -793,28 +862,25 @@ cudaError_t fused_setup() {
     return e != cudaSuccess ? e : e2;
 }
 
-int fused_qscale(const void* F, const void* M, int dtype, const Geom& g,
-                 const FusedPlan& pl, int win, float2* part, QScale* qs,
-                 cudaStream_t s) {
-    if (dtype == LM_BF16)
-        k_minmax<<<pl.minmax_ctas, NT, 0, s>>>((const __nv_bfloat16*)F,
-                                               (const __nv_bfloat16*)M, g.V,
-                                               part);
+int batch_qscale(const Batch& b, cudaStream_t s) {
+    dim3 grid(b.plan.mm_ctas, b.npairs);
+    if (b.dtype == LM_BF16)
+        k_minmax<__nv_bfloat16><<<grid, NT, 0, s>>>(b.pd, b.mm_part);
     else
-        k_minmax<<<pl.minmax_ctas, NT, 0, s>>>((const float*)F,
-                                               (const float*)M, g.V, part);
-    k_qscale<<<1, 32, 0, s>>>(part, pl.minmax_ctas, quant_bits(win), qs);
+        k_minmax<float><<<grid, NT, 0, s>>>(b.pd, b.mm_part);
+    k_qscale<<<b.npairs, 32, 0, s>>>(b.pd, b.mm_part, b.plan.mm_ctas,
+                                     quant_bits(b.c.win));
     return 2;
 }
 
-int eval_fused(const FusedLaunch& a, cudaStream_t s) {
+int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s) {
     int n = 0;
-    if (a.dtype == LM_BF16) {
-        n += launch_e1_w<__nv_bfloat16>(a, s);
-        n += launch_e2_r<__nv_bfloat16>(a, s);
+    if (b.dtype == LM_BF16) {
+        n += launch_e1_w<__nv_bfloat16>(b, mode, attempt, s);
+        n += launch_e2_r<__nv_bfloat16>(b, mode, attempt, s);
     } else {
-        n += launch_e1_w<float>(a, s);
-        n += launch_e2_r<float>(a, s);
+        n += launch_e1_w<float>(b, mode, attempt, s);
+        n += launch_e2_r<float>(b, mode, attempt, s);
     }
     return n;
 }

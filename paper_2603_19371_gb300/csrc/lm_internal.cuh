@@ -52,7 +52,7 @@ struct LogEntry {
 };
 constexpr int LOG_CAP = 8192;
 
-// Result of an explicit (stateless) evaluation.
+// Result of an explicit (stateless) evaluation of one pair.
 struct EvalOut {
     double L;
     float gmax;
@@ -73,13 +73,12 @@ enum EvalMode {
     EVAL_TRIAL = 2,     // u = trial slot (1 - cu), g -> trial slot (1 - cg)
 };
 
-// Scalar LNCC / smoothing constants of one evaluation.
+// Scalar LNCC / smoothing constants of one evaluation (shared by all pairs
+// of a batch; 1/V is per pair).
 struct LnccConsts {
     int win;        // k
     float eps_nr, eps_dr;
-    float shift;    // common intensity shift applied to F and J
     float inv_k3;   // 1 / k^3
-    float inv_V;    // 1 / V
     Taps gtaps;     // gradient smoothing taps
 };
 
@@ -95,12 +94,6 @@ __device__ __forceinline__ float ld_img(const float* p, long long i) {
 }
 __device__ __forceinline__ float ld_img(const __nv_bfloat16* p, long long i) {
     return __bfloat162float(p[i]);
-}
-
-// Device-selected slot pointers.
-template <typename T>
-__device__ __forceinline__ T* slot(T* a, T* b, int which) {
-    return which ? b : a;
 }
 
 }  // namespace lmk

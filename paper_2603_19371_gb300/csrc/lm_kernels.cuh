@@ -1,108 +1,136 @@
 // Launch interfaces of the CUDA kernels (internal).
+//
+// Every kernel works on a batch of registration pairs described by a
+// device-resident table of PairDesc entries (a single-pair context is a
+// batch of one).  CTAs are assigned to pairs in contiguous ranges, so each
+// CTA works on one pair and the per-CTA partial results reduce per pair in
+// a fixed order (deterministic).
 #pragma once
 
 #include "lm_internal.cuh"
 
 namespace lmk {
 
-// Field / gradient routing of one evaluation (see EvalMode).
-struct EvalIO {
-    const float* u_in;  // EVAL_EXPLICIT field
-    float* g_out;       // EVAL_EXPLICIT gradient (may be a scratch buffer)
-    float* u0;          // field slot 0 (the caller's field)
-    float* u1;          // field slot 1 (context scratch)
-    float* g0;          // gradient slots
-    float* g1;
-    const DevState* st;
-    int mode;
-    int attempt;        // trial attempt index within an iteration
+// Fixed-point scale of the exact window moments: Xq = round((X - shift) Q),
+// |Xq| <= qlim = 2^qb.
+struct QScale {
+    float shift;
+    float Q;
+    float invQ;
+    int qlim;
 };
 
-__device__ __forceinline__ bool eval_skip(const EvalIO& io) {
-    return io.mode == EVAL_TRIAL && io.attempt > 0 && io.st->done;
-}
-__device__ __forceinline__ const float* eval_u(const EvalIO& io) {
-    if (io.mode == EVAL_EXPLICIT) return io.u_in;
-    if (io.mode == EVAL_RESET) return io.u0;
-    return io.st->cu ? io.u0 : io.u1;
-}
-__device__ __forceinline__ float* eval_g(const EvalIO& io) {
-    if (io.mode == EVAL_EXPLICIT) return io.g_out;
-    if (io.mode == EVAL_RESET) return io.g0;
-    return io.st->cg ? io.g0 : io.g1;
-}
-
-// Per-CTA partial results of an evaluation, reduced by the finalize kernel.
-struct Partials {
-    double* loss;     // sum over the CTA's voxels of (1 - cc)
-    int n_loss;
-    float* g2max;     // max over the CTA's voxels of |g|^2
-    int n_g2;
-};
-
-// Staged scratch (one full volume per intermediate).
-struct StagedScratch {
-    float* J;     // V
-    float* dJ;    // 3V
-    float* S;     // 5V box sums
-    float* T;     // 5V separable temp
-    float* abc;   // 3V
-    float* graw;  // 3V
-};
-
-struct EvalLaunch {
+struct PairDesc {
     Geom g;
     const void* F;
     const void* M;
-    int dtype;
-    EvalIO io;
-    LnccConsts c;
-    Partials part;
-    StagedScratch sc;
-};
-
-// Launch helpers return the number of kernels they enqueued.
-
-// Pass 1 (steps (a)-(c)), staged form: one kernel per stage.
-int eval_staged(const EvalLaunch& a, cudaStream_t s);
-int eval_staged_partials(const Geom& g, int* n_loss, int* n_g2);
-
-// Pass 2 (steps (c)-(d)): trial field from the current slot.
-struct StepLaunch {
-    Geom g;
-    float* u0;
-    float* u1;
-    const float* g0;
-    const float* g1;
-    const DevState* st;
-    float step;
-    int attempt;
-    // warp smoothing (sigma_warp > 0): composed field goes to tmp first
-    Taps wtaps;
-    float* tmpA;  // 3V
-    float* tmpB;  // 3V
-};
-int step_compose(const StepLaunch& a, cudaStream_t s);
-
-// Reduction of the partials and the state update.
-enum FinMode { FIN_EXPLICIT = 0, FIN_RESET = 1, FIN_DECIDE = 2 };
-struct FinLaunch {
-    Partials part;
+    float* u0;            // field slot 0 (the caller's field)
+    float* u1;            // field slot 1 (library scratch)
+    float* g0;            // gradient slots
+    float* g1;
+    const float* u_in;    // EVAL_EXPLICIT field
+    float* g_out;         // EVAL_EXPLICIT gradient
+    float* dldj;          // dL/dJ between the two evaluation kernels
+    QScale* qs;
     DevState* st;
-    EvalOut* out;       // FIN_EXPLICIT
-    LogEntry* log;      // FIN_DECIDE
-    DecideConsts d;
-    double inv_V;       // 1 / V of the evaluated volume
-    int mode;
-    int attempt;
+    LogEntry* log;        // may be NULL
+    float* wtmpA;         // warp-smoothing temporaries (sigma_warp > 0)
+    float* wtmpB;
+    // evaluation kernel 1: columns and CTA range (loss partial slots)
+    int e1_cx, e1_cy, e1_cta0, e1_ncta;
+    // evaluation kernel 2: columns and CTA range (|g|^2 partial slots)
+    int e2_cx, e2_cy, e2_cta0, e2_ncta;
+    // step kernel: tiles, z chunks, first block
+    int st_tx, st_ty, st_nzc, st_zc, st_blk0;
+    // element-wise kernels (warp smoothing, copy-back): first block, count
+    int ln_blk0, ln_nblk;
 };
-int finalize(const FinLaunch& a, cudaStream_t s);
+
+// Pointers of an evaluation, routed by mode.
+__device__ __forceinline__ const float* eval_u(const PairDesc& p, int mode) {
+    if (mode == EVAL_EXPLICIT) return p.u_in;
+    if (mode == EVAL_RESET) return p.u0;
+    return p.st->cu ? p.u0 : p.u1;
+}
+__device__ __forceinline__ float* eval_g(const PairDesc& p, int mode) {
+    if (mode == EVAL_EXPLICIT) return p.g_out;
+    if (mode == EVAL_RESET) return p.g0;
+    return p.st->cg ? p.g0 : p.g1;
+}
+// Later attempts of an iteration are no-ops once the pair's iteration is
+// decided.
+__device__ __forceinline__ bool trial_skip(const PairDesc& p, int mode,
+                                           int attempt) {
+    return mode == EVAL_TRIAL && attempt > 0 && p.st->done;
+}
+
+// Pair whose block range starts at or below b (ranges ascend in pair
+// order).  WHICH: 1 = E1 CTAs, 2 = E2 CTAs, 3 = step blocks, 4 = line blocks.
+template <int WHICH>
+__device__ __forceinline__ int pair_of_block(const PairDesc* pd, int npairs,
+                                             int b) {
+    int lo = 0, hi = npairs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int c0 = WHICH == 1   ? pd[mid].e1_cta0
+                 : WHICH == 2 ? pd[mid].e2_cta0
+                 : WHICH == 3 ? pd[mid].st_blk0
+                              : pd[mid].ln_blk0;
+        if (c0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Partials {
+    double* loss;    // one per E1 CTA
+    float* g2max;    // one per E2 CTA
+};
+
+// Totals of a batch plan.
+struct BatchPlan {
+    int e1_ctas, e2_ctas, st_blocks, ln_blocks, mm_ctas;
+};
+
+// Everything a launch needs besides the stream.
+struct Batch {
+    const PairDesc* pd;   // device table
+    int npairs;
+    int dtype;
+    BatchPlan plan;
+    LnccConsts c;
+    DecideConsts d;
+    Taps wtaps;
+    float step;
+    Partials part;
+    float2* mm_part;      // npairs * plan.mm_ctas image-range partials
+};
+
+// Fills the column / CTA / tile fields of each host PairDesc and returns the
+// totals.  num_sms sizes the grids.
+BatchPlan plan_batch(PairDesc* host_pd, int npairs, int win, int num_sms);
+
+// Opt the kernels in to their dynamic shared memory (once per process).
+cudaError_t fused_setup();
+int quant_bits(int win);
+
+// Launch helpers; each returns the number of kernels it enqueued.
+// Image range -> QScale per pair (device-side, no host round trip).
+int batch_qscale(const Batch& b, cudaStream_t s);
+// Pass 1: loss partials, dL/dJ, smoothed gradient, |g|^2 partials.
+int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s);
+// Pass 2: trial field (Eq. tile1 + Eq. compositive, optional smoothing).
+int batch_step(const Batch& b, int attempt, cudaStream_t s);
+// Per-pair reduction and state update.
+enum FinMode { FIN_EXPLICIT = 0, FIN_RESET = 1, FIN_DECIDE = 2 };
+int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,
+                   cudaStream_t s);
+// Copy each pair's current field back to slot 0 when it sits in slot 1.
+int batch_sync_back(const Batch& b, cudaStream_t s);
 
 // Replace the calling thread's lm_last_error() message.
 void set_last_error(const char* msg);
-
-// Copy the current field back into slot 0 when it sits in slot 1.
-int sync_back(const Geom& g, float* u0, float* u1, DevState* st,
-              cudaStream_t s);
 
 }  // namespace lmk

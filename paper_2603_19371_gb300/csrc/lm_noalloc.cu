@@ -14,7 +14,6 @@
 #include <cstring>
 #include <mutex>
 
-#include "lm_fused.cuh"
 #include "lm_kernels.cuh"
 
 namespace {
@@ -24,7 +23,7 @@ namespace {
 //   loss partials       MAX_CTAS doubles
 //   |g|^2 partials      MAX_CTAS floats
 //   image range parts   MAX_CTAS float2
-//   QScale, EvalOut
+//   QScale, EvalOut, the one-pair descriptor table
 constexpr size_t MAX_CTAS = 1024;
 constexpr size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 constexpr size_t OFF_DLDJ = 0;
@@ -34,7 +33,8 @@ constexpr size_t OFF_G2 = OFF_LOSS + align256(MAX_CTAS * sizeof(double));
 constexpr size_t OFF_MM = OFF_G2 + align256(MAX_CTAS * sizeof(float));
 constexpr size_t OFF_QS = OFF_MM + align256(MAX_CTAS * sizeof(float2));
 constexpr size_t OFF_OUT = OFF_QS + align256(sizeof(lmk::QScale));
-constexpr size_t SCRATCH_BYTES = OFF_OUT + align256(sizeof(lmk::EvalOut));
+constexpr size_t OFF_PD = OFF_OUT + align256(sizeof(lmk::EvalOut));
+constexpr size_t SCRATCH_BYTES = OFF_PD + align256(sizeof(lmk::PairDesc));
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
@@ -79,6 +79,11 @@ int setup_device(int dev, unsigned char** ptr, int* sms) {
     *ptr = g_scratch_ptr[dev];
     *sms = g_num_sms[dev];
     return LM_OK;
+}
+
+// Stores the one-pair descriptor table (passed by value) on the stream.
+__global__ void k_noalloc_table(lmk::PairDesc* dst, lmk::PairDesc v) {
+    if (threadIdx.x == 0) *dst = v;
 }
 
 // Copies the reduced scalars to the caller's device outputs.
@@ -134,35 +139,40 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     int rc = setup_device(dev, &base, &sms);
     if (rc != LM_OK) return rc;
 
-    lmk::Geom g;
-    g.nx = fixed->W;
-    g.ny = fixed->H;
-    g.nz = fixed->D;
-    g.V = V;
-    lmk::FusedPlan plan = lmk::fused_plan(g, prm.win, sms);
-    if ((size_t)plan.e1_ctas > MAX_CTAS || (size_t)plan.e2_ctas > MAX_CTAS ||
-        (size_t)plan.minmax_ctas > MAX_CTAS)
-        return fail(LM_EUNSUPPORTED, "device has more SMs than the scratch covers");
-
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    float* dldj = (float*)(base + OFF_DLDJ);
-    double* loss_part = (double*)(base + OFF_LOSS);
-    float* g2_part = (float*)(base + OFF_G2);
-    float2* mm = (float2*)(base + OFF_MM);
-    lmk::QScale* qs = (lmk::QScale*)(base + OFF_QS);
+    lmk::PairDesc pd;
+    memset(&pd, 0, sizeof(pd));
+    pd.g.nx = fixed->W;
+    pd.g.ny = fixed->H;
+    pd.g.nz = fixed->D;
+    pd.g.V = V;
+    pd.F = fixed->data;
+    pd.M = moving->data;
+    pd.u_in = u;
+    pd.g_out = g_out;
+    pd.dldj = (float*)(base + OFF_DLDJ);
+    pd.qs = (lmk::QScale*)(base + OFF_QS);
+    lmk::BatchPlan plan = lmk::plan_batch(&pd, 1, prm.win, sms);
+    if ((size_t)plan.e1_ctas > MAX_CTAS || (size_t)plan.e2_ctas > MAX_CTAS ||
+        (size_t)plan.mm_ctas > MAX_CTAS)
+        return fail(LM_EUNSUPPORTED, "device has more SMs than the scratch covers");
+    lmk::PairDesc* dpd = (lmk::PairDesc*)(base + OFF_PD);
     lmk::EvalOut* out = (lmk::EvalOut*)(base + OFF_OUT);
 
-    lmk::LnccConsts lc{};
-    lc.win = prm.win;
-    lc.eps_nr = prm.eps_nr;
-    lc.eps_dr = prm.eps_dr;
-    lc.inv_k3 = (float)(1.0 / ((double)prm.win * prm.win * prm.win));
-    lc.inv_V = (float)(1.0 / (double)V);
+    lmk::Batch b{};
+    b.pd = dpd;
+    b.npairs = 1;
+    b.dtype = fixed->dtype;
+    b.plan = plan;
+    b.c.win = prm.win;
+    b.c.eps_nr = prm.eps_nr;
+    b.c.eps_dr = prm.eps_dr;
+    b.c.inv_k3 = (float)(1.0 / ((double)prm.win * prm.win * prm.win));
     // Gaussian taps, as in the context path
     {
         double sg = prm.sigma_grad;
-        lc.gtaps.R = 0;
-        lc.gtaps.t[0] = 1.f;
+        b.c.gtaps.R = 0;
+        b.c.gtaps.t[0] = 1.f;
         if (sg > 0) {
             int R = (int)ceil(3.0 * sg);
             double w[2 * lmk::MAX_R + 1], sum = 0;
@@ -170,46 +180,18 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
                 w[j + R] = exp(-(double)j * j / (2.0 * sg * sg));
                 sum += w[j + R];
             }
-            lc.gtaps.R = R;
-            for (int j = 0; j <= 2 * R; ++j) lc.gtaps.t[j] = (float)(w[j] / sum);
+            b.c.gtaps.R = R;
+            for (int j = 0; j <= 2 * R; ++j) b.c.gtaps.t[j] = (float)(w[j] / sum);
         }
     }
+    b.part.loss = (double*)(base + OFF_LOSS);
+    b.part.g2max = (float*)(base + OFF_G2);
+    b.mm_part = (float2*)(base + OFF_MM);
 
-    lmk::fused_qscale(fixed->data, moving->data, fixed->dtype, g, plan, prm.win,
-                      mm, qs, s);
-    lmk::FusedLaunch f;
-    f.g = g;
-    f.F = fixed->data;
-    f.M = moving->data;
-    f.dtype = fixed->dtype;
-    f.io.u_in = u;
-    f.io.g_out = g_out;
-    f.io.u0 = const_cast<float*>(u);
-    f.io.u1 = nullptr;
-    f.io.g0 = nullptr;
-    f.io.g1 = nullptr;
-    f.io.st = nullptr;
-    f.io.mode = lmk::EVAL_EXPLICIT;
-    f.io.attempt = 0;
-    f.c = lc;
-    f.plan = plan;
-    f.qs = qs;
-    f.dldj = dldj;
-    f.part.loss = loss_part;
-    f.part.n_loss = plan.e1_ctas;
-    f.part.g2max = g2_part;
-    f.part.n_g2 = plan.e2_ctas;
-    lmk::eval_fused(f, s);
-    lmk::FinLaunch fl;
-    fl.part = f.part;
-    fl.st = nullptr;
-    fl.out = out;
-    fl.log = nullptr;
-    fl.d = lmk::DecideConsts{};
-    fl.inv_V = 1.0 / (double)V;
-    fl.mode = lmk::FIN_EXPLICIT;
-    fl.attempt = 0;
-    lmk::finalize(fl, s);
+    k_noalloc_table<<<1, 32, 0, s>>>(dpd, pd);
+    lmk::batch_qscale(b, s);
+    lmk::batch_eval(b, lmk::EVAL_EXPLICIT, 0, s);
+    lmk::batch_finalize(b, lmk::FIN_EXPLICIT, 0, out, s);
     k_noalloc_out<<<1, 32, 0, s>>>(out, loss_out, gmax_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LM_ECUDA, cudaGetErrorString(e));

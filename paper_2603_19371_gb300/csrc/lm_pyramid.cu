@@ -1,5 +1,5 @@
-// Pyramid kernels: image means (box-sum shift), anti-aliased downsampling
-// of the images and resampling of the displacement field between levels.
+// Pyramid kernels: anti-aliased downsampling of the images and resampling
+// of the displacement field between levels (Section 2.1, coarse-to-fine).
 #include <cmath>
 
 #include "lm_pyramid.cuh"
@@ -8,31 +8,6 @@ namespace lmk {
 namespace {
 
 constexpr int TPB = 256;
-
-template <typename T>
-__global__ void k_mean_partial(const T* __restrict__ img, long long V,
-                               double* __restrict__ part) {
-    __shared__ double sh[TPB / 32];
-    double s = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V;
-         i += (long long)gridDim.x * blockDim.x)
-        s += (double)ld_img(img, i);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < TPB / 32; ++w) t += sh[w];
-        part[blockIdx.x] = t;
-    }
-}
-
-__global__ void k_mean_final(double* part, int n, long long V) {
-    if (threadIdx.x != 0) return;
-    double t = 0.0;
-    for (int i = 0; i < n; ++i) t += part[i];
-    part[0] = t / (double)V;
-}
 
 template <typename T>
 __global__ void k_blur_line(const T* __restrict__ in, Geom g, int axis,
@@ -158,25 +133,6 @@ void level_dims(int nx, int ny, int nz, int f, int* ox, int* oy, int* oz) {
     *ox = nx / f > 0 ? nx / f : 1;
     *oy = ny / f > 0 ? ny / f : 1;
     *oz = nz / f > 0 ? nz / f : 1;
-}
-
-int image_mean(const void* img, int dtype, long long V, double* tmp,
-               float* mean, cudaStream_t s) {
-    long long nbl = (V + TPB - 1) / TPB;
-    int nb = (int)(nbl < 1024 ? nbl : 1024);
-    if (nb < 1) nb = 1;
-    if (dtype == LM_BF16)
-        k_mean_partial<<<nb, TPB, 0, s>>>((const __nv_bfloat16*)img, V, tmp);
-    else
-        k_mean_partial<<<nb, TPB, 0, s>>>((const float*)img, V, tmp);
-    k_mean_final<<<1, 32, 0, s>>>(tmp, nb, V);
-    double h = 0.0;
-    if (cudaMemcpyAsync(&h, tmp, sizeof(double), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return -1;
-    *mean = (float)h;
-    return 0;
 }
 
 int downsample_image(const void* src, int dtype, const Geom& g, int f,

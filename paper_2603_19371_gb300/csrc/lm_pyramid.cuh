@@ -9,11 +9,6 @@ namespace lmk {
 // Level size: max(1, n / f) per axis.
 void level_dims(int nx, int ny, int nz, int f, int* ox, int* oy, int* oz);
 
-// Mean intensity of an image (synchronises the stream).  tmp must hold
-// max(1, min(1024, ceil(V / 256))) doubles.
-int image_mean(const void* img, int dtype, long long V, double* tmp,
-               float* mean, cudaStream_t s);
-
 // dst = level image of factor f: Gaussian blur (sigma = f / 2, zero
 // padding), then trilinear samples at f p + (f - 1) / 2.  tmp: 2V floats.
 int downsample_image(const void* src, int dtype, const Geom& g, int f,

@@ -1,5 +1,5 @@
 // Pass 2 (the factored LM step and the compositive update, steps (c)-(d))
-// and the device-side decision (step (e)).
+// and the device-side decision (step (e)), for every pair of a batch.
 //
 //   ghat = g / gmax
 //   du   = -r ghat / (|ghat|^2 + lambda)             Eq. tile1 (Appendix A)
@@ -7,7 +7,7 @@
 //   u*   = v + u o (Id + v)                           Eq. compositive
 //   u*  <- G_sigma_warp * u*   (edge-extended, optional)
 // then, after the trial is evaluated, the damping rule of Eq. lambda-update
-// and the rejection rule of Eq. rejection decide on device.
+// and the rejection rule of Eq. rejection decide on device, per pair.
 #include <algorithm>
 
 #include "lm_kernels.cuh"
@@ -25,63 +25,71 @@ __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
     return attempt > 0 && st->done;
 }
 
-// Trial field, one voxel per thread.  A CTA owns a 32 x 8 x-y tile and a z
-// range; the planes z-1, z, z+1 of u (3 components, with a one-voxel x-y
-// halo, read at edge-clamped positions) sit in a shared-memory ring, so
-// the trilinear read of u at p + v comes from shared memory whenever
-// |v| < 1 along each axis and from global memory otherwise.  The trial goes
-// to slot (1 - cu), or to dst when the warp is smoothed afterwards.
+// Trial field, one voxel per thread.  A block owns a 32 x 8 x-y tile and a
+// z range of one pair; the planes z-1, z, z+1 of u (3 components, with a
+// one-voxel x-y halo, read at edge-clamped positions) sit in a
+// shared-memory ring, so the trilinear read of u at p + v comes from shared
+// memory whenever |v| < 1 along each axis and from global memory otherwise.
+// The trial goes to slot (1 - cu), or to the pair's warp-smoothing buffer.
 constexpr int ST_X = 32, ST_Y = 8, ST_HX = ST_X + 2, ST_HY = ST_Y + 2;
 constexpr int ST_PLANE = ST_HX * ST_HY;
 
 __global__ void __launch_bounds__(ST_X * ST_Y)
-    k_step_compose(StepLaunch a, float* __restrict__ dst, int zc) {
+    k_step_compose(const PairDesc* __restrict__ pd, int npairs, int attempt,
+                   float step, int smooth) {
     __shared__ float ring[3][3][ST_PLANE];   // [z slot][component][y][x]
-    if (attempt_skip(a.st, a.attempt)) return;
-    const Geom g = a.g;
-    const int cu = a.st->cu, cg = a.st->cg;
-    const float* __restrict__ u = cu ? a.u1 : a.u0;
-    float* __restrict__ out = dst ? dst : (cu ? a.u0 : a.u1);
-    const float* __restrict__ gg = cg ? a.g1 : a.g0;
-    const float r = (float)a.st->L;
-    const float lam = (float)a.st->lambda;
-    const float gm = a.st->gmax;
+    const PairDesc& P = pd[pair_of_block<3>(pd, npairs, blockIdx.x)];
+    const DevState* st = P.st;
+    if (attempt_skip(st, attempt)) return;
+    const Geom g = P.g;
+    const int cu = st->cu, cg = st->cg;
+    const float* __restrict__ u = cu ? P.u1 : P.u0;
+    float* __restrict__ out = smooth ? P.wtmpA : (cu ? P.u0 : P.u1);
+    const float* __restrict__ gg = cg ? P.g1 : P.g0;
+    const float r = (float)st->L;
+    const float lam = (float)st->lambda;
+    const float gm = st->gmax;
     const float inv = gm > 0.f ? 1.f / gm : 0.f;
-    const float scale = -r * a.step;
+    const float scale = -r * step;
 
+    const int b = blockIdx.x - P.st_blk0;
+    const int bx = b % P.st_tx;
+    const int rest = b / P.st_tx;
+    const int by = rest % P.st_ty;
+    const int bz = rest / P.st_ty;
     const int tid = threadIdx.y * ST_X + threadIdx.x;
-    const int x0 = blockIdx.x * ST_X, y0 = blockIdx.y * ST_Y;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(z0 + zc, g.nz);
+    const int x0 = bx * ST_X, y0 = by * ST_Y;
+    const int z0 = bz * P.st_zc;
+    const int z1 = min(z0 + P.st_zc, g.nz);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int sxy = g.nx * g.ny;
     const float* U[3] = {u, u + g.V, u + 2 * g.V};
 
     // Each thread loads fixed halo positions of every plane; their clamped
-    // in-plane offsets and smem slots are computed once.
+    // in-plane sources and smem slots are computed once.
     constexpr int NLD = (3 * ST_PLANE + ST_X * ST_Y - 1) / (ST_X * ST_Y);
     const float* ld_src[NLD];
     int ld_dst[NLD];
 #pragma unroll
-    for (int r = 0; r < NLD; ++r) {
-        int k = tid + r * ST_X * ST_Y;
-        ld_dst[r] = -1;
-        ld_src[r] = u;
-        if (k < 3 * ST_PLANE) {
-            int q = k / ST_PLANE, rem = k - q * ST_PLANE;
+    for (int k = 0; k < NLD; ++k) {
+        int e = tid + k * ST_X * ST_Y;
+        ld_dst[k] = -1;
+        ld_src[k] = u;
+        if (e < 3 * ST_PLANE) {
+            int q = e / ST_PLANE, rem = e - q * ST_PLANE;
             int hy = rem / ST_HX, hx = rem - hy * ST_HX;
             int gx = min(max(x0 - 1 + hx, 0), g.nx - 1);
             int gy = min(max(y0 - 1 + hy, 0), g.ny - 1);
-            ld_src[r] = u + q * g.V + gy * g.nx + gx;
-            ld_dst[r] = q * ST_PLANE + rem;
+            ld_src[k] = u + q * g.V + gy * g.nx + gx;
+            ld_dst[k] = q * ST_PLANE + rem;
         }
     }
     auto load_plane = [&](int zp, int slot) {
         const int zo = min(max(zp, 0), g.nz - 1) * sxy;
         float* dst = &ring[slot][0][0];
 #pragma unroll
-        for (int r = 0; r < NLD; ++r)
-            if (ld_dst[r] >= 0) dst[ld_dst[r]] = __ldg(ld_src[r] + zo);
+        for (int k = 0; k < NLD; ++k)
+            if (ld_dst[k] >= 0) dst[ld_dst[k]] = __ldg(ld_src[k] + zo);
     };
     load_plane(z0 - 1, (z0 + 2) % 3);
     load_plane(z0, z0 % 3);
@@ -125,55 +133,57 @@ __global__ void __launch_bounds__(ST_X * ST_Y)
                     m[q][7] = p1[ST_HX + 1];
                 }
             } else {
-                const int ax = min(max(cx, 0), g.nx - 1), bx = min(max(cx + 1, 0), g.nx - 1);
-                const int ay = min(max(cy, 0), g.ny - 1), by = min(max(cy + 1, 0), g.ny - 1);
-                const int az = min(max(cz, 0), g.nz - 1), bz = min(max(cz + 1, 0), g.nz - 1);
+                const int ax = min(max(cx, 0), g.nx - 1), bx2 = min(max(cx + 1, 0), g.nx - 1);
+                const int ay = min(max(cy, 0), g.ny - 1), by2 = min(max(cy + 1, 0), g.ny - 1);
+                const int az = min(max(cz, 0), g.nz - 1), bz2 = min(max(cz + 1, 0), g.nz - 1);
                 const int o000 = az * sxy + ay * g.nx;
-                const int o010 = az * sxy + by * g.nx;
-                const int o001 = bz * sxy + ay * g.nx;
-                const int o011 = bz * sxy + by * g.nx;
+                const int o010 = az * sxy + by2 * g.nx;
+                const int o001 = bz2 * sxy + ay * g.nx;
+                const int o011 = bz2 * sxy + by2 * g.nx;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     m[q][0] = __ldg(U[q] + o000 + ax);
-                    m[q][1] = __ldg(U[q] + o000 + bx);
+                    m[q][1] = __ldg(U[q] + o000 + bx2);
                     m[q][2] = __ldg(U[q] + o010 + ax);
-                    m[q][3] = __ldg(U[q] + o010 + bx);
+                    m[q][3] = __ldg(U[q] + o010 + bx2);
                     m[q][4] = __ldg(U[q] + o001 + ax);
-                    m[q][5] = __ldg(U[q] + o001 + bx);
+                    m[q][5] = __ldg(U[q] + o001 + bx2);
                     m[q][6] = __ldg(U[q] + o011 + ax);
-                    m[q][7] = __ldg(U[q] + o011 + bx);
+                    m[q][7] = __ldg(U[q] + o011 + bx2);
                 }
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                float s = wz0 * (wy0 * (wx0 * m[q][0] + wx1 * m[q][1]) +
-                                 wy1 * (wx0 * m[q][2] + wx1 * m[q][3])) +
-                          wz1 * (wy0 * (wx0 * m[q][4] + wx1 * m[q][5]) +
-                                 wy1 * (wx0 * m[q][6] + wx1 * m[q][7]));
-                out[q * g.V + i] = v[q] + s;
+                float sv = wz0 * (wy0 * (wx0 * m[q][0] + wx1 * m[q][1]) +
+                                  wy1 * (wx0 * m[q][2] + wx1 * m[q][3])) +
+                           wz1 * (wy0 * (wx0 * m[q][4] + wx1 * m[q][5]) +
+                                  wy1 * (wx0 * m[q][6] + wx1 * m[q][7]));
+                out[q * g.V + i] = v[q] + sv;
             }
         }
         __syncthreads();
     }
 }
 
-// 1-D Gaussian along an axis of a 3-component field, edge-extended.  The z
-// pass writes the trial slot (1 - cu).
-__global__ void k_warp_gauss(const float* __restrict__ in, StepLaunch a,
-                             int axis, float* __restrict__ out,
-                             int final_pass) {
-    if (attempt_skip(a.st, a.attempt)) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const Geom& g = a.g;
+// 1-D Gaussian along an axis of a pair's 3-component field, edge-extended;
+// pass 0: wtmpA -> wtmpB (x), 1: wtmpB -> wtmpA (y), 2: wtmpA -> trial
+// slot (1 - cu) (z).  One thread per voxel.
+__global__ void k_warp_gauss(const PairDesc* __restrict__ pd, int npairs,
+                             int attempt, Taps t, int axis) {
+    const PairDesc& P = pd[pair_of_block<4>(pd, npairs, blockIdx.x)];
+    if (attempt_skip(P.st, attempt)) return;
+    const Geom g = P.g;
+    long long i = (long long)(blockIdx.x - P.ln_blk0) * blockDim.x + threadIdx.x;
     if (i >= g.V) return;
-    float* dst = final_pass ? (a.st->cu ? a.u0 : a.u1) : out;
+    const float* in = axis == 1 ? P.wtmpB : P.wtmpA;
+    float* dst = axis == 0 ? P.wtmpB
+                           : (axis == 1 ? P.wtmpA : (P.st->cu ? P.u0 : P.u1));
     int x = (int)(i % g.nx);
     long long rr = i / g.nx;
     int y = (int)(rr % g.ny), z = (int)(rr / g.ny);
     int pos = axis == 0 ? x : (axis == 1 ? y : z);
     int n = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
     long long stride = axis == 0 ? 1 : (axis == 1 ? g.nx : (long long)g.nx * g.ny);
-    const Taps& t = a.wtaps;
     float acc[3] = {0.f, 0.f, 0.f};
     for (int j = -t.R; j <= t.R; ++j) {
         int pp = min(max(pos + j, 0), n - 1);
@@ -211,42 +221,46 @@ __device__ __forceinline__ float block_max1024(float v, float* sh) {
     return v;
 }
 
-// Fixed-order FP64 reduction of the partials (deterministic), then the
-// per-mode state update.  One CTA.
-__global__ void k_finalize(FinLaunch a) {
+// One CTA per pair: fixed-order FP64 reduction of the pair's partials
+// (deterministic), then the per-mode state update.
+__global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
+                           DecideConsts d, int mode, int attempt,
+                           EvalOut* __restrict__ outs) {
     __shared__ double shd[32];
     __shared__ float shf[32];
-    DevState* st = a.st;
-    if (a.mode == FIN_DECIDE && attempt_skip(st, a.attempt)) return;
+    const PairDesc& P = pd[blockIdx.x];
+    DevState* st = P.st;
+    if (mode == FIN_DECIDE && attempt_skip(st, attempt)) return;
     double s = 0.0;
-    for (int i = threadIdx.x; i < a.part.n_loss; i += blockDim.x)
-        s += a.part.loss[i];
+    for (int i = threadIdx.x; i < P.e1_ncta; i += blockDim.x)
+        s += part.loss[P.e1_cta0 + i];
     s = block_sum1024(s, shd);
     float m = 0.f;
     int nf = 0;
-    for (int i = threadIdx.x; i < a.part.n_g2; i += blockDim.x) {
-        float v = a.part.g2max[i];
+    for (int i = threadIdx.x; i < P.e2_ncta; i += blockDim.x) {
+        float v = part.g2max[P.e2_cta0 + i];
         if (!(v <= 3.0e38f)) nf = 1;   // NaN or overflow
         else m = fmaxf(m, v);
     }
     nf = __syncthreads_or(nf);
     m = block_max1024(m, shf);
     if (threadIdx.x != 0) return;
-    double L = s * a.inv_V;
+    double L = s / (double)P.g.V;
     float gmax = sqrtf(m);
     bool bad = nf || !isfinite(L) || !isfinite(gmax);
-    if (a.mode == FIN_EXPLICIT) {
-        a.out->L = L;
-        a.out->gmax = gmax;
-        a.out->status = bad ? STATUS_NONFINITE : 0;
+    if (mode == FIN_EXPLICIT) {
+        EvalOut* o = outs + blockIdx.x;
+        o->L = L;
+        o->gmax = gmax;
+        o->status = bad ? STATUS_NONFINITE : 0;
         return;
     }
-    if (a.mode == FIN_RESET) {
+    if (mode == FIN_RESET) {
         st->L = L;
         st->L_prev = 0.0;
         st->L_trial = L;
         st->L_first = L;
-        st->lambda = a.d.lambda0;
+        st->lambda = d.lambda0;
         st->gmax = gmax;
         st->gmax_trial = gmax;
         st->has_prev = 0;
@@ -262,7 +276,7 @@ __global__ void k_finalize(FinLaunch a) {
         return;
     }
     // FIN_DECIDE
-    const int j = a.attempt;
+    const int j = attempt;
     st->evals += 1;
     st->L_trial = L;
     st->gmax_trial = gmax;
@@ -270,7 +284,6 @@ __global__ void k_finalize(FinLaunch a) {
         st->L_first = L;
         st->retries = 0;
     }
-    const DecideConsts& d = a.d;
     double lam = st->lambda;
     int finished = 0, accepted = 0;
     if (bad) {
@@ -311,7 +324,7 @@ __global__ void k_finalize(FinLaunch a) {
     st->accepted = accepted;
     st->done = finished;
     st->iter += 1;
-    if (a.log) {
+    if (P.log) {
         int pos = st->log_pos;
         LogEntry e;
         e.loss = st->L;
@@ -320,57 +333,46 @@ __global__ void k_finalize(FinLaunch a) {
         e.accepted = accepted;
         e.retries = j;
         e.pad = 0;
-        a.log[pos % LOG_CAP] = e;
+        P.log[pos % LOG_CAP] = e;
         st->log_pos = pos + 1;
     }
 }
 
-__global__ void k_copy_back(const Geom g, float* __restrict__ u0,
-                            const float* __restrict__ u1,
-                            const DevState* st) {
-    if (st->cu == 0) return;
-    long long n = 3 * g.V;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (; i < n; i += stride) u0[i] = u1[i];
+__global__ void k_copy_back(const PairDesc* __restrict__ pd, int npairs) {
+    const PairDesc& P = pd[pair_of_block<4>(pd, npairs, blockIdx.x)];
+    if (P.st->cu == 0) return;
+    long long i = (long long)(blockIdx.x - P.ln_blk0) * blockDim.x + threadIdx.x;
+    if (i >= P.g.V) return;
+    for (int q = 0; q < 3; ++q) P.u0[q * P.g.V + i] = P.u1[q * P.g.V + i];
 }
 
-__global__ void k_flip_slot(DevState* st) { st->cu = 0; }
+__global__ void k_flip_slot(const PairDesc* __restrict__ pd) {
+    if (threadIdx.x == 0) pd[blockIdx.x].st->cu = 0;
+}
 
 }  // namespace
 
-int step_compose(const StepLaunch& a, cudaStream_t s) {
-    unsigned nb = (unsigned)((a.g.V + TPB - 1) / TPB);
-    // z chunks so that the grid holds ~8 tiles per SM-slot of work
-    const int tx = (a.g.nx + ST_X - 1) / ST_X, ty = (a.g.ny + ST_Y - 1) / ST_Y;
-    const long long cols = (long long)tx * ty;
-    int nzc = (int)std::max<long long>(1, std::min<long long>(
-                                              a.g.nz, (2048 + cols - 1) / cols));
-    int zc = (a.g.nz + nzc - 1) / nzc;
-    nzc = (a.g.nz + zc - 1) / zc;
-    dim3 grid(tx, ty, nzc), block(ST_X, ST_Y);
-    if (a.wtaps.R > 0) {
-        k_step_compose<<<grid, block, 0, s>>>(a, a.tmpA, zc);
-        k_warp_gauss<<<nb, TPB, 0, s>>>(a.tmpA, a, 0, a.tmpB, 0);
-        k_warp_gauss<<<nb, TPB, 0, s>>>(a.tmpB, a, 1, a.tmpA, 0);
-        k_warp_gauss<<<nb, TPB, 0, s>>>(a.tmpA, a, 2, nullptr, 1);
-        return 4;
-    }
-    k_step_compose<<<grid, block, 0, s>>>(a, nullptr, zc);
+int batch_step(const Batch& b, int attempt, cudaStream_t s) {
+    const int smooth = b.wtaps.R > 0;
+    k_step_compose<<<b.plan.st_blocks, dim3(ST_X, ST_Y), 0, s>>>(
+        b.pd, b.npairs, attempt, b.step, smooth);
+    if (!smooth) return 1;
+    for (int axis = 0; axis < 3; ++axis)
+        k_warp_gauss<<<b.plan.ln_blocks, TPB, 0, s>>>(b.pd, b.npairs, attempt,
+                                                      b.wtaps, axis);
+    return 4;
+}
+
+int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,
+                   cudaStream_t s) {
+    k_finalize<<<b.npairs, 1024, 0, s>>>(b.pd, b.part, b.d, mode, attempt,
+                                         out);
     return 1;
 }
 
-int finalize(const FinLaunch& a, cudaStream_t s) {
-    k_finalize<<<1, 1024, 0, s>>>(a);
-    return 1;
-}
-
-int sync_back(const Geom& g, float* u0, float* u1, DevState* st,
-              cudaStream_t s) {
-    long long n = 3 * g.V;
-    unsigned nb = (unsigned)std::min<long long>((n + TPB - 1) / TPB, 4096);
-    k_copy_back<<<nb, TPB, 0, s>>>(g, u0, u1, st);
-    k_flip_slot<<<1, 1, 0, s>>>(st);
+int batch_sync_back(const Batch& b, cudaStream_t s) {
+    k_copy_back<<<b.plan.ln_blocks, TPB, 0, s>>>(b.pd, b.npairs);
+    k_flip_slot<<<b.npairs, 32, 0, s>>>(b.pd);
     return 2;
 }
 

@@ -103,6 +103,19 @@ def load():
         "lm_time_passes": [V, V, I, ctypes.POINTER(D), ctypes.POINTER(D)],
         "lm_eval_noalloc": [ctypes.POINTER(Volume), ctypes.POINTER(Volume),
                             ctypes.POINTER(Params), V, V, V, V, V],
+        "lm_batch_init": [ctypes.POINTER(V), I, ctypes.POINTER(Volume),
+                          ctypes.POINTER(Volume), ctypes.POINTER(Params), V],
+        "lm_batch_eval": [V, ctypes.POINTER(V), ctypes.POINTER(V),
+                          ctypes.POINTER(D), ctypes.POINTER(ctypes.c_float)],
+        "lm_batch_reset": [V, ctypes.POINTER(V)],
+        "lm_batch_iterate": [V, ctypes.POINTER(V), I,
+                             ctypes.POINTER(StepInfo)],
+        "lm_batch_register": [V, ctypes.POINTER(Schedule), ctypes.POINTER(V),
+                              ctypes.POINTER(Report)],
+        "lm_register_batch": [I, ctypes.POINTER(Volume), ctypes.POINTER(Volume),
+                              ctypes.POINTER(V), ctypes.POINTER(Params),
+                              ctypes.POINTER(Schedule), V,
+                              ctypes.POINTER(Report)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -110,6 +123,8 @@ def load():
         fn.restype = I
     lib.lm_destroy.argtypes = [V]
     lib.lm_destroy.restype = None
+    lib.lm_batch_destroy.argtypes = [V]
+    lib.lm_batch_destroy.restype = None
     lib.lm_strerror.argtypes = [I]
     lib.lm_strerror.restype = ctypes.c_char_p
     lib.lm_last_error.argtypes = []
@@ -240,11 +255,7 @@ def lm_set_state(ctx: Context, s: State):
 
 def lm_register(ctx: Context, levels, u) -> Report:
     """levels: sequence of (factor, iters)."""
-    s = Schedule()
-    s.nlevels = len(levels)
-    for i, (f, it) in enumerate(levels):
-        s.factor[i] = int(f)
-        s.iters[i] = int(it)
+    s = _schedule(levels)
     r = Report()
     _check(load().lm_register(ctx.handle, ctypes.byref(s),
                               _field_ptr(u, ctx.shape), ctypes.byref(r)),
@@ -276,6 +287,103 @@ def lm_time_passes(ctx: Context, u, n):
     return a.value, b.value
 
 
+class Batch:
+    """Owns an lm_batch handle and keeps its images alive."""
+
+    def __init__(self, handle, fixed, moving, stream):
+        self.handle = handle
+        self.fixed, self.moving = list(fixed), list(moving)
+        self.shapes = [tuple(f.shape) for f in fixed]
+        self.stream = stream
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.lm_batch_destroy(h)
+
+
+def _ptr_array(ts, shapes=None):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _field_ptr(t, shapes[i] if shapes else None).value
+    return arr
+
+
+def _schedule(levels):
+    s = Schedule()
+    s.nlevels = len(levels)
+    for i, (f, it) in enumerate(levels):
+        s.factor[i] = int(f)
+        s.iters[i] = int(it)
+    return s
+
+
+def lm_batch_init(fixed, moving, params: Params | None = None, stream=None):
+    vf = (Volume * len(fixed))(*[_volume(t) for t in fixed])
+    vm = (Volume * len(moving))(*[_volume(t) for t in moving])
+    h = ctypes.c_void_p()
+    p = ctypes.byref(params) if params is not None else None
+    _check(load().lm_batch_init(ctypes.byref(h), len(fixed), vf, vm, p,
+                                _stream_handle(stream)), "lm_batch_init")
+    return Batch(h, fixed, moving, stream)
+
+
+def lm_batch_destroy(b: Batch):
+    h, b.handle = b.handle, None
+    if h:
+        load().lm_batch_destroy(h)
+
+
+def lm_batch_eval(b: Batch, us, g_outs=None):
+    """Returns (losses, gmaxes) lists; fills g_outs when given."""
+    n = len(b)
+    L = (ctypes.c_double * n)()
+    gm = (ctypes.c_float * n)()
+    gp = _ptr_array(g_outs, b.shapes) if g_outs is not None else None
+    _check(load().lm_batch_eval(b.handle, _ptr_array(us, b.shapes), gp, L, gm),
+           "lm_batch_eval")
+    return list(L), list(gm)
+
+
+def lm_batch_reset(b: Batch, us):
+    _check(load().lm_batch_reset(b.handle, _ptr_array(us, b.shapes)),
+           "lm_batch_reset")
+
+
+def lm_batch_iterate(b: Batch, us, n, info=True):
+    infos = (StepInfo * len(b))() if info else None
+    _check(load().lm_batch_iterate(b.handle, _ptr_array(us, b.shapes), int(n),
+                                   infos), "lm_batch_iterate")
+    return list(infos) if info else None
+
+
+def lm_batch_register(b: Batch, levels, us):
+    s = _schedule(levels)
+    reps = (Report * len(b))()
+    _check(load().lm_batch_register(b.handle, ctypes.byref(s),
+                                    _ptr_array(us, b.shapes), reps),
+           "lm_batch_register")
+    return list(reps)
+
+
+def lm_register_batch(fixed, moving, us, levels, params: Params | None = None,
+                      stream=None):
+    vf = (Volume * len(fixed))(*[_volume(t) for t in fixed])
+    vm = (Volume * len(moving))(*[_volume(t) for t in moving])
+    s = _schedule(levels)
+    reps = (Report * len(fixed))()
+    p = ctypes.byref(params) if params is not None else None
+    _check(load().lm_register_batch(len(fixed), vf, vm,
+                                    _ptr_array(us, [f.shape for f in fixed]),
+                                    p, ctypes.byref(s),
+                                    _stream_handle(stream), reps),
+           "lm_register_batch")
+    return list(reps)
+
+
 def lm_eval_noalloc(fixed, moving, u, g_out, loss_out=None, gmax_out=None,
                     params: Params | None = None, stream=None):
     """Evaluation without allocation (static scratch, at most
@@ -302,5 +410,7 @@ def lm_last_error() -> str:
 EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_reset", "lm_step", "lm_iterate", "lm_get_state",
             "lm_set_state", "lm_register", "lm_state_save", "lm_state_load",
-            "lm_time_passes", "lm_eval_noalloc", "lm_strerror",
-            "lm_last_error")
+            "lm_time_passes", "lm_batch_init", "lm_batch_destroy",
+            "lm_batch_eval", "lm_batch_reset", "lm_batch_iterate",
+            "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
+            "lm_strerror", "lm_last_error")

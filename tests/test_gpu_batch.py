@@ -1,0 +1,139 @@
+"""GPU parity of the batched path: several pairs of uneven shapes share each
+kernel launch; every pair must match the FP64 oracle exactly as a single
+pair does (same bars as test_gpu_parity)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_U = 1e-4
+TOL_L = 1e-5
+TOL_G = 1e-4
+
+SHAPES = [(20, 24, 28), (32, 32, 32), (13, 17, 29), (40, 36, 44)]
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_19371_gb300 import build, lmreg
+    build.build()
+    lmreg.load()
+    return lmreg
+
+
+def _oracle_params(oracle, p):
+    return oracle.params(win=p.win, eps_nr=float(np.float32(p.eps_nr)),
+                         eps_dr=float(np.float32(p.eps_dr)),
+                         sigma_grad=float(p.sigma_grad),
+                         sigma_warp=float(p.sigma_warp), step=float(p.step),
+                         lambda0=p.lambda0, mu_inc=p.mu_inc, mu_dec=p.mu_dec,
+                         lambda_max=p.lambda_max, reject=p.reject, tau=p.tau,
+                         max_retries=p.max_retries)
+
+
+def _pairs(seed0=40, dtype=None):
+    import torch
+    import synth
+    Fs, Ms = [], []
+    for i, sh in enumerate(SHAPES):
+        F, M, _ = synth.blob_pair(sh, seed=seed0 + i)
+        Ft, Mt = torch.from_numpy(F).cuda(), torch.from_numpy(M).cuda()
+        if dtype is not None:
+            Ft, Mt = Ft.to(dtype), Mt.to(dtype)
+        Fs.append(Ft)
+        Ms.append(Mt)
+    return Fs, Ms
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_batch_eval_matches_oracle(P, oracle_mod, bf16):
+    import torch
+    import synth
+    Fs, Ms = _pairs(dtype=torch.bfloat16 if bf16 else None)
+    params = P.lm_default_params()
+    b = P.lm_batch_init(Fs, Ms, params)
+    us = [torch.from_numpy(synth.random_field(sh, seed=7 + i, scale=1.6)).cuda()
+          for i, sh in enumerate(SHAPES)]
+    gs = [torch.empty_like(u) for u in us]
+    L, gm = P.lm_batch_eval(b, us, gs)
+    Po = _oracle_params(oracle_mod, params)
+    for i in range(len(SHAPES)):
+        ev = oracle_mod.evaluate(Fs[i].float().cpu().numpy(),
+                                 Ms[i].float().cpu().numpy(),
+                                 us[i].cpu().numpy().astype(np.float64), Po)
+        assert abs(L[i] - ev["L"]) <= TOL_L * ev["L"], (i, L[i], ev["L"])
+        err = np.abs(gs[i].cpu().numpy() - ev["g"]).max()
+        assert err <= TOL_G * ev["gmax"], (i, err, ev["gmax"])
+
+
+def test_batch_iterations_teacher_forced(P, oracle_mod):
+    import torch
+    Fs, Ms = _pairs(seed0=50)
+    params = P.lm_default_params(lambda0=0.02, step=1.0)
+    Po = _oracle_params(oracle_mod, params)
+    b = P.lm_batch_init(Fs, Ms, params)
+    us = [torch.zeros((3,) + sh, device="cuda") for sh in SHAPES]
+    P.lm_batch_reset(b, us)
+    infos = P.lm_batch_iterate(b, us, 0)
+    L = [x.loss for x in infos]
+    Lp = [0.0] * len(SHAPES)
+    hp = [0] * len(SHAPES)
+    lam = [x.lambda_ for x in infos]
+    Fo = [F.cpu().numpy().astype(np.float64) for F in Fs]
+    Mo = [M.cpu().numpy().astype(np.float64) for M in Ms]
+    for t in range(4):
+        ut = [u.cpu().numpy().astype(np.float64) for u in us]
+        expect = []
+        for i in range(len(SHAPES)):
+            ev = oracle_mod.evaluate(Fo[i], Mo[i], ut[i], Po)
+            assert abs(L[i] - ev["L"]) <= TOL_L * ev["L"], (t, i)
+            u1, _ = oracle_mod.trial(ut[i], ev["g"], ev["gmax"], ev["L"],
+                                     lam[i], Po)
+            L1 = oracle_mod.loss(Fo[i], Mo[i], u1, Po)
+            act, lam_o = oracle_mod.decide(L1, ev["L"], Lp[i], hp[i], lam[i],
+                                           0, Po)
+            expect.append((u1, L1, lam_o, ev["L"]))
+        infos = P.lm_batch_iterate(b, us, 1)
+        for i, x in enumerate(infos):
+            u1, L1, lam_o, L0 = expect[i]
+            assert abs(x.loss_first - L1) <= TOL_L * L1, (t, i)
+            tie = abs(L1 - L0) < 1e-6 * L0
+            assert x.accepted == 1
+            if not tie:
+                assert x.lambda_ == pytest.approx(lam_o, rel=1e-12)
+            err = np.abs(us[i].cpu().numpy().astype(np.float64) - u1).max()
+            assert err <= TOL_U, (t, i, err)
+            Lp[i], hp[i], L[i], lam[i] = L0, 1, x.loss, x.lambda_
+
+
+def test_batch_register_lowers_every_loss(P):
+    import torch
+    Fs, Ms = _pairs(seed0=60)
+    params = P.lm_default_params(lambda0=0.006, step=1.0)
+    b = P.lm_batch_init(Fs, Ms, params)
+    us = [torch.zeros((3,) + sh, device="cuda") for sh in SHAPES]
+    L0, _ = P.lm_batch_eval(b, us)
+    reps = P.lm_batch_register(b, [(2, 10), (1, 10)], us)
+    L1, _ = P.lm_batch_eval(b, us)
+    for i, r in enumerate(reps):
+        assert r.level_iters[0] == 10 and r.level_iters[1] == 10
+        assert L1[i] < L0[i]
+        assert r.final_loss == pytest.approx(L1[i], rel=1e-6)
+    # the one-shot form gives the same fields
+    us2 = [torch.zeros((3,) + sh, device="cuda") for sh in SHAPES]
+    P.lm_register_batch(Fs, Ms, us2, [(2, 10), (1, 10)], params)
+    for a, c in zip(us, us2):
+        assert float((a - c).abs().max()) < 1e-4
+
+
+def test_batch_rejects_mixed_dtypes(P):
+    import torch
+    Fs, Ms = _pairs(seed0=70)
+    Fs[1] = Fs[1].to(torch.bfloat16)
+    Ms[1] = Ms[1].to(torch.bfloat16)
+    with pytest.raises(P.LMError) as e:
+        P.lm_batch_init(Fs, Ms, P.lm_default_params())
+    assert e.value.code == P.LM_EINVAL

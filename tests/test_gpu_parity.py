@@ -80,18 +80,9 @@ def _eval_check(P, oracle_mod, F, M, u, params, dtype="f32", atol_L=0.0):
     return err.max() / max(ev["gmax"], 1e-300)
 
 
-@pytest.fixture(params=["fused", "staged"])
-def schedule(request, monkeypatch):
-    if request.param == "staged":
-        monkeypatch.setenv("LMREG_STAGED", "1")
-    else:
-        monkeypatch.delenv("LMREG_STAGED", raising=False)
-    return request.param
-
-
 @pytest.mark.parametrize("shape", [(32, 32, 32), (13, 17, 29), (5, 7, 3),
                                    (1, 1, 1), (2, 40, 3), (9, 70, 33)])
-def test_eval_parity_shapes(P, oracle_mod, shape, schedule):
+def test_eval_parity_shapes(P, oracle_mod, shape):
     import synth
     rng = np.random.default_rng(11)
     if min(shape) >= 8:
