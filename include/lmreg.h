@@ -251,9 +251,9 @@ LM_API int lm_register_batch(int npairs, const lm_volume *fixed,
  * Same result as lm_eval on a fresh context: the loss r = 1 - LNCC and its
  * smoothed gradient at u, without a context and without any allocation.
  * Its scratch is one static device array inside the library, sized for at
- * most LM_NOALLOC_MAX_VOXELS voxels (about 8.4 MB, held by every GPU that
- * loads the library until the process exits); larger volumes return
- * LM_EINVAL.
+ * most LM_NOALLOC_MAX_VOXELS voxels (2^19, e.g. 80^3; about 14.7 MB, held
+ * by every GPU that loads the library until the process exits); larger
+ * volumes return LM_EINVAL.
  *   fixed, moving: images as for lm_init; p: parameters (NULL = defaults;
  *   only win, eps_nr, eps_dr and sigma_grad matter); u: device field
  *   [3][D][H][W]; g_out: device [3][D][H][W] (written); loss_out: device
@@ -266,7 +266,7 @@ LM_API int lm_register_batch(int npairs, const lm_volume *fixed,
  * host threads without ordering) race and corrupt each other's results;
  * order them on one stream.  The array keeps the last call's contents;
  * every call overwrites all of the scratch it reads. */
-#define LM_NOALLOC_MAX_VOXELS (1 << 21)
+#define LM_NOALLOC_MAX_VOXELS (1 << 19)
 LM_API int lm_eval_noalloc(const lm_volume *fixed, const lm_volume *moving,
                            const lm_params *p, const float *u, float *g_out,
                            double *loss_out, float *gmax_out,

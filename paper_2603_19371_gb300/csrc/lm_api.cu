@@ -314,7 +314,9 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
         if ((rc = c->dalloc(&d.u1, 3 * V * f4)) ||
             (rc = c->dalloc(&d.g0, 3 * V * f4)) ||
             (rc = c->dalloc(&d.g1, 3 * V * f4)) ||
-            (rc = c->dalloc(&d.dldj, V * f4)))
+            (rc = c->dalloc(&d.graw, 3 * V * f4)) ||
+            (rc = c->dalloc(&d.jq, V * sizeof(int))) ||
+            (rc = c->dalloc(&d.dj, 3 * V * f4)))
             return rc;
         if (smooth && ((rc = c->dalloc(&d.wtmpA, 3 * V * f4)) ||
                        (rc = c->dalloc(&d.wtmpB, 3 * V * f4))))

@@ -1,17 +1,19 @@
-// Pass 1 (loss and smoothed gradient, steps (a)-(c)) as two z-streaming
-// kernels.  Each CTA owns a column of the volume (an x-y tile) and a range
+// Pass 1 (loss and smoothed gradient, steps (a)-(c)) as a per-voxel
+// resampling kernel (J pass) and two z-streaming kernels.  Each CTA owns a column of the volume (an x-y tile) and a range
 // of z, marching along z with the planes of every stage in shared memory;
 // separable box and Gaussian filters run along x and y on the planes and
 // along z on ring buffers of the last k planes.
 //
-//  E1 (lncc): J = M(p + u) (trilinear, Section 2.1); the LNCC window
-//     moments (k^3 box, zero padding); per voxel (1 - cc) and the backward
+//  J pass: J = M(p + u) and dJ/du (trilinear, Section 2.1), J in the fixed
+//     point of the moments (int32) and dJ/du (FP32) to HBM.
+//  E1 (lncc): the LNCC window moments of F' and J' (k^3 box, zero padding); per voxel (1 - cc) and the backward
 //     coefficients (a, b, c) of the squared-loss form (Section 2.2); their
 //     box sums; and
 //        dL/dJ(y) = -V^-1 [F'(y) Box(a) + 2 J'(y) Box(b) + Box(c)]
-//     written to HBM (4 bytes / voxel), plus the CTA's loss partial.
-//  E2 (grad): dJ/du, g_raw = dL/dJ * dJ/du on the tile and an R halo,
-//     separable Gaussian (R = ceil(3 sigma)), g to HBM, CTA max |g|^2.
+//     plus the CTA's loss partial.
+//     E1 writes g_raw = dL/dJ * dJ/du (12 bytes / voxel).
+//  E2 (grad): separable Gaussian of g_raw (R = ceil(3 sigma), zero
+//     padding), g to HBM, CTA max |g|^2.
 //
 // Window moments are exact: F' = F - s and J' = J - s are rounded to fixed
 // point (Xq = round(X' * Q), |Xq| <= 2^qb) and the window sums of Xq and of
@@ -20,8 +22,9 @@
 // variance cancellation that FP32 window sums suffer in flat regions is
 // gone.  Everything after the moments is FP32.
 //
-// HBM traffic per voxel: E1 reads F, M, u (20 B) and writes dL/dJ (4 B);
-// E2 reads dL/dJ, M, u (20 B) and writes g (12 B).  Halo re-reads hit L2.
+// HBM traffic per voxel: the J pass reads u, M (16 B) and writes Jq, dJ
+// (16 B); E1 reads F, Jq, dJ (20 B) and writes g_raw (12 B); E2 reads g_raw
+// (12 B) and writes g (12 B).  Halo re-reads hit L2.
 #include <algorithm>
 #include <vector>
 
@@ -113,6 +116,64 @@ __device__ __forceinline__ Share share_of(int b, int n, long long total) {
 }
 
 // ----------------------------------------------------------------------
+// J pass: per voxel J = M(p + u(p)) and dJ/du (trilinear, Section 2.1), J
+// rounded to the fixed point of the window moments (JQ_BAD marks a
+// non-finite J), dJ/du kept in FP32.  One thread per x-y column of a 32 x 8
+// tile, marching over the tile's z range (the step kernel's tiling).
+// ----------------------------------------------------------------------
+constexpr int JQ_BAD = (int)0x80000000;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_jpass(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt) {
+    const PairDesc& P = pd[pair_of_block<3>(pd, npairs, blockIdx.x)];
+    if (trial_skip(P, mode, attempt)) return;
+    const Geom g = P.g;
+    const int b = blockIdx.x - P.st_blk0;
+    const int bx = b % P.st_tx;
+    const int rest = b / P.st_tx;
+    const int by = rest % P.st_ty;
+    const int bz = rest / P.st_ty;
+    const int x = bx * 32 + threadIdx.x, y = by * 8 + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int z0 = bz * P.st_zc;
+    const int z1 = min(z0 + P.st_zc, g.nz);
+    const T* __restrict__ M = (const T*)P.M;
+    const float* __restrict__ u = eval_u(P, mode);
+    int* __restrict__ jq = P.jq;
+    float* __restrict__ dj = P.dj;
+    const float sh = P.qs->shift, Q = P.qs->Q;
+    const int qlim = P.qs->qlim;
+    const int sxy = g.nx * g.ny;
+    int i = z0 * sxy + y * g.nx + x;
+    float nu0 = 0.f, nu1 = 0.f, nu2 = 0.f;
+    if (z0 < z1) {
+        nu0 = __ldg(u + i);
+        nu1 = __ldg(u + g.V + i);
+        nu2 = __ldg(u + 2 * g.V + i);
+    }
+    for (int z = z0; z < z1; ++z, i += sxy) {
+        // u of the next slice streams in while this one is resampled
+        const float d0 = nu0, d1 = nu1, d2 = nu2;
+        if (z + 1 < z1) {
+            nu0 = __ldg(u + i + sxy);
+            nu1 = __ldg(u + g.V + i + sxy);
+            nu2 = __ldg(u + 2 * g.V + i + sxy);
+        }
+        float m[8], f[3], d[3];
+        corners(M, g, x, y, z, d0, d1, d2, m, f);
+        const float J = interp(m, f);
+        interp_grad(m, f, d);
+        jq[i] = (fabsf(J) <= 3.0e38f)
+                    ? min(max(__float2int_rn((J - sh) * Q), -qlim), qlim)
+                    : JQ_BAD;
+        dj[i] = d[0];
+        dj[g.V + i] = d[1];
+        dj[2 * g.V + i] = d[2];
+    }
+}
+
+// ----------------------------------------------------------------------
 // E1
 // ----------------------------------------------------------------------
 template <int W>
@@ -132,8 +193,10 @@ struct E1Cfg {
     static constexpr int B_ZR64 = K * 3 * NT * 8;
     static constexpr int B_AB = 3 * SY * SX * 4;
     static constexpr int B_AX = 3 * SY * TX * 4;
+    // delay ring at the output points: F', J' of the last K slices
+    static constexpr int B_DL = K * 2 * TY * TX * 4;
     static constexpr int bytes =
-        B_GQ + B_X32 + B_X64 + B_ZR32 + B_ZR64 + B_AB + B_AX;
+        B_GQ + B_X32 + B_X64 + B_ZR32 + B_ZR64 + B_AB + B_AX + B_DL;
 };
 
 template <int W, typename T>
@@ -160,20 +223,19 @@ __global__ void __launch_bounds__(NT, 1)
     float* Ab = (float*)(smem + C::B_GQ + C::B_X32 + C::B_X64 + C::B_ZR32 +
                          C::B_ZR64);
     float* Ax = Ab + 3 * SY * SX;
+    float* DL = Ax + 3 * SY * TX;   // [K][2][TY * TX]: F', J'
     __shared__ double red[NT / 32];
 
     const PairDesc& P = pd[pair_of_block<1>(pd, npairs, blockIdx.x)];
     if (trial_skip(P, mode, attempt)) return;
     const Geom g = P.g;
     const T* __restrict__ F = (const T*)P.F;
-    const T* __restrict__ M = (const T*)P.M;
-    float* __restrict__ dldj = P.dldj;
+    const int* __restrict__ jqv = P.jq;
+    const float* __restrict__ djv = P.dj;
+    float* __restrict__ graw = P.graw;
     const QScale* __restrict__ qs = P.qs;
     const float inv_V = (float)(1.0 / (double)g.V);
     const int tid = threadIdx.x;
-    const float* __restrict__ u = eval_u(P, mode);
-    const float* __restrict__ u1 = u + g.V;
-    const float* __restrict__ u2 = u + 2 * g.V;
     const int sxy = g.nx * g.ny;
     const float sh = qs->shift, Q = qs->Q, iQ = qs->invQ;
     const int qlim = qs->qlim;
@@ -185,13 +247,17 @@ __global__ void __launch_bounds__(NT, 1)
 
     // fixed per-thread work: gather slots, x-pass unit, moment point,
     // x-box-2 slots and output point
-    int g_gx[NGS], g_gy[NGS], g_sm[NGS];
+    int g_gx[NGS], g_gy[NGS], g_sm[NGS], g_o[NGS];
 #pragma unroll
     for (int k = 0; k < NGS; ++k) {
         int idx = tid + k * NT;
         g_gy[k] = idx / GX;
         g_gx[k] = idx - g_gy[k] * GX;
         g_sm[k] = idx < GX * GY ? g_gy[k] * GXP + g_gx[k] : -1;
+        int ox_ = g_gx[k] - 2 * W, oy_ = g_gy[k] - 2 * W;
+        g_o[k] = (g_sm[k] >= 0 && ox_ >= 0 && ox_ < TX && oy_ >= 0 && oy_ < TY)
+                     ? oy_ * TX + ox_
+                     : -1;
     }
     const bool has_xu = tid < C::NXU;
     const int xu_gy = tid / (SX / 2), xu_p = tid - xu_gy * (SX / 2);
@@ -205,7 +271,6 @@ __global__ void __launch_bounds__(NT, 1)
     }
     const bool has_o = tid < TX * TY;
     const int ox = has_o ? tid % TX : 0, oy = has_o ? tid / TX : 0;
-    const int o_gi = (oy + 2 * W) * GXP + ox + 2 * W;
 
     double lacc = 0.0;
     bool bad = false;
@@ -249,61 +314,68 @@ __global__ void __launch_bounds__(NT, 1)
         int runF = 0, runJ = 0;
         long long runFF = 0, runJJ = 0, runFJ = 0;
         float r2[3][K];
-        float dF[K], dJ[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            r2[0][k] = r2[1][k] = r2[2][k] = 0.f;
-            dF[k] = dJ[k] = 0.f;
-        }
+        for (int k = 0; k < K; ++k) r2[0][k] = r2[1][k] = r2[2][k] = 0.f;
         const int s_begin = z0 - 2 * W, s_end = z1 + 2 * W;
+        // the J' and F of slice s (and dJ/du of the output slice) are loaded
+        // one step ahead, so their latency hides behind the previous step
+        int jqk[NGS];
+        float fv[NGS];
+        auto load_plane = [&](int sp) {
+            const bool zin_ = sp >= 0 && sp < g.nz;
+#pragma unroll
+            for (int k = 0; k < NGS; ++k) {
+                const int i = (zin_ && g_off[k] >= 0) ? sp * sxy + g_off[k] : -1;
+                jqk[k] = i >= 0 ? __ldg(jqv + i) : qpad;
+                fv[k] = i >= 0 ? ld_img(F, i) : 0.f;
+            }
+        };
+        float odj[3] = {0.f, 0.f, 0.f};
+        auto load_dj = [&](int r) {
+            if (o_in && r >= z0 && r < z1) {
+                const int gi = r * sxy + o_off;
+                odj[0] = __ldg(djv + gi);
+                odj[1] = __ldg(djv + g.V + gi);
+                odj[2] = __ldg(djv + 2 * g.V + gi);
+            }
+        };
+        load_plane(s_begin);
+        load_dj(s_begin - 2 * W);
         for (int base = s_begin; base < s_end; base += K) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
                 const int s = base + j;
                 if (s >= s_end) break;
                 const int t = s - s_begin;
-                // (1) gather plane: quantised F', J'
-                const bool zin = s >= 0 && s < g.nz;
+                // (1) gather plane: quantised F' and the J' of the J pass
                 {
-                    float d[NGS][3], fv[NGS];
-                    int i[NGS];
-#pragma unroll
-                    for (int k = 0; k < NGS; ++k) {
-                        i[k] = (zin && g_off[k] >= 0) ? s * sxy + g_off[k] : -1;
-                        if (i[k] >= 0) {
-                            d[k][0] = __ldg(u + i[k]);
-                            d[k][1] = __ldg(u1 + i[k]);
-                            d[k][2] = __ldg(u2 + i[k]);
-                            fv[k] = ld_img(F, i[k]);
-                        }
-                    }
 #pragma unroll
                     for (int k = 0; k < NGS; ++k) {
                         if (g_sm[k] < 0) continue;
-                        int fq = qpad, jq = qpad;
-                        if (i[k] >= 0) {
-                            float m[8], f[3];
-                            corners(M, g, x0 - 2 * W + g_gx[k],
-                                    y0 - 2 * W + g_gy[k], s, d[k][0], d[k][1],
-                                    d[k][2], m, f);
-                            float jv = interp(m, f);
-                            bad |= !(fabsf(jv) <= 3.0e38f) ||
-                                   !(fabsf(fv[k]) <= 3.0e38f);
-                            fq = min(max(__float2int_rn((fv[k] - sh) * Q), -qlim),
-                                     qlim);
-                            jq = min(max(__float2int_rn((jv - sh) * Q), -qlim),
-                                     qlim);
+                        int fq = __float2int_rn((fv[k] - sh) * Q);
+                        if (!(fabsf(fv[k]) <= 3.0e38f)) bad = true;
+                        fq = min(max(fq, -qlim), qlim);
+                        int jq = jqk[k];
+                        if (jq == JQ_BAD) {
+                            bad = true;
+                            jq = qpad;
                         }
                         GqF[g_sm[k]] = fq;
                         GqJ[g_sm[k]] = jq;
+                        if (g_o[k] >= 0) {
+                            // output point: keep F', J' for 2W slices
+                            float* dl = DL + j * 2 * TY * TX + g_o[k];
+                            dl[0] = (float)fq * iQ;
+                            dl[TY * TX] = (float)jq * iQ;
+                        }
                     }
                 }
-                __syncthreads();
-                // delay line of F', J' for this thread's output point
-                if (has_o) {
-                    dF[j] = (float)GqF[o_gi] * iQ;
-                    dJ[j] = (float)GqJ[o_gi] * iQ;
+                const float dj0 = odj[0], dj1 = odj[1], dj2 = odj[2];
+                if (s + 1 < s_end) {
+                    load_plane(s + 1);
+                    load_dj(s + 1 - 2 * W);
                 }
+                __syncthreads();
                 // (2) window sums along x: two outputs per unit
                 if (has_xu) {
                     const int* rf = GqF + xu_gy * GXP + 2 * xu_p;
@@ -438,11 +510,16 @@ __global__ void __launch_bounds__(NT, 1)
                                     v += r2[q][(j + 1 + i2) % K];
                                 b3[q] = v;
                             }
-                            const int jd = (j + 1) % K;
-                            dldj[r * sxy + o_off] =
-                                -inv_V * ((dF[jd] * b3[0] +
-                                             2.f * dJ[jd] * b3[1] + b3[2]) *
-                                            c.inv_k3);
+                            // F', J' of slice r sit in slot (j+1) % K
+                            const float* dl = DL + ((j + 1) % K) * 2 * TY * TX + tid;
+                            const float dLdJ =
+                                -inv_V * ((dl[0] * b3[0] +
+                                           2.f * dl[TY * TX] * b3[1] + b3[2]) *
+                                          c.inv_k3);
+                            const int gi = r * sxy + o_off;
+                            graw[gi] = dLdJ * dj0;
+                            graw[g.V + gi] = dLdJ * dj1;
+                            graw[2 * g.V + gi] = dLdJ * dj2;
                         }
                     }
                 }
@@ -471,7 +548,9 @@ struct E2Cfg {
     static constexpr int RX = TX + 2 * R, RY = TY + 2 * R;
     static constexpr int RXP = (RX + 3) / 4 * 4;
     static constexpr int NXU = 3 * RY * (TX / 4);   // x-pass units (4 outputs)
-    static constexpr int bytes = (3 * RY * RXP + 3 * RY * TX) * 4;
+    // g_raw plane, x-smoothed plane, z ring of xy-smoothed planes
+    static constexpr int bytes =
+        (3 * RY * RXP + 3 * RY * TX + KG * 3 * TX * TY) * 4;
 };
 
 template <int R, typename T>
@@ -486,17 +565,14 @@ __global__ void __launch_bounds__(NT, 2)
     extern __shared__ __align__(16) unsigned char smem[];
     float* Gr = (float*)smem;            // [3][RY][RXP]
     float* Gx = Gr + 3 * RY * RXP;       // [3][RY][TX]
+    float* Zr = Gx + 3 * RY * TX;        // [KG][3][TY * TX], thread-private
     __shared__ float red[NT / 32];
 
     const PairDesc& P = pd[pair_of_block<2>(pd, npairs, blockIdx.x)];
     if (trial_skip(P, mode, attempt)) return;
     const Geom g = P.g;
-    const T* __restrict__ M = (const T*)P.M;
-    const float* __restrict__ dldj = P.dldj;
+    const float* __restrict__ graw = P.graw;
     const int tid = threadIdx.x;
-    const float* __restrict__ u = eval_u(P, mode);
-    const float* __restrict__ u1 = u + g.V;
-    const float* __restrict__ u2 = u + 2 * g.V;
     float* __restrict__ gout = eval_g(P, mode);
     const int sxy = g.nx * g.ny;
     const int ox = tid & (TX - 1), oy = tid / TX;
@@ -546,41 +622,39 @@ __global__ void __launch_bounds__(NT, 2)
         }
         const bool o_in = x0 + ox < g.nx && y0 + oy < g.ny;
         const int o_off = (y0 + oy) * g.nx + x0 + ox;
-        float ring[3][KG];
-#pragma unroll
-        for (int k = 0; k < KG; ++k) ring[0][k] = ring[1][k] = ring[2][k] = 0.f;
         const int s_begin = z0 - R, s_end = z1 + R;
+        // g_raw of slice s is loaded one step ahead
+        float pg[NRS][3];
+        auto load_plane = [&](int sp) {
+            const bool zin_ = sp >= 0 && sp < g.nz;
+#pragma unroll
+            for (int k = 0; k < NRS; ++k) {
+                const bool in = zin_ && r_off[k] >= 0;
+                const int i = in ? sp * sxy + r_off[k] : 0;
+                pg[k][0] = in ? __ldg(graw + i) : 0.f;
+                pg[k][1] = in ? __ldg(graw + g.V + i) : 0.f;
+                pg[k][2] = in ? __ldg(graw + 2 * g.V + i) : 0.f;
+            }
+        };
+        load_plane(s_begin);
         for (int base = s_begin; base < s_end; base += KG) {
 #pragma unroll
             for (int j = 0; j < KG; ++j) {
                 const int s = base + j;
                 if (s >= s_end) break;
                 const int t = s - s_begin;
-                // (1) g_raw on the tile and its R halo
-                const bool zin = s >= 0 && s < g.nz;
+                // (1) g_raw of the tile and its R halo (zero outside)
                 {
 #pragma unroll
                     for (int k = 0; k < NRS; ++k) {
                         if (r_sm[k] < 0) continue;
-                        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-                        if (zin && r_off[k] >= 0) {
-                            const int i = s * sxy + r_off[k];
-                            float m[8], f[3], dd[3];
-                            float dl = __ldg(dldj + i);
-                            corners(M, g, x0 - R + (r_xy[k] & 0xffff),
-                                    y0 - R + (r_xy[k] >> 16), s,
-                                    __ldg(u + i), __ldg(u1 + i), __ldg(u2 + i),
-                                    m, f);
-                            interp_grad(m, f, dd);
-                            g0 = dl * dd[0];
-                            g1 = dl * dd[1];
-                            g2 = dl * dd[2];
-                        }
+                        const float g0 = pg[k][0], g1 = pg[k][1], g2 = pg[k][2];
                         Gr[r_sm[k]] = g0;
                         Gr[RY * RXP + r_sm[k]] = g1;
                         Gr[2 * RY * RXP + r_sm[k]] = g2;
                     }
                 }
+                if (s + 1 < s_end) load_plane(s + 1);
                 __syncthreads();
                 // (2) Gaussian along x: four outputs per unit
 #pragma unroll
@@ -611,7 +685,7 @@ __global__ void __launch_bounds__(NT, 2)
 #pragma unroll
                     for (int k = 1; k <= R; ++k)
                         a += tt[R + k] * (col[(R - k) * TX] + col[(R + k) * TX]);
-                    ring[q][j] = a;
+                    Zr[(j * 3 + q) * TX * TY + tid] = a;
                 }
                 if (t >= 2 * R && o_in) {
                     const int i = (s - R) * sxy + o_off;
@@ -619,11 +693,14 @@ __global__ void __launch_bounds__(NT, 2)
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         // slice o - R + i2 sits in slot (j + 1 + i2) mod KG
-                        float a = tt[R] * ring[q][(j + 1 + R) % KG];
+                        const float* zq = Zr + q * TX * TY + tid;
+#define ZR_AT(slot) zq[(slot) * 3 * TX * TY]
+                        float a = tt[R] * ZR_AT((j + 1 + R) % KG);
 #pragma unroll
                         for (int k = 1; k <= R; ++k)
-                            a += tt[R + k] * (ring[q][(j + 1 + R - k) % KG] +
-                                              ring[q][(j + 1 + R + k) % KG]);
+                            a += tt[R + k] * (ZR_AT((j + 1 + R - k) % KG) +
+                                              ZR_AT((j + 1 + R + k) % KG));
+#undef ZR_AT
                         gout[q * g.V + i] = a;
                         n2 += a * a;
                     }
@@ -876,9 +953,15 @@ int batch_qscale(const Batch& b, cudaStream_t s) {
 int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s) {
     int n = 0;
     if (b.dtype == LM_BF16) {
+        k_jpass<__nv_bfloat16><<<b.plan.st_blocks, dim3(32, 8), 0, s>>>(
+            b.pd, b.npairs, mode, attempt);
+        n += 1;
         n += launch_e1_w<__nv_bfloat16>(b, mode, attempt, s);
         n += launch_e2_r<__nv_bfloat16>(b, mode, attempt, s);
     } else {
+        k_jpass<float><<<b.plan.st_blocks, dim3(32, 8), 0, s>>>(
+            b.pd, b.npairs, mode, attempt);
+        n += 1;
         n += launch_e1_w<float>(b, mode, attempt, s);
         n += launch_e2_r<float>(b, mode, attempt, s);
     }

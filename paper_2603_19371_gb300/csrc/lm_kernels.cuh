@@ -30,7 +30,9 @@ struct PairDesc {
     float* g1;
     const float* u_in;    // EVAL_EXPLICIT field
     float* g_out;         // EVAL_EXPLICIT gradient
-    float* dldj;          // dL/dJ between the two evaluation kernels
+    int* jq;              // J in the moments' fixed point (V), from the J pass
+    float* dj;            // dJ/du (3 x V), from the J pass
+    float* graw;          // g_raw (3 x V) between the two evaluation kernels
     QScale* qs;
     DevState* st;
     LogEntry* log;        // may be NULL

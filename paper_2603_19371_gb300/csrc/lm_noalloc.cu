@@ -5,7 +5,8 @@
 // real-time loops that forbid cudaMalloc/cudaFree (both synchronise the
 // device), or a process that has handed all free memory to another
 // component.  For them this entry point takes only the caller's inputs and
-// outputs and keeps its scratch (dL/dJ between the two evaluation kernels,
+// outputs and keeps its scratch (J, dJ/du and g_raw between the evaluation
+// kernels,
 // per-CTA partials, the fixed-point scale and the reduced result) in one
 // file-scope static device array, sized for volumes up to
 // LM_NOALLOC_MAX_VOXELS voxels.  Every GPU that loads the library holds that
@@ -19,16 +20,22 @@
 namespace {
 
 // Scratch layout (bytes, each section 256-byte aligned):
-//   dL/dJ               LM_NOALLOC_MAX_VOXELS floats
+//   g_raw               3 x LM_NOALLOC_MAX_VOXELS floats
+//   J (fixed point)     LM_NOALLOC_MAX_VOXELS int32
+//   dJ/du               3 x LM_NOALLOC_MAX_VOXELS floats
 //   loss partials       MAX_CTAS doubles
 //   |g|^2 partials      MAX_CTAS floats
 //   image range parts   MAX_CTAS float2
 //   QScale, EvalOut, the one-pair descriptor table
 constexpr size_t MAX_CTAS = 1024;
 constexpr size_t align256(size_t n) { return (n + 255) / 256 * 256; }
-constexpr size_t OFF_DLDJ = 0;
+constexpr size_t OFF_GRAW = 0;
+constexpr size_t OFF_JQ =
+    OFF_GRAW + align256(3 * (size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
+constexpr size_t OFF_DJ =
+    OFF_JQ + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(int));
 constexpr size_t OFF_LOSS =
-    OFF_DLDJ + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
+    OFF_DJ + align256(3 * (size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
 constexpr size_t OFF_G2 = OFF_LOSS + align256(MAX_CTAS * sizeof(double));
 constexpr size_t OFF_MM = OFF_G2 + align256(MAX_CTAS * sizeof(float));
 constexpr size_t OFF_QS = OFF_MM + align256(MAX_CTAS * sizeof(float2));
@@ -116,7 +123,7 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     const long long V = (long long)fixed->D * fixed->H * fixed->W;
     if (V > (long long)LM_NOALLOC_MAX_VOXELS)
         return fail(LM_EINVAL,
-                    "volume exceeds LM_NOALLOC_MAX_VOXELS (2^21 voxels) of the "
+                    "volume exceeds LM_NOALLOC_MAX_VOXELS (2^19 voxels) of the "
                     "static scratch");
     lm_params prm;
     if (p) {
@@ -150,7 +157,9 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     pd.M = moving->data;
     pd.u_in = u;
     pd.g_out = g_out;
-    pd.dldj = (float*)(base + OFF_DLDJ);
+    pd.graw = (float*)(base + OFF_GRAW);
+    pd.jq = (int*)(base + OFF_JQ);
+    pd.dj = (float*)(base + OFF_DJ);
     pd.qs = (lmk::QScale*)(base + OFF_QS);
     lmk::BatchPlan plan = lmk::plan_batch(&pd, 1, prm.win, sms);
     if ((size_t)plan.e1_ctas > MAX_CTAS || (size_t)plan.e2_ctas > MAX_CTAS ||

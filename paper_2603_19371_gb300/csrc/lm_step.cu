@@ -93,14 +93,38 @@ __global__ void __launch_bounds__(ST_X * ST_Y)
     };
     load_plane(z0 - 1, (z0 + 2) % 3);
     load_plane(z0, z0 % 3);
+    load_plane(z0 + 1, (z0 + 1) % 3);
+    const bool in_xy = x < g.nx && y < g.ny;
+    // the gradient of voxel z is loaded one step ahead
+    float ng0 = 0.f, ng1 = 0.f, ng2 = 0.f;
+    if (in_xy && z0 < z1) {
+        const int i0 = z0 * sxy + y * g.nx + x;
+        ng0 = __ldg(gg + i0);
+        ng1 = __ldg(gg + g.V + i0);
+        ng2 = __ldg(gg + 2 * g.V + i0);
+    }
+    __syncthreads();
     for (int z = z0; z < z1; ++z) {
-        load_plane(z + 1, (z + 1) % 3);
-        __syncthreads();
-        if (x < g.nx && y < g.ny) {
+        // plane z + 2 streams into registers while voxel z is computed
+        float pre[NLD];
+        {
+            const int zo = min(max(z + 2, 0), g.nz - 1) * sxy;
+#pragma unroll
+            for (int k = 0; k < NLD; ++k)
+                pre[k] = ld_dst[k] >= 0 ? __ldg(ld_src[k] + zo) : 0.f;
+        }
+        const float cg0 = ng0, cg1 = ng1, cg2 = ng2;
+        if (in_xy && z + 1 < z1) {
+            const int i1 = (z + 1) * sxy + y * g.nx + x;
+            ng0 = __ldg(gg + i1);
+            ng1 = __ldg(gg + g.V + i1);
+            ng2 = __ldg(gg + 2 * g.V + i1);
+        }
+        if (in_xy) {
             const int i = z * sxy + y * g.nx + x;
-            float gh0 = __ldg(gg + i) * inv;
-            float gh1 = __ldg(gg + g.V + i) * inv;
-            float gh2 = __ldg(gg + 2 * g.V + i) * inv;
+            float gh0 = cg0 * inv;
+            float gh1 = cg1 * inv;
+            float gh2 = cg2 * inv;
             float n2 = gh0 * gh0 + gh1 * gh1 + gh2 * gh2;
             float sc = scale / (n2 + lam);
             float v[3] = {gh0 * sc, gh1 * sc, gh2 * sc};
@@ -160,6 +184,13 @@ __global__ void __launch_bounds__(ST_X * ST_Y)
                                   wy1 * (wx0 * m[q][6] + wx1 * m[q][7]));
                 out[q * g.V + i] = v[q] + sv;
             }
+        }
+        __syncthreads();   // slot of plane z - 1 is free
+        {
+            float* dst = &ring[(z + 2) % 3][0][0];
+#pragma unroll
+            for (int k = 0; k < NLD; ++k)
+                if (ld_dst[k] >= 0) dst[ld_dst[k]] = pre[k];
         }
         __syncthreads();
     }

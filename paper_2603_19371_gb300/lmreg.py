@@ -17,7 +17,7 @@ LM_OK, LM_EINVAL, LM_ENOMEM, LM_ECUDA = 0, -1, -2, -3
 LM_ENONFINITE, LM_ETIMEOUT, LM_EUNSUPPORTED, LM_ESTATE = -4, -5, -6, -7
 LM_F32, LM_BF16 = 0, 1
 LM_MAX_LEVELS = 4
-LM_NOALLOC_MAX_VOXELS = 1 << 21
+LM_NOALLOC_MAX_VOXELS = 1 << 19
 
 
 class LMError(RuntimeError):
