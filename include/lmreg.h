@@ -251,7 +251,7 @@ LM_API int lm_register_batch(int npairs, const lm_volume *fixed,
  * Same result as lm_eval on a fresh context: the loss r = 1 - LNCC and its
  * smoothed gradient at u, without a context and without any allocation.
  * Its scratch is one static device array inside the library, sized for at
- * most LM_NOALLOC_MAX_VOXELS voxels (2^19, e.g. 80^3; about 14.7 MB, held
+ * most LM_NOALLOC_MAX_VOXELS voxels (2^19, e.g. 80^3; about 21 MB, held
  * by every GPU that loads the library until the process exits); larger
  * volumes return LM_EINVAL.
  *   fixed, moving: images as for lm_init; p: parameters (NULL = defaults;

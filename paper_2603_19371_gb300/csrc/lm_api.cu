@@ -316,7 +316,10 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
             (rc = c->dalloc(&d.g1, 3 * V * f4)) ||
             (rc = c->dalloc(&d.graw, 3 * V * f4)) ||
             (rc = c->dalloc(&d.jq, V * sizeof(int))) ||
-            (rc = c->dalloc(&d.dj, 3 * V * f4)))
+            (rc = c->dalloc(&d.dj, 3 * V * f4)) ||
+            (rc = c->dalloc(&d.fq, V * sizeof(int))) ||
+            (rc = c->dalloc(&d.fsum, V * sizeof(int))) ||
+            (rc = c->dalloc(&d.fvar, V * f4)))
             return rc;
         if (smooth && ((rc = c->dalloc(&d.wtmpA, 3 * V * f4)) ||
                        (rc = c->dalloc(&d.wtmpB, 3 * V * f4))))
@@ -382,7 +385,7 @@ int core_eval(Core* c, const float* const* u, float* const* g_out,
     }
     rc = c->push_table();
     if (rc != LM_OK) return rc;
-    batch_qscale(c->b, c->stream);
+    batch_prepare(c->b, c->stream);
     batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);
     batch_finalize(c->b, FIN_EXPLICIT, 0, c->eout, c->stream);
     LM_CK(cudaGetLastError());
@@ -408,7 +411,7 @@ int core_reset(Core* c, float* const* u) {
     for (int i = 0; i < c->npairs; ++i) c->hpd[i].u0 = u[i];
     int rc = c->push_table();
     if (rc != LM_OK) return rc;
-    c->launches = batch_qscale(c->b, c->stream);
+    c->launches = batch_prepare(c->b, c->stream);
     c->launches += batch_eval(c->b, EVAL_RESET, 0, c->stream);
     c->launches += batch_finalize(c->b, FIN_RESET, 0, nullptr, c->stream);
     LM_CK(cudaGetLastError());

@@ -22,9 +22,13 @@
 // variance cancellation that FP32 window sums suffer in flat regions is
 // gone.  Everything after the moments is FP32.
 //
+// The fixed image's share of the moments (F' in fixed point, its exact
+// window sum and its window variance) does not change during a
+// registration; the preparation kernels compute it once per reset.
+//
 // HBM traffic per voxel: the J pass reads u, M (16 B) and writes Jq, dJ
-// (16 B); E1 reads F, Jq, dJ (20 B) and writes g_raw (12 B); E2 reads g_raw
-// (12 B) and writes g (12 B).  Halo re-reads hit L2.
+// (16 B); E1 reads F', S_F, B, Jq, dJ (28 B) and writes g_raw (12 B); E2
+// reads g_raw (12 B) and writes g (12 B).  Halo re-reads hit L2.
 #include <algorithm>
 #include <vector>
 
@@ -122,6 +126,7 @@ __device__ __forceinline__ Share share_of(int b, int n, long long total) {
 // tile, marching over the tile's z range (the step kernel's tiling).
 // ----------------------------------------------------------------------
 constexpr int JQ_BAD = (int)0x80000000;
+constexpr int FQ_BAD = JQ_BAD;   // same sentinel for a non-finite F
 
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -186,11 +191,11 @@ struct E1Cfg {
     static constexpr int NXU = GY * (SX / 2);   // x-pass units (2 outputs)
     static constexpr int NX2U = 3 * SY * (TX / 2);
     // shared memory (bytes), 16-byte aligned sections
-    static constexpr int B_GQ = 2 * GY * GXP * 4;
-    static constexpr int B_X32 = 2 * GY * SX * 4;
-    static constexpr int B_X64 = 3 * GY * SX * 8;
-    static constexpr int B_ZR32 = K * 2 * NT * 4;
-    static constexpr int B_ZR64 = K * 3 * NT * 8;
+    static constexpr int B_GQ = 2 * GY * GXP * 4;     // F', J' gather plane
+    static constexpr int B_X32 = GY * SX * 4;         // x-sums of J'
+    static constexpr int B_X64 = 2 * GY * SX * 8;     // of J'J', F'J'
+    static constexpr int B_ZR32 = K * NT * 4;         // z ring of y-sums
+    static constexpr int B_ZR64 = K * 2 * NT * 8;
     static constexpr int B_AB = 3 * SY * SX * 4;
     static constexpr int B_AX = 3 * SY * TX * 4;
     // delay ring at the output points: F', J' of the last K slices
@@ -199,7 +204,7 @@ struct E1Cfg {
         B_GQ + B_X32 + B_X64 + B_ZR32 + B_ZR64 + B_AB + B_AX + B_DL;
 };
 
-template <int W, typename T>
+template <int W>
 __global__ void __launch_bounds__(NT, 1)
     k_e1(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
          LnccConsts c, double* __restrict__ loss_part) {
@@ -212,10 +217,8 @@ __global__ void __launch_bounds__(NT, 1)
     extern __shared__ __align__(16) unsigned char smem[];
     int* GqF = (int*)smem;
     int* GqJ = GqF + GY * GXP;
-    int* XF = (int*)(smem + C::B_GQ);
-    int* XJ = XF + GY * SX;
-    long long* XFF = (long long*)(smem + C::B_GQ + C::B_X32);
-    long long* XJJ = XFF + GY * SX;
+    int* XJ = (int*)(smem + C::B_GQ);
+    long long* XJJ = (long long*)(smem + C::B_GQ + C::B_X32);
     long long* XFJ = XJJ + GY * SX;
     int* ZR32 = (int*)(smem + C::B_GQ + C::B_X32 + C::B_X64);
     long long* ZR64 =
@@ -229,7 +232,9 @@ __global__ void __launch_bounds__(NT, 1)
     const PairDesc& P = pd[pair_of_block<1>(pd, npairs, blockIdx.x)];
     if (trial_skip(P, mode, attempt)) return;
     const Geom g = P.g;
-    const T* __restrict__ F = (const T*)P.F;
+    const int* __restrict__ fqv = P.fq;
+    const int* __restrict__ fsv = P.fsum;
+    const float* __restrict__ fbv = P.fvar;
     const int* __restrict__ jqv = P.jq;
     const float* __restrict__ djv = P.dj;
     float* __restrict__ graw = P.graw;
@@ -238,7 +243,6 @@ __global__ void __launch_bounds__(NT, 1)
     const int tid = threadIdx.x;
     const int sxy = g.nx * g.ny;
     const float sh = qs->shift, Q = qs->Q, iQ = qs->invQ;
-    const int qlim = qs->qlim;
     const int qpad = __float2int_rn(-sh * Q);
     const long long k3 = (long long)K * K * K;
     // exact moment differences are k^6 Q^2 times the moments
@@ -247,14 +251,16 @@ __global__ void __launch_bounds__(NT, 1)
 
     // fixed per-thread work: gather slots, x-pass unit, moment point,
     // x-box-2 slots and output point
-    int g_gx[NGS], g_gy[NGS], g_sm[NGS], g_o[NGS];
+    // gather slot: plane point (gx | gy << 16), its smem index, its output
+    // point (-1: none)
+    int g_xy[NGS], g_sm[NGS], g_o[NGS];
 #pragma unroll
     for (int k = 0; k < NGS; ++k) {
         int idx = tid + k * NT;
-        g_gy[k] = idx / GX;
-        g_gx[k] = idx - g_gy[k] * GX;
-        g_sm[k] = idx < GX * GY ? g_gy[k] * GXP + g_gx[k] : -1;
-        int ox_ = g_gx[k] - 2 * W, oy_ = g_gy[k] - 2 * W;
+        int gy = idx / GX, gx = idx - gy * GX;
+        g_xy[k] = gx | (gy << 16);
+        g_sm[k] = idx < GX * GY ? gy * GXP + gx : -1;
+        int ox_ = gx - 2 * W, oy_ = gy - 2 * W;
         g_o[k] = (g_sm[k] >= 0 && ox_ >= 0 && ox_ < TX && oy_ >= 0 && oy_ < TY)
                      ? oy_ * TX + ox_
                      : -1;
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(NT, 1)
         int g_off[NGS];
 #pragma unroll
         for (int k = 0; k < NGS; ++k) {
-            int x = x0 - 2 * W + g_gx[k], y = y0 - 2 * W + g_gy[k];
+            int x = x0 - 2 * W + (g_xy[k] & 0xffff), y = y0 - 2 * W + (g_xy[k] >> 16);
             g_off[k] = (g_sm[k] >= 0 && x >= 0 && x < g.nx && y >= 0 &&
                         y < g.ny)
                            ? y * g.nx + x
@@ -299,35 +305,42 @@ __global__ void __launch_bounds__(NT, 1)
         const bool s_in = x0 - W + sx < g.nx && y0 - W + sy < g.ny &&
                           x0 - W + sx >= 0 && y0 - W + sy >= 0;
         const bool s_out = sx >= W && sx < W + TX && sy >= W && sy < W + TY;
+        const int s_off = (y0 - W + sy) * g.nx + x0 - W + sx;
         const bool o_in = has_o && x0 + ox < g.nx && y0 + oy < g.ny;
         const int o_off = (y0 + oy) * g.nx + x0 + ox;
 
         // ring and running sums restart for every segment
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            ZR32[(k * 2 + 0) * NT + tid] = 0;
-            ZR32[(k * 2 + 1) * NT + tid] = 0;
-            ZR64[(k * 3 + 0) * NT + tid] = 0;
-            ZR64[(k * 3 + 1) * NT + tid] = 0;
-            ZR64[(k * 3 + 2) * NT + tid] = 0;
+            ZR32[k * NT + tid] = 0;
+            ZR64[(k * 2 + 0) * NT + tid] = 0;
+            ZR64[(k * 2 + 1) * NT + tid] = 0;
         }
-        int runF = 0, runJ = 0;
-        long long runFF = 0, runJJ = 0, runFJ = 0;
+        int runJ = 0;
+        long long runJJ = 0, runFJ = 0;
         float r2[3][K];
 #pragma unroll
         for (int k = 0; k < K; ++k) r2[0][k] = r2[1][k] = r2[2][k] = 0.f;
         const int s_begin = z0 - 2 * W, s_end = z1 + 2 * W;
-        // the J' and F of slice s (and dJ/du of the output slice) are loaded
-        // one step ahead, so their latency hides behind the previous step
-        int jqk[NGS];
-        float fv[NGS];
+        // the F', J' of slice s, the F moments of the moment slice and dJ/du
+        // of the output slice are loaded one step ahead, so their latency
+        // hides behind the previous step
+        int jqk[NGS], fqk[NGS];
         auto load_plane = [&](int sp) {
             const bool zin_ = sp >= 0 && sp < g.nz;
 #pragma unroll
             for (int k = 0; k < NGS; ++k) {
                 const int i = (zin_ && g_off[k] >= 0) ? sp * sxy + g_off[k] : -1;
                 jqk[k] = i >= 0 ? __ldg(jqv + i) : qpad;
-                fv[k] = i >= 0 ? ld_img(F, i) : 0.f;
+                fqk[k] = i >= 0 ? __ldg(fqv + i) : qpad;
+            }
+        };
+        int mSF = 0;
+        float mB = 0.f;
+        auto load_mom = [&](int cz_) {
+            if (s_in && cz_ >= 0 && cz_ < g.nz) {
+                mSF = __ldg(fsv + cz_ * sxy + s_off);
+                mB = __ldg(fbv + cz_ * sxy + s_off);
             }
         };
         float odj[3] = {0.f, 0.f, 0.f};
@@ -340,6 +353,7 @@ __global__ void __launch_bounds__(NT, 1)
             }
         };
         load_plane(s_begin);
+        load_mom(s_begin - W);
         load_dj(s_begin - 2 * W);
         for (int base = s_begin; base < s_end; base += K) {
 #pragma unroll
@@ -347,15 +361,16 @@ __global__ void __launch_bounds__(NT, 1)
                 const int s = base + j;
                 if (s >= s_end) break;
                 const int t = s - s_begin;
-                // (1) gather plane: quantised F' and the J' of the J pass
+                // (1) gather plane: F' and J' in fixed point
                 {
 #pragma unroll
                     for (int k = 0; k < NGS; ++k) {
                         if (g_sm[k] < 0) continue;
-                        int fq = __float2int_rn((fv[k] - sh) * Q);
-                        if (!(fabsf(fv[k]) <= 3.0e38f)) bad = true;
-                        fq = min(max(fq, -qlim), qlim);
-                        int jq = jqk[k];
+                        int fq = fqk[k], jq = jqk[k];
+                        if (fq == FQ_BAD) {
+                            bad = true;
+                            fq = qpad;
+                        }
                         if (jq == JQ_BAD) {
                             bad = true;
                             jq = qpad;
@@ -371,8 +386,11 @@ __global__ void __launch_bounds__(NT, 1)
                     }
                 }
                 const float dj0 = odj[0], dj1 = odj[1], dj2 = odj[2];
+                const int cSF = mSF;
+                const float cB = mB;
                 if (s + 1 < s_end) {
                     load_plane(s + 1);
+                    load_mom(s + 1 - W);
                     load_dj(s + 1 - 2 * W);
                 }
                 __syncthreads();
@@ -386,30 +404,22 @@ __global__ void __launch_bounds__(NT, 1)
                         vf[o] = rf[o];
                         vj[o] = rj[o];
                     }
-                    int sf = 0, sj = 0;
-                    long long sff = 0, sjj = 0, sfj = 0;
+                    int sj = 0;
+                    long long sjj = 0, sfj = 0;
 #pragma unroll
                     for (int o = 0; o < K; ++o) {
-                        sf += vf[o];
                         sj += vj[o];
-                        sff += (long long)vf[o] * vf[o];
                         sjj += (long long)vj[o] * vj[o];
                         sfj += (long long)vf[o] * vj[o];
                     }
                     int o1 = xu_gy * SX + 2 * xu_p;
-                    XF[o1] = sf;
                     XJ[o1] = sj;
-                    XFF[o1] = sff;
                     XJJ[o1] = sjj;
                     XFJ[o1] = sfj;
-                    sf += vf[K] - vf[0];
                     sj += vj[K] - vj[0];
-                    sff += (long long)vf[K] * vf[K] - (long long)vf[0] * vf[0];
                     sjj += (long long)vj[K] * vj[K] - (long long)vj[0] * vj[0];
                     sfj += (long long)vf[K] * vj[K] - (long long)vf[0] * vj[0];
-                    XF[o1 + 1] = sf;
                     XJ[o1 + 1] = sj;
-                    XFF[o1 + 1] = sff;
                     XJJ[o1 + 1] = sjj;
                     XFJ[o1 + 1] = sfj;
                 }
@@ -417,42 +427,35 @@ __global__ void __launch_bounds__(NT, 1)
                 // (3) along y, then the z running sums (exact) and, once K
                 //     slices are in, the moments at slice cz = s - W
                 {
-                    int yf = 0, yj = 0;
-                    long long yff = 0, yjj = 0, yfj = 0;
+                    int yj = 0;
+                    long long yjj = 0, yfj = 0;
 #pragma unroll
                     for (int o = 0; o < K; ++o) {
                         int a = (sy + o) * SX + sx;
-                        yf += XF[a];
                         yj += XJ[a];
-                        yff += XFF[a];
                         yjj += XJJ[a];
                         yfj += XFJ[a];
                     }
-                    int* zr = ZR32 + j * 2 * NT + tid;
-                    long long* zr64 = ZR64 + j * 3 * NT + tid;
-                    runF += yf - zr[0];
-                    runJ += yj - zr[NT];
-                    runFF += yff - zr64[0];
-                    runJJ += yjj - zr64[NT];
-                    runFJ += yfj - zr64[2 * NT];
-                    zr[0] = yf;
-                    zr[NT] = yj;
-                    zr64[0] = yff;
-                    zr64[NT] = yjj;
-                    zr64[2 * NT] = yfj;
+                    int* zr = ZR32 + j * NT + tid;
+                    long long* zr64 = ZR64 + j * 2 * NT + tid;
+                    runJ += yj - zr[0];
+                    runJJ += yjj - zr64[0];
+                    runFJ += yfj - zr64[NT];
+                    zr[0] = yj;
+                    zr64[0] = yjj;
+                    zr64[NT] = yfj;
                 }
                 const int cz = s - W;
                 const bool coef_valid = t >= 2 * W;
                 if (coef_valid) {
                     float av = 0.f, bv = 0.f, cv = 0.f;
                     if (s_in && cz >= 0 && cz < g.nz) {
-                        long long Ai = k3 * runFJ - (long long)runF * runJ;
-                        long long Bi = k3 * runFF - (long long)runF * runF;
+                        long long Ai = k3 * runFJ - (long long)cSF * runJ;
                         long long Ci = k3 * runJJ - (long long)runJ * runJ;
                         float A = (float)Ai * mscale;
-                        float B = (float)Bi * mscale;
+                        float B = cB;
                         float Cm = (float)Ci * mscale;
-                        float mF = (float)runF * m1scale;
+                        float mF = (float)cSF * m1scale;
                         float mJ = (float)runJ * m1scale;
                         float BC = __fmul_rn(B, Cm), AA = __fmul_rn(A, A);
                         float N = AA + c.eps_nr;
@@ -781,9 +784,102 @@ __global__ void k_qscale(const PairDesc* __restrict__ pd,
     qs->qlim = (int)lim;
 }
 
-template <int W, typename T>
+// ----------------------------------------------------------------------
+// Fixed-image moments.  F does not change during a registration, so its
+// share of the window moments is computed once per preparation: F' = F - s
+// in the fixed point (FQ_BAD marks a non-finite F), and at every voxel the
+// exact k^3 window sum S_F of those values and the variance
+// B = (k^3 S_FF - S_F^2) / (k^6 Q^2), rounded once to FP32 exactly as the
+// moment stage would round it.  Zero padding: points outside the volume
+// hold the fixed point of 0.  Three separable passes (x, y, z) through
+// int32 / int64 temporaries laid out in a 12-byte-per-voxel scratch.
+// ----------------------------------------------------------------------
+struct MomTmp {
+    long long* ss;   // V sums of squares
+    int* s;          // V sums
+};
+__device__ __forceinline__ MomTmp mom_tmp(float* base, long long V) {
+    MomTmp t;
+    t.ss = (long long*)base;
+    t.s = (int*)((char*)base + 8 * V);
+    return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_fmom_x(const PairDesc* __restrict__ pd, int npairs, int W) {
+    const PairDesc& P = pd[pair_of_block<4>(pd, npairs, blockIdx.x)];
+    const Geom g = P.g;
+    const int i = (blockIdx.x - P.ln_blk0) * 256 + threadIdx.x;
+    if (i >= g.V) return;
+    const int x = i % g.nx;
+    const T* __restrict__ F = (const T*)P.F;
+    const float sh = P.qs->shift, Q = P.qs->Q;
+    const int qlim = P.qs->qlim;
+    const int qpad = __float2int_rn(-sh * Q);
+    int s = 0;
+    long long ss = 0;
+    for (int d = -W; d <= W; ++d) {
+        int q = qpad;
+        if (x + d >= 0 && x + d < g.nx) {
+            const float f = ld_img(F, i + d);
+            const bool fin = fabsf(f) <= 3.0e38f;
+            if (fin) q = min(max(__float2int_rn((f - sh) * Q), -qlim), qlim);
+            if (d == 0) P.fq[i] = fin ? q : FQ_BAD;
+        }
+        s += q;
+        ss += (long long)q * q;
+    }
+    MomTmp t = mom_tmp(P.graw, g.V);
+    t.s[i] = s;
+    t.ss[i] = ss;
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(256)
+    k_fmom_yz(const PairDesc* __restrict__ pd, int npairs, int W,
+              float inv_k3) {
+    const PairDesc& P = pd[pair_of_block<4>(pd, npairs, blockIdx.x)];
+    const Geom g = P.g;
+    const int i = (blockIdx.x - P.ln_blk0) * 256 + threadIdx.x;
+    if (i >= g.V) return;
+    const int K = 2 * W + 1;
+    const int sxy = g.nx * g.ny;
+    const int c = AXIS == 1 ? (i / g.nx) % g.ny : i / sxy;
+    const int n = AXIS == 1 ? g.ny : g.nz;
+    const int stride = AXIS == 1 ? g.nx : sxy;
+    const float sh = P.qs->shift, Q = P.qs->Q;
+    const long long qpad = __float2int_rn(-sh * Q);
+    // a line of the previous passes that lies outside the volume is padding
+    const long long pad_n = AXIS == 1 ? K : (long long)K * K;
+    const MomTmp a = mom_tmp(AXIS == 1 ? P.graw : P.dj, g.V);
+    int s = 0;
+    long long ss = 0;
+    for (int d = -W; d <= W; ++d) {
+        if (c + d >= 0 && c + d < n) {
+            s += a.s[i + d * stride];
+            ss += a.ss[i + d * stride];
+        } else {
+            s += (int)(pad_n * qpad);
+            ss += pad_n * qpad * qpad;
+        }
+    }
+    if (AXIS == 1) {
+        MomTmp t = mom_tmp(P.dj, g.V);
+        t.s[i] = s;
+        t.ss[i] = ss;
+    } else {
+        const long long k3 = (long long)K * K * K;
+        const float iQ = P.qs->invQ;
+        const float mscale = inv_k3 * inv_k3 * iQ * iQ;
+        P.fsum[i] = s;
+        P.fvar[i] = (float)(k3 * ss - (long long)s * s) * mscale;
+    }
+}
+
+template <int W>
 int launch_e1(const Batch& b, int mode, int attempt, cudaStream_t s) {
-    k_e1<W, T><<<b.plan.e1_ctas, NT, E1Cfg<W>::bytes, s>>>(
+    k_e1<W><<<b.plan.e1_ctas, NT, E1Cfg<W>::bytes, s>>>(
         b.pd, b.npairs, mode, attempt, b.c, b.part.loss);
     return 1;
 }
@@ -795,13 +891,12 @@ int launch_e2(const Batch& b, int mode, int attempt, cudaStream_t s) {
     return 1;
 }
 
-template <typename T>
 int launch_e1_w(const Batch& b, int mode, int attempt, cudaStream_t s) {
     switch ((b.c.win - 1) / 2) {
-        case 1: return launch_e1<1, T>(b, mode, attempt, s);
-        case 2: return launch_e1<2, T>(b, mode, attempt, s);
-        case 3: return launch_e1<3, T>(b, mode, attempt, s);
-        default: return launch_e1<4, T>(b, mode, attempt, s);
+        case 1: return launch_e1<1>(b, mode, attempt, s);
+        case 2: return launch_e1<2>(b, mode, attempt, s);
+        case 3: return launch_e1<3>(b, mode, attempt, s);
+        default: return launch_e1<4>(b, mode, attempt, s);
     }
 }
 
@@ -818,9 +913,9 @@ int launch_e2_r(const Batch& b, int mode, int attempt, cudaStream_t s) {
     }
 }
 
-template <int W, typename T>
+template <int W>
 cudaError_t attr_e1() {
-    return cudaFuncSetAttribute(k_e1<W, T>,
+    return cudaFuncSetAttribute(k_e1<W>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 E1Cfg<W>::bytes);
 }
@@ -834,10 +929,10 @@ cudaError_t attr_e2() {
 template <typename T>
 cudaError_t attrs_all() {
     cudaError_t e = cudaSuccess, r;
-    if ((r = attr_e1<1, T>()) != cudaSuccess) e = r;
-    if ((r = attr_e1<2, T>()) != cudaSuccess) e = r;
-    if ((r = attr_e1<3, T>()) != cudaSuccess) e = r;
-    if ((r = attr_e1<4, T>()) != cudaSuccess) e = r;
+    if ((r = attr_e1<1>()) != cudaSuccess) e = r;
+    if ((r = attr_e1<2>()) != cudaSuccess) e = r;
+    if ((r = attr_e1<3>()) != cudaSuccess) e = r;
+    if ((r = attr_e1<4>()) != cudaSuccess) e = r;
     if ((r = attr_e2<0, T>()) != cudaSuccess) e = r;
     if ((r = attr_e2<1, T>()) != cudaSuccess) e = r;
     if ((r = attr_e2<2, T>()) != cudaSuccess) e = r;
@@ -939,15 +1034,22 @@ cudaError_t fused_setup() {
     return e != cudaSuccess ? e : e2;
 }
 
-int batch_qscale(const Batch& b, cudaStream_t s) {
+int batch_prepare(const Batch& b, cudaStream_t s) {
     dim3 grid(b.plan.mm_ctas, b.npairs);
+    const int W = (b.c.win - 1) / 2;
     if (b.dtype == LM_BF16)
         k_minmax<__nv_bfloat16><<<grid, NT, 0, s>>>(b.pd, b.mm_part);
     else
         k_minmax<float><<<grid, NT, 0, s>>>(b.pd, b.mm_part);
     k_qscale<<<b.npairs, 32, 0, s>>>(b.pd, b.mm_part, b.plan.mm_ctas,
                                      quant_bits(b.c.win));
-    return 2;
+    if (b.dtype == LM_BF16)
+        k_fmom_x<__nv_bfloat16><<<b.plan.ln_blocks, 256, 0, s>>>(b.pd, b.npairs, W);
+    else
+        k_fmom_x<float><<<b.plan.ln_blocks, 256, 0, s>>>(b.pd, b.npairs, W);
+    k_fmom_yz<1><<<b.plan.ln_blocks, 256, 0, s>>>(b.pd, b.npairs, W, b.c.inv_k3);
+    k_fmom_yz<2><<<b.plan.ln_blocks, 256, 0, s>>>(b.pd, b.npairs, W, b.c.inv_k3);
+    return 5;
 }
 
 int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s) {
@@ -956,13 +1058,13 @@ int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s) {
         k_jpass<__nv_bfloat16><<<b.plan.st_blocks, dim3(32, 8), 0, s>>>(
             b.pd, b.npairs, mode, attempt);
         n += 1;
-        n += launch_e1_w<__nv_bfloat16>(b, mode, attempt, s);
+        n += launch_e1_w(b, mode, attempt, s);
         n += launch_e2_r<__nv_bfloat16>(b, mode, attempt, s);
     } else {
         k_jpass<float><<<b.plan.st_blocks, dim3(32, 8), 0, s>>>(
             b.pd, b.npairs, mode, attempt);
         n += 1;
-        n += launch_e1_w<float>(b, mode, attempt, s);
+        n += launch_e1_w(b, mode, attempt, s);
         n += launch_e2_r<float>(b, mode, attempt, s);
     }
     return n;

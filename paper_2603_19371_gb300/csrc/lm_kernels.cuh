@@ -31,6 +31,9 @@ struct PairDesc {
     const float* u_in;    // EVAL_EXPLICIT field
     float* g_out;         // EVAL_EXPLICIT gradient
     int* jq;              // J in the moments' fixed point (V), from the J pass
+    int* fq;              // F in the moments' fixed point (V), per preparation
+    int* fsum;            // exact k^3 window sum of fq (V), per preparation
+    float* fvar;          // k^3-window variance B of F (V), per preparation
     float* dj;            // dJ/du (3 x V), from the J pass
     float* graw;          // g_raw (3 x V) between the two evaluation kernels
     QScale* qs;
@@ -119,8 +122,11 @@ cudaError_t fused_setup();
 int quant_bits(int win);
 
 // Launch helpers; each returns the number of kernels it enqueued.
-// Image range -> QScale per pair (device-side, no host round trip).
-int batch_qscale(const Batch& b, cudaStream_t s);
+// Preparation of the fixed image, once per reset or explicit evaluation:
+// image range -> QScale per pair, then F in fixed point and its exact
+// window sum and variance (device-side, no host round trip).  The J-pass
+// scratch (graw, dj) serves as the separable passes' temporaries.
+int batch_prepare(const Batch& b, cudaStream_t s);
 // Pass 1: loss partials, dL/dJ, smoothed gradient, |g|^2 partials.
 int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s);
 // Pass 2: trial field (Eq. tile1 + Eq. compositive, optional smoothing).

@@ -6,7 +6,7 @@
 // device), or a process that has handed all free memory to another
 // component.  For them this entry point takes only the caller's inputs and
 // outputs and keeps its scratch (J, dJ/du and g_raw between the evaluation
-// kernels,
+// kernels, the fixed image's fixed point, window sum and variance,
 // per-CTA partials, the fixed-point scale and the reduced result) in one
 // file-scope static device array, sized for volumes up to
 // LM_NOALLOC_MAX_VOXELS voxels.  Every GPU that loads the library holds that
@@ -23,6 +23,7 @@ namespace {
 //   g_raw               3 x LM_NOALLOC_MAX_VOXELS floats
 //   J (fixed point)     LM_NOALLOC_MAX_VOXELS int32
 //   dJ/du               3 x LM_NOALLOC_MAX_VOXELS floats
+//   F fixed point, window sum (int32), variance (float): LM_NOALLOC_MAX_VOXELS each
 //   loss partials       MAX_CTAS doubles
 //   |g|^2 partials      MAX_CTAS floats
 //   image range parts   MAX_CTAS float2
@@ -34,8 +35,14 @@ constexpr size_t OFF_JQ =
     OFF_GRAW + align256(3 * (size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
 constexpr size_t OFF_DJ =
     OFF_JQ + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(int));
-constexpr size_t OFF_LOSS =
+constexpr size_t OFF_FQ =
     OFF_DJ + align256(3 * (size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
+constexpr size_t OFF_FSUM =
+    OFF_FQ + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(int));
+constexpr size_t OFF_FVAR =
+    OFF_FSUM + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(int));
+constexpr size_t OFF_LOSS =
+    OFF_FVAR + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
 constexpr size_t OFF_G2 = OFF_LOSS + align256(MAX_CTAS * sizeof(double));
 constexpr size_t OFF_MM = OFF_G2 + align256(MAX_CTAS * sizeof(float));
 constexpr size_t OFF_QS = OFF_MM + align256(MAX_CTAS * sizeof(float2));
@@ -160,6 +167,9 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     pd.graw = (float*)(base + OFF_GRAW);
     pd.jq = (int*)(base + OFF_JQ);
     pd.dj = (float*)(base + OFF_DJ);
+    pd.fq = (int*)(base + OFF_FQ);
+    pd.fsum = (int*)(base + OFF_FSUM);
+    pd.fvar = (float*)(base + OFF_FVAR);
     pd.qs = (lmk::QScale*)(base + OFF_QS);
     lmk::BatchPlan plan = lmk::plan_batch(&pd, 1, prm.win, sms);
     if ((size_t)plan.e1_ctas > MAX_CTAS || (size_t)plan.e2_ctas > MAX_CTAS ||
@@ -198,7 +208,7 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     b.mm_part = (float2*)(base + OFF_MM);
 
     k_noalloc_table<<<1, 32, 0, s>>>(dpd, pd);
-    lmk::batch_qscale(b, s);
+    lmk::batch_prepare(b, s);
     lmk::batch_eval(b, lmk::EVAL_EXPLICIT, 0, s);
     lmk::batch_finalize(b, lmk::FIN_EXPLICIT, 0, out, s);
     k_noalloc_out<<<1, 32, 0, s>>>(out, loss_out, gmax_out);

@@ -34,7 +34,7 @@ __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
 constexpr int ST_X = 32, ST_Y = 8, ST_HX = ST_X + 2, ST_HY = ST_Y + 2;
 constexpr int ST_PLANE = ST_HX * ST_HY;
 
-__global__ void __launch_bounds__(ST_X * ST_Y)
+__global__ void __launch_bounds__(ST_X * ST_Y, 3)
     k_step_compose(const PairDesc* __restrict__ pd, int npairs, int attempt,
                    float step, int smooth) {
     __shared__ float ring[3][3][ST_PLANE];   // [z slot][component][y][x]
