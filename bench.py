@@ -43,6 +43,11 @@ METRIC = "Gvoxel-iters/s"
 # read F 4 + M 4 + u 12, write g 12 (fp32 images)
 EVAL_BYTES_PER_VOXEL = 32
 STEP_BYTES_PER_VOXEL = 36
+# DRAM bytes (read + write) per voxel of one pass-1 evaluation of the current
+# kernels, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
+# the J pass, E1 and E2 at 128x160x192, k = 5, FP32), scaled by voxels.  Set to
+# None whenever those kernels change until a new capture is taken.
+PASS1_TRAFFIC_BYTES_PER_VOXEL = 103.9
 
 
 def _peaks():
@@ -252,7 +257,9 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": "pass-1 evaluation",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": None,
+                "traffic": (PASS1_TRAFFIC_BYTES_PER_VOXEL * V
+                            if PASS1_TRAFFIC_BYTES_PER_VOXEL and shape == SHAPE
+                            else None),
                 "ms_eval": ms_eval, "ms_step": ms_step,
                 "step_achieved_gbs": STEP_BYTES_PER_VOXEL * V / (ms_step / 1e3) / 1e9,
                 "bytes_per_voxel_eval": EVAL_BYTES_PER_VOXEL}
