@@ -332,6 +332,143 @@ def run_ours(args):
     return 0
 
 
+def _gen_pair(args):
+    shape, seed = args
+    import synth
+    F, M, _ = synth.voronoi_pair(shape, seed=seed)
+    return F, M
+
+
+def run_batch(args):
+    """64 pairs of uneven sizes: one batched registration (BF16 images, one
+    launch per pass, CUDA graph) against the plain single-pair LM run pair
+    after pair (FP32 images), 100 full-resolution iterations each."""
+    import multiprocessing as mp
+    import numpy as np
+    import torch
+    world, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import synth
+    npairs, iters = args.batch_pairs, args.batch_iters
+    shapes = synth.uneven_shapes(npairs, seed=0)
+    # inputs are generated in a spawn pool before the first GPU call
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        pairs = pool.map(_gen_pair, [(sh, 1000 + i)
+                                     for i, sh in enumerate(shapes)])
+    torch.cuda.set_device(local)
+    from paper_2603_19371_gb300 import build as _build
+    from paper_2603_19371_gb300 import lmreg as P
+    _build.build()
+    P.load()
+    params = P.lm_default_params()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        F32 = [torch.from_numpy(F).cuda() for F, _ in pairs]
+        M32 = [torch.from_numpy(M).cuda() for _, M in pairs]
+        F16 = [t.to(torch.bfloat16) for t in F32]
+        M16 = [t.to(torch.bfloat16) for t in M32]
+    stream.synchronize()
+    vox = sum(int(np.prod(sh)) for sh in shapes)
+
+    def batched(Fs, Ms, n=iters):
+        us = [torch.zeros((3,) + tuple(F.shape), device="cuda") for F in Fs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = P.lm_batch_init(Fs, Ms, params, stream=stream)
+        t1 = time.perf_counter()
+        P.lm_batch_reset(b, us)
+        infos = P.lm_batch_iterate(b, us, n)
+        stream.synchronize()
+        t2 = time.perf_counter()
+        P.lm_batch_destroy(b)
+        return (t2 - t0, t2 - t1, [x.loss for x in infos], us)
+
+    def sequential(Fs, Ms, n=iters):
+        us = [torch.zeros((3,) + tuple(F.shape), device="cuda") for F in Fs]
+        torch.cuda.synchronize()
+        t_init = 0.0
+        t0 = time.perf_counter()
+        losses = []
+        for i in range(len(Fs)):
+            a = time.perf_counter()
+            ctx = P.lm_init(Fs[i], Ms[i], params, stream=stream)
+            t_init += time.perf_counter() - a
+            P.lm_reset(ctx, us[i])
+            si = P.lm_iterate(ctx, us[i], n)
+            losses.append(si.loss)
+            P.lm_destroy(ctx)
+        stream.synchronize()
+        t = time.perf_counter() - t0
+        return (t, t - t_init, losses, us)
+
+    def to_target(Fs, Ms, target, chunk=10, cap=3 * iters):
+        """Batched run until every pair's loss is within 1e-3 of its target;
+        pairs that get there stop (their kernels return at once)."""
+        us = [torch.zeros((3,) + tuple(F.shape), device="cuda") for F in Fs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = P.lm_batch_init(Fs, Ms, params, stream=stream)
+        P.lm_batch_set_targets(b, [t * (1 + 1e-3) for t in target])
+        P.lm_batch_reset(b, us)
+        done = 0
+        while done < cap:
+            infos = P.lm_batch_iterate(b, us, chunk)
+            done += chunk
+            if all(x.stopped for x in infos):
+                break
+        stream.synchronize()
+        t = time.perf_counter() - t0
+        P.lm_batch_destroy(b)
+        return t, done, [x.loss for x in infos], us
+
+    # warm-up of both paths on two pairs (library set-up, first graphs)
+    batched(F16[:2], M16[:2], 3)
+    batched(F32[:2], M32[:2], 3)
+    sequential(F32[:2], M32[:2], 3)
+    ts, ts_run, Ls, us_ = sequential(F32, M32)
+    tf, tf_run, Lf, uf = batched(F32, M32)
+    tb, tb_run, Lb, ub = batched(F16, M16)
+    tt, it_t, Lt, ut = to_target(F16, M16, Ls)
+    # losses of the BF16 results measured on the FP32 images
+    bf = P.lm_batch_init(F32, M32, params, stream=stream)
+    Lt32, _ = P.lm_batch_eval(bf, ut)
+    Lb32, _ = P.lm_batch_eval(bf, ub)
+    P.lm_batch_destroy(bf)
+    rel_f32 = [abs(a - c) / c for a, c in zip(Lf, Ls)]
+    rel_bf16 = [(a - c) / c for a, c in zip(Lb32, Ls)]
+    excess_t = [(a - c) / c for a, c in zip(Lt32, Ls)]
+    du_bf16 = max(float((a - c).abs().max()) for a, c in zip(ub, uf))
+    evals = vox * (iters + 1)
+    line = {
+        "metric": "wall time to the plain LM's final loss, batched vs plain",
+        "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "data": "synthetic",
+        "config": {"workload": f"{npairs} Voronoi pairs of uneven sizes "
+                   "(per axis uniform in 64..160 x 64..192 x 64..224), "
+                   f"plain LM: {iters} full-resolution iterations per pair, "
+                   "k=5", "voxels": vox},
+        "plain_fp32_pair_by_pair": {"s": ts, "s_without_init": ts_run,
+                                    "gvox_it_s": evals / ts_run / 1e9},
+        "batched_fp32_same_iterations": {
+            "s": tf, "s_without_init": tf_run,
+            "gvox_it_s": evals / tf_run / 1e9, "speedup": ts / tf,
+            "max_rel_final_loss_diff_vs_plain": max(rel_f32)},
+        "batched_bf16_same_iterations": {
+            "s": tb, "gvox_it_s": evals / tb_run / 1e9, "speedup": ts / tb,
+            "final_loss_on_fp32_images_rel_to_plain": {
+                "max": max(rel_bf16), "min": min(rel_bf16),
+                "median": sorted(rel_bf16)[npairs // 2]},
+            "max_abs_u_diff_vs_fp32_batched_vox": du_bf16},
+        "batched_bf16_to_target": {
+            "s": tt, "iterations": it_t, "speedup": ts / tt,
+            "pairs_within_1e-3_on_fp32_images": sum(e <= 1e-3 for e in excess_t),
+            "max_rel_excess_on_fp32_images": max(excess_t)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,11 +480,17 @@ def main():
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     metavar=("D", "H", "W"),
                     help="other pair size (profiling cases)")
+    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+                    help="batch: uneven pairs, batched vs plain (own JSON line)")
+    ap.add_argument("--batch-pairs", type=int, default=64)
+    ap.add_argument("--batch-iters", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

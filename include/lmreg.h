@@ -102,6 +102,8 @@ typedef struct {
     int    accepted;    /* 1 = a trial was accepted, 0 = discarded */
     int    retries;     /* rejected trials before the outcome */
     int    evals;       /* loss evaluations spent (retries + 1) */
+    int    stopped;     /* 1 = the pair has reached its target loss
+                           (lm_batch_set_targets) and no longer iterates */
 } lm_step_info;
 
 /* Optimiser scalars of a context (for inspection, teacher forcing and
@@ -141,8 +143,8 @@ LM_API int lm_default_params(lm_params *p);
  *   unchanged for the context's lifetime.
  * p: parameters (copied); NULL = defaults.
  * cuda_stream: cudaStream_t to order all work on (NULL = default stream).
- * The context allocates its own device scratch (about 40 bytes per voxel
- * plus pyramid levels on first lm_register).  LM_EINVAL on bad shapes or
+ * The context allocates its own device scratch (76 bytes per voxel, 100
+ * with warp smoothing, plus pyramid levels on first lm_register).  LM_EINVAL on bad shapes or
  * parameters, LM_ENOMEM / LM_ECUDA on allocation failure. */
 LM_API int lm_init(lm_ctx **ctx, const lm_volume *fixed, const lm_volume *moving,
             const lm_params *p, void *cuda_stream);
@@ -231,6 +233,17 @@ LM_API int lm_batch_reset(lm_batch *b, float *const *u);
  * (host, npairs entries, may be NULL) receive each pair's last outcome. */
 LM_API int lm_batch_iterate(lm_batch *b, float *const *u, int n,
                             lm_step_info *infos);
+/* Per-pair stopping loss.  The paper has no counterpart: it serves batched
+ * runs that must bring every pair to a given loss (for instance the final
+ * loss of another run) without spending iterations on pairs already there.
+ * target: host array of npairs doubles, or NULL to clear every target; a
+ * NaN entry means no target for that pair.  After an iteration whose
+ * resulting loss is <= target[i], pair i stops: its later iterations are
+ * no-ops (its kernels return at once, its field, loss and lambda stay) and
+ * its lm_step_info reports stopped = 1, until lm_batch_reset.  Stream
+ * ordered (the table update precedes later launches); LM_EINVAL on NULL b. */
+LM_API int lm_batch_set_targets(lm_batch *b, const double *target);
+
 /* Coarse-to-fine registration of every pair (as lm_register); reps (host,
  * npairs entries, may be NULL). */
 LM_API int lm_batch_register(lm_batch *b, const lm_schedule *s,

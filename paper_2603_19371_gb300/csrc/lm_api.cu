@@ -10,6 +10,7 @@
 // captured CUDA graph serves any caller field pointers.
 #include <algorithm>
 #include <chrono>
+#include <limits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -326,6 +327,7 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
             return rc;
         d.st = st + i;
         d.qs = qs + i;
+        d.target = std::numeric_limits<double>::quiet_NaN();
         d.log = lg + (size_t)i * LOG_CAP;
         d.u0 = nullptr;
     }
@@ -436,6 +438,7 @@ void fill_info(const DevState& s, lm_step_info* info) {
     info->accepted = s.accepted;
     info->retries = s.retries;
     info->evals = s.retries + 1;
+    info->stopped = s.stopped;
 }
 
 }  // namespace
@@ -681,7 +684,7 @@ extern "C" int lm_state_save(lm_ctx* c, void* buf, size_t* nbytes) {
     h.nx = d.g.nx;
     h.ny = d.g.ny;
     h.nz = d.g.nz;
-    h.version = 1;
+    h.version = 2;
     char* q = (char*)buf;
     memcpy(q, &h, sizeof(h));
     memcpy(q + sizeof(h), k->h_st, sizeof(DevState));
@@ -703,7 +706,7 @@ extern "C" int lm_state_load(lm_ctx* c, const void* buf, size_t nbytes) {
     if (nbytes < need) return fail(LM_EINVAL, "checkpoint too small");
     CkptHeader h;
     memcpy(&h, buf, sizeof(h));
-    if (memcmp(h.magic, "LMREGCK1", 8) != 0 || h.version != 1)
+    if (memcmp(h.magic, "LMREGCK1", 8) != 0 || h.version != 2)
         return fail(LM_EINVAL, "not an lmreg checkpoint");
     if (h.nx != d.g.nx || h.ny != d.g.ny || h.nz != d.g.nz)
         return fail(LM_EINVAL, "checkpoint shape differs from the context");
@@ -901,6 +904,15 @@ extern "C" int lm_batch_iterate(lm_batch* b, float* const* u, int n,
         for (int i = 0; i < k->npairs; ++i) fill_info(k->h_st[i], &infos[i]);
     }
     return LM_OK;
+}
+
+extern "C" int lm_batch_set_targets(lm_batch* b, const double* target) {
+    if (!b) return fail(LM_EINVAL, "NULL argument");
+    Core* k = b->core.get();
+    for (int i = 0; i < k->npairs; ++i)
+        k->hpd[i].target =
+            target ? target[i] : std::numeric_limits<double>::quiet_NaN();
+    return k->push_table();
 }
 
 extern "C" int lm_batch_register(lm_batch* b, const lm_schedule* s,

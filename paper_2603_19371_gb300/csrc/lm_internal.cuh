@@ -37,6 +37,7 @@ struct DevState {
     int iter;          // finished iterations since reset
     int evals;         // loss evaluations since reset
     int log_pos;       // next log slot
+    int stopped;       // reached the pair's target loss: iterations are no-ops
 };
 
 enum { STATUS_NONFINITE = 1 };

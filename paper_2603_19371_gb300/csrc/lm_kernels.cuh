@@ -41,6 +41,7 @@ struct PairDesc {
     LogEntry* log;        // may be NULL
     float* wtmpA;         // warp-smoothing temporaries (sigma_warp > 0)
     float* wtmpB;
+    double target;        // stop once the loss is <= target (NaN: never)
     // evaluation kernel 1: columns and CTA range (loss partial slots)
     int e1_cx, e1_cy, e1_cta0, e1_ncta;
     // evaluation kernel 2: columns and CTA range (|g|^2 partial slots)
@@ -63,10 +64,11 @@ __device__ __forceinline__ float* eval_g(const PairDesc& p, int mode) {
     return p.st->cg ? p.g0 : p.g1;
 }
 // Later attempts of an iteration are no-ops once the pair's iteration is
-// decided.
+// decided, and every attempt is once the pair has reached its target loss.
 __device__ __forceinline__ bool trial_skip(const PairDesc& p, int mode,
                                            int attempt) {
-    return mode == EVAL_TRIAL && attempt > 0 && p.st->done;
+    return mode == EVAL_TRIAL &&
+           (p.st->stopped || (attempt > 0 && p.st->done));
 }
 
 // Pair whose block range starts at or below b (ranges ascend in pair

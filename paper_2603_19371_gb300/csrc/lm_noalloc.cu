@@ -162,6 +162,7 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     pd.g.V = V;
     pd.F = fixed->data;
     pd.M = moving->data;
+    pd.target = NAN;   // explicit evaluation only: no stopping rule
     pd.u_in = u;
     pd.g_out = g_out;
     pd.graw = (float*)(base + OFF_GRAW);

@@ -22,7 +22,7 @@ __device__ __forceinline__ float safe_floor(float v) {
 }
 
 __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
-    return attempt > 0 && st->done;
+    return st->stopped || (attempt > 0 && st->done);
 }
 
 // Trial field, one voxel per thread.  A block owns a 32 x 8 x-y tile and a
@@ -304,6 +304,7 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
         st->iter = 0;
         st->evals = 1;
         st->log_pos = 0;
+        st->stopped = 0;
         return;
     }
     // FIN_DECIDE
@@ -355,6 +356,7 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
     st->accepted = accepted;
     st->done = finished;
     st->iter += 1;
+    if (st->L <= P.target) st->stopped = 1;   // false for a NaN target
     if (P.log) {
         int pos = st->log_pos;
         LogEntry e;

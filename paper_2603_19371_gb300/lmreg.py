@@ -51,7 +51,7 @@ class StepInfo(ctypes.Structure):
     _fields_ = [("loss", ctypes.c_double), ("loss_first", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("gmax", ctypes.c_float),
                 ("accepted", ctypes.c_int), ("retries", ctypes.c_int),
-                ("evals", ctypes.c_int)]
+                ("evals", ctypes.c_int), ("stopped", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -110,6 +110,7 @@ def load():
         "lm_batch_reset": [V, ctypes.POINTER(V)],
         "lm_batch_iterate": [V, ctypes.POINTER(V), I,
                              ctypes.POINTER(StepInfo)],
+        "lm_batch_set_targets": [V, ctypes.POINTER(D)],
         "lm_batch_register": [V, ctypes.POINTER(Schedule), ctypes.POINTER(V),
                               ctypes.POINTER(Report)],
         "lm_register_batch": [I, ctypes.POINTER(Volume), ctypes.POINTER(Volume),
@@ -360,6 +361,14 @@ def lm_batch_iterate(b: Batch, us, n, info=True):
     return list(infos) if info else None
 
 
+def lm_batch_set_targets(b: Batch, targets=None):
+    """Per-pair stopping losses (None clears; NaN entries mean no target)."""
+    arr = None
+    if targets is not None:
+        arr = (ctypes.c_double * len(b))(*[float(t) for t in targets])
+    _check(load().lm_batch_set_targets(b.handle, arr), "lm_batch_set_targets")
+
+
 def lm_batch_register(b: Batch, levels, us):
     s = _schedule(levels)
     reps = (Report * len(b))()
@@ -412,5 +421,5 @@ EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_set_state", "lm_register", "lm_state_save", "lm_state_load",
             "lm_time_passes", "lm_batch_init", "lm_batch_destroy",
             "lm_batch_eval", "lm_batch_reset", "lm_batch_iterate",
-            "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
+            "lm_batch_set_targets", "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
             "lm_strerror", "lm_last_error")

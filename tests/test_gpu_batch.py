@@ -137,3 +137,34 @@ def test_batch_rejects_mixed_dtypes(P):
     with pytest.raises(P.LMError) as e:
         P.lm_batch_init(Fs, Ms, P.lm_default_params())
     assert e.value.code == P.LM_EINVAL
+
+
+def test_batch_targets_stop_pairs(P):
+    """A pair whose loss reaches its target stops; the others go on."""
+    import torch
+    Fs, Ms = _pairs(seed0=80)
+    params = P.lm_default_params(lambda0=0.02, step=1.0)
+    b = P.lm_batch_init(Fs, Ms, params)
+    us = [torch.zeros((3,) + sh, device="cuda") for sh in SHAPES]
+    P.lm_batch_reset(b, us)
+    P.lm_batch_iterate(b, us, 2)
+    inf, nan = float("inf"), float("nan")
+    P.lm_batch_set_targets(b, [inf] + [nan] * (len(SHAPES) - 1))
+    infos = P.lm_batch_iterate(b, us, 1)       # pair 0 stops after this one
+    assert infos[0].stopped == 1
+    assert all(x.stopped == 0 for x in infos[1:])
+    snap = [u.clone() for u in us]
+    L_stop = infos[0].loss
+    infos = P.lm_batch_iterate(b, us, 4)
+    assert infos[0].stopped == 1 and infos[0].loss == L_stop
+    assert torch.equal(us[0], snap[0])
+    for i in range(1, len(SHAPES)):
+        assert infos[i].stopped == 0
+        assert not torch.equal(us[i], snap[i])
+    # clearing the targets keeps the stop; a reset lifts it
+    P.lm_batch_set_targets(b, None)
+    assert P.lm_batch_iterate(b, us, 1)[0].stopped == 1
+    P.lm_batch_reset(b, us)
+    infos = P.lm_batch_iterate(b, us, 1)
+    assert infos[0].stopped == 0
+    assert not torch.equal(us[0], snap[0])
