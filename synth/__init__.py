@@ -203,3 +203,20 @@ def uneven_shapes(n=64, seed=0, lo=(64, 64, 64), hi=(160, 192, 224)):
     rng = np.random.default_rng(seed)
     return [tuple(int(rng.integers(lo[i], hi[i] + 1)) for i in range(3))
             for _ in range(n)]
+
+
+def unet_init(shapes, seed=0, last_scale=0.1):
+    """Initial network weights: for each (cin, cout) a (cout, cin, 3, 3, 3)
+    array drawn uniformly with the He/Kaiming bound for a leaky ReLU of
+    slope 0.2 (fan-in 27 cin) and a zero bias; the last layer is scaled by
+    ``last_scale`` so that the untrained output is near zero.  float32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n, (cin, cout) in enumerate(shapes):
+        fan_in = 27 * cin
+        bound = np.sqrt(3.0 * 2.0 / ((1.0 + 0.04) * fan_in))
+        if n == len(shapes) - 1:
+            bound *= last_scale
+        w = rng.uniform(-bound, bound, (cout, cin, 3, 3, 3))
+        out.append((w.astype(np.float32), np.zeros(cout, np.float32)))
+    return out
