@@ -469,6 +469,177 @@ def run_batch(args):
     return 0
 
 
+def _gen_pair_ws(args):
+    shape, seed = args
+    import synth
+    # the 160x192x224 recipe at 128^3, warp scaled with the volume (0.67x)
+    F, M, _ = synth.voronoi_pair(shape, seed=seed, svf_sigma=5.0, max_disp=5.0)
+    return F, M
+
+
+def run_warmstart(args):
+    """Learned warm start: a U-Net trained on multiscale-LM fields predicts
+    the initial field of held-out pairs; LM then refines at full resolution
+    until every pair is within 1e-3 of the loss plain multiscale LM reaches
+    from zero.  Both arms run batched over the held-out pairs."""
+    import multiprocessing as mp
+    import numpy as np
+    import torch
+    world, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import synth
+    S = (128, 128, 128)
+    Sh = tuple(n // 2 for n in S)
+    ntr, nte = args.ws_train, args.ws_test
+    t_gen = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        pairs = pool.map(_gen_pair_ws, [(S, 5000 + i) for i in range(ntr + nte)])
+    t_gen = time.perf_counter() - t_gen
+    torch.cuda.set_device(local)
+    from paper_2603_19371_gb300 import build as _build
+    from paper_2603_19371_gb300 import lmreg as P
+    _build.build()
+    P.load()
+    params = P.lm_default_params()
+    levels = [(4, 200), (2, 100), (1, 50)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        Fs = [torch.from_numpy(F).cuda() for F, _ in pairs]
+        Ms = [torch.from_numpy(M).cuda() for _, M in pairs]
+    stream.synchronize()
+    del pairs
+
+    # 1. targets: multiscale LM from zero on the training pairs, carried to
+    #    half resolution (values x 0.5) by the pyramid's field resampling
+    t0 = time.perf_counter()
+    targets = []
+    for g0 in range(0, ntr, 32):
+        idx = list(range(g0, min(g0 + 32, ntr)))
+        us = [torch.zeros((3,) + S, device="cuda") for _ in idx]
+        P.lm_register_batch([Fs[i] for i in idx], [Ms[i] for i in idx], us,
+                            levels, params, stream=stream)
+        for u in us:
+            th = torch.empty((3,) + Sh, device="cuda")
+            P.lm_field_resample(u, 1, th, 2, stream=stream)
+            targets.append(th)
+        del us
+    stream.synchronize()
+    t_targets = time.perf_counter() - t0
+
+    # 2. training (Adam, batches of 4 pairs, step size halved twice)
+    shapes, _ = P.lm_unet_shapes()
+    net = P.lm_unet_create(S, synth.unet_init(shapes, seed=0), stream=stream)
+    rng = np.random.default_rng(0)
+    bs, nsteps, log = 4, 0, []
+    t0 = time.perf_counter()
+    for ep in range(args.ws_epochs):
+        lr = args.ws_lr * (0.5 ** (3 * ep // max(1, args.ws_epochs)))
+        order = rng.permutation(ntr)
+        for b0 in range(0, ntr - bs + 1, bs):
+            idx = order[b0:b0 + bs]
+            last = b0 + 2 * bs > ntr
+            L = P.lm_unet_train_step(net, [Fs[i] for i in idx],
+                                     [Ms[i] for i in idx],
+                                     [targets[i] for i in idx], lr, loss=last)
+            nsteps += 1
+            if last:
+                log.append(L)
+                if not (L < 1e3):
+                    raise RuntimeError(f"U-Net training diverged (MSE {L})")
+    stream.synchronize()
+    t_train = time.perf_counter() - t0
+
+    test = list(range(ntr, ntr + nte))
+    Ft = [Fs[i] for i in test]
+    Mt = [Ms[i] for i in test]
+    # warm-up of both arms' code paths on two pairs
+    P.lm_register_batch(Ft[:2], Mt[:2], [torch.zeros((3,) + S, device="cuda")
+                                         for _ in range(2)], [(1, 2)], params,
+                        stream=stream)
+    stream.synchronize()
+
+    # 3. plain multiscale LM from zero (batched)
+    u0 = [torch.zeros((3,) + S, device="cuda") for _ in test]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = P.lm_batch_init(Ft, Mt, params, stream=stream)
+    reps = P.lm_batch_register(b, levels, u0)
+    stream.synchronize()
+    t_plain = time.perf_counter() - t0
+    P.lm_batch_destroy(b)
+    L_plain = [r.final_loss for r in reps]
+
+    # 4. warm start: network, field to full resolution, LM to the target
+    uw = [torch.empty((3,) + S, device="cuda") for _ in test]
+    uh = torch.empty((3,) + Sh, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(nte):
+        P.lm_unet_forward(net, Ft[i], Mt[i], uh)
+        P.lm_field_resample(uh, 2, uw[i], 1, stream=stream)
+    stream.synchronize()
+    t_net = time.perf_counter() - t0
+    b = P.lm_batch_init(Ft, Mt, params, stream=stream)
+    L_init, _ = P.lm_batch_eval(b, uw)
+    if args.ws_level2 > 0:
+        # a short half-resolution refinement (the network's own resolution)
+        P.lm_batch_register(b, [(2, args.ws_level2)], uw)
+    P.lm_batch_set_targets(b, [L * (1 + 1e-3) for L in L_plain])
+    P.lm_batch_reset(b, uw)
+    iters, cap = 0, args.ws_cap
+    infos = []
+    while iters < cap:
+        infos = P.lm_batch_iterate(b, uw, 5)
+        iters += 5
+        if all(x.stopped for x in infos):
+            break
+    stream.synchronize()
+    t_warm = time.perf_counter() - t0
+    P.lm_batch_destroy(b)
+    reached = sum(1 for x in infos if x.stopped)
+    mean_abs_u = {"plain": float(np.mean([float(u.abs().mean()) for u in u0])),
+                  "warm_start": float(np.mean([float(u.abs().mean()) for u in uw]))}
+    # held-out regression error of the network against the plain fields
+    mse_te, msq_te = [], []
+    for i in range(nte):
+        th = torch.empty((3,) + Sh, device="cuda")
+        P.lm_field_resample(u0[i], 1, th, 2, stream=stream)
+        P.lm_unet_forward(net, Ft[i], Mt[i], uh)
+        stream.synchronize()
+        mse_te.append(float(((uh - th) ** 2).mean()))
+        msq_te.append(float((th ** 2).mean()))
+    line = {
+        "metric": "wall time to the plain multiscale LM's final loss, "
+                  "warm-started vs from zero",
+        "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "data": "synthetic",
+        "config": {"workload": f"{ntr} training + {nte} held-out Voronoi "
+                   "pairs at 128^3 (SVF warps, max 5 voxels), k=5; plain LM "
+                   "4/2/1 x 200/100/50 from zero; warm start = U-Net "
+                   "(16/32/64/128 channels) field, then full-resolution LM "
+                   "until within 1e-3 of the plain final loss"},
+        "plain_multiscale_from_zero": {"s": t_plain, "iterations": 350},
+        "warm_start": {"s": t_warm,
+                       "network_s": t_net,
+                       "half_res_iterations": args.ws_level2,
+                       "full_res_iterations": iters,
+                       "pairs_reaching_target": reached,
+                       "speedup_vs_plain": t_plain / t_warm},
+        "loss_mean": {"plain_final": float(np.mean(L_plain)),
+                      "warm_start_initial": float(np.mean(L_init))},
+        "mean_abs_u_vox": mean_abs_u,
+        "network": {"train_pairs": ntr, "epochs": args.ws_epochs,
+                    "adam_steps": nsteps, "train_s": t_train,
+                    "train_mse_last_batch_per_epoch": log,
+                    "heldout_mse_vs_plain_fields": float(np.mean(mse_te)),
+                    "heldout_plain_field_mean_sq": float(np.mean(msq_te))},
+        "prep": {"generate_s": t_gen, "targets_s": t_targets},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,8 +651,16 @@ def main():
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     metavar=("D", "H", "W"),
                     help="other pair size (profiling cases)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
-                    help="batch: uneven pairs, batched vs plain (own JSON line)")
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batch", "warmstart"],
+                    help="batch: uneven pairs, batched vs plain; warmstart: "
+                         "U-Net warm start vs LM from zero (own JSON lines)")
+    ap.add_argument("--ws-train", type=int, default=256)
+    ap.add_argument("--ws-test", type=int, default=32)
+    ap.add_argument("--ws-epochs", type=int, default=16)
+    ap.add_argument("--ws-lr", type=float, default=3e-4)
+    ap.add_argument("--ws-cap", type=int, default=400)
+    ap.add_argument("--ws-level2", type=int, default=0)
     ap.add_argument("--batch-pairs", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=100)
     args = ap.parse_args()
@@ -491,6 +670,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     return run_ours(args)
 
 

@@ -233,6 +233,18 @@ LM_API int lm_batch_reset(lm_batch *b, float *const *u);
  * (host, npairs entries, may be NULL) receive each pair's last outcome. */
 LM_API int lm_batch_iterate(lm_batch *b, float *const *u, int n,
                             lm_step_info *infos);
+/* Carry a displacement field between pyramid levels (Section 2.1), as
+ * lm_register does between its levels: the level-b field at voxel p is the
+ * level-a field read trilinearly (clamped at the border) at the level-a
+ * coordinate of p's centre, (fb p + (fb - 1)/2 - (fa - 1)/2) / fa, times
+ * fa / fb (voxel units scale with the level).  src: device [3][Da][Ha][Wa]
+ * of a level with factor fa; dst: device [3][Db][Hb][Wb] of factor fb
+ * (written).  Asynchronous on cuda_stream.  LM_EINVAL on NULL pointers or
+ * non-positive sizes or factors. */
+LM_API int lm_field_resample(const float *src, int Da, int Ha, int Wa, int fa,
+                             float *dst, int Db, int Hb, int Wb, int fb,
+                             void *cuda_stream);
+
 /* Per-pair stopping loss.  The paper has no counterpart: it serves batched
  * runs that must bring every pair to a given loss (for instance the final
  * loss of another run) without spending iterations on pairs already there.

@@ -906,6 +906,20 @@ extern "C" int lm_batch_iterate(lm_batch* b, float* const* u, int n,
     return LM_OK;
 }
 
+extern "C" int lm_field_resample(const float* src, int Da, int Ha, int Wa,
+                                 int fa, float* dst, int Db, int Hb, int Wb,
+                                 int fb, void* stream) {
+    if (!src || !dst) return fail(LM_EINVAL, "NULL field");
+    if (Da < 1 || Ha < 1 || Wa < 1 || Db < 1 || Hb < 1 || Wb < 1 || fa < 1 ||
+        fb < 1)
+        return fail(LM_EINVAL, "sizes and factors must be positive");
+    Geom ga{Wa, Ha, Da, (long long)Wa * Ha * Da};
+    Geom gb{Wb, Hb, Db, (long long)Wb * Hb * Db};
+    resample_field(src, ga, fa, dst, gb, fb, (cudaStream_t)stream);
+    LM_CK(cudaGetLastError());
+    return LM_OK;
+}
+
 extern "C" int lm_batch_set_targets(lm_batch* b, const double* target) {
     if (!b) return fail(LM_EINVAL, "NULL argument");
     Core* k = b->core.get();

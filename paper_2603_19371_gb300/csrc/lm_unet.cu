@@ -1,0 +1,1108 @@
+// The learned warm start (include/lmunet.h): a 3-D U-Net trained on the
+// optimizer's own fields.  Every convolution runs as an implicit GEMM on the
+// tensor cores (bfloat16 operands, FP32 accumulation, mma.sync m16n8k16):
+//
+//   forward / data gradient: rows = voxels, columns = output channels,
+//     reduction k = (tap, input channel); the data gradient is the forward
+//     convolution of dy with the weights flipped in space and transposed
+//     in channels.
+//   weight gradient: rows = output channels, columns = (tap, input channel),
+//     reduction over voxels, split over voxel chunks and accumulated with
+//     FP32 atomics.
+//
+// Activations are channels-last bfloat16 ([D][H][W][C], C innermost), so a
+// 16-channel slice of one voxel is one 32-byte load; the A tile of the
+// forward GEMM is gathered with cp.async (zero fill outside the volume) in a
+// three-stage pipeline.  Pooling, upsampling, concatenation, the loss and
+// Adam are plain element-wise kernels.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lm_kernels.cuh"
+#include "lmunet.h"
+
+namespace lmu {
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr float SLOPE = 0.2f;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    lmk::set_last_error(buf);
+    return code;
+}
+
+#define UN_CK(call)                                                        \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) {                                           \
+            cudaGetLastError();                                            \
+            return fail(LM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+        }                                                                  \
+    } while (0)
+
+// ---------------------------------------------------------------------
+// Tensor-core and async-copy primitives.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem,
+                                           bool pred) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    int n = pred ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s),
+                 "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem,
+                                          bool pred) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    int n = pred ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s),
+                 "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_commit() {
+    asm volatile("cp.async.commit_group;\n" ::);
+}
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// D += A B for one 16x8x16 tile: A row-major (a: 4 registers of two
+// bfloat16), B column-major (b: 2 registers), D FP32.
+__device__ __forceinline__ void mma16816(float* d, const unsigned* a,
+                                         const unsigned* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned ld_u32(const bf16* p) {
+    return *reinterpret_cast<const unsigned*>(p);
+}
+
+// tap t = 9 kz + 3 ky + kx, offsets (kz - 1, ky - 1, kx - 1)
+__device__ __forceinline__ void tap_offset(int t, int& dz, int& dy, int& dx) {
+    dz = t / 9 - 1;
+    dy = (t / 3) % 3 - 1;
+    dx = t % 3 - 1;
+}
+
+// ---------------------------------------------------------------------
+// Forward convolution (also the data gradient): y[v][co] =
+//   act(bias[co] + sum_{t, ci} w[co][t][ci] x[v + off(t)][ci]).
+// CTA tile 128 voxels x BN channels, k step 16 (one tap and 16 input
+// channels; for cin = 2 one step holds 8 taps), 8 warps.
+// ---------------------------------------------------------------------
+constexpr int CBM = 128, CKP = 24, CSTAGES = 3;
+
+template <int BN, bool CIN2, bool OUTF32>
+__global__ void __launch_bounds__(256)
+    k_conv_fwd(const bf16* __restrict__ x, const bf16* __restrict__ w,
+               const float* __restrict__ bias, void* __restrict__ y, int D,
+               int H, int W, int cin, int cout, int act) {
+    constexpr int WM = BN >= 64 ? 4 : 8, WN = 8 / WM;
+    constexpr int MT = CBM / WM / 16, NT = BN / WN / 8;
+    __shared__ __align__(16) bf16 As[CSTAGES][CBM][CKP];
+    __shared__ __align__(16) bf16 Bs[CSTAGES][BN][CKP];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp % WM, wn = warp / WM;
+    const long long V = (long long)D * H * W;
+    const long long v0 = (long long)blockIdx.x * CBM;
+    const int n0 = blockIdx.y * BN;
+    const int cpt = CIN2 ? 1 : cin / 16;       // k steps per tap
+    const int nk = CIN2 ? 4 : 27 * cpt;
+    // gather role: row am of the A tile, half ah
+    const int am = tid >> 1, ah = tid & 1;
+    const long long av = v0 + am;
+    const bool arow = av < V;
+    int az = 0, ay = 0, ax = 0;
+    if (arow) {
+        ax = (int)(av % W);
+        const long long r = av / W;
+        ay = (int)(r % H);
+        az = (int)(r / H);
+    }
+    auto load = [&](int s, int stage) {
+        if (!CIN2) {
+            const int tap = s / cpt, c0 = (s - tap * cpt) * 16;
+            int dz, dy, dx;
+            tap_offset(tap, dz, dy, dx);
+            const int zz = az + dz, yy = ay + dy, xx = ax + dx;
+            const bool in = arow && zz >= 0 && zz < D && yy >= 0 && yy < H &&
+                            xx >= 0 && xx < W;
+            const bf16* src =
+                in ? x + (((long long)zz * H + yy) * W + xx) * cin + c0 + ah * 8
+                   : x;
+            cp_async16(&As[stage][am][ah * 8], src, in);
+            if (tid < 2 * BN) {
+                const int bn = tid >> 1, bh = tid & 1;
+                cp_async16(&Bs[stage][bn][bh * 8],
+                           w + ((long long)(n0 + bn) * 27 + tap) * cin + c0 +
+                               bh * 8,
+                           true);
+            }
+        } else {
+            // k = 2 tap + ci; step s holds taps 8 s .. 8 s + 7
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int tl = ah * 4 + j, tap = s * 8 + tl;
+                int dz, dy, dx;
+                tap_offset(tap, dz, dy, dx);
+                const int zz = az + dz, yy = ay + dy, xx = ax + dx;
+                const bool in = arow && tap < 27 && zz >= 0 && zz < D &&
+                                yy >= 0 && yy < H && xx >= 0 && xx < W;
+                const bf16* src =
+                    in ? x + (((long long)zz * H + yy) * W + xx) * 2 : x;
+                cp_async4(&As[stage][am][tl * 2], src, in);
+            }
+            for (int u = tid; u < BN * 8; u += 256) {
+                const int bn = u >> 3, tl = u & 7, tap = s * 8 + tl;
+                const bool in = tap < 27;
+                cp_async4(&Bs[stage][bn][tl * 2],
+                          in ? w + ((long long)(n0 + bn) * 27 + tap) * 2 : w,
+                          in);
+            }
+        }
+    };
+
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+#pragma unroll
+    for (int s = 0; s < CSTAGES - 1; ++s) {
+        if (s < nk) load(s, s);
+        cp_commit();
+    }
+    const int g = lane >> 2, t4 = lane & 3;
+    for (int s = 0; s < nk; ++s) {
+        cp_wait<CSTAGES - 2>();
+        __syncthreads();
+        const int st = s % CSTAGES;
+        unsigned af[MT][4], bfr[NT][2];
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi) {
+            const int r0 = wm * (CBM / WM) + mi * 16 + g;
+            af[mi][0] = ld_u32(&As[st][r0][2 * t4]);
+            af[mi][1] = ld_u32(&As[st][r0 + 8][2 * t4]);
+            af[mi][2] = ld_u32(&As[st][r0][2 * t4 + 8]);
+            af[mi][3] = ld_u32(&As[st][r0 + 8][2 * t4 + 8]);
+        }
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni) {
+            const int c = wn * (BN / WN) + ni * 8 + g;
+            bfr[ni][0] = ld_u32(&Bs[st][c][2 * t4]);
+            bfr[ni][1] = ld_u32(&Bs[st][c][2 * t4 + 8]);
+        }
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < NT; ++ni) mma16816(acc[mi][ni], af[mi], bfr[ni]);
+        const int nx = s + CSTAGES - 1;
+        if (nx < nk) load(nx, nx % CSTAGES);
+        cp_commit();
+    }
+    cp_wait<0>();
+
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni) {
+            const int r0 = wm * (CBM / WM) + mi * 16 + g;
+            const int c = n0 + wn * (BN / WN) + ni * 8 + 2 * t4;
+            const float b0 = bias ? bias[c] : 0.f, b1 = bias ? bias[c + 1] : 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long v = v0 + r0 + h * 8;
+                if (v >= V) continue;
+                float o0 = acc[mi][ni][2 * h] + b0, o1 = acc[mi][ni][2 * h + 1] + b1;
+                if (act) {
+                    o0 = o0 > 0.f ? o0 : SLOPE * o0;
+                    o1 = o1 > 0.f ? o1 : SLOPE * o1;
+                }
+                if (OUTF32)
+                    *reinterpret_cast<float2*>((float*)y + v * cout + c) =
+                        make_float2(o0, o1);
+                else
+                    *reinterpret_cast<__nv_bfloat162*>((bf16*)y + v * cout + c) =
+                        __floats2bfloat162_rn(o0, o1);
+            }
+        }
+}
+
+// ---------------------------------------------------------------------
+// Weight gradient: dw[co][n] += sum_v dy[v][co] X(v, n), with n = 27-tap
+// index t times cin plus ci and X(v, n) = x[v + off(t)][ci] (zero outside).
+// CTA tile 64 output channels x 64 columns; k = 32 voxels per step over a
+// chunk of voxels; both operands are staged transposed in shared memory.
+// ---------------------------------------------------------------------
+constexpr int WTM = 64, WTN = 64, WKV = 32, WKP = 40;
+
+template <bool CIN2>
+__global__ void __launch_bounds__(256)
+    k_conv_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy,
+                 float* __restrict__ dw, int D, int H, int W, int cin, int cout,
+                 int vchunk) {
+    __shared__ __align__(16) bf16 As[WTM][WKP];   // dy^T [co][v]
+    __shared__ __align__(16) bf16 Bs[WTN][WKP];   // X^T  [n][v]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;      // 2 x 4 warps, 32 x 16 each
+    const int ntot = 27 * cin;
+    const int n0 = blockIdx.x * WTN, m0 = blockIdx.y * WTM;
+    const long long V = (long long)D * H * W;
+    const long long vs = (long long)blockIdx.z * vchunk;
+    const long long ve = vs + vchunk < V ? vs + vchunk : V;
+    const int lv = tid >> 3, part = tid & 7;
+    const int g = lane >> 2, t4 = lane & 3;
+    float acc[2][2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    for (long long vb = vs; vb < ve; vb += WKV) {
+        const long long v = vb + lv;
+        const bool vin = v < ve;
+        {
+            const int co = m0 + part * 8;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (vin && co < cout)
+                val = *reinterpret_cast<const uint4*>(dy + v * cout + co);
+            const bf16* e = reinterpret_cast<const bf16*>(&val);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) As[part * 8 + j][lv] = e[j];
+        }
+        {
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (vin) {
+                const int xx = (int)(v % W);
+                const long long r = v / W;
+                const int yy = (int)(r % H), zz = (int)(r / H);
+                if (!CIN2) {
+                    const int n = n0 + part * 8;
+                    if (n < ntot) {
+                        const int tap = n / cin, ci = n - tap * cin;
+                        int dz, dyy, dx;
+                        tap_offset(tap, dz, dyy, dx);
+                        const int z2 = zz + dz, y2 = yy + dyy, x2 = xx + dx;
+                        if (z2 >= 0 && z2 < D && y2 >= 0 && y2 < H && x2 >= 0 &&
+                            x2 < W)
+                            val = *reinterpret_cast<const uint4*>(
+                                x + (((long long)z2 * H + y2) * W + x2) * cin + ci);
+                    }
+                } else {
+                    unsigned* vv = reinterpret_cast<unsigned*>(&val);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int tap = (n0 + part * 8) / 2 + j;
+                        if (tap >= 27) continue;
+                        int dz, dyy, dx;
+                        tap_offset(tap, dz, dyy, dx);
+                        const int z2 = zz + dz, y2 = yy + dyy, x2 = xx + dx;
+                        if (z2 >= 0 && z2 < D && y2 >= 0 && y2 < H && x2 >= 0 &&
+                            x2 < W)
+                            vv[j] = *reinterpret_cast<const unsigned*>(
+                                x + (((long long)z2 * H + y2) * W + x2) * 2);
+                    }
+                }
+            }
+            const bf16* e = reinterpret_cast<const bf16*>(&val);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) Bs[part * 8 + j][lv] = e[j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < WKV; kk += 16) {
+            unsigned af[2][4], bfr[2][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int r0 = wm * 32 + mi * 16 + g;
+                af[mi][0] = ld_u32(&As[r0][kk + 2 * t4]);
+                af[mi][1] = ld_u32(&As[r0 + 8][kk + 2 * t4]);
+                af[mi][2] = ld_u32(&As[r0][kk + 2 * t4 + 8]);
+                af[mi][3] = ld_u32(&As[r0 + 8][kk + 2 * t4 + 8]);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 2; ++ni) {
+                const int c = wn * 16 + ni * 8 + g;
+                bfr[ni][0] = ld_u32(&Bs[c][kk + 2 * t4]);
+                bfr[ni][1] = ld_u32(&Bs[c][kk + 2 * t4 + 8]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 2; ++ni)
+                    mma16816(acc[mi][ni], af[mi], bfr[ni]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = m0 + wm * 32 + mi * 16 + g + (q >> 1) * 8;
+                const int col = n0 + wn * 16 + ni * 8 + 2 * t4 + (q & 1);
+                if (row < cout && col < ntot)
+                    atomicAdd(dw + (long long)row * ntot + col, acc[mi][ni][q]);
+            }
+}
+
+// db[co] += sum_v dy[v][co]
+__global__ void k_bias_grad(const bf16* __restrict__ dy, float* __restrict__ db,
+                            long long V, int cout) {
+    __shared__ float red[256];
+    const int nr = 256 / cout;
+    const int c = threadIdx.x % cout, r = threadIdx.x / cout;
+    float s = 0.f;
+    if (r < nr)
+        for (long long v = (long long)blockIdx.x * nr + r; v < V;
+             v += (long long)gridDim.x * nr)
+            s += __bfloat162float(dy[v * cout + c]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < cout) {
+        float t = 0.f;
+        for (int k = 0; k < nr; ++k) t += red[k * cout + threadIdx.x];
+        atomicAdd(db + threadIdx.x, t);
+    }
+}
+
+// ---------------------------------------------------------------------
+// Element-wise kernels (channels-last bfloat16, 8 channels per thread).
+// ---------------------------------------------------------------------
+struct B8 {
+    __nv_bfloat162 h[4];
+};
+
+__device__ __forceinline__ B8 ld8(const bf16* p) {
+    return *reinterpret_cast<const B8*>(p);
+}
+__device__ __forceinline__ void st8(bf16* p, const B8& v) {
+    *reinterpret_cast<B8*>(p) = v;
+}
+
+// dy <- dy * a'(y) in place (y = the activation's output; y > 0 iff z > 0)
+__global__ void k_lrelu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y,
+                            long long n8) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n8) return;
+    B8 d = ld8(dy + 8 * i), a = ld8(y + 8 * i);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float2 df = __bfloat1622float2(d.h[k]), af = __bfloat1622float2(a.h[k]);
+        df.x = af.x > 0.f ? df.x : SLOPE * df.x;
+        df.y = af.y > 0.f ? df.y : SLOPE * df.y;
+        d.h[k] = __float22bfloat162_rn(df);
+    }
+    st8(dy + 8 * i, d);
+}
+
+// out[p][c] = mean of the 8 children of p (out dims D/2, H/2, W/2)
+__global__ void k_pool_fwd(const bf16* __restrict__ in, bf16* __restrict__ out,
+                           int D2, int H2, int W2, int C) {
+    const int c8 = C / 8;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)D2 * H2 * W2 * c8;
+    if (i >= n) return;
+    const int cc = (int)(i % c8) * 8;
+    const long long p = i / c8;
+    const int x = (int)(p % W2);
+    const long long r = p / W2;
+    const int y = (int)(r % H2), z = (int)(r / H2);
+    const int W = 2 * W2, H = 2 * H2;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const long long q = ((long long)(2 * z + (k >> 2)) * H + 2 * y + ((k >> 1) & 1)) * W +
+                            2 * x + (k & 1);
+        B8 v = ld8(in + q * C + cc);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float2 f = __bfloat1622float2(v.h[j]);
+            s[2 * j] += f.x;
+            s[2 * j + 1] += f.y;
+        }
+    }
+    B8 o;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        o.h[j] = __floats2bfloat162_rn(0.125f * s[2 * j], 0.125f * s[2 * j + 1]);
+    st8(out + p * C + cc, o);
+}
+
+// din[v][c] = (acc ? din[v][c] : 0) + dout[parent(v)][c] / 8
+__global__ void k_pool_bwd(const bf16* __restrict__ dout, bf16* __restrict__ din,
+                           int D, int H, int W, int C, int accumulate) {
+    const int c8 = C / 8;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)D * H * W * c8;
+    if (i >= n) return;
+    const int cc = (int)(i % c8) * 8;
+    const long long v = i / c8;
+    const int x = (int)(v % W);
+    const long long r = v / W;
+    const int y = (int)(r % H), z = (int)(r / H);
+    const long long p = ((long long)(z / 2) * (H / 2) + y / 2) * (W / 2) + x / 2;
+    B8 g = ld8(dout + p * C + cc);
+    B8 o;
+    if (accumulate) o = ld8(din + v * C + cc);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float2 f = __bfloat1622float2(g.h[j]);
+        f.x *= 0.125f;
+        f.y *= 0.125f;
+        if (accumulate) {
+            float2 a = __bfloat1622float2(o.h[j]);
+            f.x += a.x;
+            f.y += a.y;
+        }
+        o.h[j] = __float22bfloat162_rn(f);
+    }
+    st8(din + v * C + cc, o);
+}
+
+// out[v][off + c] = in[parent(v)][c] for c < C1 (out row stride Cs, fine
+// dims D, H, W)
+__global__ void k_up_fwd(const bf16* __restrict__ in, bf16* __restrict__ out,
+                         int D, int H, int W, int C1, int Cs) {
+    const int c8 = C1 / 8;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)D * H * W * c8;
+    if (i >= n) return;
+    const int cc = (int)(i % c8) * 8;
+    const long long v = i / c8;
+    const int x = (int)(v % W);
+    const long long r = v / W;
+    const int y = (int)(r % H), z = (int)(r / H);
+    const long long p = ((long long)(z / 2) * (H / 2) + y / 2) * (W / 2) + x / 2;
+    st8(out + v * Cs + cc, ld8(in + p * C1 + cc));
+}
+
+// dout[p][c] = sum over the 8 children v of dcat[v][c], c < C1 (dcat row
+// stride Cs; coarse dims D2, H2, W2)
+__global__ void k_up_bwd(const bf16* __restrict__ dcat, bf16* __restrict__ dout,
+                         int D2, int H2, int W2, int C1, int Cs) {
+    const int c8 = C1 / 8;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)D2 * H2 * W2 * c8;
+    if (i >= n) return;
+    const int cc = (int)(i % c8) * 8;
+    const long long p = i / c8;
+    const int x = (int)(p % W2);
+    const long long r = p / W2;
+    const int y = (int)(r % H2), z = (int)(r / H2);
+    const int W = 2 * W2, H = 2 * H2;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const long long q = ((long long)(2 * z + (k >> 2)) * H + 2 * y + ((k >> 1) & 1)) * W +
+                            2 * x + (k & 1);
+        B8 v = ld8(dcat + q * Cs + cc);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float2 f = __bfloat1622float2(v.h[j]);
+            s[2 * j] += f.x;
+            s[2 * j + 1] += f.y;
+        }
+    }
+    B8 o;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o.h[j] = __floats2bfloat162_rn(s[2 * j], s[2 * j + 1]);
+    st8(dout + p * C1 + cc, o);
+}
+
+// dst[v][doff + c] = src[v][soff + c], c < C (row strides Cd, Cs)
+__global__ void k_copy_ch(const bf16* __restrict__ src, bf16* __restrict__ dst,
+                          long long V, int C, int Cs, int soff, int Cd, int doff) {
+    const int c8 = C / 8;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V * c8) return;
+    const int cc = (int)(i % c8) * 8;
+    const long long v = i / c8;
+    st8(dst + v * Cd + doff + cc, ld8(src + v * Cs + soff + cc));
+}
+
+template <typename T>
+__global__ void k_prep_input(const T* __restrict__ F, const T* __restrict__ M,
+                             bf16* __restrict__ x0, long long V) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    *reinterpret_cast<__nv_bfloat162*>(x0 + 2 * v) =
+        __floats2bfloat162_rn(lmk::ld_img(F, v), lmk::ld_img(M, v));
+}
+
+// loss += sum_{v, c < 3} (pred - tgt)^2; dz[v][c] = 2 (pred - tgt) scale,
+// 0 on the padding channels.  pred [V][Cp] FP32, tgt [3][V] FP32.
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ tgt,
+                      bf16* __restrict__ dz, long long V, int Cp, float scale,
+                      double* __restrict__ loss) {
+    __shared__ double red[256];
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (v < V) {
+        for (int c = 0; c < Cp; ++c) {
+            float g = 0.f;
+            if (c < 3) {
+                const float d = pred[v * Cp + c] - tgt[c * V + v];
+                s += (double)d * d;
+                g = 2.f * d * scale;
+            }
+            dz[v * Cp + c] = __float2bfloat16_rn(g);
+        }
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+}
+
+__global__ void k_out_field(const float* __restrict__ pred, float* __restrict__ u,
+                            long long V, int Cp) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c * V + v] = pred[v * Cp + c];
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, long long n,
+                       float lr, float bc1, float bc2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+}
+
+// FP32 master [cout][27][cin] -> bfloat16 copy and the flipped transpose
+// wt[ci][26 - t][co] used by the data gradient.
+__global__ void k_pack_weights(const float* __restrict__ wm, bf16* __restrict__ w,
+                               bf16* __restrict__ wt, int cin, int cout) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)cout * 27 * cin;
+    if (i >= n) return;
+    const int ci = (int)(i % cin);
+    const long long r = i / cin;
+    const int t = (int)(r % 27), co = (int)(r / 27);
+    const bf16 b = __float2bfloat16_rn(wm[i]);
+    w[i] = b;
+    if (wt) wt[((long long)ci * 27 + (26 - t)) * cout + co] = b;
+}
+
+// bfloat16 [cout][27][cin] -> flipped transpose [cin][27][cout]
+__global__ void k_pack_wt_bf16(const bf16* __restrict__ w, bf16* __restrict__ wt,
+                               int cin, int cout) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)cout * 27 * cin;
+    if (i >= n) return;
+    const int ci = (int)(i % cin);
+    const long long r = i / cin;
+    const int t = (int)(r % 27), co = (int)(r / 27);
+    wt[((long long)ci * 27 + (26 - t)) * cout + co] = w[i];
+}
+
+int blocks(long long n, int t = 256) { return (int)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------
+// Launch helpers.
+// ---------------------------------------------------------------------
+int conv_forward(const bf16* x, const bf16* w, const float* bias, void* y,
+                 bool out_f32, int D, int H, int W, int cin, int cout, int act,
+                 cudaStream_t s) {
+    const long long V = (long long)D * H * W;
+    const int gx = (int)((V + CBM - 1) / CBM);
+    const bool c2 = cin == 2;
+#define LAUNCH(BN_, C2_, F_)                                                  \
+    k_conv_fwd<BN_, C2_, F_><<<dim3(gx, cout / BN_), 256, 0, s>>>(             \
+        x, w, bias, y, D, H, W, cin, cout, act)
+#define PICK_BN(C2_, F_)                    \
+    if (cout % 128 == 0) LAUNCH(128, C2_, F_); \
+    else if (cout % 64 == 0) LAUNCH(64, C2_, F_); \
+    else if (cout % 32 == 0) LAUNCH(32, C2_, F_); \
+    else LAUNCH(16, C2_, F_);
+    if (c2) {
+        if (out_f32) { PICK_BN(true, true) } else { PICK_BN(true, false) }
+    } else {
+        if (out_f32) { PICK_BN(false, true) } else { PICK_BN(false, false) }
+    }
+#undef PICK_BN
+#undef LAUNCH
+    return 1;
+}
+
+int conv_wgrad(const bf16* x, const bf16* dy, float* dw, int D, int H, int W,
+               int cin, int cout, cudaStream_t s) {
+    const long long V = (long long)D * H * W;
+    const int ntot = 27 * cin;
+    const int vchunk = 8192;
+    dim3 grid((ntot + WTN - 1) / WTN, (cout + WTM - 1) / WTM,
+              (unsigned)((V + vchunk - 1) / vchunk));
+    if (cin == 2)
+        k_conv_wgrad<true><<<grid, 256, 0, s>>>(x, dy, dw, D, H, W, cin, cout, vchunk);
+    else
+        k_conv_wgrad<false><<<grid, 256, 0, s>>>(x, dy, dw, D, H, W, cin, cout, vchunk);
+    return 1;
+}
+
+int bias_grad(const bf16* dy, float* db, long long V, int cout, cudaStream_t s) {
+    const int nr = 256 / cout;
+    long long nb = (V + nr * 64 - 1) / (nr * 64);
+    if (nb > 4096) nb = 4096;
+    k_bias_grad<<<(int)nb, 256, 0, s>>>(dy, db, V, cout);
+    return 1;
+}
+
+bool conv_shape_ok(int cin, int cout) {
+    return (cin == 2 || (cin % 16 == 0 && cin <= 1024)) && cout % 16 == 0 &&
+           cout >= 16 && cout <= 256;
+}
+
+// ---------------------------------------------------------------------
+// The network.
+// ---------------------------------------------------------------------
+struct LayerDef {
+    int cin, cout, act;
+};
+// c0 .. c12; the head's 3 outputs are padded to 16 channels internally
+constexpr LayerDef kLayers[LM_UNET_LAYERS] = {
+    {2, 16, 1},   {16, 16, 1},  {16, 32, 1},  {32, 32, 1}, {32, 64, 1},
+    {64, 64, 1},  {64, 128, 1}, {128, 128, 1}, {192, 64, 1}, {64, 64, 1},
+    {96, 32, 1},  {32, 32, 1},  {32, 3, 0}};
+
+int padded(int c) { return (c + 15) / 16 * 16; }
+
+}  // namespace
+}  // namespace lmu
+
+using namespace lmu;
+
+struct lm_unet {
+    int D = 0, H = 0, W = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<void*> allocs;
+    struct L {
+        int cin, cout, cp, act;          // cp = padded cout
+        long long w_off, b_off;          // offsets in the flat FP32 arrays
+        bf16* w = nullptr;               // [cp][27][cin]
+        bf16* wt = nullptr;              // [cin][27][cp]
+    } layer[LM_UNET_LAYERS];
+    long long nflat = 0;                 // internal flat parameter count
+    float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    int t = 0;                           // Adam steps taken
+    // activations (bfloat16, channels-last)
+    bf16 *x0, *e0a, *e0, *p0, *e1a, *e1, *p1, *e2a, *e2, *p2, *e3a, *e3, *cat2,
+        *d2a, *d2, *cat1, *d1a, *d1;
+    float* out;                          // [V1][16]
+    // gradients
+    bf16 *gA0, *gB0, *gcat1, *gX1, *gY1, *ge1, *gout, *gcat2, *gX2, *gY2, *ge2,
+        *gX3, *gY3;
+    double* dloss = nullptr;
+    double* hloss = nullptr;             // pinned
+
+    long long Vl(int l) const {
+        return (long long)(D >> l) * (H >> l) * (W >> l);
+    }
+    template <typename T>
+    int alloc(T** p, size_t n) {
+        void* q = nullptr;
+        if (cudaMalloc(&q, n * sizeof(T) + 16) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LM_ENOMEM, "device allocation of %zu bytes failed",
+                        n * sizeof(T));
+        }
+        allocs.push_back(q);
+        *p = (T*)q;
+        return LM_OK;
+    }
+    ~lm_unet() {
+        for (void* p : allocs) cudaFree(p);
+        if (hloss) cudaFreeHost(hloss);
+    }
+};
+
+namespace {
+
+// y = c_i(x) at pyramid level l (bias from the FP32 master weights)
+void conv(lm_unet* n, int i, const bf16* x, void* y, int l, bool out_f32 = false) {
+    const auto& L = n->layer[i];
+    conv_forward(x, L.w, n->master + L.b_off, y, out_f32, n->D >> l, n->H >> l,
+                 n->W >> l, L.cin, L.cp, L.act, n->stream);
+}
+
+// Backward through c_i at level l: dy (gradient of the layer's output,
+// overwritten with the pre-activation gradient), x (its input), y (its
+// output, for the activation mask); dx may be NULL.
+void conv_back(lm_unet* n, int i, bf16* dy, const bf16* x, const bf16* y,
+               bf16* dx, int l) {
+    const auto& L = n->layer[i];
+    const int D = n->D >> l, H = n->H >> l, W = n->W >> l;
+    const long long V = n->Vl(l);
+    cudaStream_t s = n->stream;
+    if (L.act) k_lrelu_bwd<<<blocks(V * L.cp / 8), 256, 0, s>>>(dy, y, V * L.cp / 8);
+    conv_wgrad(x, dy, n->grad + L.w_off, D, H, W, L.cin, L.cp, s);
+    bias_grad(dy, n->grad + L.b_off, V, L.cp, s);
+    if (dx)
+        conv_forward(dy, L.wt, nullptr, dx, false, D, H, W, L.cp, L.cin, 0, s);
+}
+
+void pool_fwd(lm_unet* n, const bf16* in, bf16* out, int l_out, int C) {
+    const long long N = n->Vl(l_out) * (C / 8);
+    k_pool_fwd<<<blocks(N), 256, 0, n->stream>>>(in, out, n->D >> l_out,
+                                                 n->H >> l_out, n->W >> l_out, C);
+}
+void pool_bwd(lm_unet* n, const bf16* dout, bf16* din, int l_in, int C, int acc) {
+    const long long N = n->Vl(l_in) * (C / 8);
+    k_pool_bwd<<<blocks(N), 256, 0, n->stream>>>(dout, din, n->D >> l_in,
+                                                 n->H >> l_in, n->W >> l_in, C, acc);
+}
+void up_fwd(lm_unet* n, const bf16* in, bf16* out, int l_out, int C1, int Cs) {
+    const long long N = n->Vl(l_out) * (C1 / 8);
+    k_up_fwd<<<blocks(N), 256, 0, n->stream>>>(in, out, n->D >> l_out,
+                                               n->H >> l_out, n->W >> l_out, C1, Cs);
+}
+void up_bwd(lm_unet* n, const bf16* dcat, bf16* dout, int l_out, int C1, int Cs) {
+    const long long N = n->Vl(l_out) * (C1 / 8);
+    k_up_bwd<<<blocks(N), 256, 0, n->stream>>>(dcat, dout, n->D >> l_out,
+                                               n->H >> l_out, n->W >> l_out, C1, Cs);
+}
+void copy_ch(lm_unet* n, const bf16* src, bf16* dst, int l, int C, int Cs,
+             int soff, int Cd, int doff) {
+    const long long V = n->Vl(l);
+    k_copy_ch<<<blocks(V * (C / 8)), 256, 0, n->stream>>>(src, dst, V, C, Cs,
+                                                          soff, Cd, doff);
+}
+
+int forward(lm_unet* n, const lm_volume* F, const lm_volume* M) {
+    const long long V0 = n->Vl(0);
+    if (F->dtype == LM_BF16)
+        k_prep_input<bf16><<<blocks(V0), 256, 0, n->stream>>>(
+            (const bf16*)F->data, (const bf16*)M->data, n->x0, V0);
+    else
+        k_prep_input<float><<<blocks(V0), 256, 0, n->stream>>>(
+            (const float*)F->data, (const float*)M->data, n->x0, V0);
+    conv(n, 0, n->x0, n->e0a, 0);
+    conv(n, 1, n->e0a, n->e0, 0);
+    pool_fwd(n, n->e0, n->p0, 1, 16);
+    conv(n, 2, n->p0, n->e1a, 1);
+    conv(n, 3, n->e1a, n->e1, 1);
+    pool_fwd(n, n->e1, n->p1, 2, 32);
+    conv(n, 4, n->p1, n->e2a, 2);
+    conv(n, 5, n->e2a, n->e2, 2);
+    pool_fwd(n, n->e2, n->p2, 3, 64);
+    conv(n, 6, n->p2, n->e3a, 3);
+    conv(n, 7, n->e3a, n->e3, 3);
+    up_fwd(n, n->e3, n->cat2, 2, 128, 192);
+    copy_ch(n, n->e2, n->cat2, 2, 64, 64, 0, 192, 128);
+    conv(n, 8, n->cat2, n->d2a, 2);
+    conv(n, 9, n->d2a, n->d2, 2);
+    up_fwd(n, n->d2, n->cat1, 1, 64, 96);
+    copy_ch(n, n->e1, n->cat1, 1, 32, 32, 0, 96, 64);
+    conv(n, 10, n->cat1, n->d1a, 1);
+    conv(n, 11, n->d1a, n->d1, 1);
+    conv(n, 12, n->d1, n->out, 1, true);
+    return LM_OK;
+}
+
+// Reverse pass from n->gout (gradient of the head's output); accumulates
+// the parameter gradients.
+void backward(lm_unet* n) {
+    conv_back(n, 12, n->gout, n->d1, nullptr, n->gX1, 1);
+    conv_back(n, 11, n->gX1, n->d1a, n->d1, n->gY1, 1);
+    conv_back(n, 10, n->gY1, n->cat1, n->d1a, n->gcat1, 1);
+    copy_ch(n, n->gcat1, n->ge1, 1, 32, 96, 64, 32, 0);
+    up_bwd(n, n->gcat1, n->gX2, 2, 64, 96);
+    conv_back(n, 9, n->gX2, n->d2a, n->d2, n->gY2, 2);
+    conv_back(n, 8, n->gY2, n->cat2, n->d2a, n->gcat2, 2);
+    copy_ch(n, n->gcat2, n->ge2, 2, 64, 192, 128, 64, 0);
+    up_bwd(n, n->gcat2, n->gX3, 3, 128, 192);
+    conv_back(n, 7, n->gX3, n->e3a, n->e3, n->gY3, 3);
+    conv_back(n, 6, n->gY3, n->p2, n->e3a, n->gX3, 3);      // dp2 (64 ch)
+    pool_bwd(n, n->gX3, n->ge2, 2, 64, 1);
+    conv_back(n, 5, n->ge2, n->e2a, n->e2, n->gX2, 2);
+    conv_back(n, 4, n->gX2, n->p1, n->e2a, n->gY2, 2);      // dp1 (32 ch)
+    pool_bwd(n, n->gY2, n->ge1, 1, 32, 1);
+    conv_back(n, 3, n->ge1, n->e1a, n->e1, n->gX1, 1);
+    conv_back(n, 2, n->gX1, n->p0, n->e1a, n->gY1, 1);      // dp0 (16 ch)
+    pool_bwd(n, n->gY1, n->gA0, 0, 16, 0);
+    conv_back(n, 1, n->gA0, n->e0a, n->e0, n->gB0, 0);
+    conv_back(n, 0, n->gB0, n->x0, n->e0a, nullptr, 0);
+}
+
+void repack(lm_unet* n) {
+    for (auto& L : n->layer) {
+        const long long cnt = (long long)L.cp * 27 * L.cin;
+        k_pack_weights<<<blocks(cnt), 256, 0, n->stream>>>(n->master + L.w_off,
+                                                           L.w, L.wt, L.cin, L.cp);
+    }
+}
+
+int check_vol(const lm_unet* n, const lm_volume* v) {
+    if (!v || !v->data) return fail(LM_EINVAL, "NULL volume");
+    if (v->D != n->D || v->H != n->H || v->W != n->W)
+        return fail(LM_EINVAL, "volume is %dx%dx%d, the network takes %dx%dx%d",
+                    v->D, v->H, v->W, n->D, n->H, n->W);
+    if (v->dtype != LM_F32 && v->dtype != LM_BF16)
+        return fail(LM_EINVAL, "unknown dtype %d", v->dtype);
+    return LM_OK;
+}
+
+// host packed [cout][cin][27] + [cout]  <->  internal [cp][27][cin] + [cp]
+void host_to_internal(const lm_unet* n, const float* h, std::vector<float>& o) {
+    o.assign((size_t)n->nflat, 0.f);
+    size_t k = 0;
+    for (const auto& L : n->layer) {
+        for (int co = 0; co < L.cout; ++co)
+            for (int ci = 0; ci < L.cin; ++ci)
+                for (int t = 0; t < 27; ++t)
+                    o[L.w_off + ((size_t)co * 27 + t) * L.cin + ci] = h[k++];
+        for (int co = 0; co < L.cout; ++co) o[L.b_off + co] = h[k++];
+    }
+}
+void internal_to_host(const lm_unet* n, const std::vector<float>& o, float* h) {
+    size_t k = 0;
+    for (const auto& L : n->layer) {
+        for (int co = 0; co < L.cout; ++co)
+            for (int ci = 0; ci < L.cin; ++ci)
+                for (int t = 0; t < 27; ++t)
+                    h[k++] = o[L.w_off + ((size_t)co * 27 + t) * L.cin + ci];
+        for (int co = 0; co < L.cout; ++co) h[k++] = o[L.b_off + co];
+    }
+}
+
+long long packed_count() {
+    long long c = 0;
+    for (const auto& L : kLayers) c += 27LL * L.cin * L.cout + L.cout;
+    return c;
+}
+
+}  // namespace
+
+extern "C" int lm_unet_shapes(int* cin, int* cout, long long* nparams) {
+    for (int i = 0; i < LM_UNET_LAYERS; ++i) {
+        if (cin) cin[i] = kLayers[i].cin;
+        if (cout) cout[i] = kLayers[i].cout;
+    }
+    if (nparams) *nparams = packed_count();
+    return LM_OK;
+}
+
+extern "C" int lm_unet_create(lm_unet** out, int D, int H, int W,
+                              const float* init, void* stream) {
+    if (!out) return fail(LM_EINVAL, "NULL out-pointer");
+    *out = nullptr;
+    if (!init) return fail(LM_EINVAL, "initial weights are NULL");
+    if (D < 8 || H < 8 || W < 8 || D % 8 || H % 8 || W % 8 || D > 512 ||
+        H > 512 || W > 512)
+        return fail(LM_EINVAL, "sizes must be multiples of 8 in [8, 512]");
+    auto n = new lm_unet();
+    n->D = D;
+    n->H = H;
+    n->W = W;
+    n->stream = (cudaStream_t)stream;
+    long long off = 0;
+    for (int i = 0; i < LM_UNET_LAYERS; ++i) {
+        auto& L = n->layer[i];
+        L.cin = kLayers[i].cin;
+        L.cout = kLayers[i].cout;
+        L.cp = padded(L.cout);
+        L.act = kLayers[i].act;
+        L.w_off = off;
+        off += ((long long)L.cp * 27 * L.cin + 3) / 4 * 4;
+        L.b_off = off;
+        off += (L.cp + 3) / 4 * 4;
+    }
+    n->nflat = off;
+    int rc;
+    auto A = [&](bf16** p, int l, int C) { return n->alloc(p, (size_t)n->Vl(l) * C); };
+    if ((rc = n->alloc(&n->master, off)) || (rc = n->alloc(&n->grad, off)) ||
+        (rc = n->alloc(&n->m, off)) || (rc = n->alloc(&n->v, off)) ||
+        (rc = n->alloc(&n->dloss, 1)) ||
+        (rc = A(&n->x0, 0, 2)) || (rc = A(&n->e0a, 0, 16)) || (rc = A(&n->e0, 0, 16)) ||
+        (rc = A(&n->p0, 1, 16)) || (rc = A(&n->e1a, 1, 32)) || (rc = A(&n->e1, 1, 32)) ||
+        (rc = A(&n->p1, 2, 32)) || (rc = A(&n->e2a, 2, 64)) || (rc = A(&n->e2, 2, 64)) ||
+        (rc = A(&n->p2, 3, 64)) || (rc = A(&n->e3a, 3, 128)) || (rc = A(&n->e3, 3, 128)) ||
+        (rc = A(&n->cat2, 2, 192)) || (rc = A(&n->d2a, 2, 64)) || (rc = A(&n->d2, 2, 64)) ||
+        (rc = A(&n->cat1, 1, 96)) || (rc = A(&n->d1a, 1, 32)) || (rc = A(&n->d1, 1, 32)) ||
+        (rc = n->alloc(&n->out, (size_t)n->Vl(1) * 16)) ||
+        (rc = A(&n->gA0, 0, 16)) || (rc = A(&n->gB0, 0, 16)) ||
+        (rc = A(&n->gcat1, 1, 96)) || (rc = A(&n->gX1, 1, 32)) ||
+        (rc = A(&n->gY1, 1, 32)) || (rc = A(&n->ge1, 1, 32)) ||
+        (rc = A(&n->gout, 1, 16)) || (rc = A(&n->gcat2, 2, 192)) ||
+        (rc = A(&n->gX2, 2, 64)) || (rc = A(&n->gY2, 2, 64)) ||
+        (rc = A(&n->ge2, 2, 64)) || (rc = A(&n->gX3, 3, 128)) ||
+        (rc = A(&n->gY3, 3, 128))) {
+        delete n;
+        return rc;
+    }
+    for (auto& L : n->layer) {
+        const size_t cnt = (size_t)L.cp * 27 * L.cin;
+        if ((rc = n->alloc(&L.w, cnt)) || (rc = n->alloc(&L.wt, cnt))) {
+            delete n;
+            return rc;
+        }
+    }
+    if (cudaMallocHost(&n->hloss, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        delete n;
+        return fail(LM_ENOMEM, "pinned host allocation failed");
+    }
+    std::vector<float> h;
+    host_to_internal(n, init, h);
+    cudaError_t e = cudaMemcpy(n->master, h.data(), off * sizeof(float),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, off * sizeof(float), n->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, off * sizeof(float), n->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->grad, 0, off * sizeof(float), n->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete n;
+        return fail(LM_ECUDA, "weight upload failed: %s", cudaGetErrorString(e));
+    }
+    repack(n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        delete n;
+        return fail(LM_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    *out = n;
+    return LM_OK;
+}
+
+extern "C" void lm_unet_destroy(lm_unet* n) {
+    if (!n) return;
+    cudaStreamSynchronize(n->stream);
+    delete n;
+}
+
+extern "C" int lm_unet_forward(lm_unet* n, const lm_volume* F,
+                               const lm_volume* M, float* u_half) {
+    if (!n || !u_half) return fail(LM_EINVAL, "NULL argument");
+    int rc;
+    if ((rc = check_vol(n, F)) || (rc = check_vol(n, M))) return rc;
+    if (F->dtype != M->dtype) return fail(LM_EINVAL, "fixed and moving dtypes differ");
+    forward(n, F, M);
+    const long long V1 = n->Vl(1);
+    k_out_field<<<blocks(V1), 256, 0, n->stream>>>(n->out, u_half, V1, 16);
+    UN_CK(cudaGetLastError());
+    return LM_OK;
+}
+
+extern "C" int lm_unet_train_step(lm_unet* n, int np, const lm_volume* F,
+                                  const lm_volume* M, const float* const* tgt,
+                                  float lr, double* loss) {
+    if (!n || !F || !M || !tgt || np < 1) return fail(LM_EINVAL, "bad argument");
+    int rc;
+    for (int i = 0; i < np; ++i) {
+        if ((rc = check_vol(n, &F[i])) || (rc = check_vol(n, &M[i]))) return rc;
+        if (F[i].dtype != M[i].dtype)
+            return fail(LM_EINVAL, "fixed and moving dtypes differ (pair %d)", i);
+        if (!tgt[i]) return fail(LM_EINVAL, "target %d is NULL", i);
+    }
+    cudaStream_t s = n->stream;
+    UN_CK(cudaMemsetAsync(n->grad, 0, n->nflat * sizeof(float), s));
+    UN_CK(cudaMemsetAsync(n->dloss, 0, sizeof(double), s));
+    const long long V1 = n->Vl(1);
+    const float scale = (float)(1.0 / (3.0 * (double)V1 * np));
+    for (int i = 0; i < np; ++i) {
+        forward(n, &F[i], &M[i]);
+        k_mse<<<blocks(V1), 256, 0, s>>>(n->out, tgt[i], n->gout, V1, 16, scale,
+                                         n->dloss);
+        backward(n);
+    }
+    n->t += 1;
+    const float bc1 = (float)(1.0 - pow(0.9, n->t));
+    const float bc2 = (float)(1.0 - pow(0.999, n->t));
+    k_adam<<<blocks(n->nflat), 256, 0, s>>>(n->master, n->grad, n->m, n->v,
+                                             n->nflat, lr, bc1, bc2);
+    repack(n);
+    UN_CK(cudaGetLastError());
+    if (loss) {
+        UN_CK(cudaMemcpyAsync(n->hloss, n->dloss, sizeof(double),
+                              cudaMemcpyDeviceToHost, s));
+        UN_CK(cudaStreamSynchronize(s));
+        *loss = *n->hloss / (3.0 * (double)V1 * np);
+    }
+    return LM_OK;
+}
+
+static int fetch(lm_unet* n, const float* src, float* host) {
+    std::vector<float> o((size_t)n->nflat);
+    UN_CK(cudaStreamSynchronize(n->stream));
+    UN_CK(cudaMemcpy(o.data(), src, n->nflat * sizeof(float), cudaMemcpyDeviceToHost));
+    internal_to_host(n, o, host);
+    return LM_OK;
+}
+
+extern "C" int lm_unet_get_weights(lm_unet* n, float* host) {
+    if (!n || !host) return fail(LM_EINVAL, "NULL argument");
+    return fetch(n, n->master, host);
+}
+
+extern "C" int lm_unet_get_grads(lm_unet* n, float* host) {
+    if (!n || !host) return fail(LM_EINVAL, "NULL argument");
+    return fetch(n, n->grad, host);
+}
+
+extern "C" int lm_conv3d_forward(int D, int H, int W, int cin, int cout,
+                                 const void* x, const void* w, const float* bias,
+                                 int act, float* y, void* stream) {
+    if (!x || !w || !y) return fail(LM_EINVAL, "NULL argument");
+    if (D < 1 || H < 1 || W < 1 || !conv_shape_ok(cin, cout))
+        return fail(LM_EINVAL, "unsupported convolution shape");
+    conv_forward((const bf16*)x, (const bf16*)w, bias, y, true, D, H, W, cin, cout,
+                 act ? 1 : 0, (cudaStream_t)stream);
+    UN_CK(cudaGetLastError());
+    return LM_OK;
+}
+
+extern "C" int lm_conv3d_backward(int D, int H, int W, int cin, int cout,
+                                  const void* x, const void* w, const void* dy,
+                                  void* dx, float* dw, float* db, void* stream) {
+    if (!x || !w || !dy || !dw) return fail(LM_EINVAL, "NULL argument");
+    if (D < 1 || H < 1 || W < 1 || !conv_shape_ok(cin, cout))
+        return fail(LM_EINVAL, "unsupported convolution shape");
+    if (dx && cin == 2)
+        return fail(LM_EUNSUPPORTED, "no data gradient for 2 input channels");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long V = (long long)D * H * W;
+    conv_wgrad((const bf16*)x, (const bf16*)dy, dw, D, H, W, cin, cout, s);
+    if (db) bias_grad((const bf16*)dy, db, V, cout, s);
+    if (dx) {
+        const long long cnt = (long long)cout * 27 * cin;
+        bf16* wt = nullptr;
+        UN_CK(cudaMallocAsync((void**)&wt, cnt * sizeof(bf16) + 16, s));
+        // w is bfloat16 already: widen through a float copy is not needed;
+        // transpose directly
+        k_pack_wt_bf16<<<blocks(cnt), 256, 0, s>>>((const bf16*)w, wt, cin, cout);
+        conv_forward((const bf16*)dy, wt, nullptr, dx, false, D, H, W, cout, cin, 0, s);
+        UN_CK(cudaFreeAsync(wt, s));
+    }
+    UN_CK(cudaGetLastError());
+    return LM_OK;
+}

@@ -111,12 +111,24 @@ def load():
         "lm_batch_iterate": [V, ctypes.POINTER(V), I,
                              ctypes.POINTER(StepInfo)],
         "lm_batch_set_targets": [V, ctypes.POINTER(D)],
+        "lm_field_resample": [V, I, I, I, I, V, I, I, I, I, V],
         "lm_batch_register": [V, ctypes.POINTER(Schedule), ctypes.POINTER(V),
                               ctypes.POINTER(Report)],
         "lm_register_batch": [I, ctypes.POINTER(Volume), ctypes.POINTER(Volume),
                               ctypes.POINTER(V), ctypes.POINTER(Params),
                               ctypes.POINTER(Schedule), V,
                               ctypes.POINTER(Report)],
+        "lm_unet_shapes": [ctypes.POINTER(I), ctypes.POINTER(I),
+                           ctypes.POINTER(ctypes.c_longlong)],
+        "lm_unet_create": [ctypes.POINTER(V), I, I, I, V, V],
+        "lm_unet_forward": [V, ctypes.POINTER(Volume), ctypes.POINTER(Volume), V],
+        "lm_unet_train_step": [V, I, ctypes.POINTER(Volume),
+                               ctypes.POINTER(Volume), ctypes.POINTER(V),
+                               ctypes.c_float, ctypes.POINTER(D)],
+        "lm_unet_get_weights": [V, V],
+        "lm_unet_get_grads": [V, V],
+        "lm_conv3d_forward": [I, I, I, I, I, V, V, V, I, V, V],
+        "lm_conv3d_backward": [I, I, I, I, I, V, V, V, V, V, V, V],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -126,6 +138,8 @@ def load():
     lib.lm_destroy.restype = None
     lib.lm_batch_destroy.argtypes = [V]
     lib.lm_batch_destroy.restype = None
+    lib.lm_unet_destroy.argtypes = [V]
+    lib.lm_unet_destroy.restype = None
     lib.lm_strerror.argtypes = [I]
     lib.lm_strerror.restype = ctypes.c_char_p
     lib.lm_last_error.argtypes = []
@@ -369,6 +383,16 @@ def lm_batch_set_targets(b: Batch, targets=None):
     _check(load().lm_batch_set_targets(b.handle, arr), "lm_batch_set_targets")
 
 
+def lm_field_resample(src, fa, dst, fb, stream=None):
+    """dst (3, Db, Hb, Wb) of pyramid factor fb from src (3, Da, Ha, Wa) of
+    factor fa, as between lm_register's levels."""
+    _, Da, Ha, Wa = src.shape
+    _, Db, Hb, Wb = dst.shape
+    _check(load().lm_field_resample(_field_ptr(src), Da, Ha, Wa, int(fa),
+                                    _field_ptr(dst), Db, Hb, Wb, int(fb),
+                                    _stream_handle(stream)), "lm_field_resample")
+
+
 def lm_batch_register(b: Batch, levels, us):
     s = _schedule(levels)
     reps = (Report * len(b))()
@@ -421,5 +445,142 @@ EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_set_state", "lm_register", "lm_state_save", "lm_state_load",
             "lm_time_passes", "lm_batch_init", "lm_batch_destroy",
             "lm_batch_eval", "lm_batch_reset", "lm_batch_iterate",
-            "lm_batch_set_targets", "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
-            "lm_strerror", "lm_last_error")
+            "lm_batch_set_targets", "lm_field_resample", "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
+            "lm_strerror", "lm_last_error",
+            "lm_unet_shapes", "lm_unet_create", "lm_unet_destroy",
+            "lm_unet_forward", "lm_unet_train_step", "lm_unet_get_weights",
+            "lm_unet_get_grads", "lm_conv3d_forward", "lm_conv3d_backward")
+
+
+# ---------------------------------------------------------------------------
+# Learned warm start (include/lmunet.h)
+# ---------------------------------------------------------------------------
+LM_UNET_LAYERS = 13
+
+
+def lm_unet_shapes():
+    """([(cin, cout)] of the 13 convolutions, packed parameter count)."""
+    cin = (ctypes.c_int * LM_UNET_LAYERS)()
+    cout = (ctypes.c_int * LM_UNET_LAYERS)()
+    n = ctypes.c_longlong()
+    _check(load().lm_unet_shapes(cin, cout, ctypes.byref(n)), "lm_unet_shapes")
+    return [(cin[i], cout[i]) for i in range(LM_UNET_LAYERS)], n.value
+
+
+def pack_weights(params):
+    """[(w (cout, cin, 3, 3, 3), b (cout,))] -> packed float32 host array."""
+    import numpy as np
+    parts = []
+    for w, b in params:
+        parts.append(np.asarray(w, np.float32).reshape(-1))
+        parts.append(np.asarray(b, np.float32).reshape(-1))
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
+def unpack_weights(flat):
+    import numpy as np
+    shapes, _ = lm_unet_shapes()
+    out, k = [], 0
+    for cin, cout in shapes:
+        nw = cout * cin * 27
+        w = np.asarray(flat[k:k + nw]).reshape(cout, cin, 3, 3, 3)
+        k += nw
+        out.append((w, np.asarray(flat[k:k + cout])))
+        k += cout
+    return out
+
+
+class UNet:
+    """Owns an lm_unet handle."""
+
+    def __init__(self, handle, shape, stream):
+        self.handle = handle
+        self.shape = tuple(shape)
+        self.stream = stream
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.lm_unet_destroy(h)
+
+
+def lm_unet_create(shape, params, stream=None):
+    import numpy as np
+    flat = pack_weights(params)
+    _, n = lm_unet_shapes()
+    if flat.size != n:
+        raise ValueError(f"expected {n} packed parameters, got {flat.size}")
+    h = ctypes.c_void_p()
+    D, H, W = shape
+    _check(load().lm_unet_create(ctypes.byref(h), int(D), int(H), int(W),
+                                 flat.ctypes.data_as(ctypes.c_void_p),
+                                 _stream_handle(stream)), "lm_unet_create")
+    return UNet(h, shape, stream)
+
+
+def lm_unet_destroy(net: UNet):
+    h, net.handle = net.handle, None
+    if h:
+        load().lm_unet_destroy(h)
+
+
+def lm_unet_forward(net: UNet, fixed, moving, u_half):
+    vf, vm = _volume(fixed), _volume(moving)
+    _check(load().lm_unet_forward(net.handle, ctypes.byref(vf), ctypes.byref(vm),
+                                  _field_ptr(u_half)), "lm_unet_forward")
+
+
+def lm_unet_train_step(net: UNet, fixed, moving, targets, lr, loss=True):
+    n = len(fixed)
+    vf = (Volume * n)(*[_volume(t) for t in fixed])
+    vm = (Volume * n)(*[_volume(t) for t in moving])
+    tp = _ptr_array(targets)
+    L = ctypes.c_double() if loss else None
+    _check(load().lm_unet_train_step(net.handle, n, vf, vm, tp,
+                                     ctypes.c_float(lr),
+                                     ctypes.byref(L) if L is not None else None),
+           "lm_unet_train_step")
+    return L.value if L is not None else None
+
+
+def lm_unet_get_weights(net: UNet):
+    import numpy as np
+    _, n = lm_unet_shapes()
+    out = np.empty(n, np.float32)
+    _check(load().lm_unet_get_weights(net.handle,
+                                      out.ctypes.data_as(ctypes.c_void_p)),
+           "lm_unet_get_weights")
+    return unpack_weights(out)
+
+
+def lm_unet_get_grads(net: UNet):
+    import numpy as np
+    _, n = lm_unet_shapes()
+    out = np.empty(n, np.float32)
+    _check(load().lm_unet_get_grads(net.handle,
+                                    out.ctypes.data_as(ctypes.c_void_p)),
+           "lm_unet_get_grads")
+    return unpack_weights(out)
+
+
+def lm_conv3d_forward(x, w, bias, act, y, stream=None):
+    """x bf16 (D, H, W, cin), w bf16 (cout, 27, cin), bias f32 (cout,) or
+    None, y f32 (D, H, W, cout) (all CUDA tensors)."""
+    D, H, W, cin = x.shape
+    cout = w.shape[0]
+    _check(load().lm_conv3d_forward(
+        D, H, W, cin, cout, ctypes.c_void_p(x.data_ptr()),
+        ctypes.c_void_p(w.data_ptr()),
+        ctypes.c_void_p(bias.data_ptr()) if bias is not None else None,
+        int(act), ctypes.c_void_p(y.data_ptr()), _stream_handle(stream)),
+        "lm_conv3d_forward")
+
+
+def lm_conv3d_backward(x, w, dy, dx, dw, db, stream=None):
+    D, H, W, cin = x.shape
+    cout = w.shape[0]
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    _check(load().lm_conv3d_backward(D, H, W, cin, cout, p(x), p(w), p(dy),
+                                     p(dx), p(dw), p(db),
+                                     _stream_handle(stream)),
+           "lm_conv3d_backward")

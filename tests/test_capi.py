@@ -1,5 +1,5 @@
 """C ABI checks that need no GPU: the library loads, exports every symbol
-declared in include/lmreg.h, and validates arguments on the host before any
+declared in include/*.h, and validates arguments on the host before any
 CUDA call."""
 import ctypes
 import math
@@ -9,7 +9,9 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "lmreg.h")
+HEADERS = [os.path.join(ROOT, "include", h)
+           for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -20,15 +22,20 @@ def lib():
 
 
 def _declared():
-    with open(HEADER) as f:
-        text = f.read()
-    return sorted(set(re.findall(r"LM_API\s+[\w\s\*]*?\b(lm_\w+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        with open(h) as f:
+            names |= set(re.findall(r"LM_API\s+[\w\s\*]*?\b(lm_\w+)\s*\(",
+                                    f.read()))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("lm_init", "lm_step", "lm_register", "lm_destroy",
-              "lm_strerror", "lm_state_save", "lm_state_load"):
+              "lm_strerror", "lm_state_save", "lm_state_load",
+              "lm_register_batch", "lm_unet_create", "lm_unet_forward",
+              "lm_unet_train_step"):
         assert n in names
 
 
@@ -103,3 +110,25 @@ def test_null_arguments(lib):
     assert lib.lm_step(None, None, None) == lmreg.LM_EINVAL
     assert lib.lm_register(None, None, None, None) == lmreg.LM_EINVAL
     lib.lm_destroy(None)
+
+
+def test_unet_shapes_match_the_oracle(lib):
+    from oracle import unet as U
+    from paper_2603_19371_gb300 import lmreg
+    shapes, n = lmreg.lm_unet_shapes()
+    assert shapes == [(ci, co) for ci, co, _ in U.LAYERS]
+    assert n == sum(27 * ci * co + co for ci, co, _ in U.LAYERS)
+
+
+def test_unet_create_validates_sizes_on_the_host(lib):
+    from paper_2603_19371_gb300 import lmreg
+    h = ctypes.c_void_p()
+    w = (ctypes.c_float * 4)()
+    # not a multiple of 8
+    assert lib.lm_unet_create(ctypes.byref(h), 12, 16, 16, w, None) == lmreg.LM_EINVAL
+    # no weights
+    assert lib.lm_unet_create(ctypes.byref(h), 16, 16, 16, None, None) == lmreg.LM_EINVAL
+    assert not h.value
+    # unsupported convolution shapes fail before any CUDA call
+    assert lib.lm_conv3d_forward(4, 4, 4, 3, 16, w, w, None, 0, w, None) == lmreg.LM_EINVAL
+    assert lib.lm_conv3d_forward(4, 4, 4, 16, 8, w, w, None, 0, w, None) == lmreg.LM_EINVAL

@@ -331,3 +331,21 @@ def test_full_size_eval_and_step(P, oracle_mod):
     if info.accepted and info.retries == 0:
         err = np.abs(u.cpu().numpy().astype(np.float64) - u1)
         assert err.max() <= TOL_U, _worst(err)
+
+
+@pytest.mark.parametrize("fa,shape_a,fb,shape_b", [
+    (2, (12, 10, 14), 1, (24, 20, 28)),     # up one level (odd-free sizes)
+    (1, (25, 21, 29), 2, (12, 10, 14)),     # down one level, ragged
+    (4, (5, 6, 7), 1, (21, 25, 29)),        # two levels up, ragged fine size
+])
+def test_field_resample_matches_oracle(P, oracle_mod, fa, shape_a, fb, shape_b):
+    import torch
+    import synth
+    ua = synth.random_field(shape_a, seed=3, scale=2.5)
+    ref = oracle_mod.resample_field(ua.astype(np.float64), fa, shape_b, fb)
+    src = torch.from_numpy(ua).cuda()
+    dst = torch.empty((3,) + shape_b, device="cuda")
+    P.lm_field_resample(src, fa, dst, fb)
+    torch.cuda.synchronize()
+    err = np.abs(dst.cpu().numpy() - ref).max()
+    assert err <= 1e-5 * max(1.0, np.abs(ref).max()), err
