@@ -57,7 +57,8 @@ extern "C" {
 #define LM_F32  0  /* float32 images */
 #define LM_BF16 1  /* bfloat16 images, sampled and accumulated in float32 */
 
-/* An image volume. */
+/* An image volume.  At most (2^31 - 1) / 3 voxels (715,827,882, e.g.
+ * 894^3): the kernels index the 3-component fields with 32-bit offsets. */
 typedef struct {
     int D, H, W;        /* depth (z), height (y), width (x); each >= 1 */
     int dtype;          /* LM_F32 or LM_BF16 */

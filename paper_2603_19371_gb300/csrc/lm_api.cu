@@ -114,8 +114,9 @@ int check_volume(const lm_volume* v, const char* name) {
     if (!v) return fail(LM_EINVAL, "%s is NULL", name);
     if (v->D < 1 || v->H < 1 || v->W < 1)
         return fail(LM_EINVAL, "%s has a non-positive dimension", name);
-    if ((long long)v->D * v->H * v->W > (1LL << 31) - 1)
-        return fail(LM_EINVAL, "%s exceeds 2^31 - 1 voxels", name);
+    // fields of 3 V floats are indexed with 32-bit offsets in the kernels
+    if (3LL * v->D * v->H * v->W > (1LL << 31) - 1)
+        return fail(LM_EINVAL, "%s exceeds (2^31 - 1) / 3 voxels", name);
     if (v->dtype != LM_F32 && v->dtype != LM_BF16)
         return fail(LM_EINVAL, "%s has an unknown dtype %d", name, v->dtype);
     if (!v->data) return fail(LM_EINVAL, "%s data is NULL", name);

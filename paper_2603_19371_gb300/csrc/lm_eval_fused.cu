@@ -189,7 +189,9 @@ struct E1Cfg {
     static constexpr int GX = SX + 2 * W, GY = SY + 2 * W;  // gather plane
     static constexpr int GXP = (GX + 3) / 4 * 4;            // padded stride
     static constexpr int NXU = GY * (SX / 2);   // x-pass units (2 outputs)
-    static constexpr int NX2U = 3 * SY * (TX / 2);
+    // box-2 x units: four outputs each when the tile width allows
+    static constexpr int XW = TX % 4 == 0 ? 4 : 2;
+    static constexpr int NX2U = 3 * SY * (TX / XW);
     // shared memory (bytes), 16-byte aligned sections
     static constexpr int B_GQ = 2 * GY * GXP * 4;     // F', J' gather plane
     static constexpr int B_X32 = GY * SX * 4;         // x-sums of J'
@@ -272,13 +274,14 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
     for (int k = 0; k < NX2S; ++k) {
         int uidx = tid + k * NT;
-        x2_row[k] = uidx < C::NX2U ? uidx / (TX / 2) : -1;
-        x2_p[k] = uidx - (uidx / (TX / 2)) * (TX / 2);
+        x2_row[k] = uidx < C::NX2U ? uidx / (TX / C::XW) : -1;
+        x2_p[k] = uidx - (uidx / (TX / C::XW)) * (TX / C::XW);
     }
     const bool has_o = tid < TX * TY;
     const int ox = has_o ? tid % TX : 0, oy = has_o ? tid / TX : 0;
 
     double lacc = 0.0;
+    float lacc_f = 0.f;   // at most K non-negative terms, then added to lacc
     bool bad = false;
     const int e1_cx = P.e1_cx;
     const long long total = (long long)P.e1_cx * P.e1_cy * g.nz;
@@ -460,13 +463,15 @@ __global__ void __launch_bounds__(NT, 1)
                         float BC = __fmul_rn(B, Cm), AA = __fmul_rn(A, A);
                         float N = AA + c.eps_nr;
                         float D = BC + c.eps_dr;
-                        float rD = 1.f / D;
+                        // D >= eps_dr > 0: the approximate reciprocal
+                        // (about 1 ulp) is safe and far cheaper than an
+                        // IEEE division
+                        float rD = __fdividef(1.f, D);
                         av = 2.f * A * rD;
                         bv = -N * B * rD * rD;
                         cv = -av * mF - 2.f * bv * mJ;
                         if (s_out && cz >= z0 && cz < z1)
-                            lacc += (double)(((BC - AA) + (c.eps_dr - c.eps_nr)) *
-                                             rD);
+                            lacc_f += ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD;
                     }
                     Ab[sy * SX + sx] = av;
                     Ab[SY * SX + sy * SX + sx] = bv;
@@ -474,21 +479,29 @@ __global__ void __launch_bounds__(NT, 1)
                 }
                 __syncthreads();
                 if (coef_valid) {
-                    // (4) box of (a, b, c) along x: two outputs per unit
+                    // (4) box of (a, b, c) along x: XW outputs per unit
+                    //     (the later ones slide the window by one)
 #pragma unroll
                     for (int k = 0; k < NX2S; ++k) {
                         if (x2_row[k] < 0) continue;
-                        const float* r = Ab + x2_row[k] * SX + 2 * x2_p[k];
-                        float v[K + 1];
+                        constexpr int XW = C::XW;
+                        const float* r = Ab + x2_row[k] * SX + XW * x2_p[k];
+                        float v[K + XW - 1];
 #pragma unroll
-                        for (int o = 0; o < K + 1; ++o) v[o] = r[o];
-                        float s0 = 0.f, s1 = 0.f;
+                        for (int o = 0; o < K + XW - 1; ++o) v[o] = r[o];
+                        float s0 = 0.f;
 #pragma unroll
                         for (int o = 0; o < K; ++o) s0 += v[o];
-#pragma unroll
-                        for (int o = 1; o < K + 1; ++o) s1 += v[o];
-                        float2* dst = (float2*)(Ax + x2_row[k] * TX + 2 * x2_p[k]);
-                        *dst = make_float2(s0, s1);
+                        const float s1 = (s0 - v[0]) + v[K];
+                        if constexpr (XW == 4) {
+                            const float s2 = (s1 - v[1]) + v[K + 1];
+                            const float s3 = (s2 - v[2]) + v[K + 2];
+                            *(float4*)(Ax + x2_row[k] * TX + 4 * x2_p[k]) =
+                                make_float4(s0, s1, s2, s3);
+                        } else {
+                            *(float2*)(Ax + x2_row[k] * TX + 2 * x2_p[k]) =
+                                make_float2(s0, s1);
+                        }
                     }
                     __syncthreads();
                     // (5) along y into the register ring, along z, dL/dJ at
@@ -528,6 +541,8 @@ __global__ void __launch_bounds__(NT, 1)
                 }
                 __syncthreads();
             }
+            lacc += (double)lacc_f;
+            lacc_f = 0.f;
         }
     }
     if (bad) lacc = __longlong_as_double(0x7ff8000000000000LL);   // NaN
@@ -544,32 +559,51 @@ __global__ void __launch_bounds__(NT, 1)
 // ----------------------------------------------------------------------
 // E2
 // ----------------------------------------------------------------------
+// 384 threads: in the y and z passes each thread owns one component of a
+// quad of four adjacent outputs (3 components x 8 quads x 16 rows), so its
+// shared-memory reads are 16-byte vectors and the z window of its quad sits
+// in a register ring.
+constexpr int NT2 = 384;
+
 template <int R>
 struct E2Cfg {
     static constexpr int KG = 2 * R + 1;
     static constexpr int TX = PLANE_X, TY = PLANE_Y;
     static constexpr int RX = TX + 2 * R, RY = TY + 2 * R;
     static constexpr int RXP = (RX + 3) / 4 * 4;
-    static constexpr int NXU = 3 * RY * (TX / 4);   // x-pass units (4 outputs)
-    // g_raw plane, x-smoothed plane, z ring of xy-smoothed planes
-    static constexpr int bytes =
-        (3 * RY * RXP + 3 * RY * TX + KG * 3 * TX * TY) * 4;
+    static constexpr int NQ = TX / 4;               // quads per row
+    static constexpr int NXU = 3 * RY * NQ;         // x-pass units (4 outputs)
+    // g_raw plane with halo, x-smoothed plane, xyz-smoothed plane
+    static constexpr int bytes = (3 * RY * RXP + 3 * RY * TX + 3 * TY * TX) * 4;
 };
 
+__device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z),
+                       fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 f4_add(float4 x, float4 y) {
+    return make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+}
+__device__ __forceinline__ float4 f4_mul(float a, float4 x) {
+    return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
+}
+
 template <int R, typename T>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT2, 2)
     k_e2(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
          Taps tp, float* __restrict__ g2_part) {
     using C = E2Cfg<R>;
     constexpr int KG = C::KG, RX = C::RX, RY = C::RY, RXP = C::RXP;
-    constexpr int TX = C::TX, TY = C::TY;
-    constexpr int NRS = (RX * RY + NT - 1) / NT;    // halo-plane slots
-    constexpr int NXS = (C::NXU + NT - 1) / NT;     // x-pass slots
+    constexpr int TX = C::TX, TY = C::TY, NQ = C::NQ;
+    constexpr int NRS = (3 * RX * RY + NT2 - 1) / NT2;   // halo-plane slots
+    constexpr int NXS = (C::NXU + NT2 - 1) / NT2;        // x-pass slots
+    constexpr int NVS = (TX * TY + NT2 - 1) / NT2;       // |g|^2 slots
+    static_assert(3 * NQ * TY == NT2, "one quad-component per thread");
     extern __shared__ __align__(16) unsigned char smem[];
-    float* Gr = (float*)smem;            // [3][RY][RXP]
-    float* Gx = Gr + 3 * RY * RXP;       // [3][RY][TX]
-    float* Zr = Gx + 3 * RY * TX;        // [KG][3][TY * TX], thread-private
-    __shared__ float red[NT / 32];
+    float* Gr = (float*)smem;              // [3][RY][RXP]
+    float* Gx = Gr + 3 * RY * RXP;         // [3][RY][TX]
+    float* Gz = Gx + 3 * RY * TX;          // [3][TY][TX]
+    __shared__ float red[NT2 / 32];
 
     const PairDesc& P = pd[pair_of_block<2>(pd, npairs, blockIdx.x)];
     if (trial_skip(P, mode, attempt)) return;
@@ -578,29 +612,31 @@ __global__ void __launch_bounds__(NT, 2)
     const int tid = threadIdx.x;
     float* __restrict__ gout = eval_g(P, mode);
     const int sxy = g.nx * g.ny;
-    const int ox = tid & (TX - 1), oy = tid / TX;
     // taps stay in the kernel-parameter constant bank (no registers)
     const float* tt = tp.t;
-
-    // packed per-thread slots: halo-plane point (rx | ry << 16) and its
-    // shared-memory index; x-pass unit (smem offsets of input and output)
-    int r_xy[NRS], r_sm[NRS];
+    // y/z role: component q, quad qx of row oy
+    const int q = tid / (NQ * TY);
+    const int oy = (tid - q * NQ * TY) / NQ;
+    const int qx = tid - q * NQ * TY - oy * NQ;
+    // halo slots: shared-memory index of each (component, ry, rx)
+    int r_sm[NRS];
 #pragma unroll
     for (int k = 0; k < NRS; ++k) {
-        int idx = tid + k * NT;
-        int ry = idx / RX, rx = idx - ry * RX;
-        r_xy[k] = rx | (ry << 16);
-        r_sm[k] = idx < RX * RY ? ry * RXP + rx : -1;
+        const int idx = tid + k * NT2;
+        const int cq = idx / (RX * RY), rr = idx - cq * RX * RY;
+        const int ry = rr / RX, rx = rr - ry * RX;
+        r_sm[k] = idx < 3 * RX * RY ? (cq * RY + ry) * RXP + rx : -1;
     }
     int x_in[NXS], x_out[NXS];
 #pragma unroll
     for (int k = 0; k < NXS; ++k) {
-        int uidx = tid + k * NT;
-        int row = uidx / (TX / 4), p = uidx - row * (TX / 4);
-        x_in[k] = uidx < C::NXU ? row * RXP + 4 * p : -1;
+        const int u = tid + k * NT2;
+        const int row = u / NQ, p = u - row * NQ;   // row over 3 RY rows
+        x_in[k] = u < C::NXU ? row * RXP + 4 * p : -1;
         x_out[k] = row * TX + 4 * p;
     }
     float m2 = 0.f;
+    const bool vec_store = (g.nx & 3) == 0;
 
     const int e2_cx = P.e2_cx;
     const long long total = (long long)P.e2_cx * P.e2_cy * g.nz;
@@ -617,28 +653,29 @@ __global__ void __launch_bounds__(NT, 2)
         int r_off[NRS];
 #pragma unroll
         for (int k = 0; k < NRS; ++k) {
-            int x = x0 - R + (r_xy[k] & 0xffff), y = y0 - R + (r_xy[k] >> 16);
-            r_off[k] = (r_sm[k] >= 0 && x >= 0 && x < g.nx && y >= 0 &&
-                        y < g.ny)
-                           ? y * g.nx + x
+            const int idx = tid + k * NT2;
+            const int cq = idx / (RX * RY), rr = idx - cq * RX * RY;
+            const int ry = rr / RX, rx = rr - ry * RX;
+            const int x = x0 - R + rx, y = y0 - R + ry;
+            r_off[k] = (r_sm[k] >= 0 && x >= 0 && x < g.nx && y >= 0 && y < g.ny)
+                           ? cq * (int)g.V + y * g.nx + x
                            : -1;
         }
-        const bool o_in = x0 + ox < g.nx && y0 + oy < g.ny;
-        const int o_off = (y0 + oy) * g.nx + x0 + ox;
+        const int ox = x0 + 4 * qx, oyy = y0 + oy;
+        const bool row_in = oyy < g.ny && ox < g.nx;
+        const int o_off = q * (int)g.V + oyy * g.nx + ox;
         const int s_begin = z0 - R, s_end = z1 + R;
         // g_raw of slice s is loaded one step ahead
-        float pg[NRS][3];
+        float pg[NRS];
         auto load_plane = [&](int sp) {
-            const bool zin_ = sp >= 0 && sp < g.nz;
+            const bool zin = sp >= 0 && sp < g.nz;
 #pragma unroll
-            for (int k = 0; k < NRS; ++k) {
-                const bool in = zin_ && r_off[k] >= 0;
-                const int i = in ? sp * sxy + r_off[k] : 0;
-                pg[k][0] = in ? __ldg(graw + i) : 0.f;
-                pg[k][1] = in ? __ldg(graw + g.V + i) : 0.f;
-                pg[k][2] = in ? __ldg(graw + 2 * g.V + i) : 0.f;
-            }
+            for (int k = 0; k < NRS; ++k)
+                pg[k] = (zin && r_off[k] >= 0) ? __ldg(graw + sp * sxy + r_off[k]) : 0.f;
         };
+        float4 ring[KG];
+#pragma unroll
+        for (int k = 0; k < KG; ++k) ring[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         load_plane(s_begin);
         for (int base = s_begin; base < s_end; base += KG) {
 #pragma unroll
@@ -647,16 +684,9 @@ __global__ void __launch_bounds__(NT, 2)
                 if (s >= s_end) break;
                 const int t = s - s_begin;
                 // (1) g_raw of the tile and its R halo (zero outside)
-                {
 #pragma unroll
-                    for (int k = 0; k < NRS; ++k) {
-                        if (r_sm[k] < 0) continue;
-                        const float g0 = pg[k][0], g1 = pg[k][1], g2 = pg[k][2];
-                        Gr[r_sm[k]] = g0;
-                        Gr[RY * RXP + r_sm[k]] = g1;
-                        Gr[2 * RY * RXP + r_sm[k]] = g2;
-                    }
-                }
+                for (int k = 0; k < NRS; ++k)
+                    if (r_sm[k] >= 0) Gr[r_sm[k]] = pg[k];
                 if (s + 1 < s_end) load_plane(s + 1);
                 __syncthreads();
                 // (2) Gaussian along x: four outputs per unit
@@ -672,46 +702,66 @@ __global__ void __launch_bounds__(NT, 2)
                     for (int e = 0; e < 4; ++e) {
                         float a = tt[R] * v[e + R];
 #pragma unroll
-                        for (int q = 1; q <= R; ++q)
-                            a += tt[R + q] * (v[e + R - q] + v[e + R + q]);
+                        for (int m = 1; m <= R; ++m)
+                            a += tt[R + m] * (v[e + R - m] + v[e + R + m]);
                         out[e] = a;
                     }
-                    *(float4*)(Gx + x_out[k]) =
-                        make_float4(out[0], out[1], out[2], out[3]);
+                    *(float4*)(Gx + x_out[k]) = make_float4(out[0], out[1], out[2], out[3]);
                 }
                 __syncthreads();
-                // (3) along y into the register ring; along z at o = s - R
+                // (3) along y for this thread's quad, into the ring; along
+                //     z at slice o = s - R
+                {
+                    const float* col4 = Gx + (q * RY + oy) * TX + 4 * qx;
+                    float4 a = f4_mul(tt[R], *(const float4*)(col4 + R * TX));
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const float* col = Gx + (q * RY + oy) * TX + ox;
-                    float a = tt[R] * col[R * TX];
-#pragma unroll
-                    for (int k = 1; k <= R; ++k)
-                        a += tt[R + k] * (col[(R - k) * TX] + col[(R + k) * TX]);
-                    Zr[(j * 3 + q) * TX * TY + tid] = a;
+                    for (int m = 1; m <= R; ++m)
+                        a = f4_fma(tt[R + m],
+                                   f4_add(*(const float4*)(col4 + (R - m) * TX),
+                                          *(const float4*)(col4 + (R + m) * TX)),
+                                   a);
+                    ring[j] = a;
                 }
-                if (t >= 2 * R && o_in) {
-                    const int i = (s - R) * sxy + o_off;
-                    float n2 = 0.f;
+                if (t >= 2 * R) {
+                    // slice o + d sits in slot (j + 1 + R + d) mod KG
+                    float4 zv = f4_mul(tt[R], ring[(j + 1 + R) % KG]);
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        // slice o - R + i2 sits in slot (j + 1 + i2) mod KG
-                        const float* zq = Zr + q * TX * TY + tid;
-#define ZR_AT(slot) zq[(slot) * 3 * TX * TY]
-                        float a = tt[R] * ZR_AT((j + 1 + R) % KG);
+                    for (int m = 1; m <= R; ++m)
+                        zv = f4_fma(tt[R + m],
+                                    f4_add(ring[(j + 1 + R - m) % KG],
+                                           ring[(j + 1 + R + m) % KG]),
+                                    zv);
+                    *(float4*)(Gz + (q * TY + oy) * TX + 4 * qx) = zv;
+                    if (row_in) {
+                        float* dst = gout + (s - R) * sxy + o_off;
+                        if (vec_store && ox + 3 < g.nx) {
+                            *(float4*)dst = zv;
+                        } else {
+                            const float e4[4] = {zv.x, zv.y, zv.z, zv.w};
 #pragma unroll
-                        for (int k = 1; k <= R; ++k)
-                            a += tt[R + k] * (ZR_AT((j + 1 + R - k) % KG) +
-                                              ZR_AT((j + 1 + R + k) % KG));
-#undef ZR_AT
-                        gout[q * g.V + i] = a;
-                        n2 += a * a;
+                            for (int e = 0; e < 4; ++e)
+                                if (ox + e < g.nx) dst[e] = e4[e];
+                        }
                     }
-                    m2 = (n2 != n2) ? INFINITY : fmaxf(m2, n2);
                 }
                 __syncthreads();
+                // (4) |g|^2 of the finished voxels (all three components)
+                if (t >= 2 * R) {
+#pragma unroll
+                    for (int k = 0; k < NVS; ++k) {
+                        const int v = tid + k * NT2;
+                        if (v >= TX * TY) continue;
+                        const int vy = v / TX, vx = v - vy * TX;
+                        if (x0 + vx >= g.nx || y0 + vy >= g.ny) continue;
+                        const float a0 = Gz[v], a1 = Gz[TX * TY + v],
+                                    a2 = Gz[2 * TX * TY + v];
+                        const float n2 = a0 * a0 + a1 * a1 + a2 * a2;
+                        m2 = (n2 != n2) ? INFINITY : fmaxf(m2, n2);
+                    }
+                }
             }
         }
+        __syncthreads();   // Gz is rewritten by the next segment
     }
     for (int k = 16; k > 0; k >>= 1)
         m2 = fmaxf(m2, __shfl_down_sync(0xffffffffu, m2, k));
@@ -719,7 +769,7 @@ __global__ void __launch_bounds__(NT, 2)
     __syncthreads();
     if (tid == 0) {
         float v = 0.f;
-        for (int w = 0; w < NT / 32; ++w) v = fmaxf(v, red[w]);
+        for (int w = 0; w < NT2 / 32; ++w) v = fmaxf(v, red[w]);
         g2_part[blockIdx.x] = v;
     }
 }
@@ -886,7 +936,7 @@ int launch_e1(const Batch& b, int mode, int attempt, cudaStream_t s) {
 
 template <int R, typename T>
 int launch_e2(const Batch& b, int mode, int attempt, cudaStream_t s) {
-    k_e2<R, T><<<b.plan.e2_ctas, NT, E2Cfg<R>::bytes, s>>>(
+    k_e2<R, T><<<b.plan.e2_ctas, NT2, E2Cfg<R>::bytes, s>>>(
         b.pd, b.npairs, mode, attempt, b.c.gtaps, b.part.g2max);
     return 1;
 }
