@@ -278,8 +278,9 @@ LM_API int lm_register_batch(int npairs, const lm_volume *fixed,
  * smoothed gradient at u, without a context and without any allocation.
  * Its scratch is one static device array inside the library, sized for at
  * most LM_NOALLOC_MAX_VOXELS voxels (2^19, e.g. 80^3; about 21 MB, held
- * by every GPU that loads the library until the process exits); larger
- * volumes return LM_EINVAL.
+ * by every GPU that loads the library until the process exits), counted
+ * with rows padded to a multiple of 4 voxels; larger volumes return
+ * LM_EINVAL.
  *   fixed, moving: images as for lm_init; p: parameters (NULL = defaults;
  *   only win, eps_nr, eps_dr and sigma_grad matter); u: device field
  *   [3][D][H][W]; g_out: device [3][D][H][W] (written); loss_out: device

@@ -316,7 +316,7 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
         if ((rc = c->dalloc(&d.u1, 3 * V * f4)) ||
             (rc = c->dalloc(&d.g0, 3 * V * f4)) ||
             (rc = c->dalloc(&d.g1, 3 * V * f4)) ||
-            (rc = c->dalloc(&d.graw, 3 * V * f4)) ||
+            (rc = c->dalloc(&d.graw, graw_floats(d.g) * f4)) ||
             (rc = c->dalloc(&d.jq, V * sizeof(int))) ||
             (rc = c->dalloc(&d.dj, 3 * V * f4)) ||
             (rc = c->dalloc(&d.fq, V * sizeof(int))) ||
@@ -329,8 +329,23 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
         d.st = st + i;
         d.qs = qs + i;
         d.target = std::numeric_limits<double>::quiet_NaN();
+        d.gp_w = graw_pitch(d.g.nx);
         d.log = lg + (size_t)i * LOG_CAP;
         d.u0 = nullptr;
+    }
+    // tensor maps of the g_raw buffers (E2 tiles them with TMA)
+    {
+        const int R = make_taps(prm.sigma_grad).R;
+        std::vector<unsigned char> maps((size_t)npairs * 128);
+        unsigned char* dmaps = nullptr;
+        if ((rc = c->dalloc(&dmaps, maps.size())) != LM_OK) return rc;
+        for (int i = 0; i < npairs; ++i) {
+            PairDesc& d = c->hpd[i];
+            if ((rc = encode_graw_map(maps.data() + 128 * i, d.graw, d.g, R)) != LM_OK)
+                return rc;
+            d.tm_graw = dmaps + 128 * i;
+        }
+        LM_CK(cudaMemcpy(dmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
     }
     if (cudaMallocHost(&c->h_st, npairs * sizeof(DevState)) != cudaSuccess ||
         cudaMallocHost(&c->h_eout, npairs * sizeof(EvalOut)) != cudaSuccess ||

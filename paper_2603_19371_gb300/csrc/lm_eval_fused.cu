@@ -29,6 +29,9 @@
 // HBM traffic per voxel: the J pass reads u, M (16 B) and writes Jq, dJ
 // (16 B); E1 reads F', S_F, B, Jq, dJ (28 B) and writes g_raw (12 B); E2
 // reads g_raw (12 B) and writes g (12 B).  Halo re-reads hit L2.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -240,6 +243,8 @@ __global__ void __launch_bounds__(NT, 1)
     const int* __restrict__ jqv = P.jq;
     const float* __restrict__ djv = P.dj;
     float* __restrict__ graw = P.graw;
+    const int gpw = P.gp_w;                                 // g_raw row pitch
+    const long long gcs = (long long)g.nz * g.ny * gpw;     // component stride
     const QScale* __restrict__ qs = P.qs;
     const float inv_V = (float)(1.0 / (double)g.V);
     const int tid = threadIdx.x;
@@ -532,10 +537,11 @@ __global__ void __launch_bounds__(NT, 1)
                                 -inv_V * ((dl[0] * b3[0] +
                                            2.f * dl[TY * TX] * b3[1] + b3[2]) *
                                           c.inv_k3);
-                            const int gi = r * sxy + o_off;
+                            const long long gi = (long long)(r * g.ny + y0 + oy) * gpw +
+                                                 x0 + ox;
                             graw[gi] = dLdJ * dj0;
-                            graw[g.V + gi] = dLdJ * dj1;
-                            graw[2 * g.V + gi] = dLdJ * dj2;
+                            graw[gcs + gi] = dLdJ * dj1;
+                            graw[2 * gcs + gi] = dLdJ * dj2;
                         }
                     }
                 }
@@ -562,20 +568,70 @@ __global__ void __launch_bounds__(NT, 1)
 // 384 threads: in the y and z passes each thread owns one component of a
 // quad of four adjacent outputs (3 components x 8 quads x 16 rows), so its
 // shared-memory reads are 16-byte vectors and the z window of its quad sits
-// in a register ring.
+// in a register ring.  The g_raw plane of each slice (three components
+// with the halo) arrives by one TMA tile load into a ring of E2_NB buffers,
+// issued E2_NB slices ahead and tracked by an mbarrier per buffer.
 constexpr int NT2 = 384;
+constexpr int E2_NB = 4;
 
 template <int R>
 struct E2Cfg {
     static constexpr int KG = 2 * R + 1;
     static constexpr int TX = PLANE_X, TY = PLANE_Y;
-    static constexpr int RX = TX + 2 * R, RY = TY + 2 * R;
-    static constexpr int RXP = (RX + 3) / 4 * 4;
+    // the TMA box starts at x0 - RA, a multiple of 4 floats (16 bytes)
+    static constexpr int RA = (R + 3) / 4 * 4;
+    static constexpr int BX = TX + 2 * RA, BY = TY + 2 * R;
     static constexpr int NQ = TX / 4;               // quads per row
-    static constexpr int NXU = 3 * RY * NQ;         // x-pass units (4 outputs)
-    // g_raw plane with halo, x-smoothed plane, xyz-smoothed plane
-    static constexpr int bytes = (3 * RY * RXP + 3 * RY * TX + 3 * TY * TX) * 4;
+    static constexpr int NXU = 3 * BY * NQ;         // x-pass units (4 outputs)
+    static constexpr int TXB = 3 * BY * BX * 4;     // bytes per TMA tile
+    static constexpr int GRF = (3 * BY * BX + 31) / 32 * 32;   // floats/buffer
+    // g_raw tiles, x-smoothed plane, xyz-smoothed plane (+ alignment)
+    static constexpr int bytes =
+        128 + (E2_NB * GRF + 3 * BY * TX + 3 * TY * TX) * 4;
 };
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)),
+                 "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b,
+                                               unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                     smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b,
+                                              unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within the limit.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+    for (int it = 0; it < (1 << 20); ++it)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* map, int x,
+                                            int y, int z, int c,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_"
+        "tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_u32(bar))
+        : "memory");
+}
 
 __device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 y) {
     return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z),
@@ -593,22 +649,21 @@ __global__ void __launch_bounds__(NT2, 2)
     k_e2(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
          Taps tp, float* __restrict__ g2_part) {
     using C = E2Cfg<R>;
-    constexpr int KG = C::KG, RX = C::RX, RY = C::RY, RXP = C::RXP;
-    constexpr int TX = C::TX, TY = C::TY, NQ = C::NQ;
-    constexpr int NRS = (3 * RX * RY + NT2 - 1) / NT2;   // halo-plane slots
+    constexpr int KG = C::KG, BX = C::BX, BY = C::BY, RA = C::RA;
+    constexpr int TX = C::TX, TY = C::TY, NQ = C::NQ, GRF = C::GRF;
     constexpr int NXS = (C::NXU + NT2 - 1) / NT2;        // x-pass slots
     constexpr int NVS = (TX * TY + NT2 - 1) / NT2;       // |g|^2 slots
     static_assert(3 * NQ * TY == NT2, "one quad-component per thread");
-    extern __shared__ __align__(16) unsigned char smem[];
-    float* Gr = (float*)smem;              // [3][RY][RXP]
-    float* Gx = Gr + 3 * RY * RXP;         // [3][RY][TX]
-    float* Gz = Gx + 3 * RY * TX;          // [3][TY][TX]
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* Gr = (float*)(((size_t)smem_raw + 127) & ~(size_t)127);  // [NB][GRF]
+    float* Gx = Gr + E2_NB * GRF;          // [3][BY][TX]
+    float* Gz = Gx + 3 * BY * TX;          // [3][TY][TX]
+    __shared__ __align__(8) unsigned long long mbar[E2_NB];
     __shared__ float red[NT2 / 32];
 
     const PairDesc& P = pd[pair_of_block<2>(pd, npairs, blockIdx.x)];
     if (trial_skip(P, mode, attempt)) return;
     const Geom g = P.g;
-    const float* __restrict__ graw = P.graw;
     const int tid = threadIdx.x;
     float* __restrict__ gout = eval_g(P, mode);
     const int sxy = g.nx * g.ny;
@@ -618,23 +673,25 @@ __global__ void __launch_bounds__(NT2, 2)
     const int q = tid / (NQ * TY);
     const int oy = (tid - q * NQ * TY) / NQ;
     const int qx = tid - q * NQ * TY - oy * NQ;
-    // halo slots: shared-memory index of each (component, ry, rx)
-    int r_sm[NRS];
-#pragma unroll
-    for (int k = 0; k < NRS; ++k) {
-        const int idx = tid + k * NT2;
-        const int cq = idx / (RX * RY), rr = idx - cq * RX * RY;
-        const int ry = rr / RX, rx = rr - ry * RX;
-        r_sm[k] = idx < 3 * RX * RY ? (cq * RY + ry) * RXP + rx : -1;
-    }
     int x_in[NXS], x_out[NXS];
 #pragma unroll
     for (int k = 0; k < NXS; ++k) {
         const int u = tid + k * NT2;
-        const int row = u / NQ, p = u - row * NQ;   // row over 3 RY rows
-        x_in[k] = u < C::NXU ? row * RXP + 4 * p : -1;
+        const int row = u / NQ, p = u - row * NQ;   // row over 3 BY rows
+        x_in[k] = u < C::NXU ? row * BX + (RA - R) + 4 * p : -1;
         x_out[k] = row * TX + 4 * p;
     }
+    if (tid == 0) {
+        for (int b = 0; b < E2_NB; ++b) mbar_init(&mbar[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(
+                         P.tm_graw)
+                     : "memory");
+    }
+    __syncthreads();
+    unsigned phase = 0;          // bit b: parity of buffer b's next phase
+    bool failed = false;
     float m2 = 0.f;
     const bool vec_store = (g.nx & 3) == 0;
 
@@ -642,7 +699,7 @@ __global__ void __launch_bounds__(NT2, 2)
     const long long total = (long long)P.e2_cx * P.e2_cy * g.nz;
     const Share sh_ = share_of(blockIdx.x - P.e2_cta0, P.e2_ncta, total);
     long long w0 = sh_.lo;
-    while (w0 < sh_.hi) {
+    while (w0 < sh_.hi && !failed) {
         const long long col = w0 / g.nz;
         const int z0 = (int)(w0 - col * g.nz);
         const long long zl = z0 + (sh_.hi - w0);
@@ -650,50 +707,46 @@ __global__ void __launch_bounds__(NT2, 2)
         w0 += z1 - z0;
         const int x0 = (int)(col % e2_cx) * TX;
         const int y0 = (int)(col / e2_cx) * TY;
-        int r_off[NRS];
-#pragma unroll
-        for (int k = 0; k < NRS; ++k) {
-            const int idx = tid + k * NT2;
-            const int cq = idx / (RX * RY), rr = idx - cq * RX * RY;
-            const int ry = rr / RX, rx = rr - ry * RX;
-            const int x = x0 - R + rx, y = y0 - R + ry;
-            r_off[k] = (r_sm[k] >= 0 && x >= 0 && x < g.nx && y >= 0 && y < g.ny)
-                           ? cq * (int)g.V + y * g.nx + x
-                           : -1;
-        }
         const int ox = x0 + 4 * qx, oyy = y0 + oy;
         const bool row_in = oyy < g.ny && ox < g.nx;
         const int o_off = q * (int)g.V + oyy * g.nx + ox;
         const int s_begin = z0 - R, s_end = z1 + R;
-        // g_raw of slice s is loaded one step ahead
-        float pg[NRS];
-        auto load_plane = [&](int sp) {
-            const bool zin = sp >= 0 && sp < g.nz;
-#pragma unroll
-            for (int k = 0; k < NRS; ++k)
-                pg[k] = (zin && r_off[k] >= 0) ? __ldg(graw + sp * sxy + r_off[k]) : 0.f;
-        };
+        // slices outside the volume and the halo outside it read as zero
+        if (tid == 0) {
+            for (int b = 0; b < E2_NB && s_begin + b < s_end; ++b) {
+                mbar_expect_tx(&mbar[b], C::TXB);
+                tma_load_4d(Gr + b * GRF, P.tm_graw, x0 - RA, y0 - R, s_begin + b,
+                            0, &mbar[b]);
+            }
+        }
         float4 ring[KG];
 #pragma unroll
         for (int k = 0; k < KG; ++k) ring[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        load_plane(s_begin);
-        for (int base = s_begin; base < s_end; base += KG) {
+        for (int base = s_begin; base < s_end && !failed; base += KG) {
 #pragma unroll
             for (int j = 0; j < KG; ++j) {
                 const int s = base + j;
                 if (s >= s_end) break;
                 const int t = s - s_begin;
-                // (1) g_raw of the tile and its R halo (zero outside)
-#pragma unroll
-                for (int k = 0; k < NRS; ++k)
-                    if (r_sm[k] >= 0) Gr[r_sm[k]] = pg[k];
-                if (s + 1 < s_end) load_plane(s + 1);
-                __syncthreads();
+                const int b = t % E2_NB;
+                const float* gr = Gr + b * GRF;
+                // (1) this slice's g_raw tile (TMA, issued two slices ago)
+                const bool ok = mbar_wait(&mbar[b], (phase >> b) & 1u);
+                phase ^= 1u << b;
+                if (__syncthreads_or(!ok)) {
+                    // give the copies still in flight a bounded wait
+                    for (int d = 1; d < E2_NB && s + d < s_end; ++d) {
+                        const int bb = (b + d) % E2_NB;
+                        mbar_wait(&mbar[bb], (phase >> bb) & 1u);
+                    }
+                    failed = true;
+                    break;
+                }
                 // (2) Gaussian along x: four outputs per unit
 #pragma unroll
                 for (int k = 0; k < NXS; ++k) {
                     if (x_in[k] < 0) continue;
-                    const float* rr = Gr + x_in[k];
+                    const float* rr = gr + x_in[k];
                     float v[4 + 2 * R];
 #pragma unroll
                     for (int o = 0; o < 4 + 2 * R; ++o) v[o] = rr[o];
@@ -709,10 +762,16 @@ __global__ void __launch_bounds__(NT2, 2)
                     *(float4*)(Gx + x_out[k]) = make_float4(out[0], out[1], out[2], out[3]);
                 }
                 __syncthreads();
+                // the tile is consumed: refill this buffer E2_NB slices ahead
+                if (tid == 0 && s + E2_NB < s_end) {
+                    mbar_expect_tx(&mbar[b], C::TXB);
+                    tma_load_4d(Gr + b * GRF, P.tm_graw, x0 - RA, y0 - R, s + E2_NB,
+                                0, &mbar[b]);
+                }
                 // (3) along y for this thread's quad, into the ring; along
                 //     z at slice o = s - R
                 {
-                    const float* col4 = Gx + (q * RY + oy) * TX + 4 * qx;
+                    const float* col4 = Gx + (q * BY + oy) * TX + 4 * qx;
                     float4 a = f4_mul(tt[R], *(const float4*)(col4 + R * TX));
 #pragma unroll
                     for (int m = 1; m <= R; ++m)
@@ -763,6 +822,7 @@ __global__ void __launch_bounds__(NT2, 2)
         }
         __syncthreads();   // Gz is rewritten by the next segment
     }
+    if (failed) m2 = INFINITY;   // surfaces as a non-finite gradient norm
     for (int k = 16; k > 0; k >>= 1)
         m2 = fmaxf(m2, __shfl_down_sync(0xffffffffu, m2, k));
     if ((tid & 31) == 0) red[tid >> 5] = m2;
@@ -1076,6 +1136,47 @@ BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms) {
     bp.ln_blocks = lnb;
     bp.mm_ctas = std::max(2, num_sms / npairs);
     return bp;
+}
+
+int graw_pitch(int nx) { return (nx + 3) / 4 * 4; }
+
+long long graw_floats(const Geom& g) {
+    return 3LL * g.nz * g.ny * graw_pitch(g.nx);
+}
+
+int encode_graw_map(void* map, const float* graw, const Geom& g, int R) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    if (!encode) {
+        set_last_error("cuTensorMapEncodeTiled is not available from the driver");
+        return LM_EUNSUPPORTED;
+    }
+    const int RA = (R + 3) / 4 * 4;
+    const cuuint64_t pw = (cuuint64_t)graw_pitch(g.nx);
+    cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+    cuuint64_t strides[3] = {pw * 4, pw * g.ny * 4, pw * g.ny * g.nz * 4};
+    cuuint32_t box[4] = {(cuuint32_t)(PLANE_X + 2 * RA), (cuuint32_t)(PLANE_Y + 2 * R),
+                         1, 3};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode((CUtensorMap*)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                        (void*)graw, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_last_error("cuTensorMapEncodeTiled rejected the g_raw tensor map");
+        return LM_ECUDA;
+    }
+    return LM_OK;
 }
 
 cudaError_t fused_setup() {

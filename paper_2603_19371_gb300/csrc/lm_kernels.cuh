@@ -35,7 +35,11 @@ struct PairDesc {
     int* fsum;            // exact k^3 window sum of fq (V), per preparation
     float* fvar;          // k^3-window variance B of F (V), per preparation
     float* dj;            // dJ/du (3 x V), from the J pass
-    float* graw;          // g_raw (3 x V) between the two evaluation kernels
+    float* graw;          // g_raw [3][nz][ny][gp_w] between the evaluation
+                          // kernels (rows padded to gp_w = nx rounded up
+                          // to 4, so that TMA can tile it)
+    const void* tm_graw;  // CUtensorMap (device memory) of graw for E2
+    int gp_w;
     QScale* qs;
     DevState* st;
     LogEntry* log;        // may be NULL
@@ -121,6 +125,12 @@ BatchPlan plan_batch(PairDesc* host_pd, int npairs, int win, int num_sms);
 
 // Opt the kernels in to their dynamic shared memory (once per process).
 cudaError_t fused_setup();
+// Row pitch of g_raw and its size in floats.
+int graw_pitch(int nx);
+long long graw_floats(const Geom& g);
+// Encode the 4-D tensor map (x, y, z, component) E2 reads g_raw through,
+// for Gaussian radius R, into the 128-byte host buffer map.
+int encode_graw_map(void* map, const float* graw, const Geom& g, int R);
 int quant_bits(int win);
 
 // Launch helpers; each returns the number of kernels it enqueued.

@@ -20,7 +20,7 @@
 namespace {
 
 // Scratch layout (bytes, each section 256-byte aligned):
-//   g_raw               3 x LM_NOALLOC_MAX_VOXELS floats
+//   g_raw               3 x LM_NOALLOC_MAX_VOXELS floats (rows padded to 4)
 //   J (fixed point)     LM_NOALLOC_MAX_VOXELS int32
 //   dJ/du               3 x LM_NOALLOC_MAX_VOXELS floats
 //   F fixed point, window sum (int32), variance (float): LM_NOALLOC_MAX_VOXELS each
@@ -48,7 +48,8 @@ constexpr size_t OFF_MM = OFF_G2 + align256(MAX_CTAS * sizeof(float));
 constexpr size_t OFF_QS = OFF_MM + align256(MAX_CTAS * sizeof(float2));
 constexpr size_t OFF_OUT = OFF_QS + align256(sizeof(lmk::QScale));
 constexpr size_t OFF_PD = OFF_OUT + align256(sizeof(lmk::EvalOut));
-constexpr size_t SCRATCH_BYTES = OFF_PD + align256(sizeof(lmk::PairDesc));
+constexpr size_t OFF_TMAP = OFF_PD + align256(sizeof(lmk::PairDesc));
+constexpr size_t SCRATCH_BYTES = OFF_TMAP + 256;   // g_raw's tensor map
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
@@ -96,8 +97,20 @@ int setup_device(int dev, unsigned char** ptr, int* sms) {
 }
 
 // Stores the one-pair descriptor table (passed by value) on the stream.
-__global__ void k_noalloc_table(lmk::PairDesc* dst, lmk::PairDesc v) {
-    if (threadIdx.x == 0) *dst = v;
+struct Map128 {
+    alignas(64) unsigned char b[128];
+};
+
+// The pair table and the g_raw tensor map, written by value into the
+// scratch; the release fence orders the map for the TMA unit's reads in
+// the following kernels.
+__global__ void k_noalloc_table(lmk::PairDesc* dst, lmk::PairDesc v,
+                                Map128* map_dst, Map128 map) {
+    if (threadIdx.x == 0) {
+        *dst = v;
+        *map_dst = map;
+        asm volatile("fence.proxy.tensormap::generic.release.gpu;\n" ::: "memory");
+    }
 }
 
 // Copies the reduced scalars to the caller's device outputs.
@@ -128,10 +141,12 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     if (fixed->dtype != LM_F32 && fixed->dtype != LM_BF16)
         return fail(LM_EINVAL, "unknown dtype");
     const long long V = (long long)fixed->D * fixed->H * fixed->W;
-    if (V > (long long)LM_NOALLOC_MAX_VOXELS)
+    if (V > (long long)LM_NOALLOC_MAX_VOXELS ||
+        (long long)fixed->D * fixed->H * lmk::graw_pitch(fixed->W) >
+            (long long)LM_NOALLOC_MAX_VOXELS)
         return fail(LM_EINVAL,
-                    "volume exceeds LM_NOALLOC_MAX_VOXELS (2^19 voxels) of the "
-                    "static scratch");
+                    "volume exceeds LM_NOALLOC_MAX_VOXELS (2^19 voxels, rows "
+                    "padded to a multiple of 4) of the static scratch");
     lm_params prm;
     if (p) {
         prm = *p;
@@ -176,6 +191,15 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     if ((size_t)plan.e1_ctas > MAX_CTAS || (size_t)plan.e2_ctas > MAX_CTAS ||
         (size_t)plan.mm_ctas > MAX_CTAS)
         return fail(LM_EUNSUPPORTED, "device has more SMs than the scratch covers");
+    pd.gp_w = lmk::graw_pitch(pd.g.nx);
+    pd.tm_graw = base + OFF_TMAP;
+    Map128 map;
+    {
+        double sg = prm.sigma_grad;
+        int R = sg > 0 ? (int)ceil(3.0 * sg) : 0;
+        int rc2 = lmk::encode_graw_map(map.b, pd.graw, pd.g, R);
+        if (rc2 != LM_OK) return rc2;
+    }
     lmk::PairDesc* dpd = (lmk::PairDesc*)(base + OFF_PD);
     lmk::EvalOut* out = (lmk::EvalOut*)(base + OFF_OUT);
 
@@ -208,7 +232,7 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     b.part.g2max = (float*)(base + OFF_G2);
     b.mm_part = (float2*)(base + OFF_MM);
 
-    k_noalloc_table<<<1, 32, 0, s>>>(dpd, pd);
+    k_noalloc_table<<<1, 32, 0, s>>>(dpd, pd, (Map128*)(base + OFF_TMAP), map);
     lmk::batch_prepare(b, s);
     lmk::batch_eval(b, lmk::EVAL_EXPLICIT, 0, s);
     lmk::batch_finalize(b, lmk::FIN_EXPLICIT, 0, out, s);
