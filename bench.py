@@ -127,6 +127,21 @@ def _dist():
     return world, rank, local
 
 
+def aggregate(ms, voxel_evals, device=None):
+    """Whole-job figures of a replicas run: the slowest rank's time and the
+    voxel-evaluations of all ranks (one process per GPU, launched by
+    torchrun).  Without an initialised process group: this rank's own."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms, float(voxel_evals)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([float(voxel_evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(v)
+    return float(t.item()), float(v.item())
+
+
 def cpu_baseline(F, M, iters=3):
     """The FP64 oracle, as it stands, on the host cores (OpenMP threads)."""
     import numpy as np
@@ -239,15 +254,8 @@ def run_ours(args):
     st1 = P.lm_get_state(ctx)
     evals = st1.evals - st0.evals
     launches = st1.kernel_launches - st0.kernel_launches
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        ev = torch.tensor([float(evals) * V], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(ev)
-        voxel_evals = float(ev.item())
-    else:
-        voxel_evals = float(evals) * V
+    ms, voxel_evals = aggregate(ms, float(evals) * V,
+                                device="cuda" if world > 1 else None)
     value = voxel_evals / (ms / 1e3) / 1e9
 
     # roofline of the dominant kernel (pass-1 evaluation), timed live

@@ -267,6 +267,22 @@ def test_nonfinite_field_is_reported(P):
     with pytest.raises(P.LMError) as e:
         P.lm_eval(ctx, u)
     assert e.value.code == P.LM_ENONFINITE
+    # the flag belongs to that evaluation: a finite field evaluates again
+    L, _ = P.lm_eval(ctx, torch.zeros_like(u))
+    assert np.isfinite(L)
+
+
+def test_nonfinite_fixed_image_is_reported(P):
+    import torch
+    import synth
+    F, M, _ = synth.blob_pair((16, 16, 20), seed=17)
+    F[2, 9, 11] = np.inf
+    ctx = P.lm_init(_t(F), _t(M), P.lm_default_params())
+    u = torch.zeros((3, 16, 16, 20), device="cuda")
+    for _ in range(2):
+        with pytest.raises(P.LMError) as e:
+            P.lm_eval(ctx, u)
+        assert e.value.code == P.LM_ENONFINITE
 
 
 def test_step_out_of_order(P):
