@@ -1,14 +1,14 @@
 // The learned warm start (include/lmunet.h): a 3-D U-Net trained on the
 // optimizer's own fields.  Every convolution runs as an implicit GEMM on the
-// tensor cores (bfloat16 operands, FP32 accumulation, mma.sync m16n8k16):
+// tensor cores (bfloat16 operands, FP32 accumulation):
 //
-//   forward / data gradient: rows = voxels, columns = output channels,
-//     reduction k = (tap, input channel); the data gradient is the forward
-//     convolution of dy with the weights flipped in space and transposed
-//     in channels.
-//   weight gradient: rows = output channels, columns = (tap, input channel),
-//     reduction over voxels, split over voxel chunks and accumulated with
-//     FP32 atomics.
+//   forward / data gradient (tcgen05.mma, accumulator in tensor memory):
+//     rows = voxels, columns = output channels, reduction k = (tap, input
+//     channel); the data gradient is the forward convolution of dy with the
+//     weights flipped in space and transposed in channels.
+//   weight gradient (warp-level mma.sync m16n8k16): rows = output channels,
+//     columns = (tap, input channel), reduction over voxels, split over
+//     voxel chunks and accumulated with FP32 atomics.
 //
 // Activations are channels-last bfloat16 ([D][H][W][C], C innermost), so a
 // 16-channel slice of one voxel is one 32-byte load; the A tile of the
@@ -101,31 +101,78 @@ __device__ __forceinline__ void tap_offset(int t, int& dz, int& dy, int& dx) {
 
 // ---------------------------------------------------------------------
 // Forward convolution (also the data gradient): y[v][co] =
-//   act(bias[co] + sum_{t, ci} w[co][t][ci] x[v + off(t)][ci]).
-// CTA tile 128 voxels x BN channels, k step 16 (one tap and 16 input
-// channels; for cin = 2 one step holds 8 taps), 8 warps.
+//   act(bias[co] + sum_{t, ci} w[co][t][ci] x[v + off(t)][ci])
+// on the 5th-generation tensor cores: one thread issues
+// tcgen05.mma (M = 128 voxels, N = BN channels, K = 16) with the FP32
+// accumulator in tensor memory; all 128 threads gather the A tile (and the
+// weights) with cp.async into a 4-stage ring of shared-memory tiles in the
+// canonical K-major layout without swizzle (8-row x 16-byte core matrices,
+// K-adjacent cores 2048 / 16 BN bytes apart, M/N-adjacent cores 128 bytes
+// apart).  tcgen05.commit signals per stage when the MMA has read it; the
+// epilogue reads the accumulator rows back with tcgen05.ld (warp w owns
+// TMEM lanes 32w .. 32w + 31).  Every wait is bounded; a timeout writes NaN.
 // ---------------------------------------------------------------------
-constexpr int CBM = 128, CKP = 24, CSTAGES = 3;
+constexpr int TC_STAGES = 4;
+constexpr int TC_AHEAD = 2;   // tiles gathered ahead; MMAs get TC_STAGES - TC_AHEAD steps
+
+__device__ __forceinline__ unsigned su32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long umma_desc(unsigned addr,
+                                                        unsigned lbo,
+                                                        unsigned sbo) {
+    unsigned long long d = (unsigned long long)((addr >> 4) & 0x3FFF);
+    d |= (unsigned long long)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;   // descriptor version; base offset 0, no swizzle
+    return d;
+}
+__device__ __forceinline__ bool tc_wait(unsigned long long* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, "
+            "[%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(su32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int BN>
+struct TcCfg {
+    static constexpr int A_BYTES = 128 * 16 * 2;          // one k-step of A
+    static constexpr int B_BYTES = BN * 16 * 2;           // one k-step of W
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int bytes = 1024 + TC_STAGES * STAGE;
+    static constexpr int COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    // kind::f16 instruction descriptor: D f32, A and B bf16, both K-major
+    static constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                      ((unsigned)(BN >> 3) << 17) |
+                                      ((unsigned)(128 >> 4) << 24);
+};
 
 template <int BN, bool CIN2, bool OUTF32>
-__global__ void __launch_bounds__(256)
-    k_conv_fwd(const bf16* __restrict__ x, const bf16* __restrict__ w,
-               const float* __restrict__ bias, void* __restrict__ y, int D,
-               int H, int W, int cin, int cout, int act) {
-    constexpr int WM = BN >= 64 ? 4 : 8, WN = 8 / WM;
-    constexpr int MT = CBM / WM / 16, NT = BN / WN / 8;
-    __shared__ __align__(16) bf16 As[CSTAGES][CBM][CKP];
-    __shared__ __align__(16) bf16 Bs[CSTAGES][BN][CKP];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp % WM, wn = warp / WM;
+__global__ void __launch_bounds__(128)
+    k_conv_fwd_tc(const bf16* __restrict__ x, const bf16* __restrict__ w,
+                  const float* __restrict__ bias, void* __restrict__ y, int D,
+                  int H, int W, int cin, int cout, int act) {
+    using C = TcCfg<BN>;
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+    __shared__ __align__(8) unsigned long long mbar[TC_STAGES];
+    __shared__ unsigned tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long V = (long long)D * H * W;
-    const long long v0 = (long long)blockIdx.x * CBM;
+    const long long v0 = (long long)blockIdx.x * 128;
     const int n0 = blockIdx.y * BN;
-    const int cpt = CIN2 ? 1 : cin / 16;       // k steps per tap
+    const int cpt = CIN2 ? 1 : cin / 16;
     const int nk = CIN2 ? 4 : 27 * cpt;
-    // gather role: row am of the A tile, half ah
-    const int am = tid >> 1, ah = tid & 1;
-    const long long av = v0 + am;
+    // gather role: A row = tid (one voxel per thread)
+    const long long av = v0 + tid;
     const bool arow = av < V;
     int az = 0, ay = 0, ax = 0;
     if (arow) {
@@ -134,7 +181,14 @@ __global__ void __launch_bounds__(256)
         ay = (int)(r % H);
         az = (int)(r / H);
     }
-    auto load = [&](int s, int stage) {
+    // canonical offsets: row r, k-half c (k 0-7 / 8-15) -> core (r/8, c)
+    const int a_off0 = (tid >> 3) * 128 + (tid & 7) * 16;          // c = 0
+    const int a_off1 = a_off0 + 16 * 128;                           // c = 1
+    auto stage_a = [&](int st) { return sm + st * C::STAGE; };
+    auto stage_b = [&](int st) { return sm + st * C::STAGE + C::A_BYTES; };
+    auto load = [&](int s, int st) {
+        unsigned char* As = stage_a(st);
+        unsigned char* Bs = stage_b(st);
         if (!CIN2) {
             const int tap = s / cpt, c0 = (s - tap * cpt) * 16;
             int dz, dy, dx;
@@ -143,107 +197,151 @@ __global__ void __launch_bounds__(256)
             const bool in = arow && zz >= 0 && zz < D && yy >= 0 && yy < H &&
                             xx >= 0 && xx < W;
             const bf16* src =
-                in ? x + (((long long)zz * H + yy) * W + xx) * cin + c0 + ah * 8
-                   : x;
-            cp_async16(&As[stage][am][ah * 8], src, in);
-            if (tid < 2 * BN) {
-                const int bn = tid >> 1, bh = tid & 1;
-                cp_async16(&Bs[stage][bn][bh * 8],
-                           w + ((long long)(n0 + bn) * 27 + tap) * cin + c0 +
-                               bh * 8,
+                in ? x + (((long long)zz * H + yy) * W + xx) * cin + c0 : x;
+            cp_async16(As + a_off0, src, in);
+            cp_async16(As + a_off1, in ? src + 8 : x, in);
+            for (int u = tid; u < 2 * BN; u += 128) {
+                const int n = u >> 1, c = u & 1;
+                cp_async16(Bs + (c * (BN / 8) + (n >> 3)) * 128 + (n & 7) * 16,
+                           w + ((long long)(n0 + n) * 27 + tap) * cin + c0 + c * 8,
                            true);
             }
         } else {
-            // k = 2 tap + ci; step s holds taps 8 s .. 8 s + 7
+            // k = 2 tap_local + ci, taps 8 s .. 8 s + 7; core column = tl / 4
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int tl = ah * 4 + j, tap = s * 8 + tl;
+            for (int tl = 0; tl < 8; ++tl) {
+                const int tap = s * 8 + tl;
                 int dz, dy, dx;
                 tap_offset(tap, dz, dy, dx);
                 const int zz = az + dz, yy = ay + dy, xx = ax + dx;
-                const bool in = arow && tap < 27 && zz >= 0 && zz < D &&
-                                yy >= 0 && yy < H && xx >= 0 && xx < W;
-                const bf16* src =
-                    in ? x + (((long long)zz * H + yy) * W + xx) * 2 : x;
-                cp_async4(&As[stage][am][tl * 2], src, in);
+                const bool in = arow && tap < 27 && zz >= 0 && zz < D && yy >= 0 &&
+                                yy < H && xx >= 0 && xx < W;
+                cp_async4(As + (tl >> 2) * 16 * 128 + (tid >> 3) * 128 +
+                              (tid & 7) * 16 + (tl & 3) * 4,
+                          in ? x + (((long long)zz * H + yy) * W + xx) * 2 : x, in);
             }
-            for (int u = tid; u < BN * 8; u += 256) {
-                const int bn = u >> 3, tl = u & 7, tap = s * 8 + tl;
+            for (int u = tid; u < BN * 8; u += 128) {
+                const int n = u >> 3, tl = u & 7, tap = s * 8 + tl;
                 const bool in = tap < 27;
-                cp_async4(&Bs[stage][bn][tl * 2],
-                          in ? w + ((long long)(n0 + bn) * 27 + tap) * 2 : w,
-                          in);
+                cp_async4(Bs + ((tl >> 2) * (BN / 8) + (n >> 3)) * 128 + (n & 7) * 16 +
+                              (tl & 3) * 4,
+                          in ? w + ((long long)(n0 + n) * 27 + tap) * 2 : w, in);
             }
         }
     };
 
-    float acc[MT][NT][4];
+    if (warp == 0) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                su32(&tmem_slot)),
+            "r"(C::COLS)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::
+                         : "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < TC_STAGES; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&mbar[b]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
 #pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int j = 0; j < NT; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-
-#pragma unroll
-    for (int s = 0; s < CSTAGES - 1; ++s) {
+    for (int s = 0; s < TC_AHEAD; ++s) {
         if (s < nk) load(s, s);
         cp_commit();
     }
-    const int g = lane >> 2, t4 = lane & 3;
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+    bool ok = true;
     for (int s = 0; s < nk; ++s) {
-        cp_wait<CSTAGES - 2>();
+        const int st = s % TC_STAGES;
+        cp_wait<TC_AHEAD - 1>();
+        // this thread's copies of step s have landed; make them visible to
+        // the tensor core, then to the issuing thread
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
-        const int st = s % CSTAGES;
-        unsigned af[MT][4], bfr[NT][2];
-#pragma unroll
-        for (int mi = 0; mi < MT; ++mi) {
-            const int r0 = wm * (CBM / WM) + mi * 16 + g;
-            af[mi][0] = ld_u32(&As[st][r0][2 * t4]);
-            af[mi][1] = ld_u32(&As[st][r0 + 8][2 * t4]);
-            af[mi][2] = ld_u32(&As[st][r0][2 * t4 + 8]);
-            af[mi][3] = ld_u32(&As[st][r0 + 8][2 * t4 + 8]);
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long ad =
+                umma_desc(su32(stage_a(st)), 16 * 128, 128);
+            const unsigned long long bd =
+                umma_desc(su32(stage_b(st)), (BN / 8) * 128, 128);
+            const unsigned acc = s > 0;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                    tmem),
+                "l"(ad), "l"(bd), "r"(C::IDESC), "r"(acc)
+                : "memory");
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster."
+                "b64 [%0];\n" ::"r"(su32(&mbar[st]))
+                : "memory");
         }
-#pragma unroll
-        for (int ni = 0; ni < NT; ++ni) {
-            const int c = wn * (BN / WN) + ni * 8 + g;
-            bfr[ni][0] = ld_u32(&Bs[st][c][2 * t4]);
-            bfr[ni][1] = ld_u32(&Bs[st][c][2 * t4 + 8]);
+        // gather step s + TC_AHEAD into the stage the MMA of step
+        // s + TC_AHEAD - TC_STAGES read, once that MMA is done with it
+        const int nx = s + TC_AHEAD;
+        if (nx < nk) {
+            const int pst = nx % TC_STAGES;
+            const int prev = nx - TC_STAGES;
+            if (prev >= 0)
+                ok &= tc_wait(&mbar[pst], (unsigned)((prev / TC_STAGES) & 1));
+            load(nx, pst);
         }
-#pragma unroll
-        for (int mi = 0; mi < MT; ++mi)
-#pragma unroll
-            for (int ni = 0; ni < NT; ++ni) mma16816(acc[mi][ni], af[mi], bfr[ni]);
-        const int nx = s + CSTAGES - 1;
-        if (nx < nk) load(nx, nx % CSTAGES);
         cp_commit();
     }
     cp_wait<0>();
-
+    // the last MMA (and with it all earlier ones) is done
+    const int last = nk - 1;
+    ok &= tc_wait(&mbar[last % TC_STAGES], (unsigned)((last / TC_STAGES) & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const long long v = v0 + warp * 32 + lane;   // this thread's TMEM lane
 #pragma unroll
-    for (int mi = 0; mi < MT; ++mi)
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        unsigned r[16];
+        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+              "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+              "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (v < V) {
+            float o[16];
 #pragma unroll
-        for (int ni = 0; ni < NT; ++ni) {
-            const int r0 = wm * (CBM / WM) + mi * 16 + g;
-            const int c = n0 + wn * (BN / WN) + ni * 8 + 2 * t4;
-            const float b0 = bias ? bias[c] : 0.f, b1 = bias ? bias[c + 1] : 0.f;
+            for (int j = 0; j < 16; ++j) {
+                float t = __uint_as_float(r[j]) + (bias ? bias[n0 + c0 + j] : 0.f);
+                if (act) t = t > 0.f ? t : SLOPE * t;
+                o[j] = ok ? t : __int_as_float(0x7fc00000);
+            }
+            if (OUTF32) {
+                float4* dst = reinterpret_cast<float4*>((float*)y + v * cout + n0 + c0);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const long long v = v0 + r0 + h * 8;
-                if (v >= V) continue;
-                float o0 = acc[mi][ni][2 * h] + b0, o1 = acc[mi][ni][2 * h + 1] + b1;
-                if (act) {
-                    o0 = o0 > 0.f ? o0 : SLOPE * o0;
-                    o1 = o1 > 0.f ? o1 : SLOPE * o1;
-                }
-                if (OUTF32)
-                    *reinterpret_cast<float2*>((float*)y + v * cout + c) =
-                        make_float2(o0, o1);
-                else
-                    *reinterpret_cast<__nv_bfloat162*>((bf16*)y + v * cout + c) =
-                        __floats2bfloat162_rn(o0, o1);
+                for (int j = 0; j < 4; ++j)
+                    dst[j] = make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
+            } else {
+                __nv_bfloat162 h[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+                uint4* dst = reinterpret_cast<uint4*>((bf16*)y + v * cout + n0 + c0);
+                dst[0] = *reinterpret_cast<uint4*>(&h[0]);
+                dst[1] = *reinterpret_cast<uint4*>(&h[4]);
             }
         }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(
+                         tmem),
+                     "r"(C::COLS)
+                     : "memory");
 }
 
 // ---------------------------------------------------------------------
@@ -632,28 +730,71 @@ int blocks(long long n, int t = 256) { return (int)((n + t - 1) / t); }
 // ---------------------------------------------------------------------
 // Launch helpers.
 // ---------------------------------------------------------------------
+template <int BN, bool C2, bool F>
+void launch_tc(const bf16* x, const bf16* w, const float* bias, void* y, int D,
+               int H, int W, int cin, int cout, int act, int gx, cudaStream_t s) {
+    k_conv_fwd_tc<BN, C2, F><<<dim3(gx, cout / BN), 128, TcCfg<BN>::bytes, s>>>(
+        x, w, bias, y, D, H, W, cin, cout, act);
+}
+
+template <bool C2, bool F>
+void pick_tc(const bf16* x, const bf16* w, const float* bias, void* y, int D,
+             int H, int W, int cin, int cout, int act, int gx, cudaStream_t s) {
+    // one N tile of the whole output width where the accumulator fits
+    if (cout == 16) launch_tc<16, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+    else if (cout == 32) launch_tc<32, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+    else if (cout == 64) launch_tc<64, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+    else if (cout == 96) launch_tc<96, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+    else if (cout == 192) launch_tc<192, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+    else if (cout % 128 == 0) launch_tc<128, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+    else if (cout % 64 == 0) launch_tc<64, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+    else if (cout % 32 == 0) launch_tc<32, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+    else launch_tc<16, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+}
+
 int conv_forward(const bf16* x, const bf16* w, const float* bias, void* y,
                  bool out_f32, int D, int H, int W, int cin, int cout, int act,
                  cudaStream_t s) {
     const long long V = (long long)D * H * W;
-    const int gx = (int)((V + CBM - 1) / CBM);
-    const bool c2 = cin == 2;
-#define LAUNCH(BN_, C2_, F_)                                                  \
-    k_conv_fwd<BN_, C2_, F_><<<dim3(gx, cout / BN_), 256, 0, s>>>(             \
-        x, w, bias, y, D, H, W, cin, cout, act)
-#define PICK_BN(C2_, F_)                    \
-    if (cout % 128 == 0) LAUNCH(128, C2_, F_); \
-    else if (cout % 64 == 0) LAUNCH(64, C2_, F_); \
-    else if (cout % 32 == 0) LAUNCH(32, C2_, F_); \
-    else LAUNCH(16, C2_, F_);
-    if (c2) {
-        if (out_f32) { PICK_BN(true, true) } else { PICK_BN(true, false) }
+    const int gx = (int)((V + 127) / 128);
+    if (cin == 2) {
+        if (out_f32) pick_tc<true, true>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+        else pick_tc<true, false>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
     } else {
-        if (out_f32) { PICK_BN(false, true) } else { PICK_BN(false, false) }
+        if (out_f32) pick_tc<false, true>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
+        else pick_tc<false, false>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
     }
-#undef PICK_BN
-#undef LAUNCH
     return 1;
+}
+
+template <int BN, bool C2, bool F>
+cudaError_t attr_tc() {
+    return cudaFuncSetAttribute(k_conv_fwd_tc<BN, C2, F>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<BN>::bytes);
+}
+template <bool C2, bool F>
+cudaError_t attrs_tc() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = attr_tc<16, C2, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tc<32, C2, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tc<64, C2, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tc<96, C2, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tc<128, C2, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tc<192, C2, F>()) != cudaSuccess) e = r;
+    return e;
+}
+// Shared-memory opt-in of the tensor-core convolutions (once per process).
+cudaError_t conv_setup() {
+    static cudaError_t once = [] {
+        cudaError_t e = cudaSuccess, r;
+        if ((r = attrs_tc<false, false>()) != cudaSuccess) e = r;
+        if ((r = attrs_tc<false, true>()) != cudaSuccess) e = r;
+        if ((r = attrs_tc<true, false>()) != cudaSuccess) e = r;
+        if ((r = attrs_tc<true, true>()) != cudaSuccess) e = r;
+        return e;
+    }();
+    return once;
 }
 
 int conv_wgrad(const bf16* x, const bf16* dy, float* dw, int D, int H, int W,
@@ -920,6 +1061,10 @@ extern "C" int lm_unet_create(lm_unet** out, int D, int H, int W,
     if (D < 8 || H < 8 || W < 8 || D % 8 || H % 8 || W % 8 || D > 512 ||
         H > 512 || W > 512)
         return fail(LM_EINVAL, "sizes must be multiples of 8 in [8, 512]");
+    if (conv_setup() != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LM_ECUDA, "shared-memory opt-in of the convolutions failed");
+    }
     auto n = new lm_unet();
     n->D = D;
     n->H = H;
@@ -1075,6 +1220,7 @@ extern "C" int lm_conv3d_forward(int D, int H, int W, int cin, int cout,
     if (!x || !w || !y) return fail(LM_EINVAL, "NULL argument");
     if (D < 1 || H < 1 || W < 1 || !conv_shape_ok(cin, cout))
         return fail(LM_EINVAL, "unsupported convolution shape");
+    UN_CK(conv_setup());
     conv_forward((const bf16*)x, (const bf16*)w, bias, y, true, D, H, W, cin, cout,
                  act ? 1 : 0, (cudaStream_t)stream);
     UN_CK(cudaGetLastError());
@@ -1089,6 +1235,7 @@ extern "C" int lm_conv3d_backward(int D, int H, int W, int cin, int cout,
         return fail(LM_EINVAL, "unsupported convolution shape");
     if (dx && cin == 2)
         return fail(LM_EUNSUPPORTED, "no data gradient for 2 input channels");
+    UN_CK(conv_setup());
     cudaStream_t s = (cudaStream_t)stream;
     const long long V = (long long)D * H * W;
     conv_wgrad((const bf16*)x, (const bf16*)dy, dw, D, H, W, cin, cout, s);
