@@ -208,7 +208,7 @@ struct Core {
         int n = 0;
         for (int j = 0; j < attempts; ++j) {
             n += batch_step(b, j, s);
-            n += batch_eval(b, EVAL_TRIAL, j, s);
+            n += batch_eval(b, EVAL_TRIAL, j, s, !step_resamples(b));
             n += batch_finalize(b, FIN_DECIDE, j, nullptr, s);
         }
         return n;
@@ -650,7 +650,8 @@ int lm_time_passes(lm_ctx* c, float* u, int n, double* ms_eval,
     LM_CK(cudaEventRecord(e0, k->stream));
     for (int i = 0; i < n; ++i) batch_step(k->b, 0, k->stream);
     LM_CK(cudaEventRecord(e1, k->stream));
-    for (int i = 0; i < n; ++i) batch_eval(k->b, EVAL_TRIAL, 0, k->stream);
+    for (int i = 0; i < n; ++i)
+        batch_eval(k->b, EVAL_TRIAL, 0, k->stream, !step_resamples(k->b));
     LM_CK(cudaEventRecord(e2, k->stream));
     LM_CK(cudaEventSynchronize(e2));
     float a = 0.f, bb = 0.f;

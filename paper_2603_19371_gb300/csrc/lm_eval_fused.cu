@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "lm_kernels.cuh"
+#include "lm_sample.cuh"
 
 namespace lmk {
 namespace {
@@ -43,72 +44,6 @@ namespace {
 constexpr int NT = 512;       // threads per CTA (both kernels)
 constexpr int PLANE_X = 32;   // E1 moment plane / E2 output tile width
 constexpr int PLANE_Y = 16;   // and height
-
-__device__ __forceinline__ float safe_floor(float v) {
-    return fminf(fmaxf(floorf(v), -1048576.f), 1048576.f);
-}
-
-// Trilinear corners of M around p + d (d = u(p) already loaded), zero
-// outside the volume.  Offsets are 32-bit (V < 2^31).
-template <typename T>
-__device__ __forceinline__ void corners(const T* __restrict__ M, const Geom& g,
-                                        int x, int y, int z, float d0,
-                                        float d1, float d2, float m[8],
-                                        float f[3]) {
-    float l0 = safe_floor(d0), l1 = safe_floor(d1), l2 = safe_floor(d2);
-    f[0] = d0 - l0;
-    f[1] = d1 - l1;
-    f[2] = d2 - l2;
-    int cx = x + (int)l0, cy = y + (int)l1, cz = z + (int)l2;
-    const int sxy = g.nx * g.ny;
-    if (cx >= 0 && cx + 1 < g.nx && cy >= 0 && cy + 1 < g.ny && cz >= 0 &&
-        cz + 1 < g.nz) {
-        int b = cz * sxy + cy * g.nx + cx;
-        m[0] = ld_img(M, b);
-        m[1] = ld_img(M, b + 1);
-        m[2] = ld_img(M, b + g.nx);
-        m[3] = ld_img(M, b + g.nx + 1);
-        m[4] = ld_img(M, b + sxy);
-        m[5] = ld_img(M, b + sxy + 1);
-        m[6] = ld_img(M, b + sxy + g.nx);
-        m[7] = ld_img(M, b + sxy + g.nx + 1);
-    } else {
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            int qx = cx + (s & 1), qy = cy + ((s >> 1) & 1), qz = cz + (s >> 2);
-            bool in = qx >= 0 && qx < g.nx && qy >= 0 && qy < g.ny && qz >= 0 &&
-                      qz < g.nz;
-            m[s] = in ? ld_img(M, qz * sxy + qy * g.nx + qx) : 0.f;
-        }
-    }
-}
-
-// J from the corners (corner index = x + 2y + 4z).
-__device__ __forceinline__ float interp(const float m[8], const float f[3]) {
-    float a0 = m[0] + f[0] * (m[1] - m[0]);
-    float a1 = m[2] + f[0] * (m[3] - m[2]);
-    float a2 = m[4] + f[0] * (m[5] - m[4]);
-    float a3 = m[6] + f[0] * (m[7] - m[6]);
-    float b0 = a0 + f[1] * (a1 - a0);
-    float b1 = a2 + f[1] * (a3 - a2);
-    return b0 + f[2] * (b1 - b0);
-}
-
-// dJ/du from the corners.
-__device__ __forceinline__ void interp_grad(const float m[8], const float f[3],
-                                            float d[3]) {
-    float ex0 = m[1] - m[0], ex1 = m[3] - m[2], ex2 = m[5] - m[4],
-          ex3 = m[7] - m[6];
-    float gx0 = ex0 + f[1] * (ex1 - ex0);
-    float gx1 = ex2 + f[1] * (ex3 - ex2);
-    d[0] = gx0 + f[2] * (gx1 - gx0);
-    float a0 = m[0] + f[0] * ex0, a1 = m[2] + f[0] * ex1;
-    float a2 = m[4] + f[0] * ex2, a3 = m[6] + f[0] * ex3;
-    float ey0 = a1 - a0, ey1 = a3 - a2;
-    d[1] = ey0 + f[2] * (ey1 - ey0);
-    float b0 = a0 + f[1] * ey0, b1 = a2 + f[1] * ey1;
-    d[2] = b1 - b0;
-}
 
 // Contiguous share of the (column, slice) work of CTA b out of n: the CTA
 // walks segments [col, z0, z1) covering work units [lo, hi).
@@ -128,7 +63,6 @@ __device__ __forceinline__ Share share_of(int b, int n, long long total) {
 // non-finite J), dJ/du kept in FP32.  One thread per x-y column of a 32 x 8
 // tile, marching over the tile's z range (the step kernel's tiling).
 // ----------------------------------------------------------------------
-constexpr int JQ_BAD = (int)0x80000000;
 constexpr int FQ_BAD = JQ_BAD;   // same sentinel for a non-finite F
 
 template <typename T>
@@ -148,10 +82,6 @@ __global__ void __launch_bounds__(256)
     const int z1 = min(z0 + P.st_zc, g.nz);
     const T* __restrict__ M = (const T*)P.M;
     const float* __restrict__ u = eval_u(P, mode);
-    int* __restrict__ jq = P.jq;
-    float* __restrict__ dj = P.dj;
-    const float sh = P.qs->shift, Q = P.qs->Q;
-    const int qlim = P.qs->qlim;
     const int sxy = g.nx * g.ny;
     int i = z0 * sxy + y * g.nx + x;
     float nu0 = 0.f, nu1 = 0.f, nu2 = 0.f;
@@ -168,16 +98,7 @@ __global__ void __launch_bounds__(256)
             nu1 = __ldg(u + g.V + i + sxy);
             nu2 = __ldg(u + 2 * g.V + i + sxy);
         }
-        float m[8], f[3], d[3];
-        corners(M, g, x, y, z, d0, d1, d2, m, f);
-        const float J = interp(m, f);
-        interp_grad(m, f, d);
-        jq[i] = (fabsf(J) <= 3.0e38f)
-                    ? min(max(__float2int_rn((J - sh) * Q), -qlim), qlim)
-                    : JQ_BAD;
-        dj[i] = d[0];
-        dj[g.V + i] = d[1];
-        dj[2 * g.V + i] = d[2];
+        resample_voxel(P, M, x, y, z, i, d0, d1, d2);
     }
 }
 
@@ -1203,18 +1124,23 @@ int batch_prepare(const Batch& b, cudaStream_t s) {
     return 5;
 }
 
-int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s) {
+int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
+               bool jpass) {
     int n = 0;
     if (b.dtype == LM_BF16) {
-        k_jpass<__nv_bfloat16><<<b.plan.st_blocks, dim3(32, 8), 0, s>>>(
-            b.pd, b.npairs, mode, attempt);
-        n += 1;
+        if (jpass) {
+            k_jpass<__nv_bfloat16><<<b.plan.st_blocks, dim3(32, 8), 0, s>>>(
+                b.pd, b.npairs, mode, attempt);
+            n += 1;
+        }
         n += launch_e1_w(b, mode, attempt, s);
         n += launch_e2_r<__nv_bfloat16>(b, mode, attempt, s);
     } else {
-        k_jpass<float><<<b.plan.st_blocks, dim3(32, 8), 0, s>>>(
-            b.pd, b.npairs, mode, attempt);
-        n += 1;
+        if (jpass) {
+            k_jpass<float><<<b.plan.st_blocks, dim3(32, 8), 0, s>>>(
+                b.pd, b.npairs, mode, attempt);
+            n += 1;
+        }
         n += launch_e1_w(b, mode, attempt, s);
         n += launch_e2_r<float>(b, mode, attempt, s);
     }

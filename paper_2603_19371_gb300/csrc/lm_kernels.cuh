@@ -139,10 +139,15 @@ int quant_bits(int win);
 // window sum and variance (device-side, no host round trip).  The J-pass
 // scratch (graw, dj) serves as the separable passes' temporaries.
 int batch_prepare(const Batch& b, cudaStream_t s);
-// Pass 1: loss partials, dL/dJ, smoothed gradient, |g|^2 partials.
-int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s);
+// Pass 1: loss partials, dL/dJ, smoothed gradient, |g|^2 partials.  With
+// jpass = false the J pass is left out (the step kernel already resampled
+// the trial).
+int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
+               bool jpass = true);
 // Pass 2: trial field (Eq. tile1 + Eq. compositive, optional smoothing).
 int batch_step(const Batch& b, int attempt, cudaStream_t s);
+// Whether batch_step also resamples M at the trial (no warp smoothing).
+bool step_resamples(const Batch& b);
 // Per-pair reduction and state update.
 enum FinMode { FIN_EXPLICIT = 0, FIN_RESET = 1, FIN_DECIDE = 2 };
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,

@@ -1,0 +1,100 @@
+// Trilinear sampling of an image at displaced points (Section 2.1): the
+// cell split is taken on the displacement (c = p + floor(d), f = d -
+// floor(d)), the image reads as zero outside the volume.  Shared by the J
+// pass and the fused step kernel.
+#pragma once
+
+#include "lm_kernels.cuh"
+
+namespace lmk {
+
+__device__ __forceinline__ float safe_floor(float v) {
+    return fminf(fmaxf(floorf(v), -1048576.f), 1048576.f);
+}
+
+// Trilinear corners of M around p + d (d = u(p) already loaded), zero
+// outside the volume.  Offsets are 32-bit.
+template <typename T>
+__device__ __forceinline__ void corners(const T* __restrict__ M, const Geom& g,
+                                        int x, int y, int z, float d0,
+                                        float d1, float d2, float m[8],
+                                        float f[3]) {
+    float l0 = safe_floor(d0), l1 = safe_floor(d1), l2 = safe_floor(d2);
+    f[0] = d0 - l0;
+    f[1] = d1 - l1;
+    f[2] = d2 - l2;
+    int cx = x + (int)l0, cy = y + (int)l1, cz = z + (int)l2;
+    const int sxy = g.nx * g.ny;
+    if (cx >= 0 && cx + 1 < g.nx && cy >= 0 && cy + 1 < g.ny && cz >= 0 &&
+        cz + 1 < g.nz) {
+        int b = cz * sxy + cy * g.nx + cx;
+        m[0] = ld_img(M, b);
+        m[1] = ld_img(M, b + 1);
+        m[2] = ld_img(M, b + g.nx);
+        m[3] = ld_img(M, b + g.nx + 1);
+        m[4] = ld_img(M, b + sxy);
+        m[5] = ld_img(M, b + sxy + 1);
+        m[6] = ld_img(M, b + sxy + g.nx);
+        m[7] = ld_img(M, b + sxy + g.nx + 1);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            int qx = cx + (s & 1), qy = cy + ((s >> 1) & 1), qz = cz + (s >> 2);
+            bool in = qx >= 0 && qx < g.nx && qy >= 0 && qy < g.ny && qz >= 0 &&
+                      qz < g.nz;
+            m[s] = in ? ld_img(M, qz * sxy + qy * g.nx + qx) : 0.f;
+        }
+    }
+}
+
+// J from the corners (corner index = x + 2y + 4z).
+__device__ __forceinline__ float interp(const float m[8], const float f[3]) {
+    float a0 = m[0] + f[0] * (m[1] - m[0]);
+    float a1 = m[2] + f[0] * (m[3] - m[2]);
+    float a2 = m[4] + f[0] * (m[5] - m[4]);
+    float a3 = m[6] + f[0] * (m[7] - m[6]);
+    float b0 = a0 + f[1] * (a1 - a0);
+    float b1 = a2 + f[1] * (a3 - a2);
+    return b0 + f[2] * (b1 - b0);
+}
+
+// dJ/du from the corners.
+__device__ __forceinline__ void interp_grad(const float m[8], const float f[3],
+                                            float d[3]) {
+    float ex0 = m[1] - m[0], ex1 = m[3] - m[2], ex2 = m[5] - m[4],
+          ex3 = m[7] - m[6];
+    float gx0 = ex0 + f[1] * (ex1 - ex0);
+    float gx1 = ex2 + f[1] * (ex3 - ex2);
+    d[0] = gx0 + f[2] * (gx1 - gx0);
+    float a0 = m[0] + f[0] * ex0, a1 = m[2] + f[0] * ex1;
+    float a2 = m[4] + f[0] * ex2, a3 = m[6] + f[0] * ex3;
+    float ey0 = a1 - a0, ey1 = a3 - a2;
+    d[1] = ey0 + f[2] * (ey1 - ey0);
+    float b0 = a0 + f[1] * ey0, b1 = a2 + f[1] * ey1;
+    d[2] = b1 - b0;
+}
+
+// Fixed-point value of a non-finite J (never a valid code).
+constexpr int JQ_BAD = (int)0x80000000;
+
+// J and dJ/du of voxel (x, y, z) under displacement (d0, d1, d2): J in the
+// moments' fixed point (JQ_BAD if not finite) and dJ/du to dj (3 x V).
+template <typename T>
+__device__ __forceinline__ void resample_voxel(const PairDesc& P, const T* M,
+                                               int x, int y, int z, int i,
+                                               float d0, float d1, float d2) {
+    float m[8], f[3], d[3];
+    corners(M, P.g, x, y, z, d0, d1, d2, m, f);
+    const float J = interp(m, f);
+    interp_grad(m, f, d);
+    const float sh = P.qs->shift, Q = P.qs->Q;
+    const int qlim = P.qs->qlim;
+    P.jq[i] = (fabsf(J) <= 3.0e38f)
+                  ? min(max(__float2int_rn((J - sh) * Q), -qlim), qlim)
+                  : JQ_BAD;
+    P.dj[i] = d[0];
+    P.dj[P.g.V + i] = d[1];
+    P.dj[2 * P.g.V + i] = d[2];
+}
+
+}  // namespace lmk

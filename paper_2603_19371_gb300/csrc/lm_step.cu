@@ -11,15 +11,12 @@
 #include <algorithm>
 
 #include "lm_kernels.cuh"
+#include "lm_sample.cuh"
 
 namespace lmk {
 namespace {
 
 constexpr int TPB = 256;
-
-__device__ __forceinline__ float safe_floor(float v) {
-    return fminf(fmaxf(floorf(v), -1048576.f), 1048576.f);
-}
 
 __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
     return st->stopped || (attempt > 0 && st->done);
@@ -31,10 +28,14 @@ __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
 // shared-memory ring, so the trilinear read of u at p + v comes from shared
 // memory whenever |v| < 1 along each axis and from global memory otherwise.
 // The trial goes to slot (1 - cu), or to the pair's warp-smoothing buffer.
+// Without warp smoothing the kernel also resamples M at the trial (J and
+// dJ/du of the trial's evaluation, Section 2.1) while the trial is in
+// registers, so the evaluation starts at the moment kernel.
 constexpr int ST_X = 32, ST_Y = 8, ST_HX = ST_X + 2, ST_HY = ST_Y + 2;
 constexpr int ST_PLANE = ST_HX * ST_HY;
 
-__global__ void __launch_bounds__(ST_X * ST_Y, 3)
+template <typename T, bool RESAMPLE>
+__global__ void __launch_bounds__(ST_X * ST_Y, 4)
     k_step_compose(const PairDesc* __restrict__ pd, int npairs, int attempt,
                    float step, int smooth) {
     __shared__ float ring[3][3][ST_PLANE];   // [z slot][component][y][x]
@@ -176,14 +177,18 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
                     m[q][7] = __ldg(U[q] + o011 + bx2);
                 }
             }
+            float ut[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 float sv = wz0 * (wy0 * (wx0 * m[q][0] + wx1 * m[q][1]) +
                                   wy1 * (wx0 * m[q][2] + wx1 * m[q][3])) +
                            wz1 * (wy0 * (wx0 * m[q][4] + wx1 * m[q][5]) +
                                   wy1 * (wx0 * m[q][6] + wx1 * m[q][7]));
-                out[q * g.V + i] = v[q] + sv;
+                ut[q] = v[q] + sv;
+                out[q * g.V + i] = ut[q];
             }
+            if (RESAMPLE)
+                resample_voxel(P, (const T*)P.M, x, y, z, i, ut[0], ut[1], ut[2]);
         }
         __syncthreads();   // slot of plane z - 1 is free
         {
@@ -385,11 +390,22 @@ __global__ void k_flip_slot(const PairDesc* __restrict__ pd) {
 
 }  // namespace
 
+bool step_resamples(const Batch& b) { return b.wtaps.R == 0; }
+
 int batch_step(const Batch& b, int attempt, cudaStream_t s) {
     const int smooth = b.wtaps.R > 0;
-    k_step_compose<<<b.plan.st_blocks, dim3(ST_X, ST_Y), 0, s>>>(
-        b.pd, b.npairs, attempt, b.step, smooth);
-    if (!smooth) return 1;
+    const dim3 grid(b.plan.st_blocks), block(ST_X, ST_Y);
+    if (!smooth) {
+        if (b.dtype == LM_BF16)
+            k_step_compose<__nv_bfloat16, true><<<grid, block, 0, s>>>(
+                b.pd, b.npairs, attempt, b.step, 0);
+        else
+            k_step_compose<float, true><<<grid, block, 0, s>>>(
+                b.pd, b.npairs, attempt, b.step, 0);
+        return 1;
+    }
+    k_step_compose<float, false><<<grid, block, 0, s>>>(b.pd, b.npairs, attempt,
+                                                         b.step, 1);
     for (int axis = 0; axis < 3; ++axis)
         k_warp_gauss<<<b.plan.ln_blocks, TPB, 0, s>>>(b.pd, b.npairs, attempt,
                                                       b.wtaps, axis);
