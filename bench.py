@@ -48,7 +48,7 @@ ITER_BYTES_PER_VOXEL = 68
 # kernels, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
 # of every kernel of an iteration at 128x160x192, k = 5, FP32), scaled by
 # voxels.  None whenever those kernels changed since the last capture.
-ITER_TRAFFIC_BYTES_PER_VOXEL = None
+ITER_TRAFFIC_BYTES_PER_VOXEL = 130.9
 
 
 def _peaks():
@@ -143,7 +143,7 @@ def aggregate(ms, voxel_evals, device=None):
     return float(t.item()), float(v.item())
 
 
-def cpu_baseline(F, M, iters=3):
+def cpu_baseline(F, M, iters=20):
     """The FP64 oracle, as it stands, on the host cores (OpenMP threads)."""
     import numpy as np
     import oracle
@@ -656,7 +656,7 @@ def run_warmstart(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
