@@ -226,7 +226,7 @@ def run_ours(args):
     F, M, _ = synth.voronoi_pair(shape, seed=rank)
     V = F.size
     stream = torch.cuda.Stream()
-    params = P.lm_default_params()
+    params = P.lm_default_params(win=args.win)
     with torch.cuda.stream(stream):
         Ft = torch.from_numpy(F).cuda()
         Mt = torch.from_numpy(M).cuda()
@@ -272,6 +272,7 @@ def run_ours(args):
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": (ITER_TRAFFIC_BYTES_PER_VOXEL * V
                             if ITER_TRAFFIC_BYTES_PER_VOXEL and shape == SHAPE
+                            and args.win == 5
                             else None),
                 "bytes_per_voxel": ITER_BYTES_PER_VOXEL,
                 "ms_iteration": ms_iter,
@@ -327,8 +328,10 @@ def run_ours(args):
         "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if shape == SHAPE else
-                   WORKLOAD.replace("160x192x224", "x".join(map(str, shape))),
+        "config": {"workload": (WORKLOAD if shape == SHAPE else
+                                WORKLOAD.replace("160x192x224",
+                                                 "x".join(map(str, shape))))
+                   .replace("LNCC k=5", f"LNCC k={args.win}"),
                    "voxels": V,
                    "l2": "no flush: per-iteration working set (F, M, u, "
                          "trial u, two gradients: 385 MB) exceeds the "
@@ -664,6 +667,8 @@ def main():
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     metavar=("D", "H", "W"),
                     help="other pair size (profiling cases)")
+    ap.add_argument("--win", type=int, default=5,
+                    help="LNCC window (5 for the brain workload, 7 for lung CT)")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batch", "warmstart"],
                     help="batch: uneven pairs, batched vs plain; warmstart: "

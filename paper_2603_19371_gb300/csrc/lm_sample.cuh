@@ -77,14 +77,12 @@ __device__ __forceinline__ void interp_grad(const float m[8], const float f[3],
 // Fixed-point value of a non-finite J (never a valid code).
 constexpr int JQ_BAD = (int)0x80000000;
 
-// J and dJ/du of voxel (x, y, z) under displacement (d0, d1, d2): J in the
-// moments' fixed point (JQ_BAD if not finite) and dJ/du to dj (3 x V).
-template <typename T>
-__device__ __forceinline__ void resample_voxel(const PairDesc& P, const T* M,
-                                               int x, int y, int z, int i,
-                                               float d0, float d1, float d2) {
-    float m[8], f[3], d[3];
-    corners(M, P.g, x, y, z, d0, d1, d2, m, f);
+// J and dJ/du of voxel i from its corners: J in the moments' fixed point
+// (JQ_BAD if not finite) and dJ/du to dj (3 x V).
+__device__ __forceinline__ void store_resampled(const PairDesc& P, int i,
+                                                const float m[8],
+                                                const float f[3]) {
+    float d[3];
     const float J = interp(m, f);
     interp_grad(m, f, d);
     const float sh = P.qs->shift, Q = P.qs->Q;
@@ -95,6 +93,16 @@ __device__ __forceinline__ void resample_voxel(const PairDesc& P, const T* M,
     P.dj[i] = d[0];
     P.dj[P.g.V + i] = d[1];
     P.dj[2 * P.g.V + i] = d[2];
+}
+
+// J and dJ/du of voxel (x, y, z) under displacement (d0, d1, d2).
+template <typename T>
+__device__ __forceinline__ void resample_voxel(const PairDesc& P, const T* M,
+                                               int x, int y, int z, int i,
+                                               float d0, float d1, float d2) {
+    float m[8], f[3];
+    corners(M, P.g, x, y, z, d0, d1, d2, m, f);
+    store_resampled(P, i, m, f);
 }
 
 }  // namespace lmk

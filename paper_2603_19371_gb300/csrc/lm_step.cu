@@ -35,7 +35,7 @@ constexpr int ST_X = 32, ST_Y = 8, ST_HX = ST_X + 2, ST_HY = ST_Y + 2;
 constexpr int ST_PLANE = ST_HX * ST_HY;
 
 template <typename T, bool RESAMPLE>
-__global__ void __launch_bounds__(ST_X * ST_Y, 4)
+__global__ void __launch_bounds__(ST_X * ST_Y, 3)
     k_step_compose(const PairDesc* __restrict__ pd, int npairs, int attempt,
                    float step, int smooth) {
     __shared__ float ring[3][3][ST_PLANE];   // [z slot][component][y][x]
@@ -105,6 +105,10 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 4)
         ng2 = __ldg(gg + 2 * g.V + i0);
     }
     __syncthreads();
+    // resampling is pipelined by one voxel: the corners of M at the trial of
+    // voxel z are requested at step z and consumed at step z + 1
+    float pm[8], pf[3];
+    int pi = -1;
     for (int z = z0; z < z1; ++z) {
         // plane z + 2 streams into registers while voxel z is computed
         float pre[NLD];
@@ -187,8 +191,17 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 4)
                 ut[q] = v[q] + sv;
                 out[q * g.V + i] = ut[q];
             }
-            if (RESAMPLE)
-                resample_voxel(P, (const T*)P.M, x, y, z, i, ut[0], ut[1], ut[2]);
+            if (RESAMPLE) {
+                float cm[8], cf[3];
+                corners((const T*)P.M, g, x, y, z, ut[0], ut[1], ut[2], cm, cf);
+                if (pi >= 0) store_resampled(P, pi, pm, pf);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) pm[k] = cm[k];
+                pf[0] = cf[0];
+                pf[1] = cf[1];
+                pf[2] = cf[2];
+                pi = i;
+            }
         }
         __syncthreads();   // slot of plane z - 1 is free
         {
@@ -199,6 +212,7 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 4)
         }
         __syncthreads();
     }
+    if (RESAMPLE && pi >= 0) store_resampled(P, pi, pm, pf);
 }
 
 // 1-D Gaussian along an axis of a pair's 3-component field, edge-extended;
