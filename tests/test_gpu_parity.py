@@ -365,3 +365,31 @@ def test_field_resample_matches_oracle(P, oracle_mod, fa, shape_a, fb, shape_b):
     torch.cuda.synchronize()
     err = np.abs(dst.cpu().numpy() - ref).max()
     assert err <= 1e-5 * max(1.0, np.abs(ref).max()), err
+
+
+@pytest.mark.parametrize("value", [0.0, 0.37])
+def test_constant_images(P, oracle_mod, value):
+    """Degenerate images: F = M = constant (0 exercises the all-zero image
+    range).  At a smooth random field the loss and gradient match the
+    oracle; at u = 0, J = F exactly, so A = B = C in every window, cc = 1,
+    the loss is 0 and the step leaves u at 0."""
+    import torch
+    import synth
+    shape = (12, 14, 18)
+    F = np.full(shape, value, np.float32)
+    params = P.lm_default_params()
+    ctx = P.lm_init(_t(F), _t(F.copy()), params)
+    u0 = synth.random_field(shape, seed=4, scale=1.2)
+    u = _t(u0)
+    g = torch.empty_like(u)
+    L, gmax = P.lm_eval(ctx, u, g)
+    ev = oracle_mod.evaluate(F, F, u0.astype(np.float64),
+                             _oracle_params(oracle_mod, params))
+    assert abs(L - ev["L"]) <= TOL_L * max(ev["L"], 1e-2)
+    assert np.abs(g.cpu().numpy() - ev["g"]).max() <= 1e-9 + TOL_G * ev["gmax"]
+    z = torch.zeros_like(u)
+    L0, _ = P.lm_eval(ctx, z)
+    assert abs(L0) < 1e-7
+    P.lm_reset(ctx, z)
+    P.lm_step(ctx, z)
+    assert float(z.abs().max()) <= 1e-6

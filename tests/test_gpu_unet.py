@@ -216,3 +216,57 @@ def test_unet_training_lowers_the_loss(P):
               for _ in range(30)]
     print("losses:", losses[::5])
     assert losses[-1] < 0.7 * losses[0], losses[::5]
+
+
+@pytest.mark.parametrize("D,cin,cout", [(128, 16, 16), (64, 96, 32), (128, 2, 16)])
+def test_conv3d_forward_full_size_sampled(P, oracle_mod, D, cin, cout):
+    """The network's largest layer shapes (128^3 and 64^3 levels): sampled
+    outputs against the oracle's convolution of each sample's 3x3x3
+    neighbourhood."""
+    import torch
+    from oracle import unet as U
+    r = np.random.default_rng(D + cin)
+    xt = torch.randn((D, D, D, cin), generator=torch.Generator().manual_seed(5)).to(torch.bfloat16)
+    w = r.standard_normal((cout, cin, 3, 3, 3)) / np.sqrt(27 * cin)
+    wt, w64 = _bf(_w_internal(w))
+    b = r.standard_normal(cout).astype(np.float32)
+    y = torch.empty((D, D, D, cout), device="cuda")
+    P.lm_conv3d_forward(xt.cuda(), wt, torch.from_numpy(b).cuda(), 1, y)
+    torch.cuda.synchronize()
+    x64 = xt.float().numpy().astype(np.float64)
+    xp = np.pad(x64, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    w_or = w64.reshape(cout, 27, cin).transpose(0, 2, 1).reshape(cout, cin, 3, 3, 3)
+    yg = y.cpu().numpy()
+    pts = r.integers(0, D, (300, 3))
+    pts[:20] = [[0, 0, 0], [D - 1, D - 1, D - 1], [0, D - 1, 5]] * 6 + [[1, 0, D - 1]] * 2
+    for z, yy, x in pts:
+        patch = np.moveaxis(xp[z:z + 3, yy:yy + 3, x:x + 3], -1, 0)   # (cin, 3, 3, 3)
+        ref = U.leaky_relu(U.conv3d(patch, w_or, b.astype(np.float64))[:, 1, 1, 1])
+        assert np.abs(yg[z, yy, x] - ref).max() <= 2e-5 * max(1.0, np.abs(ref).max())
+
+
+def test_unet_full_size_properties(P):
+    """128^3 input: with every convolution weight zero the output is the
+    head's bias everywhere (exactly); with real weights the forward is
+    finite and deterministic."""
+    import torch
+    import synth
+    from oracle import unet as U
+    shapes = [(ci, co) for ci, co, _ in U.LAYERS]
+    init = synth.unet_init(shapes, seed=11)
+    zero = [(np.zeros_like(w), b) for w, b in init]
+    zero[-1] = (zero[-1][0], np.array([0.25, -1.5, 3.0], np.float32))
+    F = torch.rand((128, 128, 128), generator=torch.Generator().manual_seed(1)).cuda()
+    M = torch.rand((128, 128, 128), generator=torch.Generator().manual_seed(2)).cuda()
+    u = torch.empty((3, 64, 64, 64), device="cuda")
+    net0 = P.lm_unet_create((128, 128, 128), zero)
+    P.lm_unet_forward(net0, F, M, u)
+    torch.cuda.synchronize()
+    for c, v in enumerate([0.25, -1.5, 3.0]):
+        assert bool((u[c] == v).all())
+    net = P.lm_unet_create((128, 128, 128), init)
+    u1, u2 = torch.empty_like(u), torch.empty_like(u)
+    P.lm_unet_forward(net, F, M, u1)
+    P.lm_unet_forward(net, F, M, u2)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(u1).all()) and torch.equal(u1, u2)
