@@ -105,6 +105,13 @@ __global__ void __launch_bounds__(256)
 // ----------------------------------------------------------------------
 // E1
 // ----------------------------------------------------------------------
+// The five stages run as a software pipeline over the z-slices: in round t
+// the CTA stores the gather plane of slice t + 1, takes the x sums of slice
+// t, the y sums, exact z running sums and coefficients of slice t - 1, the
+// x box of the coefficients of slice t - 2 and the output (y and z boxes,
+// dL/dJ) of slice t - 3, with one barrier per round.  Every stage boundary
+// has a double buffer, so the stages of one round touch different buffers
+// and each warp carries independent work of several stages.
 template <int W>
 struct E1Cfg {
     static constexpr int K = 2 * W + 1;
@@ -116,16 +123,18 @@ struct E1Cfg {
     // box-2 x units: four outputs each when the tile width allows
     static constexpr int XW = TX % 4 == 0 ? 4 : 2;
     static constexpr int NX2U = 3 * SY * (TX / XW);
-    // shared memory (bytes), 16-byte aligned sections
-    static constexpr int B_GQ = 2 * GY * GXP * 4;     // F', J' gather plane
-    static constexpr int B_X32 = GY * SX * 4;         // x-sums of J'
-    static constexpr int B_X64 = 2 * GY * SX * 8;     // of J'J', F'J'
+    static constexpr int KD = 16;   // delay ring (>= 2W + 5 slices of skew)
+    // shared memory (bytes), 16-byte aligned sections; [2] = double buffer
+    static constexpr int GP = GY * GXP, XP = GY * SX, AP = 3 * SY * SX,
+                         XQ = 3 * SY * TX, OP = TY * TX;
+    static constexpr int B_GQ = 2 * 2 * GP * 4;       // F', J' gather planes
+    static constexpr int B_X32 = 2 * XP * 4;          // x-sums of J'
+    static constexpr int B_X64 = 2 * 2 * XP * 8;      // of J'J', F'J'
     static constexpr int B_ZR32 = K * NT * 4;         // z ring of y-sums
     static constexpr int B_ZR64 = K * 2 * NT * 8;
-    static constexpr int B_AB = 3 * SY * SX * 4;
-    static constexpr int B_AX = 3 * SY * TX * 4;
-    // delay ring at the output points: F', J' of the last K slices
-    static constexpr int B_DL = K * 2 * TY * TX * 4;
+    static constexpr int B_AB = 2 * AP * 4;           // (a, b, c)
+    static constexpr int B_AX = 2 * XQ * 4;           // their x box
+    static constexpr int B_DL = KD * 2 * OP * 4;      // F', J' at the outputs
     static constexpr int bytes =
         B_GQ + B_X32 + B_X64 + B_ZR32 + B_ZR64 + B_AB + B_AX + B_DL;
 };
@@ -136,23 +145,23 @@ __global__ void __launch_bounds__(NT, 1)
          LnccConsts c, double* __restrict__ loss_part) {
     using C = E1Cfg<W>;
     constexpr int K = C::K, SX = C::SX, SY = C::SY, TX = C::TX, TY = C::TY;
-    constexpr int GX = C::GX, GY = C::GY, GXP = C::GXP;
+    constexpr int GX = C::GX, GY = C::GY, GXP = C::GXP, KD = C::KD;
+    constexpr int GP = C::GP, XP = C::XP, AP = C::AP, XQ = C::XQ, OP = C::OP;
     constexpr int NGS = (GX * GY + NT - 1) / NT;      // gather slots / thread
     constexpr int NX2S = (C::NX2U + NT - 1) / NT;     // x-box-2 slots
     static_assert(C::NXU <= NT, "one x-pass unit per thread");
+    static_assert(KD >= 2 * W + 5 && (KD & (KD - 1)) == 0, "delay ring");
     extern __shared__ __align__(16) unsigned char smem[];
-    int* GqF = (int*)smem;
-    int* GqJ = GqF + GY * GXP;
-    int* XJ = (int*)(smem + C::B_GQ);
-    long long* XJJ = (long long*)(smem + C::B_GQ + C::B_X32);
-    long long* XFJ = XJJ + GY * SX;
+    int* Gq = (int*)smem;                                   // [2][F, J][GP]
+    int* XJ = (int*)(smem + C::B_GQ);                       // [2][XP]
+    long long* X64 = (long long*)(smem + C::B_GQ + C::B_X32);   // [2][JJ, FJ][XP]
     int* ZR32 = (int*)(smem + C::B_GQ + C::B_X32 + C::B_X64);
     long long* ZR64 =
         (long long*)(smem + C::B_GQ + C::B_X32 + C::B_X64 + C::B_ZR32);
     float* Ab = (float*)(smem + C::B_GQ + C::B_X32 + C::B_X64 + C::B_ZR32 +
-                         C::B_ZR64);
-    float* Ax = Ab + 3 * SY * SX;
-    float* DL = Ax + 3 * SY * TX;   // [K][2][TY * TX]: F', J'
+                         C::B_ZR64);                         // [2][AP]
+    float* Ax = Ab + 2 * AP;                                 // [2][XQ]
+    float* DL = Ax + 2 * XQ;                                 // [KD][F', J'][OP]
     __shared__ double red[NT / 32];
 
     const PairDesc& P = pd[pair_of_block<1>(pd, npairs, blockIdx.x)];
@@ -177,10 +186,9 @@ __global__ void __launch_bounds__(NT, 1)
     const float mscale = c.inv_k3 * c.inv_k3 * iQ * iQ;
     const float m1scale = c.inv_k3 * iQ;
 
-    // fixed per-thread work: gather slots, x-pass unit, moment point,
-    // x-box-2 slots and output point
-    // gather slot: plane point (gx | gy << 16), its smem index, its output
-    // point (-1: none)
+    // fixed per-thread work: gather slots (plane point gx | gy << 16, smem
+    // index, output point or -1), x-pass unit, moment point, x-box-2 slots
+    // and output point
     int g_xy[NGS], g_sm[NGS], g_o[NGS];
 #pragma unroll
     for (int k = 0; k < NGS; ++k) {
@@ -251,9 +259,9 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
         for (int k = 0; k < K; ++k) r2[0][k] = r2[1][k] = r2[2][k] = 0.f;
         const int s_begin = z0 - 2 * W, s_end = z1 + 2 * W;
-        // the F', J' of slice s, the F moments of the moment slice and dJ/du
-        // of the output slice are loaded one step ahead, so their latency
-        // hides behind the previous step
+        const int nsl = s_end - s_begin;
+        // loaded one round ahead: the J' and F' of the next gather plane,
+        // S_F and B of the next moment slice, dJ/du of the next output slice
         int jqk[NGS], fqk[NGS];
         auto load_plane = [&](int sp) {
             const bool zin_ = sp >= 0 && sp < g.nz;
@@ -264,9 +272,33 @@ __global__ void __launch_bounds__(NT, 1)
                 fqk[k] = i >= 0 ? __ldg(fqv + i) : qpad;
             }
         };
+        // the loaded plane into gather buffer gf and delay-ring slot dl
+        auto store_plane = [&](int* gf, float* dl) {
+#pragma unroll
+            for (int k = 0; k < NGS; ++k) {
+                if (g_sm[k] < 0) continue;
+                int fq = fqk[k], jq = jqk[k];
+                if (fq == FQ_BAD) {
+                    bad = true;
+                    fq = qpad;
+                }
+                if (jq == JQ_BAD) {
+                    bad = true;
+                    jq = qpad;
+                }
+                gf[g_sm[k]] = fq;
+                gf[GP + g_sm[k]] = jq;
+                if (g_o[k] >= 0) {
+                    dl[g_o[k]] = (float)fq * iQ;
+                    dl[OP + g_o[k]] = (float)jq * iQ;
+                }
+            }
+        };
         int mSF = 0;
         float mB = 0.f;
         auto load_mom = [&](int cz_) {
+            mSF = 0;
+            mB = 0.f;
             if (s_in && cz_ >= 0 && cz_ < g.nz) {
                 mSF = __ldg(fsv + cz_ * sxy + s_off);
                 mB = __ldg(fbv + cz_ * sxy + s_off);
@@ -281,52 +313,46 @@ __global__ void __launch_bounds__(NT, 1)
                 odj[2] = __ldg(djv + 2 * g.V + gi);
             }
         };
+        // double buffers as (this round's, the other) pointer pairs, swapped
+        // every round: gather planes (x pass reads, store writes), x sums
+        // (x pass writes, y pass reads), coefficients (y pass writes, x box
+        // reads), their x box (x box writes, output reads)
+        int* gq_x = Gq;
+        int* gq_s = Gq + 2 * GP;
+        int* xj_w = XJ;
+        int* xj_r = XJ + XP;
+        long long* x64_w = X64;
+        long long* x64_r = X64 + 2 * XP;
+        float* ab_w = Ab;
+        float* ab_r = Ab + AP;
+        float* ax_w = Ax;
+        float* ax_r = Ax + XQ;
+        // prologue: plane 0 stored, plane 1 in flight
         load_plane(s_begin);
-        load_mom(s_begin - W);
-        load_dj(s_begin - 2 * W);
-        for (int base = s_begin; base < s_end; base += K) {
+        store_plane(gq_x, DL);
+        if (nsl > 1) load_plane(s_begin + 1);
+        __syncthreads();
+        const int nrounds = nsl + 3;
+        for (int base = 0; base < nrounds; base += K) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const int s = base + j;
-                if (s >= s_end) break;
-                const int t = s - s_begin;
-                // (1) gather plane: F' and J' in fixed point
-                {
-#pragma unroll
-                    for (int k = 0; k < NGS; ++k) {
-                        if (g_sm[k] < 0) continue;
-                        int fq = fqk[k], jq = jqk[k];
-                        if (fq == FQ_BAD) {
-                            bad = true;
-                            fq = qpad;
-                        }
-                        if (jq == JQ_BAD) {
-                            bad = true;
-                            jq = qpad;
-                        }
-                        GqF[g_sm[k]] = fq;
-                        GqJ[g_sm[k]] = jq;
-                        if (g_o[k] >= 0) {
-                            // output point: keep F', J' for 2W slices
-                            float* dl = DL + j * 2 * TY * TX + g_o[k];
-                            dl[0] = (float)fq * iQ;
-                            dl[TY * TX] = (float)jq * iQ;
-                        }
-                    }
-                }
-                const float dj0 = odj[0], dj1 = odj[1], dj2 = odj[2];
+                const int t = base + j;
+                if (t >= nrounds) break;
+                // this round's inputs, loaded last round
                 const int cSF = mSF;
                 const float cB = mB;
-                if (s + 1 < s_end) {
-                    load_plane(s + 1);
-                    load_mom(s + 1 - W);
-                    load_dj(s + 1 - 2 * W);
+                const float dj0 = odj[0], dj1 = odj[1], dj2 = odj[2];
+                // (G) plane t + 1 into its buffer; plane t + 2 requested
+                if (t + 1 < nsl) {
+                    store_plane(gq_s, DL + ((t + 1) & (KD - 1)) * 2 * OP);
+                    if (t + 2 < nsl) load_plane(s_begin + t + 2);
                 }
-                __syncthreads();
-                // (2) window sums along x: two outputs per unit
-                if (has_xu) {
-                    const int* rf = GqF + xu_gy * GXP + 2 * xu_p;
-                    const int* rj = GqJ + xu_gy * GXP + 2 * xu_p;
+                load_mom(s_begin + t - W);          // moment slice of round t+1
+                load_dj(s_begin + t - 2 - 2 * W);   // output slice of round t+1
+                // (X) window sums along x of slice t, two outputs per unit
+                if (t < nsl && has_xu) {
+                    const int* rf = gq_x + xu_gy * GXP + 2 * xu_p;
+                    const int* rj = rf + GP;
                     int vf[K + 1], vj[K + 1];
 #pragma unroll
                     for (int o = 0; o < K + 1; ++o) {
@@ -341,77 +367,82 @@ __global__ void __launch_bounds__(NT, 1)
                         sjj += (long long)vj[o] * vj[o];
                         sfj += (long long)vf[o] * vj[o];
                     }
-                    int o1 = xu_gy * SX + 2 * xu_p;
-                    XJ[o1] = sj;
-                    XJJ[o1] = sjj;
-                    XFJ[o1] = sfj;
+                    const int o1 = xu_gy * SX + 2 * xu_p;
+                    int* xj = xj_w + o1;
+                    long long* xjj = x64_w + o1;
+                    xj[0] = sj;
+                    xjj[0] = sjj;
+                    xjj[XP] = sfj;
                     sj += vj[K] - vj[0];
                     sjj += (long long)vj[K] * vj[K] - (long long)vj[0] * vj[0];
                     sfj += (long long)vf[K] * vj[K] - (long long)vf[0] * vj[0];
-                    XJ[o1 + 1] = sj;
-                    XJJ[o1 + 1] = sjj;
-                    XFJ[o1 + 1] = sfj;
+                    xj[1] = sj;
+                    xjj[1] = sjj;
+                    xjj[XP + 1] = sfj;
                 }
-                __syncthreads();
-                // (3) along y, then the z running sums (exact) and, once K
-                //     slices are in, the moments at slice cz = s - W
-                {
+                // (Y) y sums of slice t - 1, the z running sums (exact) and,
+                //     once K slices are in, the coefficients at its moment
+                //     slice
+                if (t >= 1 && t - 1 < nsl) {
+                    const int ty = t - 1;
+                    const int* xj = xj_r;
+                    const long long* xjj = x64_r;
                     int yj = 0;
                     long long yjj = 0, yfj = 0;
 #pragma unroll
                     for (int o = 0; o < K; ++o) {
-                        int a = (sy + o) * SX + sx;
-                        yj += XJ[a];
-                        yjj += XJJ[a];
-                        yfj += XFJ[a];
+                        const int a = (sy + o) * SX + sx;
+                        yj += xj[a];
+                        yjj += xjj[a];
+                        yfj += xjj[XP + a];
                     }
-                    int* zr = ZR32 + j * NT + tid;
-                    long long* zr64 = ZR64 + j * 2 * NT + tid;
+                    const int slot = (j + K - 1) % K;   // ring slot of slice t - 1
+                    int* zr = ZR32 + slot * NT + tid;
+                    long long* zr64 = ZR64 + slot * 2 * NT + tid;
                     runJ += yj - zr[0];
                     runJJ += yjj - zr64[0];
                     runFJ += yfj - zr64[NT];
                     zr[0] = yj;
                     zr64[0] = yjj;
                     zr64[NT] = yfj;
-                }
-                const int cz = s - W;
-                const bool coef_valid = t >= 2 * W;
-                if (coef_valid) {
-                    float av = 0.f, bv = 0.f, cv = 0.f;
-                    if (s_in && cz >= 0 && cz < g.nz) {
-                        long long Ai = k3 * runFJ - (long long)cSF * runJ;
-                        long long Ci = k3 * runJJ - (long long)runJ * runJ;
-                        float A = (float)Ai * mscale;
-                        float B = cB;
-                        float Cm = (float)Ci * mscale;
-                        float mF = (float)cSF * m1scale;
-                        float mJ = (float)runJ * m1scale;
-                        float BC = __fmul_rn(B, Cm), AA = __fmul_rn(A, A);
-                        float N = AA + c.eps_nr;
-                        float D = BC + c.eps_dr;
-                        // D >= eps_dr > 0: the approximate reciprocal
-                        // (about 1 ulp) is safe and far cheaper than an
-                        // IEEE division
-                        float rD = __fdividef(1.f, D);
-                        av = 2.f * A * rD;
-                        bv = -N * B * rD * rD;
-                        cv = -av * mF - 2.f * bv * mJ;
-                        if (s_out && cz >= z0 && cz < z1)
-                            lacc_f += ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD;
+                    if (ty >= 2 * W) {
+                        const int cz = s_begin + ty - W;
+                        float av = 0.f, bv = 0.f, cv = 0.f;
+                        if (s_in && cz >= 0 && cz < g.nz) {
+                            long long Ai = k3 * runFJ - (long long)cSF * runJ;
+                            long long Ci = k3 * runJJ - (long long)runJ * runJ;
+                            float A = (float)Ai * mscale;
+                            float B = cB;
+                            float Cm = (float)Ci * mscale;
+                            float mF = (float)cSF * m1scale;
+                            float mJ = (float)runJ * m1scale;
+                            float BC = __fmul_rn(B, Cm), AA = __fmul_rn(A, A);
+                            float N = AA + c.eps_nr;
+                            float D = BC + c.eps_dr;
+                            // D >= eps_dr > 0: the approximate reciprocal
+                            // (about 1 ulp) is safe and far cheaper than an
+                            // IEEE division
+                            float rD = __fdividef(1.f, D);
+                            av = 2.f * A * rD;
+                            bv = -N * B * rD * rD;
+                            cv = -av * mF - 2.f * bv * mJ;
+                            if (s_out && cz >= z0 && cz < z1)
+                                lacc_f += ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD;
+                        }
+                        float* ab = ab_w + sy * SX + sx;
+                        ab[0] = av;
+                        ab[SY * SX] = bv;
+                        ab[2 * SY * SX] = cv;
                     }
-                    Ab[sy * SX + sx] = av;
-                    Ab[SY * SX + sy * SX + sx] = bv;
-                    Ab[2 * SY * SX + sy * SX + sx] = cv;
                 }
-                __syncthreads();
-                if (coef_valid) {
-                    // (4) box of (a, b, c) along x: XW outputs per unit
-                    //     (the later ones slide the window by one)
+                // (B) box of (a, b, c) of slice t - 2 along x: XW outputs per
+                //     unit (the later ones slide the window by one)
+                if (t >= 2 && t - 2 < nsl && t - 2 >= 2 * W) {
 #pragma unroll
                     for (int k = 0; k < NX2S; ++k) {
                         if (x2_row[k] < 0) continue;
                         constexpr int XW = C::XW;
-                        const float* r = Ab + x2_row[k] * SX + XW * x2_p[k];
+                        const float* r = ab_r + x2_row[k] * SX + XW * x2_p[k];
                         float v[K + XW - 1];
 #pragma unroll
                         for (int o = 0; o < K + XW - 1; ++o) v[o] = r[o];
@@ -419,52 +450,69 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
                         for (int o = 0; o < K; ++o) s0 += v[o];
                         const float s1 = (s0 - v[0]) + v[K];
+                        float* dst = ax_w + x2_row[k] * TX + XW * x2_p[k];
                         if constexpr (XW == 4) {
                             const float s2 = (s1 - v[1]) + v[K + 1];
                             const float s3 = (s2 - v[2]) + v[K + 2];
-                            *(float4*)(Ax + x2_row[k] * TX + 4 * x2_p[k]) =
-                                make_float4(s0, s1, s2, s3);
+                            *(float4*)dst = make_float4(s0, s1, s2, s3);
                         } else {
-                            *(float2*)(Ax + x2_row[k] * TX + 2 * x2_p[k]) =
-                                make_float2(s0, s1);
+                            *(float2*)dst = make_float2(s0, s1);
                         }
                     }
-                    __syncthreads();
-                    // (5) along y into the register ring, along z, dL/dJ at
-                    //     slice r = s - 2W
-                    if (has_o) {
+                }
+                // (O) slice t - 3: box along y into the register ring, along
+                //     z, dL/dJ at the output slice two windows back
+                if (has_o && t >= 3 && t - 3 < nsl && t - 3 >= 2 * W) {
+                    const int to = t - 3;
+                    const int oslot = (j + 2 * K - 3) % K;   // ring slot of slice t-3
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int o = 0; o < K; ++o)
+                            v += ax_r[(q * SY + oy + o) * TX + ox];
+                        r2[q][oslot] = v;
+                    }
+                    const int ro = s_begin + to - 2 * W;
+                    if (to >= 4 * W && o_in) {
+                        float b3[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
                             float v = 0.f;
 #pragma unroll
-                            for (int o = 0; o < K; ++o)
-                                v += Ax[(q * SY + oy + o) * TX + ox];
-                            r2[q][j] = v;
+                            for (int i2 = 0; i2 < K; ++i2)
+                                v += r2[q][(oslot + 1 + i2) % K];
+                            b3[q] = v;
                         }
-                        const int r = cz - W;
-                        if (t >= 4 * W && o_in) {
-                            float b3[3];
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) {
-                                float v = 0.f;
-#pragma unroll
-                                for (int i2 = 0; i2 < K; ++i2)
-                                    v += r2[q][(j + 1 + i2) % K];
-                                b3[q] = v;
-                            }
-                            // F', J' of slice r sit in slot (j+1) % K
-                            const float* dl = DL + ((j + 1) % K) * 2 * TY * TX + tid;
-                            const float dLdJ =
-                                -inv_V * ((dl[0] * b3[0] +
-                                           2.f * dl[TY * TX] * b3[1] + b3[2]) *
-                                          c.inv_k3);
-                            const long long gi = (long long)(r * g.ny + y0 + oy) * gpw +
-                                                 x0 + ox;
-                            graw[gi] = dLdJ * dj0;
-                            graw[gcs + gi] = dLdJ * dj1;
-                            graw[2 * gcs + gi] = dLdJ * dj2;
-                        }
+                        // F', J' of the output slice (local to - 2W)
+                        const float* dl = DL + ((to - 2 * W) & (KD - 1)) * 2 * OP + tid;
+                        const float dLdJ =
+                            -inv_V * ((dl[0] * b3[0] + 2.f * dl[OP] * b3[1] + b3[2]) *
+                                      c.inv_k3);
+                        const long long gi = (long long)(ro * g.ny + y0 + oy) * gpw +
+                                             x0 + ox;
+                        graw[gi] = dLdJ * dj0;
+                        graw[gcs + gi] = dLdJ * dj1;
+                        graw[2 * gcs + gi] = dLdJ * dj2;
                     }
+                }
+                // this round's write buffers are next round's read buffers
+                {
+                    int* a = gq_x;
+                    gq_x = gq_s;
+                    gq_s = a;
+                    int* b = xj_w;
+                    xj_w = xj_r;
+                    xj_r = b;
+                    long long* c2 = x64_w;
+                    x64_w = x64_r;
+                    x64_r = c2;
+                    float* d = ab_w;
+                    ab_w = ab_r;
+                    ab_r = d;
+                    float* e = ax_w;
+                    ax_w = ax_r;
+                    ax_r = e;
                 }
                 __syncthreads();
             }
