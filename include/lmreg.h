@@ -234,6 +234,18 @@ LM_API int lm_batch_reset(lm_batch *b, float *const *u);
  * (host, npairs entries, may be NULL) receive each pair's last outcome. */
 LM_API int lm_batch_iterate(lm_batch *b, float *const *u, int n,
                             lm_step_info *infos);
+/* Autotuner of the batch's work split (the paper has no counterpart: it
+ * serves batches of many pairs of uneven sizes).  The evaluation kernels
+ * run a fixed number of CTA waves split among the pairs in proportion to
+ * their voxels; this call times reps evaluations at u (device fields, as
+ * for lm_batch_eval) for each candidate pair of wave counts (E1: 1, 2, 4,
+ * 8; E2: 2, 4, 8, 16 CTAs per SM in total) and keeps the fastest for all
+ * later calls (the captured iteration graph is rebuilt).  e1_waves,
+ * e2_waves, ms_best (host, may be NULL) receive the choice and its time per
+ * evaluation.  Synchronises.  LM_EINVAL on NULL b / u or reps < 1. */
+LM_API int lm_batch_autotune(lm_batch *b, float *const *u, int reps,
+                             int *e1_waves, int *e2_waves, double *ms_best);
+
 /* Carry a displacement field between pyramid levels (Section 2.1), as
  * lm_register does between its levels: the level-b field at voxel p is the
  * level-a field read trilinearly (clamped at the border) at the level-a

@@ -157,6 +157,8 @@ struct Core {
     cudaGraphExec_t gexec = nullptr;
     int graph_launches = 0;
     long long launches = 0;
+    int num_sms = 0;
+    int e1_cap = 0, e2_cap = 0;    // partial slots allocated (any plan fits)
 
     ~Core() {
         if (stream) cudaStreamSynchronize(stream);
@@ -242,6 +244,11 @@ struct Core {
     }
 };
 
+// Wave counts the autotuner tries (CTAs per SM in total for E1 and E2).
+constexpr int kE1Waves[] = {1, 2, 4, 8};
+constexpr int kE2Waves[] = {2, 4, 8, 16};
+constexpr int kMaxE1Waves = 8, kMaxE2Waves = 16;
+
 // Creates a Core for npairs pairs (all of one dtype).
 int core_create(std::unique_ptr<Core>& out, int npairs,
                 const lm_volume* fixed, const lm_volume* moving,
@@ -294,6 +301,10 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
         d.M = moving[i].data;
     }
     BatchPlan plan = plan_batch(c->hpd.data(), npairs, prm.win, num_sms);
+    c->num_sms = num_sms;
+    // partial slots for the largest plan the autotuner may pick
+    c->e1_cap = kMaxE1Waves * num_sms + npairs;
+    c->e2_cap = kMaxE2Waves * num_sms + npairs;
     const size_t f4 = sizeof(float);
     const bool smooth = prm.sigma_warp > 0;
     // per-pair buffers
@@ -305,8 +316,8 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
         (rc = c->dalloc(&lg, npairs * sizeof(LogEntry) * LOG_CAP)) ||
         (rc = c->dalloc(&c->eout, npairs * sizeof(EvalOut))) ||
         (rc = c->dalloc(&c->dpd, npairs * sizeof(PairDesc))) ||
-        (rc = c->dalloc(&c->b.part.loss, plan.e1_ctas * sizeof(double))) ||
-        (rc = c->dalloc(&c->b.part.g2max, plan.e2_ctas * sizeof(float))) ||
+        (rc = c->dalloc(&c->b.part.loss, c->e1_cap * sizeof(long long))) ||
+        (rc = c->dalloc(&c->b.part.g2max, c->e2_cap * sizeof(float))) ||
         (rc = c->dalloc(&c->b.mm_part,
                         (size_t)npairs * plan.mm_ctas * sizeof(float2))))
         return rc;
@@ -920,6 +931,81 @@ extern "C" int lm_batch_iterate(lm_batch* b, float* const* u, int n,
         if ((rc = k->read_states()) != LM_OK) return rc;
         for (int i = 0; i < k->npairs; ++i) fill_info(k->h_st[i], &infos[i]);
     }
+    return LM_OK;
+}
+
+namespace {
+// Re-split the evaluation kernels' CTAs with the given wave counts; the
+// captured iteration graph is dropped (its grids change).
+int core_replan(Core* c, int e1w, int e2w) {
+    BatchPlan plan = plan_batch(c->hpd.data(), c->npairs, c->p.win, c->num_sms,
+                                e1w, e2w);
+    if (plan.e1_ctas > c->e1_cap || plan.e2_ctas > c->e2_cap)
+        return fail(LM_EINVAL, "plan exceeds the partial slots");
+    c->b.plan = plan;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return c->push_table();
+}
+}  // namespace
+
+extern "C" int lm_batch_autotune(lm_batch* b, float* const* u, int reps,
+                                 int* e1_waves, int* e2_waves, double* ms_best) {
+    if (!b || !u) return fail(LM_EINVAL, "NULL argument");
+    if (reps < 1) return fail(LM_EINVAL, "reps must be >= 1");
+    Core* c = b->core.get();
+    int rc;
+    for (int i = 0; i < c->npairs; ++i)
+        if (!is_device_ptr(u[i]))
+            return fail(LM_EINVAL, "u of pair %d is not a device pointer", i);
+    for (int i = 0; i < c->npairs; ++i) {
+        if (c->gsink[i]) continue;
+        if ((rc = c->dalloc(&c->gsink[i],
+                            3 * (size_t)c->hpd[i].g.V * sizeof(float))) != LM_OK)
+            return rc;
+    }
+    std::vector<PairDesc> save = c->hpd;
+    for (int i = 0; i < c->npairs; ++i) {
+        c->hpd[i].u_in = u[i];
+        c->hpd[i].g_out = c->gsink[i];
+    }
+    if ((rc = c->push_table()) != LM_OK) return rc;
+    batch_prepare(c->b, c->stream);
+    cudaEvent_t e0, e1;
+    LM_CK(cudaEventCreate(&e0));
+    LM_CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int b1 = 0, b2 = 0;
+    for (int w1 : kE1Waves)
+        for (int w2 : kE2Waves) {
+            if ((rc = core_replan(c, w1, w2)) != LM_OK) break;
+            batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);   // warm-up
+            LM_CK(cudaEventRecord(e0, c->stream));
+            for (int r = 0; r < reps; ++r)
+                batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);
+            LM_CK(cudaEventRecord(e1, c->stream));
+            LM_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / reps < best) {
+                best = ms / reps;
+                b1 = w1;
+                b2 = w2;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LM_OK) return rc;
+    // restore the evaluation pointers, keep the chosen plan
+    c->hpd = save;
+    if ((rc = core_replan(c, b1, b2)) != LM_OK) return rc;
+    LM_CK(cudaStreamSynchronize(c->stream));
+    LM_CK(cudaGetLastError());
+    if (e1_waves) *e1_waves = b1;
+    if (e2_waves) *e2_waves = b2;
+    if (ms_best) *ms_best = best;
     return LM_OK;
 }
 

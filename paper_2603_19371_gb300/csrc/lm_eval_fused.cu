@@ -142,7 +142,7 @@ struct E1Cfg {
 template <int W>
 __global__ void __launch_bounds__(NT, 1)
     k_e1(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
-         LnccConsts c, double* __restrict__ loss_part) {
+         LnccConsts c, long long* __restrict__ loss_part) {
     using C = E1Cfg<W>;
     constexpr int K = C::K, SX = C::SX, SY = C::SY, TX = C::TX, TY = C::TY;
     constexpr int GX = C::GX, GY = C::GY, GXP = C::GXP, KD = C::KD;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(NT, 1)
                          C::B_ZR64);                         // [2][AP]
     float* Ax = Ab + 2 * AP;                                 // [2][XQ]
     float* DL = Ax + 2 * XQ;                                 // [KD][F', J'][OP]
-    __shared__ double red[NT / 32];
+    __shared__ long long red[NT / 32];
 
     const PairDesc& P = pd[pair_of_block<1>(pd, npairs, blockIdx.x)];
     if (trial_skip(P, mode, attempt)) return;
@@ -214,8 +214,7 @@ __global__ void __launch_bounds__(NT, 1)
     const bool has_o = tid < TX * TY;
     const int ox = has_o ? tid % TX : 0, oy = has_o ? tid / TX : 0;
 
-    double lacc = 0.0;
-    float lacc_f = 0.f;   // at most K non-negative terms, then added to lacc
+    long long lacc = 0;   // loss terms in fixed point LOSS_Q (exact sum)
     bool bad = false;
     const int e1_cx = P.e1_cx;
     const long long total = (long long)P.e1_cx * P.e1_cy * g.nz;
@@ -427,7 +426,8 @@ __global__ void __launch_bounds__(NT, 1)
                             bv = -N * B * rD * rD;
                             cv = -av * mF - 2.f * bv * mJ;
                             if (s_out && cz >= z0 && cz < z1)
-                                lacc_f += ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD;
+                                lacc += __float2ll_rn(
+                                    ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD * LOSS_Q);
                         }
                         float* ab = ab_w + sy * SX + sx;
                         ab[0] = av;
@@ -516,18 +516,15 @@ __global__ void __launch_bounds__(NT, 1)
                 }
                 __syncthreads();
             }
-            lacc += (double)lacc_f;
-            lacc_f = 0.f;
         }
     }
-    if (bad) lacc = __longlong_as_double(0x7ff8000000000000LL);   // NaN
     for (int o = 16; o > 0; o >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, o);
     if ((tid & 31) == 0) red[tid >> 5] = lacc;
-    __syncthreads();
+    const int any_bad = __syncthreads_or(bad);
     if (tid == 0) {
-        double v = 0.0;
+        long long v = 0;
         for (int w = 0; w < NT / 32; ++w) v += red[w];
-        loss_part[blockIdx.x] = v;
+        loss_part[blockIdx.x] = any_bad ? LOSS_BAD : v;
     }
 }
 
@@ -1037,8 +1034,8 @@ int quant_bits(int win) {
     }
 }
 
-// CTA ranges per pair: a single pair takes the whole grid (one CTA per SM
-// for E1, two for E2); a batch shares a grid of several waves among its
+// CTA ranges per pair: by default a single pair takes the whole grid (one
+// CTA per SM for E1, two for E2); a batch shares a grid of several waves among its
 // pairs in proportion to their work, at least one CTA each, so that every
 // CTA works on one pair.
 static void split_ctas(const long long* work, int npairs, long long target,
@@ -1055,7 +1052,8 @@ static void split_ctas(const long long* work, int npairs, long long target,
     }
 }
 
-BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms) {
+BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
+                     int e1_waves, int e2_waves) {
     BatchPlan bp{};
     const int W = (win - 1) / 2;
     const int tx1 = PLANE_X - 2 * W, ty1 = PLANE_Y - 2 * W;
@@ -1070,8 +1068,10 @@ BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms) {
         pd[p].e2_cy = (int)ceil_div(g.ny, PLANE_Y);
         w2[p] = (long long)pd[p].e2_cx * pd[p].e2_cy * g.nz;
     }
-    const long long t1 = npairs == 1 ? num_sms : 4LL * num_sms;
-    const long long t2 = npairs == 1 ? 2LL * num_sms : 8LL * num_sms;
+    if (e1_waves < 1) e1_waves = npairs == 1 ? 1 : 4;
+    if (e2_waves < 1) e2_waves = npairs == 1 ? 2 : 8;
+    const long long t1 = (long long)e1_waves * num_sms;
+    const long long t2 = (long long)e2_waves * num_sms;
     split_ctas(w1.data(), npairs, t1, c0.data(), n.data());
     for (int p = 0; p < npairs; ++p) {
         pd[p].e1_cta0 = c0[p];

@@ -95,9 +95,15 @@ __device__ __forceinline__ int pair_of_block(const PairDesc* pd, int npairs,
     return lo;
 }
 
+// Loss partials are exact: each voxel's term (1 - cc) is rounded to the
+// fixed point 2^-32 and summed in int64, so the loss does not depend on how
+// the voxels are split among CTAs (V < 2^31 keeps the sum below 2^63).
+constexpr float LOSS_Q = 4294967296.f;            // 2^32
+constexpr long long LOSS_BAD = (long long)(1ULL << 63);   // non-finite marker
+
 struct Partials {
-    double* loss;    // one per E1 CTA
-    float* g2max;    // one per E2 CTA
+    long long* loss;  // one per E1 CTA, fixed point LOSS_Q (or LOSS_BAD)
+    float* g2max;     // one per E2 CTA
 };
 
 // Totals of a batch plan.
@@ -120,8 +126,11 @@ struct Batch {
 };
 
 // Fills the column / CTA / tile fields of each host PairDesc and returns the
-// totals.  num_sms sizes the grids.
-BatchPlan plan_batch(PairDesc* host_pd, int npairs, int win, int num_sms);
+// totals.  num_sms sizes the grids: E1 and E2 run e1_waves and e2_waves CTAs
+// per SM in total, split among the pairs in proportion to their work (0: the
+// defaults, 1 and 2 for a single pair, 4 and 8 for a batch).
+BatchPlan plan_batch(PairDesc* host_pd, int npairs, int win, int num_sms,
+                     int e1_waves = 0, int e2_waves = 0);
 
 // Opt the kernels in to their dynamic shared memory (once per process).
 cudaError_t fused_setup();

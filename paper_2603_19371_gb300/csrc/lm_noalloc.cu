@@ -24,7 +24,7 @@ namespace {
 //   J (fixed point)     LM_NOALLOC_MAX_VOXELS int32
 //   dJ/du               3 x LM_NOALLOC_MAX_VOXELS floats
 //   F fixed point, window sum (int32), variance (float): LM_NOALLOC_MAX_VOXELS each
-//   loss partials       MAX_CTAS doubles
+//   loss partials       MAX_CTAS int64 (fixed point)
 //   |g|^2 partials      MAX_CTAS floats
 //   image range parts   MAX_CTAS float2
 //   QScale, EvalOut, the one-pair descriptor table
@@ -43,7 +43,7 @@ constexpr size_t OFF_FVAR =
     OFF_FSUM + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(int));
 constexpr size_t OFF_LOSS =
     OFF_FVAR + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
-constexpr size_t OFF_G2 = OFF_LOSS + align256(MAX_CTAS * sizeof(double));
+constexpr size_t OFF_G2 = OFF_LOSS + align256(MAX_CTAS * sizeof(long long));
 constexpr size_t OFF_MM = OFF_G2 + align256(MAX_CTAS * sizeof(float));
 constexpr size_t OFF_QS = OFF_MM + align256(MAX_CTAS * sizeof(float2));
 constexpr size_t OFF_OUT = OFF_QS + align256(sizeof(lmk::QScale));
@@ -228,7 +228,7 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
             for (int j = 0; j <= 2 * R; ++j) b.c.gtaps.t[j] = (float)(w[j] / sum);
         }
     }
-    b.part.loss = (double*)(base + OFF_LOSS);
+    b.part.loss = (long long*)(base + OFF_LOSS);
     b.part.g2max = (float*)(base + OFF_G2);
     b.mm_part = (float2*)(base + OFF_MM);
 

@@ -246,12 +246,12 @@ __global__ void k_warp_gauss(const PairDesc* __restrict__ pd, int npairs,
     for (int q = 0; q < 3; ++q) dst[q * g.V + i] = acc[q];
 }
 
-__device__ __forceinline__ double block_sum1024(double v, double* sh) {
+__device__ __forceinline__ long long block_sum1024_ll(long long v, long long* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) sh[wid] = v;
     __syncthreads();
-    v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0;
     if (wid == 0)
         for (int o = 16; o > 0; o >>= 1)
             v += __shfl_down_sync(0xffffffffu, v, o);
@@ -276,15 +276,21 @@ __device__ __forceinline__ float block_max1024(float v, float* sh) {
 __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
                            DecideConsts d, int mode, int attempt,
                            EvalOut* __restrict__ outs) {
-    __shared__ double shd[32];
+    __shared__ long long shl[32];
     __shared__ float shf[32];
     const PairDesc& P = pd[blockIdx.x];
     DevState* st = P.st;
     if (mode == FIN_DECIDE && attempt_skip(st, attempt)) return;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < P.e1_ncta; i += blockDim.x)
-        s += part.loss[P.e1_cta0 + i];
-    s = block_sum1024(s, shd);
+    // exact: integer partials in fixed point LOSS_Q
+    long long s = 0;
+    int lbad = 0;
+    for (int i = threadIdx.x; i < P.e1_ncta; i += blockDim.x) {
+        const long long v = part.loss[P.e1_cta0 + i];
+        if (v == LOSS_BAD) lbad = 1;
+        else s += v;
+    }
+    lbad = __syncthreads_or(lbad);
+    s = block_sum1024_ll(s, shl);
     float m = 0.f;
     int nf = 0;
     for (int i = threadIdx.x; i < P.e2_ncta; i += blockDim.x) {
@@ -295,9 +301,9 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
     nf = __syncthreads_or(nf);
     m = block_max1024(m, shf);
     if (threadIdx.x != 0) return;
-    double L = s / (double)P.g.V;
+    double L = ((double)s / (double)LOSS_Q) / (double)P.g.V;
     float gmax = sqrtf(m);
-    bool bad = nf || !isfinite(L) || !isfinite(gmax);
+    bool bad = nf || lbad || !isfinite(L) || !isfinite(gmax);
     if (mode == FIN_EXPLICIT) {
         EvalOut* o = outs + blockIdx.x;
         o->L = L;

@@ -112,6 +112,8 @@ def load():
                              ctypes.POINTER(StepInfo)],
         "lm_batch_set_targets": [V, ctypes.POINTER(D)],
         "lm_field_resample": [V, I, I, I, I, V, I, I, I, I, V],
+        "lm_batch_autotune": [V, ctypes.POINTER(V), I, ctypes.POINTER(I),
+                              ctypes.POINTER(I), ctypes.POINTER(D)],
         "lm_batch_register": [V, ctypes.POINTER(Schedule), ctypes.POINTER(V),
                               ctypes.POINTER(Report)],
         "lm_register_batch": [I, ctypes.POINTER(Volume), ctypes.POINTER(Volume),
@@ -383,6 +385,16 @@ def lm_batch_set_targets(b: Batch, targets=None):
     _check(load().lm_batch_set_targets(b.handle, arr), "lm_batch_set_targets")
 
 
+def lm_batch_autotune(b: Batch, us, reps=3):
+    """Pick the fastest evaluation work split for this batch; returns
+    (e1_waves, e2_waves, ms per evaluation)."""
+    w1, w2, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(load().lm_batch_autotune(b.handle, _ptr_array(us, b.shapes), int(reps),
+                                    ctypes.byref(w1), ctypes.byref(w2),
+                                    ctypes.byref(ms)), "lm_batch_autotune")
+    return w1.value, w2.value, ms.value
+
+
 def lm_field_resample(src, fa, dst, fb, stream=None):
     """dst (3, Db, Hb, Wb) of pyramid factor fb from src (3, Da, Ha, Wa) of
     factor fa, as between lm_register's levels."""
@@ -445,7 +457,8 @@ EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_set_state", "lm_register", "lm_state_save", "lm_state_load",
             "lm_time_passes", "lm_batch_init", "lm_batch_destroy",
             "lm_batch_eval", "lm_batch_reset", "lm_batch_iterate",
-            "lm_batch_set_targets", "lm_field_resample", "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
+            "lm_batch_set_targets", "lm_field_resample", "lm_batch_autotune",
+            "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
             "lm_strerror", "lm_last_error",
             "lm_unet_shapes", "lm_unet_create", "lm_unet_destroy",
             "lm_unet_forward", "lm_unet_train_step", "lm_unet_get_weights",

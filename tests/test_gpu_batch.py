@@ -168,3 +168,49 @@ def test_batch_targets_stop_pairs(P):
     infos = P.lm_batch_iterate(b, us, 1)
     assert infos[0].stopped == 0
     assert not torch.equal(us[0], snap[0])
+
+
+def test_batch_autotune_keeps_results(P, oracle_mod):
+    """The autotuned work split changes timing, not results: evaluations
+    still match the oracle and iterations still run."""
+    import torch
+    import synth
+    Fs, Ms = _pairs(seed0=90)
+    params = P.lm_default_params()
+    b = P.lm_batch_init(Fs, Ms, params)
+    us = [torch.from_numpy(synth.random_field(sh, seed=20 + i, scale=1.3)).cuda()
+          for i, sh in enumerate(SHAPES)]
+    w1, w2, ms = P.lm_batch_autotune(b, us, reps=2)
+    assert w1 in (1, 2, 4, 8) and w2 in (2, 4, 8, 16) and ms > 0
+    gs = [torch.empty_like(u) for u in us]
+    L, _ = P.lm_batch_eval(b, us, gs)
+    Po = _oracle_params(oracle_mod, params)
+    for i in range(len(SHAPES)):
+        ev = oracle_mod.evaluate(Fs[i].cpu().numpy(), Ms[i].cpu().numpy(),
+                                 us[i].cpu().numpy().astype(np.float64), Po)
+        assert abs(L[i] - ev["L"]) <= TOL_L * ev["L"]
+        assert np.abs(gs[i].cpu().numpy() - ev["g"]).max() <= TOL_G * ev["gmax"]
+    P.lm_batch_reset(b, us)
+    infos = P.lm_batch_iterate(b, us, 3)
+    assert all(np.isfinite(x.loss) for x in infos)
+
+
+def test_batch_equals_single_pair_bitwise(P):
+    """The loss is an exact integer sum, so neither the batch's work split
+    nor the autotuner's choice changes any result: a batch and one context
+    per pair end on bitwise-equal fields after the same iterations."""
+    import torch
+    Fs, Ms = _pairs(seed0=100)
+    params = P.lm_default_params(lambda0=0.02, step=1.0)
+    b = P.lm_batch_init(Fs, Ms, params)
+    ub = [torch.zeros((3,) + sh, device="cuda") for sh in SHAPES]
+    P.lm_batch_autotune(b, ub, reps=1)
+    P.lm_batch_reset(b, ub)
+    ib = P.lm_batch_iterate(b, ub, 8)
+    for i, sh in enumerate(SHAPES):
+        ctx = P.lm_init(Fs[i], Ms[i], params)
+        u = torch.zeros((3,) + sh, device="cuda")
+        P.lm_reset(ctx, u)
+        info = P.lm_iterate(ctx, u, 8)
+        assert info.loss == ib[i].loss and info.lambda_ == ib[i].lambda_
+        assert torch.equal(u, ub[i]), i
