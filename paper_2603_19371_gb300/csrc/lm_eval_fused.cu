@@ -410,9 +410,9 @@ __global__ void __launch_bounds__(NT, 1)
                         if (s_in && cz >= 0 && cz < g.nz) {
                             long long Ai = k3 * runFJ - (long long)cSF * runJ;
                             long long Ci = k3 * runJJ - (long long)runJ * runJ;
-                            float A = (float)Ai * mscale;
+                            float A = i64_to_f32(Ai) * mscale;
                             float B = cB;
-                            float Cm = (float)Ci * mscale;
+                            float Cm = i64_to_f32(Ci) * mscale;
                             float mF = (float)cSF * m1scale;
                             float mJ = (float)runJ * m1scale;
                             float BC = __fmul_rn(B, Cm), AA = __fmul_rn(A, A);
@@ -426,8 +426,9 @@ __global__ void __launch_bounds__(NT, 1)
                             bv = -N * B * rD * rD;
                             cv = -av * mF - 2.f * bv * mJ;
                             if (s_out && cz >= z0 && cz < z1)
-                                lacc += __float2ll_rn(
-                                    ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD * LOSS_Q);
+                                lacc += loss_fixed(
+                                    ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD * LOSS_Q,
+                                    &bad);
                         }
                         float* ab = ab_w + sy * SX + sx;
                         ab[0] = av;
@@ -865,8 +866,8 @@ __global__ void k_qscale(const PairDesc* __restrict__ pd,
 // share of the window moments is computed once per preparation: F' = F - s
 // in the fixed point (FQ_BAD marks a non-finite F), and at every voxel the
 // exact k^3 window sum S_F of those values and the variance
-// B = (k^3 S_FF - S_F^2) / (k^6 Q^2), rounded once to FP32 exactly as the
-// moment stage would round it.  Zero padding: points outside the volume
+// B = (k^3 S_FF - S_F^2) / (k^6 Q^2), converted to FP32 exactly as the
+// moment stage converts A and C.  Zero padding: points outside the volume
 // hold the fixed point of 0.  Three separable passes (x, y, z) through
 // int32 / int64 temporaries laid out in a 12-byte-per-voxel scratch.
 // ----------------------------------------------------------------------
@@ -949,7 +950,7 @@ __global__ void __launch_bounds__(256)
         const float iQ = P.qs->invQ;
         const float mscale = inv_k3 * inv_k3 * iQ * iQ;
         P.fsum[i] = s;
-        P.fvar[i] = (float)(k3 * ss - (long long)s * s) * mscale;
+        P.fvar[i] = i64_to_f32(k3 * ss - (long long)s * s) * mscale;
     }
 }
 

@@ -96,10 +96,39 @@ __device__ __forceinline__ int pair_of_block(const PairDesc* pd, int npairs,
 }
 
 // Loss partials are exact: each voxel's term (1 - cc) is rounded to the
-// fixed point 2^-32 and summed in int64, so the loss does not depend on how
-// the voxels are split among CTAs (V < 2^31 keeps the sum below 2^63).
-constexpr float LOSS_Q = 4294967296.f;            // 2^32
+// fixed point 2^-30 and summed in int64, so the loss does not depend on how
+// the voxels are split among CTAs (V < 2^31 keeps the sum below 2^63 for
+// terms below 2^2 in magnitude, and any term that cc <= max(1, eps_nr /
+// eps_dr) allows stays far below 2^32).
+constexpr float LOSS_Q = 1073741824.f;            // 2^30
 constexpr long long LOSS_BAD = (long long)(1ULL << 63);   // non-finite marker
+
+// The 64-bit integer <-> FP32 conversions share the FP64 pipe, which is
+// narrow on this part; the two helpers below use 32-bit conversions only.
+//
+// int64 -> FP32: v = hi 2^32 + lo with lo the signed low word, so that
+// |v| < 2^31 converts exactly as one rounding of lo and larger values with
+// at most ~1.3 ulp of error (one fused multiply-add of two converted words).
+__device__ __forceinline__ float i64_to_f32(long long v) {
+    const int lo = (int)(unsigned)(unsigned long long)v;
+    const int hi = (int)((v - (long long)lo) >> 32);
+    return fmaf((float)hi, 4294967296.f, (float)lo);
+}
+
+// A loss term scaled by LOSS_Q, rounded to the nearest integer (ties to
+// even).  |v| < 2^31 takes one 32-bit conversion; a larger finite v is an
+// integer already (its ulp is >= 256) and is split exactly at 2^31.  A
+// non-finite or out-of-range v sets *bad.
+__device__ __forceinline__ long long loss_fixed(float v, bool* bad) {
+    if (fabsf(v) < 0x1p31f) return (long long)__float2int_rn(v);
+    if (!(fabsf(v) < 0x1p61f)) {
+        *bad = true;
+        return 0;
+    }
+    const float h = truncf(v * 0x1p-31f);
+    return ((long long)__float2int_rz(h) << 31) +
+           (long long)__float2int_rn(fmaf(-h, 0x1p31f, v));
+}
 
 struct Partials {
     long long* loss;  // one per E1 CTA, fixed point LOSS_Q (or LOSS_BAD)
