@@ -350,13 +350,17 @@ __global__ void __launch_bounds__(NT, 1)
                 load_dj(s_begin + t - 2 - 2 * W);   // output slice of round t+1
                 // (X) window sums along x of slice t, two outputs per unit
                 if (t < nsl && has_xu) {
-                    const int* rf = gq_x + xu_gy * GXP + 2 * xu_p;
-                    const int* rj = rf + GP;
+                    // K + 1 values per row, read as 8-byte pairs
+                    const int2* rf = (const int2*)(gq_x + xu_gy * GXP + 2 * xu_p);
+                    const int2* rj = (const int2*)(gq_x + GP + xu_gy * GXP + 2 * xu_p);
                     int vf[K + 1], vj[K + 1];
 #pragma unroll
-                    for (int o = 0; o < K + 1; ++o) {
-                        vf[o] = rf[o];
-                        vj[o] = rj[o];
+                    for (int o = 0; o < (K + 1) / 2; ++o) {
+                        const int2 a = rf[o], b2 = rj[o];
+                        vf[2 * o] = a.x;
+                        vf[2 * o + 1] = a.y;
+                        vj[2 * o] = b2.x;
+                        vj[2 * o + 1] = b2.y;
                     }
                     int sj = 0;
                     long long sjj = 0, sfj = 0;
@@ -367,17 +371,15 @@ __global__ void __launch_bounds__(NT, 1)
                         sfj += (long long)vf[o] * vj[o];
                     }
                     const int o1 = xu_gy * SX + 2 * xu_p;
-                    int* xj = xj_w + o1;
-                    long long* xjj = x64_w + o1;
-                    xj[0] = sj;
-                    xjj[0] = sjj;
-                    xjj[XP] = sfj;
-                    sj += vj[K] - vj[0];
-                    sjj += (long long)vj[K] * vj[K] - (long long)vj[0] * vj[0];
-                    sfj += (long long)vf[K] * vj[K] - (long long)vf[0] * vj[0];
-                    xj[1] = sj;
-                    xjj[1] = sjj;
-                    xjj[XP + 1] = sfj;
+                    const int sj1 = sj + vj[K] - vj[0];
+                    const long long sjj1 =
+                        sjj + (long long)vj[K] * vj[K] - (long long)vj[0] * vj[0];
+                    const long long sfj1 =
+                        sfj + (long long)vf[K] * vj[K] - (long long)vf[0] * vj[0];
+                    // the two outputs as one 8-byte and two 16-byte stores
+                    *(int2*)(xj_w + o1) = make_int2(sj, sj1);
+                    *(longlong2*)(x64_w + o1) = make_longlong2(sjj, sjj1);
+                    *(longlong2*)(x64_w + XP + o1) = make_longlong2(sfj, sfj1);
                 }
                 // (Y) y sums of slice t - 1, the z running sums (exact) and,
                 //     once K slices are in, the coefficients at its moment
@@ -444,9 +446,31 @@ __global__ void __launch_bounds__(NT, 1)
                         if (x2_row[k] < 0) continue;
                         constexpr int XW = C::XW;
                         const float* r = ab_r + x2_row[k] * SX + XW * x2_p[k];
-                        float v[K + XW - 1];
+                        // K + XW - 1 values: 16-byte reads, an 8-byte tail
+                        constexpr int NV = K + XW - 1;
+                        float v[NV];
+                        if constexpr (XW == 4) {
 #pragma unroll
-                        for (int o = 0; o < K + XW - 1; ++o) v[o] = r[o];
+                            for (int o = 0; o + 4 <= NV; o += 4) {
+                                const float4 a = *(const float4*)(r + o);
+                                v[o] = a.x;
+                                v[o + 1] = a.y;
+                                v[o + 2] = a.z;
+                                v[o + 3] = a.w;
+                            }
+                            if constexpr (NV % 4 == 2) {
+                                const float2 a = *(const float2*)(r + NV - 2);
+                                v[NV - 2] = a.x;
+                                v[NV - 1] = a.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int o = 0; o < NV; o += 2) {
+                                const float2 a = *(const float2*)(r + o);
+                                v[o] = a.x;
+                                v[o + 1] = a.y;
+                            }
+                        }
                         float s0 = 0.f;
 #pragma unroll
                         for (int o = 0; o < K; ++o) s0 += v[o];
