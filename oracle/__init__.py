@@ -58,6 +58,7 @@ class Params(ctypes.Structure):
         ("reject", ctypes.c_int),
         ("tau", ctypes.c_double),
         ("max_retries", ctypes.c_int),
+        ("tile", ctypes.c_int),
     ]
 
 
@@ -66,7 +67,7 @@ class Params(ctypes.Structure):
 DEFAULTS = dict(win=5, eps_nr=1e-5, eps_dr=1e-5, sigma_grad=1.0,
                 sigma_warp=0.0, step=0.5, lambda0=0.006, mu_inc=1.5,
                 mu_dec=0.975, lambda_max=math.inf, reject=0, tau=1.0,
-                max_retries=10)
+                max_retries=10, tile=1)
 
 
 def params(**kw) -> Params:
@@ -102,6 +103,7 @@ def _load():
         lib.or_eval.argtypes = [I, I, I, P, P, P, PP, P, P, P, P, P, P]
         lib.or_compose.argtypes = [I, I, I, P, P, P]
         lib.or_trial.argtypes = [I, I, I, P, P, D, D, D, PP, P, P]
+        lib.or_tile_du.argtypes = [I, I, I, I, P, D, D, P]
         lib.or_decide.argtypes = [D, D, D, I, D, I, PP, P]
         lib.or_decide.restype = I
         lib.or_lm_step.argtypes = [I, I, I, P, P, PP, P, P, P, P, P, PI, P,
@@ -220,8 +222,21 @@ def compose(u, v):
     return out
 
 
+def tile_du(ghat, k, r, lam):
+    """Step of the pooled curvature, Eq. tilen: per non-overlapping k^3 tile
+    the mean of ghat ghat^T, then du = -(H + lam I)^-1 r ghat per voxel
+    (k = 1 is Eq. tile1)."""
+    ghat = _f64(ghat)
+    nx, ny, nz = _dims(ghat)
+    du = np.empty_like(ghat)
+    _load().or_tile_du(nx, ny, nz, int(k), _ptr(ghat), float(r), float(lam),
+                       _ptr(du))
+    return du
+
+
 def trial(u, g, gmax, r, lam, P: Params):
-    """Trial field from Eq. tile1 + Eq. compositive; returns (u', du)."""
+    """Trial field from Eq. tile1 (Eq. tilen when P.tile > 1) + Eq.
+    compositive; returns (u', du)."""
     u, g = _f64(u), _f64(g)
     nx, ny, nz = _dims(u)
     out = np.empty_like(u)

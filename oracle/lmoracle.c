@@ -24,8 +24,9 @@
  * path, not facts printed in the paper.
  *
  * Pins (tests/test_oracle_*.py): FD gradients, brute-force and library
- * filters, explicit 3x3 solves (Appendix A), identity invariants, scripted
- * loss traces for the damping/rejection rules, translation recovery.
+ * filters, explicit 3x3 solves (Appendix A, Eq. tilen), identity
+ * invariants, scripted loss traces for the damping/rejection rules,
+ * translation recovery.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -46,6 +47,7 @@ typedef struct {
     int    reject;       /* 1 = rejection rule on */
     double tau;          /* rejection tolerance ratio */
     int    max_retries;  /* retries after a rejection */
+    int    tile;         /* curvature tile side k (1 = Eq. tile1) */
 } or_params;
 
 #define OR_ACCEPT  0
@@ -399,10 +401,89 @@ void or_compose(int nx, int ny, int nz, const double *u, const double *v,
 }
 
 /* ------------------------------------------------------------------ */
+/* Pooled curvature, Eq. tilen (Section 2.3; tile side k, Section 3):   */
+/*   H_T   = |T|^-1 sum_{q in T} ghat(q) ghat(q)^T                       */
+/*   du(p) = -(H_T + lambda I)^-1 r ghat(p),   T = the tile holding p    */
+/* Readings: the tiles are the non-overlapping k x k x k blocks of the   */
+/* grid (p lies in tile floor(p / k) along each axis; the last tile of   */
+/* an axis is cut at the volume edge), and the pooling is the mean over  */
+/* the tile (a local covariance), so that k = 1 is Eq. tile1 exactly.    */
+/* Each 3 x 3 system is solved by Gaussian elimination with partial      */
+/* pivoting.  ghat: [3V]; du: [3V] (written).                            */
+/* ------------------------------------------------------------------ */
+static void solve3(double A[3][3], double b[3], double x[3])
+{
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (piv != c) {
+            for (int j = 0; j < 3; ++j) {
+                double t = A[c][j];
+                A[c][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+            double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = c + 1; r < 3; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int j = c; j < 3; ++j) A[r][j] -= f * A[c][j];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = 2; r >= 0; --r) {
+        double s = b[r];
+        for (int j = r + 1; j < 3; ++j) s -= A[r][j] * x[j];
+        x[r] = s / A[r][r];
+    }
+}
+
+void or_tile_du(int nx, int ny, int nz, int k, const double *gh, double r,
+                double lambda, double *du)
+{
+    size_t V = vox(nx, ny, nz);
+    int tx = (nx + k - 1) / k, ty = (ny + k - 1) / k, tz = (nz + k - 1) / k;
+    size_t nt = (size_t)tx * ty * tz;
+    double *H = calloc(nt * 9, sizeof(double));
+    double *cnt = calloc(nt, sizeof(double));
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t p = at(nx, ny, x, y, z);
+                size_t t = ((size_t)(z / k) * ty + y / k) * tx + x / k;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        H[9 * t + 3 * i + j] += gh[i * V + p] * gh[j * V + p];
+                cnt[t] += 1.0;
+            }
+    for (size_t t = 0; t < nt; ++t)
+        for (int e = 0; e < 9; ++e) H[9 * t + e] /= cnt[t];
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t p = at(nx, ny, x, y, z);
+                size_t t = ((size_t)(z / k) * ty + y / k) * tx + x / k;
+                double A[3][3], b[3], sol[3];
+                for (int i = 0; i < 3; ++i) {
+                    for (int j = 0; j < 3; ++j)
+                        A[i][j] = H[9 * t + 3 * i + j] + (i == j ? lambda : 0.0);
+                    b[i] = r * gh[i * V + p];
+                }
+                solve3(A, b, sol);
+                for (int i = 0; i < 3; ++i) du[i * V + p] = -sol[i];
+            }
+    free(H);
+    free(cnt);
+}
+
+/* ------------------------------------------------------------------ */
 /* Steps (c)-(d): the trial field from the current state.              */
 /*   ghat = g / gmax (0 if gmax = 0)   (reading of "normalised by the    */
 /*   same choice of epsilon": unit max-norm gradient, fixed epsilon)    */
 /*   du = -r ghat / (|ghat|^2 + lambda)          Eq. tile1, Appendix A  */
+/*   (tile side k > 1: du from the pooled curvature, or_tile_du)        */
 /*   v = step * du;  u' = v + u o (Id + v)       Eq. compositive        */
 /*   u' <- G_sigma_warp * u'  (off when sigma_warp = 0; reading: the    */
 /*   field is edge-extended, like the resampling of Eq. compositive)    */
@@ -414,15 +495,26 @@ void or_trial(int nx, int ny, int nz, const double *u, const double *g,
 {
     size_t V = vox(nx, ny, nz);
     double *v = malloc(3 * V * sizeof(double));
-    for (size_t p = 0; p < V; ++p) {
-        double gh[3];
-        for (int i = 0; i < 3; ++i)
-            gh[i] = gmax > 0 ? g[i * V + p] / gmax : 0.0;
-        double n2 = gh[0] * gh[0] + gh[1] * gh[1] + gh[2] * gh[2];
-        for (int i = 0; i < 3; ++i) {
-            double du = -r * gh[i] / (n2 + lambda);
-            if (du_out) du_out[i * V + p] = du;
-            v[i * V + p] = P->step * du;
+    if (P->tile > 1) {
+        double *gh = malloc(3 * V * sizeof(double));
+        for (size_t e = 0; e < 3 * V; ++e) gh[e] = gmax > 0 ? g[e] / gmax : 0.0;
+        or_tile_du(nx, ny, nz, P->tile, gh, r, lambda, v);
+        for (size_t e = 0; e < 3 * V; ++e) {
+            if (du_out) du_out[e] = v[e];
+            v[e] *= P->step;
+        }
+        free(gh);
+    } else {
+        for (size_t p = 0; p < V; ++p) {
+            double gh[3];
+            for (int i = 0; i < 3; ++i)
+                gh[i] = gmax > 0 ? g[i * V + p] / gmax : 0.0;
+            double n2 = gh[0] * gh[0] + gh[1] * gh[1] + gh[2] * gh[2];
+            for (int i = 0; i < 3; ++i) {
+                double du = -r * gh[i] / (n2 + lambda);
+                if (du_out) du_out[i * V + p] = du;
+                v[i * V + p] = P->step * du;
+            }
         }
     }
     or_compose(nx, ny, nz, u, v, u_out);
