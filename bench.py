@@ -226,7 +226,7 @@ def run_ours(args):
     F, M, _ = synth.voronoi_pair(shape, seed=rank)
     V = F.size
     stream = torch.cuda.Stream()
-    params = P.lm_default_params(win=args.win)
+    params = P.lm_default_params(win=args.win, tile=args.tile)
     with torch.cuda.stream(stream):
         Ft = torch.from_numpy(F).cuda()
         Mt = torch.from_numpy(M).cuda()
@@ -272,7 +272,7 @@ def run_ours(args):
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": (ITER_TRAFFIC_BYTES_PER_VOXEL * V
                             if ITER_TRAFFIC_BYTES_PER_VOXEL and shape == SHAPE
-                            and args.win == 5
+                            and args.win == 5 and args.tile == 1
                             else None),
                 "bytes_per_voxel": ITER_BYTES_PER_VOXEL,
                 "ms_iteration": ms_iter,
@@ -320,7 +320,8 @@ def run_ours(args):
     if rank != 0:
         return 0
     cpu = None
-    if world == 1 and not args.no_cpu_baseline and shape == SHAPE:
+    if (world == 1 and not args.no_cpu_baseline and shape == SHAPE
+            and args.tile == 1):
         cpu = cpu_baseline(F, M)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
@@ -331,7 +332,9 @@ def run_ours(args):
         "config": {"workload": (WORKLOAD if shape == SHAPE else
                                 WORKLOAD.replace("160x192x224",
                                                  "x".join(map(str, shape))))
-                   .replace("LNCC k=5", f"LNCC k={args.win}"),
+                   .replace("LNCC k=5", f"LNCC k={args.win}")
+                   + (f", pooled curvature tiles {args.tile}^3 (Eq. tilen)"
+                      if args.tile > 1 else ""),
                    "voxels": V,
                    "l2": "no flush: per-iteration working set (F, M, u, "
                          "trial u, two gradients: 385 MB) exceeds the "
@@ -683,6 +686,8 @@ def main():
                     help="other pair size (profiling cases)")
     ap.add_argument("--win", type=int, default=5,
                     help="LNCC window (5 for the brain workload, 7 for lung CT)")
+    ap.add_argument("--tile", type=int, default=1,
+                    help="curvature tile side k (1: Eq. tile1, >1: Eq. tilen)")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batch", "warmstart"],
                     help="batch: uneven pairs, batched vs plain; warmstart: "

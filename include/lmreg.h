@@ -82,6 +82,13 @@ typedef struct {
     int    reject;      /* 1: Eq. rejection on.                         [0] */
     double tau;         /* rejection tolerance ratio, >= 0.          [1.0] */
     int    max_retries; /* retries after a rejection, 0..32.          [10] */
+    int    tile;        /* curvature tile side k, 1..16 (Eq. tilen):    [1]
+                           1 = the pointwise step of Eq. tile1; k > 1
+                           pools ghat ghat^T as its mean over the
+                           non-overlapping k x k x k tiles of the grid
+                           (the last tile of an axis cut at the volume
+                           edge) and solves (H_tile + lambda I) du =
+                           -r ghat per voxel. */
 } lm_params;
 
 /* Coarse-to-fine schedule: levels run in order, factor[l] in {1, 2, 4}

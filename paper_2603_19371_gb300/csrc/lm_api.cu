@@ -106,6 +106,8 @@ int check_params(const lm_params* p) {
         return fail(LM_EINVAL, "tau must be finite and >= 0");
     if (p->max_retries < 0 || p->max_retries > 32)
         return fail(LM_EINVAL, "max_retries must be in [0, 32]");
+    if (p->tile < 1 || p->tile > 16)
+        return fail(LM_EINVAL, "tile must be in [1, 16], got %d", p->tile);
     return LM_OK;
 }
 
@@ -337,6 +339,7 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
         if (smooth && ((rc = c->dalloc(&d.wtmpA, 3 * V * f4)) ||
                        (rc = c->dalloc(&d.wtmpB, 3 * V * f4))))
             return rc;
+        d.tileH = nullptr;
         d.st = st + i;
         d.qs = qs + i;
         d.target = std::numeric_limits<double>::quiet_NaN();
@@ -383,6 +386,16 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
     c->b.d.max_retries = prm.max_retries;
     c->b.wtaps = make_taps(prm.sigma_warp);
     c->b.step = prm.step;
+    c->b.tile = prm.tile;
+    c->b.th_blocks = 0;
+    if (prm.tile > 1) {
+        c->b.th_blocks = plan_tiles(c->hpd.data(), npairs, prm.tile);
+        for (int i = 0; i < npairs; ++i) {
+            PairDesc& d = c->hpd[i];
+            const size_t nt = (size_t)d.th_nx * d.th_ny * d.th_nz;
+            if ((rc = c->dalloc(&d.tileH, nt * 8 * f4)) != LM_OK) return rc;
+        }
+    }
     if ((rc = c->push_table()) != LM_OK) return rc;
     out = std::move(c);
     return LM_OK;
@@ -523,6 +536,7 @@ int lm_default_params(lm_params* p) {
     p->reject = 0;
     p->tau = 1.0;
     p->max_retries = 10;
+    p->tile = 1;
     return LM_OK;
 }
 

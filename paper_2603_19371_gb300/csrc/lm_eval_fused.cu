@@ -1132,6 +1132,23 @@ BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
     return bp;
 }
 
+int plan_tiles(PairDesc* pd, int npairs, int k) {
+    // TILE_WARPS / tile_group(k) tile rows and slices per block, blocks
+    // never shared between pairs
+    const int rows_per_block = TILE_WARPS / tile_group(k);
+    int blk = 0;
+    for (int p = 0; p < npairs; ++p) {
+        const Geom& g = pd[p].g;
+        pd[p].th_nx = (int)ceil_div(g.nx, k);
+        pd[p].th_ny = (int)ceil_div(g.ny, k);
+        pd[p].th_nz = (int)ceil_div(g.nz, k);
+        pd[p].th_blk0 = blk;
+        blk += (int)ceil_div((long long)pd[p].th_ny * pd[p].th_nz,
+                             rows_per_block);
+    }
+    return blk;
+}
+
 int graw_pitch(int nx) { return (nx + 3) / 4 * 4; }
 
 long long graw_floats(const Geom& g) {

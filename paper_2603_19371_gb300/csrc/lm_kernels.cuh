@@ -54,6 +54,12 @@ struct PairDesc {
     int st_tx, st_ty, st_nzc, st_zc, st_blk0;
     // element-wise kernels (warp smoothing, copy-back): first block, count
     int ln_blk0, ln_nblk;
+    // pooled curvature (tile side k > 1, Eq. tilen): per tile the mean of
+    // g g^T of the current gradient, [th_nz][th_ny][th_nx][8] floats (xx,
+    // xy, xz, yy, yz, zz, 2 unused), or NULL; tiles per axis and the first
+    // block of the tile kernel (one block per tile row and slice)
+    float* tileH;
+    int th_nx, th_ny, th_nz, th_blk0;
 };
 
 // Pointers of an evaluation, routed by mode.
@@ -76,7 +82,8 @@ __device__ __forceinline__ bool trial_skip(const PairDesc& p, int mode,
 }
 
 // Pair whose block range starts at or below b (ranges ascend in pair
-// order).  WHICH: 1 = E1 CTAs, 2 = E2 CTAs, 3 = step blocks, 4 = line blocks.
+// order).  WHICH: 1 = E1 CTAs, 2 = E2 CTAs, 3 = step blocks, 4 = line
+// blocks, 5 = tile-curvature blocks.
 template <int WHICH>
 __device__ __forceinline__ int pair_of_block(const PairDesc* pd, int npairs,
                                              int b) {
@@ -86,7 +93,8 @@ __device__ __forceinline__ int pair_of_block(const PairDesc* pd, int npairs,
         int c0 = WHICH == 1   ? pd[mid].e1_cta0
                  : WHICH == 2 ? pd[mid].e2_cta0
                  : WHICH == 3 ? pd[mid].st_blk0
-                              : pd[mid].ln_blk0;
+                 : WHICH == 4 ? pd[mid].ln_blk0
+                              : pd[mid].th_blk0;
         if (c0 <= b)
             lo = mid;
         else
@@ -150,6 +158,8 @@ struct Batch {
     DecideConsts d;
     Taps wtaps;
     float step;
+    int tile;             // curvature tile side k (1 = Eq. tile1)
+    int th_blocks;        // blocks of the tile-curvature kernel (tile > 1)
     Partials part;
     float2* mm_part;      // npairs * plan.mm_ctas image-range partials
 };
@@ -170,6 +180,15 @@ long long graw_floats(const Geom& g);
 // for Gaussian radius R, into the 128-byte host buffer map.
 int encode_graw_map(void* map, const float* graw, const Geom& g, int R);
 int quant_bits(int win);
+// Tiles of side k per axis and the tile kernel's block range of each pair
+// (a group of tile_group(k) of a block's TILE_WARPS warps per tile row and
+// slice, so that each warp sums a few of the row's k^2 lines); returns the
+// total block count.
+constexpr int TILE_WARPS = 8;
+__host__ __device__ inline int tile_group(int k) {
+    return k * k < 8 ? 1 : k * k < 16 ? 2 : k * k < 32 ? 4 : 8;
+}
+int plan_tiles(PairDesc* host_pd, int npairs, int k);
 
 // Launch helpers; each returns the number of kernels it enqueued.
 // Preparation of the fixed image, once per reset or explicit evaluation:
@@ -182,7 +201,8 @@ int batch_prepare(const Batch& b, cudaStream_t s);
 // the trial).
 int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
                bool jpass = true);
-// Pass 2: trial field (Eq. tile1 + Eq. compositive, optional smoothing).
+// Pass 2: trial field (Eq. tile1, or Eq. tilen for tile > 1, + Eq.
+// compositive, optional smoothing).
 int batch_step(const Batch& b, int attempt, cudaStream_t s);
 // Whether batch_step also resamples M at the trial (no warp smoothing).
 bool step_resamples(const Batch& b);

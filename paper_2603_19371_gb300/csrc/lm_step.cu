@@ -3,6 +3,7 @@
 //
 //   ghat = g / gmax
 //   du   = -r ghat / (|ghat|^2 + lambda)             Eq. tile1 (Appendix A)
+//   du   = -(H_tile + lambda I)^-1 r ghat            Eq. tilen (tile side k > 1)
 //   v    = step * du
 //   u*   = v + u o (Id + v)                           Eq. compositive
 //   u*  <- G_sigma_warp * u*   (edge-extended, optional)
@@ -22,6 +23,155 @@ __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
     return st->stopped || (attempt > 0 && st->done);
 }
 
+// Pooled curvature of Eq. tilen (tile side k > 1).  For every
+// non-overlapping k x k x k tile T of the current gradient the kernel
+// forms H_T = |T|^-1 sum_T g g^T and stores the inverse of
+// A_T = H_T / gmax^2 + lambda I (the damped pooled curvature of ghat), so
+// that the step kernel's solve is one 3 x 3 product per voxel.  A group
+// of G = tile_group(k) warps owns one tile row and slice (ty, tz) (a
+// block holds 8 / G of them) and walks it two strips of 32 / k whole
+// tiles along x at a time: lane i of warp j sums g g^T of voxel columns
+// x0 + i and x0 + cw + i over the (y, z) lines j, j + G, ... of the k x k
+// lines of the strips (coalesced loads, several lines and both strips in
+// flight); then one lane per tile adds the G partials of its k columns
+// in a fixed order (deterministic) and inverts A_T by Cholesky,
+// A^-1 = L^-T L^-1 (reciprocal square roots of the pivots, about 2 ulp
+// each).  Every pivot of H + lambda I is >= lambda
+// (each Schur complement of a matrix >= lambda I is >= lambda I), so a
+// pivot that rounding pushes below lambda is raised back to it.  Runs
+// before the step kernel of every attempt, as lambda changes between
+// retries.
+constexpr int TH_W = TILE_WARPS;
+
+__device__ __forceinline__ void spd3_inverse(float a00, float a01, float a02,
+                                             float a11, float a12, float a22,
+                                             float lam, float inv[6]) {
+    // M = L^-1 from the reciprocal square roots of the pivots (the
+    // factor L itself is never needed: l_ij = a_ij m_jj - ...)
+    const float m00 = rsqrtf(fmaxf(a00, lam));
+    const float l10 = a01 * m00, l20 = a02 * m00;
+    const float m11 = rsqrtf(fmaxf(a11 - l10 * l10, lam));
+    const float l21 = (a12 - l20 * l10) * m11;
+    const float m22 = rsqrtf(fmaxf(a22 - l20 * l20 - l21 * l21, lam));
+    const float m10 = -l10 * m00 * m11;
+    const float m21 = -l21 * m11 * m22;
+    const float m20 = -(l20 * m00 + l21 * m10) * m22;
+    // A^-1 = M^T M: xx, xy, xz, yy, yz, zz
+    inv[0] = m00 * m00 + m10 * m10 + m20 * m20;
+    inv[1] = m10 * m11 + m20 * m21;
+    inv[2] = m20 * m22;
+    inv[3] = m11 * m11 + m21 * m21;
+    inv[4] = m21 * m22;
+    inv[5] = m22 * m22;
+}
+
+__global__ void __launch_bounds__(TH_W * 32)
+    k_tile_hess(const PairDesc* __restrict__ pd, int npairs, int attempt,
+                int k) {
+    __shared__ float part[TH_W][6][64];
+    const PairDesc& P = pd[pair_of_block<5>(pd, npairs, blockIdx.x)];
+    const DevState* st = P.st;
+    if (attempt_skip(st, attempt)) return;   // block-uniform
+    const Geom g = P.g;
+    const int G = tile_group(k);             // warps per tile row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lead = warp / G * G, j = warp - lead;
+    const int row = (blockIdx.x - P.th_blk0) * (TH_W / G) + warp / G;
+    const bool has_row = row < P.th_ny * P.th_nz;
+    const int ty = row % P.th_ny, tz = row / P.th_ny;
+    const int y0 = ty * k, y1 = min(y0 + k, g.ny);
+    const int z0 = tz * k, z1 = min(z0 + k, g.nz);
+    const int ky = y1 - y0, nlines = ky * (z1 - z0);
+    const float* __restrict__ gg = st->cg ? P.g1 : P.g0;
+    const int sxy = g.nx * g.ny;
+    // this warp's lines j, j + G, ... (at most 32): lane i holds the
+    // offset of line j + i G, broadcast to the warp in the sum loop
+    const int nl = has_row ? (nlines - j + G - 1) / G : 0;
+    int my_off = 0;
+    if (lane < nl) {
+        const int l = j + lane * G, dz = l / ky;
+        my_off = (z0 + dz) * sxy + (y0 + l - dz * ky) * g.nx;
+    }
+    // |T|^-1 gmax^-2 of a full tile along x and of the cut last one, and
+    // lambda
+    const float gm = st->gmax;
+    const float ig = gm > 0.f ? 1.f / gm : 0.f;
+    const float lam = (float)st->lambda;
+    const float sc_full = ig * ig / (float)(nlines * k);
+    const int w_last = g.nx - (g.nx - 1) / k * k;
+    const float sc_last = ig * ig / (float)(nlines * w_last);
+    // two strips of cw columns (whole tiles) per pass: lane i takes
+    // columns x0 + i and x0 + cw + i
+    const int cw = 32 / k * k;
+    for (int x0 = 0; x0 < g.nx; x0 += 2 * cw) {
+        const int xa = x0 + lane, xb = xa + cw;
+        const bool aa = lane < cw && xa < g.nx;
+        const bool ab = lane < cw && xb < g.nx;
+        const float* pa = gg + (aa ? xa : 0);
+        const float* pb = gg + (ab ? xb : 0);
+        float h[12];
+#pragma unroll
+        for (int e = 0; e < 12; ++e) h[e] = 0.f;
+#pragma unroll 4
+        for (int it = 0; it < nl; ++it) {
+            const int i = __shfl_sync(0xffffffffu, my_off, it);
+            if (aa) {
+                const float a0 = __ldg(pa + i);
+                const float a1 = __ldg(pa + g.V + i);
+                const float a2 = __ldg(pa + 2 * g.V + i);
+                h[0] = fmaf(a0, a0, h[0]);
+                h[1] = fmaf(a0, a1, h[1]);
+                h[2] = fmaf(a0, a2, h[2]);
+                h[3] = fmaf(a1, a1, h[3]);
+                h[4] = fmaf(a1, a2, h[4]);
+                h[5] = fmaf(a2, a2, h[5]);
+            }
+            if (ab) {
+                const float b0 = __ldg(pb + i);
+                const float b1 = __ldg(pb + g.V + i);
+                const float b2 = __ldg(pb + 2 * g.V + i);
+                h[6] = fmaf(b0, b0, h[6]);
+                h[7] = fmaf(b0, b1, h[7]);
+                h[8] = fmaf(b0, b2, h[8]);
+                h[9] = fmaf(b1, b1, h[9]);
+                h[10] = fmaf(b1, b2, h[10]);
+                h[11] = fmaf(b2, b2, h[11]);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            part[warp][e][lane] = h[e];
+            part[warp][e][32 + lane] = h[6 + e];
+        }
+        __syncthreads();
+        // one lane per tile of the two strips (at most 2 x 16)
+        const int ntile = cw / k;
+        const int sb = lane >= ntile;           // strip of this lane's tile
+        const int tl = lane - sb * ntile;       // tile within the strip
+        const int xt0 = x0 + sb * cw + tl * k;
+        if (has_row && j == 0 && lane < 2 * ntile && xt0 < g.nx) {
+            const int w = min(k, g.nx - xt0);
+            const int c0 = sb * 32 + tl * k;
+            float sum[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < G; ++q)
+                for (int c = 0; c < w; ++c)
+#pragma unroll
+                    for (int e = 0; e < 6; ++e)
+                        sum[e] += part[lead + q][e][c0 + c];
+            const float sc = w == k ? sc_full : sc_last;
+            float inv[6];
+            spd3_inverse(fmaf(sum[0], sc, lam), sum[1] * sc, sum[2] * sc,
+                         fmaf(sum[3], sc, lam), sum[4] * sc,
+                         fmaf(sum[5], sc, lam), lam, inv);
+            float* dst = P.tileH +
+                         ((size_t)(tz * P.th_ny + ty) * P.th_nx + xt0 / k) * 8;
+            *(float4*)dst = make_float4(inv[0], inv[1], inv[2], inv[3]);
+            *(float4*)(dst + 4) = make_float4(inv[4], inv[5], 0.f, 0.f);
+        }
+        __syncthreads();
+    }
+}
+
 // Trial field, one voxel per thread.  A block owns a 32 x 8 x-y tile and a
 // z range of one pair; the planes z-1, z, z+1 of u (3 components, with a
 // one-voxel x-y halo, read at edge-clamped positions) sit in a
@@ -34,10 +184,10 @@ __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
 constexpr int ST_X = 32, ST_Y = 8, ST_HX = ST_X + 2, ST_HY = ST_Y + 2;
 constexpr int ST_PLANE = ST_HX * ST_HY;
 
-template <typename T, bool RESAMPLE>
+template <typename T, bool RESAMPLE, bool TILE>
 __global__ void __launch_bounds__(ST_X * ST_Y, 3)
     k_step_compose(const PairDesc* __restrict__ pd, int npairs, int attempt,
-                   float step, int smooth) {
+                   float step, int smooth, int tile) {
     __shared__ float ring[3][3][ST_PLANE];   // [z slot][component][y][x]
     const PairDesc& P = pd[pair_of_block<3>(pd, npairs, blockIdx.x)];
     const DevState* st = P.st;
@@ -96,6 +246,15 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
     load_plane(z0, z0 % 3);
     load_plane(z0 + 1, (z0 + 1) % 3);
     const bool in_xy = x < g.nx && y < g.ny;
+    // Eq. tilen: this column's tiles (x / k, y / k fixed; z / k counted),
+    // as tile indices of the pair's table
+    int tile_col = 0, tile_slice = 0, tz_ = 0, tzr = 0;
+    if (TILE) {
+        tile_col = (y / tile) * P.th_nx + x / tile;
+        tile_slice = P.th_nx * P.th_ny;
+        tz_ = z0 / tile;
+        tzr = z0 - tz_ * tile;
+    }
     // the gradient of voxel z is loaded one step ahead
     float ng0 = 0.f, ng1 = 0.f, ng2 = 0.f;
     if (in_xy && z0 < z1) {
@@ -130,9 +289,22 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
             float gh0 = cg0 * inv;
             float gh1 = cg1 * inv;
             float gh2 = cg2 * inv;
-            float n2 = gh0 * gh0 + gh1 * gh1 + gh2 * gh2;
-            float sc = scale / (n2 + lam);
-            float v[3] = {gh0 * sc, gh1 * sc, gh2 * sc};
+            float v[3];
+            if (TILE) {
+                // the tile's (H / gmax^2 + lambda I)^-1, symmetric
+                const float* a8 = P.tileH + (size_t)(tz_ * tile_slice + tile_col) * 8;
+                const float4 ia = __ldg((const float4*)a8);
+                const float4 ib = __ldg((const float4*)(a8 + 4));
+                v[0] = scale * (ia.x * gh0 + ia.y * gh1 + ia.z * gh2);
+                v[1] = scale * (ia.y * gh0 + ia.w * gh1 + ib.x * gh2);
+                v[2] = scale * (ia.z * gh0 + ib.x * gh1 + ib.y * gh2);
+            } else {
+                float n2 = gh0 * gh0 + gh1 * gh1 + gh2 * gh2;
+                float sc = scale / (n2 + lam);
+                v[0] = gh0 * sc;
+                v[1] = gh1 * sc;
+                v[2] = gh2 * sc;
+            }
             float fl[3], f[3];
             for (int k = 0; k < 3; ++k) {
                 fl[k] = safe_floor(v[k]);
@@ -209,6 +381,10 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
 #pragma unroll
             for (int k = 0; k < NLD; ++k)
                 if (ld_dst[k] >= 0) dst[ld_dst[k]] = pre[k];
+        }
+        if (TILE && ++tzr == tile) {
+            tzr = 0;
+            ++tz_;
         }
         __syncthreads();
     }
@@ -412,24 +588,32 @@ __global__ void k_flip_slot(const PairDesc* __restrict__ pd) {
 
 bool step_resamples(const Batch& b) { return b.wtaps.R == 0; }
 
-int batch_step(const Batch& b, int attempt, cudaStream_t s) {
+template <bool TILE>
+int launch_step(const Batch& b, int attempt, cudaStream_t s) {
     const int smooth = b.wtaps.R > 0;
     const dim3 grid(b.plan.st_blocks), block(ST_X, ST_Y);
     if (!smooth) {
         if (b.dtype == LM_BF16)
-            k_step_compose<__nv_bfloat16, true><<<grid, block, 0, s>>>(
-                b.pd, b.npairs, attempt, b.step, 0);
+            k_step_compose<__nv_bfloat16, true, TILE><<<grid, block, 0, s>>>(
+                b.pd, b.npairs, attempt, b.step, 0, b.tile);
         else
-            k_step_compose<float, true><<<grid, block, 0, s>>>(
-                b.pd, b.npairs, attempt, b.step, 0);
+            k_step_compose<float, true, TILE><<<grid, block, 0, s>>>(
+                b.pd, b.npairs, attempt, b.step, 0, b.tile);
         return 1;
     }
-    k_step_compose<float, false><<<grid, block, 0, s>>>(b.pd, b.npairs, attempt,
-                                                         b.step, 1);
+    k_step_compose<float, false, TILE><<<grid, block, 0, s>>>(
+        b.pd, b.npairs, attempt, b.step, 1, b.tile);
     for (int axis = 0; axis < 3; ++axis)
         k_warp_gauss<<<b.plan.ln_blocks, TPB, 0, s>>>(b.pd, b.npairs, attempt,
                                                       b.wtaps, axis);
     return 4;
+}
+
+int batch_step(const Batch& b, int attempt, cudaStream_t s) {
+    if (b.tile <= 1) return launch_step<false>(b, attempt, s);
+    k_tile_hess<<<b.th_blocks, TH_W * 32, 0, s>>>(b.pd, b.npairs, attempt,
+                                                  b.tile);
+    return 1 + launch_step<true>(b, attempt, s);
 }
 
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,

@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
                 ("lambda0", ctypes.c_double), ("mu_inc", ctypes.c_double),
                 ("mu_dec", ctypes.c_double), ("lambda_max", ctypes.c_double),
                 ("reject", ctypes.c_int), ("tau", ctypes.c_double),
-                ("max_retries", ctypes.c_int)]
+                ("max_retries", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
 class Schedule(ctypes.Structure):
@@ -208,9 +208,11 @@ class Context:
 def lm_default_params(**overrides) -> Params:
     p = Params()
     _check(load().lm_default_params(ctypes.byref(p)), "lm_default_params")
+    names = {f[0] for f in Params._fields_}
     for k, v in overrides.items():
-        setattr(p, "lambda_max" if k == "lambda_max" else k,
-                math.inf if v is None and k == "lambda_max" else v)
+        if k not in names:
+            raise KeyError(f"lm_params has no field {k!r}")
+        setattr(p, k, math.inf if v is None and k == "lambda_max" else v)
     return p
 
 

@@ -58,6 +58,10 @@ def test_default_params_match_the_paper(lib):
     assert p.mu_inc == 1.5 and p.mu_dec == pytest.approx(0.975)
     assert p.reject == 0 and p.tau == 1.0 and p.max_retries == 10
     assert math.isinf(p.lambda_max) and p.win == 5
+    # Section 3: tile_size 1 (the pointwise step of Eq. tile1)
+    assert p.tile == 1
+    with pytest.raises(KeyError):
+        lmreg.lm_default_params(tile_size=2)
 
 
 def test_strerror(lib):
@@ -97,7 +101,8 @@ def test_init_rejects_bad_arguments_on_host(lib):
                              ("sigma_grad", 3.0, "sigma"),
                              ("step", float("nan"), "step"),
                              ("max_retries", 99, "max_retries"),
-                             ("lambda_max", 1e-9, "lambda_max")]:
+                             ("lambda_max", 1e-9, "lambda_max"),
+                             ("tile", 0, "tile"), ("tile", 17, "tile")]:
         p = lmreg.lm_default_params()
         setattr(p, field, val)
         rc, msg = _init(lib, ok, ok, p)

@@ -43,7 +43,7 @@ def _oracle_params(oracle, p):
                          sigma_warp=float(p.sigma_warp), step=float(p.step),
                          lambda0=p.lambda0, mu_inc=p.mu_inc, mu_dec=p.mu_dec,
                          lambda_max=p.lambda_max, reject=p.reject, tau=p.tau,
-                         max_retries=p.max_retries)
+                         max_retries=p.max_retries, tile=p.tile)
 
 
 def _images(F, M, dtype):
@@ -128,7 +128,7 @@ def test_identity_gives_zero_loss_and_step(P, oracle_mod):
 
 
 def _teacher_forced(P, oracle_mod, F, M, params, iters, dtype="f32",
-                    u0=None, use_iterate=False):
+                    u0=None, use_iterate=False, tol_u=TOL_U):
     """Run the GPU iteration and check every step against the oracle."""
     import torch
     Ft, Mt, Fo, Mo = _images(F, M, dtype)
@@ -165,7 +165,7 @@ def _teacher_forced(P, oracle_mod, F, M, params, iters, dtype="f32",
         if info.retries == 0 and info.accepted == 1 and not tie:
             assert info.lambda_ == pytest.approx(lam_o, rel=1e-12), t
             err = np.abs(u.cpu().numpy().astype(np.float64) - u1)
-            assert err.max() <= TOL_U, (t, _worst(err), st.lambda_, ev["L"])
+            assert err.max() <= tol_u, (t, _worst(err), st.lambda_, ev["L"])
         decisions.append((info.accepted, info.retries))
     P.lm_destroy(ctx)
     assert near_ties <= max(1, iters // 10)
@@ -208,6 +208,45 @@ def test_lm_step_parity_bf16(P, oracle_mod):
     F, M, _ = synth.blob_pair((32, 32, 32), seed=12)
     params = P.lm_default_params(lambda0=1.0)
     _teacher_forced(P, oracle_mod, F, M, params, 6, dtype="bf16")
+
+
+# Eq. tilen (tile side k > 1).  Shapes span several tiles with ragged last
+# tiles, one tile larger than the volume (k = 16), BF16 images and the
+# rejection rule.
+@pytest.mark.parametrize("k,shape,lam0", [(2, (24, 24, 24), 0.05),
+                                          (3, (19, 23, 37), 0.05),
+                                          (4, (32, 32, 32), 1.0),
+                                          (5, (26, 17, 33), 0.006),
+                                          (16, (13, 17, 29), 0.05)])
+def test_lm_step_parity_tile(P, oracle_mod, k, shape, lam0):
+    import synth
+    F, M, _ = synth.blob_pair(shape, seed=20 + k)
+    params = P.lm_default_params(lambda0=lam0, step=1.0, tile=k)
+    _teacher_forced(P, oracle_mod, F, M, params, 8)
+
+
+def test_lm_step_parity_tile_bf16_rejection(P, oracle_mod):
+    import synth
+    F, M, _ = synth.blob_pair((24, 28, 20), seed=31)
+    params = P.lm_default_params(lambda0=1e-3, step=3.0, reject=1, tau=1.0,
+                                 lambda_max=1.0, max_retries=4, tile=2)
+    _teacher_forced(P, oracle_mod, F, M, params, 8, dtype="bf16")
+
+
+def test_tile_one_is_the_pointwise_step(P):
+    """tile = 1 runs the Eq. tile1 kernel: bitwise the default path."""
+    import torch
+    import synth
+    F, M, _ = synth.blob_pair((20, 22, 24), seed=33)
+    out = []
+    for prm in (P.lm_default_params(), P.lm_default_params(tile=1)):
+        ctx = P.lm_init(_t(F), _t(M), prm)
+        u = torch.zeros((3, 20, 22, 24), device="cuda")
+        P.lm_reset(ctx, u)
+        P.lm_iterate(ctx, u, 5)
+        out.append(u.cpu().numpy())
+        P.lm_destroy(ctx)
+    assert np.array_equal(out[0], out[1])
 
 
 def test_iterate_equals_repeated_steps_and_is_deterministic(P):
@@ -318,13 +357,15 @@ def test_register_multilevel_tracks_oracle(P, oracle_mod):
     assert np.abs(u.cpu().numpy() - uo).max() < 1e-2
 
 
-def test_full_size_eval_and_step(P, oracle_mod):
-    """160x192x224 brain-shaped pair: loss, sampled gradients, one step."""
+@pytest.mark.parametrize("tile", [1, 3])
+def test_full_size_eval_and_step(P, oracle_mod, tile):
+    """160x192x224 brain-shaped pair: loss, sampled gradients, one step
+    (Eq. tile1, and Eq. tilen with k = 3)."""
     import torch
     import synth
     F, M, _ = synth.voronoi_pair((160, 192, 224), seed=0)
     shape = F.shape
-    params = P.lm_default_params()
+    params = P.lm_default_params(tile=tile)
     Po = _oracle_params(oracle_mod, params)
     u0 = synth.random_field(shape, seed=3, scale=1.5)
     ctx = P.lm_init(_t(F), _t(M), params)
