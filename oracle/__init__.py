@@ -59,6 +59,9 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_double),
         ("max_retries", ctypes.c_int),
         ("tile", ctypes.c_int),
+        ("loss", ctypes.c_int),
+        ("method", ctypes.c_int),
+        ("alpha", ctypes.c_double),
     ]
 
 
@@ -67,7 +70,10 @@ class Params(ctypes.Structure):
 DEFAULTS = dict(win=5, eps_nr=1e-5, eps_dr=1e-5, sigma_grad=1.0,
                 sigma_warp=0.0, step=0.5, lambda0=0.006, mu_inc=1.5,
                 mu_dec=0.975, lambda_max=math.inf, reject=0, tau=1.0,
-                max_retries=10, tile=1)
+                max_retries=10, tile=1, loss=0, method=0, alpha=1.0)
+
+LNCC, MSE = 0, 1          # Section 2.2 squared-loss forms
+LM, DEMONS = 0, 1         # Section 2.2 optimiser / Section 2.4 special case
 
 
 def params(**kw) -> Params:
@@ -104,6 +110,8 @@ def _load():
         lib.or_compose.argtypes = [I, I, I, P, P, P]
         lib.or_trial.argtypes = [I, I, I, P, P, D, D, D, PP, P, P]
         lib.or_tile_du.argtypes = [I, I, I, I, P, D, D, P]
+        lib.or_demons_force.argtypes = [I, I, I, P, P, P, D, P]
+        lib.or_demons_eval.argtypes = [I, I, I, P, P, P, PP, P, P, P]
         lib.or_decide.argtypes = [D, D, D, I, D, I, PP, P]
         lib.or_decide.restype = I
         lib.or_lm_step.argtypes = [I, I, I, P, P, PP, P, P, P, P, P, PI, P,
@@ -185,11 +193,40 @@ def smooth(X, sigma, clamp=False):
     return Y
 
 
+def demons_force(F, M, u, alpha):
+    """Update of Eq. demons (Section 2.4): r n / (|n|^2 + alpha^2 r^2) with
+    r = F - M(p + u) and n the gradient of M at p + u."""
+    F, M, u = _f64(F), _f64(M), _f64(u)
+    nx, ny, nz = _dims(F)
+    du = np.empty_like(u)
+    _load().or_demons_force(nx, ny, nz, _ptr(F), _ptr(M), _ptr(u),
+                            float(alpha), _ptr(du))
+    return du
+
+
+def demons_evaluate(F, M, u, P: Params):
+    """Demons evaluation: L = MSE and g = G_sigma_grad * (Eq. demons)."""
+    F, M, u = _f64(F), _f64(M), _f64(u)
+    nx, ny, nz = _dims(F)
+    L = ctypes.c_double()
+    gmax = ctypes.c_double()
+    g = np.empty((3,) + F.shape)
+    _load().or_demons_eval(nx, ny, nz, _ptr(F), _ptr(M), _ptr(u),
+                           ctypes.byref(P), ctypes.byref(L), _ptr(g),
+                           ctypes.byref(gmax))
+    return dict(L=L.value, g=g, gmax=gmax.value)
+
+
 def evaluate(F, M, u, P: Params):
     """One loss/gradient evaluation, steps (a)-(c).
 
-    Returns dict with L (= r = 1 - LNCC), dLdJ, graw, g (smoothed), gmax, cc.
+    Returns dict with L (= r = 1 - LNCC, or the MSE for P.loss = MSE),
+    dLdJ, graw, g (smoothed), gmax, cc (per-voxel cc, or (F - J)^2).
+    For P.method = DEMONS, L is the MSE and g the smoothed update of
+    Eq. demons (no dLdJ, graw, cc).
     """
+    if P.method == DEMONS:
+        return demons_evaluate(F, M, u, P)
     F, M, u = _f64(F), _f64(M), _f64(u)
     nx, ny, nz = _dims(F)
     L = ctypes.c_double()
@@ -205,6 +242,8 @@ def evaluate(F, M, u, P: Params):
 
 
 def loss(F, M, u, P: Params) -> float:
+    if P.method == DEMONS:
+        return demons_evaluate(F, M, u, P)["L"]
     F, M, u = _f64(F), _f64(M), _f64(u)
     nx, ny, nz = _dims(F)
     L = ctypes.c_double()

@@ -48,7 +48,15 @@ typedef struct {
     double tau;          /* rejection tolerance ratio */
     int    max_retries;  /* retries after a rejection */
     int    tile;         /* curvature tile side k (1 = Eq. tile1) */
+    int    loss;         /* OR_LNCC or OR_MSE */
+    int    method;       /* OR_LM or OR_DEMONS */
+    double alpha;        /* Demons damping weight, lambda_x = alpha^2 r_x^2 */
 } or_params;
+
+#define OR_LNCC   0
+#define OR_MSE    1
+#define OR_LM     0
+#define OR_DEMONS 1
 
 #define OR_ACCEPT  0
 #define OR_RETRY   1
@@ -325,19 +333,37 @@ void or_eval(int nx, int ny, int nz, const double *F, const double *M,
     double *gr = malloc(3 * V * sizeof(double));
 
     or_sample(nx, ny, nz, M, u, J, dJ);
-    or_lncc_terms(nx, ny, nz, P->win, P->eps_nr, P->eps_dr, F, J, cc, a, b, c);
-
-    double sum = 0;
-    for (size_t p = 0; p < V; ++p) sum += cc[p];
-    double L = 1.0 - sum / (double)V;
-
-    or_box(nx, ny, nz, P->win, a, Ba);
-    or_box(nx, ny, nz, P->win, b, Bb);
-    or_box(nx, ny, nz, P->win, c, Bc);
-    for (size_t p = 0; p < V; ++p) {
-        double dl = -(F[p] * Ba[p] + 2.0 * J[p] * Bb[p] + Bc[p]) / (double)V;
-        if (dLdJ) dLdJ[p] = dl;
-        for (int i = 0; i < 3; ++i) gr[i * V + p] = dl * dJ[i * V + p];
+    double L;
+    if (P->loss == OR_MSE) {
+        /* Section 2.2, MSE: L = r = V^-1 sum_p (F(p) - J(p))^2 (already a
+         * squared loss; reading: r is the loss value, as for LNCC), and
+         * dL/dJ(p) = -2 (F(p) - J(p)) / V.  cc receives (F - J)^2. */
+        double sum = 0;
+        for (size_t p = 0; p < V; ++p) {
+            double d = F[p] - J[p];
+            cc[p] = d * d;
+            sum += d * d;
+        }
+        L = sum / (double)V;
+        for (size_t p = 0; p < V; ++p) {
+            double dl = -2.0 * (F[p] - J[p]) / (double)V;
+            if (dLdJ) dLdJ[p] = dl;
+            for (int i = 0; i < 3; ++i) gr[i * V + p] = dl * dJ[i * V + p];
+        }
+    } else {
+        or_lncc_terms(nx, ny, nz, P->win, P->eps_nr, P->eps_dr, F, J, cc, a, b,
+                      c);
+        double sum = 0;
+        for (size_t p = 0; p < V; ++p) sum += cc[p];
+        L = 1.0 - sum / (double)V;
+        or_box(nx, ny, nz, P->win, a, Ba);
+        or_box(nx, ny, nz, P->win, b, Bb);
+        or_box(nx, ny, nz, P->win, c, Bc);
+        for (size_t p = 0; p < V; ++p) {
+            double dl = -(F[p] * Ba[p] + 2.0 * J[p] * Bb[p] + Bc[p]) / (double)V;
+            if (dLdJ) dLdJ[p] = dl;
+            for (int i = 0; i < 3; ++i) gr[i * V + p] = dl * dJ[i * V + p];
+        }
     }
     if (graw) memcpy(graw, gr, 3 * V * sizeof(double));
 
@@ -358,6 +384,63 @@ void or_eval(int nx, int ny, int nz, const double *F, const double *M,
     if (ccmap) memcpy(ccmap, cc, V * sizeof(double));
     free(J); free(dJ); free(cc); free(a); free(b); free(c); free(Ba);
     free(Bb); free(Bc); free(gr);
+}
+
+/* ------------------------------------------------------------------ */
+/* Demons as per-voxel LM on MSE, Eq. demons (Section 2.4):             */
+/*   r(p) = F(p) - J(p),  n(p) = dJ/du(p) (the gradient of M at p + u),  */
+/*   du(p) = r n / (|n|^2 + lambda_p),  lambda_p = alpha^2 r^2           */
+/* (0 where r and n both vanish).  du: [3V] (written).                  */
+/* ------------------------------------------------------------------ */
+void or_demons_force(int nx, int ny, int nz, const double *F,
+                     const double *M, const double *u, double alpha,
+                     double *du)
+{
+    size_t V = vox(nx, ny, nz);
+    double *J = malloc(V * sizeof(double));
+    double *dJ = malloc(3 * V * sizeof(double));
+    or_sample(nx, ny, nz, M, u, J, dJ);
+    for (size_t p = 0; p < V; ++p) {
+        double r = F[p] - J[p];
+        double n2 = dJ[p] * dJ[p] + dJ[V + p] * dJ[V + p] +
+                    dJ[2 * V + p] * dJ[2 * V + p];
+        double den = n2 + alpha * alpha * r * r;
+        for (int i = 0; i < 3; ++i)
+            du[i * V + p] = den > 0 ? r * dJ[i * V + p] / den : 0.0;
+    }
+    free(J);
+    free(dJ);
+}
+
+/* Demons evaluation of a field: L = MSE (as or_eval with OR_MSE) and     */
+/* the smoothed update g = G_sigma_grad * du of Eq. demons (reading: the  */
+/* Gaussian of the gradient doubles as the fluid-like smoothing of the    */
+/* update, Section 2.4 leaves the regulariser open); gmax = max |g|.      */
+void or_demons_eval(int nx, int ny, int nz, const double *F, const double *M,
+                    const double *u, const or_params *P, double *L_out,
+                    double *g, double *gmax_out)
+{
+    size_t V = vox(nx, ny, nz);
+    double *J = malloc(V * sizeof(double));
+    double *dJ = malloc(3 * V * sizeof(double));
+    double *du = malloc(3 * V * sizeof(double));
+    or_sample(nx, ny, nz, M, u, J, dJ);
+    double sum = 0;
+    for (size_t p = 0; p < V; ++p) sum += (F[p] - J[p]) * (F[p] - J[p]);
+    or_demons_force(nx, ny, nz, F, M, u, P->alpha, du);
+    for (int i = 0; i < 3; ++i)
+        or_smooth(nx, ny, nz, P->sigma_grad, du + i * V, g + i * V);
+    double gm = 0;
+    for (size_t p = 0; p < V; ++p) {
+        double n = sqrt(g[p] * g[p] + g[V + p] * g[V + p] +
+                        g[2 * V + p] * g[2 * V + p]);
+        if (n > gm) gm = n;
+    }
+    if (L_out) *L_out = sum / (double)V;
+    if (gmax_out) *gmax_out = gm;
+    free(J);
+    free(dJ);
+    free(du);
 }
 
 /* ------------------------------------------------------------------ */
@@ -483,7 +566,8 @@ void or_tile_du(int nx, int ny, int nz, int k, const double *gh, double r,
 /*   ghat = g / gmax (0 if gmax = 0)   (reading of "normalised by the    */
 /*   same choice of epsilon": unit max-norm gradient, fixed epsilon)    */
 /*   du = -r ghat / (|ghat|^2 + lambda)          Eq. tile1, Appendix A  */
-/*   (tile side k > 1: du from the pooled curvature, or_tile_du)        */
+/*   (tile side k > 1: du from the pooled curvature, or_tile_du;        */
+/*   Demons: du = g, the smoothed update of Eq. demons, or_demons_eval) */
 /*   v = step * du;  u' = v + u o (Id + v)       Eq. compositive        */
 /*   u' <- G_sigma_warp * u'  (off when sigma_warp = 0; reading: the    */
 /*   field is edge-extended, like the resampling of Eq. compositive)    */
@@ -495,7 +579,13 @@ void or_trial(int nx, int ny, int nz, const double *u, const double *g,
 {
     size_t V = vox(nx, ny, nz);
     double *v = malloc(3 * V * sizeof(double));
-    if (P->tile > 1) {
+    if (P->method == OR_DEMONS) {
+        /* Demons: g is the smoothed update of Eq. demons; v = step * g */
+        for (size_t e = 0; e < 3 * V; ++e) {
+            if (du_out) du_out[e] = g[e];
+            v[e] = P->step * g[e];
+        }
+    } else if (P->tile > 1) {
         double *gh = malloc(3 * V * sizeof(double));
         for (size_t e = 0; e < 3 * V; ++e) gh[e] = gmax > 0 ? g[e] / gmax : 0.0;
         or_tile_du(nx, ny, nz, P->tile, gh, r, lambda, v);
@@ -587,13 +677,20 @@ void or_lm_step(int nx, int ny, int nz, const double *F, const double *M,
     for (;;) {
         double Lt, gmt, lam;
         or_trial(nx, ny, nz, u, g, *gmax, *L_t, *lambda, P, ut, NULL);
-        or_eval(nx, ny, nz, F, M, ut, P, &Lt, NULL, NULL, gt, &gmt, NULL);
+        if (P->method == OR_DEMONS)
+            or_demons_eval(nx, ny, nz, F, M, ut, P, &Lt, gt, &gmt);
+        else
+            or_eval(nx, ny, nz, F, M, ut, P, &Lt, NULL, NULL, gt, &gmt, NULL);
         ++nev;
         if (nev == 1) {
             if (u_first) memcpy(u_first, ut, 3 * V * sizeof(double));
             if (L_first) *L_first = Lt;
         }
-        int act = or_decide(Lt, *L_t, *L_prev, *has_prev, *lambda, nret, P,
+        /* Demons: no damping rule, every step is kept (Section 2.4) */
+        int act = OR_ACCEPT;
+        lam = *lambda;
+        if (P->method != OR_DEMONS)
+            act = or_decide(Lt, *L_t, *L_prev, *has_prev, *lambda, nret, P,
                             &lam);
         *lambda = lam;
         if (act == OR_RETRY) {
@@ -742,7 +839,10 @@ void or_register(int nx, int ny, int nz, const double *F, const double *M,
             or_resample_field(cx, cy, cz, cf, cur, lx, ly, lz, f, ul);
         double L, gmax, Lp = 0, lam = P->lambda0;
         int hp = 0;
-        or_eval(lx, ly, lz, Fl, Ml, ul, P, &L, NULL, NULL, gl, &gmax, NULL);
+        if (P->method == OR_DEMONS)
+            or_demons_eval(lx, ly, lz, Fl, Ml, ul, P, &L, gl, &gmax);
+        else
+            or_eval(lx, ly, lz, Fl, Ml, ul, P, &L, NULL, NULL, gl, &gmax, NULL);
         ++evals;
         for (int it = 0; it < iters[l]; ++it) {
             int acc, ret, ev;
