@@ -226,7 +226,12 @@ def run_ours(args):
     F, M, _ = synth.voronoi_pair(shape, seed=rank)
     V = F.size
     stream = torch.cuda.Stream()
-    params = P.lm_default_params(win=args.win, tile=args.tile)
+    params = P.lm_default_params(
+        win=args.win, tile=args.tile,
+        loss=P.LM_LOSS_MSE if args.loss == "mse" else P.LM_LOSS_LNCC,
+        method=(P.LM_METHOD_DEMONS if args.method == "demons"
+                else P.LM_METHOD_LM),
+        alpha=args.alpha, **({"step": 1.0} if args.method == "demons" else {}))
     with torch.cuda.stream(stream):
         Ft = torch.from_numpy(F).cuda()
         Mt = torch.from_numpy(M).cuda()
@@ -273,6 +278,7 @@ def run_ours(args):
                 "traffic": (ITER_TRAFFIC_BYTES_PER_VOXEL * V
                             if ITER_TRAFFIC_BYTES_PER_VOXEL and shape == SHAPE
                             and args.win == 5 and args.tile == 1
+                            and args.loss == "lncc"
                             else None),
                 "bytes_per_voxel": ITER_BYTES_PER_VOXEL,
                 "ms_iteration": ms_iter,
@@ -321,7 +327,7 @@ def run_ours(args):
         return 0
     cpu = None
     if (world == 1 and not args.no_cpu_baseline and shape == SHAPE
-            and args.tile == 1):
+            and args.tile == 1 and args.loss == "lncc"):
         cpu = cpu_baseline(F, M)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
@@ -334,7 +340,11 @@ def run_ours(args):
                                                  "x".join(map(str, shape))))
                    .replace("LNCC k=5", f"LNCC k={args.win}")
                    + (f", pooled curvature tiles {args.tile}^3 (Eq. tilen)"
-                      if args.tile > 1 else ""),
+                      if args.tile > 1 else "")
+                   + (", MSE loss" if args.loss == "mse" and
+                      args.method == "lm" else "")
+                   + (f", Demons (Eq. demons, alpha {args.alpha:g}, step 1)"
+                      if args.method == "demons" else ""),
                    "voxels": V,
                    "l2": "no flush: per-iteration working set (F, M, u, "
                          "trial u, two gradients: 385 MB) exceeds the "
@@ -673,6 +683,12 @@ def run_warmstart(args):
     return 0
 
 
+def _normalise_args(args):
+    if args.method == "demons":
+        args.loss = "mse"
+    return args
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -688,6 +704,11 @@ def main():
                     help="LNCC window (5 for the brain workload, 7 for lung CT)")
     ap.add_argument("--tile", type=int, default=1,
                     help="curvature tile side k (1: Eq. tile1, >1: Eq. tilen)")
+    ap.add_argument("--loss", default="lncc", choices=["lncc", "mse"])
+    ap.add_argument("--method", default="lm", choices=["lm", "demons"],
+                    help="demons implies --loss mse")
+    ap.add_argument("--alpha", type=float, default=1.0,
+                    help="Demons damping weight (lambda_x = alpha^2 r^2)")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batch", "warmstart"],
                     help="batch: uneven pairs, batched vs plain; warmstart: "
@@ -700,7 +721,7 @@ def main():
     ap.add_argument("--ws-level2", type=int, default=0)
     ap.add_argument("--batch-pairs", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=100)
-    args = ap.parse_args()
+    args = _normalise_args(ap.parse_args())
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

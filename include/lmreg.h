@@ -53,6 +53,12 @@ extern "C" {
 #define LM_EUNSUPPORTED -6  /* valid request this build does not handle */
 #define LM_ESTATE       -7  /* call out of order (e.g. lm_step before reset) */
 
+/* ---- similarity and method (lm_params.loss, lm_params.method) ---------- */
+#define LM_LOSS_LNCC     0  /* r = 1 - LNCC (Section 2.2)                    */
+#define LM_LOSS_MSE      1  /* r = V^-1 sum (F - M(p + u))^2 (Section 2.2)   */
+#define LM_METHOD_LM     0  /* factored LM, Eq. tile1 / Eq. tilen            */
+#define LM_METHOD_DEMONS 1  /* Demons as per-voxel LM on MSE, Eq. demons     */
+
 /* ---- image storage types ----------------------------------------------- */
 #define LM_F32  0  /* float32 images */
 #define LM_BF16 1  /* bfloat16 images, sampled and accumulated in float32 */
@@ -89,6 +95,20 @@ typedef struct {
                            (the last tile of an axis cut at the volume
                            edge) and solves (H_tile + lambda I) du =
                            -r ghat per voxel. */
+    int    loss;        /* LM_LOSS_LNCC or LM_LOSS_MSE.              [LNCC] */
+    int    method;      /* LM_METHOD_LM or LM_METHOD_DEMONS.           [LM]
+                           Demons (Section 2.4) needs LM_LOSS_MSE, tile 1
+                           and reject 0.  Each iteration takes, per voxel,
+                           du = r n / (|n|^2 + alpha^2 r^2) with the voxel's
+                           residual r = F - M(p + u) and n the gradient of
+                           M at p + u (Eq. demons), smooths du with the
+                           sigma_grad Gaussian, scales it by step and
+                           composes it (Eq. compositive; sigma_warp
+                           smoothing as for LM).  Every step is kept; the
+                           damping fields are unused; the reported loss is
+                           the MSE and gmax the largest smoothed update. */
+    float  alpha;       /* Demons damping weight, lambda_x = alpha^2 r^2,
+                           > 0.                                          [1] */
 } lm_params;
 
 /* Coarse-to-fine schedule: levels run in order, factor[l] in {1, 2, 4}

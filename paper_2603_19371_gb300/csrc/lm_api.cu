@@ -108,6 +108,18 @@ int check_params(const lm_params* p) {
         return fail(LM_EINVAL, "max_retries must be in [0, 32]");
     if (p->tile < 1 || p->tile > 16)
         return fail(LM_EINVAL, "tile must be in [1, 16], got %d", p->tile);
+    if (p->loss != LM_LOSS_LNCC && p->loss != LM_LOSS_MSE)
+        return fail(LM_EINVAL, "loss must be LM_LOSS_LNCC or LM_LOSS_MSE");
+    if (p->method != LM_METHOD_LM && p->method != LM_METHOD_DEMONS)
+        return fail(LM_EINVAL,
+                    "method must be LM_METHOD_LM or LM_METHOD_DEMONS");
+    if (!(p->alpha > 0) || !std::isfinite(p->alpha))
+        return fail(LM_EINVAL, "alpha must be finite and > 0");
+    if (p->method == LM_METHOD_DEMONS &&
+        (p->loss != LM_LOSS_MSE || p->tile != 1 || p->reject != 0))
+        return fail(LM_EINVAL,
+                    "method LM_METHOD_DEMONS needs loss LM_LOSS_MSE, tile 1 "
+                    "and reject 0");
     return LM_OK;
 }
 
@@ -384,6 +396,11 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
     c->b.d.tau = prm.tau;
     c->b.d.reject = prm.reject;
     c->b.d.max_retries = prm.max_retries;
+    c->b.d.mse = prm.loss == LM_LOSS_MSE;
+    c->b.d.demons = prm.method == LM_METHOD_DEMONS;
+    c->b.loss = prm.loss;
+    c->b.method = prm.method;
+    c->b.alpha = prm.alpha;
     c->b.wtaps = make_taps(prm.sigma_warp);
     c->b.step = prm.step;
     c->b.tile = prm.tile;
@@ -537,6 +554,9 @@ int lm_default_params(lm_params* p) {
     p->tau = 1.0;
     p->max_retries = 10;
     p->tile = 1;
+    p->loss = LM_LOSS_LNCC;
+    p->method = LM_METHOD_LM;
+    p->alpha = 1.f;
     return LM_OK;
 }
 

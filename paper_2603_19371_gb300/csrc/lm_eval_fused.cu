@@ -28,7 +28,8 @@
 //
 // HBM traffic per voxel: the J pass reads u, M (16 B) and writes Jq, dJ
 // (16 B); E1 reads F', S_F, B, Jq, dJ (28 B) and writes g_raw (12 B); E2
-// reads g_raw (12 B) and writes g (12 B).  Halo re-reads hit L2.
+// reads g_raw (12 B) and writes g (12 B).  Halo re-reads hit L2.  For the
+// MSE loss and for Demons a pointwise kernel takes E1's place.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -549,6 +550,79 @@ __global__ void __launch_bounds__(NT, 1)
     if (tid == 0) {
         long long v = 0;
         for (int w = 0; w < NT / 32; ++w) v += red[w];
+        loss_part[blockIdx.x] = any_bad ? LOSS_BAD : v;
+    }
+}
+
+// ----------------------------------------------------------------------
+// Pointwise evaluation for MSE (Section 2.2) and Demons (Section 2.4), in
+// place of E1.  Per voxel: dq = Fq - Jq, the fixed-point F - J (exact);
+// the loss term dq^2, rounded to the MSE unit (mse_shift) and summed
+// exactly; and g_raw:
+//   MSE:    g_raw = dL/dJ dJ/du,  dL/dJ = -2 (F - J) / V
+//   Demons: g_raw = r n / (|n|^2 + alpha^2 r^2), r = F - J, n = dJ/du
+//           (Eq. demons; 0 where r and n both vanish)
+// The CTAs of a pair (its E1 partial slots) split its voxels into
+// contiguous ranges.  HBM traffic per voxel: Fq, Jq, dJ/du (20 B) in,
+// g_raw (12 B) out.
+// ----------------------------------------------------------------------
+constexpr int NTP = 1024;   // pointwise kernel: one CTA of 32 warps per slot
+
+template <bool DEMONS>
+__global__ void __launch_bounds__(NTP)
+    k_pointwise(const PairDesc* __restrict__ pd, int npairs, int mode,
+                int attempt, float alpha, long long* __restrict__ loss_part) {
+    __shared__ long long red[NTP / 32];
+    const PairDesc& P = pd[pair_of_block<1>(pd, npairs, blockIdx.x)];
+    if (trial_skip(P, mode, attempt)) return;
+    const Geom g = P.g;
+    const int c = blockIdx.x - P.e1_cta0;
+    const long long i0 = g.V * c / P.e1_ncta, i1 = g.V * (c + 1) / P.e1_ncta;
+    const int* __restrict__ fqv = P.fq;
+    const int* __restrict__ jqv = P.jq;
+    const float* __restrict__ djv = P.dj;
+    float* __restrict__ graw = P.graw;
+    const float iQ = P.qs->invQ;
+    const int sh = mse_shift(P.qs->qlim);
+    const long long half = sh > 0 ? 1LL << (sh - 1) : 0;
+    const float coef = -2.f / (float)g.V;
+    const float a2 = alpha * alpha;
+    const int gpw = P.gp_w;
+    const long long gcs = (long long)g.nz * g.ny * gpw;
+    const bool dense = gpw == g.nx;
+    long long lacc = 0;
+    bool bad = false;
+#pragma unroll 4
+    for (long long i = i0 + threadIdx.x; i < i1; i += NTP) {
+        const int fq = __ldg(fqv + i), jq = __ldg(jqv + i);
+        const float d0 = __ldg(djv + i), d1 = __ldg(djv + g.V + i),
+                    d2 = __ldg(djv + 2 * g.V + i);
+        float s = 0.f;
+        if (fq == FQ_BAD || jq == JQ_BAD) {
+            bad = true;
+        } else {
+            const int dq = fq - jq;
+            lacc += ((long long)dq * dq + half) >> sh;
+            const float r = (float)dq * iQ;
+            if (DEMONS) {
+                const float den = d0 * d0 + d1 * d1 + d2 * d2 + a2 * r * r;
+                s = den > 0.f ? r / den : 0.f;
+            } else {
+                s = coef * r;
+            }
+        }
+        const long long gi =
+            dense ? i : (i / g.nx) * gpw + (i - (i / g.nx) * g.nx);
+        graw[gi] = s * d0;
+        graw[gcs + gi] = s * d1;
+        graw[2 * gcs + gi] = s * d2;
+    }
+    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
+    const int any_bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        long long v = 0;
+        for (int w = 0; w < NTP / 32; ++w) v += red[w];
         loss_part[blockIdx.x] = any_bad ? LOSS_BAD : v;
     }
 }
@@ -1214,6 +1288,21 @@ int batch_prepare(const Batch& b, cudaStream_t s) {
     return 5;
 }
 
+// The loss kernel of pass 1: E1 for LNCC, the pointwise kernel otherwise.
+static int launch_loss(const Batch& b, int mode, int attempt, cudaStream_t s) {
+    if (b.method == LM_METHOD_DEMONS) {
+        k_pointwise<true><<<b.plan.e1_ctas, NTP, 0, s>>>(
+            b.pd, b.npairs, mode, attempt, b.alpha, b.part.loss);
+        return 1;
+    }
+    if (b.loss == LM_LOSS_MSE) {
+        k_pointwise<false><<<b.plan.e1_ctas, NTP, 0, s>>>(
+            b.pd, b.npairs, mode, attempt, b.alpha, b.part.loss);
+        return 1;
+    }
+    return launch_e1_w(b, mode, attempt, s);
+}
+
 int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
                bool jpass) {
     int n = 0;
@@ -1223,7 +1312,7 @@ int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
                 b.pd, b.npairs, mode, attempt);
             n += 1;
         }
-        n += launch_e1_w(b, mode, attempt, s);
+        n += launch_loss(b, mode, attempt, s);
         n += launch_e2_r<__nv_bfloat16>(b, mode, attempt, s);
     } else {
         if (jpass) {
@@ -1231,7 +1320,7 @@ int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
                 b.pd, b.npairs, mode, attempt);
             n += 1;
         }
-        n += launch_e1_w(b, mode, attempt, s);
+        n += launch_loss(b, mode, attempt, s);
         n += launch_e2_r<float>(b, mode, attempt, s);
     }
     return n;

@@ -87,6 +87,8 @@ struct LnccConsts {
 struct DecideConsts {
     double lambda0, mu_inc, mu_dec, lambda_max, tau;
     int reject, max_retries;
+    int mse;      // loss partials are MSE sums (unit from the pair's QScale)
+    int demons;   // every trial is kept (Section 2.4), lambda unused
 };
 
 // Image element load as float.

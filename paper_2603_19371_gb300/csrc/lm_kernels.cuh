@@ -111,6 +111,17 @@ __device__ __forceinline__ int pair_of_block(const PairDesc* pd, int npairs,
 constexpr float LOSS_Q = 1073741824.f;            // 2^30
 constexpr long long LOSS_BAD = (long long)(1ULL << 63);   // non-finite marker
 
+// MSE partials: per voxel the exact square of the fixed-point difference
+// dq = Fq - Jq (|dq| <= 2^(qb + 1)), shifted right by mse_shift(qlim) with
+// rounding so that a term stays below 2^32 and a pair's sum (V < 2^30)
+// below 2^62.  The loss is sum * 2^shift / (Q^2 V).
+__host__ __device__ inline int mse_shift(int qlim) {
+    int qb = 0;
+    while ((1 << (qb + 1)) <= qlim) ++qb;
+    const int sh = 2 * (qb + 1) - 32;
+    return sh > 0 ? sh : 0;
+}
+
 // The 64-bit integer <-> FP32 conversions share the FP64 pipe, which is
 // narrow on this part; the two helpers below use 32-bit conversions only.
 //
@@ -160,6 +171,9 @@ struct Batch {
     float step;
     int tile;             // curvature tile side k (1 = Eq. tile1)
     int th_blocks;        // blocks of the tile-curvature kernel (tile > 1)
+    int loss;             // LM_LOSS_LNCC / LM_LOSS_MSE
+    int method;           // LM_METHOD_LM / LM_METHOD_DEMONS
+    float alpha;          // Demons damping weight
     Partials part;
     float2* mm_part;      // npairs * plan.mm_ctas image-range partials
 };
@@ -198,7 +212,9 @@ int plan_tiles(PairDesc* host_pd, int npairs, int k);
 int batch_prepare(const Batch& b, cudaStream_t s);
 // Pass 1: loss partials, dL/dJ, smoothed gradient, |g|^2 partials.  With
 // jpass = false the J pass is left out (the step kernel already resampled
-// the trial).
+// the trial).  LNCC runs E1; MSE and Demons run one pointwise kernel in
+// its place (MSE: g_raw = dL/dJ dJ/du; Demons: g_raw = the update of
+// Eq. demons), both followed by E2.
 int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
                bool jpass = true);
 // Pass 2: trial field (Eq. tile1, or Eq. tilen for tile > 1, + Eq.

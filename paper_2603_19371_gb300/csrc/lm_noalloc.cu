@@ -157,6 +157,11 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
         !(prm.sigma_grad >= 0 && prm.sigma_grad <= 2) || !(prm.eps_dr > 0) ||
         !(prm.eps_nr >= 0))
         return fail(LM_EINVAL, "win, sigma_grad or eps out of range");
+    if ((prm.loss != LM_LOSS_LNCC && prm.loss != LM_LOSS_MSE) ||
+        (prm.method != LM_METHOD_LM && prm.method != LM_METHOD_DEMONS) ||
+        !(prm.alpha > 0) ||
+        (prm.method == LM_METHOD_DEMONS && prm.loss != LM_LOSS_MSE))
+        return fail(LM_EINVAL, "loss, method or alpha out of range");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -228,6 +233,11 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
             for (int j = 0; j <= 2 * R; ++j) b.c.gtaps.t[j] = (float)(w[j] / sum);
         }
     }
+    b.loss = prm.loss;
+    b.method = prm.method;
+    b.alpha = prm.alpha;
+    b.d.mse = prm.loss == LM_LOSS_MSE;
+    b.d.demons = prm.method == LM_METHOD_DEMONS;
     b.part.loss = (long long*)(base + OFF_LOSS);
     b.part.g2max = (float*)(base + OFF_G2);
     b.mm_part = (float2*)(base + OFF_MM);

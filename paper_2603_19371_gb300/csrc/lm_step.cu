@@ -4,6 +4,7 @@
 //   ghat = g / gmax
 //   du   = -r ghat / (|ghat|^2 + lambda)             Eq. tile1 (Appendix A)
 //   du   = -(H_tile + lambda I)^-1 r ghat            Eq. tilen (tile side k > 1)
+//   v    = step * g  (Demons: g is the smoothed update of Eq. demons)
 //   v    = step * du
 //   u*   = v + u o (Id + v)                           Eq. compositive
 //   u*  <- G_sigma_warp * u*   (edge-extended, optional)
@@ -184,7 +185,14 @@ __global__ void __launch_bounds__(TH_W * 32)
 constexpr int ST_X = 32, ST_Y = 8, ST_HX = ST_X + 2, ST_HY = ST_Y + 2;
 constexpr int ST_PLANE = ST_HX * ST_HY;
 
-template <typename T, bool RESAMPLE, bool TILE>
+// How the step kernel forms v from the current g.
+enum StepMode {
+    STEP_POINT = 0,   // Eq. tile1
+    STEP_TILE = 1,    // Eq. tilen with the tile kernel's inverses
+    STEP_DIRECT = 2,  // v = step * g (Demons)
+};
+
+template <typename T, bool RESAMPLE, int MODE>
 __global__ void __launch_bounds__(ST_X * ST_Y, 3)
     k_step_compose(const PairDesc* __restrict__ pd, int npairs, int attempt,
                    float step, int smooth, int tile) {
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
     // Eq. tilen: this column's tiles (x / k, y / k fixed; z / k counted),
     // as tile indices of the pair's table
     int tile_col = 0, tile_slice = 0, tz_ = 0, tzr = 0;
-    if (TILE) {
+    if (MODE == STEP_TILE) {
         tile_col = (y / tile) * P.th_nx + x / tile;
         tile_slice = P.th_nx * P.th_ny;
         tz_ = z0 / tile;
@@ -290,7 +298,11 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
             float gh1 = cg1 * inv;
             float gh2 = cg2 * inv;
             float v[3];
-            if (TILE) {
+            if (MODE == STEP_DIRECT) {
+                v[0] = cg0 * step;
+                v[1] = cg1 * step;
+                v[2] = cg2 * step;
+            } else if (MODE == STEP_TILE) {
                 // the tile's (H / gmax^2 + lambda I)^-1, symmetric
                 const float* a8 = P.tileH + (size_t)(tz_ * tile_slice + tile_col) * 8;
                 const float4 ia = __ldg((const float4*)a8);
@@ -382,7 +394,7 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
             for (int k = 0; k < NLD; ++k)
                 if (ld_dst[k] >= 0) dst[ld_dst[k]] = pre[k];
         }
-        if (TILE && ++tzr == tile) {
+        if (MODE == STEP_TILE && ++tzr == tile) {
             tzr = 0;
             ++tz_;
         }
@@ -477,7 +489,15 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
     nf = __syncthreads_or(nf);
     m = block_max1024(m, shf);
     if (threadIdx.x != 0) return;
-    double L = ((double)s / (double)LOSS_Q) / (double)P.g.V;
+    double L;
+    if (d.mse) {
+        // exact MSE sum in units of 2^shift / Q^2
+        const QScale q = *P.qs;
+        L = (double)s * ldexp(1.0, mse_shift(q.qlim)) /
+            ((double)q.Q * (double)q.Q) / (double)P.g.V;
+    } else {
+        L = ((double)s / (double)LOSS_Q) / (double)P.g.V;
+    }
     float gmax = sqrtf(m);
     bool bad = nf || lbad || !isfinite(L) || !isfinite(gmax);
     if (mode == FIN_EXPLICIT) {
@@ -522,6 +542,9 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
     if (bad) {
         st->status |= STATUS_NONFINITE;
         finished = 1;   // the trial is dropped, the state kept
+    } else if (d.demons) {
+        finished = 1;   // Demons keeps every step; lambda is unused
+        accepted = 1;
     } else {
         bool rejected = false;
         if (d.reject) {
@@ -588,20 +611,20 @@ __global__ void k_flip_slot(const PairDesc* __restrict__ pd) {
 
 bool step_resamples(const Batch& b) { return b.wtaps.R == 0; }
 
-template <bool TILE>
+template <int MODE>
 int launch_step(const Batch& b, int attempt, cudaStream_t s) {
     const int smooth = b.wtaps.R > 0;
     const dim3 grid(b.plan.st_blocks), block(ST_X, ST_Y);
     if (!smooth) {
         if (b.dtype == LM_BF16)
-            k_step_compose<__nv_bfloat16, true, TILE><<<grid, block, 0, s>>>(
+            k_step_compose<__nv_bfloat16, true, MODE><<<grid, block, 0, s>>>(
                 b.pd, b.npairs, attempt, b.step, 0, b.tile);
         else
-            k_step_compose<float, true, TILE><<<grid, block, 0, s>>>(
+            k_step_compose<float, true, MODE><<<grid, block, 0, s>>>(
                 b.pd, b.npairs, attempt, b.step, 0, b.tile);
         return 1;
     }
-    k_step_compose<float, false, TILE><<<grid, block, 0, s>>>(
+    k_step_compose<float, false, MODE><<<grid, block, 0, s>>>(
         b.pd, b.npairs, attempt, b.step, 1, b.tile);
     for (int axis = 0; axis < 3; ++axis)
         k_warp_gauss<<<b.plan.ln_blocks, TPB, 0, s>>>(b.pd, b.npairs, attempt,
@@ -610,10 +633,12 @@ int launch_step(const Batch& b, int attempt, cudaStream_t s) {
 }
 
 int batch_step(const Batch& b, int attempt, cudaStream_t s) {
-    if (b.tile <= 1) return launch_step<false>(b, attempt, s);
+    if (b.method == LM_METHOD_DEMONS)
+        return launch_step<STEP_DIRECT>(b, attempt, s);
+    if (b.tile <= 1) return launch_step<STEP_POINT>(b, attempt, s);
     k_tile_hess<<<b.th_blocks, TH_W * 32, 0, s>>>(b.pd, b.npairs, attempt,
                                                   b.tile);
-    return 1 + launch_step<true>(b, attempt, s);
+    return 1 + launch_step<STEP_TILE>(b, attempt, s);
 }
 
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,

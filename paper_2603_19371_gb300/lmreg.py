@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(HERE, "liblmreg.so")
 LM_OK, LM_EINVAL, LM_ENOMEM, LM_ECUDA = 0, -1, -2, -3
 LM_ENONFINITE, LM_ETIMEOUT, LM_EUNSUPPORTED, LM_ESTATE = -4, -5, -6, -7
 LM_F32, LM_BF16 = 0, 1
+LM_LOSS_LNCC, LM_LOSS_MSE = 0, 1
+LM_METHOD_LM, LM_METHOD_DEMONS = 0, 1
 LM_MAX_LEVELS = 4
 LM_NOALLOC_MAX_VOXELS = 1 << 19
 
@@ -38,7 +40,9 @@ class Params(ctypes.Structure):
                 ("lambda0", ctypes.c_double), ("mu_inc", ctypes.c_double),
                 ("mu_dec", ctypes.c_double), ("lambda_max", ctypes.c_double),
                 ("reject", ctypes.c_int), ("tau", ctypes.c_double),
-                ("max_retries", ctypes.c_int), ("tile", ctypes.c_int)]
+                ("max_retries", ctypes.c_int), ("tile", ctypes.c_int),
+                ("loss", ctypes.c_int), ("method", ctypes.c_int),
+                ("alpha", ctypes.c_float)]
 
 
 class Schedule(ctypes.Structure):
