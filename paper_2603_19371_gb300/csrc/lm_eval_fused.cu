@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(NT, 1)
 // contiguous ranges.  HBM traffic per voxel: Fq, Jq, dJ/du (20 B) in,
 // g_raw (12 B) out.
 // ----------------------------------------------------------------------
-constexpr int NTP = 1024;   // pointwise kernel: one CTA of 32 warps per slot
+constexpr int NTP = 1024;   // pointwise kernel threads per CTA (one CTA per slot)
 
 template <bool DEMONS>
 __global__ void __launch_bounds__(NTP)
@@ -592,30 +592,46 @@ __global__ void __launch_bounds__(NTP)
     const bool dense = gpw == g.nx;
     long long lacc = 0;
     bool bad = false;
-#pragma unroll 4
-    for (long long i = i0 + threadIdx.x; i < i1; i += NTP) {
-        const int fq = __ldg(fqv + i), jq = __ldg(jqv + i);
-        const float d0 = __ldg(djv + i), d1 = __ldg(djv + g.V + i),
-                    d2 = __ldg(djv + 2 * g.V + i);
-        float s = 0.f;
-        if (fq == FQ_BAD || jq == JQ_BAD) {
-            bad = true;
-        } else {
-            const int dq = fq - jq;
-            lacc += ((long long)dq * dq + half) >> sh;
-            const float r = (float)dq * iQ;
-            if (DEMONS) {
-                const float den = d0 * d0 + d1 * d1 + d2 * d2 + a2 * r * r;
-                s = den > 0.f ? r / den : 0.f;
-            } else {
-                s = coef * r;
-            }
+    // two voxels per thread and pass, all loads issued before any use
+    constexpr int U = 2;
+    for (long long base = i0; base < i1; base += (long long)U * NTP) {
+        int fq[U], jq[U];
+        float d[U][3];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const long long i = base + threadIdx.x + (long long)k * NTP;
+            const bool in = i < i1;
+            fq[k] = in ? __ldg(fqv + i) : 0;
+            jq[k] = in ? __ldg(jqv + i) : 0;
+            d[k][0] = in ? __ldg(djv + i) : 0.f;
+            d[k][1] = in ? __ldg(djv + g.V + i) : 0.f;
+            d[k][2] = in ? __ldg(djv + 2 * g.V + i) : 0.f;
         }
-        const long long gi =
-            dense ? i : (i / g.nx) * gpw + (i - (i / g.nx) * g.nx);
-        graw[gi] = s * d0;
-        graw[gcs + gi] = s * d1;
-        graw[2 * gcs + gi] = s * d2;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const long long i = base + threadIdx.x + (long long)k * NTP;
+            if (i >= i1) break;
+            float sc = 0.f;
+            if (fq[k] == FQ_BAD || jq[k] == JQ_BAD) {
+                bad = true;
+            } else {
+                const int dq = fq[k] - jq[k];
+                lacc += ((long long)dq * dq + half) >> sh;
+                const float r = (float)dq * iQ;
+                if (DEMONS) {
+                    const float den = d[k][0] * d[k][0] + d[k][1] * d[k][1] +
+                                      d[k][2] * d[k][2] + a2 * r * r;
+                    sc = den > 0.f ? r / den : 0.f;
+                } else {
+                    sc = coef * r;
+                }
+            }
+            const long long gi =
+                dense ? i : (i / g.nx) * gpw + (i - (i / g.nx) * g.nx);
+            graw[gi] = sc * d[k][0];
+            graw[gcs + gi] = sc * d[k][1];
+            graw[2 * gcs + gi] = sc * d[k][2];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
