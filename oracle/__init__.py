@@ -62,6 +62,7 @@ class Params(ctypes.Structure):
         ("loss", ctypes.c_int),
         ("method", ctypes.c_int),
         ("alpha", ctypes.c_double),
+        ("bins", ctypes.c_int),
     ]
 
 
@@ -70,9 +71,10 @@ class Params(ctypes.Structure):
 DEFAULTS = dict(win=5, eps_nr=1e-5, eps_dr=1e-5, sigma_grad=1.0,
                 sigma_warp=0.0, step=0.5, lambda0=0.006, mu_inc=1.5,
                 mu_dec=0.975, lambda_max=math.inf, reject=0, tau=1.0,
-                max_retries=10, tile=1, loss=0, method=0, alpha=1.0)
+                max_retries=10, tile=1, loss=0, method=0, alpha=1.0,
+                bins=32)
 
-LNCC, MSE = 0, 1          # Section 2.2 squared-loss forms
+LNCC, MSE, MI = 0, 1, 2   # Section 2.2 squared-loss forms
 LM, DEMONS = 0, 1         # Section 2.2 optimiser / Section 2.4 special case
 
 
@@ -111,6 +113,8 @@ def _load():
         lib.or_trial.argtypes = [I, I, I, P, P, D, D, D, PP, P, P]
         lib.or_tile_du.argtypes = [I, I, I, I, P, D, D, P]
         lib.or_demons_force.argtypes = [I, I, I, P, P, P, D, P]
+        lib.or_mi_range.argtypes = [I, I, I, P, P, P, P]
+        lib.or_mi.argtypes = [I, I, I, I, D, D, P, P, P, P]
         lib.or_demons_eval.argtypes = [I, I, I, P, P, P, PP, P, P, P]
         lib.or_decide.argtypes = [D, D, D, I, D, I, PP, P]
         lib.or_decide.restype = I
@@ -193,6 +197,28 @@ def smooth(X, sigma, clamp=False):
     return Y
 
 
+def mi_range(F, M):
+    """Joint intensity range [lo, hi] of F, M and 0 (the MI binning)."""
+    F, M = _f64(F), _f64(M)
+    nx, ny, nz = _dims(F)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _load().or_mi_range(nx, ny, nz, _ptr(F), _ptr(M), ctypes.byref(lo),
+                        ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def mi(F, J, bins, lo, hi):
+    """Parzen-window (cubic B-spline) mutual information in bits of the
+    pair (F, J) and dMI/dJ per voxel (Section 2.2, MI loss)."""
+    F, J = _f64(F), _f64(J)
+    nx, ny, nz = _dims(F)
+    out = ctypes.c_double()
+    d = np.empty_like(F)
+    _load().or_mi(nx, ny, nz, int(bins), float(lo), float(hi), _ptr(F),
+                  _ptr(J), ctypes.byref(out), _ptr(d))
+    return out.value, d
+
+
 def demons_force(F, M, u, alpha):
     """Update of Eq. demons (Section 2.4): r n / (|n|^2 + alpha^2 r^2) with
     r = F - M(p + u) and n the gradient of M at p + u."""
@@ -220,8 +246,9 @@ def demons_evaluate(F, M, u, P: Params):
 def evaluate(F, M, u, P: Params):
     """One loss/gradient evaluation, steps (a)-(c).
 
-    Returns dict with L (= r = 1 - LNCC, or the MSE for P.loss = MSE),
-    dLdJ, graw, g (smoothed), gmax, cc (per-voxel cc, or (F - J)^2).
+    Returns dict with L (= r = 1 - LNCC, the MSE for P.loss = MSE, or
+    log2(B) - MI for P.loss = MI), dLdJ, graw, g (smoothed), gmax, cc
+    (per-voxel cc, (F - J)^2 for MSE, 0 for MI).
     For P.method = DEMONS, L is the MSE and g the smoothed update of
     Eq. demons (no dLdJ, graw, cc).
     """

@@ -51,10 +51,12 @@ typedef struct {
     int    loss;         /* OR_LNCC or OR_MSE */
     int    method;       /* OR_LM or OR_DEMONS */
     double alpha;        /* Demons damping weight, lambda_x = alpha^2 r_x^2 */
+    int    bins;         /* MI: histogram bins B per image */
 } or_params;
 
 #define OR_LNCC   0
 #define OR_MSE    1
+#define OR_MI     2
 #define OR_LM     0
 #define OR_DEMONS 1
 
@@ -308,6 +310,111 @@ void or_smooth_field(int nx, int ny, int nz, double sigma, const double *X,
 }
 
 /* ------------------------------------------------------------------ */
+/* Mutual information with Parzen windows (Section 2.2: the squared-loss */
+/* form (log2 B - MI)^2, B bins).  Readings (the paper names only the    */
+/* Parzen windowing and B):                                              */
+/*   - both images map to [0, 1] through the joint range [lo, hi] of F,   */
+/*     M and 0 (0 is the resampler's padding value);                     */
+/*   - a value v sits at bin coordinate t = 1 + (B - 3) (v - lo)/(hi - lo)*/
+/*     and spreads over the four bins floor(t) - 1 .. floor(t) + 2 with  */
+/*     cubic B-spline weights beta3(t - i), which sum to one;            */
+/*   - p_ij = V^-1 sum_x a_i(F(x)) b_j(J(x)), with the fixed and moving   */
+/*     marginals p_i = sum_j p_ij, q_j = sum_i p_ij;                      */
+/*   - MI = sum_ij p_ij log2(p_ij / (p_i q_j)) (0 log 0 = 0), in bits, so */
+/*     0 <= MI <= log2 B.                                                */
+/* dMI/dJ(x) = V^-1 dt/dv sum_ij a_i(F(x)) b_j'(J(x)) log2(p_ij / q_j)     */
+/* (the marginal of F does not depend on J; the terms of the derivative  */
+/* of the logs cancel because sum_ij dp_ij = sum_j dq_j).                */
+/* ------------------------------------------------------------------ */
+static double bspline3(double x)
+{
+    double a = fabs(x);
+    if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+    if (a < 2.0) {
+        double b = 2.0 - a;
+        return b * b * b / 6.0;
+    }
+    return 0.0;
+}
+
+static double bspline3_deriv(double x)
+{
+    double a = fabs(x), s = x < 0 ? -1.0 : 1.0;
+    if (a < 1.0) return s * (-2.0 * a + 1.5 * a * a);
+    if (a < 2.0) {
+        double b = 2.0 - a;
+        return -s * 0.5 * b * b;
+    }
+    return 0.0;
+}
+
+void or_mi_range(int nx, int ny, int nz, const double *F, const double *M,
+                 double *lo, double *hi)
+{
+    size_t V = vox(nx, ny, nz);
+    double a = 0.0, b = 0.0;
+    for (size_t p = 0; p < V; ++p) {
+        if (F[p] < a) a = F[p];
+        if (F[p] > b) b = F[p];
+        if (M[p] < a) a = M[p];
+        if (M[p] > b) b = M[p];
+    }
+    if (!(b > a)) b = a + 1.0;   /* constant images: any width */
+    *lo = a;
+    *hi = b;
+}
+
+/* MI of (F, J) and dMI/dJ per voxel (dmi, may be NULL). */
+void or_mi(int nx, int ny, int nz, int B, double lo, double hi,
+           const double *F, const double *J, double *mi_out, double *dmi)
+{
+    size_t V = vox(nx, ny, nz);
+    double sc = (B - 3) / (hi - lo);
+    double *pj = calloc((size_t)B * B, sizeof(double));
+    for (size_t p = 0; p < V; ++p) {
+        double tf = 1.0 + sc * (F[p] - lo), tm = 1.0 + sc * (J[p] - lo);
+        for (int i = 0; i < B; ++i) {
+            double a = bspline3(tf - i);
+            if (a == 0.0) continue;
+            for (int j = 0; j < B; ++j) pj[i * B + j] += a * bspline3(tm - j);
+        }
+    }
+    for (int e = 0; e < B * B; ++e) pj[e] /= (double)V;
+    double *pf = calloc(B, sizeof(double)), *qm = calloc(B, sizeof(double));
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+            pf[i] += pj[i * B + j];
+            qm[j] += pj[i * B + j];
+        }
+    double mi = 0.0;
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+            double v = pj[i * B + j];
+            if (v > 0) mi += v * log2(v / (pf[i] * qm[j]));
+        }
+    *mi_out = mi;
+    if (dmi) {
+        for (size_t p = 0; p < V; ++p) {
+            double tf = 1.0 + sc * (F[p] - lo), tm = 1.0 + sc * (J[p] - lo);
+            double s = 0.0;
+            for (int i = 0; i < B; ++i) {
+                double a = bspline3(tf - i);
+                if (a == 0.0) continue;
+                for (int j = 0; j < B; ++j) {
+                    double v = pj[i * B + j];
+                    if (v > 0)
+                        s += a * bspline3_deriv(tm - j) * log2(v / qm[j]);
+                }
+            }
+            dmi[p] = s * sc / (double)V;
+        }
+    }
+    free(pj);
+    free(pf);
+    free(qm);
+}
+
+/* ------------------------------------------------------------------ */
 /* Steps (a)-(c): one evaluation of the loss and its smoothed gradient. */
 /*   L = r = 1 - LNCC, LNCC = V^-1 sum_p cc(p)  (Section 2.2, (1-LNCC)  */
 /*   is the residual of the squared-loss form; reading: the rules of    */
@@ -334,7 +441,20 @@ void or_eval(int nx, int ny, int nz, const double *F, const double *M,
 
     or_sample(nx, ny, nz, M, u, J, dJ);
     double L;
-    if (P->loss == OR_MSE) {
+    if (P->loss == OR_MI) {
+        /* Section 2.2, MI: r = L = log2(B) - MI (the residual of the
+         * squared-loss form), dL/dJ = -dMI/dJ; cc receives 0. */
+        double lo, hi, mi;
+        or_mi_range(nx, ny, nz, F, M, &lo, &hi);
+        or_mi(nx, ny, nz, P->bins, lo, hi, F, J, &mi, a);
+        L = log2((double)P->bins) - mi;
+        for (size_t p = 0; p < V; ++p) {
+            double dl = -a[p];
+            if (dLdJ) dLdJ[p] = dl;
+            for (int i = 0; i < 3; ++i) gr[i * V + p] = dl * dJ[i * V + p];
+            cc[p] = 0.0;
+        }
+    } else if (P->loss == OR_MSE) {
         /* Section 2.2, MSE: L = r = V^-1 sum_p (F(p) - J(p))^2 (already a
          * squared loss; reading: r is the loss value, as for LNCC), and
          * dL/dJ(p) = -2 (F(p) - J(p)) / V.  cc receives (F - J)^2. */
