@@ -227,12 +227,19 @@ def run_ours(args):
     F, M, _ = synth.voronoi_pair(shape, seed=rank)
     V = F.size
     stream = torch.cuda.Stream()
+    extra = {}
+    if args.method == "demons":
+        extra = {"step": 1.0}
+    elif args.loss == "mi":
+        # r = log2 B - MI is of order 1: damping and step for sub-voxel steps
+        extra = {"lambda0": 1.0, "step": 0.25}
     params = P.lm_default_params(
-        win=args.win, tile=args.tile,
-        loss=P.LM_LOSS_MSE if args.loss == "mse" else P.LM_LOSS_LNCC,
+        win=args.win, tile=args.tile, bins=args.bins,
+        loss={"lncc": P.LM_LOSS_LNCC, "mse": P.LM_LOSS_MSE,
+              "mi": P.LM_LOSS_MI}[args.loss],
         method=(P.LM_METHOD_DEMONS if args.method == "demons"
                 else P.LM_METHOD_LM),
-        alpha=args.alpha, **({"step": 1.0} if args.method == "demons" else {}))
+        alpha=args.alpha, **extra)
     with torch.cuda.stream(stream):
         Ft = torch.from_numpy(F).cuda()
         Mt = torch.from_numpy(M).cuda()
@@ -344,6 +351,8 @@ def run_ours(args):
                       if args.tile > 1 else "")
                    + (", MSE loss" if args.loss == "mse" and
                       args.method == "lm" else "")
+                   + (f", MI loss ({args.bins} bins, lambda0 1, step 0.25)"
+                      if args.loss == "mi" else "")
                    + (f", Demons (Eq. demons, alpha {args.alpha:g}, step 1)"
                       if args.method == "demons" else ""),
                    "voxels": V,
@@ -814,7 +823,8 @@ def main():
                     help="LNCC window (5 for the brain workload, 7 for lung CT)")
     ap.add_argument("--tile", type=int, default=1,
                     help="curvature tile side k (1: Eq. tile1, >1: Eq. tilen)")
-    ap.add_argument("--loss", default="lncc", choices=["lncc", "mse"])
+    ap.add_argument("--loss", default="lncc", choices=["lncc", "mse", "mi"])
+    ap.add_argument("--bins", type=int, default=32, help="MI histogram bins")
     ap.add_argument("--method", default="lm", choices=["lm", "demons"],
                     help="demons implies --loss mse")
     ap.add_argument("--alpha", type=float, default=1.0,

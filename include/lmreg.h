@@ -56,6 +56,7 @@ extern "C" {
 /* ---- similarity and method (lm_params.loss, lm_params.method) ---------- */
 #define LM_LOSS_LNCC     0  /* r = 1 - LNCC (Section 2.2)                    */
 #define LM_LOSS_MSE      1  /* r = V^-1 sum (F - M(p + u))^2 (Section 2.2)   */
+#define LM_LOSS_MI       2  /* r = log2 B - MI, Parzen MI (Section 2.2)      */
 #define LM_METHOD_LM     0  /* factored LM, Eq. tile1 / Eq. tilen            */
 #define LM_METHOD_DEMONS 1  /* Demons as per-voxel LM on MSE, Eq. demons     */
 
@@ -95,7 +96,12 @@ typedef struct {
                            (the last tile of an axis cut at the volume
                            edge) and solves (H_tile + lambda I) du =
                            -r ghat per voxel. */
-    int    loss;        /* LM_LOSS_LNCC or LM_LOSS_MSE.              [LNCC] */
+    int    loss;        /* LM_LOSS_LNCC, LM_LOSS_MSE or LM_LOSS_MI. [LNCC]
+                           MI: both images are binned over the joint range
+                           of F, M and 0 into B = bins bins with cubic
+                           B-spline Parzen windows; MI in bits; the
+                           residual is r = log2 B - MI (the squared-loss
+                           form (log2 B - MI)^2 of Section 2.2). */
     int    method;      /* LM_METHOD_LM or LM_METHOD_DEMONS.           [LM]
                            Demons (Section 2.4) needs LM_LOSS_MSE, tile 1
                            and reject 0.  Each iteration takes, per voxel,
@@ -109,6 +115,7 @@ typedef struct {
                            the MSE and gmax the largest smoothed update. */
     float  alpha;       /* Demons damping weight, lambda_x = alpha^2 r^2,
                            > 0.                                          [1] */
+    int    bins;        /* MI histogram bins B per image, 4..64.       [32] */
 } lm_params;
 
 /* Coarse-to-fine schedule: levels run in order, factor[l] in {1, 2, 4}

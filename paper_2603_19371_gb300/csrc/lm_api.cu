@@ -108,8 +108,13 @@ int check_params(const lm_params* p) {
         return fail(LM_EINVAL, "max_retries must be in [0, 32]");
     if (p->tile < 1 || p->tile > 16)
         return fail(LM_EINVAL, "tile must be in [1, 16], got %d", p->tile);
-    if (p->loss != LM_LOSS_LNCC && p->loss != LM_LOSS_MSE)
-        return fail(LM_EINVAL, "loss must be LM_LOSS_LNCC or LM_LOSS_MSE");
+    if (p->loss != LM_LOSS_LNCC && p->loss != LM_LOSS_MSE &&
+        p->loss != LM_LOSS_MI)
+        return fail(LM_EINVAL,
+                    "loss must be LM_LOSS_LNCC, LM_LOSS_MSE or LM_LOSS_MI");
+    if (p->bins < 4 || p->bins > MI_MAX_BINS)
+        return fail(LM_EINVAL, "bins must be in [4, %d], got %d", MI_MAX_BINS,
+                    p->bins);
     if (p->method != LM_METHOD_LM && p->method != LM_METHOD_DEMONS)
         return fail(LM_EINVAL,
                     "method must be LM_METHOD_LM or LM_METHOD_DEMONS");
@@ -397,10 +402,24 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
     c->b.d.reject = prm.reject;
     c->b.d.max_retries = prm.max_retries;
     c->b.d.mse = prm.loss == LM_LOSS_MSE;
+    c->b.d.mi = prm.loss == LM_LOSS_MI;
     c->b.d.demons = prm.method == LM_METHOD_DEMONS;
     c->b.loss = prm.loss;
     c->b.method = prm.method;
     c->b.alpha = prm.alpha;
+    c->b.bins = prm.bins;
+    if (prm.loss == LM_LOSS_MI) {
+        const size_t bb = (size_t)prm.bins * prm.bins;
+        if ((rc = c->dalloc(&c->b.part.mi_hist,
+                            npairs * bb * sizeof(unsigned long long))) ||
+            (rc = c->dalloc(&c->b.part.mi_loss, npairs * sizeof(double))) ||
+            (rc = c->dalloc(&c->b.part.mi_table, npairs * bb * sizeof(float))))
+            return rc;
+        // the histogram kernel adds to it; the table kernel clears it
+        LM_CK(cudaMemsetAsync(c->b.part.mi_hist, 0,
+                              npairs * bb * sizeof(unsigned long long),
+                              c->stream));
+    }
     c->b.wtaps = make_taps(prm.sigma_warp);
     c->b.step = prm.step;
     c->b.tile = prm.tile;
@@ -557,6 +576,7 @@ int lm_default_params(lm_params* p) {
     p->loss = LM_LOSS_LNCC;
     p->method = LM_METHOD_LM;
     p->alpha = 1.f;
+    p->bins = 32;
     return LM_OK;
 }
 

@@ -973,6 +973,8 @@ __global__ void k_qscale(const PairDesc* __restrict__ pd,
     qs->Q = Q;
     qs->invQ = (float)(1.0 / (double)Q);
     qs->qlim = (int)lim;
+    qs->lo = lo;
+    qs->hi = hi;
 }
 
 // ----------------------------------------------------------------------
@@ -1283,7 +1285,8 @@ int encode_graw_map(void* map, const float* graw, const Geom& g, int R) {
 cudaError_t fused_setup() {
     cudaError_t e = attrs_all<float>();
     cudaError_t e2 = attrs_all<__nv_bfloat16>();
-    return e != cudaSuccess ? e : e2;
+    cudaError_t e3 = mi_setup();
+    return e != cudaSuccess ? e : e2 != cudaSuccess ? e2 : e3;
 }
 
 int batch_prepare(const Batch& b, cudaStream_t s) {
@@ -1316,6 +1319,7 @@ static int launch_loss(const Batch& b, int mode, int attempt, cudaStream_t s) {
             b.pd, b.npairs, mode, attempt, b.alpha, b.part.loss);
         return 1;
     }
+    if (b.loss == LM_LOSS_MI) return launch_mi(b, mode, attempt, s);
     return launch_e1_w(b, mode, attempt, s);
 }
 

@@ -88,6 +88,7 @@ struct DecideConsts {
     double lambda0, mu_inc, mu_dec, lambda_max, tau;
     int reject, max_retries;
     int mse;      // loss partials are MSE sums (unit from the pair's QScale)
+    int mi;       // the loss is r = log2 B - MI, from the MI table kernel
     int demons;   // every trial is kept (Section 2.4), lambda unused
 };
 

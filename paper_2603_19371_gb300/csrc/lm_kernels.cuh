@@ -18,6 +18,7 @@ struct QScale {
     float Q;
     float invQ;
     int qlim;
+    float lo, hi;   // the range itself: min and max of F, M and 0
 };
 
 struct PairDesc {
@@ -152,7 +153,17 @@ __device__ __forceinline__ long long loss_fixed(float v, bool* bad) {
 struct Partials {
     long long* loss;  // one per E1 CTA, fixed point LOSS_Q (or LOSS_BAD)
     float* g2max;     // one per E2 CTA
+    // MI loss only, per pair: the B x B joint histogram (fixed point MI_HQ;
+    // the CTAs add to it, the table kernel reads and clears it), the loss
+    // r = log2 B - MI and the gradient table log2(p_ij / q_j) (B x B floats)
+    unsigned long long* mi_hist;
+    double* mi_loss;
+    float* mi_table;
 };
+
+// Fixed point of one voxel's joint-histogram weight a_i b_j (<= 4/9).
+constexpr float MI_HQ = 8388608.f;   // 2^23
+constexpr int MI_MAX_BINS = 64;
 
 // Totals of a batch plan.
 struct BatchPlan {
@@ -171,9 +182,10 @@ struct Batch {
     float step;
     int tile;             // curvature tile side k (1 = Eq. tile1)
     int th_blocks;        // blocks of the tile-curvature kernel (tile > 1)
-    int loss;             // LM_LOSS_LNCC / LM_LOSS_MSE
+    int loss;             // LM_LOSS_LNCC / LM_LOSS_MSE / LM_LOSS_MI
     int method;           // LM_METHOD_LM / LM_METHOD_DEMONS
     float alpha;          // Demons damping weight
+    int bins;             // MI histogram bins B
     Partials part;
     float2* mm_part;      // npairs * plan.mm_ctas image-range partials
 };
@@ -222,6 +234,11 @@ int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
 int batch_step(const Batch& b, int attempt, cudaStream_t s);
 // Whether batch_step also resamples M at the trial (no warp smoothing).
 bool step_resamples(const Batch& b);
+// MI loss (pass 1's loss stage for LM_LOSS_MI): joint histogram partials,
+// per-pair MI, loss and gradient table, then g_raw.  Returns the launches.
+int launch_mi(const Batch& b, int mode, int attempt, cudaStream_t s);
+// Opt the MI histogram kernel in to its dynamic shared memory.
+cudaError_t mi_setup();
 // Per-pair reduction and state update.
 enum FinMode { FIN_EXPLICIT = 0, FIN_RESET = 1, FIN_DECIDE = 2 };
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,

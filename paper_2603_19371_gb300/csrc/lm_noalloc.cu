@@ -157,6 +157,9 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
         !(prm.sigma_grad >= 0 && prm.sigma_grad <= 2) || !(prm.eps_dr > 0) ||
         !(prm.eps_nr >= 0))
         return fail(LM_EINVAL, "win, sigma_grad or eps out of range");
+    if (prm.loss == LM_LOSS_MI)
+        return fail(LM_EUNSUPPORTED,
+                    "the MI loss needs its histogram buffers: use lm_init");
     if ((prm.loss != LM_LOSS_LNCC && prm.loss != LM_LOSS_MSE) ||
         (prm.method != LM_METHOD_LM && prm.method != LM_METHOD_DEMONS) ||
         !(prm.alpha > 0) ||

@@ -490,7 +490,9 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
     m = block_max1024(m, shf);
     if (threadIdx.x != 0) return;
     double L;
-    if (d.mse) {
+    if (d.mi) {
+        L = part.mi_loss[blockIdx.x];   // r = log2 B - MI, from k_mi_table
+    } else if (d.mse) {
         // exact MSE sum in units of 2^shift / Q^2
         const QScale q = *P.qs;
         L = (double)s * ldexp(1.0, mse_shift(q.qlim)) /

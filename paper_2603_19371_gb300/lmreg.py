@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "liblmreg.so")
 LM_OK, LM_EINVAL, LM_ENOMEM, LM_ECUDA = 0, -1, -2, -3
 LM_ENONFINITE, LM_ETIMEOUT, LM_EUNSUPPORTED, LM_ESTATE = -4, -5, -6, -7
 LM_F32, LM_BF16 = 0, 1
-LM_LOSS_LNCC, LM_LOSS_MSE = 0, 1
+LM_LOSS_LNCC, LM_LOSS_MSE, LM_LOSS_MI = 0, 1, 2
 LM_METHOD_LM, LM_METHOD_DEMONS = 0, 1
 LM_MAX_LEVELS = 4
 LM_NOALLOC_MAX_VOXELS = 1 << 19
@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("reject", ctypes.c_int), ("tau", ctypes.c_double),
                 ("max_retries", ctypes.c_int), ("tile", ctypes.c_int),
                 ("loss", ctypes.c_int), ("method", ctypes.c_int),
-                ("alpha", ctypes.c_float)]
+                ("alpha", ctypes.c_float), ("bins", ctypes.c_int)]
 
 
 class Schedule(ctypes.Structure):

@@ -61,7 +61,7 @@ def test_default_params_match_the_paper(lib):
     # Section 3: tile_size 1 (the pointwise step of Eq. tile1)
     assert p.tile == 1
     assert p.loss == lmreg.LM_LOSS_LNCC and p.method == lmreg.LM_METHOD_LM
-    assert p.alpha == 1.0
+    assert p.alpha == 1.0 and p.bins == 32
     with pytest.raises(KeyError):
         lmreg.lm_default_params(tile_size=2)
 
@@ -105,8 +105,9 @@ def test_init_rejects_bad_arguments_on_host(lib):
                              ("max_retries", 99, "max_retries"),
                              ("lambda_max", 1e-9, "lambda_max"),
                              ("tile", 0, "tile"), ("tile", 17, "tile"),
-                             ("loss", 2, "loss"), ("method", 5, "method"),
-                             ("alpha", 0.0, "alpha")]:
+                             ("loss", 3, "loss"), ("method", 5, "method"),
+                             ("alpha", 0.0, "alpha"), ("bins", 3, "bins"),
+                             ("bins", 65, "bins")]:
         p = lmreg.lm_default_params()
         setattr(p, field, val)
         rc, msg = _init(lib, ok, ok, p)

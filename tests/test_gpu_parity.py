@@ -45,7 +45,7 @@ def _oracle_params(oracle, p):
                          lambda_max=p.lambda_max, reject=p.reject, tau=p.tau,
                          max_retries=p.max_retries, tile=p.tile,
                          loss=p.loss, method=p.method,
-                         alpha=float(np.float32(p.alpha)))
+                         alpha=float(np.float32(p.alpha)), bins=p.bins)
 
 
 def _images(F, M, dtype):
@@ -307,6 +307,66 @@ def test_demons_rejects_lm_only_settings(P):
         assert e.value.code == P.LM_EINVAL
 
 
+# MI loss, (log2 B - MI) with cubic B-spline Parzen windows (Section 2.2).
+@pytest.mark.parametrize("shape,bins", [((32, 32, 32), 32), ((19, 23, 37), 16),
+                                        ((5, 7, 3), 8), ((24, 20, 28), 64)])
+def test_eval_parity_mi(P, oracle_mod, shape, bins):
+    import synth
+    if min(shape) >= 8:
+        F, M, _ = synth.blob_pair(shape, seed=3)
+    else:
+        rng = np.random.default_rng(11)
+        F = rng.random(shape).astype(np.float32)
+        M = rng.random(shape).astype(np.float32)
+    u = synth.random_field(shape, seed=5, scale=1.7)
+    _eval_check(P, oracle_mod, F, M, u,
+                P.lm_default_params(loss=P.LM_LOSS_MI, bins=bins))
+
+
+@pytest.mark.parametrize("shape,dtype,extra", [
+    ((32, 32, 32), "f32", {}),
+    ((19, 23, 37), "f32", dict(bins=16)),
+    ((24, 24, 24), "bf16", dict(reject=1, tau=1.0, lambda_max=10.0,
+                                 max_retries=4)),
+])
+def test_lm_step_parity_mi(P, oracle_mod, shape, dtype, extra):
+    import synth
+    F, M, _ = synth.blob_pair(shape, seed=42)
+    # r = log2 B - MI is of order 1: lambda0 = 1 and step 0.25 keep the
+    # LM step below half a voxel
+    kw = dict(loss=P.LM_LOSS_MI, lambda0=1.0, step=0.25)
+    kw.update(extra)
+    _teacher_forced(P, oracle_mod, F, M, P.lm_default_params(**kw), 8,
+                    dtype=dtype)
+
+
+def test_mi_batch_equals_single_bitwise(P):
+    """The joint histogram is an exact integer sum: the loss does not depend
+    on how the voxels are split among CTAs."""
+    import torch
+    import synth
+    pairs = [synth.blob_pair(s, seed=i) for i, s in
+             enumerate([(24, 28, 20), (16, 16, 16), (30, 18, 22)])]
+    prm = P.lm_default_params(loss=P.LM_LOSS_MI, lambda0=1.0, step=0.25)
+    single = []
+    for F, M, _ in pairs:
+        ctx = P.lm_init(_t(F), _t(M), prm)
+        u = torch.zeros((3,) + F.shape, device="cuda")
+        P.lm_reset(ctx, u)
+        P.lm_iterate(ctx, u, 4)
+        single.append((P.lm_get_state(ctx).loss, u.cpu().numpy()))
+        P.lm_destroy(ctx)
+    b = P.lm_batch_init([_t(F) for F, _, _ in pairs],
+                        [_t(M) for _, M, _ in pairs], prm)
+    us = [torch.zeros((3,) + F.shape, device="cuda") for F, _, _ in pairs]
+    P.lm_batch_reset(b, us)
+    P.lm_batch_iterate(b, us, 4)
+    torch.cuda.synchronize()
+    for (L, u1), ub in zip(single, us):
+        np.testing.assert_array_equal(ub.cpu().numpy(), u1)
+    P.lm_batch_destroy(b)
+
+
 def test_tile_one_is_the_pointwise_step(P):
     """tile = 1 runs the Eq. tile1 kernel: bitwise the default path."""
     import torch
@@ -462,7 +522,7 @@ def _demons_g_bound(oracle_mod, F, M, u, alpha, sigma, qb=24):
     return oracle_mod.smooth(e, sigma)
 
 
-@pytest.mark.parametrize("kind", ["lncc", "tile3", "mse", "demons"])
+@pytest.mark.parametrize("kind", ["lncc", "tile3", "mse", "demons", "mi"])
 def test_full_size_eval_and_step(P, oracle_mod, kind):
     """160x192x224 brain-shaped pair: loss, sampled gradients, one step
     (LNCC with Eq. tile1 and with Eq. tilen at k = 3, MSE, Demons)."""
@@ -473,7 +533,8 @@ def test_full_size_eval_and_step(P, oracle_mod, kind):
     params = P.lm_default_params(**{
         "lncc": {}, "tile3": dict(tile=3), "mse": dict(loss=P.LM_LOSS_MSE),
         "demons": dict(loss=P.LM_LOSS_MSE, method=P.LM_METHOD_DEMONS,
-                       step=1.0)}[kind])
+                       step=1.0),
+        "mi": dict(loss=P.LM_LOSS_MI, lambda0=1.0, step=0.25)}[kind])
     Po = _oracle_params(oracle_mod, params)
     u0 = synth.random_field(shape, seed=3, scale=1.5)
     ctx = P.lm_init(_t(F), _t(M), params)
