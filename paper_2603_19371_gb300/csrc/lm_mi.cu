@@ -22,9 +22,10 @@
 //               64-bit ones, and at the end
 //               the CTA adds them to the pair's global histogram (64-bit
 //               integer atomics: the sum does not depend on order or split).
-//   k_mi_table  one CTA per pair reads (and clears) the histogram, then in
-//               FP64 the marginals, MI, the loss r and the gradient table
-//               G_ij = log2(p_ij / q_j) (0 where p_ij = 0).
+//   k_mi_table  one CTA per pair reads (and clears) the histogram, then the
+//               marginals and MI (sums in FP64, ratios and logs in FP32), the
+//               loss r and the gradient table G_ij = log2(p_ij / q_j) (0
+//               where p_ij = 0).
 //   k_mi_grad   per voxel, g_raw = dL/dJ dJ/du with the table in shared
 //               memory.
 // F and J enter through their fixed-point codes (Fq, Jq) and the pair's
@@ -197,13 +198,16 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
     float* G = mi_table + (size_t)blockIdx.x * BB;
     double m = 0.0;
+    // the ratios and their logs in FP32 (about 1e-7 relative): FP64
+    // division and log2 would run on the narrow FP64 pipe
     for (int e = tid; e < BB; e += blockDim.x) {
         const int i = e / B, j = e - i * B;
         const double v = pj[e];
         float gv = 0.f;
         if (v > 0.0) {
-            m += v * log2(v / (pf[i] * qm[j]));
-            gv = (float)log2(v / qm[j]);
+            const float vf = (float)v, qf = (float)qm[j];
+            m += v * (double)log2f(vf / ((float)pf[i] * qf));
+            gv = log2f(vf / qf);
         }
         G[e] = gv;
     }
