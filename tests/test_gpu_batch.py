@@ -195,13 +195,18 @@ def test_batch_autotune_keeps_results(P, oracle_mod):
     assert all(np.isfinite(x.loss) for x in infos)
 
 
-def test_batch_equals_single_pair_bitwise(P):
+@pytest.mark.parametrize("mode", ["lncc", "tile2", "mse", "demons"])
+def test_batch_equals_single_pair_bitwise(P, mode):
     """The loss is an exact integer sum, so neither the batch's work split
     nor the autotuner's choice changes any result: a batch and one context
-    per pair end on bitwise-equal fields after the same iterations."""
+    per pair end on bitwise-equal fields after the same iterations (LNCC
+    with Eq. tile1 and Eq. tilen, MSE, Demons)."""
     import torch
     Fs, Ms = _pairs(seed0=100)
-    params = P.lm_default_params(lambda0=0.02, step=1.0)
+    params = P.lm_default_params(lambda0=0.02, step=1.0, **{
+        "lncc": {}, "tile2": dict(tile=2), "mse": dict(loss=P.LM_LOSS_MSE),
+        "demons": dict(loss=P.LM_LOSS_MSE,
+                       method=P.LM_METHOD_DEMONS)}[mode])
     b = P.lm_batch_init(Fs, Ms, params)
     ub = [torch.zeros((3,) + sh, device="cuda") for sh in SHAPES]
     P.lm_batch_autotune(b, ub, reps=1)

@@ -40,7 +40,8 @@ def _call(P, Ft, Mt, u, g, loss, gmax, params):
     return rc
 
 
-def test_noalloc_matches_lm_eval_on_two_calls(lib):
+@pytest.mark.parametrize("loss", ["lncc", "mse"])
+def test_noalloc_matches_lm_eval_on_two_calls(lib, loss):
     import torch
     import synth
     P = lib
@@ -48,7 +49,8 @@ def test_noalloc_matches_lm_eval_on_two_calls(lib):
     F, M, _ = synth.blob_pair(shape, seed=21)
     Ft = torch.from_numpy(F).cuda()
     Mt = torch.from_numpy(M).cuda()
-    params = P.lm_default_params()
+    params = P.lm_default_params(
+        loss=P.LM_LOSS_MSE if loss == "mse" else P.LM_LOSS_LNCC)
     ctx = P.lm_init(Ft, Mt, params)
     for seed in (31, 32):
         u = torch.from_numpy(synth.random_field(shape, seed=seed, scale=1.6)).cuda()
@@ -82,3 +84,19 @@ def test_noalloc_rejects_volumes_above_the_limit(lib):
                                   None, None)
     assert rc == P.LM_EINVAL
     assert "LM_NOALLOC_MAX_VOXELS" in P.lm_last_error()
+
+
+def test_noalloc_refuses_the_mi_loss(lib):
+    """The MI loss needs per-pair histogram buffers, which only lm_init
+    allocates."""
+    import torch
+    P = lib
+    small = torch.zeros(4 * 4 * 4 * 3, device="cuda")
+    vf = P.Volume(4, 4, 4, P.LM_F32, small.data_ptr())
+    params = P.lm_default_params(loss=P.LM_LOSS_MI)
+    rc = P.load().lm_eval_noalloc(ctypes.byref(vf), ctypes.byref(vf),
+                                  ctypes.byref(params),
+                                  ctypes.c_void_p(small.data_ptr()),
+                                  ctypes.c_void_p(small.data_ptr()),
+                                  None, None, ctypes.c_void_p(0))
+    assert rc == P.LM_EUNSUPPORTED and "MI" in P.lm_last_error()
