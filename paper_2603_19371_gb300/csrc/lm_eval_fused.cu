@@ -103,6 +103,16 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Sum of v[L .. L + N) as a balanced tree (depth ceil(log2 N) instead of
+// N - 1 dependent adds); N and L are compile-time, so v stays in registers.
+template <int L, int N, typename T>
+__device__ __forceinline__ T tree_sum(const T* v) {
+    if constexpr (N == 1)
+        return v[L];
+    else
+        return tree_sum<L, N / 2, T>(v) + tree_sum<L + N / 2, N - N / 2, T>(v);
+}
+
 // ----------------------------------------------------------------------
 // E1
 // ----------------------------------------------------------------------
@@ -389,15 +399,18 @@ __global__ void __launch_bounds__(NT, 1)
                     const int ty = t - 1;
                     const int* xj = xj_r;
                     const long long* xjj = x64_r;
-                    int yj = 0;
-                    long long yjj = 0, yfj = 0;
+                    int vj[K];
+                    long long vjj[K], vfj[K];
 #pragma unroll
                     for (int o = 0; o < K; ++o) {
                         const int a = (sy + o) * SX + sx;
-                        yj += xj[a];
-                        yjj += xjj[a];
-                        yfj += xjj[XP + a];
+                        vj[o] = xj[a];
+                        vjj[o] = xjj[a];
+                        vfj[o] = xjj[XP + a];
                     }
+                    const int yj = tree_sum<0, K>(vj);
+                    const long long yjj = tree_sum<0, K>(vjj);
+                    const long long yfj = tree_sum<0, K>(vfj);
                     const int slot = (j + K - 1) % K;   // ring slot of slice t - 1
                     int* zr = ZR32 + slot * NT + tid;
                     long long* zr64 = ZR64 + slot * 2 * NT + tid;
@@ -472,9 +485,7 @@ __global__ void __launch_bounds__(NT, 1)
                                 v[o + 1] = a.y;
                             }
                         }
-                        float s0 = 0.f;
-#pragma unroll
-                        for (int o = 0; o < K; ++o) s0 += v[o];
+                        const float s0 = tree_sum<0, K>(v);
                         const float s1 = (s0 - v[0]) + v[K];
                         float* dst = ax_w + x2_row[k] * TX + XW * x2_p[k];
                         if constexpr (XW == 4) {
@@ -493,22 +504,22 @@ __global__ void __launch_bounds__(NT, 1)
                     const int oslot = (j + 2 * K - 3) % K;   // ring slot of slice t-3
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
-                        float v = 0.f;
+                        float v[K];
 #pragma unroll
                         for (int o = 0; o < K; ++o)
-                            v += ax_r[(q * SY + oy + o) * TX + ox];
-                        r2[q][oslot] = v;
+                            v[o] = ax_r[(q * SY + oy + o) * TX + ox];
+                        r2[q][oslot] = tree_sum<0, K>(v);
                     }
                     const int ro = s_begin + to - 2 * W;
                     if (to >= 4 * W && o_in) {
                         float b3[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            float v = 0.f;
+                            float v[K];
 #pragma unroll
                             for (int i2 = 0; i2 < K; ++i2)
-                                v += r2[q][(oslot + 1 + i2) % K];
-                            b3[q] = v;
+                                v[i2] = r2[q][(oslot + 1 + i2) % K];
+                            b3[q] = tree_sum<0, K>(v);
                         }
                         // F', J' of the output slice (local to - 2W)
                         const float* dl = DL + ((to - 2 * W) & (KD - 1)) * 2 * OP + tid;
