@@ -201,8 +201,9 @@ LM_API int lm_reset(lm_ctx *ctx, float *u);
 
 /* One LM iteration (Section 2.2 / 3.3) on the field u passed to the last
  * lm_reset: the trial u* = v + u o (Id + v) with v = step * du from
- * Eq. tile1, its loss, and the damping / rejection decision.  On return u
- * holds u_{t+1}.  info (host, may be NULL): filled after a stream
+ * Eq. tile1 (Eq. tilen for tile > 1; for Demons v = step * the smoothed
+ * update of Eq. demons), its loss, and the damping / rejection decision
+ * (Demons keeps every step).  On return u holds u_{t+1}.  info (host, may be NULL): filled after a stream
  * synchronisation; NULL keeps the call asynchronous.  LM_ESTATE if u is not
  * the pointer given to lm_reset. */
 LM_API int lm_step(lm_ctx *ctx, float *u, lm_step_info *info);
@@ -233,9 +234,10 @@ LM_API int lm_state_save(lm_ctx *ctx, void *buf, size_t *nbytes);
 LM_API int lm_state_load(lm_ctx *ctx, const void *buf, size_t nbytes);
 
 /* Measurement aid: time the two passes of the iteration separately.  With
- * the state of the last lm_reset / lm_step on u, launches the trial kernel
- * (pass 2: Eq. tile1 + Eq. compositive) n times, then the evaluation kernels
- * (pass 1: resampling, LNCC and its gradient, smoothing) n times, each run
+ * the state of the last lm_reset / lm_step on u, launches the trial kernels
+ * (pass 2: Eq. tile1 or Eq. tilen + Eq. compositive) n times, then the
+ * evaluation kernels (pass 1: resampling, the loss and its gradient,
+ * smoothing) n times, each run
  * bracketed by CUDA events on the context's stream, and returns the mean
  * milliseconds per launch in *ms_step and *ms_eval (host).  The optimiser
  * state is not changed.  Synchronises the stream. */
@@ -320,15 +322,19 @@ LM_API int lm_register_batch(int npairs, const lm_volume *fixed,
  * device synchronisation of cudaMalloc / cudaFree is not allowed, processes
  * that gave their free memory to another component).
  *
- * Same result as lm_eval on a fresh context: the loss r = 1 - LNCC and its
- * smoothed gradient at u, without a context and without any allocation.
+ * Same result as lm_eval on a fresh context: the loss (r = 1 - LNCC, or
+ * the MSE) and its smoothed gradient at u (the smoothed update of
+ * Eq. demons for LM_METHOD_DEMONS), without a context and without any
+ * allocation.  The MI loss needs per-pair histogram buffers and returns
+ * LM_EUNSUPPORTED here.
  * Its scratch is one static device array inside the library, sized for at
  * most LM_NOALLOC_MAX_VOXELS voxels (2^19, e.g. 80^3; about 21 MB, held
  * by every GPU that loads the library until the process exits), counted
  * with rows padded to a multiple of 4 voxels; larger volumes return
  * LM_EINVAL.
  *   fixed, moving: images as for lm_init; p: parameters (NULL = defaults;
- *   only win, eps_nr, eps_dr and sigma_grad matter); u: device field
+ *   only win, eps_nr, eps_dr, sigma_grad, loss, method and alpha matter);
+ *   u: device field
  *   [3][D][H][W]; g_out: device [3][D][H][W] (written); loss_out: device
  *   double (written; NaN if the loss or gradient is not finite; may be
  *   NULL); gmax_out: device float (may be NULL); cuda_stream: the stream.
