@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -77,20 +78,6 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-// D += A B for one 16x8x16 tile: A row-major (a: 4 registers of two
-// bfloat16), B column-major (b: 2 registers), D FP32.
-__device__ __forceinline__ void mma16816(float* d, const unsigned* a,
-                                         const unsigned* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ unsigned ld_u32(const bf16* p) {
-    return *reinterpret_cast<const unsigned*>(p);
-}
 
 // tap t = 9 kz + 3 ky + kx, offsets (kz - 1, ky - 1, kx - 1)
 __device__ __forceinline__ void tap_offset(int t, int& dz, int& dy, int& dx) {
@@ -345,124 +332,202 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---------------------------------------------------------------------
-// Weight gradient: dw[co][n] += sum_v dy[v][co] X(v, n), with n = 27-tap
-// index t times cin plus ci and X(v, n) = x[v + off(t)][ci] (zero outside).
-// CTA tile 64 output channels x 64 columns; k = 32 voxels per step over a
-// chunk of voxels; both operands are staged transposed in shared memory.
+// Weight gradient on the tensor cores: for each tile of 128 rows
+// m = 27-tap index t times cin plus ci,
+//   dw[co][m] += sum_v X(v, m) dy[v][co],  X(v, m) = x[v + off(t)][ci]
+// (zero outside the volume), i.e. D = A B^T with A = X^T (M = 128 rows, K
+// = voxels) and B = dy^T (N = cout rows, K = voxels), FP32 accumulator in
+// tensor memory, 16 voxels per tcgen05.mma.  Both operands arrive with
+// channels contiguous, so they are staged MN-major: a core matrix is 8
+// voxels (rows) of 8 consecutive channels (16 bytes), which is exactly one
+// 16-byte cp.async from x or dy per voxel.  Core matrices adjacent along
+// M / N are 128 bytes apart, along K 16 x 128 (A) or BN / 8 x 128 (B)
+// bytes.  The ring, the commits and the bounded waits are the forward
+// kernel's; the epilogue adds the accumulator rows to dw with FP32 atomics
+// (coalesced along m), NaN after a timeout.
 // ---------------------------------------------------------------------
-constexpr int WTM = 64, WTN = 64, WKV = 32, WKP = 40;
+template <int BN>
+struct WgCfg {
+    static constexpr int A_BYTES = 128 * 16 * 2;   // 128 rows x 16 voxels
+    static constexpr int B_BYTES = BN * 16 * 2;    // BN rows x 16 voxels
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int bytes = 1024 + TC_STAGES * STAGE;
+    // kind::f16, D f32, A and B bf16, both MN-major (bits 15, 16)
+    static constexpr unsigned IDESC = TcCfg<BN>::IDESC | (1u << 15) | (1u << 16);
+};
 
-template <bool CIN2>
-__global__ void __launch_bounds__(256)
-    k_conv_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy,
-                 float* __restrict__ dw, int D, int H, int W, int cin, int cout,
-                 int vchunk) {
-    __shared__ __align__(16) bf16 As[WTM][WKP];   // dy^T [co][v]
-    __shared__ __align__(16) bf16 Bs[WTN][WKP];   // X^T  [n][v]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 1, wn = warp >> 1;      // 2 x 4 warps, 32 x 16 each
-    const int ntot = 27 * cin;
-    const int n0 = blockIdx.x * WTN, m0 = blockIdx.y * WTM;
+template <int BN, bool CIN2>
+__global__ void __launch_bounds__(128)
+    k_conv_wgrad_tc(const bf16* __restrict__ x, const bf16* __restrict__ dy,
+                    float* __restrict__ dw, int D, int H, int W, int cin,
+                    int cout, int vchunk) {
+    using C = WgCfg<BN>;
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+    __shared__ __align__(8) unsigned long long mbar[TC_STAGES];
+    __shared__ unsigned tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long V = (long long)D * H * W;
+    const int ntot = 27 * cin;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
     const long long vs = (long long)blockIdx.z * vchunk;
     const long long ve = vs + vchunk < V ? vs + vchunk : V;
-    const int lv = tid >> 3, part = tid & 7;
-    const int g = lane >> 2, t4 = lane & 3;
-    float acc[2][2][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-
-    for (long long vb = vs; vb < ve; vb += WKV) {
-        const long long v = vb + lv;
-        const bool vin = v < ve;
-        {
-            const int co = m0 + part * 8;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (vin && co < cout)
-                val = *reinterpret_cast<const uint4*>(dy + v * cout + co);
-            const bf16* e = reinterpret_cast<const bf16*>(&val);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) As[part * 8 + j][lv] = e[j];
-        }
-        {
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+    const int nk = (int)((ve - vs + 15) / 16);
+    auto stage_a = [&](int st) { return sm + st * C::STAGE; };
+    auto stage_b = [&](int st) { return sm + st * C::STAGE + C::A_BYTES; };
+    // voxel k of the step, channel group g (8 channels) -> smem offset
+    auto a_off = [&](int k, int g) { return (k >> 3) * (16 * 128) + g * 128 + (k & 7) * 16; };
+    auto b_off = [&](int k, int g) {
+        return (k >> 3) * ((BN / 8) * 128) + g * 128 + (k & 7) * 16;
+    };
+    auto load = [&](int s, int st) {
+        unsigned char* As = stage_a(st);
+        unsigned char* Bs = stage_b(st);
+        const long long vb = vs + 16LL * s;
+        // A: 16 voxels x 16 channel groups, two per thread
+        for (int u = tid; u < 16 * 16; u += 128) {
+            const int k = u >> 4, g = u & 15;
+            const long long v = vb + k;
+            int xx = 0, yy = 0, zz = 0;
+            const bool vin = v < ve;
             if (vin) {
-                const int xx = (int)(v % W);
+                xx = (int)(v % W);
                 const long long r = v / W;
-                const int yy = (int)(r % H), zz = (int)(r / H);
-                if (!CIN2) {
-                    const int n = n0 + part * 8;
-                    if (n < ntot) {
-                        const int tap = n / cin, ci = n - tap * cin;
-                        int dz, dyy, dx;
-                        tap_offset(tap, dz, dyy, dx);
-                        const int z2 = zz + dz, y2 = yy + dyy, x2 = xx + dx;
-                        if (z2 >= 0 && z2 < D && y2 >= 0 && y2 < H && x2 >= 0 &&
-                            x2 < W)
-                            val = *reinterpret_cast<const uint4*>(
-                                x + (((long long)z2 * H + y2) * W + x2) * cin + ci);
-                    }
-                } else {
-                    unsigned* vv = reinterpret_cast<unsigned*>(&val);
+                yy = (int)(r % H);
+                zz = (int)(r / H);
+            }
+            if (!CIN2) {
+                const int m = m0 + 8 * g;
+                const int tap = m / cin, ci = m - tap * cin;
+                int dz, dyy, dx;
+                tap_offset(tap < 27 ? tap : 0, dz, dyy, dx);
+                const int z2 = zz + dz, y2 = yy + dyy, x2 = xx + dx;
+                const bool in = vin && m < ntot && z2 >= 0 && z2 < D && y2 >= 0 &&
+                                y2 < H && x2 >= 0 && x2 < W;
+                cp_async16(As + a_off(k, g),
+                           in ? x + (((long long)z2 * H + y2) * W + x2) * cin + ci : x,
+                           in);
+            } else {
+                // group g: taps 4 g .. 4 g + 3, both channels of each
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int tap = (n0 + part * 8) / 2 + j;
-                        if (tap >= 27) continue;
-                        int dz, dyy, dx;
-                        tap_offset(tap, dz, dyy, dx);
-                        const int z2 = zz + dz, y2 = yy + dyy, x2 = xx + dx;
-                        if (z2 >= 0 && z2 < D && y2 >= 0 && y2 < H && x2 >= 0 &&
-                            x2 < W)
-                            vv[j] = *reinterpret_cast<const unsigned*>(
-                                x + (((long long)z2 * H + y2) * W + x2) * 2);
-                    }
+                for (int q = 0; q < 4; ++q) {
+                    const int tap = (m0 >> 1) + 4 * g + q;
+                    int dz, dyy, dx;
+                    tap_offset(tap < 27 ? tap : 0, dz, dyy, dx);
+                    const int z2 = zz + dz, y2 = yy + dyy, x2 = xx + dx;
+                    const bool in = vin && tap < 27 && z2 >= 0 && z2 < D && y2 >= 0 &&
+                                    y2 < H && x2 >= 0 && x2 < W;
+                    cp_async4(As + a_off(k, g) + 4 * q,
+                              in ? x + (((long long)z2 * H + y2) * W + x2) * 2 : x, in);
                 }
             }
-            const bf16* e = reinterpret_cast<const bf16*>(&val);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) Bs[part * 8 + j][lv] = e[j];
         }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < WKV; kk += 16) {
-            unsigned af[2][4], bfr[2][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r0 = wm * 32 + mi * 16 + g;
-                af[mi][0] = ld_u32(&As[r0][kk + 2 * t4]);
-                af[mi][1] = ld_u32(&As[r0 + 8][kk + 2 * t4]);
-                af[mi][2] = ld_u32(&As[r0][kk + 2 * t4 + 8]);
-                af[mi][3] = ld_u32(&As[r0 + 8][kk + 2 * t4 + 8]);
-            }
-#pragma unroll
-            for (int ni = 0; ni < 2; ++ni) {
-                const int c = wn * 16 + ni * 8 + g;
-                bfr[ni][0] = ld_u32(&Bs[c][kk + 2 * t4]);
-                bfr[ni][1] = ld_u32(&Bs[c][kk + 2 * t4 + 8]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 2; ++ni)
-                    mma16816(acc[mi][ni], af[mi], bfr[ni]);
+        // B: 16 voxels x BN / 8 channel groups
+        for (int u = tid; u < 16 * (BN / 8); u += 128) {
+            const int k = u / (BN / 8), g = u - k * (BN / 8);
+            const long long v = vb + k;
+            const bool in = v < ve;
+            cp_async16(Bs + b_off(k, g), in ? dy + v * cout + n0 + 8 * g : dy, in);
         }
-        __syncthreads();
+    };
+
+    if (warp == 0) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                su32(&tmem_slot)),
+            "r"(TcCfg<BN>::COLS)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::
+                         : "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < TC_STAGES; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&mbar[b]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+    for (int s = 0; s < TC_AHEAD; ++s) {
+        if (s < nk) load(s, s);
+        cp_commit();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+    // MN-major, no swizzle: as for K-major operands, the leading byte
+    // offset is the stride between core matrices along K and the stride
+    // byte offset the stride along M / N
+    const unsigned a_lbo = 16u * 128u, a_sbo = 128u;
+    const unsigned b_lbo = (unsigned)(BN / 8) * 128u, b_sbo = 128u;
+    bool ok = true;
+    for (int s = 0; s < nk; ++s) {
+        const int st = s % TC_STAGES;
+        cp_wait<TC_AHEAD - 1>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long ad = umma_desc(su32(stage_a(st)), a_lbo, a_sbo);
+            const unsigned long long bd = umma_desc(su32(stage_b(st)), b_lbo, b_sbo);
+            const unsigned acc = s > 0;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                    tmem),
+                "l"(ad), "l"(bd), "r"(C::IDESC), "r"(acc)
+                : "memory");
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster."
+                "b64 [%0];\n" ::"r"(su32(&mbar[st]))
+                : "memory");
+        }
+        const int nx = s + TC_AHEAD;
+        if (nx < nk) {
+            const int pst = nx % TC_STAGES;
+            const int prev = nx - TC_STAGES;
+            if (prev >= 0)
+                ok &= tc_wait(&mbar[pst], (unsigned)((prev / TC_STAGES) & 1));
+            load(nx, pst);
+        }
+        cp_commit();
+    }
+    cp_wait<0>();
+    if (nk > 0) {
+        const int last = nk - 1;
+        ok &= tc_wait(&mbar[last % TC_STAGES], (unsigned)((last / TC_STAGES) & 1));
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int m = m0 + warp * 32 + lane;   // this thread's TMEM lane
 #pragma unroll
-        for (int ni = 0; ni < 2; ++ni)
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            unsigned r[16];
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+                  "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+                  "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (m < ntot) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = m0 + wm * 32 + mi * 16 + g + (q >> 1) * 8;
-                const int col = n0 + wn * 16 + ni * 8 + 2 * t4 + (q & 1);
-                if (row < cout && col < ntot)
-                    atomicAdd(dw + (long long)row * ntot + col, acc[mi][ni][q]);
+                for (int jj = 0; jj < 16; ++jj)
+                    atomicAdd(dw + (long long)(n0 + c0 + jj) * ntot + m,
+                              ok ? __uint_as_float(r[jj]) : __int_as_float(0x7fc00000));
             }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(
+                         tmem),
+                     "r"(TcCfg<BN>::COLS)
+                     : "memory");
 }
 
 // db[co] += sum_v dy[v][co]
@@ -784,6 +849,23 @@ cudaError_t attrs_tc() {
     if ((r = attr_tc<192, C2, F>()) != cudaSuccess) e = r;
     return e;
 }
+template <int BN, bool C2>
+cudaError_t attr_wg() {
+    return cudaFuncSetAttribute(k_conv_wgrad_tc<BN, C2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                WgCfg<BN>::bytes);
+}
+template <bool C2>
+cudaError_t attrs_wg() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = attr_wg<16, C2>()) != cudaSuccess) e = r;
+    if ((r = attr_wg<32, C2>()) != cudaSuccess) e = r;
+    if ((r = attr_wg<64, C2>()) != cudaSuccess) e = r;
+    if ((r = attr_wg<96, C2>()) != cudaSuccess) e = r;
+    if ((r = attr_wg<128, C2>()) != cudaSuccess) e = r;
+    if ((r = attr_wg<192, C2>()) != cudaSuccess) e = r;
+    return e;
+}
 // Shared-memory opt-in of the tensor-core convolutions (once per process).
 cudaError_t conv_setup() {
     static cudaError_t once = [] {
@@ -792,22 +874,44 @@ cudaError_t conv_setup() {
         if ((r = attrs_tc<false, true>()) != cudaSuccess) e = r;
         if ((r = attrs_tc<true, false>()) != cudaSuccess) e = r;
         if ((r = attrs_tc<true, true>()) != cudaSuccess) e = r;
+        if ((r = attrs_wg<false>()) != cudaSuccess) e = r;
+        if ((r = attrs_wg<true>()) != cudaSuccess) e = r;
         return e;
     }();
     return once;
 }
 
-int conv_wgrad(const bf16* x, const bf16* dy, float* dw, int D, int H, int W,
+template <int BN, bool C2>
+void launch_wg(const bf16* x, const bf16* dy, float* dw, int D, int H, int W,
                int cin, int cout, cudaStream_t s) {
     const long long V = (long long)D * H * W;
-    const int ntot = 27 * cin;
-    const int vchunk = 8192;
-    dim3 grid((ntot + WTN - 1) / WTN, (cout + WTM - 1) / WTM,
-              (unsigned)((V + vchunk - 1) / vchunk));
-    if (cin == 2)
-        k_conv_wgrad<true><<<grid, 256, 0, s>>>(x, dy, dw, D, H, W, cin, cout, vchunk);
-    else
-        k_conv_wgrad<false><<<grid, 256, 0, s>>>(x, dy, dw, D, H, W, cin, cout, vchunk);
+    const int mt = (27 * cin + 127) / 128, nt = cout / BN;
+    // enough CTAs for about eight per SM, chunks of 256 to 8192 voxels
+    long long vc = V * mt * nt / (8 * 152);
+    vc = std::max<long long>(256, std::min<long long>(8192, (vc + 15) / 16 * 16));
+    const unsigned vz = (unsigned)((V + vc - 1) / vc);
+    k_conv_wgrad_tc<BN, C2><<<dim3(mt, nt, vz), 128, WgCfg<BN>::bytes, s>>>(
+        x, dy, dw, D, H, W, cin, cout, (int)vc);
+}
+
+template <bool C2>
+void pick_wg(const bf16* x, const bf16* dy, float* dw, int D, int H, int W,
+             int cin, int cout, cudaStream_t s) {
+    if (cout == 16) launch_wg<16, C2>(x, dy, dw, D, H, W, cin, cout, s);
+    else if (cout == 32) launch_wg<32, C2>(x, dy, dw, D, H, W, cin, cout, s);
+    else if (cout == 64) launch_wg<64, C2>(x, dy, dw, D, H, W, cin, cout, s);
+    else if (cout == 96) launch_wg<96, C2>(x, dy, dw, D, H, W, cin, cout, s);
+    else if (cout == 192) launch_wg<192, C2>(x, dy, dw, D, H, W, cin, cout, s);
+    else if (cout % 128 == 0) launch_wg<128, C2>(x, dy, dw, D, H, W, cin, cout, s);
+    else if (cout % 64 == 0) launch_wg<64, C2>(x, dy, dw, D, H, W, cin, cout, s);
+    else if (cout % 32 == 0) launch_wg<32, C2>(x, dy, dw, D, H, W, cin, cout, s);
+    else launch_wg<16, C2>(x, dy, dw, D, H, W, cin, cout, s);
+}
+
+int conv_wgrad(const bf16* x, const bf16* dy, float* dw, int D, int H, int W,
+               int cin, int cout, cudaStream_t s) {
+    if (cin == 2) pick_wg<true>(x, dy, dw, D, H, W, cin, cout, s);
+    else pick_wg<false>(x, dy, dw, D, H, W, cin, cout, s);
     return 1;
 }
 
