@@ -838,10 +838,25 @@ __global__ void __launch_bounds__(NT2, 2)
 #pragma unroll
                 for (int k = 0; k < NXS; ++k) {
                     if (x_in[k] < 0) continue;
-                    const float* rr = gr + x_in[k];
+                    // the unit's 4 + 2R inputs start DOFF floats into a
+                    // 16-byte-aligned run of NV4 float4 (inside the row:
+                    // 4 (NQ - 1) + 4 NV4 <= BX for every R)
+                    constexpr int DOFF = RA - R;
+                    constexpr int NV4 = (DOFF + 4 + 2 * R + 3) / 4;
+                    static_assert(4 * (NQ - 1) + 4 * NV4 <= BX, "x-pass read in row");
+                    const float4* rr4 = (const float4*)(gr + x_in[k] - DOFF);
+                    float w4[4 * NV4];
+#pragma unroll
+                    for (int q4 = 0; q4 < NV4; ++q4) {
+                        const float4 t4 = rr4[q4];
+                        w4[4 * q4] = t4.x;
+                        w4[4 * q4 + 1] = t4.y;
+                        w4[4 * q4 + 2] = t4.z;
+                        w4[4 * q4 + 3] = t4.w;
+                    }
                     float v[4 + 2 * R];
 #pragma unroll
-                    for (int o = 0; o < 4 + 2 * R; ++o) v[o] = rr[o];
+                    for (int o = 0; o < 4 + 2 * R; ++o) v[o] = w4[DOFF + o];
                     float out[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
