@@ -52,6 +52,21 @@ extern "C" {
 #define LM_ETIMEOUT     -5  /* a bounded device wait ran out */
 #define LM_EUNSUPPORTED -6  /* valid request this build does not handle */
 #define LM_ESTATE       -7  /* call out of order (e.g. lm_step before reset) */
+#define LM_EBOUNDS      -8  /* debug-bounds build: a kernel wrote outside a
+                               buffer (lm_debug_check) */
+/* LM_ETIMEOUT: the gradient-smoothing kernel waits on its TMA tiles with a
+ * bound (2^20 polls or 0.5 s); a wait that runs out voids that evaluation
+ * and the call returns LM_ETIMEOUT with the context still usable (the state
+ * keeps its last accepted field).
+ *
+ * Host-side fault injection (read when a context is created; tests only):
+ *   LM_FAULT_ALLOC=n    the context's n-th device allocation fails as if
+ *                       cudaMalloc had (the create call returns LM_ENOMEM
+ *                       and frees what it had allocated);
+ *   LM_FAULT_TIMEOUT=1  every evaluation's smoothing kernel first waits on a
+ *                       barrier that no copy completes (nothing is in flight),
+ *                       so that the bounded wait runs out: evaluations return
+ *                       LM_ETIMEOUT.  Neither faults nor hangs the device. */
 
 /* ---- similarity and method (lm_params.loss, lm_params.method) ---------- */
 #define LM_LOSS_LNCC     0  /* r = 1 - LNCC (Section 2.2)                    */
@@ -350,6 +365,18 @@ LM_API int lm_eval_noalloc(const lm_volume *fixed, const lm_volume *moving,
                            const lm_params *p, const float *u, float *g_out,
                            double *loss_out, float *gmax_out,
                            void *cuda_stream);
+
+/* Debug-bounds build (compiled with -DLM_DEBUG_BOUNDS, the library
+ * liblmreg_dbg.so): every device buffer a context allocates sits between
+ * two 64 KiB guard bands of 0xFF bytes (NaN as a float, -1 as an integer),
+ * so that a kernel reading past a buffer reads NaN or -1 and one writing
+ * past it changes a band.  lm_debug_check synchronises and returns LM_OK
+ * if every band of the context (and of its pyramid levels) is intact, else
+ * LM_EBOUNDS with the buffer and byte in lm_last_error().  The release
+ * build returns LM_EUNSUPPORTED.  The caller's own buffers (F, M, u,
+ * g_out) are the caller's to guard. */
+LM_API int lm_debug_check(lm_ctx *ctx);
+LM_API int lm_batch_debug_check(lm_batch *b);
 
 /* Static message for an LM_E* code. */
 LM_API const char *lm_strerror(int code);

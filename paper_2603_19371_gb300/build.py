@@ -3,6 +3,9 @@
 Each translation unit is compiled by nvcc for sm_103a in parallel, then
 linked into ``paper_2603_19371_gb300/liblmreg.so`` with the CUDA runtime
 linked statically (the library then loads beside any PyTorch build).
+``build(debug_bounds=True)`` makes the guard-band variant
+``liblmreg_dbg.so`` (-DLM_DEBUG_BOUNDS, objects in ``_build_dbg/``), which
+the bounds tests load in a process of their own.
 """
 from __future__ import annotations
 
@@ -18,6 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblmreg.so")
+BUILD_DBG = os.path.join(HERE, "_build_dbg")
+LIB_DBG = os.path.join(HERE, "liblmreg_dbg.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -51,16 +56,20 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(),
+          debug_bounds: bool = False) -> str:
     """Compile and link; returns the library path."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir, lib = (BUILD_DBG, LIB_DBG) if debug_bounds else (BUILD, LIB)
+    if debug_bounds:
+        extra = [*extra, "-DLM_DEBUG_BOUNDS"]
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     hdrs = _headers()
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             cmd = [nvcc, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-I", CSRC,
@@ -80,12 +89,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
         run(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -153,6 +154,25 @@ int check_pair(const lm_volume* f, const lm_volume* m) {
     return LM_OK;
 }
 
+// Host-side fault injection: an environment variable read as an integer
+// (0 when unset or not a number).
+int env_int(const char* name) {
+    const char* v = getenv(name);
+    return v ? atoi(v) : 0;
+}
+
+// Error code of a pair's device status word: a wait that ran out comes
+// before a non-finite result (its partials are void).
+int status_error(int status, int pair) {
+    if (status & STATUS_TIMEOUT)
+        return fail(LM_ETIMEOUT, "a bounded device wait ran out (pair %d)",
+                    pair);
+    if (status & STATUS_NONFINITE)
+        return fail(LM_ENONFINITE, "loss or gradient is not finite (pair %d)",
+                    pair);
+    return LM_OK;
+}
+
 // ---------------------------------------------------------------------
 // Core: a batch of pairs with its device scratch and state.
 // ---------------------------------------------------------------------
@@ -178,6 +198,8 @@ struct Core {
     long long launches = 0;
     int num_sms = 0;
     int e1_cap = 0, e2_cap = 0;    // partial slots allocated (any plan fits)
+    int nalloc = 0;                // device allocations so far
+    int fault_alloc = env_int("LM_FAULT_ALLOC");   // 0: no injected failure
 
     ~Core() {
         if (stream) cudaStreamSynchronize(stream);
@@ -190,18 +212,67 @@ struct Core {
         if (h_log) cudaFreeHost(h_log);
     }
 
+#ifdef LM_DEBUG_BOUNDS
+    // Guard bands of GUARD bytes before and after every device buffer,
+    // filled with 0xFF (NaN as a float, -1 as an integer): a kernel that
+    // writes outside its buffer changes a band (check_guards), one that
+    // reads outside it reads NaN or -1 and fails parity.
+    static constexpr size_t GUARD = 1 << 16;
+    std::vector<std::pair<unsigned char*, size_t>> guarded;
+#else
+    static constexpr size_t GUARD = 0;
+#endif
+
     template <typename T>
     int dalloc(T** out, size_t bytes) {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, bytes);
+        // LM_FAULT_ALLOC=n: the context's n-th device allocation fails
+        if (++nalloc == fault_alloc)
+            return fail(LM_ENOMEM, "cudaMalloc(%zu) failed: injected by "
+                                   "LM_FAULT_ALLOC=%d", bytes, fault_alloc);
+        cudaError_t e = cudaMalloc(&q, bytes + 2 * GUARD);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(LM_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes,
                         cudaGetErrorString(e));
         }
         allocs.push_back(q);
-        *out = (T*)q;
+#ifdef LM_DEBUG_BOUNDS
+        unsigned char* base = (unsigned char*)q;
+        LM_CK(cudaMemset(base, 0xFF, GUARD));
+        LM_CK(cudaMemset(base + GUARD + bytes, 0xFF, GUARD));
+        guarded.emplace_back(base, bytes);
+#endif
+        *out = (T*)((unsigned char*)q + GUARD);
         return LM_OK;
+    }
+
+    // Debug-bounds build: LM_OK if every guard band is intact, LM_EBOUNDS
+    // naming the first changed byte otherwise.
+    int check_guards() {
+#ifdef LM_DEBUG_BOUNDS
+        LM_CK(cudaStreamSynchronize(stream));
+        LM_CK(cudaDeviceSynchronize());
+        std::vector<unsigned char> h(GUARD);
+        for (size_t a = 0; a < guarded.size(); ++a) {
+            for (int side = 0; side < 2; ++side) {
+                const unsigned char* band =
+                    guarded[a].first + (side ? GUARD + guarded[a].second : 0);
+                LM_CK(cudaMemcpy(h.data(), band, GUARD, cudaMemcpyDeviceToHost));
+                for (size_t i = 0; i < GUARD; ++i)
+                    if (h[i] != 0xFF)
+                        return fail(LM_EBOUNDS,
+                                    "a kernel wrote byte %lld of buffer %zu "
+                                    "(%zu bytes long)",
+                                    side ? (long long)(guarded[a].second + i)
+                                         : (long long)i - (long long)GUARD,
+                                    a, guarded[a].second);
+            }
+        }
+        return LM_OK;
+#else
+        return fail(LM_EUNSUPPORTED, "built without LM_DEBUG_BOUNDS");
+#endif
     }
 
     // Host table -> device (pageable source: safe to modify on return).
@@ -216,9 +287,7 @@ struct Core {
                               cudaMemcpyDeviceToHost, stream));
         LM_CK(cudaStreamSynchronize(stream));
         for (int i = 0; i < npairs; ++i)
-            if (h_st[i].status & STATUS_NONFINITE)
-                return fail(LM_ENONFINITE,
-                            "loss or gradient is not finite (pair %d)", i);
+            if (int rc = status_error(h_st[i].status, i)) return rc;
         return LM_OK;
     }
 
@@ -363,6 +432,7 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
         d.gp_w = graw_pitch(d.g.nx);
         d.log = lg + (size_t)i * LOG_CAP;
         d.u0 = nullptr;
+        d.fault_wait = env_int("LM_FAULT_TIMEOUT") != 0;
     }
     // tensor maps of the g_raw buffers (E2 tiles them with TMA)
     {
@@ -475,9 +545,7 @@ int core_eval(Core* c, const float* const* u, float* const* g_out,
     for (int i = 0; i < c->npairs; ++i) {
         if (loss) loss[i] = c->h_eout[i].L;
         if (gmax) gmax[i] = c->h_eout[i].gmax;
-        if (c->h_eout[i].status & STATUS_NONFINITE)
-            return fail(LM_ENONFINITE,
-                        "loss or gradient is not finite (pair %d)", i);
+        if ((rc = status_error(c->h_eout[i].status, i)) != LM_OK) return rc;
     }
     return LM_OK;
 }
@@ -588,6 +656,7 @@ const char* lm_strerror(int code) {
         case LM_ECUDA: return "CUDA error";
         case LM_ENONFINITE: return "non-finite loss or gradient";
         case LM_ETIMEOUT: return "device wait timed out";
+        case LM_EBOUNDS: return "a kernel wrote outside its buffer";
         case LM_EUNSUPPORTED: return "unsupported";
         case LM_ESTATE: return "call out of order";
         default: return "unknown error";
@@ -595,6 +664,14 @@ const char* lm_strerror(int code) {
 }
 
 const char* lm_last_error(void) { return g_err; }
+
+int lm_debug_check(lm_ctx* c) {
+    if (!c) return fail(LM_EINVAL, "ctx is NULL");
+    int rc = c->core->check_guards();
+    for (auto& l : c->levels)
+        if (rc == LM_OK && l.ctx) rc = lm_debug_check(l.ctx);
+    return rc;
+}
 
 void lm_destroy(lm_ctx* c) {
     if (!c) return;
@@ -954,6 +1031,14 @@ extern "C" int lm_batch_init(lm_batch** out, int npairs,
     }
     *out = b;
     return LM_OK;
+}
+
+extern "C" int lm_batch_debug_check(lm_batch* b) {
+    if (!b) return fail(LM_EINVAL, "batch is NULL");
+    int rc = b->core->check_guards();
+    for (auto& l : b->levels)
+        if (rc == LM_OK && l.b) rc = lm_batch_debug_check(l.b);
+    return rc;
 }
 
 extern "C" void lm_batch_destroy(lm_batch* b) {

@@ -40,7 +40,9 @@ struct DevState {
     int stopped;       // reached the pair's target loss: iterations are no-ops
 };
 
-enum { STATUS_NONFINITE = 1 };
+// STATUS_TIMEOUT: a bounded device wait ran out (the evaluation's result is
+// void); the host reports it as LM_ETIMEOUT ahead of STATUS_NONFINITE.
+enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 
 // One record per finished iteration, written by the decision kernel.
 struct LogEntry {

@@ -61,6 +61,9 @@ struct PairDesc {
     // block of the tile kernel (one block per tile row and slice)
     float* tileH;
     int th_nx, th_ny, th_nz, th_blk0;
+    // injected fault (LM_FAULT_TIMEOUT, host-side): E2 first waits on a
+    // barrier that no copy completes, so that its bounded wait runs out
+    int fault_wait;
 };
 
 // Pointers of an evaluation, routed by mode.

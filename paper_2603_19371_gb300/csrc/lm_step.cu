@@ -480,13 +480,15 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
     lbad = __syncthreads_or(lbad);
     s = block_sum1024_ll(s, shl);
     float m = 0.f;
-    int nf = 0;
+    int nf = 0, to = 0;
     for (int i = threadIdx.x; i < P.e2_ncta; i += blockDim.x) {
         float v = part.g2max[P.e2_cta0 + i];
-        if (!(v <= 3.0e38f)) nf = 1;   // NaN or overflow
+        if (v < 0.f) to = 1;                 // E2's bounded wait ran out
+        else if (!(v <= 3.0e38f)) nf = 1;    // NaN or overflow
         else m = fmaxf(m, v);
     }
     nf = __syncthreads_or(nf);
+    to = __syncthreads_or(to);
     m = block_max1024(m, shf);
     if (threadIdx.x != 0) return;
     double L;
@@ -501,12 +503,14 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
         L = ((double)s / (double)LOSS_Q) / (double)P.g.V;
     }
     float gmax = sqrtf(m);
-    bool bad = nf || lbad || !isfinite(L) || !isfinite(gmax);
+    const bool nonfinite = nf || lbad || !isfinite(L) || !isfinite(gmax);
+    const bool bad = nonfinite || to;
+    const int bits = (nonfinite ? STATUS_NONFINITE : 0) | (to ? STATUS_TIMEOUT : 0);
     if (mode == FIN_EXPLICIT) {
         EvalOut* o = outs + blockIdx.x;
         o->L = L;
         o->gmax = gmax;
-        o->status = bad ? STATUS_NONFINITE : 0;
+        o->status = bits;
         return;
     }
     if (mode == FIN_RESET) {
@@ -523,7 +527,7 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
         st->retries = 0;
         st->done = 0;
         st->accepted = 0;
-        st->status = bad ? STATUS_NONFINITE : 0;
+        st->status = bits;
         st->iter = 0;
         st->evals = 1;
         st->log_pos = 0;
@@ -542,7 +546,7 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
     double lam = st->lambda;
     int finished = 0, accepted = 0;
     if (bad) {
-        st->status |= STATUS_NONFINITE;
+        st->status |= bits;
         finished = 1;   // the trial is dropped, the state kept
     } else if (d.demons) {
         finished = 1;   // Demons keeps every step; lambda is unused

@@ -11,10 +11,13 @@ import math
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblmreg.so")
+# LMREG_LIBRARY selects another build of the same ABI (the debug-bounds
+# liblmreg_dbg.so); it is read once, at import
+LIB_PATH = os.environ.get("LMREG_LIBRARY") or os.path.join(HERE, "liblmreg.so")
 
 LM_OK, LM_EINVAL, LM_ENOMEM, LM_ECUDA = 0, -1, -2, -3
 LM_ENONFINITE, LM_ETIMEOUT, LM_EUNSUPPORTED, LM_ESTATE = -4, -5, -6, -7
+LM_EBOUNDS = -8
 LM_F32, LM_BF16 = 0, 1
 LM_LOSS_LNCC, LM_LOSS_MSE, LM_LOSS_MI = 0, 1, 2
 LM_METHOD_LM, LM_METHOD_DEMONS = 0, 1
@@ -135,6 +138,8 @@ def load():
         "lm_unet_get_grads": [V, V],
         "lm_conv3d_forward": [I, I, I, I, I, V, V, V, I, V, V],
         "lm_conv3d_backward": [I, I, I, I, I, V, V, V, V, V, V, V],
+        "lm_debug_check": [V],
+        "lm_batch_debug_check": [V],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +239,12 @@ def lm_destroy(ctx: Context):
     h, ctx.handle = ctx.handle, None
     if h:
         load().lm_destroy(h)
+
+
+def lm_debug_check(ctx: Context):
+    """Debug-bounds build: raises LMError (LM_EBOUNDS) if a kernel wrote
+    into a guard band of the context's buffers."""
+    _check(load().lm_debug_check(ctx.handle), "lm_debug_check")
 
 
 def lm_eval(ctx: Context, u, g_out=None):
@@ -360,6 +371,10 @@ def lm_batch_destroy(b: Batch):
         load().lm_batch_destroy(h)
 
 
+def lm_batch_debug_check(b: Batch):
+    _check(load().lm_batch_debug_check(b.handle), "lm_batch_debug_check")
+
+
 def lm_batch_eval(b: Batch, us, g_outs=None):
     """Returns (losses, gmaxes) lists; fills g_outs when given."""
     n = len(b)
@@ -465,7 +480,8 @@ EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_batch_eval", "lm_batch_reset", "lm_batch_iterate",
             "lm_batch_set_targets", "lm_field_resample", "lm_batch_autotune",
             "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
-            "lm_strerror", "lm_last_error",
+            "lm_strerror", "lm_last_error", "lm_debug_check",
+            "lm_batch_debug_check",
             "lm_unet_shapes", "lm_unet_create", "lm_unet_destroy",
             "lm_unet_forward", "lm_unet_train_step", "lm_unet_get_weights",
             "lm_unet_get_grads", "lm_conv3d_forward", "lm_conv3d_backward")
