@@ -49,7 +49,7 @@ ITER_BYTES_PER_VOXEL = 68
 # kernels, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
 # of every kernel of an iteration at 128x160x192, k = 5, FP32), scaled by
 # voxels.  None whenever those kernels changed since the last capture.
-ITER_TRAFFIC_BYTES_PER_VOXEL = 129.3
+ITER_TRAFFIC_BYTES_PER_VOXEL = 128.4
 
 
 def _peaks():
