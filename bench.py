@@ -144,6 +144,42 @@ def aggregate(ms, voxel_evals, device=None):
     return float(t.item()), float(v.item())
 
 
+def _oracle_slab(iters):
+    """The oracle on a 40-slice z-slab (40x192x224) of the pair: initial
+    evaluation + iters LM iterations with the current OpenMP threads;
+    returns (Gvox-it/s, evaluations, seconds)."""
+    import numpy as np
+    import oracle
+    import synth
+    oracle.build()
+    F, M, _ = synth.voronoi_pair(SHAPE, seed=0)
+    Fs, Ms = F[60:100].astype(np.float64), M[60:100].astype(np.float64)
+    t0 = time.perf_counter()
+    st = oracle.State(Fs, Ms, np.zeros((3,) + Fs.shape), oracle.params())
+    evals = 1
+    for _ in range(iters):
+        evals += oracle.lm_step(st)["evals"]
+    dt = time.perf_counter() - t0
+    return Fs.size * evals / dt / 1e9, evals, dt
+
+
+def single_thread_baseline(iters=3):
+    """The oracle on one host thread, in a process of its own (OpenMP reads
+    OMP_NUM_THREADS at start-up); None if that process fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__),
+                            "--oracle-slab", str(iters)], env=env,
+                           capture_output=True, text=True, timeout=600)
+        v, evals, dt = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle on one thread, initial evaluation + "
+                      f"{iters} LM iterations of a 40x192x224 z-slab, "
+                      f"{evals} evaluations in {dt:.1f} s"}
+
+
 def cpu_baseline(F, M, iters=20):
     """The FP64 oracle, as it stands, on the host cores (OpenMP threads)."""
     import numpy as np
@@ -161,7 +197,8 @@ def cpu_baseline(F, M, iters=20):
             "kind": "oracle",
             "sample": f"FP64 C oracle (OpenMP), initial evaluation + {iters} "
                       f"LM iterations of the full 160x192x224 pair, "
-                      f"{evals} evaluations in {dt:.1f} s"}
+                      f"{evals} evaluations in {dt:.1f} s",
+            "single_thread": single_thread_baseline()}
 
 
 def run_reference(args):
@@ -842,7 +879,12 @@ def main():
     ap.add_argument("--ws-level2", type=int, default=0)
     ap.add_argument("--batch-pairs", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=100)
+    ap.add_argument("--oracle-slab", type=int, default=None,
+                    help=argparse.SUPPRESS)
     args = _normalise_args(ap.parse_args())
+    if args.oracle_slab is not None:
+        print(json.dumps(list(_oracle_slab(args.oracle_slab))), flush=True)
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
