@@ -37,6 +37,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 SHAPE = (160, 192, 224)
+LUNG_SHAPE = (384, 448, 448)      # D x H x W: 448 x 448 in-plane, 384 slices
 WORKLOAD = ("brain-MRI-shaped Voronoi pair 160x192x224 fp32, full-resolution "
             "LM iterations, LNCC k=5, sigma_grad=1, lambda0=0.006, mu+=1.5, "
             "mu-=0.975")
@@ -260,8 +261,12 @@ def run_ours(args):
         torch.distributed.barrier()
     P.load()
 
-    shape = tuple(args.shape) if args.shape else SHAPE
-    F, M, _ = synth.voronoi_pair(shape, seed=rank)
+    if args.phantom == "lung":
+        shape = tuple(args.shape) if args.shape else LUNG_SHAPE
+        F, M, _ = synth.lung_pair(shape, seed=rank)
+    else:
+        shape = tuple(args.shape) if args.shape else SHAPE
+        F, M, _ = synth.voronoi_pair(shape, seed=rank)
     V = F.size
     stream = torch.cuda.Stream()
     extra = {}
@@ -383,6 +388,10 @@ def run_ours(args):
         "config": {"workload": (WORKLOAD if shape == SHAPE else
                                 WORKLOAD.replace("160x192x224",
                                                  "x".join(map(str, shape))))
+                   .replace("brain-MRI-shaped Voronoi pair",
+                            "lung-CT-shaped pair (D x H x W)"
+                            if args.phantom == "lung" else
+                            "brain-MRI-shaped Voronoi pair")
                    .replace("LNCC k=5", f"LNCC k={args.win}")
                    + (f", pooled curvature tiles {args.tile}^3 (Eq. tilen)"
                       if args.tile > 1 else "")
@@ -858,6 +867,9 @@ def main():
                     help="other pair size (profiling cases)")
     ap.add_argument("--win", type=int, default=5,
                     help="LNCC window (5 for the brain workload, 7 for lung CT)")
+    ap.add_argument("--phantom", default="voronoi", choices=["voronoi", "lung"],
+                    help="lung: the lung-CT-shaped pair (448x448x384, use "
+                         "--win 7)")
     ap.add_argument("--tile", type=int, default=1,
                     help="curvature tile side k (1: Eq. tile1, >1: Eq. tilen)")
     ap.add_argument("--loss", default="lncc", choices=["lncc", "mse", "mi"])

@@ -19,6 +19,13 @@ Recipes (the paper's datasets are not available; these stand in for them):
     Voronoi partition with label intensities U[0, 1], a smooth multiplicative
     bias field in [0.8, 1.2], N(0, 0.02) noise, clipped to [0, 1]; SVF warp
     with sigma 8 and max displacement 8 vox.
+  * ``lung_pair``     -- lung-CT-shaped phantom at 448x448x384 (W x H x D):
+    HU -1000 (air) outside an ellipsoidal body, tissue U[-100, 100] inside
+    (smoothed at sigma 1 and rescaled to that range), 200 vessel-like tubes
+    (random smoothed splines, radius 1-3 vox, values U[200, 400] HU);
+    clipped to [-1000, 400] and mapped to [0, 1]; SVF warp with sigma 10
+    and max displacement 15 vox.  The cross-modal variant remaps the moving
+    image by the monotone cubic 3m^2 - 2m^3 and adds N(0, 0.02).
   * ``translation_pair`` -- moving(p) = fixed(p + t) for an integer t.
   * ``uneven_shapes`` -- per-pair shapes drawn uniformly per axis between
     64^3 and 160x192x224.
@@ -85,15 +92,35 @@ def _warp_field(f, u):
                      for i in range(3)])
 
 
-def svf_field(shape, rng, sigma, max_disp, squarings=6, coarse=1):
+def svf_field(shape, rng, sigma, max_disp, squarings=6, coarse=1,
+              coarse_exp=False):
     """Exponential of a smooth random stationary velocity field.
 
     v ~ N(0, 1) per component, Gaussian-smoothed (sigma voxels), scaled so
     max |v| = max_disp, then exp(v) by scaling and squaring.  ``coarse`` > 1
     draws v on a grid ``coarse`` times smaller and upsamples it (a cheaper
-    route to the same band-limited field for large volumes).
+    route to the same band-limited field for large volumes); with
+    ``coarse_exp`` the squarings run on that grid too (in its units) and
+    the resulting displacement is upsampled and rescaled.
     """
     shape = tuple(int(n) for n in shape)
+    if coarse > 1 and coarse_exp:
+        cs = tuple(max(4, -(-n // coarse)) for n in shape)
+        v = np.stack([ndimage.gaussian_filter(rng.standard_normal(cs),
+                                              sigma / coarse)
+                      for _ in range(3)])
+        nrm = np.sqrt((v ** 2).sum(0)).max()
+        v *= (max_disp / coarse) / max(nrm, 1e-12)
+        u = v / (2.0 ** squarings)
+        for _ in range(squarings):
+            u = u + _warp_field(u, u)
+        zoom = [n / c for n, c in zip(shape, cs)]
+        out = np.empty((3,) + shape, dtype=np.float32)
+        for i in range(3):
+            # component i is along axis 2 - i: rescale by that axis' zoom
+            out[i] = ndimage.zoom(u[i], zoom, order=1)[
+                :shape[0], :shape[1], :shape[2]] * zoom[2 - i]
+        return out
     if coarse > 1:
         cs = tuple(max(4, -(-n // coarse)) for n in shape)
         v = np.stack([ndimage.gaussian_filter(rng.standard_normal(cs),
@@ -176,6 +203,71 @@ def voronoi_pair(shape=(160, 192, 224), seed=0, svf_sigma=8.0, max_disp=8.0):
                 u.astype(np.float32))
     return _cached(f"voronoi{tuple(shape)}:{seed}:{svf_sigma}:{max_disp}",
                    make)
+
+
+def _spline_points(rng, lo, hi, n_ctrl=5, step=0.5):
+    """Points every ``step`` voxels along a smooth random curve through
+    n_ctrl control points drawn inside the box [lo, hi] (Catmull-Rom)."""
+    P = rng.uniform(lo, hi, (n_ctrl, 3))
+    P = np.vstack([2 * P[0] - P[1], P, 2 * P[-1] - P[-2]])
+    pts = []
+    for i in range(1, n_ctrl):
+        p0, p1, p2, p3 = P[i - 1], P[i], P[i + 1], P[i + 2]
+        n = max(2, int(np.linalg.norm(p2 - p1) / step))
+        t = np.linspace(0, 1, n, endpoint=False)[:, None]
+        pts.append(0.5 * (2 * p1 + (-p0 + p2) * t
+                          + (2 * p0 - 5 * p1 + 4 * p2 - p3) * t ** 2
+                          + (-p0 + 3 * p1 - 3 * p2 + p3) * t ** 3))
+    return np.vstack(pts)
+
+
+def lung_image(shape, rng, n_tubes=200):
+    """Lung-CT-shaped phantom in [0, 1] (HU clipped to [-1000, 400])."""
+    shape = tuple(int(n) for n in shape)
+    c = (np.array(shape) - 1) / 2.0
+    ax = 0.45 * np.array(shape)               # body semi-axes
+    zz = ((np.arange(shape[0]) - c[0]) / ax[0]) ** 2
+    yy = ((np.arange(shape[1]) - c[1]) / ax[1]) ** 2
+    xx = ((np.arange(shape[2]) - c[2]) / ax[2]) ** 2
+    body = (zz[:, None, None] + yy[None, :, None] + xx[None, None, :]) <= 1.0
+    t = ndimage.gaussian_filter(rng.random(shape, dtype=np.float32), 1.0)
+    t = (t - t.min()) / max(float(t.max() - t.min()), 1e-12) * 200 - 100
+    hu = np.where(body, t, np.float32(-1000.0)).astype(np.float32)
+    del t
+    lo, hi = c - 0.8 * ax / np.sqrt(3), c + 0.8 * ax / np.sqrt(3)
+    for _ in range(n_tubes):
+        pts = _spline_points(rng, lo, hi)
+        r = rng.uniform(1.0, 3.0)
+        val = rng.uniform(200.0, 400.0)
+        R = int(np.ceil(r))
+        o = np.arange(-R, R + 1)
+        off = np.stack(np.meshgrid(o, o, o, indexing="ij"), -1).reshape(-1, 3)
+        off = off[(off ** 2).sum(1) <= r * r]
+        vox = np.unique((np.rint(pts)[:, None, :] + off[None]).reshape(-1, 3)
+                        .astype(np.int64), axis=0)
+        ok = np.all((vox >= 0) & (vox < np.array(shape)), axis=1)
+        vox = vox[ok]
+        hu[vox[:, 0], vox[:, 1], vox[:, 2]] = np.maximum(
+            hu[vox[:, 0], vox[:, 1], vox[:, 2]], val)
+    return (np.clip(hu, -1000.0, 400.0) + 1000.0) / 1400.0
+
+
+def lung_pair(shape=(384, 448, 448), seed=0, svf_sigma=10.0, max_disp=15.0,
+              cross_modal=False):
+    """(F, M, u_true) float32 for the lung-CT-shaped workload (shape is
+    (D, H, W): 448 x 448 in-plane, 384 slices)."""
+    def make():
+        rng = np.random.default_rng(seed)
+        F = lung_image(shape, rng)
+        u = svf_field(shape, rng, svf_sigma, max_disp, coarse=4,
+                      coarse_exp=True)
+        M = _warp_image(F, u)
+        if cross_modal:
+            M = 3 * M ** 2 - 2 * M ** 3 + rng.normal(0.0, 0.02, M.shape)
+        return (F.astype(np.float32), M.astype(np.float32),
+                u.astype(np.float32))
+    return _cached(f"lung{tuple(shape)}:{seed}:{svf_sigma}:{max_disp}:"
+                   f"{int(cross_modal)}", make)
 
 
 def translation_pair(shape=(32, 32, 32), seed=0, t=(2, -1, 1)):

@@ -589,6 +589,41 @@ def test_full_size_eval_and_step(P, oracle_mod, kind):
             assert (err <= bound[None]).all(), _worst(err - bound[None])
 
 
+def test_full_size_lung_k7(P, oracle_mod):
+    """Lung-CT-shaped pair at 448x448x384 (W x H x D), LNCC k = 7: the loss,
+    sampled gradient entries and one LM step against the oracle, in the
+    launch configuration the bench times at that size."""
+    import torch
+    import synth
+    F, M, _ = synth.lung_pair(seed=0)
+    shape = F.shape
+    params = P.lm_default_params(win=7)
+    Po = _oracle_params(oracle_mod, params)
+    u0 = synth.random_field(shape, seed=3, scale=1.5)
+    ctx = P.lm_init(_t(F), _t(M), params)
+    u = _t(u0)
+    g = torch.empty_like(u)
+    L, gmax = P.lm_eval(ctx, u, g)
+    ev = oracle_mod.evaluate(F, M, u0.astype(np.float64), Po)
+    assert abs(L - ev["L"]) <= TOL_L * ev["L"], (L, ev["L"])
+    assert abs(gmax - ev["gmax"]) <= 1e-4 * ev["gmax"], (gmax, ev["gmax"])
+    rng = np.random.default_rng(1)
+    idx = tuple(rng.integers(0, n, 20000) for n in shape)
+    gg = g.cpu().numpy()
+    for c in range(3):
+        err = np.abs(gg[c][idx] - ev["g"][c][idx])
+        assert err.max() <= TOL_G * ev["gmax"], (c, err.max(), ev["gmax"])
+    del gg, g
+    P.lm_reset(ctx, u)
+    st = P.lm_get_state(ctx)
+    info = P.lm_iterate(ctx, u, 1)
+    assert info.accepted == 1 and info.retries == 0
+    u1, _ = oracle_mod.trial(u0.astype(np.float64), ev["g"], ev["gmax"],
+                             ev["L"], st.lambda_, Po)
+    err = np.abs(u.cpu().numpy().astype(np.float64) - u1)
+    assert err.max() <= TOL_U, _worst(err)
+
+
 @pytest.mark.parametrize("fa,shape_a,fb,shape_b", [
     (2, (12, 10, 14), 1, (24, 20, 28)),     # up one level (odd-free sizes)
     (1, (25, 21, 29), 2, (12, 10, 14)),     # down one level, ragged
