@@ -624,6 +624,38 @@ def test_full_size_lung_k7(P, oracle_mod):
     assert err.max() <= TOL_U, _worst(err)
 
 
+@pytest.mark.parametrize("kind", ["lncc", "mi"])
+def test_cross_modal_lung_pair(P, oracle_mod, kind):
+    """The cross-modal form of the lung-CT-shaped pair (M remapped by a
+    monotone cubic plus noise) at 64x96x96: LNCC k = 7 and MI (32 bins),
+    loss, gradient and one step against the oracle."""
+    import torch
+    import synth
+    F, M, _ = synth.lung_pair((64, 96, 96), seed=2, max_disp=4.0,
+                              cross_modal=True)
+    shape = F.shape
+    params = P.lm_default_params(**(
+        dict(win=7) if kind == "lncc"
+        else dict(loss=P.LM_LOSS_MI, bins=32, lambda0=1.0, step=0.25)))
+    Po = _oracle_params(oracle_mod, params)
+    u0 = synth.random_field(shape, seed=5, scale=1.5)
+    ctx = P.lm_init(_t(F), _t(M), params)
+    u = _t(u0)
+    g = torch.empty_like(u)
+    L, gmax = P.lm_eval(ctx, u, g)
+    ev = oracle_mod.evaluate(F, M, u0.astype(np.float64), Po)
+    assert abs(L - ev["L"]) <= TOL_L * ev["L"], (L, ev["L"])
+    err = np.abs(g.cpu().numpy() - ev["g"])
+    assert err.max() <= TOL_G * ev["gmax"], (_worst(err), ev["gmax"])
+    P.lm_reset(ctx, u)
+    st = P.lm_get_state(ctx)
+    P.lm_iterate(ctx, u, 1)
+    u1, _ = oracle_mod.trial(u0.astype(np.float64), ev["g"], ev["gmax"],
+                             ev["L"], st.lambda_, Po)
+    err = np.abs(u.cpu().numpy().astype(np.float64) - u1)
+    assert err.max() <= TOL_U, _worst(err)
+
+
 @pytest.mark.parametrize("fa,shape_a,fb,shape_b", [
     (2, (12, 10, 14), 1, (24, 20, 28)),     # up one level (odd-free sizes)
     (1, (25, 21, 29), 2, (12, 10, 14)),     # down one level, ragged
