@@ -170,6 +170,19 @@ typedef struct {
                                   lm_reset (read-only for lm_set_state) */
 } lm_state;
 
+/* One record per finished LM iteration, written on the device by the
+ * decision that ends the iteration (Eq. lambda-update, Eq. rejection). */
+typedef struct {
+    double loss;        /* loss of the field after the iteration */
+    double lambda;      /* damping after the iteration */
+    float  gmax;        /* max_p |g(p)| of the field after the iteration */
+    int    accepted;    /* 1 = a trial was accepted, 0 = discarded */
+    int    retries;     /* rejected trials before the outcome */
+} lm_log_entry;
+
+/* Records the device keeps per context (a ring: the most recent ones). */
+#define LM_LOG_CAP 8192
+
 /* Summary of a registration run. */
 typedef struct {
     int    nlevels;
@@ -231,6 +244,14 @@ LM_API int lm_iterate(lm_ctx *ctx, float *u, int n, lm_step_info *info);
  * keeps the context's field and gradient, replacing only the scalars. */
 LM_API int lm_get_state(lm_ctx *ctx, lm_state *out);
 LM_API int lm_set_state(lm_ctx *ctx, const lm_state *in);
+
+/* The context's iteration log since its last lm_reset, oldest first
+ * (synchronising).  With out NULL, *n receives the number of records
+ * available (at most LM_LOG_CAP); otherwise out (host, caller-owned) holds
+ * cap records and receives the most recent min(cap, available) of them,
+ * their number in *n.  After lm_register the log is that of the finest
+ * level.  LM_EINVAL on a NULL ctx or n, or a negative cap. */
+LM_API int lm_get_log(lm_ctx *ctx, lm_log_entry *out, int cap, int *n);
 
 /* Whole coarse-to-fine registration (Section 2.1 pyramid).  u (device,
  * full resolution [3][D][H][W]): in = initial field, out = result.  At each

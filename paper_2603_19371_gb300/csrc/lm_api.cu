@@ -665,6 +665,38 @@ const char* lm_strerror(int code) {
 
 const char* lm_last_error(void) { return g_err; }
 
+static_assert(LM_LOG_CAP == LOG_CAP, "device log ring and public cap");
+
+int lm_get_log(lm_ctx* c, lm_log_entry* out, int cap, int* n) {
+    if (!c || !n) return fail(LM_EINVAL, "NULL argument");
+    if (out && cap < 0) return fail(LM_EINVAL, "cap must be >= 0");
+    Core* k = c->core.get();
+    LM_CK(cudaMemcpyAsync(k->h_st, k->hpd[0].st, sizeof(DevState),
+                          cudaMemcpyDeviceToHost, k->stream));
+    LM_CK(cudaStreamSynchronize(k->stream));
+    const int pos = k->h_st[0].log_pos;
+    const int avail = pos < LOG_CAP ? pos : LOG_CAP;
+    if (!out) {
+        *n = avail;
+        return LM_OK;
+    }
+    const int m = cap < avail ? cap : avail;
+    if (m > 0) {
+        LM_CK(cudaMemcpy(k->h_log, k->hpd[0].log, LOG_CAP * sizeof(LogEntry),
+                         cudaMemcpyDeviceToHost));
+        for (int i = 0; i < m; ++i) {
+            const LogEntry& e = k->h_log[(pos - m + i) % LOG_CAP];
+            out[i].loss = e.loss;
+            out[i].lambda = e.lambda;
+            out[i].gmax = e.gmax;
+            out[i].accepted = e.accepted;
+            out[i].retries = e.retries;
+        }
+    }
+    *n = m;
+    return LM_OK;
+}
+
 int lm_debug_check(lm_ctx* c) {
     if (!c) return fail(LM_EINVAL, "ctx is NULL");
     int rc = c->core->check_guards();

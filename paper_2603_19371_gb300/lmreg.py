@@ -68,6 +68,12 @@ class State(ctypes.Structure):
                 ("evals", ctypes.c_int), ("kernel_launches", ctypes.c_longlong)]
 
 
+class LogEntry(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("gmax", ctypes.c_float), ("accepted", ctypes.c_int),
+                ("retries", ctypes.c_int)]
+
+
 class Report(ctypes.Structure):
     _fields_ = [("nlevels", ctypes.c_int),
                 ("level_dims", (ctypes.c_int * 3) * LM_MAX_LEVELS),
@@ -139,6 +145,7 @@ def load():
         "lm_conv3d_forward": [I, I, I, I, I, V, V, V, I, V, V],
         "lm_conv3d_backward": [I, I, I, I, I, V, V, V, V, V, V, V],
         "lm_debug_check": [V],
+        "lm_get_log": [V, V, I, ctypes.POINTER(I)],
         "lm_batch_debug_check": [V],
     }
     for name, args in sig.items():
@@ -239,6 +246,28 @@ def lm_destroy(ctx: Context):
     h, ctx.handle = ctx.handle, None
     if h:
         load().lm_destroy(h)
+
+
+def lm_get_log(ctx: Context):
+    """The iteration log since the last lm_reset, oldest first: a list of
+    dicts (loss, lambda, gmax, accepted, retries)."""
+    n = ctypes.c_int()
+    _check(load().lm_get_log(ctx.handle, None, 0, ctypes.byref(n)),
+           "lm_get_log")
+    buf = (LogEntry * max(n.value, 1))()
+    _check(load().lm_get_log(ctx.handle, buf, n.value, ctypes.byref(n)),
+           "lm_get_log")
+    return [{"loss": e.loss, "lambda": e.lambda_, "gmax": e.gmax,
+             "accepted": e.accepted, "retries": e.retries}
+            for e in buf[:n.value]]
+
+
+def lm_log_jsonl(ctx: Context, path):
+    """Appends the iteration log to a JSON-lines file, one record a line."""
+    import json
+    with open(path, "a") as f:
+        for i, r in enumerate(lm_get_log(ctx)):
+            f.write(json.dumps(dict(r, iteration=i)) + "\n")
 
 
 def lm_debug_check(ctx: Context):
@@ -480,7 +509,7 @@ EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_batch_eval", "lm_batch_reset", "lm_batch_iterate",
             "lm_batch_set_targets", "lm_field_resample", "lm_batch_autotune",
             "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
-            "lm_strerror", "lm_last_error", "lm_debug_check",
+            "lm_strerror", "lm_last_error", "lm_debug_check", "lm_get_log",
             "lm_batch_debug_check",
             "lm_unet_shapes", "lm_unet_create", "lm_unet_destroy",
             "lm_unet_forward", "lm_unet_train_step", "lm_unet_get_weights",

@@ -430,6 +430,37 @@ def test_checkpoint_resume_is_bitwise(P):
     assert s2.loss == ref_state.loss and s2.lambda_ == ref_state.lambda_
 
 
+def test_iteration_log_matches_step_infos(P, tmp_path):
+    """The device log holds one record per finished iteration, equal to what
+    lm_step reported, oldest first, restarting at lm_reset."""
+    import json
+    import torch
+    import synth
+    F, M, _ = synth.blob_pair((24, 20, 28), seed=19)
+    params = P.lm_default_params(lambda0=1e-3, step=3.0, reject=1, tau=1.0,
+                                 max_retries=3)
+    ctx = P.lm_init(_t(F), _t(M), params)
+    u = torch.zeros((3, 24, 20, 28), device="cuda")
+    P.lm_reset(ctx, u)
+    assert P.lm_get_log(ctx) == []
+    infos = [P.lm_step(ctx, u) for _ in range(7)]
+    P.lm_iterate(ctx, u, 3)
+    log = P.lm_get_log(ctx)
+    assert len(log) == 10
+    for r, i in zip(log, infos):
+        assert r["loss"] == i.loss and r["lambda"] == i.lambda_
+        assert r["gmax"] == np.float32(i.gmax)
+        assert r["accepted"] == i.accepted and r["retries"] == i.retries
+    st = P.lm_get_state(ctx)
+    assert log[-1]["loss"] == st.loss and log[-1]["lambda"] == st.lambda_
+    path = tmp_path / "log.jsonl"
+    P.lm_log_jsonl(ctx, path)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert [x["iteration"] for x in lines] == list(range(10))
+    P.lm_reset(ctx, u)
+    assert P.lm_get_log(ctx) == []
+
+
 def test_nonfinite_field_is_reported(P):
     import torch
     import synth
