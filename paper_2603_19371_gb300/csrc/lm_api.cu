@@ -241,6 +241,8 @@ struct Core {
         unsigned char* base = (unsigned char*)q;
         LM_CK(cudaMemset(base, 0xFF, GUARD));
         LM_CK(cudaMemset(base + GUARD + bytes, 0xFF, GUARD));
+        // the bands are in place before any kernel on any stream runs
+        LM_CK(cudaDeviceSynchronize());
         guarded.emplace_back(base, bytes);
 #endif
         *out = (T*)((unsigned char*)q + GUARD);
