@@ -883,9 +883,9 @@ def main():
                     help="batch: uneven pairs, batched vs plain; warmstart: "
                          "U-Net warm start vs LM from zero; damping: mu+ / "
                          "cap / rejection sweep (own JSON lines)")
-    ap.add_argument("--ws-train", type=int, default=256)
+    ap.add_argument("--ws-train", type=int, default=512)
     ap.add_argument("--ws-test", type=int, default=32)
-    ap.add_argument("--ws-epochs", type=int, default=16)
+    ap.add_argument("--ws-epochs", type=int, default=24)
     ap.add_argument("--ws-lr", type=float, default=3e-4)
     ap.add_argument("--ws-cap", type=int, default=400)
     ap.add_argument("--ws-level2", type=int, default=0)
