@@ -767,9 +767,11 @@ def run_damping(args):
     configured setting (blob lambda0 = 1, step 0.5; Voronoi lambda0 =
     0.006, step 0.5) and a stress setting (lambda0 = 0.006, step 2 voxels)
     in which steps raise the loss often enough for mu+, the cap and the
-    rejection rule to act.  Reported per run: final loss, the residual of
-    the recovered field against the known warp, loss evaluations, rejected
-    trials and accepted steps that raised the loss."""
+    rejection rule to act, and a lambda0 sweep over [1e-4, 1] at the
+    configured step (mu+ = 1.5, no cap, no rejection).  Reported per run:
+    final loss, the residual of the recovered field against the known warp,
+    loss evaluations, rejected trials and accepted steps that raised the
+    loss."""
     import numpy as np
     import torch
     world, rank, local = _dist()
@@ -785,6 +787,52 @@ def run_damping(args):
              ("voronoi 160x192x224", synth.voronoi_pair(SHAPE, seed=0),
               [(4, 200), (2, 100), (1, 50)]))
     cases = []
+
+    def run_case(name, F, Ft, Mt, ut, sched, setting, lam0, step, mu, cap,
+                 reject):
+        prm = P.lm_default_params(lambda0=lam0, step=step, mu_inc=mu,
+                                  lambda_max=cap, reject=reject, tau=1.0,
+                                  max_retries=10)
+        ctx = P.lm_init(Ft, Mt, prm)
+        u = torch.zeros((3,) + F.shape, device="cuda")
+        t0 = time.perf_counter()
+        rises = None
+        if sched is None:
+            P.lm_reset(ctx, u)
+            prev = P.lm_get_state(ctx).loss
+            curve, rises, iters = [], 0, 100
+            for _ in range(iters):
+                info = P.lm_step(ctx, u)
+                if info.accepted and info.loss > prev:
+                    rises += 1
+                prev = info.loss
+                curve.append(info.loss)
+            st = P.lm_get_state(ctx)
+            final, evals = st.loss, st.evals - 1
+        else:
+            rep = P.lm_register(ctx, sched, u)
+            curve = [rep.level_loss[i] for i in range(rep.nlevels)]
+            final = rep.final_loss
+            iters = sum(rep.level_iters[i] for i in range(rep.nlevels))
+            evals = sum(rep.level_evals[i]
+                        for i in range(rep.nlevels)) - rep.nlevels
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        r_mean, r95 = _inverse_residual(u.cpu().numpy(), ut)
+        lam = P.lm_get_state(ctx).lambda_
+        P.lm_destroy(ctx)
+        cases.append({
+            "pair": name, "setting": setting,
+            "lambda0": lam0, "step": step, "mu_inc": mu,
+            "lambda_max": "inf" if math.isinf(cap) else cap,
+            "reject": reject, "final_loss": final,
+            "residual_mean_vox": r_mean,
+            "residual_p95_vox": r95, "final_lambda": lam,
+            "iterations": iters, "trial_evals": evals,
+            "retries": evals - iters,
+            "accepted_rises": rises, "wall_ms": ms,
+            "curve": curve})
+
     for name, pair, sched in pairs:
         F, M, ut = pair
         Ft, Mt = torch.from_numpy(F).cuda(), torch.from_numpy(M).cuda()
@@ -794,52 +842,13 @@ def run_damping(args):
             for reject in (0, 1):
                 for cap in (1.0, math.inf):
                     for mu in mus:
-                        prm = P.lm_default_params(
-                            lambda0=lam0, step=step, mu_inc=mu,
-                            lambda_max=cap, reject=reject, tau=1.0,
-                            max_retries=10)
-                        ctx = P.lm_init(Ft, Mt, prm)
-                        u = torch.zeros((3,) + F.shape, device="cuda")
-                        t0 = time.perf_counter()
-                        rises = None
-                        if sched is None:
-                            P.lm_reset(ctx, u)
-                            prev = P.lm_get_state(ctx).loss
-                            curve, rises, iters = [], 0, 100
-                            for _ in range(iters):
-                                info = P.lm_step(ctx, u)
-                                if info.accepted and info.loss > prev:
-                                    rises += 1
-                                prev = info.loss
-                                curve.append(info.loss)
-                            st = P.lm_get_state(ctx)
-                            final, evals = st.loss, st.evals - 1
-                        else:
-                            rep = P.lm_register(ctx, sched, u)
-                            curve = [rep.level_loss[i]
-                                     for i in range(rep.nlevels)]
-                            final = rep.final_loss
-                            iters = sum(rep.level_iters[i]
-                                        for i in range(rep.nlevels))
-                            evals = sum(rep.level_evals[i]
-                                        for i in range(rep.nlevels)) \
-                                - rep.nlevels
-                        torch.cuda.synchronize()
-                        ms = (time.perf_counter() - t0) * 1e3
-                        r_mean, r95 = _inverse_residual(u.cpu().numpy(), ut)
-                        lam = P.lm_get_state(ctx).lambda_
-                        P.lm_destroy(ctx)
-                        cases.append({
-                            "pair": name, "setting": setting,
-                            "lambda0": lam0, "step": step, "mu_inc": mu,
-                            "lambda_max": "inf" if math.isinf(cap) else cap,
-                            "reject": reject, "final_loss": final,
-                            "residual_mean_vox": r_mean,
-                            "residual_p95_vox": r95, "final_lambda": lam,
-                            "iterations": iters, "trial_evals": evals,
-                            "retries": evals - iters,
-                            "accepted_rises": rises, "wall_ms": ms,
-                            "curve": curve})
+                        run_case(name, F, Ft, Mt, ut, sched, setting, lam0,
+                                 step, mu, cap, reject)
+        # lambda0 sensitivity (Section 3): the configured step, mu+ = 1.5,
+        # no cap, no rejection
+        for lam0 in (1e-4, 1e-3, 6e-3, 0.05, 0.5, 1.0):
+            run_case(name, F, Ft, Mt, ut, sched, "lambda0 sweep", lam0, 0.5,
+                     1.5, math.inf, 0)
     r0 = {name: _inverse_residual(np.zeros_like(ut), ut)[0]
           for name, (_, _, ut), _ in pairs}
     print(json.dumps({"workload": "damping sweep and rejection ablation",
