@@ -119,7 +119,22 @@ def test_null_arguments(lib):
     assert lib.lm_default_params(None) == lmreg.LM_EINVAL
     assert lib.lm_step(None, None, None) == lmreg.LM_EINVAL
     assert lib.lm_register(None, None, None, None) == lmreg.LM_EINVAL
+    n = ctypes.c_int(-1)
+    assert lib.lm_get_log(None, None, 0, ctypes.byref(n)) == lmreg.LM_EINVAL
+    assert lib.lm_debug_check(None) == lmreg.LM_EINVAL
+    assert lib.lm_batch_debug_check(None) == lmreg.LM_EINVAL
     lib.lm_destroy(None)
+
+
+def test_failure_codes_have_messages(lib):
+    from paper_2603_19371_gb300 import lmreg
+    assert "timed out" in lmreg.lm_strerror(lmreg.LM_ETIMEOUT)
+    assert "outside" in lmreg.lm_strerror(lmreg.LM_EBOUNDS)
+    assert "finite" in lmreg.lm_strerror(lmreg.LM_ENONFINITE)
+    with open(os.path.join(ROOT, "include", "lmreg.h")) as f:
+        h = f.read()
+    assert re.search(r"#define LM_EBOUNDS\s+-8\b", h)
+    assert re.search(r"#define LM_LOG_CAP 8192\b", h)
 
 
 def test_unet_shapes_match_the_oracle(lib):
