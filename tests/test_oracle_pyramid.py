@@ -59,3 +59,24 @@ def test_multilevel_register_lowers_loss(oracle_mod):
     L1 = oracle_mod.loss(F, M, u, P)
     assert L1 < 0.9 * L0
     assert evals >= 25 + 3
+
+
+@pytest.mark.parametrize("f", [2, 4])
+def test_downsample_matches_scipy(oracle_mod, f):
+    """Every level voxel, borders included, against SciPy: the zero-padded
+    Gaussian of sigma f/2 truncated at ceil(3 sigma) taps (scipy's radius
+    int(3 sigma + 0.5) is the same for these sigmas), then trilinear reads
+    with zero padding at the fine coordinate f p + (f - 1)/2."""
+    from scipy import ndimage
+    rng = np.random.default_rng(7)
+    X = rng.random((20, 22, 24))
+    Y = oracle_mod.downsample(X, f)
+    B = ndimage.gaussian_filter(X, 0.5 * f, mode="constant", cval=0.0,
+                                truncate=3.0)
+    dims = oracle_mod.level_dims(X.shape, f)
+    q = [f * np.arange(m) + 0.5 * (f - 1) for m in dims]
+    coords = np.stack(np.meshgrid(*q, indexing="ij"))
+    want = ndimage.map_coordinates(B, coords, order=1, mode="constant",
+                                   cval=0.0)
+    assert Y.shape == want.shape
+    np.testing.assert_allclose(Y, want, rtol=0, atol=1e-13)
