@@ -202,6 +202,52 @@ def cpu_baseline(F, M, iters=20):
             "single_thread": single_thread_baseline()}
 
 
+def oracle_check(P, ctx, u, F, M, params):
+    """One LM iteration of the benched context checked against the FP64
+    oracle stepping from the same FP32 state (teacher-forced): the relative
+    error of the current loss and of the trial's loss, max |du| of the
+    accepted field, and whether the accept / reject decision matches."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    Po = oracle.params(win=params.win,
+                       eps_nr=float(np.float32(params.eps_nr)),
+                       eps_dr=float(np.float32(params.eps_dr)),
+                       sigma_grad=float(params.sigma_grad),
+                       sigma_warp=float(params.sigma_warp),
+                       step=float(params.step), lambda0=params.lambda0,
+                       mu_inc=params.mu_inc, mu_dec=params.mu_dec,
+                       lambda_max=params.lambda_max, reject=params.reject,
+                       tau=params.tau, max_retries=params.max_retries,
+                       tile=params.tile, loss=params.loss,
+                       method=params.method,
+                       alpha=float(np.float32(params.alpha)),
+                       bins=params.bins)
+    t0 = time.perf_counter()
+    Fo, Mo = F.astype(np.float64), M.astype(np.float64)
+    st = P.lm_get_state(ctx)
+    ut = u.cpu().numpy().astype(np.float64)
+    ev = oracle.evaluate(Fo, Mo, ut, Po)
+    u1, _ = oracle.trial(ut, ev["g"], ev["gmax"], ev["L"], st.lambda_, Po)
+    L1 = oracle.loss(Fo, Mo, u1, Po)
+    act, lam_o = oracle.decide(L1, ev["L"], st.loss_prev, st.has_prev,
+                               st.lambda_, 0, Po)
+    info = P.lm_step(ctx, u)
+    same = (info.retries == 0 and info.accepted == 1) == (act == oracle.ACCEPT)
+    du = None
+    if info.retries == 0 and info.accepted == 1:
+        du = float(np.abs(u.cpu().numpy().astype(np.float64) - u1).max())
+    return {"what": "one LM iteration of the benched pair after the timed "
+                    "windows, GPU vs FP64 oracle from the same FP32 state",
+            "rel_loss_err": abs(st.loss - ev["L"]) / ev["L"],
+            "rel_trial_loss_err": abs(info.loss_first - L1) / L1,
+            "max_du_voxel": du, "decision_match": bool(same),
+            "lambda_match": bool(abs(info.lambda_ - lam_o)
+                                 <= 1e-12 * lam_o) if same else False,
+            "bars": {"rel_loss": 1e-5, "du_voxel": 1e-4},
+            "seconds": time.perf_counter() - t0}
+
+
 def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
@@ -292,24 +338,42 @@ def run_ours(args):
     P.lm_iterate(ctx, u, args.warmup, info=False)
     st0 = P.lm_get_state(ctx)
 
+    # Timed windows of exactly K = --steps iterations each, every window
+    # bracketed by a barrier and a device synchronisation on both sides.  A
+    # K-step window of this kernel lasts milliseconds, far below the clock
+    # sampler's 100 ms period, so windows repeat (same count on every rank)
+    # until about a second has been timed; the median window is reported.
     clocks = Clocks(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    P.lm_iterate(ctx, u, args.steps, info=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ck = clocks.stop()
+
+    def window():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        P.lm_iterate(ctx, u, args.steps, info=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return e0.elapsed_time(e1)
+
+    clocks.start()
+    wins = [window()]
+    nwin = max(args.min_windows,
+               min(args.max_windows, math.ceil(args.timed_ms / wins[0])))
     if world > 1:
-        torch.distributed.barrier()
-    ms = e0.elapsed_time(e1)
+        t = torch.tensor([nwin], dtype=torch.int64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        nwin = int(t.item())
+    while len(wins) < nwin:
+        wins.append(window())
+    ck = clocks.stop()
     st1 = P.lm_get_state(ctx)
-    evals = st1.evals - st0.evals
-    launches = st1.kernel_launches - st0.kernel_launches
+    ms = sorted(wins)[len(wins) // 2]
+    evals = (st1.evals - st0.evals) / len(wins)
+    launches = (st1.kernel_launches - st0.kernel_launches) // len(wins)
     ms, voxel_evals = aggregate(ms, float(evals) * V,
                                 device="cuda" if world > 1 else None)
     value = voxel_evals / (ms / 1e3) / 1e9
@@ -333,6 +397,12 @@ def run_ours(args):
                 "bytes_per_voxel": ITER_BYTES_PER_VOXEL,
                 "ms_iteration": ms_iter,
                 "ms_step_with_resampling": ms_step, "ms_e1_e2": ms_eval}
+
+    # error against the FP64 oracle of one teacher-forced iteration of the
+    # benched pair, outside the timed region (rank 0 only)
+    oracle_err = None
+    if rank == 0 and not args.no_oracle_check and V <= 20_000_000:
+        oracle_err = oracle_check(P, ctx, u, F, M, params)
 
     # end to end: host buffers in, whole registration, field out
     e2e = None
@@ -411,7 +481,13 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": ck,
-        "evals": int(evals),
+        "evals": int(round(evals)),
+        "timing": {"windows": len(wins), "steps_per_window": args.steps,
+                   "ms_window_min": min(wins), "ms_window_median": ms,
+                   "ms_window_max": max(wins),
+                   "note": "value, ms_per_step and gpu_launches are per "
+                           "K-step window (median window)"},
+        "oracle_error": oracle_err,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -759,7 +835,7 @@ def _inverse_residual(u, u_true, stride=4):
 
 def run_damping(args):
     """Damping-cliff sweep and rejection ablation (Section 3 sensitivity
-    study, Section 3.3) on the synthetic phantoms: mu+ against the cap
+    study, Section 3.4) on the synthetic phantoms: mu+ against the cap
     lambda_max in {1, inf}, with and without Eq. rejection (tau = 1, 10
     retries).  32^3 blob pair: 100 full-resolution iterations,
     per-iteration loss curve.  160x192x224 Voronoi pair: levels 4/2/1 x
@@ -871,6 +947,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the teacher-forced iteration against the oracle")
+    ap.add_argument("--timed-ms", type=float, default=1000.0,
+                    help="repeat K-step windows until about this long")
+    ap.add_argument("--min-windows", type=int, default=5)
+    ap.add_argument("--max-windows", type=int, default=400)
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     metavar=("D", "H", "W"),
                     help="other pair size (profiling cases)")

@@ -8,7 +8,7 @@
  * Registration"), with the per-voxel rank-1 damped step of Eq. tile1
  * (Appendix A), the compositive update of Eq. compositive (Section 2.1), the
  * damping rule of Eq. lambda-update and the rejection rule of Eq. rejection
- * (Section 3.3), on a coarse-to-fine pyramid (Section 2.1).
+ * (Section 3.4), on a coarse-to-fine pyramid (Section 2.1).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -89,7 +89,7 @@ typedef struct {
 
 /* Optimiser and loss parameters.  lm_default_params() fills the paper's
  * defaults: lambda0 = 0.006, mu+ = 1.5, mu- = 0.975 (Section 3), rejection
- * off with tau = 1 and 10 retries (Section 3.3). */
+ * off with tau = 1 and 10 retries (Section 3.4). */
 typedef struct {
     int    win;         /* LNCC box side k: odd, 3..9.                 [5] */
     float  eps_nr;      /* LNCC numerator stabiliser, >= 0.         [1e-5] */
@@ -118,7 +118,7 @@ typedef struct {
                            residual is r = log2 B - MI (the squared-loss
                            form (log2 B - MI)^2 of Section 2.2). */
     int    method;      /* LM_METHOD_LM or LM_METHOD_DEMONS.           [LM]
-                           Demons (Section 2.4) needs LM_LOSS_MSE, tile 1
+                           Demons (Section 2.3) needs LM_LOSS_MSE, tile 1
                            and reject 0.  Each iteration takes, per voxel,
                            du = r n / (|n|^2 + alpha^2 r^2) with the voxel's
                            residual r = F - M(p + u) and n the gradient of
@@ -201,7 +201,10 @@ typedef struct lm_ctx lm_ctx;
 /* Fill *p with the defaults listed above.  LM_EINVAL if p is NULL. */
 LM_API int lm_default_params(lm_params *p);
 
-/* Create a context for one fixed/moving pair of equal shape and dtype.
+/* Create a context for one fixed/moving pair of equal shape and dtype: the
+ * registration problem of Section 1, Eq. 1 (minimise L_sim(F, M o (Id + u))
+ * over the displacement u), with the LM parameters of Section 3 (lambda0,
+ * mu+, mu-) and the rejection parameters of Section 3.4 in p.
  * fixed, moving: image descriptors; their device data must stay valid and
  *   unchanged for the context's lifetime.
  * p: parameters (copied); NULL = defaults.
@@ -215,16 +218,21 @@ LM_API int lm_init(lm_ctx **ctx, const lm_volume *fixed, const lm_volume *moving
 /* Release the context and its scratch.  NULL is ignored. */
 LM_API void lm_destroy(lm_ctx *ctx);
 
-/* Evaluate the loss and its smoothed gradient at u (steps (a)-(c)) without
- * touching the optimiser state.  u: device [3][D][H][W].  loss (host, may be
+/* Evaluate the loss and its smoothed gradient at u without touching the
+ * optimiser state: M resampled at Id + u (Section 2.1), the residual r of
+ * the squared-loss form of Section 2.2 and its gradient with respect to u,
+ * smoothed by the sigma_grad Gaussian (the gradient g that Eq. tile1 takes;
+ * Section 3 describes the FireANTs-style smoothed gradient).  This is what
+ * every LM iteration evaluates for its trial.  u: device [3][D][H][W].  loss (host, may be
  * NULL), g_out (device [3][D][H][W], may be NULL), gmax (host, may be NULL).
  * Synchronises the stream.  LM_ENONFINITE if the loss is not finite. */
 LM_API int lm_eval(lm_ctx *ctx, const float *u, double *loss, float *g_out,
             float *gmax);
 
 /* Start an LM run from the field u (device, in/out for later lm_step
- * calls): evaluates L_0 and g_0 at u, sets lambda = lambda0 and clears the
- * loss history.  Asynchronous. */
+ * calls): evaluates L_0 and g_0 at u, sets lambda = lambda0 (Section 3) and
+ * clears the loss history that Eq. lambda-update and Eq. rejection compare
+ * against.  Asynchronous. */
 LM_API int lm_reset(lm_ctx *ctx, float *u);
 
 /* One LM iteration (Section 2.2 / 3.3) on the field u passed to the last
@@ -236,8 +244,10 @@ LM_API int lm_reset(lm_ctx *ctx, float *u);
  * the pointer given to lm_reset. */
 LM_API int lm_step(lm_ctx *ctx, float *u, lm_step_info *info);
 
-/* n LM iterations as lm_step, replayed from a captured CUDA graph; info of
- * the last iteration (host, may be NULL). */
+/* n LM iterations, each exactly the iteration of lm_step (Eq. tile1 or
+ * Eq. tilen, Eq. compositive, Eq. lambda-update and Eq. rejection, Sections
+ * 2.1-2.2 and 3.4), replayed from a captured CUDA graph; info of the last
+ * iteration (host, may be NULL).  u as for lm_step. */
 LM_API int lm_iterate(lm_ctx *ctx, float *u, int n, lm_step_info *info);
 
 /* Read / overwrite the optimiser scalars (synchronising).  lm_set_state
@@ -269,7 +279,8 @@ LM_API int lm_register(lm_ctx *ctx, const lm_schedule *s, float *u, lm_report *r
 LM_API int lm_state_save(lm_ctx *ctx, void *buf, size_t *nbytes);
 LM_API int lm_state_load(lm_ctx *ctx, const void *buf, size_t nbytes);
 
-/* Measurement aid: time the two passes of the iteration separately.  With
+/* Measurement aid (the paper times whole steps, Section 3.5; this splits
+ * one iteration into its two passes): time the two passes separately.  With
  * the state of the last lm_reset / lm_step on u, launches the trial kernels
  * (pass 2: Eq. tile1 or Eq. tilen + Eq. compositive) n times, then the
  * evaluation kernels (pass 1: resampling, the loss and its gradient,
@@ -330,6 +341,23 @@ LM_API int lm_field_resample(const float *src, int Da, int Ha, int Wa, int fa,
                              float *dst, int Db, int Hb, int Wb, int fb,
                              void *cuda_stream);
 
+/* Pyramid level of an image (Section 2.1, coarse-to-fine), as lm_register
+ * builds it: Gaussian blur with sigma = factor / 2 (taps exp(-j^2 / 2
+ * sigma^2), |j| <= ceil(3 sigma), normalised, zero padding), then the
+ * level voxel p is the blurred image read trilinearly (zero outside) at the
+ * fine coordinate factor p + (factor - 1) / 2.
+ *   src: device image [D][H][W] of src->dtype (caller-owned, read);
+ *   factor: 2 or 4; the level is [Dl][Hl][Wl] with Dl = max(1, D / factor)
+ *   (rounded down) and likewise for H and W;
+ *   dst: device, Dl*Hl*Wl elements of src->dtype (written; BF16 levels are
+ *   rounded once from the FP32 value);
+ *   tmp: device scratch of 2*D*H*W floats (caller-owned, overwritten);
+ *   dims (host, may be NULL) receives Dl, Hl, Wl.
+ * Asynchronous on cuda_stream.  LM_EINVAL on NULL or host pointers, bad
+ * sizes, dtypes or factors. */
+LM_API int lm_downsample(const lm_volume *src, int factor, void *dst,
+                         float *tmp, int *dims, void *cuda_stream);
+
 /* Per-pair stopping loss.  The paper has no counterpart: it serves batched
  * runs that must bring every pair to a given loss (for instance the final
  * loss of another run) without spending iterations on pairs already there.
@@ -369,11 +397,14 @@ LM_API int lm_register_batch(int npairs, const lm_volume *fixed,
  * with rows padded to a multiple of 4 voxels; larger volumes return
  * LM_EINVAL.
  *   fixed, moving: images as for lm_init; p: parameters (NULL = defaults;
- *   only win, eps_nr, eps_dr, sigma_grad, loss, method and alpha matter);
+ *   every field is checked as lm_init checks it, and only win, eps_nr,
+ *   eps_dr, sigma_grad, loss, method and alpha change the result);
  *   u: device field
  *   [3][D][H][W]; g_out: device [3][D][H][W] (written); loss_out: device
  *   double (written; NaN if the loss or gradient is not finite; may be
  *   NULL); gmax_out: device float (may be NULL); cuda_stream: the stream.
+ *   Every non-NULL pointer must be device (or managed) memory; a host
+ *   pointer returns LM_EINVAL before anything is launched.
  * Asynchronous on cuda_stream.  The first call on a device looks up the
  * array's device address and prepares the kernels (no allocation); make
  * that first call before any stream capture.  Every call shares the one

@@ -67,7 +67,7 @@ class Params(ctypes.Structure):
 
 
 # Section 3 (experiments): lambda0 = 0.006, mu+ = 1.5, mu- = 0.975, tile 1;
-# Section 3.3 (rejection): tau = 1 with cap 1 when rejection is on.
+# Section 3.4 (rejection): tau = 1 with cap 1 when rejection is on.
 DEFAULTS = dict(win=5, eps_nr=1e-5, eps_dr=1e-5, sigma_grad=1.0,
                 sigma_warp=0.0, step=0.5, lambda0=0.006, mu_inc=1.5,
                 mu_dec=0.975, lambda_max=math.inf, reject=0, tau=1.0,
@@ -75,7 +75,7 @@ DEFAULTS = dict(win=5, eps_nr=1e-5, eps_dr=1e-5, sigma_grad=1.0,
                 bins=32)
 
 LNCC, MSE, MI = 0, 1, 2   # Section 2.2 squared-loss forms
-LM, DEMONS = 0, 1         # Section 2.2 optimiser / Section 2.4 special case
+LM, DEMONS = 0, 1         # Section 2.2 optimiser / Section 2.3 special case
 
 
 def params(**kw) -> Params:
@@ -220,7 +220,7 @@ def mi(F, J, bins, lo, hi):
 
 
 def demons_force(F, M, u, alpha):
-    """Update of Eq. demons (Section 2.4): r n / (|n|^2 + alpha^2 r^2) with
+    """Update of Eq. demons (Section 2.3): r n / (|n|^2 + alpha^2 r^2) with
     r = F - M(p + u) and n the gradient of M at p + u."""
     F, M, u = _f64(F), _f64(M), _f64(u)
     nx, ny, nz = _dims(F)

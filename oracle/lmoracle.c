@@ -507,7 +507,7 @@ void or_eval(int nx, int ny, int nz, const double *F, const double *M,
 }
 
 /* ------------------------------------------------------------------ */
-/* Demons as per-voxel LM on MSE, Eq. demons (Section 2.4):             */
+/* Demons as per-voxel LM on MSE, Eq. demons (Section 2.3):             */
 /*   r(p) = F(p) - J(p),  n(p) = dJ/du(p) (the gradient of M at p + u),  */
 /*   du(p) = r n / (|n|^2 + lambda_p),  lambda_p = alpha^2 r^2           */
 /* (0 where r and n both vanish).  du: [3V] (written).                  */
@@ -535,7 +535,7 @@ void or_demons_force(int nx, int ny, int nz, const double *F,
 /* Demons evaluation of a field: L = MSE (as or_eval with OR_MSE) and     */
 /* the smoothed update g = G_sigma_grad * du of Eq. demons (reading: the  */
 /* Gaussian of the gradient doubles as the fluid-like smoothing of the    */
-/* update, Section 2.4 leaves the regulariser open); gmax = max |g|.      */
+/* update, Section 2.3 leaves the regulariser open); gmax = max |g|.      */
 void or_demons_eval(int nx, int ny, int nz, const double *F, const double *M,
                     const double *u, const or_params *P, double *L_out,
                     double *g, double *gmax_out)
@@ -604,7 +604,7 @@ void or_compose(int nx, int ny, int nz, const double *u, const double *v,
 }
 
 /* ------------------------------------------------------------------ */
-/* Pooled curvature, Eq. tilen (Section 2.3; tile side k, Section 3):   */
+/* Pooled curvature, Eq. tilen (Section 2.2; tile side k, Section 3):   */
 /*   H_T   = |T|^-1 sum_{q in T} ghat(q) ghat(q)^T                       */
 /*   du(p) = -(H_T + lambda I)^-1 r ghat(p),   T = the tile holding p    */
 /* Readings: the tiles are the non-overlapping k x k x k blocks of the   */
@@ -806,7 +806,7 @@ void or_lm_step(int nx, int ny, int nz, const double *F, const double *M,
             if (u_first) memcpy(u_first, ut, 3 * V * sizeof(double));
             if (L_first) *L_first = Lt;
         }
-        /* Demons: no damping rule, every step is kept (Section 2.4) */
+        /* Demons: no damping rule, every step is kept (Section 2.3) */
         int act = OR_ACCEPT;
         lam = *lambda;
         if (P->method != OR_DEMONS)

@@ -43,17 +43,7 @@ void lmk::set_last_error(const char* msg) {
     snprintf(g_err, sizeof(g_err), "%s", msg);
 }
 
-namespace {
-
-#define LM_CK(call)                                                        \
-    do {                                                                   \
-        cudaError_t e_ = (call);                                           \
-        if (e_ != cudaSuccess)                                             \
-            return fail(LM_ECUDA, "%s failed: %s", #call,                  \
-                        cudaGetErrorString(e_));                           \
-    } while (0)
-
-bool is_device_ptr(const void* p) {
+bool lmk::is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -63,7 +53,7 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-Taps make_taps(double sigma) {
+Taps lmk::make_taps(double sigma) {
     Taps t;
     memset(&t, 0, sizeof(t));
     if (!(sigma > 0)) {
@@ -82,7 +72,7 @@ Taps make_taps(double sigma) {
     return t;
 }
 
-int check_params(const lm_params* p) {
+int lmk::check_params(const lm_params* p) {
     if (!(p->win >= 3 && p->win <= 9 && (p->win & 1)))
         return fail(LM_EINVAL, "win must be odd in [3, 9], got %d", p->win);
     if (!(p->eps_nr >= 0) || !(p->eps_dr > 0) || !std::isfinite(p->eps_nr) ||
@@ -128,6 +118,16 @@ int check_params(const lm_params* p) {
                     "and reject 0");
     return LM_OK;
 }
+
+namespace {
+
+#define LM_CK(call)                                                        \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess)                                             \
+            return fail(LM_ECUDA, "%s failed: %s", #call,                  \
+                        cudaGetErrorString(e_));                           \
+    } while (0)
 
 // Shape and dtype checks (host only, no CUDA call).
 int check_volume(const lm_volume* v, const char* name) {
@@ -1193,6 +1193,30 @@ extern "C" int lm_field_resample(const float* src, int Da, int Ha, int Wa,
     Geom gb{Wb, Hb, Db, (long long)Wb * Hb * Db};
     resample_field(src, ga, fa, dst, gb, fb, (cudaStream_t)stream);
     LM_CK(cudaGetLastError());
+    return LM_OK;
+}
+
+extern "C" int lm_downsample(const lm_volume* src, int factor, void* dst,
+                             float* tmp, int* dims, void* stream) {
+    int rc = check_volume(src, "src");
+    if (rc != LM_OK) return rc;
+    if (factor != 2 && factor != 4)
+        return fail(LM_EINVAL, "factor must be 2 or 4, got %d", factor);
+    if (!is_device_ptr(src->data) || !is_device_ptr(dst) ||
+        !is_device_ptr(tmp))
+        return fail(LM_EINVAL, "src data, dst and tmp must be device pointers");
+    const Geom g{src->W, src->H, src->D, (long long)src->W * src->H * src->D};
+    int lx, ly, lz;
+    level_dims(g.nx, g.ny, g.nz, factor, &lx, &ly, &lz);
+    if (downsample_image(src->data, src->dtype, g, factor, dst, tmp,
+                         (cudaStream_t)stream))
+        return fail(LM_ECUDA, "downsample failed: %s",
+                    cudaGetErrorString(cudaGetLastError()));
+    if (dims) {
+        dims[0] = lz;
+        dims[1] = ly;
+        dims[2] = lx;
+    }
     return LM_OK;
 }
 

@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // ----------------------------------------------------------------------
-// Pointwise evaluation for MSE (Section 2.2) and Demons (Section 2.4), in
+// Pointwise evaluation for MSE (Section 2.2) and Demons (Section 2.3), in
 // place of E1.  Per voxel: dq = Fq - Jq, the fixed-point F - J (exact);
 // the loss term dq^2, rounded to the MSE unit (mse_shift) and summed
 // exactly; and g_raw:

@@ -91,7 +91,7 @@ struct DecideConsts {
     int reject, max_retries;
     int mse;      // loss partials are MSE sums (unit from the pair's QScale)
     int mi;       // the loss is r = log2 B - MI, from the MI table kernel
-    int demons;   // every trial is kept (Section 2.4), lambda unused
+    int demons;   // every trial is kept (Section 2.3), lambda unused
 };
 
 // Image element load as float.

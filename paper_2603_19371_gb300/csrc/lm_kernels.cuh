@@ -252,4 +252,13 @@ int batch_sync_back(const Batch& b, cudaStream_t s);
 // Replace the calling thread's lm_last_error() message.
 void set_last_error(const char* msg);
 
+// Host-side argument checks shared by every entry point (lm_api.cu).
+// is_device_ptr: p is device or managed memory (no allocation, no sync).
+bool is_device_ptr(const void* p);
+// Gaussian taps exp(-j^2 / 2 sigma^2), |j| <= ceil(3 sigma), normalised to
+// sum 1; sigma <= 0 gives the identity (R = 0).
+Taps make_taps(double sigma);
+// Every lm_params field in range; LM_EINVAL with lm_last_error() set.
+int check_params(const lm_params* p);
+
 }  // namespace lmk

@@ -69,7 +69,9 @@ int fail(int code, const char* m) {
 // the SM count, and the kernels' shared-memory opt-in.
 int setup_device(int dev, unsigned char** ptr, int* sms) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (dev < 0 || dev >= MAX_DEVICES) return LM_EUNSUPPORTED;
+    if (dev < 0 || dev >= MAX_DEVICES)
+        return fail(LM_EUNSUPPORTED,
+                    "device ordinal beyond the no-alloc device table");
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -153,18 +155,21 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     } else {
         lm_default_params(&prm);
     }
-    if (!(prm.win >= 3 && prm.win <= 9 && (prm.win & 1)) ||
-        !(prm.sigma_grad >= 0 && prm.sigma_grad <= 2) || !(prm.eps_dr > 0) ||
-        !(prm.eps_nr >= 0))
-        return fail(LM_EINVAL, "win, sigma_grad or eps out of range");
+    // the same parameter rules as lm_init
+    int rc = lmk::check_params(&prm);
+    if (rc != LM_OK) return rc;
     if (prm.loss == LM_LOSS_MI)
         return fail(LM_EUNSUPPORTED,
                     "the MI loss needs its histogram buffers: use lm_init");
-    if ((prm.loss != LM_LOSS_LNCC && prm.loss != LM_LOSS_MSE) ||
-        (prm.method != LM_METHOD_LM && prm.method != LM_METHOD_DEMONS) ||
-        !(prm.alpha > 0) ||
-        (prm.method == LM_METHOD_DEMONS && prm.loss != LM_LOSS_MSE))
-        return fail(LM_EINVAL, "loss, method or alpha out of range");
+    // every pointer the kernels dereference must be device memory: a host
+    // pointer here would only fail inside a kernel
+    if (!lmk::is_device_ptr(fixed->data) || !lmk::is_device_ptr(moving->data))
+        return fail(LM_EINVAL, "fixed or moving data is not a device pointer");
+    if (!lmk::is_device_ptr(u) || !lmk::is_device_ptr(g_out))
+        return fail(LM_EINVAL, "u or g_out is not a device pointer");
+    if ((loss_out && !lmk::is_device_ptr(loss_out)) ||
+        (gmax_out && !lmk::is_device_ptr(gmax_out)))
+        return fail(LM_EINVAL, "loss_out or gmax_out is not a device pointer");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -173,7 +178,7 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     }
     unsigned char* base = nullptr;
     int sms = 0;
-    int rc = setup_device(dev, &base, &sms);
+    rc = setup_device(dev, &base, &sms);
     if (rc != LM_OK) return rc;
 
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -203,9 +208,8 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     pd.tm_graw = base + OFF_TMAP;
     Map128 map;
     {
-        double sg = prm.sigma_grad;
-        int R = sg > 0 ? (int)ceil(3.0 * sg) : 0;
-        int rc2 = lmk::encode_graw_map(map.b, pd.graw, pd.g, R);
+        int rc2 = lmk::encode_graw_map(map.b, pd.graw, pd.g,
+                                       lmk::make_taps(prm.sigma_grad).R);
         if (rc2 != LM_OK) return rc2;
     }
     lmk::PairDesc* dpd = (lmk::PairDesc*)(base + OFF_PD);
@@ -220,22 +224,7 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     b.c.eps_nr = prm.eps_nr;
     b.c.eps_dr = prm.eps_dr;
     b.c.inv_k3 = (float)(1.0 / ((double)prm.win * prm.win * prm.win));
-    // Gaussian taps, as in the context path
-    {
-        double sg = prm.sigma_grad;
-        b.c.gtaps.R = 0;
-        b.c.gtaps.t[0] = 1.f;
-        if (sg > 0) {
-            int R = (int)ceil(3.0 * sg);
-            double w[2 * lmk::MAX_R + 1], sum = 0;
-            for (int j = -R; j <= R; ++j) {
-                w[j + R] = exp(-(double)j * j / (2.0 * sg * sg));
-                sum += w[j + R];
-            }
-            b.c.gtaps.R = R;
-            for (int j = 0; j <= 2 * R; ++j) b.c.gtaps.t[j] = (float)(w[j] / sum);
-        }
-    }
+    b.c.gtaps = lmk::make_taps(prm.sigma_grad);   // as lm_init's
     b.loss = prm.loss;
     b.method = prm.method;
     b.alpha = prm.alpha;

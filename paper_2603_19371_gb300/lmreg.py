@@ -125,6 +125,8 @@ def load():
                              ctypes.POINTER(StepInfo)],
         "lm_batch_set_targets": [V, ctypes.POINTER(D)],
         "lm_field_resample": [V, I, I, I, I, V, I, I, I, I, V],
+        "lm_downsample": [ctypes.POINTER(Volume), I, V, V, ctypes.POINTER(I),
+                          V],
         "lm_batch_autotune": [V, ctypes.POINTER(V), I, ctypes.POINTER(I),
                               ctypes.POINTER(I), ctypes.POINTER(D)],
         "lm_batch_register": [V, ctypes.POINTER(Schedule), ctypes.POINTER(V),
@@ -455,6 +457,25 @@ def lm_field_resample(src, fa, dst, fb, stream=None):
                                     _stream_handle(stream)), "lm_field_resample")
 
 
+def lm_downsample(src, factor, stream=None):
+    """Pyramid level of factor 2 or 4 of a 3-D CUDA image (as lm_register
+    builds it); returns a new tensor of the image's dtype."""
+    import torch
+    v = _volume(src)
+    dims = (ctypes.c_int * 3)()
+    D, H, W = src.shape
+    Dl, Hl, Wl = (max(1, n // int(factor)) for n in (D, H, W))
+    dst = torch.empty((Dl, Hl, Wl), dtype=src.dtype, device=src.device)
+    tmp = torch.empty((2 * D * H * W,), dtype=torch.float32,
+                      device=src.device)
+    _check(load().lm_downsample(ctypes.byref(v), int(factor),
+                                ctypes.c_void_p(dst.data_ptr()),
+                                ctypes.c_void_p(tmp.data_ptr()), dims,
+                                _stream_handle(stream)), "lm_downsample")
+    assert tuple(dims) == (Dl, Hl, Wl)
+    return dst
+
+
 def lm_batch_register(b: Batch, levels, us):
     s = _schedule(levels)
     reps = (Report * len(b))()
@@ -482,11 +503,25 @@ def lm_register_batch(fixed, moving, us, levels, params: Params | None = None,
 def lm_eval_noalloc(fixed, moving, u, g_out, loss_out=None, gmax_out=None,
                     params: Params | None = None, stream=None):
     """Evaluation without allocation (static scratch, at most
-    LM_NOALLOC_MAX_VOXELS voxels); outputs are device tensors."""
+    LM_NOALLOC_MAX_VOXELS voxels); outputs are device tensors: g_out a
+    (3, D, H, W) float32 field, loss_out a float64 and gmax_out a float32
+    CUDA tensor of at least one element (the kernel writes element 0)."""
+    import torch
     vf, vm = _volume(fixed), _volume(moving)
+    if tuple(moving.shape) != tuple(fixed.shape):
+        raise ValueError("fixed and moving differ in shape")
     p = ctypes.byref(params) if params is not None else None
-    lp = ctypes.c_void_p(loss_out.data_ptr()) if loss_out is not None else None
-    gp = ctypes.c_void_p(gmax_out.data_ptr()) if gmax_out is not None else None
+
+    def scalar_ptr(t, dtype, name):
+        if t is None:
+            return None
+        if not t.is_cuda or t.dtype != dtype or t.numel() < 1:
+            raise ValueError(f"{name} must be a CUDA {dtype} tensor with at "
+                             "least one element")
+        return ctypes.c_void_p(t.data_ptr())
+
+    lp = scalar_ptr(loss_out, torch.float64, "loss_out")
+    gp = scalar_ptr(gmax_out, torch.float32, "gmax_out")
     _check(load().lm_eval_noalloc(ctypes.byref(vf), ctypes.byref(vm), p,
                                   _field_ptr(u, fixed.shape),
                                   _field_ptr(g_out, fixed.shape), lp, gp,
@@ -508,6 +543,7 @@ EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_time_passes", "lm_batch_init", "lm_batch_destroy",
             "lm_batch_eval", "lm_batch_reset", "lm_batch_iterate",
             "lm_batch_set_targets", "lm_field_resample", "lm_batch_autotune",
+            "lm_downsample",
             "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
             "lm_strerror", "lm_last_error", "lm_debug_check", "lm_get_log",
             "lm_batch_debug_check",

@@ -52,7 +52,7 @@ def test_binding_covers_every_declared_symbol():
 def test_default_params_match_the_paper(lib):
     from paper_2603_19371_gb300 import lmreg
     p = lmreg.lm_default_params()
-    # Section 3: lambda0 = 0.006, mu+ = 1.5, mu- = 0.975; Section 3.3: tau 1,
+    # Section 3: lambda0 = 0.006, mu+ = 1.5, mu- = 0.975; Section 3.4: tau 1,
     # 10 retries, rejection off by default
     assert p.lambda0 == pytest.approx(0.006)
     assert p.mu_inc == 1.5 and p.mu_dec == pytest.approx(0.975)
@@ -157,3 +157,25 @@ def test_unet_create_validates_sizes_on_the_host(lib):
     # unsupported convolution shapes fail before any CUDA call
     assert lib.lm_conv3d_forward(4, 4, 4, 3, 16, w, w, None, 0, w, None) == lmreg.LM_EINVAL
     assert lib.lm_conv3d_forward(4, 4, 4, 16, 8, w, w, None, 0, w, None) == lmreg.LM_EINVAL
+
+
+def test_noalloc_validates_on_the_host(lib):
+    """lm_eval_noalloc checks its parameters with lm_init's rules and refuses
+    pointers that are not device memory before any launch (on a machine
+    without a GPU no pointer is device memory)."""
+    from paper_2603_19371_gb300 import lmreg
+    V = lmreg.Volume
+    buf = (ctypes.c_float * 64)()
+    addr = ctypes.addressof(buf)
+    vol = V(4, 4, 4, lmreg.LM_F32, addr)
+    p = lmreg.lm_default_params()
+    p.eps_nr = float("inf")
+    rc = lib.lm_eval_noalloc(ctypes.byref(vol), ctypes.byref(vol),
+                             ctypes.byref(p), ctypes.c_void_p(addr),
+                             ctypes.c_void_p(addr), None, None, None)
+    assert rc == lmreg.LM_EINVAL and "eps" in lmreg.lm_last_error()
+    rc = lib.lm_eval_noalloc(ctypes.byref(vol), ctypes.byref(vol), None,
+                             ctypes.c_void_p(addr), ctypes.c_void_p(addr),
+                             None, None, None)
+    assert rc == lmreg.LM_EINVAL
+    assert "device pointer" in lmreg.lm_last_error()

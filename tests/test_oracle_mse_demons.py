@@ -1,5 +1,5 @@
 """Pins for the oracle's MSE loss (Section 2.2) and its Demons special case
-(Section 2.4, Eq. demons).
+(Section 2.3, Eq. demons).
 
 MSE: the closed form at the identity, the gradient against central
 finite differences of the loss, and the smoothing of the raw gradient.

@@ -1,4 +1,4 @@
-"""Pins for the oracle's pooled-curvature step, Eq. tilen (Section 2.3; tile
+"""Pins for the oracle's pooled-curvature step, Eq. tilen (Section 2.2; tile
 side k swept in Section 3).
 
 Readings under test: non-overlapping k^3 tiles aligned at the grid origin
