@@ -392,10 +392,12 @@ LM_API int lm_register_batch(int npairs, const lm_volume *fixed,
  * allocation.  The MI loss needs per-pair histogram buffers and returns
  * LM_EUNSUPPORTED here.
  * Its scratch is one static device array inside the library, sized for at
- * most LM_NOALLOC_MAX_VOXELS voxels (2^19, e.g. 80^3; about 21 MB, held
+ * most LM_NOALLOC_MAX_VOXELS voxels (2^19, e.g. 80^3; about 29 MB, held
  * by every GPU that loads the library until the process exits), counted
  * with rows padded to a multiple of 4 voxels; larger volumes return
- * LM_EINVAL.
+ * LM_EINVAL, and so do LNCC volumes whose halo-padded fixed-point layout
+ * ((32 ceil(W / 32) + 4w) (32 ceil(H / 32) + 4w) (D + 4w + 2) elements for
+ * window k = 2w + 1) exceeds 3 LM_NOALLOC_MAX_VOXELS.
  *   fixed, moving: images as for lm_init; p: parameters (NULL = defaults;
  *   every field is checked as lm_init checks it, and only win, eps_nr,
  *   eps_dr, sigma_grad, loss, method and alpha change the result);

@@ -401,7 +401,9 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
     DevState* st = nullptr;
     QScale* qs = nullptr;
     LogEntry* lg = nullptr;
+    unsigned* flags = nullptr;
     if ((rc = c->dalloc(&st, npairs * sizeof(DevState))) ||
+        (rc = c->dalloc(&flags, npairs * sizeof(unsigned))) ||
         (rc = c->dalloc(&qs, npairs * sizeof(QScale))) ||
         (rc = c->dalloc(&lg, npairs * sizeof(LogEntry) * LOG_CAP)) ||
         (rc = c->dalloc(&c->eout, npairs * sizeof(EvalOut))) ||
@@ -414,13 +416,18 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
     for (int i = 0; i < npairs; ++i) {
         PairDesc& d = c->hpd[i];
         size_t V = (size_t)d.g.V;
+        // jq and fq: halo-padded for the LNCC moment kernel
+        const long long nq = set_q_layout(d, prm.win, prm.loss);
+        if (nq > (1LL << 31) - 1)
+            return fail(LM_EINVAL, "pair %d is too large for the padded "
+                                   "fixed-point layout", i);
         if ((rc = c->dalloc(&d.u1, 3 * V * f4)) ||
             (rc = c->dalloc(&d.g0, 3 * V * f4)) ||
             (rc = c->dalloc(&d.g1, 3 * V * f4)) ||
             (rc = c->dalloc(&d.graw, graw_floats(d.g) * f4)) ||
-            (rc = c->dalloc(&d.jq, V * sizeof(int))) ||
+            (rc = c->dalloc(&d.jq, (size_t)nq * sizeof(int))) ||
             (rc = c->dalloc(&d.dj, 3 * V * f4)) ||
-            (rc = c->dalloc(&d.fq, V * sizeof(int))) ||
+            (rc = c->dalloc(&d.fq, (size_t)nq * sizeof(int))) ||
             (rc = c->dalloc(&d.fsum, V * sizeof(int))) ||
             (rc = c->dalloc(&d.fvar, V * f4)))
             return rc;
@@ -428,6 +435,7 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
                        (rc = c->dalloc(&d.wtmpB, 3 * V * f4))))
             return rc;
         d.tileH = nullptr;
+        d.flags = flags + i;
         d.st = st + i;
         d.qs = qs + i;
         d.target = std::numeric_limits<double>::quiet_NaN();
@@ -457,6 +465,7 @@ int core_create(std::unique_ptr<Core>& out, int npairs,
         return fail(LM_ENOMEM, "pinned host allocation failed");
     }
     LM_CK(cudaMemsetAsync(st, 0, npairs * sizeof(DevState), c->stream));
+    LM_CK(cudaMemsetAsync(flags, 0, npairs * sizeof(unsigned), c->stream));
     c->b.pd = c->dpd;
     c->b.npairs = npairs;
     c->b.dtype = c->dtype;

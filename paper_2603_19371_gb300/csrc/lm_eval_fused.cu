@@ -46,17 +46,6 @@ constexpr int NT = 512;       // threads per CTA (both kernels)
 constexpr int PLANE_X = 32;   // E1 moment plane / E2 output tile width
 constexpr int PLANE_Y = 16;   // and height
 
-// Contiguous share of the (column, slice) work of CTA b out of n: the CTA
-// walks segments [col, z0, z1) covering work units [lo, hi).
-struct Share {
-    long long lo, hi;
-};
-__device__ __forceinline__ Share share_of(int b, int n, long long total) {
-    Share s;
-    s.lo = total * b / n;
-    s.hi = total * (b + 1) / n;
-    return s;
-}
 
 // ----------------------------------------------------------------------
 // J pass: per voxel J = M(p + u(p)) and dJ/du (trilinear, Section 2.1), J
@@ -103,467 +92,6 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Sum of v[L .. L + N) as a balanced tree (depth ceil(log2 N) instead of
-// N - 1 dependent adds); N and L are compile-time, so v stays in registers.
-template <int L, int N, typename T>
-__device__ __forceinline__ T tree_sum(const T* v) {
-    if constexpr (N == 1)
-        return v[L];
-    else
-        return tree_sum<L, N / 2, T>(v) + tree_sum<L + N / 2, N - N / 2, T>(v);
-}
-
-// ----------------------------------------------------------------------
-// E1
-// ----------------------------------------------------------------------
-// The five stages run as a software pipeline over the z-slices: in round t
-// the CTA stores the gather plane of slice t + 1, takes the x sums of slice
-// t, the y sums, exact z running sums and coefficients of slice t - 1, the
-// x box of the coefficients of slice t - 2 and the output (y and z boxes,
-// dL/dJ) of slice t - 3, with one barrier per round.  Every stage boundary
-// has a double buffer, so the stages of one round touch different buffers
-// and each warp carries independent work of several stages.
-template <int W>
-struct E1Cfg {
-    static constexpr int K = 2 * W + 1;
-    static constexpr int SX = PLANE_X, SY = PLANE_Y;   // moment plane
-    static constexpr int TX = SX - 2 * W, TY = SY - 2 * W;  // output tile
-    static constexpr int GX = SX + 2 * W, GY = SY + 2 * W;  // gather plane
-    static constexpr int GXP = (GX + 3) / 4 * 4;            // padded stride
-    static constexpr int NXU = GY * (SX / 2);   // x-pass units (2 outputs)
-    // box-2 x units: four outputs each when the tile width allows
-    static constexpr int XW = TX % 4 == 0 ? 4 : 2;
-    static constexpr int NX2U = 3 * SY * (TX / XW);
-    static constexpr int KD = 16;   // delay ring (>= 2W + 5 slices of skew)
-    // shared memory (bytes), 16-byte aligned sections; [2] = double buffer
-    static constexpr int GP = GY * GXP, XP = GY * SX, AP = 3 * SY * SX,
-                         XQ = 3 * SY * TX, OP = TY * TX;
-    static constexpr int B_GQ = 2 * 2 * GP * 4;       // F', J' gather planes
-    static constexpr int B_X32 = 2 * XP * 4;          // x-sums of J'
-    static constexpr int B_X64 = 2 * 2 * XP * 8;      // of J'J', F'J'
-    static constexpr int B_ZR32 = K * NT * 4;         // z ring of y-sums
-    static constexpr int B_ZR64 = K * 2 * NT * 8;
-    static constexpr int B_AB = 2 * AP * 4;           // (a, b, c)
-    static constexpr int B_AX = 2 * XQ * 4;           // their x box
-    static constexpr int B_DL = KD * 2 * OP * 4;      // F', J' at the outputs
-    static constexpr int bytes =
-        B_GQ + B_X32 + B_X64 + B_ZR32 + B_ZR64 + B_AB + B_AX + B_DL;
-};
-
-template <int W>
-__global__ void __launch_bounds__(NT, 1)
-    k_e1(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
-         LnccConsts c, long long* __restrict__ loss_part) {
-    using C = E1Cfg<W>;
-    constexpr int K = C::K, SX = C::SX, SY = C::SY, TX = C::TX, TY = C::TY;
-    constexpr int GX = C::GX, GY = C::GY, GXP = C::GXP, KD = C::KD;
-    constexpr int GP = C::GP, XP = C::XP, AP = C::AP, XQ = C::XQ, OP = C::OP;
-    constexpr int NGS = (GX * GY + NT - 1) / NT;      // gather slots / thread
-    constexpr int NX2S = (C::NX2U + NT - 1) / NT;     // x-box-2 slots
-    static_assert(C::NXU <= NT, "one x-pass unit per thread");
-    static_assert(KD >= 2 * W + 5 && (KD & (KD - 1)) == 0, "delay ring");
-    extern __shared__ __align__(16) unsigned char smem[];
-    int* Gq = (int*)smem;                                   // [2][F, J][GP]
-    int* XJ = (int*)(smem + C::B_GQ);                       // [2][XP]
-    long long* X64 = (long long*)(smem + C::B_GQ + C::B_X32);   // [2][JJ, FJ][XP]
-    int* ZR32 = (int*)(smem + C::B_GQ + C::B_X32 + C::B_X64);
-    long long* ZR64 =
-        (long long*)(smem + C::B_GQ + C::B_X32 + C::B_X64 + C::B_ZR32);
-    float* Ab = (float*)(smem + C::B_GQ + C::B_X32 + C::B_X64 + C::B_ZR32 +
-                         C::B_ZR64);                         // [2][AP]
-    float* Ax = Ab + 2 * AP;                                 // [2][XQ]
-    float* DL = Ax + 2 * XQ;                                 // [KD][F', J'][OP]
-    __shared__ long long red[NT / 32];
-
-    const PairDesc& P = pd[pair_of_block<1>(pd, npairs, blockIdx.x)];
-    if (trial_skip(P, mode, attempt)) return;
-    const Geom g = P.g;
-    const int* __restrict__ fqv = P.fq;
-    const int* __restrict__ fsv = P.fsum;
-    const float* __restrict__ fbv = P.fvar;
-    const int* __restrict__ jqv = P.jq;
-    const float* __restrict__ djv = P.dj;
-    float* __restrict__ graw = P.graw;
-    const int gpw = P.gp_w;                                 // g_raw row pitch
-    const long long gcs = (long long)g.nz * g.ny * gpw;     // component stride
-    const QScale* __restrict__ qs = P.qs;
-    const float inv_V = (float)(1.0 / (double)g.V);
-    const int tid = threadIdx.x;
-    const int sxy = g.nx * g.ny;
-    const float sh = qs->shift, Q = qs->Q, iQ = qs->invQ;
-    const int qpad = __float2int_rn(-sh * Q);
-    const long long k3 = (long long)K * K * K;
-    // exact moment differences are k^6 Q^2 times the moments
-    const float mscale = c.inv_k3 * c.inv_k3 * iQ * iQ;
-    const float m1scale = c.inv_k3 * iQ;
-
-    // fixed per-thread work: gather slots (plane point gx | gy << 16, smem
-    // index, output point or -1), x-pass unit, moment point, x-box-2 slots
-    // and output point
-    int g_xy[NGS], g_sm[NGS], g_o[NGS];
-#pragma unroll
-    for (int k = 0; k < NGS; ++k) {
-        int idx = tid + k * NT;
-        int gy = idx / GX, gx = idx - gy * GX;
-        g_xy[k] = gx | (gy << 16);
-        g_sm[k] = idx < GX * GY ? gy * GXP + gx : -1;
-        int ox_ = gx - 2 * W, oy_ = gy - 2 * W;
-        g_o[k] = (g_sm[k] >= 0 && ox_ >= 0 && ox_ < TX && oy_ >= 0 && oy_ < TY)
-                     ? oy_ * TX + ox_
-                     : -1;
-    }
-    const bool has_xu = tid < C::NXU;
-    const int xu_gy = tid / (SX / 2), xu_p = tid - xu_gy * (SX / 2);
-    const int sx = tid & (SX - 1), sy = tid / SX;
-    int x2_row[NX2S], x2_p[NX2S];
-#pragma unroll
-    for (int k = 0; k < NX2S; ++k) {
-        int uidx = tid + k * NT;
-        x2_row[k] = uidx < C::NX2U ? uidx / (TX / C::XW) : -1;
-        x2_p[k] = uidx - (uidx / (TX / C::XW)) * (TX / C::XW);
-    }
-    const bool has_o = tid < TX * TY;
-    const int ox = has_o ? tid % TX : 0, oy = has_o ? tid / TX : 0;
-
-    long long lacc = 0;   // loss terms in fixed point LOSS_Q (exact sum)
-    bool bad = false;
-    const int e1_cx = P.e1_cx;
-    const long long total = (long long)P.e1_cx * P.e1_cy * g.nz;
-    const Share sh_ = share_of(blockIdx.x - P.e1_cta0, P.e1_ncta, total);
-    long long w0 = sh_.lo;
-    while (w0 < sh_.hi) {
-        const long long col = w0 / g.nz;
-        const int z0 = (int)(w0 - col * g.nz);
-        const long long zl = z0 + (sh_.hi - w0);
-        const int z1 = zl < g.nz ? (int)zl : g.nz;
-        w0 += z1 - z0;
-        const int x0 = (int)(col % e1_cx) * TX;
-        const int y0 = (int)(col / e1_cx) * TY;
-        // in-plane offsets of the gather slots (-1: outside the volume)
-        int g_off[NGS];
-#pragma unroll
-        for (int k = 0; k < NGS; ++k) {
-            int x = x0 - 2 * W + (g_xy[k] & 0xffff), y = y0 - 2 * W + (g_xy[k] >> 16);
-            g_off[k] = (g_sm[k] >= 0 && x >= 0 && x < g.nx && y >= 0 &&
-                        y < g.ny)
-                           ? y * g.nx + x
-                           : -1;
-        }
-        const bool s_in = x0 - W + sx < g.nx && y0 - W + sy < g.ny &&
-                          x0 - W + sx >= 0 && y0 - W + sy >= 0;
-        const bool s_out = sx >= W && sx < W + TX && sy >= W && sy < W + TY;
-        const int s_off = (y0 - W + sy) * g.nx + x0 - W + sx;
-        const bool o_in = has_o && x0 + ox < g.nx && y0 + oy < g.ny;
-        const int o_off = (y0 + oy) * g.nx + x0 + ox;
-
-        // ring and running sums restart for every segment
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            ZR32[k * NT + tid] = 0;
-            ZR64[(k * 2 + 0) * NT + tid] = 0;
-            ZR64[(k * 2 + 1) * NT + tid] = 0;
-        }
-        int runJ = 0;
-        long long runJJ = 0, runFJ = 0;
-        float r2[3][K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) r2[0][k] = r2[1][k] = r2[2][k] = 0.f;
-        const int s_begin = z0 - 2 * W, s_end = z1 + 2 * W;
-        const int nsl = s_end - s_begin;
-        // loaded one round ahead: the J' and F' of the next gather plane,
-        // S_F and B of the next moment slice, dJ/du of the next output slice
-        int jqk[NGS], fqk[NGS];
-        auto load_plane = [&](int sp) {
-            const bool zin_ = sp >= 0 && sp < g.nz;
-#pragma unroll
-            for (int k = 0; k < NGS; ++k) {
-                const int i = (zin_ && g_off[k] >= 0) ? sp * sxy + g_off[k] : -1;
-                jqk[k] = i >= 0 ? __ldg(jqv + i) : qpad;
-                fqk[k] = i >= 0 ? __ldg(fqv + i) : qpad;
-            }
-        };
-        // the loaded plane into gather buffer gf and delay-ring slot dl
-        auto store_plane = [&](int* gf, float* dl) {
-#pragma unroll
-            for (int k = 0; k < NGS; ++k) {
-                if (g_sm[k] < 0) continue;
-                int fq = fqk[k], jq = jqk[k];
-                if (fq == FQ_BAD) {
-                    bad = true;
-                    fq = qpad;
-                }
-                if (jq == JQ_BAD) {
-                    bad = true;
-                    jq = qpad;
-                }
-                gf[g_sm[k]] = fq;
-                gf[GP + g_sm[k]] = jq;
-                if (g_o[k] >= 0) {
-                    dl[g_o[k]] = (float)fq * iQ;
-                    dl[OP + g_o[k]] = (float)jq * iQ;
-                }
-            }
-        };
-        int mSF = 0;
-        float mB = 0.f;
-        auto load_mom = [&](int cz_) {
-            mSF = 0;
-            mB = 0.f;
-            if (s_in && cz_ >= 0 && cz_ < g.nz) {
-                mSF = __ldg(fsv + cz_ * sxy + s_off);
-                mB = __ldg(fbv + cz_ * sxy + s_off);
-            }
-        };
-        float odj[3] = {0.f, 0.f, 0.f};
-        auto load_dj = [&](int r) {
-            if (o_in && r >= z0 && r < z1) {
-                const int gi = r * sxy + o_off;
-                odj[0] = __ldg(djv + gi);
-                odj[1] = __ldg(djv + g.V + gi);
-                odj[2] = __ldg(djv + 2 * g.V + gi);
-            }
-        };
-        // double buffers as (this round's, the other) pointer pairs, swapped
-        // every round: gather planes (x pass reads, store writes), x sums
-        // (x pass writes, y pass reads), coefficients (y pass writes, x box
-        // reads), their x box (x box writes, output reads)
-        int* gq_x = Gq;
-        int* gq_s = Gq + 2 * GP;
-        int* xj_w = XJ;
-        int* xj_r = XJ + XP;
-        long long* x64_w = X64;
-        long long* x64_r = X64 + 2 * XP;
-        float* ab_w = Ab;
-        float* ab_r = Ab + AP;
-        float* ax_w = Ax;
-        float* ax_r = Ax + XQ;
-        // prologue: plane 0 stored, plane 1 in flight
-        load_plane(s_begin);
-        store_plane(gq_x, DL);
-        if (nsl > 1) load_plane(s_begin + 1);
-        __syncthreads();
-        const int nrounds = nsl + 3;
-        for (int base = 0; base < nrounds; base += K) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const int t = base + j;
-                if (t >= nrounds) break;
-                // this round's inputs, loaded last round
-                const int cSF = mSF;
-                const float cB = mB;
-                const float dj0 = odj[0], dj1 = odj[1], dj2 = odj[2];
-                // (G) plane t + 1 into its buffer; plane t + 2 requested
-                if (t + 1 < nsl) {
-                    store_plane(gq_s, DL + ((t + 1) & (KD - 1)) * 2 * OP);
-                    if (t + 2 < nsl) load_plane(s_begin + t + 2);
-                }
-                load_mom(s_begin + t - W);          // moment slice of round t+1
-                load_dj(s_begin + t - 2 - 2 * W);   // output slice of round t+1
-                // (X) window sums along x of slice t, two outputs per unit
-                if (t < nsl && has_xu) {
-                    // K + 1 values per row, read as 8-byte pairs
-                    const int2* rf = (const int2*)(gq_x + xu_gy * GXP + 2 * xu_p);
-                    const int2* rj = (const int2*)(gq_x + GP + xu_gy * GXP + 2 * xu_p);
-                    int vf[K + 1], vj[K + 1];
-#pragma unroll
-                    for (int o = 0; o < (K + 1) / 2; ++o) {
-                        const int2 a = rf[o], b2 = rj[o];
-                        vf[2 * o] = a.x;
-                        vf[2 * o + 1] = a.y;
-                        vj[2 * o] = b2.x;
-                        vj[2 * o + 1] = b2.y;
-                    }
-                    int sj = 0;
-                    long long sjj = 0, sfj = 0;
-#pragma unroll
-                    for (int o = 0; o < K; ++o) {
-                        sj += vj[o];
-                        sjj += (long long)vj[o] * vj[o];
-                        sfj += (long long)vf[o] * vj[o];
-                    }
-                    const int o1 = xu_gy * SX + 2 * xu_p;
-                    const int sj1 = sj + vj[K] - vj[0];
-                    const long long sjj1 =
-                        sjj + (long long)vj[K] * vj[K] - (long long)vj[0] * vj[0];
-                    const long long sfj1 =
-                        sfj + (long long)vf[K] * vj[K] - (long long)vf[0] * vj[0];
-                    // the two outputs as one 8-byte and two 16-byte stores
-                    *(int2*)(xj_w + o1) = make_int2(sj, sj1);
-                    *(longlong2*)(x64_w + o1) = make_longlong2(sjj, sjj1);
-                    *(longlong2*)(x64_w + XP + o1) = make_longlong2(sfj, sfj1);
-                }
-                // (Y) y sums of slice t - 1, the z running sums (exact) and,
-                //     once K slices are in, the coefficients at its moment
-                //     slice
-                if (t >= 1 && t - 1 < nsl) {
-                    const int ty = t - 1;
-                    const int* xj = xj_r;
-                    const long long* xjj = x64_r;
-                    int vj[K];
-                    long long vjj[K], vfj[K];
-#pragma unroll
-                    for (int o = 0; o < K; ++o) {
-                        const int a = (sy + o) * SX + sx;
-                        vj[o] = xj[a];
-                        vjj[o] = xjj[a];
-                        vfj[o] = xjj[XP + a];
-                    }
-                    const int yj = tree_sum<0, K>(vj);
-                    const long long yjj = tree_sum<0, K>(vjj);
-                    const long long yfj = tree_sum<0, K>(vfj);
-                    const int slot = (j + K - 1) % K;   // ring slot of slice t - 1
-                    int* zr = ZR32 + slot * NT + tid;
-                    long long* zr64 = ZR64 + slot * 2 * NT + tid;
-                    runJ += yj - zr[0];
-                    runJJ += yjj - zr64[0];
-                    runFJ += yfj - zr64[NT];
-                    zr[0] = yj;
-                    zr64[0] = yjj;
-                    zr64[NT] = yfj;
-                    if (ty >= 2 * W) {
-                        const int cz = s_begin + ty - W;
-                        float av = 0.f, bv = 0.f, cv = 0.f;
-                        if (s_in && cz >= 0 && cz < g.nz) {
-                            long long Ai = k3 * runFJ - (long long)cSF * runJ;
-                            long long Ci = k3 * runJJ - (long long)runJ * runJ;
-                            float A = i64_to_f32(Ai) * mscale;
-                            float B = cB;
-                            float Cm = i64_to_f32(Ci) * mscale;
-                            float mF = (float)cSF * m1scale;
-                            float mJ = (float)runJ * m1scale;
-                            float BC = __fmul_rn(B, Cm), AA = __fmul_rn(A, A);
-                            float N = AA + c.eps_nr;
-                            float D = BC + c.eps_dr;
-                            // D >= eps_dr > 0: the approximate reciprocal
-                            // (about 1 ulp) is safe and far cheaper than an
-                            // IEEE division
-                            float rD = __fdividef(1.f, D);
-                            av = 2.f * A * rD;
-                            bv = -N * B * rD * rD;
-                            cv = -av * mF - 2.f * bv * mJ;
-                            if (s_out && cz >= z0 && cz < z1)
-                                lacc += loss_fixed(
-                                    ((BC - AA) + (c.eps_dr - c.eps_nr)) * rD * LOSS_Q,
-                                    &bad);
-                        }
-                        float* ab = ab_w + sy * SX + sx;
-                        ab[0] = av;
-                        ab[SY * SX] = bv;
-                        ab[2 * SY * SX] = cv;
-                    }
-                }
-                // (B) box of (a, b, c) of slice t - 2 along x: XW outputs per
-                //     unit (the later ones slide the window by one)
-                if (t >= 2 && t - 2 < nsl && t - 2 >= 2 * W) {
-#pragma unroll
-                    for (int k = 0; k < NX2S; ++k) {
-                        if (x2_row[k] < 0) continue;
-                        constexpr int XW = C::XW;
-                        const float* r = ab_r + x2_row[k] * SX + XW * x2_p[k];
-                        // K + XW - 1 values: 16-byte reads, an 8-byte tail
-                        constexpr int NV = K + XW - 1;
-                        float v[NV];
-                        if constexpr (XW == 4) {
-#pragma unroll
-                            for (int o = 0; o + 4 <= NV; o += 4) {
-                                const float4 a = *(const float4*)(r + o);
-                                v[o] = a.x;
-                                v[o + 1] = a.y;
-                                v[o + 2] = a.z;
-                                v[o + 3] = a.w;
-                            }
-                            if constexpr (NV % 4 == 2) {
-                                const float2 a = *(const float2*)(r + NV - 2);
-                                v[NV - 2] = a.x;
-                                v[NV - 1] = a.y;
-                            }
-                        } else {
-#pragma unroll
-                            for (int o = 0; o < NV; o += 2) {
-                                const float2 a = *(const float2*)(r + o);
-                                v[o] = a.x;
-                                v[o + 1] = a.y;
-                            }
-                        }
-                        const float s0 = tree_sum<0, K>(v);
-                        const float s1 = (s0 - v[0]) + v[K];
-                        float* dst = ax_w + x2_row[k] * TX + XW * x2_p[k];
-                        if constexpr (XW == 4) {
-                            const float s2 = (s1 - v[1]) + v[K + 1];
-                            const float s3 = (s2 - v[2]) + v[K + 2];
-                            *(float4*)dst = make_float4(s0, s1, s2, s3);
-                        } else {
-                            *(float2*)dst = make_float2(s0, s1);
-                        }
-                    }
-                }
-                // (O) slice t - 3: box along y into the register ring, along
-                //     z, dL/dJ at the output slice two windows back
-                if (has_o && t >= 3 && t - 3 < nsl && t - 3 >= 2 * W) {
-                    const int to = t - 3;
-                    const int oslot = (j + 2 * K - 3) % K;   // ring slot of slice t-3
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        float v[K];
-#pragma unroll
-                        for (int o = 0; o < K; ++o)
-                            v[o] = ax_r[(q * SY + oy + o) * TX + ox];
-                        r2[q][oslot] = tree_sum<0, K>(v);
-                    }
-                    const int ro = s_begin + to - 2 * W;
-                    if (to >= 4 * W && o_in) {
-                        float b3[3];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            float v[K];
-#pragma unroll
-                            for (int i2 = 0; i2 < K; ++i2)
-                                v[i2] = r2[q][(oslot + 1 + i2) % K];
-                            b3[q] = tree_sum<0, K>(v);
-                        }
-                        // F', J' of the output slice (local to - 2W)
-                        const float* dl = DL + ((to - 2 * W) & (KD - 1)) * 2 * OP + tid;
-                        const float dLdJ =
-                            -inv_V * ((dl[0] * b3[0] + 2.f * dl[OP] * b3[1] + b3[2]) *
-                                      c.inv_k3);
-                        const long long gi = (long long)(ro * g.ny + y0 + oy) * gpw +
-                                             x0 + ox;
-                        graw[gi] = dLdJ * dj0;
-                        graw[gcs + gi] = dLdJ * dj1;
-                        graw[2 * gcs + gi] = dLdJ * dj2;
-                    }
-                }
-                // this round's write buffers are next round's read buffers
-                {
-                    int* a = gq_x;
-                    gq_x = gq_s;
-                    gq_s = a;
-                    int* b = xj_w;
-                    xj_w = xj_r;
-                    xj_r = b;
-                    long long* c2 = x64_w;
-                    x64_w = x64_r;
-                    x64_r = c2;
-                    float* d = ab_w;
-                    ab_w = ab_r;
-                    ab_r = d;
-                    float* e = ax_w;
-                    ax_w = ax_r;
-                    ax_r = e;
-                }
-                __syncthreads();
-            }
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, o);
-    if ((tid & 31) == 0) red[tid >> 5] = lacc;
-    const int any_bad = __syncthreads_or(bad);
-    if (tid == 0) {
-        long long v = 0;
-        for (int w = 0; w < NT / 32; ++w) v += red[w];
-        loss_part[blockIdx.x] = any_bad ? LOSS_BAD : v;
-    }
-}
 
 // ----------------------------------------------------------------------
 // Pointwise evaluation for MSE (Section 2.2) and Demons (Section 2.3), in
@@ -1040,6 +568,25 @@ __device__ __forceinline__ MomTmp mom_tmp(float* base, long long V) {
     return t;
 }
 
+// Fills the halo-padded jq and fq of each pair with the fixed point of 0
+// (the interior is written later: fq by k_fmom_x, jq by every resampling)
+// and clears the pair's non-finite flags.  Grid (blocks per pair, pairs).
+__global__ void k_qfill(const PairDesc* __restrict__ pd) {
+    const PairDesc& P = pd[blockIdx.y];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *P.flags = 0u;
+    if (!P.qw) return;
+    const int qpad = __float2int_rn(-P.qs->shift * P.qs->Q);
+    const long long n = (long long)P.qw * P.qh * (P.g.nz + 2 * P.qz);
+    const int4 v = make_int4(qpad, qpad, qpad, qpad);
+    int4* jq4 = (int4*)P.jq;
+    int4* fq4 = (int4*)P.fq;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+         i < n / 4; i += (long long)gridDim.x * blockDim.x) {
+        jq4[i] = v;
+        fq4[i] = v;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_fmom_x(const PairDesc* __restrict__ pd, int npairs, int W) {
@@ -1060,7 +607,11 @@ __global__ void __launch_bounds__(256)
             const float f = ld_img(F, i + d);
             const bool fin = fabsf(f) <= 3.0e38f;
             if (fin) q = min(max(__float2int_rn((f - sh) * Q), -qlim), qlim);
-            if (d == 0) P.fq[i] = fin ? q : FQ_BAD;
+            if (d == 0) {
+                const int r = i / g.nx;
+                P.fq[qidx(P, x, r % g.ny, r / g.ny)] = fin ? q : FQ_BAD;
+                if (!fin) atomicOr(P.flags, QFLAG_FBAD);
+            }
         }
         s += q;
         ss += (long long)q * q;
@@ -1112,27 +663,11 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <int W>
-int launch_e1(const Batch& b, int mode, int attempt, cudaStream_t s) {
-    k_e1<W><<<b.plan.e1_ctas, NT, E1Cfg<W>::bytes, s>>>(
-        b.pd, b.npairs, mode, attempt, b.c, b.part.loss);
-    return 1;
-}
-
 template <int R, typename T>
 int launch_e2(const Batch& b, int mode, int attempt, cudaStream_t s) {
     k_e2<R, T><<<b.plan.e2_ctas, NT2, E2Cfg<R>::bytes, s>>>(
         b.pd, b.npairs, mode, attempt, b.c.gtaps, b.part.g2max);
     return 1;
-}
-
-int launch_e1_w(const Batch& b, int mode, int attempt, cudaStream_t s) {
-    switch ((b.c.win - 1) / 2) {
-        case 1: return launch_e1<1>(b, mode, attempt, s);
-        case 2: return launch_e1<2>(b, mode, attempt, s);
-        case 3: return launch_e1<3>(b, mode, attempt, s);
-        default: return launch_e1<4>(b, mode, attempt, s);
-    }
 }
 
 template <typename T>
@@ -1148,12 +683,6 @@ int launch_e2_r(const Batch& b, int mode, int attempt, cudaStream_t s) {
     }
 }
 
-template <int W>
-cudaError_t attr_e1() {
-    return cudaFuncSetAttribute(k_e1<W>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                E1Cfg<W>::bytes);
-}
 template <int R, typename T>
 cudaError_t attr_e2() {
     return cudaFuncSetAttribute(k_e2<R, T>,
@@ -1164,10 +693,6 @@ cudaError_t attr_e2() {
 template <typename T>
 cudaError_t attrs_all() {
     cudaError_t e = cudaSuccess, r;
-    if ((r = attr_e1<1>()) != cudaSuccess) e = r;
-    if ((r = attr_e1<2>()) != cudaSuccess) e = r;
-    if ((r = attr_e1<3>()) != cudaSuccess) e = r;
-    if ((r = attr_e1<4>()) != cudaSuccess) e = r;
     if ((r = attr_e2<0, T>()) != cudaSuccess) e = r;
     if ((r = attr_e2<1, T>()) != cudaSuccess) e = r;
     if ((r = attr_e2<2, T>()) != cudaSuccess) e = r;
@@ -1214,8 +739,7 @@ static void split_ctas(const long long* work, int npairs, long long target,
 BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
                      int e1_waves, int e2_waves) {
     BatchPlan bp{};
-    const int W = (win - 1) / 2;
-    const int tx1 = PLANE_X - 2 * W, ty1 = PLANE_Y - 2 * W;
+    const int tx1 = E1_OX, ty1 = E1_OY;
     std::vector<long long> w1(npairs), w2(npairs);
     std::vector<int> c0(npairs), n(npairs);
     for (int p = 0; p < npairs; ++p) {
@@ -1227,7 +751,7 @@ BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
         pd[p].e2_cy = (int)ceil_div(g.ny, PLANE_Y);
         w2[p] = (long long)pd[p].e2_cx * pd[p].e2_cy * g.nz;
     }
-    if (e1_waves < 1) e1_waves = npairs == 1 ? 1 : 4;
+    if (e1_waves < 1) e1_waves = npairs == 1 ? 2 : 4;
     if (e2_waves < 1) e2_waves = npairs == 1 ? 2 : 8;
     const long long t1 = (long long)e1_waves * num_sms;
     const long long t2 = (long long)e2_waves * num_sms;
@@ -1283,6 +807,19 @@ int plan_tiles(PairDesc* pd, int npairs, int k) {
     return blk;
 }
 
+long long set_q_layout(PairDesc& d, int win, int loss) {
+    if (loss != LM_LOSS_LNCC) {
+        d.qw = d.qh = d.qx = d.qz = 0;
+        return d.g.V;
+    }
+    const int W = (win - 1) / 2;
+    d.qx = 2 * W;
+    d.qz = 2 * W + 1;
+    d.qw = (int)ceil_div(d.g.nx, E1_OX) * E1_OX + 4 * W;
+    d.qh = (int)ceil_div(d.g.ny, E1_OY) * E1_OY + 4 * W;
+    return (long long)d.qw * d.qh * (d.g.nz + 2 * d.qz);
+}
+
 int graw_pitch(int nx) { return (nx + 3) / 4 * 4; }
 
 long long graw_floats(const Geom& g) {
@@ -1328,7 +865,9 @@ cudaError_t fused_setup() {
     cudaError_t e = attrs_all<float>();
     cudaError_t e2 = attrs_all<__nv_bfloat16>();
     cudaError_t e3 = mi_setup();
-    return e != cudaSuccess ? e : e2 != cudaSuccess ? e2 : e3;
+    cudaError_t e4 = lncc_setup();
+    return e != cudaSuccess ? e : e2 != cudaSuccess ? e2
+                                 : e3 != cudaSuccess ? e3 : e4;
 }
 
 int batch_prepare(const Batch& b, cudaStream_t s) {
@@ -1340,13 +879,14 @@ int batch_prepare(const Batch& b, cudaStream_t s) {
         k_minmax<float><<<grid, NT, 0, s>>>(b.pd, b.mm_part);
     k_qscale<<<b.npairs, 32, 0, s>>>(b.pd, b.mm_part, b.plan.mm_ctas,
                                      quant_bits(b.c.win));
+    k_qfill<<<grid, 256, 0, s>>>(b.pd);
     if (b.dtype == LM_BF16)
         k_fmom_x<__nv_bfloat16><<<b.plan.ln_blocks, 256, 0, s>>>(b.pd, b.npairs, W);
     else
         k_fmom_x<float><<<b.plan.ln_blocks, 256, 0, s>>>(b.pd, b.npairs, W);
     k_fmom_yz<1><<<b.plan.ln_blocks, 256, 0, s>>>(b.pd, b.npairs, W, b.c.inv_k3);
     k_fmom_yz<2><<<b.plan.ln_blocks, 256, 0, s>>>(b.pd, b.npairs, W, b.c.inv_k3);
-    return 5;
+    return 6;
 }
 
 // The loss kernel of pass 1: E1 for LNCC, the pointwise kernel otherwise.
@@ -1362,7 +902,7 @@ static int launch_loss(const Batch& b, int mode, int attempt, cudaStream_t s) {
         return 1;
     }
     if (b.loss == LM_LOSS_MI) return launch_mi(b, mode, attempt, s);
-    return launch_e1_w(b, mode, attempt, s);
+    return launch_lncc(b, mode, attempt, s);
 }
 
 int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,

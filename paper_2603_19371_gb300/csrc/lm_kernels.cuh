@@ -64,7 +64,30 @@ struct PairDesc {
     // injected fault (LM_FAULT_TIMEOUT, host-side): E2 first waits on a
     // barrier that no copy completes, so that its bounded wait runs out
     int fault_wait;
+    // Layout of jq and fq.  qw = 0: plain [nz][ny][nx].  For the LNCC loss
+    // a halo-padded volume [nz + 2 qz][qh][qw] whose halo holds the fixed
+    // point of 0 (the zero padding of the window sums): voxel (x, y, z)
+    // sits at ((z + qz) qh + y + qx) qw + x + qx, with qx = 2W, qz = 2W + 1,
+    // qw = 32 ceil(nx / 32) + 4W and qh = 32 ceil(ny / 32) + 4W, so that the
+    // moment kernel reads every gather row of every tile as aligned 16-byte
+    // vectors without bounds tests.
+    int qw, qh, qx, qz;
+    // QFLAG_* bits of the pair: a non-finite J (set by the resampling
+    // writers, cleared by the decision kernel that reads it) or F (set by
+    // the preparation until the next one)
+    unsigned* flags;
 };
+enum { QFLAG_JBAD = 1u, QFLAG_FBAD = 2u };
+
+// Index of voxel (x, y, z) in the pair's jq / fq layout.
+__host__ __device__ __forceinline__ long long qidx(const PairDesc& P, int x,
+                                                  int y, int z) {
+    return P.qw ? ((long long)(z + P.qz) * P.qh + y + P.qx) * P.qw + x + P.qx
+                : ((long long)z * P.g.ny + y) * P.g.nx + x;
+}
+// Sets the jq / fq layout of a pair (halo-padded for the LNCC loss) and
+// returns the number of elements each of the two buffers needs.
+long long set_q_layout(PairDesc& d, int win, int loss);
 
 // Pointers of an evaluation, routed by mode.
 __device__ __forceinline__ const float* eval_u(const PairDesc& p, int mode) {
@@ -153,6 +176,34 @@ __device__ __forceinline__ long long loss_fixed(float v, bool* bad) {
            (long long)__float2int_rn(fmaf(-h, 0x1p31f, v));
 }
 
+// Contiguous share of the (column, slice) work of CTA b out of n: the CTA
+// walks segments [col, z0, z1) covering work units [lo, hi).
+struct Share {
+    long long lo, hi;
+};
+__device__ __forceinline__ Share share_of(int b, int n, long long total) {
+    Share s;
+    s.lo = total * b / n;
+    s.hi = total * (b + 1) / n;
+    return s;
+}
+
+// Sum of v[L .. L + N) as a balanced tree (depth ceil(log2 N) instead of
+// N - 1 dependent adds); N and L are compile-time, so v stays in registers.
+template <int L, int N, typename T>
+__device__ __forceinline__ T tree_sum(const T* v) {
+    if constexpr (N == 1)
+        return v[L];
+    else
+        return tree_sum<L, N / 2, T>(v) + tree_sum<L + N / 2, N - N / 2, T>(v);
+}
+
+// Output tile (x, y) of the LNCC moment kernel; a CTA marches along z over a
+// column of such tiles.  Two CTAs fit an SM for k <= 7, so one CTA's
+// barriers overlap the other's work.
+constexpr int E1_OX = 32, E1_OY = 16;
+constexpr int E1_THREADS = 256;
+
 struct Partials {
     long long* loss;  // one per E1 CTA, fixed point LOSS_Q (or LOSS_BAD)
     float* g2max;     // one per E2 CTA
@@ -232,6 +283,10 @@ int batch_prepare(const Batch& b, cudaStream_t s);
 // Eq. demons), both followed by E2.
 int batch_eval(const Batch& b, int mode, int attempt, cudaStream_t s,
                bool jpass = true);
+// The LNCC moment kernel (loss partials and g_raw) of pass 1 and its
+// shared-memory opt-in.
+int launch_lncc(const Batch& b, int mode, int attempt, cudaStream_t s);
+cudaError_t lncc_setup();
 // Pass 2: trial field (Eq. tile1, or Eq. tilen for tile > 1, + Eq.
 // compositive, optional smoothing).
 int batch_step(const Batch& b, int attempt, cudaStream_t s);

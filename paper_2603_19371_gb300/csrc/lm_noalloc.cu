@@ -21,24 +21,28 @@ namespace {
 
 // Scratch layout (bytes, each section 256-byte aligned):
 //   g_raw               3 x LM_NOALLOC_MAX_VOXELS floats (rows padded to 4)
-//   J (fixed point)     LM_NOALLOC_MAX_VOXELS int32
+//   J (fixed point)     MAX_Q int32 (the LNCC kernel's halo-padded layout)
 //   dJ/du               3 x LM_NOALLOC_MAX_VOXELS floats
-//   F fixed point, window sum (int32), variance (float): LM_NOALLOC_MAX_VOXELS each
+//   F fixed point       MAX_Q int32
+//   F window sum (int32), variance (float): LM_NOALLOC_MAX_VOXELS each
 //   loss partials       MAX_CTAS int64 (fixed point)
 //   |g|^2 partials      MAX_CTAS floats
 //   image range parts   MAX_CTAS float2
-//   QScale, EvalOut, the one-pair descriptor table
+//   QScale, EvalOut, the one-pair descriptor table, g_raw's tensor map,
+//   the pair's non-finite flags
 constexpr size_t MAX_CTAS = 1024;
+// J and F in fixed point take the LNCC kernel's halo-padded layout: room
+// for three times the voxel limit (a volume whose padded layout needs more
+// is refused)
+constexpr size_t MAX_Q = 3 * (size_t)LM_NOALLOC_MAX_VOXELS;
 constexpr size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 constexpr size_t OFF_GRAW = 0;
 constexpr size_t OFF_JQ =
     OFF_GRAW + align256(3 * (size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
-constexpr size_t OFF_DJ =
-    OFF_JQ + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(int));
+constexpr size_t OFF_DJ = OFF_JQ + align256(MAX_Q * sizeof(int));
 constexpr size_t OFF_FQ =
     OFF_DJ + align256(3 * (size_t)LM_NOALLOC_MAX_VOXELS * sizeof(float));
-constexpr size_t OFF_FSUM =
-    OFF_FQ + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(int));
+constexpr size_t OFF_FSUM = OFF_FQ + align256(MAX_Q * sizeof(int));
 constexpr size_t OFF_FVAR =
     OFF_FSUM + align256((size_t)LM_NOALLOC_MAX_VOXELS * sizeof(int));
 constexpr size_t OFF_LOSS =
@@ -49,7 +53,8 @@ constexpr size_t OFF_QS = OFF_MM + align256(MAX_CTAS * sizeof(float2));
 constexpr size_t OFF_OUT = OFF_QS + align256(sizeof(lmk::QScale));
 constexpr size_t OFF_PD = OFF_OUT + align256(sizeof(lmk::EvalOut));
 constexpr size_t OFF_TMAP = OFF_PD + align256(sizeof(lmk::PairDesc));
-constexpr size_t SCRATCH_BYTES = OFF_TMAP + 256;   // g_raw's tensor map
+constexpr size_t OFF_FLAGS = OFF_TMAP + 256;       // g_raw's tensor map
+constexpr size_t SCRATCH_BYTES = OFF_FLAGS + 256;  // the pair's flags
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
@@ -194,6 +199,12 @@ extern "C" int lm_eval_noalloc(const lm_volume* fixed, const lm_volume* moving,
     pd.u_in = u;
     pd.g_out = g_out;
     pd.graw = (float*)(base + OFF_GRAW);
+    if (lmk::set_q_layout(pd, prm.win, prm.loss) > (long long)MAX_Q)
+        return fail(LM_EINVAL,
+                    "volume exceeds the static scratch: its halo-padded "
+                    "fixed-point layout needs more than 3 LM_NOALLOC_MAX_VOXELS "
+                    "elements");
+    pd.flags = (unsigned*)(base + OFF_FLAGS);
     pd.jq = (int*)(base + OFF_JQ);
     pd.dj = (float*)(base + OFF_DJ);
     pd.fq = (int*)(base + OFF_FQ);

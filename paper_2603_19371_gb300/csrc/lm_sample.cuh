@@ -77,9 +77,11 @@ __device__ __forceinline__ void interp_grad(const float m[8], const float f[3],
 // Fixed-point value of a non-finite J (never a valid code).
 constexpr int JQ_BAD = (int)0x80000000;
 
-// J and dJ/du of voxel i from its corners: J in the moments' fixed point
-// (JQ_BAD if not finite) and dJ/du to dj (3 x V).
+// J and dJ/du of voxel (x, y, z) (linear index i) from its corners: J in
+// the moments' fixed point at the pair's jq layout (JQ_BAD, and the pair's
+// QFLAG_JBAD, if not finite) and dJ/du to dj (3 x V).
 __device__ __forceinline__ void store_resampled(const PairDesc& P, int i,
+                                                int x, int y, int z,
                                                 const float m[8],
                                                 const float f[3]) {
     float d[3];
@@ -87,9 +89,10 @@ __device__ __forceinline__ void store_resampled(const PairDesc& P, int i,
     interp_grad(m, f, d);
     const float sh = P.qs->shift, Q = P.qs->Q;
     const int qlim = P.qs->qlim;
-    P.jq[i] = (fabsf(J) <= 3.0e38f)
-                  ? min(max(__float2int_rn((J - sh) * Q), -qlim), qlim)
-                  : JQ_BAD;
+    const bool fin = fabsf(J) <= 3.0e38f;
+    if (!fin) atomicOr(P.flags, QFLAG_JBAD);
+    P.jq[qidx(P, x, y, z)] =
+        fin ? min(max(__float2int_rn((J - sh) * Q), -qlim), qlim) : JQ_BAD;
     P.dj[i] = d[0];
     P.dj[P.g.V + i] = d[1];
     P.dj[2 * P.g.V + i] = d[2];
@@ -102,7 +105,7 @@ __device__ __forceinline__ void resample_voxel(const PairDesc& P, const T* M,
                                                float d0, float d1, float d2) {
     float m[8], f[3];
     corners(M, P.g, x, y, z, d0, d1, d2, m, f);
-    store_resampled(P, i, m, f);
+    store_resampled(P, i, x, y, z, m, f);
 }
 
 }  // namespace lmk

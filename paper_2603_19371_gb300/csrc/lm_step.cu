@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
             if (RESAMPLE) {
                 float cm[8], cf[3];
                 corners((const T*)P.M, g, x, y, z, ut[0], ut[1], ut[2], cm, cf);
-                if (pi >= 0) store_resampled(P, pi, pm, pf);
+                if (pi >= 0) store_resampled(P, pi, x, y, z - 1, pm, pf);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) pm[k] = cm[k];
                 pf[0] = cf[0];
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
         }
         __syncthreads();
     }
-    if (RESAMPLE && pi >= 0) store_resampled(P, pi, pm, pf);
+    if (RESAMPLE && pi >= 0) store_resampled(P, pi, x, y, z1 - 1, pm, pf);
 }
 
 // 1-D Gaussian along an axis of a pair's 3-component field, edge-extended;
@@ -503,7 +503,10 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
         L = ((double)s / (double)LOSS_Q) / (double)P.g.V;
     }
     float gmax = sqrtf(m);
-    const bool nonfinite = nf || lbad || !isfinite(L) || !isfinite(gmax);
+    // a non-finite J of this evaluation (its flag is cleared here) or F
+    const unsigned fl = *P.flags;
+    if (fl & QFLAG_JBAD) *P.flags = fl & ~QFLAG_JBAD;
+    const bool nonfinite = nf || lbad || fl || !isfinite(L) || !isfinite(gmax);
     const bool bad = nonfinite || to;
     const int bits = (nonfinite ? STATUS_NONFINITE : 0) | (to ? STATUS_TIMEOUT : 0);
     if (mode == FIN_EXPLICIT) {
