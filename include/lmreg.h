@@ -317,17 +317,28 @@ LM_API int lm_batch_reset(lm_batch *b, float *const *u);
  * (host, npairs entries, may be NULL) receive each pair's last outcome. */
 LM_API int lm_batch_iterate(lm_batch *b, float *const *u, int n,
                             lm_step_info *infos);
-/* Autotuner of the batch's work split (the paper has no counterpart: it
- * serves batches of many pairs of uneven sizes).  The evaluation kernels
- * run a fixed number of CTA waves split among the pairs in proportion to
- * their voxels; this call times reps evaluations at u (device fields, as
- * for lm_batch_eval) for each candidate pair of wave counts (E1: 1, 2, 4,
- * 8; E2: 2, 4, 8, 16 CTAs per SM in total) and keeps the fastest for all
- * later calls (the captured iteration graph is rebuilt).  e1_waves,
- * e2_waves, ms_best (host, may be NULL) receive the choice and its time per
+/* Autotuner of the evaluation's tile shape and work split (the paper has
+ * no counterpart: it serves batches of many pairs of uneven sizes and
+ * volumes of any shape).  The LNCC moment kernel has two output tiles per
+ * CTA (LM_E1_TILE_32X16: 256 threads, two CTAs per SM; LM_E1_TILE_32X32:
+ * 512 threads, one per SM, k <= 7), and the evaluation kernels run a fixed
+ * number of CTA waves split among the pairs in proportion to their voxels.
+ * This call times reps evaluations at u (device fields, as for
+ * lm_batch_eval) for every candidate (tile; E1 waves 1, 2, 4, 8; E2 waves
+ * 2, 4, 8, 16 CTAs per SM in total) and keeps the fastest for all later
+ * calls (the captured iteration graph is rebuilt).  Tile and waves change
+ * the timing only: the loss is an exact integer sum and every gradient sum
+ * has the same order under every choice.  e1_tile, e1_waves, e2_waves,
+ * ms_best (host, may be NULL) receive the choice and its time per
  * evaluation.  Synchronises.  LM_EINVAL on NULL b / u or reps < 1. */
+#define LM_E1_TILE_32X16 0
+#define LM_E1_TILE_32X32 1
 LM_API int lm_batch_autotune(lm_batch *b, float *const *u, int reps,
-                             int *e1_waves, int *e2_waves, double *ms_best);
+                             int *e1_tile, int *e1_waves, int *e2_waves,
+                             double *ms_best);
+/* The same for a single-pair context, at its field u (device). */
+LM_API int lm_autotune(lm_ctx *ctx, const float *u, int reps, int *e1_tile,
+                       int *e1_waves, int *e2_waves, double *ms_best);
 
 /* Carry a displacement field between pyramid levels (Section 2.1), as
  * lm_register does between its levels: the level-b field at voxel p is the

@@ -1117,11 +1117,12 @@ extern "C" int lm_batch_iterate(lm_batch* b, float* const* u, int n,
 }
 
 namespace {
-// Re-split the evaluation kernels' CTAs with the given wave counts; the
-// captured iteration graph is dropped (its grids change).
-int core_replan(Core* c, int e1w, int e2w) {
+// Re-split the evaluation kernels' CTAs with the given wave counts and
+// moment-kernel tile; the captured iteration graph is dropped (its grids
+// change).
+int core_replan(Core* c, int e1w, int e2w, int tile) {
     BatchPlan plan = plan_batch(c->hpd.data(), c->npairs, c->p.win, c->num_sms,
-                                e1w, e2w);
+                                e1w, e2w, tile);
     if (plan.e1_ctas > c->e1_cap || plan.e2_ctas > c->e2_cap)
         return fail(LM_EINVAL, "plan exceeds the partial slots");
     c->b.plan = plan;
@@ -1131,13 +1132,13 @@ int core_replan(Core* c, int e1w, int e2w) {
     }
     return c->push_table();
 }
-}  // namespace
 
-extern "C" int lm_batch_autotune(lm_batch* b, float* const* u, int reps,
-                                 int* e1_waves, int* e2_waves, double* ms_best) {
-    if (!b || !u) return fail(LM_EINVAL, "NULL argument");
+// Times reps evaluations at u for every candidate (moment-kernel tile, E1
+// waves, E2 waves) and keeps the fastest plan.
+int core_autotune(Core* c, const float* const* u, int reps, int* e1_tile,
+                  int* e1_waves, int* e2_waves, double* ms_best) {
+    if (!u) return fail(LM_EINVAL, "NULL argument");
     if (reps < 1) return fail(LM_EINVAL, "reps must be >= 1");
-    Core* c = b->core.get();
     int rc;
     for (int i = 0; i < c->npairs; ++i)
         if (!is_device_ptr(u[i]))
@@ -1159,36 +1160,59 @@ extern "C" int lm_batch_autotune(lm_batch* b, float* const* u, int reps,
     LM_CK(cudaEventCreate(&e0));
     LM_CK(cudaEventCreate(&e1));
     double best = 1e300;
-    int b1 = 0, b2 = 0;
-    for (int w1 : kE1Waves)
-        for (int w2 : kE2Waves) {
-            if ((rc = core_replan(c, w1, w2)) != LM_OK) break;
-            batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);   // warm-up
-            LM_CK(cudaEventRecord(e0, c->stream));
-            for (int r = 0; r < reps; ++r)
-                batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);
-            LM_CK(cudaEventRecord(e1, c->stream));
-            LM_CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms / reps < best) {
-                best = ms / reps;
-                b1 = w1;
-                b2 = w2;
+    int bt = c->b.plan.e1_tile, b1 = 0, b2 = 0;
+    // the tile only matters to the LNCC moment kernel
+    const int ntiles = c->p.loss == LM_LOSS_LNCC ? E1_NTILES : 1;
+    for (int t = 0; t < ntiles && rc == LM_OK; ++t) {
+        if (!e1_tile_ok(t, c->p.win)) continue;
+        for (int w1 : kE1Waves)
+            for (int w2 : kE2Waves) {
+                if ((rc = core_replan(c, w1, w2, t)) != LM_OK) break;
+                batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);   // warm-up
+                LM_CK(cudaEventRecord(e0, c->stream));
+                for (int r = 0; r < reps; ++r)
+                    batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);
+                LM_CK(cudaEventRecord(e1, c->stream));
+                LM_CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms / reps < best) {
+                    best = ms / reps;
+                    bt = t;
+                    b1 = w1;
+                    b2 = w2;
+                }
             }
-        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LM_OK) return rc;
     // restore the evaluation pointers, keep the chosen plan
     c->hpd = save;
-    if ((rc = core_replan(c, b1, b2)) != LM_OK) return rc;
+    if ((rc = core_replan(c, b1, b2, bt)) != LM_OK) return rc;
     LM_CK(cudaStreamSynchronize(c->stream));
     LM_CK(cudaGetLastError());
+    if (e1_tile) *e1_tile = bt;
     if (e1_waves) *e1_waves = b1;
     if (e2_waves) *e2_waves = b2;
     if (ms_best) *ms_best = best;
     return LM_OK;
+}
+}  // namespace
+
+extern "C" int lm_batch_autotune(lm_batch* b, float* const* u, int reps,
+                                 int* e1_tile, int* e1_waves, int* e2_waves,
+                                 double* ms_best) {
+    if (!b) return fail(LM_EINVAL, "NULL argument");
+    return core_autotune(b->core.get(), u, reps, e1_tile, e1_waves, e2_waves,
+                         ms_best);
+}
+
+extern "C" int lm_autotune(lm_ctx* c, const float* u, int reps, int* e1_tile,
+                           int* e1_waves, int* e2_waves, double* ms_best) {
+    if (!c) return fail(LM_EINVAL, "NULL argument");
+    return core_autotune(c->core.get(), &u, reps, e1_tile, e1_waves, e2_waves,
+                         ms_best);
 }
 
 extern "C" int lm_field_resample(const float* src, int Da, int Ha, int Wa,

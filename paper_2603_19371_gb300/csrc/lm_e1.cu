@@ -41,12 +41,11 @@
 namespace lmk {
 namespace {
 
-constexpr int NT = E1_THREADS;
-
-template <int W>
+template <int W, int TILE>
 struct E1Z {
+    static constexpr int NT = e1_tile_threads(TILE);
     static constexpr int K = 2 * W + 1;
-    static constexpr int OX = E1_OX, OY = E1_OY;       // output tile
+    static constexpr int OX = E1_OX, OY = e1_tile_oy(TILE);   // output tile
     static constexpr int MX = OX + 2 * W, MY = OY + 2 * W;   // moment plane
     static constexpr int GX = OX + 4 * W, GY = OY + 4 * W;   // gather plane
     static constexpr int MXP = (MX + 3) / 4 * 4;       // padded row stride
@@ -56,8 +55,8 @@ struct E1Z {
     static constexpr int XW = MX % 4 == 0 ? 4 : 2;     // x-pass outputs / unit
     static constexpr int NXU = GY * (MX / XW);
     static constexpr int NXS = (NXU + NT - 1) / NT;
-    // y outputs per unit (a divisor of MY = 16 + 2W)
-    static constexpr int YW = W == 1 ? 3 : (W == 3 ? 2 : 4);
+    // y outputs per unit: the largest of 4, 3, 2 dividing MY = OY + 2W
+    static constexpr int YW = MY % 4 == 0 ? 4 : (MY % 3 == 0 ? 3 : 2);
     static constexpr int NYU = MX * (MY / YW);
     static constexpr int NYS = (NYU + NT - 1) / NT;
     static constexpr int NBU = 3 * MY * (OX / 4);      // coefficient x box
@@ -222,11 +221,13 @@ __device__ __forceinline__ void ymap(int u, int* mx, int* my0) {
     }
 }
 
-template <int W>
-__global__ void __launch_bounds__(NT, 2)
+template <int W, int TILE>
+__global__ void __launch_bounds__(e1_tile_threads(TILE),
+                                  TILE == E1_TILE_32X16 ? 2 : 1)
     k_lncc(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
            LnccConsts c, long long* __restrict__ loss_part) {
-    using C = E1Z<W>;
+    using C = E1Z<W, TILE>;
+    constexpr int NT = C::NT;
     constexpr int K = C::K, OX = C::OX, OY = C::OY, MX = C::MX, MY = C::MY;
     constexpr int MXP = C::MXP, GU = C::GU;
     constexpr int NZS = C::NZS, XW = C::XW, YW = C::YW;
@@ -557,37 +558,48 @@ __global__ void __launch_bounds__(NT, 2)
     }
 }
 
-template <int W>
+template <int W, int TILE>
 int launch_w(const Batch& b, int mode, int attempt, cudaStream_t s) {
-    k_lncc<W><<<b.plan.e1_ctas, NT, E1Z<W>::bytes, s>>>(
+    using C = E1Z<W, TILE>;
+    k_lncc<W, TILE><<<b.plan.e1_ctas, C::NT, C::bytes, s>>>(
         b.pd, b.npairs, mode, attempt, b.c, b.part.loss);
     return 1;
 }
 
-template <int W>
+template <int W, int TILE>
 cudaError_t attr_w() {
-    return cudaFuncSetAttribute(k_lncc<W>,
+    return cudaFuncSetAttribute(k_lncc<W, TILE>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                E1Z<W>::bytes);
+                                E1Z<W, TILE>::bytes);
+}
+
+template <int TILE>
+int launch_t(const Batch& b, int mode, int attempt, cudaStream_t s) {
+    switch ((b.c.win - 1) / 2) {
+        case 1: return launch_w<1, TILE>(b, mode, attempt, s);
+        case 2: return launch_w<2, TILE>(b, mode, attempt, s);
+        default: return launch_w<3, TILE>(b, mode, attempt, s);
+    }
 }
 
 }  // namespace
 
 int launch_lncc(const Batch& b, int mode, int attempt, cudaStream_t s) {
-    switch ((b.c.win - 1) / 2) {
-        case 1: return launch_w<1>(b, mode, attempt, s);
-        case 2: return launch_w<2>(b, mode, attempt, s);
-        case 3: return launch_w<3>(b, mode, attempt, s);
-        default: return launch_w<4>(b, mode, attempt, s);
-    }
+    if (b.c.win == 9) return launch_w<4, E1_TILE_32X16>(b, mode, attempt, s);
+    if (b.plan.e1_tile == E1_TILE_32X32)
+        return launch_t<E1_TILE_32X32>(b, mode, attempt, s);
+    return launch_t<E1_TILE_32X16>(b, mode, attempt, s);
 }
 
 cudaError_t lncc_setup() {
     cudaError_t e = cudaSuccess, r;
-    if ((r = attr_w<1>()) != cudaSuccess) e = r;
-    if ((r = attr_w<2>()) != cudaSuccess) e = r;
-    if ((r = attr_w<3>()) != cudaSuccess) e = r;
-    if ((r = attr_w<4>()) != cudaSuccess) e = r;
+    if ((r = attr_w<1, E1_TILE_32X16>()) != cudaSuccess) e = r;
+    if ((r = attr_w<2, E1_TILE_32X16>()) != cudaSuccess) e = r;
+    if ((r = attr_w<3, E1_TILE_32X16>()) != cudaSuccess) e = r;
+    if ((r = attr_w<4, E1_TILE_32X16>()) != cudaSuccess) e = r;
+    if ((r = attr_w<1, E1_TILE_32X32>()) != cudaSuccess) e = r;
+    if ((r = attr_w<2, E1_TILE_32X32>()) != cudaSuccess) e = r;
+    if ((r = attr_w<3, E1_TILE_32X32>()) != cudaSuccess) e = r;
     return e;
 }
 

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(256)
     const int z1 = min(z0 + P.st_zc, g.nz);
     const T* __restrict__ M = (const T*)P.M;
     const float* __restrict__ u = eval_u(P, mode);
+    const JOut jo = jout_of(P);
     const int sxy = g.nx * g.ny;
     int i = z0 * sxy + y * g.nx + x;
     float nu0 = 0.f, nu1 = 0.f, nu2 = 0.f;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256)
             nu1 = __ldg(u + g.V + i + sxy);
             nu2 = __ldg(u + 2 * g.V + i + sxy);
         }
-        resample_voxel(P, M, x, y, z, i, d0, d1, d2);
+        resample_voxel(jo, g, M, x, y, z, i, d0, d1, d2);
     }
 }
 
@@ -185,13 +186,13 @@ __global__ void __launch_bounds__(NTP)
 // ----------------------------------------------------------------------
 // E2
 // ----------------------------------------------------------------------
-// 384 threads: in the y and z passes each thread owns one component of a
-// quad of four adjacent outputs (3 components x 8 quads x 16 rows), so its
-// shared-memory reads are 16-byte vectors and the z window of its quad sits
-// in a register ring.  The g_raw plane of each slice (three components
-// with the halo) arrives by one TMA tile load into a ring of E2_NB buffers,
-// issued E2_NB slices ahead and tracked by an mbarrier per buffer.
-constexpr int NT2 = 384;
+// 256 threads: in the y and z passes each thread owns two x-adjacent
+// outputs of one row with all three components (8-byte shared-memory reads,
+// 8-byte global stores), and the z window of those six values sits in a
+// register ring.  The g_raw plane of each slice (three components with the
+// halo) arrives by one TMA tile load into a ring of E2_NB buffers, issued
+// E2_NB slices ahead and tracked by an mbarrier per buffer.
+constexpr int NT2 = 256;
 constexpr int E2_NB = 4;
 
 template <int R>
@@ -205,9 +206,9 @@ struct E2Cfg {
     static constexpr int NXU = 3 * BY * NQ;         // x-pass units (4 outputs)
     static constexpr int TXB = 3 * BY * BX * 4;     // bytes per TMA tile
     static constexpr int GRF = (3 * BY * BX + 31) / 32 * 32;   // floats/buffer
-    // g_raw tiles, x-smoothed plane, xyz-smoothed plane (+ alignment)
-    static constexpr int bytes =
-        128 + (E2_NB * GRF + 3 * BY * TX + 3 * TY * TX) * 4;
+    static_assert(TX * TY == 2 * NT2, "two outputs per thread");
+    // g_raw tiles and the x-smoothed plane (+ alignment)
+    static constexpr int bytes = 128 + (E2_NB * GRF + 3 * BY * TX) * 4;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -276,19 +277,16 @@ __device__ __forceinline__ float4 f4_mul(float a, float4 x) {
 }
 
 template <int R, typename T>
-__global__ void __launch_bounds__(NT2, 2)
+__global__ void __launch_bounds__(NT2, R <= 3 ? 3 : 2)
     k_e2(const PairDesc* __restrict__ pd, int npairs, int mode, int attempt,
          Taps tp, float* __restrict__ g2_part) {
     using C = E2Cfg<R>;
     constexpr int KG = C::KG, BX = C::BX, BY = C::BY, RA = C::RA;
     constexpr int TX = C::TX, TY = C::TY, NQ = C::NQ, GRF = C::GRF;
     constexpr int NXS = (C::NXU + NT2 - 1) / NT2;        // x-pass slots
-    constexpr int NVS = (TX * TY + NT2 - 1) / NT2;       // |g|^2 slots
-    static_assert(3 * NQ * TY == NT2, "one quad-component per thread");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* Gr = (float*)(((size_t)smem_raw + 127) & ~(size_t)127);  // [NB][GRF]
     float* Gx = Gr + E2_NB * GRF;          // [3][BY][TX]
-    float* Gz = Gx + 3 * BY * TX;          // [3][TY][TX]
     __shared__ __align__(8) unsigned long long mbar[E2_NB];
     __shared__ float red[NT2 / 32];
 
@@ -300,16 +298,14 @@ __global__ void __launch_bounds__(NT2, 2)
     const int sxy = g.nx * g.ny;
     // taps stay in the kernel-parameter constant bank (no registers)
     const float* tt = tp.t;
-    // y/z role: component q, quad qx of row oy
-    const int q = tid / (NQ * TY);
-    const int oy = (tid - q * NQ * TY) / NQ;
-    const int qx = tid - q * NQ * TY - oy * NQ;
+    // y/z role: outputs 2 px, 2 px + 1 of row oy, all three components
+    const int px = tid % (TX / 2), oy = tid / (TX / 2);
     int x_in[NXS], x_out[NXS];
 #pragma unroll
     for (int k = 0; k < NXS; ++k) {
         const int u = tid + k * NT2;
         const int row = u / NQ, p = u - row * NQ;   // row over 3 BY rows
-        x_in[k] = u < C::NXU ? row * BX + (RA - R) + 4 * p : -1;
+        x_in[k] = u < C::NXU ? row * BX + 4 * p : -1;
         x_out[k] = row * TX + 4 * p;
     }
     if (tid == 0) {
@@ -329,7 +325,7 @@ __global__ void __launch_bounds__(NT2, 2)
         failed = __syncthreads_or(!mbar_wait(&mbar[0], 0)) != 0;
     }
     float m2 = 0.f;
-    const bool vec_store = (g.nx & 3) == 0;
+    const bool pair_store = (g.nx & 1) == 0;   // 8-byte aligned pairs
 
     const int e2_cx = P.e2_cx;
     const long long total = (long long)P.e2_cx * P.e2_cy * g.nz;
@@ -343,9 +339,10 @@ __global__ void __launch_bounds__(NT2, 2)
         w0 += z1 - z0;
         const int x0 = (int)(col % e2_cx) * TX;
         const int y0 = (int)(col / e2_cx) * TY;
-        const int ox = x0 + 4 * qx, oyy = y0 + oy;
-        const bool row_in = oyy < g.ny && ox < g.nx;
-        const int o_off = q * (int)g.V + oyy * g.nx + ox;
+        const int ox = x0 + 2 * px, oyy = y0 + oy;
+        const bool in0 = oyy < g.ny && ox < g.nx;
+        const bool in1 = oyy < g.ny && ox + 1 < g.nx;
+        const int o_off = oyy * g.nx + ox;
         const int s_begin = z0 - R, s_end = z1 + R;
         // slices outside the volume and the halo outside it read as zero
         if (tid == 0) {
@@ -355,9 +352,11 @@ __global__ void __launch_bounds__(NT2, 2)
                             0, &mbar[b]);
             }
         }
-        float4 ring[KG];
+        float2 ring[KG][3];
 #pragma unroll
-        for (int k = 0; k < KG; ++k) ring[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < KG; ++k)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ring[k][q] = make_float2(0.f, 0.f);
         for (int base = s_begin; base < s_end && !failed; base += KG) {
 #pragma unroll
             for (int j = 0; j < KG; ++j) {
@@ -366,7 +365,8 @@ __global__ void __launch_bounds__(NT2, 2)
                 const int t = s - s_begin;
                 const int b = t % E2_NB;
                 const float* gr = Gr + b * GRF;
-                // (1) this slice's g_raw tile (TMA, issued two slices ago)
+                // (1) this slice's g_raw tile (TMA, issued E2_NB slices ago);
+                //     the barrier also frees the x-smoothed plane
                 const bool ok = mbar_wait(&mbar[b], (phase >> b) & 1u);
                 phase ^= 1u << b;
                 if (__syncthreads_or(!ok)) {
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(NT2, 2)
                     constexpr int DOFF = RA - R;
                     constexpr int NV4 = (DOFF + 4 + 2 * R + 3) / 4;
                     static_assert(4 * (NQ - 1) + 4 * NV4 <= BX, "x-pass read in row");
-                    const float4* rr4 = (const float4*)(gr + x_in[k] - DOFF);
+                    const float4* rr4 = (const float4*)(gr + x_in[k]);
                     float w4[4 * NV4];
 #pragma unroll
                     for (int q4 = 0; q4 < NV4; ++q4) {
@@ -398,16 +398,13 @@ __global__ void __launch_bounds__(NT2, 2)
                         w4[4 * q4 + 2] = t4.z;
                         w4[4 * q4 + 3] = t4.w;
                     }
-                    float v[4 + 2 * R];
-#pragma unroll
-                    for (int o = 0; o < 4 + 2 * R; ++o) v[o] = w4[DOFF + o];
                     float out[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        float a = tt[R] * v[e + R];
+                        float a = tt[R] * w4[DOFF + e + R];
 #pragma unroll
                         for (int m = 1; m <= R; ++m)
-                            a += tt[R + m] * (v[e + R - m] + v[e + R + m]);
+                            a += tt[R + m] * (w4[DOFF + e + R - m] + w4[DOFF + e + R + m]);
                         out[e] = a;
                     }
                     *(float4*)(Gx + x_out[k]) = make_float4(out[0], out[1], out[2], out[3]);
@@ -419,59 +416,60 @@ __global__ void __launch_bounds__(NT2, 2)
                     tma_load_4d(Gr + b * GRF, P.tm_graw, x0 - RA, y0 - R, s + E2_NB,
                                 0, &mbar[b]);
                 }
-                // (3) along y for this thread's quad, into the ring; along
-                //     z at slice o = s - R
-                {
-                    const float* col4 = Gx + (q * BY + oy) * TX + 4 * qx;
-                    float4 a = f4_mul(tt[R], *(const float4*)(col4 + R * TX));
+                // (3) along y for this thread's pair, all components, into
+                //     the ring; along z at slice o = s - R
 #pragma unroll
-                    for (int m = 1; m <= R; ++m)
-                        a = f4_fma(tt[R + m],
-                                   f4_add(*(const float4*)(col4 + (R - m) * TX),
-                                          *(const float4*)(col4 + (R + m) * TX)),
-                                   a);
-                    ring[j] = a;
+                for (int q = 0; q < 3; ++q) {
+                    const float* c2 = Gx + (q * BY + oy) * TX + 2 * px;
+                    const float2 mid = *(const float2*)(c2 + R * TX);
+                    float2 a = make_float2(tt[R] * mid.x, tt[R] * mid.y);
+#pragma unroll
+                    for (int m = 1; m <= R; ++m) {
+                        const float2 lo = *(const float2*)(c2 + (R - m) * TX);
+                        const float2 hi = *(const float2*)(c2 + (R + m) * TX);
+                        a.x = fmaf(tt[R + m], lo.x + hi.x, a.x);
+                        a.y = fmaf(tt[R + m], lo.y + hi.y, a.y);
+                    }
+                    ring[j][q] = a;
                 }
                 if (t >= 2 * R) {
                     // slice o + d sits in slot (j + 1 + R + d) mod KG
-                    float4 zv = f4_mul(tt[R], ring[(j + 1 + R) % KG]);
+                    float2 zv[3];
 #pragma unroll
-                    for (int m = 1; m <= R; ++m)
-                        zv = f4_fma(tt[R + m],
-                                    f4_add(ring[(j + 1 + R - m) % KG],
-                                           ring[(j + 1 + R + m) % KG]),
-                                    zv);
-                    *(float4*)(Gz + (q * TY + oy) * TX + 4 * qx) = zv;
-                    if (row_in) {
-                        float* dst = gout + (s - R) * sxy + o_off;
-                        if (vec_store && ox + 3 < g.nx) {
-                            *(float4*)dst = zv;
-                        } else {
-                            const float e4[4] = {zv.x, zv.y, zv.z, zv.w};
+                    for (int q = 0; q < 3; ++q) {
+                        const float2 mid = ring[(j + 1 + R) % KG][q];
+                        float2 a = make_float2(tt[R] * mid.x, tt[R] * mid.y);
 #pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (ox + e < g.nx) dst[e] = e4[e];
+                        for (int m = 1; m <= R; ++m) {
+                            const float2 lo = ring[(j + 1 + R - m) % KG][q];
+                            const float2 hi = ring[(j + 1 + R + m) % KG][q];
+                            a.x = fmaf(tt[R + m], lo.x + hi.x, a.x);
+                            a.y = fmaf(tt[R + m], lo.y + hi.y, a.y);
+                        }
+                        zv[q] = a;
+                    }
+                    float* dst = gout + (s - R) * sxy + o_off;
+                    if (in1 && pair_store) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            *(float2*)(dst + (long long)q * g.V) = zv[q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            if (in0) dst[(long long)q * g.V] = zv[q].x;
+                            if (in1) dst[(long long)q * g.V + 1] = zv[q].y;
                         }
                     }
-                }
-                __syncthreads();
-                // (4) |g|^2 of the finished voxels (all three components)
-                if (t >= 2 * R) {
-#pragma unroll
-                    for (int k = 0; k < NVS; ++k) {
-                        const int v = tid + k * NT2;
-                        if (v >= TX * TY) continue;
-                        const int vy = v / TX, vx = v - vy * TX;
-                        if (x0 + vx >= g.nx || y0 + vy >= g.ny) continue;
-                        const float a0 = Gz[v], a1 = Gz[TX * TY + v],
-                                    a2 = Gz[2 * TX * TY + v];
-                        const float n2 = a0 * a0 + a1 * a1 + a2 * a2;
-                        m2 = (n2 != n2) ? INFINITY : fmaxf(m2, n2);
-                    }
+                    const float n0 = zv[0].x * zv[0].x + zv[1].x * zv[1].x +
+                                     zv[2].x * zv[2].x;
+                    const float n1 = zv[0].y * zv[0].y + zv[1].y * zv[1].y +
+                                     zv[2].y * zv[2].y;
+                    if (in0) m2 = (n0 != n0) ? INFINITY : fmaxf(m2, n0);
+                    if (in1) m2 = (n1 != n1) ? INFINITY : fmaxf(m2, n1);
                 }
             }
         }
-        __syncthreads();   // Gz is rewritten by the next segment
+        __syncthreads();   // Gx is rewritten by the next segment
     }
     for (int k = 16; k > 0; k >>= 1)
         m2 = fmaxf(m2, __shfl_down_sync(0xffffffffu, m2, k));
@@ -736,10 +734,17 @@ static void split_ctas(const long long* work, int npairs, long long target,
     }
 }
 
+bool e1_tile_ok(int t, int win) {
+    // the 32 x 32 variant's shared memory does not fit k = 9
+    return t == E1_TILE_32X16 || (t == E1_TILE_32X32 && win <= 7);
+}
+
 BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
-                     int e1_waves, int e2_waves) {
+                     int e1_waves, int e2_waves, int e1_tile) {
     BatchPlan bp{};
-    const int tx1 = E1_OX, ty1 = E1_OY;
+    if (e1_tile < 0 || !e1_tile_ok(e1_tile, win)) e1_tile = E1_TILE_32X16;
+    bp.e1_tile = e1_tile;
+    const int tx1 = E1_OX, ty1 = e1_tile_oy(e1_tile);
     std::vector<long long> w1(npairs), w2(npairs);
     std::vector<int> c0(npairs), n(npairs);
     for (int p = 0; p < npairs; ++p) {
@@ -751,7 +756,9 @@ BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
         pd[p].e2_cy = (int)ceil_div(g.ny, PLANE_Y);
         w2[p] = (long long)pd[p].e2_cx * pd[p].e2_cy * g.nz;
     }
-    if (e1_waves < 1) e1_waves = npairs == 1 ? 2 : 4;
+    // one wave is one CTA per SM (the 32 x 16 variant runs two at a time)
+    if (e1_waves < 1)
+        e1_waves = npairs == 1 ? (e1_tile == E1_TILE_32X16 ? 2 : 1) : 4;
     if (e2_waves < 1) e2_waves = npairs == 1 ? 2 : 8;
     const long long t1 = (long long)e1_waves * num_sms;
     const long long t2 = (long long)e2_waves * num_sms;
@@ -816,7 +823,7 @@ long long set_q_layout(PairDesc& d, int win, int loss) {
     d.qx = 2 * W;
     d.qz = 2 * W + 1;
     d.qw = (int)ceil_div(d.g.nx, E1_OX) * E1_OX + 4 * W;
-    d.qh = (int)ceil_div(d.g.ny, E1_OY) * E1_OY + 4 * W;
+    d.qh = (int)ceil_div(d.g.ny, E1_QY) * E1_QY + 4 * W;
     return (long long)d.qw * d.qh * (d.g.nz + 2 * d.qz);
 }
 

@@ -198,11 +198,19 @@ __device__ __forceinline__ T tree_sum(const T* v) {
         return tree_sum<L, N / 2, T>(v) + tree_sum<L + N / 2, N - N / 2, T>(v);
 }
 
-// Output tile (x, y) of the LNCC moment kernel; a CTA marches along z over a
-// column of such tiles.  Two CTAs fit an SM for k <= 7, so one CTA's
-// barriers overlap the other's work.
-constexpr int E1_OX = 32, E1_OY = 16;
-constexpr int E1_THREADS = 256;
+// Output tile variants of the LNCC moment kernel (a CTA marches along z
+// over a column of such tiles; the autotuner picks one per batch):
+//   E1_TILE_32X16: 32 x 16 outputs, 256 threads, two CTAs per SM (k <= 7),
+//                  so one CTA's barriers overlap the other's work;
+//   E1_TILE_32X32: 32 x 32 outputs, 512 threads, one CTA per SM, a smaller
+//                  halo share per output (k <= 7 only).
+enum { E1_TILE_32X16 = 0, E1_TILE_32X32 = 1, E1_NTILES = 2 };
+constexpr int E1_OX = 32;
+__host__ __device__ constexpr int e1_tile_oy(int t) { return t ? 32 : 16; }
+__host__ __device__ constexpr int e1_tile_threads(int t) { return t ? 512 : 256; }
+// the y granularity of the padded fixed-point layout: a multiple of every
+// variant's tile height
+constexpr int E1_QY = 32;
 
 struct Partials {
     long long* loss;  // one per E1 CTA, fixed point LOSS_Q (or LOSS_BAD)
@@ -222,6 +230,7 @@ constexpr int MI_MAX_BINS = 64;
 // Totals of a batch plan.
 struct BatchPlan {
     int e1_ctas, e2_ctas, st_blocks, ln_blocks, mm_ctas;
+    int e1_tile;      // E1_TILE_* of the LNCC moment kernel
 };
 
 // Everything a launch needs besides the stream.
@@ -249,7 +258,9 @@ struct Batch {
 // per SM in total, split among the pairs in proportion to their work (0: the
 // defaults, 1 and 2 for a single pair, 4 and 8 for a batch).
 BatchPlan plan_batch(PairDesc* host_pd, int npairs, int win, int num_sms,
-                     int e1_waves = 0, int e2_waves = 0);
+                     int e1_waves = 0, int e2_waves = 0, int e1_tile = -1);
+// Whether the LNCC moment kernel has the tile variant t for window win.
+bool e1_tile_ok(int t, int win);
 
 // Opt the kernels in to their dynamic shared memory (once per process).
 cudaError_t fused_setup();

@@ -77,35 +77,66 @@ __device__ __forceinline__ void interp_grad(const float m[8], const float f[3],
 // Fixed-point value of a non-finite J (never a valid code).
 constexpr int JQ_BAD = (int)0x80000000;
 
+// Where the resampling writes go, loaded once per kernel from the pair's
+// table (a store through jq could alias the table, so reading the fields
+// at every store would reload them).
+struct JOut {
+    int* jq;
+    float* dj;
+    unsigned* flags;
+    int V;                    // dj component stride
+    int qw, qh, qx, qz;       // jq layout (qw = 0: plain)
+    int nx, ny;
+    float sh, Q;
+    int qlim;
+};
+__device__ __forceinline__ JOut jout_of(const PairDesc& P) {
+    JOut o;
+    o.jq = P.jq;
+    o.dj = P.dj;
+    o.flags = P.flags;
+    o.V = (int)P.g.V;
+    o.qw = P.qw;
+    o.qh = P.qh;
+    o.qx = P.qx;
+    o.qz = P.qz;
+    o.nx = P.g.nx;
+    o.ny = P.g.ny;
+    o.sh = P.qs->shift;
+    o.Q = P.qs->Q;
+    o.qlim = P.qs->qlim;
+    return o;
+}
+
 // J and dJ/du of voxel (x, y, z) (linear index i) from its corners: J in
 // the moments' fixed point at the pair's jq layout (JQ_BAD, and the pair's
 // QFLAG_JBAD, if not finite) and dJ/du to dj (3 x V).
-__device__ __forceinline__ void store_resampled(const PairDesc& P, int i,
-                                                int x, int y, int z,
-                                                const float m[8],
+__device__ __forceinline__ void store_resampled(const JOut& o, int i, int x,
+                                                int y, int z, const float m[8],
                                                 const float f[3]) {
     float d[3];
     const float J = interp(m, f);
     interp_grad(m, f, d);
-    const float sh = P.qs->shift, Q = P.qs->Q;
-    const int qlim = P.qs->qlim;
     const bool fin = fabsf(J) <= 3.0e38f;
-    if (!fin) atomicOr(P.flags, QFLAG_JBAD);
-    P.jq[qidx(P, x, y, z)] =
-        fin ? min(max(__float2int_rn((J - sh) * Q), -qlim), qlim) : JQ_BAD;
-    P.dj[i] = d[0];
-    P.dj[P.g.V + i] = d[1];
-    P.dj[2 * P.g.V + i] = d[2];
+    if (!fin) atomicOr(o.flags, QFLAG_JBAD);
+    const int qi = o.qw ? ((z + o.qz) * o.qh + y + o.qx) * o.qw + x + o.qx
+                        : i;
+    o.jq[qi] = fin ? min(max(__float2int_rn((J - o.sh) * o.Q), -o.qlim), o.qlim)
+                   : JQ_BAD;
+    o.dj[i] = d[0];
+    o.dj[o.V + i] = d[1];
+    o.dj[2 * o.V + i] = d[2];
 }
 
 // J and dJ/du of voxel (x, y, z) under displacement (d0, d1, d2).
 template <typename T>
-__device__ __forceinline__ void resample_voxel(const PairDesc& P, const T* M,
-                                               int x, int y, int z, int i,
-                                               float d0, float d1, float d2) {
+__device__ __forceinline__ void resample_voxel(const JOut& o, const Geom& g,
+                                               const T* M, int x, int y, int z,
+                                               int i, float d0, float d1,
+                                               float d2) {
     float m[8], f[3];
-    corners(M, P.g, x, y, z, d0, d1, d2, m, f);
-    store_resampled(P, i, x, y, z, m, f);
+    corners(M, g, x, y, z, d0, d1, d2, m, f);
+    store_resampled(o, i, x, y, z, m, f);
 }
 
 }  // namespace lmk

@@ -175,13 +175,14 @@ __global__ void __launch_bounds__(TH_W * 32)
 
 // Trial field, one voxel per thread.  A block owns a 32 x 8 x-y tile and a
 // z range of one pair; the planes z-1, z, z+1 of u (3 components, with a
-// one-voxel x-y halo, read at edge-clamped positions) sit in a
-// shared-memory ring, so the trilinear read of u at p + v comes from shared
-// memory whenever |v| < 1 along each axis and from global memory otherwise.
-// The trial goes to slot (1 - cu), or to the pair's warp-smoothing buffer.
-// Without warp smoothing the kernel also resamples M at the trial (J and
-// dJ/du of the trial's evaluation, Section 2.1) while the trial is in
-// registers, so the evaluation starts at the moment kernel.
+// one-voxel x-y halo, read at edge-clamped positions) sit in a four-slot
+// shared-memory ring that cp.async fills one plane ahead, so the trilinear
+// read of u at p + v comes from shared memory whenever |v| < 1 along each
+// axis and from global memory otherwise.  The trial goes to slot (1 - cu),
+// or to the pair's warp-smoothing buffer.  Without warp smoothing the
+// kernel also resamples M at the trial (J and dJ/du of the trial's
+// evaluation, Section 2.1) while the trial is in registers, so the
+// evaluation starts at the moment kernel.
 constexpr int ST_X = 32, ST_Y = 8, ST_HX = ST_X + 2, ST_HY = ST_Y + 2;
 constexpr int ST_PLANE = ST_HX * ST_HY;
 
@@ -192,11 +193,24 @@ enum StepMode {
     STEP_DIRECT = 2,  // v = step * g (Demons)
 };
 
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 template <typename T, bool RESAMPLE, int MODE>
 __global__ void __launch_bounds__(ST_X * ST_Y, 3)
     k_step_compose(const PairDesc* __restrict__ pd, int npairs, int attempt,
                    float step, int smooth, int tile) {
-    __shared__ float ring[3][3][ST_PLANE];   // [z slot][component][y][x]
+    __shared__ __align__(16) float ring[4][3][ST_PLANE];   // [slot][comp][y][x]
     const PairDesc& P = pd[pair_of_block<3>(pd, npairs, blockIdx.x)];
     const DevState* st = P.st;
     if (attempt_skip(st, attempt)) return;
@@ -205,11 +219,14 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
     const float* __restrict__ u = cu ? P.u1 : P.u0;
     float* __restrict__ out = smooth ? P.wtmpA : (cu ? P.u0 : P.u1);
     const float* __restrict__ gg = cg ? P.g1 : P.g0;
+    const T* __restrict__ M = (const T*)P.M;
     const float r = (float)st->L;
     const float lam = (float)st->lambda;
     const float gm = st->gmax;
     const float inv = gm > 0.f ? 1.f / gm : 0.f;
     const float scale = -r * step;
+    JOut jo;
+    if (RESAMPLE) jo = jout_of(P);
 
     const int b = blockIdx.x - P.st_blk0;
     const int bx = b % P.st_tx;
@@ -222,37 +239,41 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
     const int z1 = min(z0 + P.st_zc, g.nz);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int sxy = g.nx * g.ny;
-    const float* U[3] = {u, u + g.V, u + 2 * g.V};
+    const int V = (int)g.V;
+    // Tile-mode pair fields (read once)
+    const float* __restrict__ tileH = MODE == STEP_TILE ? P.tileH : nullptr;
 
-    // Each thread loads fixed halo positions of every plane; their clamped
-    // in-plane sources and smem slots are computed once.
+    // Each thread copies fixed halo positions of every plane; their clamped
+    // in-plane sources (offsets from u, component included) and ring
+    // offsets are computed once.
     constexpr int NLD = (3 * ST_PLANE + ST_X * ST_Y - 1) / (ST_X * ST_Y);
-    const float* ld_src[NLD];
-    int ld_dst[NLD];
+    int ld_src[NLD], ld_dst[NLD];
 #pragma unroll
     for (int k = 0; k < NLD; ++k) {
-        int e = tid + k * ST_X * ST_Y;
+        const int e = tid + k * ST_X * ST_Y;
         ld_dst[k] = -1;
-        ld_src[k] = u;
+        ld_src[k] = 0;
         if (e < 3 * ST_PLANE) {
-            int q = e / ST_PLANE, rem = e - q * ST_PLANE;
-            int hy = rem / ST_HX, hx = rem - hy * ST_HX;
-            int gx = min(max(x0 - 1 + hx, 0), g.nx - 1);
-            int gy = min(max(y0 - 1 + hy, 0), g.ny - 1);
-            ld_src[k] = u + q * g.V + gy * g.nx + gx;
+            const int q = e / ST_PLANE, rem = e - q * ST_PLANE;
+            const int hy = rem / ST_HX, hx = rem - hy * ST_HX;
+            const int gx = min(max(x0 - 1 + hx, 0), g.nx - 1);
+            const int gy = min(max(y0 - 1 + hy, 0), g.ny - 1);
+            ld_src[k] = q * V + gy * g.nx + gx;
             ld_dst[k] = q * ST_PLANE + rem;
         }
     }
-    auto load_plane = [&](int zp, int slot) {
-        const int zo = min(max(zp, 0), g.nz - 1) * sxy;
-        float* dst = &ring[slot][0][0];
+    // plane zp (edge-clamped) into ring slot zp mod 4
+    auto issue_plane = [&](int zp) {
+        const float* src = u + min(max(zp, 0), g.nz - 1) * sxy;
+        float* dst = &ring[zp & 3][0][0];
 #pragma unroll
         for (int k = 0; k < NLD; ++k)
-            if (ld_dst[k] >= 0) dst[ld_dst[k]] = __ldg(ld_src[k] + zo);
+            if (ld_dst[k] >= 0) cp_async4(dst + ld_dst[k], src + ld_src[k]);
     };
-    load_plane(z0 - 1, (z0 + 2) % 3);
-    load_plane(z0, z0 % 3);
-    load_plane(z0 + 1, (z0 + 1) % 3);
+    issue_plane(z0 - 1);
+    issue_plane(z0);
+    issue_plane(z0 + 1);
+    cp_async_commit_wait_all();
     const bool in_xy = x < g.nx && y < g.ny;
     // Eq. tilen: this column's tiles (x / k, y / k fixed; z / k counted),
     // as tile indices of the pair's table
@@ -264,60 +285,57 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
         tzr = z0 - tz_ * tile;
     }
     // the gradient of voxel z is loaded one step ahead
+    int i = z0 * sxy + y * g.nx + x;
     float ng0 = 0.f, ng1 = 0.f, ng2 = 0.f;
     if (in_xy && z0 < z1) {
-        const int i0 = z0 * sxy + y * g.nx + x;
-        ng0 = __ldg(gg + i0);
-        ng1 = __ldg(gg + g.V + i0);
-        ng2 = __ldg(gg + 2 * g.V + i0);
+        ng0 = __ldg(gg + i);
+        ng1 = __ldg(gg + V + i);
+        ng2 = __ldg(gg + 2 * V + i);
     }
     __syncthreads();
     // resampling is pipelined by one voxel: the corners of M at the trial of
     // voxel z are requested at step z and consumed at step z + 1
     float pm[8], pf[3];
-    int pi = -1;
-    for (int z = z0; z < z1; ++z) {
-        // plane z + 2 streams into registers while voxel z is computed
-        float pre[NLD];
-        {
-            const int zo = min(max(z + 2, 0), g.nz - 1) * sxy;
-#pragma unroll
-            for (int k = 0; k < NLD; ++k)
-                pre[k] = ld_dst[k] >= 0 ? __ldg(ld_src[k] + zo) : 0.f;
-        }
+    bool have = false;
+    for (int z = z0; z < z1; ++z, i += sxy) {
+        // plane z + 2 (read from step z + 1 on) streams into its slot, the
+        // one plane z - 2 left
+        if (z + 2 <= z1) issue_plane(z + 2);
+        cp_async_commit();
         const float cg0 = ng0, cg1 = ng1, cg2 = ng2;
         if (in_xy && z + 1 < z1) {
-            const int i1 = (z + 1) * sxy + y * g.nx + x;
-            ng0 = __ldg(gg + i1);
-            ng1 = __ldg(gg + g.V + i1);
-            ng2 = __ldg(gg + 2 * g.V + i1);
+            ng0 = __ldg(gg + i + sxy);
+            ng1 = __ldg(gg + V + i + sxy);
+            ng2 = __ldg(gg + 2 * V + i + sxy);
         }
         if (in_xy) {
-            const int i = z * sxy + y * g.nx + x;
-            float gh0 = cg0 * inv;
-            float gh1 = cg1 * inv;
-            float gh2 = cg2 * inv;
             float v[3];
             if (MODE == STEP_DIRECT) {
                 v[0] = cg0 * step;
                 v[1] = cg1 * step;
                 v[2] = cg2 * step;
-            } else if (MODE == STEP_TILE) {
-                // the tile's (H / gmax^2 + lambda I)^-1, symmetric
-                const float* a8 = P.tileH + (size_t)(tz_ * tile_slice + tile_col) * 8;
-                const float4 ia = __ldg((const float4*)a8);
-                const float4 ib = __ldg((const float4*)(a8 + 4));
-                v[0] = scale * (ia.x * gh0 + ia.y * gh1 + ia.z * gh2);
-                v[1] = scale * (ia.y * gh0 + ia.w * gh1 + ib.x * gh2);
-                v[2] = scale * (ia.z * gh0 + ib.x * gh1 + ib.y * gh2);
             } else {
-                float n2 = gh0 * gh0 + gh1 * gh1 + gh2 * gh2;
-                float sc = scale / (n2 + lam);
-                v[0] = gh0 * sc;
-                v[1] = gh1 * sc;
-                v[2] = gh2 * sc;
+                const float gh0 = cg0 * inv, gh1 = cg1 * inv, gh2 = cg2 * inv;
+                if (MODE == STEP_TILE) {
+                    // the tile's (H / gmax^2 + lambda I)^-1, symmetric
+                    const float* a8 = tileH + (size_t)(tz_ * tile_slice + tile_col) * 8;
+                    const float4 ia = __ldg((const float4*)a8);
+                    const float4 ib = __ldg((const float4*)(a8 + 4));
+                    v[0] = scale * (ia.x * gh0 + ia.y * gh1 + ia.z * gh2);
+                    v[1] = scale * (ia.y * gh0 + ia.w * gh1 + ib.x * gh2);
+                    v[2] = scale * (ia.z * gh0 + ib.x * gh1 + ib.y * gh2);
+                } else {
+                    // n2 + lam >= lam > 0: the approximate division (about
+                    // 2 ulp) is safe
+                    const float n2 = gh0 * gh0 + gh1 * gh1 + gh2 * gh2;
+                    const float sc = __fdividef(scale, n2 + lam);
+                    v[0] = gh0 * sc;
+                    v[1] = gh1 * sc;
+                    v[2] = gh2 * sc;
+                }
             }
             float fl[3], f[3];
+#pragma unroll
             for (int k = 0; k < 3; ++k) {
                 fl[k] = safe_floor(v[k]);
                 f[k] = v[k] - fl[k];
@@ -329,21 +347,19 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
             float m[3][8];
             if (cx >= x0 - 1 && cx + 1 <= x0 + ST_X && cy >= y0 - 1 &&
                 cy + 1 <= y0 + ST_Y && cz >= z - 1 && cz + 1 <= z + 1) {
-                const int hx = cx - (x0 - 1), hy = cy - (y0 - 1);
-                const int s0 = (cz + 3) % 3, s1 = (cz + 4) % 3;
-                const int o = hy * ST_HX + hx;
+                const int o = (cy - (y0 - 1)) * ST_HX + cx - (x0 - 1);
+                const float* p0 = &ring[cz & 3][0][0] + o;
+                const float* p1 = &ring[(cz + 1) & 3][0][0] + o;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    const float* p0 = ring[s0][q] + o;
-                    const float* p1 = ring[s1][q] + o;
-                    m[q][0] = p0[0];
-                    m[q][1] = p0[1];
-                    m[q][2] = p0[ST_HX];
-                    m[q][3] = p0[ST_HX + 1];
-                    m[q][4] = p1[0];
-                    m[q][5] = p1[1];
-                    m[q][6] = p1[ST_HX];
-                    m[q][7] = p1[ST_HX + 1];
+                    m[q][0] = p0[q * ST_PLANE];
+                    m[q][1] = p0[q * ST_PLANE + 1];
+                    m[q][2] = p0[q * ST_PLANE + ST_HX];
+                    m[q][3] = p0[q * ST_PLANE + ST_HX + 1];
+                    m[q][4] = p1[q * ST_PLANE];
+                    m[q][5] = p1[q * ST_PLANE + 1];
+                    m[q][6] = p1[q * ST_PLANE + ST_HX];
+                    m[q][7] = p1[q * ST_PLANE + ST_HX + 1];
                 }
             } else {
                 const int ax = min(max(cx, 0), g.nx - 1), bx2 = min(max(cx + 1, 0), g.nx - 1);
@@ -355,14 +371,15 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
                 const int o011 = bz2 * sxy + by2 * g.nx;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    m[q][0] = __ldg(U[q] + o000 + ax);
-                    m[q][1] = __ldg(U[q] + o000 + bx2);
-                    m[q][2] = __ldg(U[q] + o010 + ax);
-                    m[q][3] = __ldg(U[q] + o010 + bx2);
-                    m[q][4] = __ldg(U[q] + o001 + ax);
-                    m[q][5] = __ldg(U[q] + o001 + bx2);
-                    m[q][6] = __ldg(U[q] + o011 + ax);
-                    m[q][7] = __ldg(U[q] + o011 + bx2);
+                    const float* U = u + q * V;
+                    m[q][0] = __ldg(U + o000 + ax);
+                    m[q][1] = __ldg(U + o000 + bx2);
+                    m[q][2] = __ldg(U + o010 + ax);
+                    m[q][3] = __ldg(U + o010 + bx2);
+                    m[q][4] = __ldg(U + o001 + ax);
+                    m[q][5] = __ldg(U + o001 + bx2);
+                    m[q][6] = __ldg(U + o011 + ax);
+                    m[q][7] = __ldg(U + o011 + bx2);
                 }
             }
             float ut[3];
@@ -373,34 +390,30 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
                            wz1 * (wy0 * (wx0 * m[q][4] + wx1 * m[q][5]) +
                                   wy1 * (wx0 * m[q][6] + wx1 * m[q][7]));
                 ut[q] = v[q] + sv;
-                out[q * g.V + i] = ut[q];
+                out[q * V + i] = ut[q];
             }
             if (RESAMPLE) {
                 float cm[8], cf[3];
-                corners((const T*)P.M, g, x, y, z, ut[0], ut[1], ut[2], cm, cf);
-                if (pi >= 0) store_resampled(P, pi, x, y, z - 1, pm, pf);
+                corners(M, g, x, y, z, ut[0], ut[1], ut[2], cm, cf);
+                if (have) store_resampled(jo, i - sxy, x, y, z - 1, pm, pf);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) pm[k] = cm[k];
                 pf[0] = cf[0];
                 pf[1] = cf[1];
                 pf[2] = cf[2];
-                pi = i;
+                have = true;
             }
-        }
-        __syncthreads();   // slot of plane z - 1 is free
-        {
-            float* dst = &ring[(z + 2) % 3][0][0];
-#pragma unroll
-            for (int k = 0; k < NLD; ++k)
-                if (ld_dst[k] >= 0) dst[ld_dst[k]] = pre[k];
         }
         if (MODE == STEP_TILE && ++tzr == tile) {
             tzr = 0;
             ++tz_;
         }
+        // plane z + 2 has landed (this thread's copies), and every thread
+        // is done with plane z - 1 before step z + 1 overwrites its slot
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
     }
-    if (RESAMPLE && pi >= 0) store_resampled(P, pi, x, y, z1 - 1, pm, pf);
+    if (RESAMPLE && have) store_resampled(jo, i - sxy, x, y, z1 - 1, pm, pf);
 }
 
 // 1-D Gaussian along an axis of a pair's 3-component field, edge-extended;

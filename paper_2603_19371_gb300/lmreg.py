@@ -23,6 +23,7 @@ LM_LOSS_LNCC, LM_LOSS_MSE, LM_LOSS_MI = 0, 1, 2
 LM_METHOD_LM, LM_METHOD_DEMONS = 0, 1
 LM_MAX_LEVELS = 4
 LM_NOALLOC_MAX_VOXELS = 1 << 19
+LM_E1_TILE_32X16, LM_E1_TILE_32X32 = 0, 1
 
 
 class LMError(RuntimeError):
@@ -128,7 +129,10 @@ def load():
         "lm_downsample": [ctypes.POINTER(Volume), I, V, V, ctypes.POINTER(I),
                           V],
         "lm_batch_autotune": [V, ctypes.POINTER(V), I, ctypes.POINTER(I),
-                              ctypes.POINTER(I), ctypes.POINTER(D)],
+                              ctypes.POINTER(I), ctypes.POINTER(I),
+                              ctypes.POINTER(D)],
+        "lm_autotune": [V, V, I, ctypes.POINTER(I), ctypes.POINTER(I),
+                        ctypes.POINTER(I), ctypes.POINTER(D)],
         "lm_batch_register": [V, ctypes.POINTER(Schedule), ctypes.POINTER(V),
                               ctypes.POINTER(Report)],
         "lm_register_batch": [I, ctypes.POINTER(Volume), ctypes.POINTER(Volume),
@@ -438,13 +442,26 @@ def lm_batch_set_targets(b: Batch, targets=None):
 
 
 def lm_batch_autotune(b: Batch, us, reps=3):
-    """Pick the fastest evaluation work split for this batch; returns
-    (e1_waves, e2_waves, ms per evaluation)."""
-    w1, w2, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    """Pick the fastest moment-kernel tile and evaluation work split for
+    this batch; returns (e1_tile, e1_waves, e2_waves, ms per evaluation)."""
+    t, w1, w2 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
     _check(load().lm_batch_autotune(b.handle, _ptr_array(us, b.shapes), int(reps),
-                                    ctypes.byref(w1), ctypes.byref(w2),
-                                    ctypes.byref(ms)), "lm_batch_autotune")
-    return w1.value, w2.value, ms.value
+                                    ctypes.byref(t), ctypes.byref(w1),
+                                    ctypes.byref(w2), ctypes.byref(ms)),
+           "lm_batch_autotune")
+    return t.value, w1.value, w2.value, ms.value
+
+
+def lm_autotune(ctx: Context, u, reps=3):
+    """As lm_batch_autotune for a single-pair context at field u."""
+    t, w1, w2 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(load().lm_autotune(ctx.handle, _field_ptr(u, ctx.shape), int(reps),
+                              ctypes.byref(t), ctypes.byref(w1),
+                              ctypes.byref(w2), ctypes.byref(ms)),
+           "lm_autotune")
+    return t.value, w1.value, w2.value, ms.value
 
 
 def lm_field_resample(src, fa, dst, fb, stream=None):
@@ -543,7 +560,7 @@ EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_time_passes", "lm_batch_init", "lm_batch_destroy",
             "lm_batch_eval", "lm_batch_reset", "lm_batch_iterate",
             "lm_batch_set_targets", "lm_field_resample", "lm_batch_autotune",
-            "lm_downsample",
+            "lm_downsample", "lm_autotune",
             "lm_batch_register", "lm_register_batch", "lm_eval_noalloc",
             "lm_strerror", "lm_last_error", "lm_debug_check", "lm_get_log",
             "lm_batch_debug_check",

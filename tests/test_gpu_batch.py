@@ -180,8 +180,9 @@ def test_batch_autotune_keeps_results(P, oracle_mod):
     b = P.lm_batch_init(Fs, Ms, params)
     us = [torch.from_numpy(synth.random_field(sh, seed=20 + i, scale=1.3)).cuda()
           for i, sh in enumerate(SHAPES)]
-    w1, w2, ms = P.lm_batch_autotune(b, us, reps=2)
-    assert w1 in (1, 2, 4, 8) and w2 in (2, 4, 8, 16) and ms > 0
+    t, w1, w2, ms = P.lm_batch_autotune(b, us, reps=2)
+    assert t in (0, 1) and w1 in (1, 2, 4, 8) and w2 in (2, 4, 8, 16)
+    assert ms > 0
     gs = [torch.empty_like(u) for u in us]
     L, _ = P.lm_batch_eval(b, us, gs)
     Po = _oracle_params(oracle_mod, params)
