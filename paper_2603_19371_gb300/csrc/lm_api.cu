@@ -194,7 +194,9 @@ struct Core {
     std::vector<float*> gsink;     // lm_eval gradient sinks (lazy)
     bool have_reset = false;
     cudaGraphExec_t gexec = nullptr;
-    int graph_launches = 0;
+    int graph_launches = 0;        // kernels of a graph launch outside any loop
+    int body_launches = 0;         // kernels of one pass of the attempt loop
+    int att_runs_seen = 0;         // attempt-loop passes already counted
     long long launches = 0;
     int num_sms = 0;
     int e1_cap = 0, e2_cap = 0;    // partial slots allocated (any plan fits)
@@ -288,6 +290,9 @@ struct Core {
         LM_CK(cudaMemcpyAsync(h_st, hpd[0].st, npairs * sizeof(DevState),
                               cudaMemcpyDeviceToHost, stream));
         LM_CK(cudaStreamSynchronize(stream));
+        // passes of the attempt loop run since the last read
+        launches += (long long)(h_st[0].att_runs - att_runs_seen) * body_launches;
+        att_runs_seen = h_st[0].att_runs;
         for (int i = 0; i < npairs; ++i)
             if (int rc = status_error(h_st[i].status, i)) return rc;
         return LM_OK;
@@ -306,21 +311,75 @@ struct Core {
         return n;
     }
 
-    int iterate(int n) {
-        if (n <= 0) return LM_OK;
-        if (!gexec) {
-            if (!cap_stream)
-                LM_CK(cudaStreamCreateWithFlags(&cap_stream,
-                                                cudaStreamNonBlocking));
-            cudaGraph_t graph;
+    // With rejection the attempts of an iteration run in a graph WHILE
+    // loop: its body (trial, evaluation, decision with the attempt read from
+    // the device state, then k_att_next) repeats only while some pair
+    // rejected its trial and has retries left, so an iteration without
+    // rejections costs one attempt.  Without rejection the graph holds the
+    // single attempt.
+    bool loop_attempts() const { return p.reject && p.max_retries > 0; }
+
+    int capture_graph(cudaGraph_t* out) {
+        if (!cap_stream)
+            LM_CK(cudaStreamCreateWithFlags(&cap_stream,
+                                            cudaStreamNonBlocking));
+        if (!loop_attempts()) {
             LM_CK(cudaStreamBeginCapture(cap_stream,
                                          cudaStreamCaptureModeThreadLocal));
             graph_launches = enqueue_iteration(cap_stream);
-            cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
-            if (e != cudaSuccess)
-                return fail(LM_ECUDA, "graph capture failed: %s",
-                            cudaGetErrorString(e));
-            e = cudaGraphInstantiate(&gexec, graph, 0);
+            LM_CK(cudaStreamEndCapture(cap_stream, out));
+            body_launches = 0;
+            return LM_OK;
+        }
+        // attempt 0, whose decision kernel sets the loop condition, then
+        // the loop node over the later attempts (the decision kernels keep
+        // the attempt index; it returns to 0 when the loop ends)
+        cudaGraph_t graph;
+        LM_CK(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle h;
+        LM_CK(cudaGraphConditionalHandleCreate(&h, graph, 0,
+                                               cudaGraphCondAssignDefault));
+        LM_CK(cudaStreamBeginCaptureToGraph(cap_stream, graph, nullptr,
+                                            nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+        int n0 = batch_step(b, 0, cap_stream);
+        n0 += batch_eval(b, EVAL_TRIAL, 0, cap_stream, !step_resamples(b));
+        n0 += batch_finalize(b, FIN_DECIDE, 0, nullptr, cap_stream, h);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* dp = nullptr;
+        size_t nd = 0;
+        LM_CK(cudaStreamGetCaptureInfo(cap_stream, &cs, nullptr, nullptr, &dp,
+                                       nullptr, &nd));
+        std::vector<cudaGraphNode_t> deps(dp, dp + nd);
+        LM_CK(cudaStreamEndCapture(cap_stream, &graph));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t loop;
+        LM_CK(cudaGraphAddNode(&loop, graph, deps.data(), nullptr, deps.size(),
+                               &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        LM_CK(cudaStreamBeginCaptureToGraph(cap_stream, body, nullptr, nullptr,
+                                            0, cudaStreamCaptureModeThreadLocal));
+        int nb = batch_step(b, -1, cap_stream);
+        nb += batch_eval(b, EVAL_TRIAL, -1, cap_stream, !step_resamples(b));
+        nb += batch_finalize(b, FIN_DECIDE, -1, nullptr, cap_stream, h);
+        LM_CK(cudaStreamEndCapture(cap_stream, &body));
+        graph_launches = n0;
+        body_launches = nb;
+        *out = graph;
+        return LM_OK;
+    }
+
+    int iterate(int n) {
+        if (n <= 0) return LM_OK;
+        if (!gexec) {
+            cudaGraph_t graph;
+            int rc = capture_graph(&graph);
+            if (rc != LM_OK) return rc;
+            cudaError_t e = cudaGraphInstantiate(&gexec, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess)
                 return fail(LM_ECUDA, "graph instantiate failed: %s",
@@ -572,6 +631,7 @@ int core_reset(Core* c, float* const* u) {
     c->launches += batch_eval(c->b, EVAL_RESET, 0, c->stream);
     c->launches += batch_finalize(c->b, FIN_RESET, 0, nullptr, c->stream);
     LM_CK(cudaGetLastError());
+    c->att_runs_seen = 0;   // the reset decision clears the device count
     c->have_reset = true;
     return LM_OK;
 }
@@ -886,7 +946,7 @@ extern "C" int lm_state_save(lm_ctx* c, void* buf, size_t* nbytes) {
     h.nx = d.g.nx;
     h.ny = d.g.ny;
     h.nz = d.g.nz;
-    h.version = 2;
+    h.version = 3;
     char* q = (char*)buf;
     memcpy(q, &h, sizeof(h));
     memcpy(q + sizeof(h), k->h_st, sizeof(DevState));
@@ -908,7 +968,7 @@ extern "C" int lm_state_load(lm_ctx* c, const void* buf, size_t nbytes) {
     if (nbytes < need) return fail(LM_EINVAL, "checkpoint too small");
     CkptHeader h;
     memcpy(&h, buf, sizeof(h));
-    if (memcmp(h.magic, "LMREGCK1", 8) != 0 || h.version != 2)
+    if (memcmp(h.magic, "LMREGCK1", 8) != 0 || h.version != 3)
         return fail(LM_EINVAL, "not an lmreg checkpoint");
     if (h.nx != d.g.nx || h.ny != d.g.ny || h.nz != d.g.nz)
         return fail(LM_EINVAL, "checkpoint shape differs from the context");
@@ -917,6 +977,10 @@ extern "C" int lm_state_load(lm_ctx* c, const void* buf, size_t nbytes) {
     s.cu = 0;       // the field is the caller's (slot 0)
     s.cg = 0;       // the gradient is restored into slot 0
     s.done = 0;
+    s.att = 0;
+    s.att_runs = 0;     // counted from this load on
+    s.fin_count = 0u;
+    k->att_runs_seen = 0;
     k->h_st[0] = s;
     LM_CK(cudaMemcpyAsync(d.st, k->h_st, sizeof(DevState),
                           cudaMemcpyHostToDevice, k->stream));

@@ -102,10 +102,15 @@ __device__ __forceinline__ float* eval_g(const PairDesc& p, int mode) {
 }
 // Later attempts of an iteration are no-ops once the pair's iteration is
 // decided, and every attempt is once the pair has reached its target loss.
+// attempt < 0: the attempt index lives in the pair's device state (set by
+// the graph loop that repeats the attempts).
+__device__ __forceinline__ int attempt_of(const DevState* st, int attempt) {
+    return attempt >= 0 ? attempt : st->att;
+}
 __device__ __forceinline__ bool trial_skip(const PairDesc& p, int mode,
                                            int attempt) {
     return mode == EVAL_TRIAL &&
-           (p.st->stopped || (attempt > 0 && p.st->done));
+           (p.st->stopped || (attempt_of(p.st, attempt) > 0 && p.st->done));
 }
 
 // Pair whose block range starts at or below b (ranges ascend in pair
@@ -310,10 +315,13 @@ int launch_mi(const Batch& b, int mode, int attempt, cudaStream_t s);
 cudaError_t mi_setup();
 // Per-pair reduction and state update.
 enum FinMode { FIN_EXPLICIT = 0, FIN_RESET = 1, FIN_DECIDE = 2 };
+// attempt -1 with FIN_DECIDE: the pass of a graph attempt loop whose
+// condition handle is loop (see k_finalize).
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,
-                   cudaStream_t s);
+                   cudaStream_t s, cudaGraphConditionalHandle loop = 0);
 // Copy each pair's current field back to slot 0 when it sits in slot 1.
 int batch_sync_back(const Batch& b, cudaStream_t s);
+
 
 // Replace the calling thread's lm_last_error() message.
 void set_last_error(const char* msg);

@@ -21,7 +21,7 @@ namespace {
 constexpr int TPB = 256;
 
 __device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
-    return st->stopped || (attempt > 0 && st->done);
+    return st->stopped || (attempt_of(st, attempt) > 0 && st->done);
 }
 
 // Pooled curvature of Eq. tilen (tile side k > 1).  For every
@@ -474,9 +474,11 @@ __device__ __forceinline__ float block_max1024(float v, float* sh) {
 
 // One CTA per pair: fixed-order FP64 reduction of the pair's partials
 // (deterministic), then the per-mode state update.
-__global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
-                           DecideConsts d, int mode, int attempt,
-                           EvalOut* __restrict__ outs) {
+__device__ __forceinline__ void finalize_pair(const PairDesc* __restrict__ pd,
+                                              const Partials& part,
+                                              const DecideConsts& d, int mode,
+                                              int attempt,
+                                              EvalOut* __restrict__ outs) {
     __shared__ long long shl[32];
     __shared__ float shf[32];
     const PairDesc& P = pd[blockIdx.x];
@@ -548,10 +550,13 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
         st->evals = 1;
         st->log_pos = 0;
         st->stopped = 0;
+        st->att = 0;
+        st->att_runs = 0;
+        st->fin_count = 0u;
         return;
     }
     // FIN_DECIDE
-    const int j = attempt;
+    const int j = attempt_of(st, attempt);
     st->evals += 1;
     st->L_trial = L;
     st->gmax_trial = gmax;
@@ -617,6 +622,37 @@ __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
     }
 }
 
+// One CTA per pair: fixed-order reduction of the pair's partials, then the
+// per-mode state update.  With a graph attempt loop (loop != 0: attempt 0
+// runs unconditionally, then a graph WHILE node repeats trial, evaluation
+// and this kernel with attempt -1 while its condition holds) the last CTA
+// to finish, once every pair's decision is written, sets the next attempt
+// and the loop condition: another pass while some pair rejected its trial
+// with retries left (its decision left done = 0; acceptance and the
+// discard after the last retry set done = 1).  Without a rejection the
+// loop's body never runs; the attempt returns to 0 when the loop ends.
+__global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
+                           DecideConsts d, int mode, int attempt,
+                           EvalOut* __restrict__ outs, int npairs,
+                           cudaGraphConditionalHandle loop) {
+    finalize_pair(pd, part, d, mode, attempt, outs);
+    if (!loop || mode != FIN_DECIDE || threadIdx.x != 0) return;
+    DevState* st0 = pd[0].st;
+    __threadfence();   // this pair's decision before the count
+    if (atomicAdd(&st0->fin_count, 1u) != (unsigned)npairs - 1) return;
+    __threadfence();   // every pair's decision is visible
+    int any = 0;
+    for (int i = 0; i < npairs; ++i) {
+        const volatile DevState* s = pd[i].st;
+        if (!s->done && !s->stopped) any = 1;
+    }
+    const int next = any ? attempt_of(st0, attempt) + 1 : 0;
+    for (int i = 0; i < npairs; ++i) pd[i].st->att = next;
+    if (attempt < 0) st0->att_runs += 1;   // passes of the loop body
+    st0->fin_count = 0u;
+    cudaGraphSetConditional(loop, (any && next <= d.max_retries) ? 1u : 0u);
+}
+
 __global__ void k_copy_back(const PairDesc* __restrict__ pd, int npairs) {
     const PairDesc& P = pd[pair_of_block<4>(pd, npairs, blockIdx.x)];
     if (P.st->cu == 0) return;
@@ -664,9 +700,9 @@ int batch_step(const Batch& b, int attempt, cudaStream_t s) {
 }
 
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,
-                   cudaStream_t s) {
+                   cudaStream_t s, cudaGraphConditionalHandle loop) {
     k_finalize<<<b.npairs, 1024, 0, s>>>(b.pd, b.part, b.d, mode, attempt,
-                                         out);
+                                         out, b.npairs, loop);
     return 1;
 }
 

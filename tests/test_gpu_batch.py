@@ -220,3 +220,32 @@ def test_batch_equals_single_pair_bitwise(P, mode):
         info = P.lm_iterate(ctx, u, 8)
         assert info.loss == ib[i].loss and info.lambda_ == ib[i].lambda_
         assert torch.equal(u, ub[i]), i
+
+
+def test_batch_rejection_loop_matches_single_pairs(P):
+    """Eq. rejection in a batch: the graph's attempt loop keeps running
+    while any pair still retries, every other pair's later attempts are
+    no-ops, and each pair ends bitwise where a context of its own stepping
+    through lm_step (every attempt launched) ends."""
+    import torch
+    Fs, Ms = _pairs(seed0=120)
+    params = P.lm_default_params(lambda0=1e-3, step=3.0, reject=1, tau=1.0,
+                                 lambda_max=1.0, max_retries=3)
+    b = P.lm_batch_init(Fs, Ms, params)
+    ub = [torch.zeros((3,) + sh, device="cuda") for sh in SHAPES]
+    P.lm_batch_reset(b, ub)
+    ib = P.lm_batch_iterate(b, ub, 6)
+    retried = False
+    for i, sh in enumerate(SHAPES):
+        ctx = P.lm_init(Fs[i], Ms[i], params)
+        u = torch.zeros((3,) + sh, device="cuda")
+        P.lm_reset(ctx, u)
+        for _ in range(6):
+            info = P.lm_step(ctx, u)
+        retried = retried or any(r["retries"] > 0 for r in P.lm_get_log(ctx))
+        assert info.loss == ib[i].loss and info.lambda_ == ib[i].lambda_
+        assert info.retries == ib[i].retries
+        assert torch.equal(u, ub[i]), i
+        P.lm_destroy(ctx)
+    assert retried
+    P.lm_batch_destroy(b)

@@ -120,6 +120,40 @@ def test_lm_step_parity_rejection(P, oracle_mod):
     assert any(r > 0 for _, r in dec), dec
 
 
+@pytest.mark.parametrize("warp", [0.0, 1.0])
+def test_rejection_loop_matches_unrolled_attempts(P, warp):
+    """With rejection the graph-replayed iteration runs its attempts in a
+    graph WHILE loop that stops once every decision is taken; lm_step runs
+    every attempt as launched kernels that turn into no-ops.  Both give the
+    same trajectory bit for bit (retries included), and the loop launches
+    fewer kernels."""
+    import torch
+    import synth
+    F, M, _ = synth.blob_pair((24, 24, 24), seed=9)
+    params = P.lm_default_params(lambda0=1e-3, step=3.0, reject=1, tau=1.0,
+                                 lambda_max=1.0, max_retries=4,
+                                 sigma_warp=warp)
+    Ft, Mt = _t(F), _t(M)
+    ca, cb = P.lm_init(Ft, Mt, params), P.lm_init(Ft, Mt, params)
+    ua = torch.zeros((3, 24, 24, 24), device="cuda")
+    ub = torch.zeros_like(ua)
+    P.lm_reset(ca, ua)
+    P.lm_reset(cb, ub)
+    steps = [P.lm_step(ca, ua) for _ in range(10)]
+    P.lm_iterate(cb, ub, 10)
+    la, lb = P.lm_get_log(ca), P.lm_get_log(cb)
+    assert la == lb
+    assert any(r["retries"] > 0 for r in la), la
+    assert [r["retries"] for r in la] == [s.retries for s in steps]
+    assert torch.equal(ua, ub)
+    sa, sb = P.lm_get_state(ca), P.lm_get_state(cb)
+    assert sa.loss == sb.loss and sa.lambda_ == sb.lambda_
+    assert sa.evals == sb.evals
+    assert sb.kernel_launches < sa.kernel_launches
+    P.lm_destroy(ca)
+    P.lm_destroy(cb)
+
+
 def test_lm_step_parity_warp_smoothing(P, oracle_mod):
     import synth
     F, M, _ = synth.blob_pair((24, 24, 24), seed=10)
