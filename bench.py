@@ -422,7 +422,11 @@ def run_ours(args):
             Md.copy_(Mh, non_blocking=True)
         stream.synchronize()
         ctx2 = P.lm_init(Fd, Md, params, stream=stream)
-        P.lm_register(ctx2, levels, ud)            # warm-up (allocations)
+        if not args.no_autotune:
+            P.lm_autotune(ctx2, ud, reps=3)
+        # warm-up: allocations, and the coarse levels' contexts tune their
+        # work split when first used
+        P.lm_register(ctx2, levels, ud)
         n_e2e = max(1, min(args.steps, 3))
         vox = 0
         torch.cuda.synchronize()

@@ -325,8 +325,13 @@ LM_API int lm_batch_iterate(lm_batch *b, float *const *u, int n,
  * number of CTA waves split among the pairs in proportion to their voxels.
  * This call times reps evaluations at u (device fields, as for
  * lm_batch_eval) for every candidate (tile; E1 waves 1, 2, 4, 8; E2 waves
- * 2, 4, 8, 16 CTAs per SM in total) and keeps the fastest for all later
- * calls (the captured iteration graph is rebuilt).  Tile and waves change
+ * 2, 3, 4, 8, 16 CTAs per SM in total; at least 8 or 1 z slices per
+ * z-streaming CTA), then reps trial-field passes for 512, 1024, 2048 or
+ * 4096 step-kernel blocks per pair, and keeps the fastest for all later
+ * calls (the captured iteration graph is rebuilt).  The trial passes write
+ * only the trial slot and the resampling scratch, which the next iteration
+ * recomputes, so the optimiser state is unchanged.  lm_register tunes each
+ * coarse level's context this way when it first uses it.  Tile and waves change
  * the timing only: the loss is an exact integer sum and every gradient sum
  * has the same order under every choice.  e1_tile, e1_waves, e2_waves,
  * ms_best (host, may be NULL) receive the choice and its time per

@@ -395,7 +395,9 @@ struct Core {
 
 // Wave counts the autotuner tries (CTAs per SM in total for E1 and E2).
 constexpr int kE1Waves[] = {1, 2, 4, 8};
-constexpr int kE2Waves[] = {2, 4, 8, 16};
+constexpr int kE2Waves[] = {2, 3, 4, 8, 16};
+constexpr int kMinSlices[] = {8, 1};
+constexpr int kStepBlocks[] = {512, 1024, 2048, 4096};
 constexpr int kMaxE1Waves = 8, kMaxE2Waves = 16;
 
 // Creates a Core for npairs pairs (all of one dtype).
@@ -667,6 +669,7 @@ struct lm_ctx {
         void* Fl = nullptr;
         void* Ml = nullptr;
         float* ul = nullptr;
+        bool tuned = false;        // work split autotuned
     };
     std::vector<Level> levels;
     float* u_tmp = nullptr;      // full-res staging (3V floats)
@@ -996,6 +999,9 @@ extern "C" int lm_state_load(lm_ctx* c, const void* buf, size_t nbytes) {
 // ---------------------------------------------------------------------
 namespace {
 
+int core_autotune(Core* c, const float* const* u, int reps, int* e1_tile,
+                  int* e1_waves, int* e2_waves, double* ms_best);
+
 int check_schedule(const lm_schedule* s) {
     if (!s) return fail(LM_EINVAL, "schedule is NULL");
     if (s->nlevels < 1 || s->nlevels > LM_MAX_LEVELS)
@@ -1101,6 +1107,19 @@ extern "C" int lm_register(lm_ctx* c, const lm_schedule* s, float* u,
                 return fail(LM_ECUDA, "field resampling failed");
         }
         Core* k = lc->core.get();
+        if (f != 1) {
+            // a coarse level's context is tuned once, when first used: its
+            // volumes are small enough for the work split to decide the time
+            lm_ctx::Level* lv = nullptr;
+            for (auto& x : c->levels)
+                if (x.factor == f) lv = &x;
+            if (lv && !lv->tuned) {
+                if ((rc = core_autotune(k, &ul, 2, nullptr, nullptr, nullptr,
+                                        nullptr)) != LM_OK)
+                    return rc;
+                lv->tuned = true;
+            }
+        }
         if ((rc = core_reset(k, &ul)) != LM_OK) return rc;
         if ((rc = k->iterate(s->iters[l])) != LM_OK) return rc;
         if ((rc = k->read_states()) != LM_OK) return rc;
@@ -1184,9 +1203,11 @@ namespace {
 // Re-split the evaluation kernels' CTAs with the given wave counts and
 // moment-kernel tile; the captured iteration graph is dropped (its grids
 // change).
-int core_replan(Core* c, int e1w, int e2w, int tile) {
+int core_replan(Core* c, int e1w, int e2w, int tile, int min_slices,
+                int st_target) {
     BatchPlan plan = plan_batch(c->hpd.data(), c->npairs, c->p.win, c->num_sms,
-                                e1w, e2w, tile);
+                                e1w, e2w, tile, min_slices, st_target);
+
     if (plan.e1_ctas > c->e1_cap || plan.e2_ctas > c->e2_cap)
         return fail(LM_EINVAL, "plan exceeds the partial slots");
     c->b.plan = plan;
@@ -1217,6 +1238,12 @@ int core_autotune(Core* c, const float* const* u, int reps, int* e1_tile,
     for (int i = 0; i < c->npairs; ++i) {
         c->hpd[i].u_in = u[i];
         c->hpd[i].g_out = c->gsink[i];
+        // the trial passes read the current field: before any lm_reset
+        // there is none bound, so the tuning field stands in (between API
+        // calls the current field is always in slot 0 and the trial goes
+        // to the library's slot 1)
+        if (!c->hpd[i].u0)   // only read: with no reset the trial slot is 1
+            c->hpd[i].u0 = const_cast<float*>(u[i]);
     }
     if ((rc = c->push_table()) != LM_OK) return rc;
     batch_prepare(c->b, c->stream);
@@ -1224,14 +1251,16 @@ int core_autotune(Core* c, const float* const* u, int reps, int* e1_tile,
     LM_CK(cudaEventCreate(&e0));
     LM_CK(cudaEventCreate(&e1));
     double best = 1e300;
-    int bt = c->b.plan.e1_tile, b1 = 0, b2 = 0;
+    int bt = c->b.plan.e1_tile, b1 = 0, b2 = 0, bm = 8;
+    const int bs = c->b.plan.st_target;
     // the tile only matters to the LNCC moment kernel
     const int ntiles = c->p.loss == LM_LOSS_LNCC ? E1_NTILES : 1;
     for (int t = 0; t < ntiles && rc == LM_OK; ++t) {
         if (!e1_tile_ok(t, c->p.win)) continue;
+        for (int mn : kMinSlices)
         for (int w1 : kE1Waves)
             for (int w2 : kE2Waves) {
-                if ((rc = core_replan(c, w1, w2, t)) != LM_OK) break;
+                if ((rc = core_replan(c, w1, w2, t, mn, bs)) != LM_OK) break;
                 batch_eval(c->b, EVAL_EXPLICIT, 0, c->stream);   // warm-up
                 LM_CK(cudaEventRecord(e0, c->stream));
                 for (int r = 0; r < reps; ++r)
@@ -1245,15 +1274,49 @@ int core_autotune(Core* c, const float* const* u, int reps, int* e1_tile,
                     bt = t;
                     b1 = w1;
                     b2 = w2;
+                    bm = mn;
                 }
             }
+    }
+    // then the step kernel's z chunking, timed on its own (it writes only
+    // the trial slot and the resampling scratch, which the next iteration
+    // recomputes)
+    int bsb = bs;
+    if (rc == LM_OK && !c->have_reset) {
+        // no gradient computed yet: a zero step (the trial reads u from
+        // shared memory, as the usual sub-voxel steps do)
+        for (int i = 0; i < c->npairs; ++i) {
+            LM_CK(cudaMemsetAsync(c->hpd[i].g0, 0,
+                                  3 * (size_t)c->hpd[i].g.V * sizeof(float),
+                                  c->stream));
+            LM_CK(cudaMemsetAsync(c->hpd[i].g1, 0,
+                                  3 * (size_t)c->hpd[i].g.V * sizeof(float),
+                                  c->stream));
+        }
+    }
+    if (rc == LM_OK) {
+        double bst = 1e300;
+        for (int st : kStepBlocks) {
+            if ((rc = core_replan(c, b1, b2, bt, bm, st)) != LM_OK) break;
+            batch_step(c->b, 0, c->stream);   // warm-up
+            LM_CK(cudaEventRecord(e0, c->stream));
+            for (int r = 0; r < reps; ++r) batch_step(c->b, 0, c->stream);
+            LM_CK(cudaEventRecord(e1, c->stream));
+            LM_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / reps < bst) {
+                bst = ms / reps;
+                bsb = st;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LM_OK) return rc;
-    // restore the evaluation pointers, keep the chosen plan
+    // restore the table's pointers, keep the chosen plan
     c->hpd = save;
-    if ((rc = core_replan(c, b1, b2, bt)) != LM_OK) return rc;
+    if ((rc = core_replan(c, b1, b2, bt, bm, bsb)) != LM_OK) return rc;
     LM_CK(cudaStreamSynchronize(c->stream));
     LM_CK(cudaGetLastError());
     if (e1_tile) *e1_tile = bt;

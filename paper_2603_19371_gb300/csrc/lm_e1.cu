@@ -300,8 +300,7 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
         auto ld4 = [&](const int* base, int z, int k) -> int4 {
             return __ldg((const int4*)(base + z * qplane + zoff[k]));
         };
-        // moment slices m0 .. m1 - 1 feed the outputs z0 .. z1 - 1; the z
-        // sums start from zero K slices earlier (additions only until m0)
+        // moment slices m0 .. m1 - 1 feed the outputs z0 .. z1 - 1
         const int m0 = z0 - W, m1 = z1 + W;
         int4 pjn[NZS], pfn[NZS], pjo[NZS], pfo[NZS];
         const int4 zero4 = make_int4(0, 0, 0, 0);
@@ -317,9 +316,39 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
             ((longlong2*)(ZJJ + gy * C::SZL))[GU + zg4[k]] = make_longlong2(0, 0);
             ((longlong2*)(ZFJ + gy * C::SZL))[zg4[k]] = make_longlong2(0, 0);
             ((longlong2*)(ZFJ + gy * C::SZL))[GU + zg4[k]] = make_longlong2(0, 0);
-            pjn[k] = ld4(jq0, m0 - K + W, k);
-            pfn[k] = ld4(fq0, m0 - K + W, k);
-            pjo[k] = pfo[k] = zero4;
+        }
+        // the window of slice m0 - 1 (J slices m0 - W - 1 .. m0 + W - 1)
+        // into the z sums, three slices' loads in flight at a time
+        for (int c0 = 0; c0 < K; c0 += 3) {
+            int4 wj[3][NZS], wf[3][NZS];
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int k = 0; k < NZS; ++k) {
+                    const bool on = c0 + e < K && zsm[k] >= 0;
+                    wj[e][k] = on ? ld4(jq0, m0 - W - 1 + c0 + e, k) : zero4;
+                    wf[e][k] = on ? ld4(fq0, m0 - W - 1 + c0 + e, k) : zero4;
+                }
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int k = 0; k < NZS; ++k) {
+                    if (c0 + e >= K || zsm[k] < 0) continue;
+                    const int gy = zsm[k];
+                    zupdate<GU>(ZJ + gy * C::SZJ + 4 * zg4[k],
+                                (longlong2*)(ZJJ + gy * C::SZL),
+                                (longlong2*)(ZFJ + gy * C::SZL), zg4[k],
+                                wj[e][k], wf[e][k], zero4, zero4);
+                }
+        }
+        // slice m0's entering and leaving J slices
+#pragma unroll
+        for (int k = 0; k < NZS; ++k) {
+            if (zsm[k] < 0) continue;
+            pjn[k] = ld4(jq0, m0 + W, k);
+            pfn[k] = ld4(fq0, m0 + W, k);
+            pjo[k] = ld4(jq0, m0 - W - 1, k);
+            pfo[k] = ld4(fq0, m0 - W - 1, k);
         }
 
         // F's share of the moments at this thread's y units, one slice ahead
@@ -366,7 +395,7 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
             }
         };
 
-        for (int m = m0 - K, j = 0; m < m1; ++m) {
+        for (int m = m0, j = 0; m < m1; ++m) {
             // ---- Z: slide the z sums to the window of slice m, then
             //      request the next slice's values ----
 #pragma unroll
@@ -380,13 +409,10 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
                 if (m + 1 < m1) {
                     pjn[k] = ld4(jq0, m + 1 + W, k);
                     pfn[k] = ld4(fq0, m + 1 + W, k);
-                    if (m + 1 >= m0) {
-                        pjo[k] = ld4(jq0, m - W, k);
-                        pfo[k] = ld4(fq0, m - W, k);
-                    }
+                    pjo[k] = ld4(jq0, m - W, k);
+                    pfo[k] = ld4(fq0, m - W, k);
                 }
             }
-            if (m < m0) continue;   // warm-up: the z sums only (uniform)
             __syncthreads();
             // ---- X: sums along x over the moment columns ----
 #pragma unroll

@@ -721,13 +721,14 @@ int quant_bits(int win) {
 // pairs in proportion to their work, at least one CTA each, so that every
 // CTA works on one pair.
 static void split_ctas(const long long* work, int npairs, long long target,
-                       int* c0, int* n) {
+                       int min_work, int* c0, int* n) {
     long long tot = 0;
     for (int p = 0; p < npairs; ++p) tot += work[p];
     int acc = 0;
     for (int p = 0; p < npairs; ++p) {
         long long k = tot > 0 ? (target * work[p] + tot / 2) / tot : 1;
-        k = std::max<long long>(1, std::min<long long>(k, std::max<long long>(1, work[p] / 8)));
+        k = std::max<long long>(
+            1, std::min<long long>(k, std::max<long long>(1, work[p] / min_work)));
         c0[p] = acc;
         n[p] = (int)k;
         acc += (int)k;
@@ -740,8 +741,13 @@ bool e1_tile_ok(int t, int win) {
 }
 
 BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
-                     int e1_waves, int e2_waves, int e1_tile) {
+                     int e1_waves, int e2_waves, int e1_tile, int min_slices,
+                     int st_target) {
     BatchPlan bp{};
+    if (min_slices < 1) min_slices = 8;
+    if (st_target < 1) st_target = 2048;
+    bp.min_slices = min_slices;
+    bp.st_target = st_target;
     if (e1_tile < 0 || !e1_tile_ok(e1_tile, win)) e1_tile = E1_TILE_32X16;
     bp.e1_tile = e1_tile;
     const int tx1 = E1_OX, ty1 = e1_tile_oy(e1_tile);
@@ -762,19 +768,19 @@ BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
     if (e2_waves < 1) e2_waves = npairs == 1 ? 2 : 8;
     const long long t1 = (long long)e1_waves * num_sms;
     const long long t2 = (long long)e2_waves * num_sms;
-    split_ctas(w1.data(), npairs, t1, c0.data(), n.data());
+    split_ctas(w1.data(), npairs, t1, min_slices, c0.data(), n.data());
     for (int p = 0; p < npairs; ++p) {
         pd[p].e1_cta0 = c0[p];
         pd[p].e1_ncta = n[p];
     }
     bp.e1_ctas = c0[npairs - 1] + n[npairs - 1];
-    split_ctas(w2.data(), npairs, t2, c0.data(), n.data());
+    split_ctas(w2.data(), npairs, t2, min_slices, c0.data(), n.data());
     for (int p = 0; p < npairs; ++p) {
         pd[p].e2_cta0 = c0[p];
         pd[p].e2_ncta = n[p];
     }
     bp.e2_ctas = c0[npairs - 1] + n[npairs - 1];
-    // step kernel: 32 x 8 tiles, z chunks with ~2048 tiles per pair
+    // step kernel: 32 x 8 tiles, z chunks with ~st_target blocks per pair
     int blk = 0, lnb = 0;
     for (int p = 0; p < npairs; ++p) {
         Geom& g = pd[p].g;
@@ -782,7 +788,7 @@ BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
         pd[p].st_ty = (int)ceil_div(g.ny, 8);
         long long cols = (long long)pd[p].st_tx * pd[p].st_ty;
         long long nzc = std::max<long long>(
-            1, std::min<long long>(g.nz, ceil_div(2048, cols)));
+            1, std::min<long long>(g.nz, ceil_div(st_target, cols)));
         pd[p].st_zc = (int)ceil_div(g.nz, nzc);
         pd[p].st_nzc = (int)ceil_div(g.nz, pd[p].st_zc);
         pd[p].st_blk0 = blk;

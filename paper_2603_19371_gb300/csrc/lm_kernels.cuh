@@ -236,6 +236,10 @@ constexpr int MI_MAX_BINS = 64;
 struct BatchPlan {
     int e1_ctas, e2_ctas, st_blocks, ln_blocks, mm_ctas;
     int e1_tile;      // E1_TILE_* of the LNCC moment kernel
+    int min_slices;   // z slices a z-streaming CTA gets at least (where the
+                      // pair has that much work): long segments amortise the
+                      // pipeline's warm-up, short ones add parallelism
+    int st_target;    // step-kernel blocks per pair (z chunks of its tiles)
 };
 
 // Everything a launch needs besides the stream.
@@ -263,7 +267,8 @@ struct Batch {
 // per SM in total, split among the pairs in proportion to their work (0: the
 // defaults, 1 and 2 for a single pair, 4 and 8 for a batch).
 BatchPlan plan_batch(PairDesc* host_pd, int npairs, int win, int num_sms,
-                     int e1_waves = 0, int e2_waves = 0, int e1_tile = -1);
+                     int e1_waves = 0, int e2_waves = 0, int e1_tile = -1,
+                     int min_slices = 8, int st_target = 2048);
 // Whether the LNCC moment kernel has the tile variant t for window win.
 bool e1_tile_ok(int t, int win);
 

@@ -325,10 +325,12 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
                     v[1] = scale * (ia.y * gh0 + ia.w * gh1 + ib.x * gh2);
                     v[2] = scale * (ia.z * gh0 + ib.x * gh1 + ib.y * gh2);
                 } else {
-                    // n2 + lam >= lam > 0: the approximate division (about
-                    // 2 ulp) is safe
+                    // n2 + lam >= lam > 0 in every iteration: the
+                    // approximate division (about 2 ulp) is safe; a context
+                    // timed before its first reset (lambda 0, g 0) steps 0
                     const float n2 = gh0 * gh0 + gh1 * gh1 + gh2 * gh2;
-                    const float sc = __fdividef(scale, n2 + lam);
+                    const float den = n2 + lam;
+                    const float sc = den > 0.f ? __fdividef(scale, den) : 0.f;
                     v[0] = gh0 * sc;
                     v[1] = gh1 * sc;
                     v[2] = gh2 * sc;
