@@ -47,10 +47,11 @@ METRIC = "Gvoxel-iters/s"
 # 12, write u 12
 ITER_BYTES_PER_VOXEL = 68
 # DRAM bytes (read + write) per voxel of one iteration of the current
-# kernels, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-# of every kernel of an iteration at 128x160x192, k = 5, FP32), scaled by
-# voxels.  None whenever those kernels changed since the last capture.
-ITER_TRAFFIC_BYTES_PER_VOXEL = 128.4
+# kernels under the default plan, from an ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum of every kernel of an iteration at 128x160x192,
+# k = 5, FP32), scaled by voxels.  None whenever those kernels changed since
+# the last capture, and for other plans (--autotune).
+ITER_TRAFFIC_BYTES_PER_VOXEL = 98.7
 
 
 def _peaks():
@@ -334,9 +335,10 @@ def run_ours(args):
         u = torch.zeros((3,) + shape, device="cuda")
     stream.synchronize()
     ctx = P.lm_init(Ft, Mt, params, stream=stream)
-    # the tile shape and work split of the evaluation kernels, picked by
-    # timing (outside the timed region; results do not depend on it)
-    tune = P.lm_autotune(ctx, u, reps=3) if not args.no_autotune else None
+    # optionally the tile shape and work split picked by timing (outside the
+    # timed region; results do not depend on it); by default the library's
+    # default plan, the one the committed profiles describe
+    tune = P.lm_autotune(ctx, u, reps=3) if args.autotune else None
     P.lm_reset(ctx, u)
     P.lm_iterate(ctx, u, args.warmup, info=False)
     st0 = P.lm_get_state(ctx)
@@ -395,7 +397,7 @@ def run_ours(args):
                 "traffic": (ITER_TRAFFIC_BYTES_PER_VOXEL * V
                             if ITER_TRAFFIC_BYTES_PER_VOXEL and shape == SHAPE
                             and args.win == 5 and args.tile == 1
-                            and args.loss == "lncc"
+                            and args.loss == "lncc" and tune is None
                             else None),
                 "bytes_per_voxel": ITER_BYTES_PER_VOXEL,
                 "ms_iteration": ms_iter,
@@ -422,7 +424,7 @@ def run_ours(args):
             Md.copy_(Mh, non_blocking=True)
         stream.synchronize()
         ctx2 = P.lm_init(Fd, Md, params, stream=stream)
-        if not args.no_autotune:
+        if args.autotune:
             P.lm_autotune(ctx2, ud, reps=3)
         # warm-up: allocations, and the coarse levels' contexts tune their
         # work split when first used
@@ -959,8 +961,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default tile and work split")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the tile and work-split candidates first "
+                         "(lm_autotune) instead of the default plan")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the teacher-forced iteration against the oracle")
     ap.add_argument("--timed-ms", type=float, default=1000.0,
