@@ -55,8 +55,15 @@ struct E1Z {
     static constexpr int XW = MX % 4 == 0 ? 4 : 2;     // x-pass outputs / unit
     static constexpr int NXU = GY * (MX / XW);
     static constexpr int NXS = (NXU + NT - 1) / NT;
-    // y outputs per unit: the largest of 4, 3, 2 dividing MY = OY + 2W
-    static constexpr int YW = MY % 4 == 0 ? 4 : (MY % 3 == 0 ? 3 : 2);
+    // y outputs per unit: the divisor of MY = OY + 2W among 4, 3, 2 that
+    // gives the busiest thread the fewest moment points (ties: the larger,
+    // whose sliding sums share more loads)
+    static constexpr int ypts(int yw) {
+        return MY % yw ? 1 << 30 : (MX * (MY / yw) + NT - 1) / NT * yw;
+    }
+    static constexpr int YW = ypts(4) <= ypts(3) && ypts(4) <= ypts(2)
+                                  ? 4
+                                  : (ypts(3) <= ypts(2) ? 3 : 2);
     static constexpr int NYU = MX * (MY / YW);
     static constexpr int NYS = (NYU + NT - 1) / NT;
     static constexpr int NBU = 3 * MY * (OX / 4);      // coefficient x box
@@ -88,16 +95,28 @@ struct E1Z {
     static constexpr int B_XL = r16(GY * SXL * 8);
     static constexpr int B_C = r16(MY * MXP * 4);
     static constexpr int B_B = r16(MY * OX * 4);
+    // Pipelined schedule (two barriers per slice, the x-sum and x-box
+    // planes double-buffered) where its shared memory still lets the
+    // variant keep its CTAs per SM
+    static constexpr int bytes_for(int nb) {
+        return B_ZJ + 2 * B_ZL + nb * (B_XJ + 2 * B_XL) + 3 * B_C +
+               nb * 3 * B_B + K * 3 * NT * 8;
+    }
+    // (the 32 x 16 tile runs two CTAs per SM: past 96 KB each, the L1 left
+    // beside them throttles the gathers more than the barriers cost)
+    static constexpr bool PIPE = bytes_for(2) <= (TILE == 0 ? 96 : 226) * 1024;
+    static constexpr int NXB = PIPE ? 2 : 1;
     static constexpr int O_ZJ = 0;
     static constexpr int O_ZJJ = O_ZJ + B_ZJ;
     static constexpr int O_ZFJ = O_ZJJ + B_ZL;
-    static constexpr int O_XJ = O_ZFJ + B_ZL;
-    static constexpr int O_XJJ = O_XJ + B_XJ;
-    static constexpr int O_XFJ = O_XJJ + B_XL;
-    static constexpr int O_C = O_XFJ + B_XL;           // a, b, c planes
-    static constexpr int O_B = O_C + 3 * B_C;          // their x boxes
-    static constexpr int O_R = O_B + 3 * B_B;          // coefficient ring
+    static constexpr int O_XJ = O_ZFJ + B_ZL;            // [NXB] x-sum planes
+    static constexpr int O_XJJ = O_XJ + NXB * B_XJ;
+    static constexpr int O_XFJ = O_XJJ + NXB * B_XL;
+    static constexpr int O_C = O_XFJ + NXB * B_XL;       // a, b, c planes
+    static constexpr int O_B = O_C + 3 * B_C;            // [NXB] their x boxes
+    static constexpr int O_R = O_B + NXB * 3 * B_B;      // coefficient ring
     static constexpr int bytes = O_R + K * 3 * NT * 8;
+    static_assert(bytes == bytes_for(NXB), "layout");
 };
 
 // The int64 z-sum rows are held as 16-byte pairs of columns with the even
@@ -270,6 +289,10 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
 
     // out stage role: column ox, rows oy and oy + 1 of the output tile
     const int ox = tid % OX, oy = 2 * (tid / OX);
+    // y units: in the pipelined schedule they run beside the x units, which
+    // take the low threads, so they start from the high ones (whole warps
+    // keep whole groups of 32 units)
+    const int yunit = C::PIPE ? NT - 1 - tid : tid;
 
     long long lacc = 0;
     bool bad = false;
@@ -357,7 +380,7 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
         auto ld_mom = [&](int m) {
 #pragma unroll
             for (int s = 0; s < C::NYS; ++s) {
-                const int u = tid + s * NT;
+                const int u = yunit + s * NT;
                 int mx, my0;
                 ymap<C>(u, &mx, &my0);
                 const int x = x0 - W + mx;
@@ -395,9 +418,10 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
             }
         };
 
-        for (int m = m0, j = 0; m < m1; ++m) {
-            // ---- Z: slide the z sums to the window of slice m, then
-            //      request the next slice's values ----
+        int j = 0;   // ring slot of the next out stage's slice
+        // ---- Z: slide the z sums to the window of slice m, then request
+        //      the next slice's values ----
+        auto stage_z = [&](int m) {
 #pragma unroll
             for (int k = 0; k < NZS; ++k) {
                 if (zsm[k] < 0) continue;
@@ -413,33 +437,41 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
                     pfo[k] = ld4(fq0, m - W, k);
                 }
             }
-            __syncthreads();
-            // ---- X: sums along x over the moment columns ----
+        };
+        // ---- X: sums along x over the moment columns (x-sum buffer xb) ----
+        auto stage_x = [&](int xb) {
+            int* xj = XJ + xb * (C::B_XJ / 4);
+            long long* xjj = XJJ + xb * (C::B_XL / 8);
+            long long* xfj = XFJ + xb * (C::B_XL / 8);
 #pragma unroll
             for (int s = 0; s < C::NXS; ++s) {
                 const int u = tid + s * NT;
                 if (u >= C::NXU) break;
                 // consecutive lanes take consecutive rows (see the strides)
                 const int gy = u % C::GY, c0 = (u / C::GY) * XW;
-                xsum_i32<K, XW>(ZJ + gy * C::SZJ + c0, XJ + gy * C::SXJ + c0);
+                xsum_i32<K, XW>(ZJ + gy * C::SZJ + c0, xj + gy * C::SXJ + c0);
                 xsum_i64<K, XW, GU>((const longlong2*)(ZJJ + gy * C::SZL), c0,
-                                    XJJ + gy * C::SXL + c0);
+                                    xjj + gy * C::SXL + c0);
                 xsum_i64<K, XW, GU>((const longlong2*)(ZFJ + gy * C::SZL), c0,
-                                    XFJ + gy * C::SXL + c0);
+                                    xfj + gy * C::SXL + c0);
             }
-            __syncthreads();
-            // ---- Y: sums along y, cc, loss term, (a, b, c) ----
+        };
+        // ---- Y: sums along y, cc, loss term, (a, b, c) of slice m ----
+        auto stage_y = [&](int m, int xb) {
+            const int* xj = XJ + xb * (C::B_XJ / 4);
+            const long long* xjj = XJJ + xb * (C::B_XL / 8);
+            const long long* xfj = XFJ + xb * (C::B_XL / 8);
 #pragma unroll
             for (int s = 0; s < C::NYS; ++s) {
-                const int u = tid + s * NT;
+                const int u = yunit + s * NT;
                 if (u >= C::NYU) break;
                 int mx, my0;
                 ymap<C>(u, &mx, &my0);
                 int SJv[YW];
                 long long SJJv[YW], SFJv[YW];
-                ysum<K, YW, C::SXJ>(XJ + my0 * C::SXJ + mx, SJv);
-                ysum<K, YW, C::SXL>(XJJ + my0 * C::SXL + mx, SJJv);
-                ysum<K, YW, C::SXL>(XFJ + my0 * C::SXL + mx, SFJv);
+                ysum<K, YW, C::SXJ>(xj + my0 * C::SXJ + mx, SJv);
+                ysum<K, YW, C::SXL>(xjj + my0 * C::SXL + mx, SJJv);
+                ysum<K, YW, C::SXL>(xfj + my0 * C::SXL + mx, SFJv);
                 const int x = x0 - W + mx;
                 const bool xin = x >= 0 && x < g.nx;
                 const bool xout = mx >= W && mx < W + OX;
@@ -483,8 +515,11 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
             }
             // F's share of the next slice's moments
             if (m + 1 < m1) ld_mom(m + 1);
-            __syncthreads();
-            // ---- B: box of (a, b, c) along x, four outputs per unit ----
+        };
+        // ---- B: box of (a, b, c) along x, four outputs per unit (box
+        //      buffer bb) ----
+        auto stage_b = [&](int bb) {
+            float* bp = BP + bb * 3 * BPS;
 #pragma unroll
             for (int s = 0; s < C::NBS; ++s) {
                 const int u = tid + s * NT;
@@ -509,68 +544,100 @@ __global__ void __launch_bounds__(e1_tile_threads(TILE),
                 const float s1 = (s0 - v[0]) + v[K];
                 const float s2 = (s1 - v[1]) + v[K + 1];
                 const float s3 = (s2 - v[2]) + v[K + 2];
-                *(float4*)(BP + q * BPS + my * OX + c0) = make_float4(s0, s1, s2, s3);
+                *(float4*)(bp + q * BPS + my * OX + c0) = make_float4(s0, s1, s2, s3);
             }
-            __syncthreads();
-            // ---- out: box along y into the ring, along z, dL/dJ ----
-            {
+        };
+        // ---- out: box along y of slice m into the ring, along z, dL/dJ ----
+        auto stage_out = [&](int m, int bb) {
+            const float* bp = BP + bb * 3 * BPS;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float v[K + 1];
+#pragma unroll
+                for (int o = 0; o <= K; ++o)
+                    v[o] = bp[q * BPS + (oy + o) * OX + ox];
+                const float t0 = tree_sum<0, K>(v);
+                RG[(j * 3 + q) * NT + tid] = make_float2(t0, (t0 - v[0]) + v[K]);
+            }
+            // output slice zo = m - W once the ring holds the slices
+            // zo - W .. zo + W: slice zo - W + d sits in slot
+            // (j + 1 + d) mod K
+            const int zo = m - W;
+            if (zo >= z0) {
+                float cF[2], cJ[2], cd[2][3];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    cF[e] = (float)pFq[e] * iQ;
+                    cJ[e] = (float)pJq[e] * iQ;
+                    cd[e][0] = pdj[e][0];
+                    cd[e][1] = pdj[e][1];
+                    cd[e][2] = pdj[e][2];
+                }
+                if (zo + 1 < z1) ld_out(zo + 1);
+                float b3[3][2];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    float v[K + 1];
+                    float v0[K], v1[K];
 #pragma unroll
-                    for (int o = 0; o <= K; ++o)
-                        v[o] = BP[q * BPS + (oy + o) * OX + ox];
-                    const float t0 = tree_sum<0, K>(v);
-                    RG[(j * 3 + q) * NT + tid] = make_float2(t0, (t0 - v[0]) + v[K]);
+                    for (int d = 0; d < K; ++d) {
+                        int sl = j + 1 + d;
+                        sl = sl >= K ? sl - K : sl;
+                        const float2 t = RG[(sl * 3 + q) * NT + tid];
+                        v0[d] = t.x;
+                        v1[d] = t.y;
+                    }
+                    b3[q][0] = tree_sum<0, K>(v0);
+                    b3[q][1] = tree_sum<0, K>(v1);
                 }
-                // output slice zo = m - W once the ring holds the slices
-                // zo - W .. zo + W: slice zo - W + d sits in slot
-                // (j + 1 + d) mod K
-                const int zo = m - W;
-                if (zo >= z0) {
-                    float cF[2], cJ[2], cd[2][3];
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        cF[e] = (float)pFq[e] * iQ;
-                        cJ[e] = (float)pJq[e] * iQ;
-                        cd[e][0] = pdj[e][0];
-                        cd[e][1] = pdj[e][1];
-                        cd[e][2] = pdj[e][2];
-                    }
-                    if (zo + 1 < z1) ld_out(zo + 1);
-                    float b3[3][2];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        float v0[K], v1[K];
-#pragma unroll
-                        for (int d = 0; d < K; ++d) {
-                            int sl = j + 1 + d;
-                            sl = sl >= K ? sl - K : sl;
-                            const float2 t = RG[(sl * 3 + q) * NT + tid];
-                            v0[d] = t.x;
-                            v1[d] = t.y;
-                        }
-                        b3[q][0] = tree_sum<0, K>(v0);
-                        b3[q][1] = tree_sum<0, K>(v1);
-                    }
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        if (!ov[e]) continue;
-                        const float dLdJ =
-                            -inv_V * ((cF[e] * b3[0][e] + 2.f * cJ[e] * b3[1][e] +
-                                       b3[2][e]) *
-                                      c.inv_k3);
-                        const long long gi =
-                            (long long)(zo * g.ny + y0 + oy + e) * gpw + x0 + ox;
-                        graw[gi] = dLdJ * cd[e][0];
-                        graw[gcs + gi] = dLdJ * cd[e][1];
-                        graw[2 * gcs + gi] = dLdJ * cd[e][2];
-                    }
-                } else if (zo + 1 == z0) {
-                    ld_out(z0);
+                for (int e = 0; e < 2; ++e) {
+                    if (!ov[e]) continue;
+                    const float dLdJ =
+                        -inv_V * ((cF[e] * b3[0][e] + 2.f * cJ[e] * b3[1][e] +
+                                   b3[2][e]) *
+                                  c.inv_k3);
+                    const long long gi =
+                        (long long)(zo * g.ny + y0 + oy + e) * gpw + x0 + ox;
+                    graw[gi] = dLdJ * cd[e][0];
+                    graw[gcs + gi] = dLdJ * cd[e][1];
+                    graw[2 * gcs + gi] = dLdJ * cd[e][2];
                 }
+            } else if (zo + 1 == z0) {
+                ld_out(z0);
             }
             j = j + 1 == K ? 0 : j + 1;
+        };
+
+        if constexpr (C::PIPE) {
+            // Round t: Z(t) | X(t) and Y(t - 1) | B(t - 1) and out(t - 2).
+            // The x sums of consecutive slices and the x boxes alternate
+            // between two buffers, so every hazard is crossed by one of the
+            // two barriers: X(t) reads Z(t) after the first, Z(t + 1)
+            // rewrites the z sums after the second; Y(t - 1) reads X(t - 1)
+            // and rewrites the (a, b, c) planes after B(t - 2) read them;
+            // B(t - 1) reads them after the second; out(t - 2) reads the box
+            // B(t - 2) wrote a round earlier.
+            for (int t = m0; t < m1 + 2; ++t) {
+                if (t < m1) stage_z(t);
+                __syncthreads();
+                if (t < m1) stage_x(t & 1);
+                if (t > m0 && t <= m1) stage_y(t - 1, (t - 1) & 1);
+                __syncthreads();
+                if (t > m0 && t <= m1) stage_b((t - 1) & 1);
+                if (t >= m0 + 2) stage_out(t - 2, t & 1);
+            }
+        } else {
+            for (int m = m0; m < m1; ++m) {
+                stage_z(m);
+                __syncthreads();
+                stage_x(0);
+                __syncthreads();
+                stage_y(m, 0);
+                __syncthreads();
+                stage_b(0);
+                __syncthreads();
+                stage_out(m, 0);
+            }
         }
         __syncthreads();   // the planes are rewritten by the next segment
     }

@@ -748,7 +748,10 @@ BatchPlan plan_batch(PairDesc* pd, int npairs, int win, int num_sms,
     if (st_target < 1) st_target = 2048;
     bp.min_slices = min_slices;
     bp.st_target = st_target;
-    if (e1_tile < 0 || !e1_tile_ok(e1_tile, win)) e1_tile = E1_TILE_32X16;
+    // default: the 32 x 32 tile for k = 5 and 7 (a smaller share of halo
+    // rows, and the pipelined schedule at k = 5)
+    if (e1_tile < 0 || !e1_tile_ok(e1_tile, win))
+        e1_tile = win == 5 || win == 7 ? E1_TILE_32X32 : E1_TILE_32X16;
     bp.e1_tile = e1_tile;
     const int tx1 = E1_OX, ty1 = e1_tile_oy(e1_tile);
     std::vector<long long> w1(npairs), w2(npairs);

@@ -1,19 +1,21 @@
 // The learned warm start (include/lmunet.h): a 3-D U-Net trained on the
 // optimizer's own fields.  Every convolution runs as an implicit GEMM on the
-// tensor cores (bfloat16 operands, FP32 accumulation):
+// 5th-generation tensor cores (tcgen05.mma, bfloat16 operands, FP32
+// accumulator in tensor memory, one issuing thread per CTA):
 //
-//   forward / data gradient (tcgen05.mma, accumulator in tensor memory):
-//     rows = voxels, columns = output channels, reduction k = (tap, input
-//     channel); the data gradient is the forward convolution of dy with the
-//     weights flipped in space and transposed in channels.
-//   weight gradient (warp-level mma.sync m16n8k16): rows = output channels,
-//     columns = (tap, input channel), reduction over voxels, split over
-//     voxel chunks and accumulated with FP32 atomics.
+//   forward / data gradient: rows = voxels, columns = output channels,
+//     reduction k = (tap, input channel), operands K-major; the data
+//     gradient is the forward convolution of dy with the weights flipped
+//     in space and transposed in channels.
+//   weight gradient: rows = (tap, input channel), columns = output
+//     channels, reduction over voxels, operands MN-major; split over voxel
+//     chunks and accumulated into dw with FP32 atomics.
 //
 // Activations are channels-last bfloat16 ([D][H][W][C], C innermost), so a
-// 16-channel slice of one voxel is one 32-byte load; the A tile of the
-// forward GEMM is gathered with cp.async (zero fill outside the volume) in a
-// three-stage pipeline.  Pooling, upsampling, concatenation, the loss and
+// 16-channel slice of one voxel is one 32-byte load; both kernels gather
+// their tiles with cp.async (zero fill outside the volume) into a 4-stage
+// shared-memory ring, two tiles ahead of the MMA, with per-stage
+// tcgen05.commit barriers.  Pooling, upsampling, concatenation, the loss and
 // Adam are plain element-wise kernels.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
