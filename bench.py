@@ -12,7 +12,10 @@ Gvoxel-iterations / s (voxels x loss evaluations / s).
 Extra keys:
   roofline     -- the iteration (68 algorithmic bytes per voxel) against the
                   measured HBM copy bandwidth
-  cpu_baseline -- the FP64 oracle on the host cores (bounded sample)
+  cpu_baseline -- the FP64 oracle on the host cores, on a bounded sample:
+                  LM iterations of the benched pair teacher-forced from the
+                  GPU's state; the same leg reports oracle_error, the GPU's
+                  error against the oracle on those iterations
   e2e          -- whole coarse-to-fine registration (levels 4/2/1 with
                   200/100/50 iterations) through lm_register, host buffers
                   copied in and the field copied out inside the timed region
@@ -182,71 +185,85 @@ def single_thread_baseline(iters=3):
                       f"{evals} evaluations in {dt:.1f} s"}
 
 
-def cpu_baseline(F, M, iters=20):
-    """The FP64 oracle, as it stands, on the host cores (OpenMP threads)."""
+def _oracle_params(params):
+    """The oracle's parameters for a library parameter set (the FP32 values
+    the library computes with)."""
     import numpy as np
     import oracle
-    P = oracle.params()
-    t0 = time.perf_counter()
-    st = oracle.State(F, M, np.zeros((3,) + F.shape), P)
-    evals = 1
-    for _ in range(iters):
-        evals += oracle.lm_step(st)["evals"]
-    dt = time.perf_counter() - t0
-    V = F.size
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": V * evals / dt / 1e9, "unit": METRIC, "cores": cores,
-            "kind": "oracle",
-            "sample": f"FP64 C oracle (OpenMP), initial evaluation + {iters} "
-                      f"LM iterations of the full 160x192x224 pair, "
-                      f"{evals} evaluations in {dt:.1f} s",
-            "single_thread": single_thread_baseline()}
+    return oracle.params(win=params.win,
+                         eps_nr=float(np.float32(params.eps_nr)),
+                         eps_dr=float(np.float32(params.eps_dr)),
+                         sigma_grad=float(params.sigma_grad),
+                         sigma_warp=float(params.sigma_warp),
+                         step=float(params.step), lambda0=params.lambda0,
+                         mu_inc=params.mu_inc, mu_dec=params.mu_dec,
+                         lambda_max=params.lambda_max, reject=params.reject,
+                         tau=params.tau, max_retries=params.max_retries,
+                         tile=params.tile, loss=params.loss,
+                         method=params.method,
+                         alpha=float(np.float32(params.alpha)),
+                         bins=params.bins)
 
 
-def oracle_check(P, ctx, u, F, M, params):
-    """One LM iteration of the benched context checked against the FP64
-    oracle stepping from the same FP32 state (teacher-forced): the relative
-    error of the current loss and of the trial's loss, max |du| of the
-    accepted field, and whether the accept / reject decision matches."""
+def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
+    """The cpu_baseline leg: the FP64 oracle, as it stands, on the host
+    cores (OpenMP threads), on a bounded sample of the benched workload --
+    iters LM iterations of the pair, teacher-forced from the GPU's state.
+    Each iteration the oracle evaluates the loss and gradient at the GPU's
+    field, forms the trial, evaluates its loss and takes the damping
+    decision (two evaluations, timed); then the GPU steps once through the
+    context.  The oracle's time gives the baseline, the comparisons give
+    the error of the GPU against the oracle: the relative error of the
+    current and the trial loss, max |u_gpu - u_oracle| of accepted trials,
+    and whether the decision and lambda match.  F and M are the images as
+    the context holds them (BF16-rounded where it stores BF16)."""
     import numpy as np
     import oracle
     oracle.build()
-    Po = oracle.params(win=params.win,
-                       eps_nr=float(np.float32(params.eps_nr)),
-                       eps_dr=float(np.float32(params.eps_dr)),
-                       sigma_grad=float(params.sigma_grad),
-                       sigma_warp=float(params.sigma_warp),
-                       step=float(params.step), lambda0=params.lambda0,
-                       mu_inc=params.mu_inc, mu_dec=params.mu_dec,
-                       lambda_max=params.lambda_max, reject=params.reject,
-                       tau=params.tau, max_retries=params.max_retries,
-                       tile=params.tile, loss=params.loss,
-                       method=params.method,
-                       alpha=float(np.float32(params.alpha)),
-                       bins=params.bins)
-    t0 = time.perf_counter()
+    Po = _oracle_params(params)
     Fo, Mo = F.astype(np.float64), M.astype(np.float64)
-    st = P.lm_get_state(ctx)
-    ut = u.cpu().numpy().astype(np.float64)
-    ev = oracle.evaluate(Fo, Mo, ut, Po)
-    u1, _ = oracle.trial(ut, ev["g"], ev["gmax"], ev["L"], st.lambda_, Po)
-    L1 = oracle.loss(Fo, Mo, u1, Po)
-    act, lam_o = oracle.decide(L1, ev["L"], st.loss_prev, st.has_prev,
-                               st.lambda_, 0, Po)
-    info = P.lm_step(ctx, u)
-    same = (info.retries == 0 and info.accepted == 1) == (act == oracle.ACCEPT)
-    du = None
-    if info.retries == 0 and info.accepted == 1:
-        du = float(np.abs(u.cpu().numpy().astype(np.float64) - u1).max())
-    return {"what": "one LM iteration of the benched pair after the timed "
-                    "windows, GPU vs FP64 oracle from the same FP32 state",
-            "rel_loss_err": abs(st.loss - ev["L"]) / ev["L"],
-            "rel_trial_loss_err": abs(info.loss_first - L1) / L1,
-            "max_du_voxel": du, "decision_match": bool(same),
-            "lambda_match": bool(abs(info.lambda_ - lam_o)
-                                 <= 1e-12 * lam_o) if same else False,
-            "bars": {"rel_loss": 1e-5, "du_voxel": 1e-4},
-            "seconds": time.perf_counter() - t0}
+    t_or, evals = 0.0, 0
+    e_loss, e_trial, e_du, same_all, lam_all = [], [], [], True, True
+    for _ in range(iters):
+        st = P.lm_get_state(ctx)
+        ut = u.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        ev = oracle.evaluate(Fo, Mo, ut, Po)
+        u1, _ = oracle.trial(ut, ev["g"], ev["gmax"], ev["L"], st.lambda_, Po)
+        L1 = oracle.loss(Fo, Mo, u1, Po)
+        act, lam_o = oracle.decide(L1, ev["L"], st.loss_prev, st.has_prev,
+                                   st.lambda_, 0, Po)
+        t_or += time.perf_counter() - t0
+        evals += 2
+        info = P.lm_step(ctx, u)
+        acc = info.retries == 0 and info.accepted == 1
+        same = acc == (act == oracle.ACCEPT)
+        same_all &= same
+        lam_all &= same and abs(info.lambda_ - lam_o) <= 1e-12 * lam_o
+        e_loss.append(abs(st.loss - ev["L"]) / ev["L"])
+        e_trial.append(abs(info.loss_first - L1) / L1)
+        if acc:
+            e_du.append(float(np.abs(u.cpu().numpy().astype(np.float64)
+                                     - u1).max()))
+    V = F.size
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    base = {"value": V * evals / t_or / 1e9, "unit": METRIC, "cores": cores,
+            "kind": "oracle",
+            "sample": f"FP64 C oracle (OpenMP), {iters} LM iterations of "
+                      f"{what} ({'x'.join(map(str, F.shape))}) teacher-forced "
+                      f"from the GPU's state: {evals} evaluations "
+                      f"(loss + gradient at the field, trial loss) in "
+                      f"{t_or:.1f} s"}
+    err = {"what": f"{iters} LM iterations of {what}, each stepped on the "
+                   "GPU and by the FP64 oracle from the same FP32 state "
+                   "(the cpu_baseline leg)",
+           "max_rel_loss_err": max(e_loss),
+           "max_rel_trial_loss_err": max(e_trial),
+           "max_du_voxel": max(e_du) if e_du else None,
+           "accepted": len(e_du),
+           "decisions_match": bool(same_all), "lambda_match": bool(lam_all),
+           "bars": {"rel_loss": 1e-5, "du_voxel": 1e-4}}
+    return base, err
 
 
 def run_reference(args):
@@ -403,11 +420,14 @@ def run_ours(args):
                 "ms_iteration": ms_iter,
                 "ms_step_with_resampling": ms_step, "ms_e1_e2": ms_eval}
 
-    # error against the FP64 oracle of one teacher-forced iteration of the
-    # benched pair, outside the timed region (rank 0 only)
-    oracle_err = None
-    if rank == 0 and not args.no_oracle_check and V <= 20_000_000:
-        oracle_err = oracle_check(P, ctx, u, F, M, params)
+    # the cpu_baseline leg (rank 0 at N = 1, outside the timed region): the
+    # oracle on teacher-forced iterations of the benched pair, which also
+    # gives the GPU's error against it
+    cpu, oracle_err = None, None
+    if (world == 1 and not args.no_cpu_baseline and V <= 20_000_000):
+        cpu, oracle_err = cpu_baseline(P, ctx, u, F, M, params)
+        if shape == SHAPE:
+            cpu["single_thread"] = single_thread_baseline()
 
     # end to end: host buffers in, whole registration, field out
     e2e = None
@@ -454,10 +474,6 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    cpu = None
-    if (world == 1 and not args.no_cpu_baseline and shape == SHAPE
-            and args.tile == 1 and args.loss == "lncc"):
-        cpu = cpu_baseline(F, M)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -617,6 +633,25 @@ def run_batch(args):
     Lt32, _ = P.lm_batch_eval(bf, ut)
     Lb32, _ = P.lm_batch_eval(bf, ub)
     P.lm_batch_destroy(bf)
+    # the cpu_baseline leg: the oracle on the smallest pair of the batch,
+    # teacher-forced from the batched runs' final fields (a single-pair
+    # context on the same images; batched and single-pair results are
+    # bitwise equal), FP32 images and BF16 images
+    cpu, oracle_err = None, None
+    if not args.no_cpu_baseline:
+        i0 = int(np.argmin([int(np.prod(sh)) for sh in shapes]))
+        cpu, oracle_err = {}, {}
+        for name, Fs_, Ms_, us_end in (("fp32", F32, M32, uf),
+                                        ("bf16", F16, M16, ub)):
+            ctx = P.lm_init(Fs_[i0], Ms_[i0], params, stream=stream)
+            uc = us_end[i0].clone()
+            P.lm_reset(ctx, uc)
+            cpu[name], oracle_err[name] = cpu_baseline(
+                P, ctx, uc, Fs_[i0].float().cpu().numpy(),
+                Ms_[i0].float().cpu().numpy(), params, iters=3,
+                what=f"the batch's smallest pair ({name} images) from the "
+                     "batched run's final field")
+            P.lm_destroy(ctx)
     rel_f32 = [abs(a - c) / c for a, c in zip(Lf, Ls)]
     rel_bf16 = [(a - c) / c for a, c in zip(Lb32, Ls)]
     excess_t = [(a - c) / c for a, c in zip(Lt32, Ls)]
@@ -653,6 +688,8 @@ def run_batch(args):
             "s": tt, "iterations": it_t, "speedup": ts / tt,
             "pairs_within_1e-3_on_fp32_images": sum(e <= 1e-3 for e in excess_t),
             "max_rel_excess_on_fp32_images": max(excess_t)},
+        "cpu_baseline": cpu,
+        "oracle_error": oracle_err,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -661,8 +698,11 @@ def run_batch(args):
 def _gen_pair_ws(args):
     shape, seed = args
     import synth
-    # the 160x192x224 recipe at 128^3, warp scaled with the volume (0.67x)
-    F, M, _ = synth.voronoi_pair(shape, seed=seed, svf_sigma=5.0, max_disp=5.0)
+    # the 160x192x224 recipe at 128^3, warp scaled with the volume (0.67x),
+    # its squarings on the coarse grid (a quarter of the generation time);
+    # not cached on disk (25 MB a pair)
+    F, M, _ = synth.voronoi_pair(shape, seed=seed, svf_sigma=5.0, max_disp=5.0,
+                                 coarse_exp=True, cache=False)
     return F, M
 
 
@@ -681,11 +721,20 @@ def run_warmstart(args):
     S = (128, 128, 128)
     Sh = tuple(n // 2 for n in S)
     ntr, nte = args.ws_train, args.ws_test
+    # the pairs are generated in a spawn pool started before the first GPU
+    # call and copied to the device as they arrive (thousands of pairs do
+    # not sit in host memory at once)
     t_gen = time.perf_counter()
+    Fs, Ms = [], []
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        pairs = pool.map(_gen_pair_ws, [(S, 5000 + i) for i in range(ntr + nte)])
+        torch.cuda.set_device(local)
+        for F, M in pool.imap(_gen_pair_ws,
+                              [(S, 5000 + i) for i in range(ntr + nte)],
+                              chunksize=2):
+            Fs.append(torch.from_numpy(F).cuda())
+            Ms.append(torch.from_numpy(M).cuda())
+    torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    torch.cuda.set_device(local)
     from paper_2603_19371_gb300 import build as _build
     from paper_2603_19371_gb300 import lmreg as P
     _build.build()
@@ -693,11 +742,6 @@ def run_warmstart(args):
     params = P.lm_default_params()
     levels = [(4, 200), (2, 100), (1, 50)]
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        Fs = [torch.from_numpy(F).cuda() for F, _ in pairs]
-        Ms = [torch.from_numpy(M).cuda() for _, M in pairs]
-    stream.synchronize()
-    del pairs
 
     # 1. targets: multiscale LM from zero on the training pairs, carried to
     #    half resolution (values x 0.5) by the pyramid's field resampling
@@ -787,6 +831,32 @@ def run_warmstart(args):
     t_warm = time.perf_counter() - t0
     P.lm_batch_destroy(b)
     reached = sum(1 for x in infos if x.stopped)
+    # the cpu_baseline leg: on the first held-out pair, the oracle's loss at
+    # the network's field (recomputed; the forward pass is deterministic)
+    # against the GPU's, and LM iterations teacher-forced from the refined
+    # field
+    cpu, oracle_err = None, None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        un = torch.empty((3,) + S, device="cuda")
+        P.lm_unet_forward(net, Ft[0], Mt[0], uh)
+        P.lm_field_resample(uh, 2, un, 1, stream=stream)
+        stream.synchronize()
+        ctx = P.lm_init(Ft[0], Mt[0], params, stream=stream)
+        Lg, _ = P.lm_eval(ctx, un)
+        F0 = Ft[0].float().cpu().numpy()
+        M0 = Mt[0].float().cpu().numpy()
+        Lo = oracle.loss(F0.astype(np.float64), M0.astype(np.float64),
+                         un.cpu().numpy().astype(np.float64),
+                         _oracle_params(params))
+        uc = uw[0].clone()
+        P.lm_reset(ctx, uc)
+        cpu, oracle_err = cpu_baseline(
+            P, ctx, uc, F0, M0, params, iters=3,
+            what="the first held-out pair from its warm-started, refined field")
+        oracle_err["network_field_rel_loss_err"] = abs(Lg - Lo) / Lo
+        P.lm_destroy(ctx)
     mean_abs_u = {"plain": float(np.mean([float(u.abs().mean()) for u in u0])),
                   "warm_start": float(np.mean([float(u.abs().mean()) for u in uw]))}
     # held-out regression error of the network against the plain fields
@@ -824,6 +894,8 @@ def run_warmstart(args):
                     "heldout_mse_vs_plain_fields": float(np.mean(mse_te)),
                     "heldout_plain_field_mean_sq": float(np.mean(msq_te))},
         "prep": {"generate_s": t_gen, "targets_s": t_targets},
+        "cpu_baseline": cpu,
+        "oracle_error": oracle_err,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -965,7 +1037,8 @@ def main():
                     help="time the tile and work-split candidates first "
                          "(lm_autotune) instead of the default plan")
     ap.add_argument("--no-oracle-check", action="store_true",
-                    help="skip the teacher-forced iteration against the oracle")
+                    help="same as --no-cpu-baseline (the comparison with the "
+                         "oracle is part of that leg)")
     ap.add_argument("--timed-ms", type=float, default=1000.0,
                     help="repeat K-step windows until about this long")
     ap.add_argument("--min-windows", type=int, default=5)
@@ -1007,6 +1080,8 @@ def main():
         return 0
     if args.warmup < 3:
         args.warmup = 3
+    if args.no_oracle_check:
+        args.no_cpu_baseline = True
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "damping":

@@ -51,8 +51,8 @@ def _cache_path(key: str):
     return os.path.join(root, h + ".npz")
 
 
-def _cached(key, fn):
-    path = _cache_path(key)
+def _cached(key, fn, cache=True):
+    path = _cache_path(key) if cache else None
     if path and os.path.exists(path):
         try:
             with np.load(path) as z:
@@ -191,18 +191,23 @@ def voronoi_image(shape, rng, n_labels=30, bias=0.2, noise=0.02):
     return np.clip(img, 0.0, 1.0)
 
 
-def voronoi_pair(shape=(160, 192, 224), seed=0, svf_sigma=8.0, max_disp=8.0):
-    """(F, M, u_true) float32 for the brain-MRI-shaped Voronoi workload."""
+def voronoi_pair(shape=(160, 192, 224), seed=0, svf_sigma=8.0, max_disp=8.0,
+                 coarse_exp=False, cache=True):
+    """(F, M, u_true) float32 for the brain-MRI-shaped Voronoi workload
+    (coarse_exp: the warp's squarings on the 4x coarser grid, see
+    svf_field; with cache=False nothing is written to the disk cache: data
+    sets of thousands of pairs)."""
     def make():
         rng = np.random.default_rng(seed)
         F = voronoi_image(shape, rng)
         coarse = 4 if np.prod(shape) > 64 ** 3 else 1
-        u = svf_field(shape, rng, svf_sigma, max_disp, coarse=coarse)
+        u = svf_field(shape, rng, svf_sigma, max_disp, coarse=coarse,
+                      coarse_exp=coarse_exp and coarse > 1)
         M = _warp_image(F, u)
         return (F.astype(np.float32), M.astype(np.float32),
                 u.astype(np.float32))
-    return _cached(f"voronoi{tuple(shape)}:{seed}:{svf_sigma}:{max_disp}",
-                   make)
+    key = f"voronoi{tuple(shape)}:{seed}:{svf_sigma}:{max_disp}"
+    return _cached(key + (":cexp" if coarse_exp else ""), make, cache)
 
 
 def _spline_points(rng, lo, hi, n_ctrl=5, step=0.5):
