@@ -17,6 +17,8 @@
 // shared-memory ring, two tiles ahead of the MMA, with per-stage
 // tcgen05.commit barriers.  Pooling, upsampling, concatenation, the loss and
 // Adam are plain element-wise kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -330,6 +332,238 @@ __global__ void __launch_bounds__(128)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(
                          tmem),
                      "r"(C::COLS)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------------
+// Forward convolution with TMA-fed operands, for inputs whose channel
+// count is a multiple of 16 and whose x-y planes tile into runs of 128
+// voxels (W a multiple of 128, or W dividing 128 and H a multiple of
+// 128 / W).  The M tile is 128 consecutive voxels of one z plane: R =
+// 128 / TX rows of TX = min(W, 128) voxels.  For tap (dz, dy, dx) and a
+// group of CB channels (CB = 64, 32 or 16, the largest dividing cin) its A
+// operand is that tile displaced by the tap, which one TMA tiled load of
+// the channels-last activations reads directly: the box {CB channels, TX,
+// R, 1} at (c0, x0 + dx, y0 + dy, z + dz) lands as 128 rows of 2 CB bytes
+// in the canonical K-major layout with the 2 CB-byte swizzle (32, 64 or
+// 128 B), which is the pattern the MMA's shared-memory descriptor of the
+// same swizzle reads; the CB / 16 MMAs of the stage start 32 bytes apart
+// within the rows.  TMA reads every point outside the volume as zero, the
+// convolution's zero padding.  The tap's weights arrive the same way (box
+// {CB channels, 1 tap, BN outputs} of w[cout][27][cin]).  Whole-voxel rows
+// keep the number of TMA requests per operand byte low.  One thread
+// issues the loads into a ring of stages and a second one the MMAs; full
+// mbarriers (TMA transaction bytes) and empty mbarriers (tcgen05.commit)
+// order them, so the loop has no block barrier.  Every wait is bounded; a
+// timeout writes NaN.
+// ---------------------------------------------------------------------
+template <int BN, int CB>
+struct TmaCfg {
+    static_assert(CB == 16 || CB == 32 || CB == 64, "swizzle spans");
+    static constexpr int r1k(int b) { return (b + 1023) / 1024 * 1024; }
+    static constexpr int A_BYTES = 128 * CB * 2;
+    static constexpr int B_BYTES = BN * CB * 2;
+    static constexpr int B_OFF = r1k(A_BYTES);        // swizzle atoms aligned
+    static constexpr int STAGE = r1k(B_OFF + B_BYTES);
+    // as many stages as fit about 96 KB (two CTAs per SM), 2 .. 6
+    static constexpr int CS = 96 * 1024 / STAGE < 2 ? 2
+                              : (96 * 1024 / STAGE > 6 ? 6 : 96 * 1024 / STAGE);
+    static constexpr int bytes = 1024 + CS * STAGE;
+    static constexpr int SBO = 8 * CB * 2;             // 8-row groups
+    // shared-memory descriptor layout codes: 128 B = 2, 64 B = 4, 32 B = 6
+    static constexpr unsigned long long LAYOUT = CB == 64 ? 2 : (CB == 32 ? 4 : 6);
+};
+
+__device__ __forceinline__ unsigned long long umma_desc_sw(unsigned addr,
+                                                           unsigned sbo,
+                                                           unsigned long long layout) {
+    unsigned long long d = (unsigned long long)((addr >> 4) & 0x3FFF);
+    d |= 1ull << 16;   // leading byte offset (unused by swizzled K-major)
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;   // descriptor version; base offset 0
+    d |= layout << 61;
+    return d;
+}
+
+__device__ __forceinline__ void un_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                     su32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void un_tma_4d(void* dst, const CUtensorMap* map, int c0,
+                                          int c1, int c2, int c3,
+                                          unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_"
+        "tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(su32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void un_tma_3d(void* dst, const CUtensorMap* map, int c0,
+                                          int c1, int c2, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_"
+        "tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(su32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(su32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void un_commit(unsigned long long* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+        "[%0];\n" ::"r"(su32(bar))
+        : "memory");
+}
+
+template <int BN, int CB, bool OUTF32>
+__global__ void __launch_bounds__(128)
+    k_conv_fwd_tma(const __grid_constant__ CUtensorMap xm,
+                   const __grid_constant__ CUtensorMap wm,
+                   const float* __restrict__ bias, void* __restrict__ y, int H,
+                   int W, int cin, int cout, int act) {
+    using C = TmaCfg<BN, CB>;
+    constexpr int CS = C::CS;
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+    __shared__ __align__(8) unsigned long long full[CS], empty[CS], done;
+    __shared__ unsigned tmem_slot;
+    __shared__ int bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long v0 = (long long)blockIdx.x * 128;
+    const int n0 = blockIdx.y * BN;
+    const long long plane = (long long)H * W;
+    const int z = (int)(v0 / plane);
+    const int rem = (int)(v0 - (long long)z * plane);
+    const int y0 = rem / W, x0 = rem - y0 * W;
+    const int cpt = cin / CB, nk = 27 * cpt;
+
+    if (warp == 0) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                su32(&tmem_slot)),
+            "r"(TcCfg<BN>::COLS)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::
+                         : "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < CS; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&full[b]))
+                         : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&empty[b]))
+                         : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&done))
+                     : "memory");
+        bad = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    if (tid == 0) {
+        // producer: step s = (tap, channel group) into stage s mod CS, once
+        // the MMAs of step s - CS have read that stage
+        int s = 0;
+        for (; s < nk; ++s) {
+            const int st = s % CS;
+            if (s >= CS && !tc_wait(&empty[st], (unsigned)(((s / CS) - 1) & 1))) {
+                bad = 1;
+                break;
+            }
+            const int tap = s / cpt, c0 = (s - tap * cpt) * CB;
+            int dz, dy, dx;
+            tap_offset(tap, dz, dy, dx);
+            unsigned char* A = sm + st * C::STAGE;
+            un_expect_tx(&full[st], C::A_BYTES + C::B_BYTES);
+            un_tma_4d(A, &xm, c0, x0 + dx, y0 + dy, z + dz, &full[st]);
+            un_tma_3d(A + C::B_OFF, &wm, c0, tap, n0, &full[st]);
+        }
+        // every load issued has landed before the CTA can leave (they have,
+        // unless a wait above gave up)
+        for (int st = 0; st < CS && st < s; ++st) {
+            const int last = st + ((s - 1 - st) / CS) * CS;
+            tc_wait(&full[st], (unsigned)((last / CS) & 1));
+        }
+    } else if (tid == 32) {
+        // MMA issuer: CB / 16 MMAs per stage, 32 bytes apart along K
+        for (int s = 0; s < nk; ++s) {
+            const int st = s % CS;
+            if (!tc_wait(&full[st], (unsigned)((s / CS) & 1))) {
+                bad = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned a0 = su32(sm + st * C::STAGE);
+#pragma unroll
+            for (int k = 0; k < CB / 16; ++k) {
+                const unsigned long long ad =
+                    umma_desc_sw(a0 + 32 * k, C::SBO, C::LAYOUT);
+                const unsigned long long bd =
+                    umma_desc_sw(a0 + C::B_OFF + 32 * k, C::SBO, C::LAYOUT);
+                const unsigned accf = (s > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                        tmem),
+                    "l"(ad), "l"(bd), "r"(TcCfg<BN>::IDESC), "r"(accf)
+                    : "memory");
+            }
+            un_commit(&empty[st]);
+        }
+        // arrives once every MMA issued above has completed
+        un_commit(&done);
+    }
+    __syncwarp();
+    bool ok = tc_wait(&done, 0u);
+    __syncthreads();
+    ok = ok && !bad;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const long long v = v0 + warp * 32 + lane;   // this thread's TMEM lane
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        unsigned r[16];
+        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+              "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+              "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        float o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float t = __uint_as_float(r[j]) + (bias ? bias[n0 + c0 + j] : 0.f);
+            if (act) t = t > 0.f ? t : SLOPE * t;
+            o[j] = ok ? t : __int_as_float(0x7fc00000);
+        }
+        if (OUTF32) {
+            float4* dst = reinterpret_cast<float4*>((float*)y + v * cout + n0 + c0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                dst[j] = make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
+        } else {
+            __nv_bfloat162 h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+            uint4* dst = reinterpret_cast<uint4*>((bf16*)y + v * cout + n0 + c0);
+            dst[0] = *reinterpret_cast<uint4*>(&h[0]);
+            dst[1] = *reinterpret_cast<uint4*>(&h[4]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(
+                         tmem),
+                     "r"(TcCfg<BN>::COLS)
                      : "memory");
 }
 
@@ -819,11 +1053,109 @@ void pick_tc(const bf16* x, const bf16* w, const float* bias, void* y, int D,
     else launch_tc<16, C2, F>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
 }
 
+// N tile of the TMA-fed forward (the same choice as pick_tc)
+int pick_bn(int cout) {
+    if (cout == 16 || cout == 32 || cout == 64 || cout == 96 || cout == 192)
+        return cout;
+    if (cout % 128 == 0) return 128;
+    if (cout % 64 == 0) return 64;
+    if (cout % 32 == 0) return 32;
+    return 16;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    return encode;
+}
+
+// Channel group of the TMA-fed forward: the largest of 64, 32, 16 that
+// divides cin (rows of 128, 64 or 32 bytes, each its own swizzle span).
+int pick_cb(int cin) { return cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16); }
+
+// Tensor maps of the TMA-fed forward: the activations x[D][H][W][cin] with
+// the box {CB channels, TX, R, 1}, the weights w[cout][27][cin] with the
+// box {CB channels, 1, BN}, both with the 2 CB-byte swizzle; false where
+// the shape does not qualify or the driver refuses a map (the gathering
+// kernel runs instead).
+bool conv_maps(CUtensorMap* xm, CUtensorMap* wm, const bf16* x, const bf16* w,
+               int D, int H, int W, int cin, int cout, int bn, int cb) {
+    if (cin % 16 != 0 || ((size_t)x & 15) || ((size_t)w & 15)) return false;
+    if (!(W % 128 == 0 || (128 % W == 0 && H % (128 / W) == 0))) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const CUtensorMapSwizzle sw = cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : cb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_32B;
+    const int TX = W < 128 ? W : 128, R = 128 / TX;
+    const cuuint64_t e = sizeof(bf16);
+    cuuint64_t xd[4] = {(cuuint64_t)cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
+    cuuint64_t xs[3] = {cin * e, (cuuint64_t)W * cin * e, (cuuint64_t)H * W * cin * e};
+    cuuint32_t xb[4] = {(cuuint32_t)cb, (cuuint32_t)TX, (cuuint32_t)R, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(xm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)x, xd, xs, xb, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    cuuint64_t wd[3] = {(cuuint64_t)cin, 27, (cuuint64_t)cout};
+    cuuint64_t wsd[2] = {cin * e, 27 * cin * e};
+    cuuint32_t wb[3] = {(cuuint32_t)cb, 1, (cuuint32_t)bn};
+    return enc(wm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)w, wd, wsd, wb, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, bool F>
+void launch_tma_b(const CUtensorMap& xm, const CUtensorMap& wm, const float* bias,
+                  void* y, const dim3& grid, int H, int W, int cin, int cout,
+                  int act, int cb, cudaStream_t s) {
+    if (cb == 64)
+        k_conv_fwd_tma<BN, 64, F><<<grid, 128, TmaCfg<BN, 64>::bytes, s>>>(
+            xm, wm, bias, y, H, W, cin, cout, act);
+    else if (cb == 32)
+        k_conv_fwd_tma<BN, 32, F><<<grid, 128, TmaCfg<BN, 32>::bytes, s>>>(
+            xm, wm, bias, y, H, W, cin, cout, act);
+    else
+        k_conv_fwd_tma<BN, 16, F><<<grid, 128, TmaCfg<BN, 16>::bytes, s>>>(
+            xm, wm, bias, y, H, W, cin, cout, act);
+}
+
+template <bool F>
+void launch_tma(const CUtensorMap& xm, const CUtensorMap& wm, const float* bias,
+                void* y, long long V, int H, int W, int cin, int cout, int act,
+                int bn, int cb, cudaStream_t s) {
+    const dim3 grid((unsigned)(V / 128), (unsigned)(cout / bn));
+    switch (bn) {
+        case 16: launch_tma_b<16, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
+        case 32: launch_tma_b<32, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
+        case 64: launch_tma_b<64, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
+        case 96: launch_tma_b<96, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
+        case 128: launch_tma_b<128, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
+        default: launch_tma_b<192, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
+    }
+}
+
 int conv_forward(const bf16* x, const bf16* w, const float* bias, void* y,
                  bool out_f32, int D, int H, int W, int cin, int cout, int act,
                  cudaStream_t s) {
     const long long V = (long long)D * H * W;
     const int gx = (int)((V + 127) / 128);
+    CUtensorMap xm, wm;
+    const int bn = pick_bn(cout), cb = pick_cb(cin);
+    if (cin != 2 && conv_maps(&xm, &wm, x, w, D, H, W, cin, cout, bn, cb)) {
+        if (out_f32) launch_tma<true>(xm, wm, bias, y, V, H, W, cin, cout, act, bn, cb, s);
+        else launch_tma<false>(xm, wm, bias, y, V, H, W, cin, cout, act, bn, cb, s);
+        return 1;
+    }
     if (cin == 2) {
         if (out_f32) pick_tc<true, true>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
         else pick_tc<true, false>(x, w, bias, y, D, H, W, cin, cout, act, gx, s);
@@ -851,6 +1183,34 @@ cudaError_t attrs_tc() {
     if ((r = attr_tc<192, C2, F>()) != cudaSuccess) e = r;
     return e;
 }
+template <int BN, bool F>
+cudaError_t attr_tma() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = cudaFuncSetAttribute(k_conv_fwd_tma<BN, 16, F>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TmaCfg<BN, 16>::bytes)) != cudaSuccess)
+        e = r;
+    if ((r = cudaFuncSetAttribute(k_conv_fwd_tma<BN, 32, F>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TmaCfg<BN, 32>::bytes)) != cudaSuccess)
+        e = r;
+    if ((r = cudaFuncSetAttribute(k_conv_fwd_tma<BN, 64, F>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TmaCfg<BN, 64>::bytes)) != cudaSuccess)
+        e = r;
+    return e;
+}
+template <bool F>
+cudaError_t attrs_tma() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = attr_tma<16, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tma<32, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tma<64, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tma<96, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tma<128, F>()) != cudaSuccess) e = r;
+    if ((r = attr_tma<192, F>()) != cudaSuccess) e = r;
+    return e;
+}
 template <int BN, bool C2>
 cudaError_t attr_wg() {
     return cudaFuncSetAttribute(k_conv_wgrad_tc<BN, C2>,
@@ -876,6 +1236,8 @@ cudaError_t conv_setup() {
         if ((r = attrs_tc<false, true>()) != cudaSuccess) e = r;
         if ((r = attrs_tc<true, false>()) != cudaSuccess) e = r;
         if ((r = attrs_tc<true, true>()) != cudaSuccess) e = r;
+        if ((r = attrs_tma<false>()) != cudaSuccess) e = r;
+        if ((r = attrs_tma<true>()) != cudaSuccess) e = r;
         if ((r = attrs_wg<false>()) != cudaSuccess) e = r;
         if ((r = attrs_wg<true>()) != cudaSuccess) e = r;
         return e;

@@ -57,11 +57,23 @@ def _w_internal(w):
     return np.ascontiguousarray(w.reshape(co, ci, 27).transpose(0, 2, 1))
 
 
+# the odd shapes take the gathering kernel; the rest (channels a multiple
+# of 16, x-y planes that tile into runs of 128 voxels) the TMA-fed one:
+# W = 16 / 32 / 64 (several rows per tile), 128 (one row) and 256 (half a
+# row), every one with a zero-padded border on all six faces
 @pytest.mark.parametrize("shape,cin,cout", [((5, 6, 7), 16, 16),
                                             ((5, 6, 7), 2, 32),
                                             ((9, 10, 11), 32, 64),
                                             ((4, 8, 12), 64, 128),
-                                            ((6, 6, 6), 192, 64)])
+                                            ((6, 6, 6), 192, 64),
+                                            ((4, 8, 16), 16, 32),
+                                            ((3, 4, 32), 32, 64),
+                                            ((2, 2, 64), 64, 16),
+                                            ((3, 2, 128), 16, 16),
+                                            ((2, 3, 256), 32, 96),
+                                            ((3, 8, 16), 192, 64),
+                                            ((2, 8, 16), 96, 192),
+                                            ((2, 8, 16), 128, 128)])
 def test_conv3d_forward_matches_oracle(P, oracle_mod, shape, cin, cout):
     import torch
     from oracle import unet as U
@@ -89,7 +101,9 @@ def test_conv3d_forward_matches_oracle(P, oracle_mod, shape, cin, cout):
                                             ((5, 6, 7), 2, 16),
                                             ((9, 10, 11), 32, 64),
                                             ((6, 6, 6), 192, 64),
-                                            ((8, 8, 8), 96, 32)])
+                                            ((8, 8, 8), 96, 32),
+                                            ((4, 8, 16), 32, 16),
+                                            ((3, 4, 32), 64, 32)])
 def test_conv3d_backward_matches_oracle(P, oracle_mod, shape, cin, cout):
     import torch
     from oracle import unet as U
