@@ -357,18 +357,33 @@ __global__ void __launch_bounds__(128)
 // order them, so the loop has no block barrier.  Every wait is bounded; a
 // timeout writes NaN.
 // ---------------------------------------------------------------------
-template <int BN, int CB>
+constexpr int CONV_MAXCS = 6;   // ring stages at most
+constexpr int CONV_MAXMT = 4;   // M tiles per CTA at most
+
+// Shared-memory layout of the TMA-fed forward.  A stage holds the A rows of
+// each of the CTA's mt tiles, then the weights of its NX taps; every
+// operand starts on a 1024-byte boundary (whole swizzle atoms).
+template <int BN, int CB, bool XM = false>
 struct TmaCfg {
     static_assert(CB == 16 || CB == 32 || CB == 64, "swizzle spans");
     static constexpr int r1k(int b) { return (b + 1023) / 1024 * 1024; }
-    static constexpr int A_BYTES = 128 * CB * 2;
-    static constexpr int B_BYTES = BN * CB * 2;
-    static constexpr int B_OFF = r1k(A_BYTES);        // swizzle atoms aligned
-    static constexpr int STAGE = r1k(B_OFF + B_BYTES);
-    // as many stages as fit about 96 KB (two CTAs per SM), 2 .. 6
-    static constexpr int CS = 96 * 1024 / STAGE < 2 ? 2
-                              : (96 * 1024 / STAGE > 6 ? 6 : 96 * 1024 / STAGE);
-    static constexpr int bytes = 1024 + CS * STAGE;
+    // XM: the three taps along x share one load of 130 voxels
+    static constexpr int NX = XM ? 3 : 1;
+    static constexpr int A_BYTES = (XM ? 130 : 128) * CB * 2;   // one tile
+    static constexpr int A_PAD = r1k(A_BYTES);
+    static constexpr int B_BYTES = BN * CB * 2;                 // one tap
+    static constexpr int B_PAD = r1k(NX * B_BYTES);
+    __host__ __device__ static constexpr int stage(int mt) { return mt * A_PAD + B_PAD; }
+    // as many stages as fit about 100 KB (two CTAs per SM), 2 .. CONV_MAXCS
+    __host__ __device__ static constexpr int stages(int mt) {
+        return 100 * 1024 / stage(mt) < 2
+                   ? 2
+                   : (100 * 1024 / stage(mt) > CONV_MAXCS ? CONV_MAXCS
+                                                          : 100 * 1024 / stage(mt));
+    }
+    __host__ __device__ static constexpr int bytes(int mt) {
+        return 1024 + stages(mt) * stage(mt);
+    }
     static constexpr int SBO = 8 * CB * 2;             // 8-row groups
     // shared-memory descriptor layout codes: 128 B = 2, 64 B = 4, 32 B = 6
     static constexpr unsigned long long LAYOUT = CB == 64 ? 2 : (CB == 32 ? 4 : 6);
@@ -415,34 +430,33 @@ __device__ __forceinline__ void un_commit(unsigned long long* bar) {
         : "memory");
 }
 
-template <int BN, int CB, bool OUTF32>
+template <int BN, int CB, bool OUTF32, bool XM>
 __global__ void __launch_bounds__(128)
     k_conv_fwd_tma(const __grid_constant__ CUtensorMap xm,
                    const __grid_constant__ CUtensorMap wm,
                    const float* __restrict__ bias, void* __restrict__ y, int H,
-                   int W, int cin, int cout, int act) {
-    using C = TmaCfg<BN, CB>;
-    constexpr int CS = C::CS;
+                   int W, int cin, int cout, int act, int mt, int ncols) {
+    using C = TmaCfg<BN, CB, XM>;
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
-    __shared__ __align__(8) unsigned long long full[CS], empty[CS], done;
+    __shared__ __align__(8) unsigned long long full[CONV_MAXCS], empty[CONV_MAXCS], done;
     __shared__ unsigned tmem_slot;
     __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long v0 = (long long)blockIdx.x * 128;
+    // this CTA's tiles: mt consecutive runs of 128 voxels from vb
+    const long long vb = (long long)blockIdx.x * mt * 128;
     const int n0 = blockIdx.y * BN;
     const long long plane = (long long)H * W;
-    const int z = (int)(v0 / plane);
-    const int rem = (int)(v0 - (long long)z * plane);
-    const int y0 = rem / W, x0 = rem - y0 * W;
-    const int cpt = cin / CB, nk = 27 * cpt;
+    const int CS = C::stages(mt), STG = C::stage(mt);
+    // steps: (tap, channel group), or with XM (tap row, channel group)
+    const int cpt = cin / CB, nk = (XM ? 9 : 27) * cpt;
 
     if (warp == 0) {
         asm volatile(
             "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                 su32(&tmem_slot)),
-            "r"(TcCfg<BN>::COLS)
+            "r"(ncols)
             : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::
                          : "memory");
@@ -466,21 +480,54 @@ __global__ void __launch_bounds__(128)
 
     if (tid == 0) {
         // producer: step s = (tap, channel group) into stage s mod CS, once
-        // the MMAs of step s - CS have read that stage
-        int s = 0;
+        // the MMAs of step s - CS have read that stage; the weights of a
+        // step serve all mt tiles.  The tiles' origins are computed once.
+        int tz[CONV_MAXMT], ty[CONV_MAXMT], tx[CONV_MAXMT];
+#pragma unroll
+        for (int j = 0; j < CONV_MAXMT; ++j) {
+            const long long v0 = vb + 128LL * (j < mt ? j : 0);
+            tz[j] = (int)(v0 / plane);
+            const int rem = (int)(v0 - (long long)tz[j] * plane);
+            ty[j] = rem / W;
+            tx[j] = rem - ty[j] * W;
+        }
+        // s = round * CS + st, s = g * cpt + cg (counters, no divisions)
+        int s = 0, st = 0, round = 0, g = 0, cg = 0;
         for (; s < nk; ++s) {
-            const int st = s % CS;
-            if (s >= CS && !tc_wait(&empty[st], (unsigned)(((s / CS) - 1) & 1))) {
+            if (round > 0 && !tc_wait(&empty[st], (unsigned)((round - 1) & 1))) {
                 bad = 1;
                 break;
             }
-            const int tap = s / cpt, c0 = (s - tap * cpt) * CB;
+            const int c0 = cg * CB;
+            unsigned char* S0 = sm + st * STG;
+            un_expect_tx(&full[st], mt * C::A_BYTES + C::NX * C::B_BYTES);
             int dz, dy, dx;
-            tap_offset(tap, dz, dy, dx);
-            unsigned char* A = sm + st * C::STAGE;
-            un_expect_tx(&full[st], C::A_BYTES + C::B_BYTES);
-            un_tma_4d(A, &xm, c0, x0 + dx, y0 + dy, z + dz, &full[st]);
-            un_tma_3d(A + C::B_OFF, &wm, c0, tap, n0, &full[st]);
+            if (XM) {
+                // taps 3 g .. 3 g + 2 (dx = -1, 0, 1): voxels x0 - 1 .. x0 + 128
+                dz = g / 3 - 1;
+                dy = g % 3 - 1;
+                dx = -1;
+            } else {
+                tap_offset(g, dz, dy, dx);
+            }
+#pragma unroll
+            for (int j = 0; j < CONV_MAXMT; ++j)
+                if (j < mt)
+                    un_tma_4d(S0 + j * C::A_PAD, &xm, c0, tx[j] + dx, ty[j] + dy,
+                              tz[j] + dz, &full[st]);
+            unsigned char* Bs = S0 + mt * C::A_PAD;
+#pragma unroll
+            for (int kx = 0; kx < C::NX; ++kx)
+                un_tma_3d(Bs + kx * C::B_BYTES, &wm, c0, XM ? 3 * g + kx : g, n0,
+                          &full[st]);
+            if (++cg == cpt) {
+                cg = 0;
+                ++g;
+            }
+            if (++st == CS) {
+                st = 0;
+                ++round;
+            }
         }
         // every load issued has landed before the CTA can leave (they have,
         // unless a wait above gave up)
@@ -489,30 +536,39 @@ __global__ void __launch_bounds__(128)
             tc_wait(&full[st], (unsigned)((last / CS) & 1));
         }
     } else if (tid == 32) {
-        // MMA issuer: CB / 16 MMAs per stage, 32 bytes apart along K
-        for (int s = 0; s < nk; ++s) {
-            const int st = s % CS;
-            if (!tc_wait(&full[st], (unsigned)((s / CS) & 1))) {
+        // MMA issuer: per tile, NX taps x CB / 16 MMAs (32 bytes apart
+        // along K; tap kx of an XM stage reads the rows kx .. kx + 127)
+        for (int s = 0, st = 0, round = 0; s < nk; ++s) {
+            if (!tc_wait(&full[st], (unsigned)(round & 1))) {
                 bad = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const unsigned a0 = su32(sm + st * C::STAGE);
+            const unsigned s0 = su32(sm + st * STG);
+            const unsigned b0 = s0 + mt * C::A_PAD;
+            for (int j = 0; j < mt; ++j) {
+                const unsigned a0 = s0 + j * C::A_PAD;
 #pragma unroll
-            for (int k = 0; k < CB / 16; ++k) {
-                const unsigned long long ad =
-                    umma_desc_sw(a0 + 32 * k, C::SBO, C::LAYOUT);
-                const unsigned long long bd =
-                    umma_desc_sw(a0 + C::B_OFF + 32 * k, C::SBO, C::LAYOUT);
-                const unsigned accf = (s > 0 || k > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                        tmem),
-                    "l"(ad), "l"(bd), "r"(TcCfg<BN>::IDESC), "r"(accf)
-                    : "memory");
+                for (int q = 0; q < C::NX * (CB / 16); ++q) {
+                    const int kx = q / (CB / 16), k = q - kx * (CB / 16);
+                    const unsigned long long ad =
+                        umma_desc_sw(a0 + kx * CB * 2 + 32 * k, C::SBO, C::LAYOUT);
+                    const unsigned long long bd = umma_desc_sw(
+                        b0 + kx * C::B_BYTES + 32 * k, C::SBO, C::LAYOUT);
+                    const unsigned accf = (s > 0 || q > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                            tmem + (unsigned)(j * BN)),
+                        "l"(ad), "l"(bd), "r"(TcCfg<BN>::IDESC), "r"(accf)
+                        : "memory");
+                }
             }
             un_commit(&empty[st]);
+            if (++st == CS) {
+                st = 0;
+                ++round;
+            }
         }
         // arrives once every MMA issued above has completed
         un_commit(&done);
@@ -522,40 +578,44 @@ __global__ void __launch_bounds__(128)
     __syncthreads();
     ok = ok && !bad;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const long long v = v0 + warp * 32 + lane;   // this thread's TMEM lane
+    for (int j = 0; j < mt; ++j) {
+        const long long v = vb + 128LL * j + warp * 32 + lane;   // TMEM lane
 #pragma unroll
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-        unsigned r[16];
-        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
-              "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
-              "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        float o[16];
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            unsigned r[16];
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) +
+                                   (unsigned)(j * BN + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+                  "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+                  "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            float o[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            float t = __uint_as_float(r[j]) + (bias ? bias[n0 + c0 + j] : 0.f);
-            if (act) t = t > 0.f ? t : SLOPE * t;
-            o[j] = ok ? t : __int_as_float(0x7fc00000);
-        }
-        if (OUTF32) {
-            float4* dst = reinterpret_cast<float4*>((float*)y + v * cout + n0 + c0);
+            for (int e = 0; e < 16; ++e) {
+                float t = __uint_as_float(r[e]) + (bias ? bias[n0 + c0 + e] : 0.f);
+                if (act) t = t > 0.f ? t : SLOPE * t;
+                o[e] = ok ? t : __int_as_float(0x7fc00000);
+            }
+            if (OUTF32) {
+                float4* dst = reinterpret_cast<float4*>((float*)y + v * cout + n0 + c0);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                dst[j] = make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
-        } else {
-            __nv_bfloat162 h[8];
+                for (int e = 0; e < 4; ++e)
+                    dst[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
+            } else {
+                __nv_bfloat162 h[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
-            uint4* dst = reinterpret_cast<uint4*>((bf16*)y + v * cout + n0 + c0);
-            dst[0] = *reinterpret_cast<uint4*>(&h[0]);
-            dst[1] = *reinterpret_cast<uint4*>(&h[4]);
+                for (int e = 0; e < 8; ++e)
+                    h[e] = __floats2bfloat162_rn(o[2 * e], o[2 * e + 1]);
+                uint4* dst = reinterpret_cast<uint4*>((bf16*)y + v * cout + n0 + c0);
+                dst[0] = *reinterpret_cast<uint4*>(&h[0]);
+                dst[1] = *reinterpret_cast<uint4*>(&h[4]);
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -563,7 +623,7 @@ __global__ void __launch_bounds__(128)
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(
                          tmem),
-                     "r"(TcCfg<BN>::COLS)
+                     "r"(ncols)
                      : "memory");
 }
 
@@ -1088,7 +1148,7 @@ int pick_cb(int cin) { return cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16); }
 // the shape does not qualify or the driver refuses a map (the gathering
 // kernel runs instead).
 bool conv_maps(CUtensorMap* xm, CUtensorMap* wm, const bf16* x, const bf16* w,
-               int D, int H, int W, int cin, int cout, int bn, int cb) {
+               int D, int H, int W, int cin, int cout, int bn, int cb, bool xmrg) {
     if (cin % 16 != 0 || ((size_t)x & 15) || ((size_t)w & 15)) return false;
     if (!(W % 128 == 0 || (128 % W == 0 && H % (128 / W) == 0))) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
@@ -1100,7 +1160,8 @@ bool conv_maps(CUtensorMap* xm, CUtensorMap* wm, const bf16* x, const bf16* w,
     const cuuint64_t e = sizeof(bf16);
     cuuint64_t xd[4] = {(cuuint64_t)cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
     cuuint64_t xs[3] = {cin * e, (cuuint64_t)W * cin * e, (cuuint64_t)H * W * cin * e};
-    cuuint32_t xb[4] = {(cuuint32_t)cb, (cuuint32_t)TX, (cuuint32_t)R, 1};
+    cuuint32_t xb[4] = {(cuuint32_t)cb, (cuuint32_t)(xmrg ? TX + 2 : TX),
+                        (cuuint32_t)R, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     if (enc(xm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)x, xd, xs, xb, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1114,34 +1175,85 @@ bool conv_maps(CUtensorMap* xm, CUtensorMap* wm, const bf16* x, const bf16* w,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, bool F>
-void launch_tma_b(const CUtensorMap& xm, const CUtensorMap& wm, const float* bias,
+int num_sms() {
+    static int n = [] {
+        int d = 0, v = 0;
+        if (cudaGetDevice(&d) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+            cudaGetLastError();
+            v = 148;
+        }
+        return v;
+    }();
+    return n;
+}
+
+// M tiles per CTA: 4 or 2 where the tiles divide evenly, at least 16 CTAs
+// per SM remain, the accumulators fit 128 TMEM columns and a stage 40 KB
+// (setup, the pipeline's fill and the weights' loads are shared by the
+// tiles: it pays for the short reductions of the 128^3 level, where fewer,
+// longer CTAs lose less than they save); else 1.
+template <int BN, int CB, bool XM>
+int pick_mt(long long ntiles) {
+    using C = TmaCfg<BN, CB, XM>;
+    for (int m = CONV_MAXMT; m > 1; m /= 2)
+        if (ntiles % m == 0 && ntiles / m >= 16LL * num_sms() && m * BN <= 128 &&
+            C::stage(m) <= 40 * 1024)
+            return m;
+    return 1;
+}
+
+template <int BN, int CB, bool F, bool XM>
+void launch_tma1(const CUtensorMap& xm, const CUtensorMap& wm, const float* bias,
+                 void* y, long long ntiles, int nt, int H, int W, int cin, int cout,
+                 int act, cudaStream_t s) {
+    using C = TmaCfg<BN, CB, XM>;
+    const int mt = pick_mt<BN, CB, XM>(ntiles);
+    int ncols = 32;
+    while (ncols < mt * BN) ncols *= 2;
+    const dim3 grid((unsigned)(ntiles / mt), (unsigned)nt);
+    k_conv_fwd_tma<BN, CB, F, XM><<<grid, 128, C::bytes(mt), s>>>(
+        xm, wm, bias, y, H, W, cin, cout, act, mt, ncols);
+}
+
+template <int BN, bool F, bool XM>
+void launch_tma_x(const CUtensorMap& xm, const CUtensorMap& wm, const float* bias,
                   void* y, const dim3& grid, int H, int W, int cin, int cout,
                   int act, int cb, cudaStream_t s) {
     if (cb == 64)
-        k_conv_fwd_tma<BN, 64, F><<<grid, 128, TmaCfg<BN, 64>::bytes, s>>>(
-            xm, wm, bias, y, H, W, cin, cout, act);
+        launch_tma1<BN, 64, F, XM>(xm, wm, bias, y, grid.x, grid.y, H, W, cin, cout,
+                                   act, s);
     else if (cb == 32)
-        k_conv_fwd_tma<BN, 32, F><<<grid, 128, TmaCfg<BN, 32>::bytes, s>>>(
-            xm, wm, bias, y, H, W, cin, cout, act);
+        launch_tma1<BN, 32, F, XM>(xm, wm, bias, y, grid.x, grid.y, H, W, cin, cout,
+                                   act, s);
     else
-        k_conv_fwd_tma<BN, 16, F><<<grid, 128, TmaCfg<BN, 16>::bytes, s>>>(
-            xm, wm, bias, y, H, W, cin, cout, act);
+        launch_tma1<BN, 16, F, XM>(xm, wm, bias, y, grid.x, grid.y, H, W, cin, cout,
+                                   act, s);
+}
+template <int BN, bool F>
+void launch_tma_b(const CUtensorMap& xm, const CUtensorMap& wm, const float* bias,
+                  void* y, const dim3& grid, int H, int W, int cin, int cout,
+                  int act, int cb, bool xmrg, cudaStream_t s) {
+    if (xmrg) launch_tma_x<BN, F, true>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s);
+    else launch_tma_x<BN, F, false>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s);
 }
 
 template <bool F>
 void launch_tma(const CUtensorMap& xm, const CUtensorMap& wm, const float* bias,
                 void* y, long long V, int H, int W, int cin, int cout, int act,
-                int bn, int cb, cudaStream_t s) {
+                int bn, int cb, bool xmrg, cudaStream_t s) {
     const dim3 grid((unsigned)(V / 128), (unsigned)(cout / bn));
+#define UN_TMA(BN) \
+    launch_tma_b<BN, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, xmrg, s)
     switch (bn) {
-        case 16: launch_tma_b<16, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
-        case 32: launch_tma_b<32, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
-        case 64: launch_tma_b<64, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
-        case 96: launch_tma_b<96, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
-        case 128: launch_tma_b<128, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
-        default: launch_tma_b<192, F>(xm, wm, bias, y, grid, H, W, cin, cout, act, cb, s); break;
+        case 16: UN_TMA(16); break;
+        case 32: UN_TMA(32); break;
+        case 64: UN_TMA(64); break;
+        case 96: UN_TMA(96); break;
+        case 128: UN_TMA(128); break;
+        default: UN_TMA(192); break;
     }
+#undef UN_TMA
 }
 
 int conv_forward(const bf16* x, const bf16* w, const float* bias, void* y,
@@ -1151,9 +1263,14 @@ int conv_forward(const bf16* x, const bf16* w, const float* bias, void* y,
     const int gx = (int)((V + 127) / 128);
     CUtensorMap xm, wm;
     const int bn = pick_bn(cout), cb = pick_cb(cin);
-    if (cin != 2 && conv_maps(&xm, &wm, x, w, D, H, W, cin, cout, bn, cb)) {
-        if (out_f32) launch_tma<true>(xm, wm, bias, y, V, H, W, cin, cout, act, bn, cb, s);
-        else launch_tma<false>(xm, wm, bias, y, V, H, W, cin, cout, act, bn, cb, s);
+    // tiles of one row (W a multiple of 128): the three taps along x share
+    // one load
+    const bool xmrg = W % 128 == 0;
+    if (cin != 2 && conv_maps(&xm, &wm, x, w, D, H, W, cin, cout, bn, cb, xmrg)) {
+        if (out_f32)
+            launch_tma<true>(xm, wm, bias, y, V, H, W, cin, cout, act, bn, cb, xmrg, s);
+        else
+            launch_tma<false>(xm, wm, bias, y, V, H, W, cin, cout, act, bn, cb, xmrg, s);
         return 1;
     }
     if (cin == 2) {
@@ -1183,21 +1300,25 @@ cudaError_t attrs_tc() {
     if ((r = attr_tc<192, C2, F>()) != cudaSuccess) e = r;
     return e;
 }
+template <int BN, int CB, bool F, bool XM>
+cudaError_t attr_tma1() {
+    using C = TmaCfg<BN, CB, XM>;
+    // the largest of the layouts pick_mt can choose
+    int mx = C::bytes(1);
+    for (int m = 2; m <= CONV_MAXMT; m *= 2)
+        if (m * BN <= 128 && C::stage(m) <= 40 * 1024) mx = std::max(mx, C::bytes(m));
+    return cudaFuncSetAttribute(k_conv_fwd_tma<BN, CB, F, XM>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
 template <int BN, bool F>
 cudaError_t attr_tma() {
     cudaError_t e = cudaSuccess, r;
-    if ((r = cudaFuncSetAttribute(k_conv_fwd_tma<BN, 16, F>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  TmaCfg<BN, 16>::bytes)) != cudaSuccess)
-        e = r;
-    if ((r = cudaFuncSetAttribute(k_conv_fwd_tma<BN, 32, F>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  TmaCfg<BN, 32>::bytes)) != cudaSuccess)
-        e = r;
-    if ((r = cudaFuncSetAttribute(k_conv_fwd_tma<BN, 64, F>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  TmaCfg<BN, 64>::bytes)) != cudaSuccess)
-        e = r;
+    if ((r = attr_tma1<BN, 16, F, false>()) != cudaSuccess) e = r;
+    if ((r = attr_tma1<BN, 32, F, false>()) != cudaSuccess) e = r;
+    if ((r = attr_tma1<BN, 64, F, false>()) != cudaSuccess) e = r;
+    if ((r = attr_tma1<BN, 16, F, true>()) != cudaSuccess) e = r;
+    if ((r = attr_tma1<BN, 32, F, true>()) != cudaSuccess) e = r;
+    if ((r = attr_tma1<BN, 64, F, true>()) != cudaSuccess) e = r;
     return e;
 }
 template <bool F>

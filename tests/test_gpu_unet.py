@@ -232,27 +232,35 @@ def test_unet_training_lowers_the_loss(P):
     assert losses[-1] < 0.7 * losses[0], losses[::5]
 
 
-@pytest.mark.parametrize("D,cin,cout", [(128, 16, 16), (64, 96, 32), (128, 2, 16)])
-def test_conv3d_forward_full_size_sampled(P, oracle_mod, D, cin, cout):
+# 128^3 16 -> 16: four one-row tiles per CTA sharing their x taps' loads;
+# 64^3 96 -> 32: one two-row tile per CTA; 320x64x64 32 -> 32: four
+# two-row tiles per CTA; 128^3 2 -> 16: the gathering kernel
+@pytest.mark.parametrize("shape,cin,cout", [((128, 128, 128), 16, 16),
+                                            ((64, 64, 64), 96, 32),
+                                            ((320, 64, 64), 32, 32),
+                                            ((128, 128, 128), 2, 16)])
+def test_conv3d_forward_full_size_sampled(P, oracle_mod, shape, cin, cout):
     """The network's largest layer shapes (128^3 and 64^3 levels): sampled
     outputs against the oracle's convolution of each sample's 3x3x3
     neighbourhood."""
     import torch
     from oracle import unet as U
-    r = np.random.default_rng(D + cin)
-    xt = torch.randn((D, D, D, cin), generator=torch.Generator().manual_seed(5)).to(torch.bfloat16)
+    D, H, W = shape
+    r = np.random.default_rng(D + H + cin)
+    xt = torch.randn(shape + (cin,), generator=torch.Generator().manual_seed(5)).to(torch.bfloat16)
     w = r.standard_normal((cout, cin, 3, 3, 3)) / np.sqrt(27 * cin)
     wt, w64 = _bf(_w_internal(w))
     b = r.standard_normal(cout).astype(np.float32)
-    y = torch.empty((D, D, D, cout), device="cuda")
+    y = torch.empty(shape + (cout,), device="cuda")
     P.lm_conv3d_forward(xt.cuda(), wt, torch.from_numpy(b).cuda(), 1, y)
     torch.cuda.synchronize()
     x64 = xt.float().numpy().astype(np.float64)
     xp = np.pad(x64, ((1, 1), (1, 1), (1, 1), (0, 0)))
     w_or = w64.reshape(cout, 27, cin).transpose(0, 2, 1).reshape(cout, cin, 3, 3, 3)
     yg = y.cpu().numpy()
-    pts = r.integers(0, D, (300, 3))
-    pts[:20] = [[0, 0, 0], [D - 1, D - 1, D - 1], [0, D - 1, 5]] * 6 + [[1, 0, D - 1]] * 2
+    pts = np.stack([r.integers(0, n, 300) for n in shape], axis=1)
+    pts[:20] = ([[0, 0, 0], [D - 1, H - 1, W - 1], [0, H - 1, 5]] * 6 +
+                [[1, 0, W - 1]] * 2)
     for z, yy, x in pts:
         patch = np.moveaxis(xp[z:z + 3, yy:yy + 3, x:x + 3], -1, 0)   # (cin, 3, 3, 3)
         ref = U.leaky_relu(U.conv3d(patch, w_or, b.astype(np.float64))[:, 1, 1, 1])
