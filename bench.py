@@ -54,7 +54,7 @@ ITER_BYTES_PER_VOXEL = 68
 # + dram__bytes_write.sum of every kernel of an iteration at 128x160x192,
 # k = 5, FP32), scaled by voxels.  None whenever those kernels changed since
 # the last capture, and for other plans (--autotune).
-ITER_TRAFFIC_BYTES_PER_VOXEL = 98.7
+ITER_TRAFFIC_BYTES_PER_VOXEL = 97.6
 
 
 def _peaks():
@@ -1064,10 +1064,10 @@ def main():
                     help="batch: uneven pairs, batched vs plain; warmstart: "
                          "U-Net warm start vs LM from zero; damping: mu+ / "
                          "cap / rejection sweep (own JSON lines)")
-    ap.add_argument("--ws-train", type=int, default=512)
-    ap.add_argument("--ws-test", type=int, default=32)
-    ap.add_argument("--ws-epochs", type=int, default=24)
-    ap.add_argument("--ws-lr", type=float, default=3e-4)
+    ap.add_argument("--ws-train", type=int, default=2000)
+    ap.add_argument("--ws-test", type=int, default=200)
+    ap.add_argument("--ws-epochs", type=int, default=12)
+    ap.add_argument("--ws-lr", type=float, default=1e-4)
     ap.add_argument("--ws-cap", type=int, default=400)
     ap.add_argument("--ws-level2", type=int, default=0)
     ap.add_argument("--batch-pairs", type=int, default=64)
