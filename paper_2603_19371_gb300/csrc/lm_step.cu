@@ -175,8 +175,10 @@ __global__ void __launch_bounds__(TH_W * 32)
 
 // Trial field, one voxel per thread.  A block owns a 32 x 8 x-y tile and a
 // z range of one pair; the planes z-1, z, z+1 of u (3 components, with a
-// one-voxel x-y halo, read at edge-clamped positions) sit in a four-slot
-// shared-memory ring that cp.async fills one plane ahead, so the trilinear
+// one-voxel x-y halo, read at edge-clamped positions) sit in an eight-slot
+// shared-memory ring that cp.async fills two planes ahead (the block's g
+// tile of each slice rides along three slices ahead of its use, in a
+// four-slot ring of its own), so the trilinear
 // read of u at p + v comes from shared memory whenever |v| < 1 along each
 // axis and from global memory otherwise.  The trial goes to slot (1 - cu),
 // or to the pair's warp-smoothing buffer.  Without warp smoothing the
@@ -199,6 +201,13 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
                  "l"(src)
                  : "memory");
 }
+// zero-filled where !pred
+__device__ __forceinline__ void cp_async4_zf(float* dst, const float* src, bool pred) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(pred ? 4 : 0)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -210,7 +219,8 @@ template <typename T, bool RESAMPLE, int MODE>
 __global__ void __launch_bounds__(ST_X * ST_Y, 3)
     k_step_compose(const PairDesc* __restrict__ pd, int npairs, int attempt,
                    float step, int smooth, int tile) {
-    __shared__ __align__(16) float ring[4][3][ST_PLANE];   // [slot][comp][y][x]
+    __shared__ __align__(16) float ring[8][3][ST_PLANE];   // [slot][comp][y][x]
+    __shared__ __align__(16) float gring[4][3][ST_X * ST_Y];   // g tiles
     const PairDesc& P = pd[pair_of_block<3>(pd, npairs, blockIdx.x)];
     const DevState* st = P.st;
     if (attempt_skip(st, attempt)) return;
@@ -262,19 +272,36 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
             ld_dst[k] = q * ST_PLANE + rem;
         }
     }
-    // plane zp (edge-clamped) into ring slot zp mod 4
+    // plane zp (edge-clamped) into ring slot zp mod 8
     auto issue_plane = [&](int zp) {
         const float* src = u + min(max(zp, 0), g.nz - 1) * sxy;
-        float* dst = &ring[zp & 3][0][0];
+        float* dst = &ring[zp & 7][0][0];
 #pragma unroll
         for (int k = 0; k < NLD; ++k)
             if (ld_dst[k] >= 0) cp_async4(dst + ld_dst[k], src + ld_src[k]);
     };
+    const bool in_xy = x < g.nx && y < g.ny;
+    // this thread's g at slice zp into g slot zp mod 4 (zero outside the
+    // volume or past the block's range; only this thread reads it back)
+    const int gxy = in_xy ? y * g.nx + x : 0;
+    auto issue_g = [&](int zp) {
+        const bool on = in_xy && zp < z1;
+        const float* src = gg + (on ? zp * sxy + gxy : 0);
+        float* dst = &gring[zp & 3][0][tid];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            cp_async4_zf(dst + q * ST_X * ST_Y, src + (on ? q * V : 0), on);
+    };
     issue_plane(z0 - 1);
     issue_plane(z0);
     issue_plane(z0 + 1);
+    issue_g(z0);
+    issue_g(z0 + 1);
     cp_async_commit_wait_all();
-    const bool in_xy = x < g.nx && y < g.ny;
+    // the first group in flight: plane z0 + 2 and g at z0 + 2
+    if (z0 + 2 <= z1) issue_plane(z0 + 2);
+    issue_g(z0 + 2);
+    cp_async_commit();
     // Eq. tilen: this column's tiles (x / k, y / k fixed; z / k counted),
     // as tile indices of the pair's table
     int tile_col = 0, tile_slice = 0, tz_ = 0, tzr = 0;
@@ -284,30 +311,20 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
         tz_ = z0 / tile;
         tzr = z0 - tz_ * tile;
     }
-    // the gradient of voxel z is loaded one step ahead
     int i = z0 * sxy + y * g.nx + x;
-    float ng0 = 0.f, ng1 = 0.f, ng2 = 0.f;
-    if (in_xy && z0 < z1) {
-        ng0 = __ldg(gg + i);
-        ng1 = __ldg(gg + V + i);
-        ng2 = __ldg(gg + 2 * V + i);
-    }
     __syncthreads();
     // resampling is pipelined by one voxel: the corners of M at the trial of
     // voxel z are requested at step z and consumed at step z + 1
     float pm[8], pf[3];
     bool have = false;
     for (int z = z0; z < z1; ++z, i += sxy) {
-        // plane z + 2 (read from step z + 1 on) streams into its slot, the
-        // one plane z - 2 left
-        if (z + 2 <= z1) issue_plane(z + 2);
+        // plane z + 3 (read from step z + 2 on) and g at z + 3 stream into
+        // their slots, the ones plane z - 5 and g at z - 1 left
+        if (z + 3 <= z1) issue_plane(z + 3);
+        issue_g(z + 3);
         cp_async_commit();
-        const float cg0 = ng0, cg1 = ng1, cg2 = ng2;
-        if (in_xy && z + 1 < z1) {
-            ng0 = __ldg(gg + i + sxy);
-            ng1 = __ldg(gg + V + i + sxy);
-            ng2 = __ldg(gg + 2 * V + i + sxy);
-        }
+        const float cg0 = gring[z & 3][0][tid], cg1 = gring[z & 3][1][tid],
+                    cg2 = gring[z & 3][2][tid];
         if (in_xy) {
             float v[3];
             if (MODE == STEP_DIRECT) {
@@ -350,8 +367,8 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
             if (cx >= x0 - 1 && cx + 1 <= x0 + ST_X && cy >= y0 - 1 &&
                 cy + 1 <= y0 + ST_Y && cz >= z - 1 && cz + 1 <= z + 1) {
                 const int o = (cy - (y0 - 1)) * ST_HX + cx - (x0 - 1);
-                const float* p0 = &ring[cz & 3][0][0] + o;
-                const float* p1 = &ring[(cz + 1) & 3][0][0] + o;
+                const float* p0 = &ring[cz & 7][0][0] + o;
+                const float* p1 = &ring[(cz + 1) & 7][0][0] + o;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     m[q][0] = p0[q * ST_PLANE];
@@ -410,9 +427,10 @@ __global__ void __launch_bounds__(ST_X * ST_Y, 3)
             tzr = 0;
             ++tz_;
         }
-        // plane z + 2 has landed (this thread's copies), and every thread
-        // is done with plane z - 1 before step z + 1 overwrites its slot
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        // the group issued at step z - 1 (plane z + 2, g at z + 2) has
+        // landed, this step's may still be in flight; the barrier makes the
+        // plane's copies of every thread visible before step z + 1
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncthreads();
     }
     if (RESAMPLE && have) store_resampled(jo, i - sxy, x, y, z1 - 1, pm, pf);
