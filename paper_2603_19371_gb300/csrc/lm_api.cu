@@ -396,7 +396,7 @@ struct Core {
 // Wave counts the autotuner tries (CTAs per SM in total for E1 and E2).
 constexpr int kE1Waves[] = {1, 2, 4, 8};
 constexpr int kE2Waves[] = {2, 3, 4, 8, 16};
-constexpr int kMinSlices[] = {8, 1};
+constexpr int kMinSlices[] = {8, 4, 2, 1};
 constexpr int kStepBlocks[] = {512, 1024, 2048, 4096};
 constexpr int kMaxE1Waves = 8, kMaxE2Waves = 16;
 
