@@ -54,7 +54,7 @@ ITER_BYTES_PER_VOXEL = 68
 # + dram__bytes_write.sum of every kernel of an iteration at 128x160x192,
 # k = 5, FP32), scaled by voxels.  None whenever those kernels changed since
 # the last capture, and for other plans (--autotune).
-ITER_TRAFFIC_BYTES_PER_VOXEL = None
+ITER_TRAFFIC_BYTES_PER_VOXEL = 97.5
 
 
 def _peaks():
