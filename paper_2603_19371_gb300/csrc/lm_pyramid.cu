@@ -10,26 +10,6 @@ namespace {
 constexpr int TPB = 256;
 
 template <typename T>
-__global__ void k_blur_line(const T* __restrict__ in, Geom g, int axis,
-                            Taps t, float* __restrict__ out) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.V) return;
-    int x = (int)(i % g.nx);
-    long long r = i / g.nx;
-    int y = (int)(r % g.ny), z = (int)(r / g.ny);
-    int pos = axis == 0 ? x : (axis == 1 ? y : z);
-    int n = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
-    long long stride = axis == 0 ? 1 : (axis == 1 ? g.nx : (long long)g.nx * g.ny);
-    float acc = 0.f;
-    for (int j = -t.R; j <= t.R; ++j) {
-        int pp = pos + j;
-        if (pp < 0 || pp >= n) continue;
-        acc += t.t[j + t.R] * ld_img(in, i + j * stride);
-    }
-    out[i] = acc;
-}
-
-template <typename T>
 __device__ __forceinline__ void store_img(T* p, long long i, float v);
 template <>
 __device__ __forceinline__ void store_img(float* p, long long i, float v) {
@@ -41,39 +21,46 @@ __device__ __forceinline__ void store_img(__nv_bfloat16* p, long long i,
     p[i] = __float2bfloat16_rn(v);
 }
 
-template <typename T>
-__global__ void k_level_sample(const float* __restrict__ bl, Geom g, int f,
-                               Geom go, T* __restrict__ dst) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= go.V) return;
-    int x = (int)(i % go.nx);
-    long long r = i / go.nx;
-    int y = (int)(r % go.ny), z = (int)(r / go.ny);
-    float off = 0.5f * (f - 1);
-    float q[3] = {f * x + off, f * y + off, f * z + off};
-    int c[3];
-    float w[3];
-    for (int k = 0; k < 3; ++k) {
-        float fl = floorf(q[k]);
-        c[k] = (int)fl;
-        w[k] = q[k] - fl;
-    }
-    const int n[3] = {g.nx, g.ny, g.nz};
-    float acc = 0.f;
-    for (int s = 0; s < 8; ++s) {
-        int o[3] = {s & 1, (s >> 1) & 1, s >> 2};
-        int qq[3];
-        bool in = true;
-        float wt = 1.f;
-        for (int k = 0; k < 3; ++k) {
-            qq[k] = c[k] + o[k];
-            in = in && qq[k] >= 0 && qq[k] < n[k];
-            wt *= o[k] ? w[k] : 1.f - w[k];
+// One axis of a level's anti-aliased sampling.  Blurring with the taps t
+// (zero outside the volume) and then reading linearly at f p + (f - 1) / 2
+// (a corner outside the volume weighs nothing) are both linear and
+// separable, so each axis is filtered and sampled in one pass that computes
+// only the level's points along it: x first (full y, z), then y, then z.
+// The input has extents (ix, iy, iz); the output replaces the axis' extent
+// by n_out.  One thread per output point, the other two coordinates from
+// the grid (no divisions).
+template <typename TI, typename TO>
+__global__ void k_level_axis(const TI* __restrict__ in, int ix, int iy, int iz,
+                             int axis, int f, int n_out, Taps t,
+                             TO* __restrict__ out) {
+    const int ox = axis == 0 ? n_out : ix;
+    const int oy = axis == 1 ? n_out : iy;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= ox) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int p = axis == 0 ? x : (axis == 1 ? y : z);
+    const int n = axis == 0 ? ix : (axis == 1 ? iy : iz);
+    const long long stride = axis == 0 ? 1 : (axis == 1 ? ix : (long long)ix * iy);
+    const long long base = ((long long)(axis == 2 ? 0 : z) * iy + (axis == 1 ? 0 : y)) * ix +
+                           (axis == 0 ? 0 : x);
+    const float q = f * p + 0.5f * (f - 1);
+    const float fl = floorf(q);
+    const int c = (int)fl;
+    const float w = q - fl;
+    float v = 0.f;
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        const int pos = c + o;
+        if (pos < 0 || pos >= n) continue;
+        float b = 0.f;
+        for (int j = -t.R; j <= t.R; ++j) {
+            const int pp = pos + j;
+            if (pp < 0 || pp >= n) continue;
+            b += t.t[j + t.R] * ld_img(in, base + pp * stride);
         }
-        if (in)
-            acc += wt * bl[((long long)qq[2] * g.ny + qq[1]) * g.nx + qq[0]];
+        v += (o ? w : 1.f - w) * b;
     }
-    store_img(dst, i, acc);
+    store_img(out, ((long long)z * oy + y) * ox + x, v);
 }
 
 __global__ void k_resample_field(const float* __restrict__ src, Geom ga,
@@ -139,23 +126,29 @@ int downsample_image(const void* src, int dtype, const Geom& g, int f,
                      void* dst, float* tmp, cudaStream_t s) {
     Taps t = blur_taps(0.5 * f);
     if (t.R > MAX_R) return -1;
-    unsigned nb = (unsigned)((g.V + TPB - 1) / TPB);
-    float* A = tmp;
-    float* B = tmp + g.V;
-    if (dtype == LM_BF16)
-        k_blur_line<<<nb, TPB, 0, s>>>((const __nv_bfloat16*)src, g, 0, t, A);
-    else
-        k_blur_line<<<nb, TPB, 0, s>>>((const float*)src, g, 0, t, A);
-    k_blur_line<<<nb, TPB, 0, s>>>((const float*)A, g, 1, t, B);
-    k_blur_line<<<nb, TPB, 0, s>>>((const float*)B, g, 2, t, A);
     Geom go;
     level_dims(g.nx, g.ny, g.nz, f, &go.nx, &go.ny, &go.nz);
-    go.V = (long long)go.nx * go.ny * go.nz;
-    unsigned nbo = (unsigned)((go.V + TPB - 1) / TPB);
+    // x: (nx, ny, nz) -> (lx, ny, nz); y: -> (lx, ly, nz); z: -> (lx, ly, lz)
+    float* A = tmp;
+    float* B = tmp + (long long)go.nx * g.ny * g.nz;
+    const int TB = 128;
+    const dim3 gx((go.nx + TB - 1) / TB, g.ny, g.nz);
+    const dim3 gy((go.nx + TB - 1) / TB, go.ny, g.nz);
+    const dim3 gz((go.nx + TB - 1) / TB, go.ny, go.nz);
     if (dtype == LM_BF16)
-        k_level_sample<<<nbo, TPB, 0, s>>>(A, g, f, go, (__nv_bfloat16*)dst);
+        k_level_axis<__nv_bfloat16, float><<<gx, TB, 0, s>>>(
+            (const __nv_bfloat16*)src, g.nx, g.ny, g.nz, 0, f, go.nx, t, A);
     else
-        k_level_sample<<<nbo, TPB, 0, s>>>(A, g, f, go, (float*)dst);
+        k_level_axis<float, float><<<gx, TB, 0, s>>>(
+            (const float*)src, g.nx, g.ny, g.nz, 0, f, go.nx, t, A);
+    k_level_axis<float, float><<<gy, TB, 0, s>>>(A, go.nx, g.ny, g.nz, 1, f,
+                                                 go.ny, t, B);
+    if (dtype == LM_BF16)
+        k_level_axis<float, __nv_bfloat16><<<gz, TB, 0, s>>>(
+            B, go.nx, go.ny, g.nz, 2, f, go.nz, t, (__nv_bfloat16*)dst);
+    else
+        k_level_axis<float, float><<<gz, TB, 0, s>>>(B, go.nx, go.ny, g.nz, 2, f,
+                                                     go.nz, t, (float*)dst);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
