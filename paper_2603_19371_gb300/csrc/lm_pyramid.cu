@@ -7,7 +7,6 @@
 namespace lmk {
 namespace {
 
-constexpr int TPB = 256;
 
 template <typename T>
 __device__ __forceinline__ void store_img(T* p, long long i, float v);
@@ -66,11 +65,11 @@ __global__ void k_level_axis(const TI* __restrict__ in, int ix, int iy, int iz,
 __global__ void k_resample_field(const float* __restrict__ src, Geom ga,
                                  int fa, float* __restrict__ dst, Geom gb,
                                  int fb) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= gb.V) return;
-    int x = (int)(i % gb.nx);
-    long long r = i / gb.nx;
-    int y = (int)(r % gb.ny), z = (int)(r / gb.ny);
+    // one thread per destination voxel; y and z from the grid
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= gb.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long i = ((long long)z * gb.ny + y) * gb.nx + x;
     const int p[3] = {x, y, z};
     const int n[3] = {ga.nx, ga.ny, ga.nz};
     int c0[3], c1[3];
@@ -154,8 +153,8 @@ int downsample_image(const void* src, int dtype, const Geom& g, int f,
 
 int resample_field(const float* src, const Geom& ga, int fa, float* dst,
                    const Geom& gb, int fb, cudaStream_t s) {
-    unsigned nb = (unsigned)((gb.V + TPB - 1) / TPB);
-    k_resample_field<<<nb, TPB, 0, s>>>(src, ga, fa, dst, gb, fb);
+    const dim3 grid((gb.nx + 127) / 128, gb.ny, gb.nz);
+    k_resample_field<<<grid, 128, 0, s>>>(src, ga, fa, dst, gb, fb);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
