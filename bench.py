@@ -222,7 +222,7 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
     oracle.build()
     Po = _oracle_params(params)
     Fo, Mo = F.astype(np.float64), M.astype(np.float64)
-    t_or, evals = 0.0, 0
+    t_or, evals, rejected = 0.0, 0, 0
     e_loss, e_trial, e_du, same_all, lam_all = [], [], [], True, True
     for _ in range(iters):
         st = P.lm_get_state(ctx)
@@ -239,7 +239,12 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
         acc = info.retries == 0 and info.accepted == 1
         same = acc == (act == oracle.ACCEPT)
         same_all &= same
-        lam_all &= same and abs(info.lambda_ - lam_o) <= 1e-12 * lam_o
+        # lambda after the first attempt's decision (a rejected trial's
+        # retries move it further on the GPU within the same step)
+        if acc:
+            lam_all &= same and abs(info.lambda_ - lam_o) <= 1e-12 * lam_o
+        else:
+            rejected += 1
         e_loss.append(abs(st.loss - ev["L"]) / ev["L"])
         e_trial.append(abs(info.loss_first - L1) / L1)
         if acc:
@@ -260,7 +265,7 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
            "max_rel_loss_err": max(e_loss),
            "max_rel_trial_loss_err": max(e_trial),
            "max_du_voxel": max(e_du) if e_du else None,
-           "accepted": len(e_du),
+           "accepted": len(e_du), "rejected_first_trials": rejected,
            "decisions_match": bool(same_all), "lambda_match": bool(lam_all),
            "bars": {"rel_loss": 1e-5, "du_voxel": 1e-4}}
     return base, err
@@ -1013,9 +1018,27 @@ def run_damping(args):
                      1.5, math.inf, 0)
     r0 = {name: _inverse_residual(np.zeros_like(ut), ut)[0]
           for name, (_, _, ut), _ in pairs}
+    # the cpu_baseline leg: the stress setting with rejection on the blob
+    # pair (trials that raise the loss are rejected there), teacher-forced
+    cpu, oracle_err = None, None
+    if not args.no_cpu_baseline:
+        F, M, _ = pairs[0][1]
+        prm = P.lm_default_params(lambda0=0.006, step=2.0, mu_inc=1.5,
+                                  lambda_max=math.inf, reject=1, tau=1.0,
+                                  max_retries=10)
+        ctx = P.lm_init(torch.from_numpy(F).cuda(), torch.from_numpy(M).cuda(),
+                        prm)
+        u = torch.zeros((3,) + F.shape, device="cuda")
+        P.lm_reset(ctx, u)
+        cpu, oracle_err = cpu_baseline(
+            P, ctx, u, F, M, prm, iters=20,
+            what="the blob pair, stress setting with rejection (lambda0 "
+                 "0.006, step 2, mu+ 1.5, tau 1)")
+        P.lm_destroy(ctx)
     print(json.dumps({"workload": "damping sweep and rejection ablation",
                       "data": "synthetic", "residual_at_zero_field": r0,
-                      "cases": cases}), flush=True)
+                      "cases": cases, "cpu_baseline": cpu,
+                      "oracle_error": oracle_err}), flush=True)
     return 0
 
 
