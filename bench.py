@@ -1089,7 +1089,7 @@ def main():
                          "cap / rejection sweep (own JSON lines)")
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
-    ap.add_argument("--ws-epochs", type=int, default=12)
+    ap.add_argument("--ws-epochs", type=int, default=24)
     ap.add_argument("--ws-lr", type=float, default=1e-4)
     ap.add_argument("--ws-cap", type=int, default=400)
     ap.add_argument("--ws-level2", type=int, default=0)
