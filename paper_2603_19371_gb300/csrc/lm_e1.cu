@@ -1,10 +1,11 @@
 // LNCC loss and backward pass of pass 1 (Section 2.2), as one z-streaming
-// kernel per pair.  A CTA owns a column of 32 x 16 output voxels and a range
-// of z slices and walks it one moment slice at a time.  For moment slice m
-// (window k = 2W + 1, zero padding, fixed divisor k^3):
+// kernel per pair.  A CTA owns a column of 32 x OY output voxels (OY = 16
+// or 32, the tile variant) and a range of z slices and walks it one moment
+// slice at a time.  For moment slice m (window k = 2W + 1, zero padding,
+// fixed divisor k^3):
 //
 //  Z  running sums along z over the slices m - W .. m + W of J', J'J' and
-//     F'J' at every point of the (32 + 4W) x (16 + 4W) gather plane, kept in shared
+//     F'J' at every point of the (32 + 4W) x (OY + 4W) gather plane, kept in shared
 //     memory; each step adds slice m + W and subtracts slice m - W - 1,
 //     whose values are read again (they are in L2) rather than kept.  J'
 //     and F' come from a halo-padded layout whose halo holds the fixed
@@ -12,7 +13,7 @@
 //     with no bounds tests;
 //  X  sums along x of those, over the (32 + 2W) moment columns;
 //  Y  sums along y, which completes the exact window sums S_J, S_JJ, S_FJ
-//     at every point of the (32 + 2W) x (16 + 2W) moment plane, and per point the
+//     at every point of the (32 + 2W) x (OY + 2W) moment plane, and per point the
 //     squared local correlation cc = (A^2 + eps_nr) / (B C + eps_dr), its
 //     loss term (1 - cc) and the backward coefficients (a, b, c) with
 //     A = S_FJ - S_F S_J / k^3, C = S_JJ - S_J^2 / k^3 (B, S_F precomputed
@@ -22,6 +23,10 @@
 //     output slice m - W:
 //        dL/dJ(y) = -V^-1 [F'(y) Box(a) + 2 J'(y) Box(b) + Box(c)],
 //        g_raw = dL/dJ dJ/du.
+//
+// The stages of a slice are separated by four barriers or, where the x-sum
+// and x-box planes fit twice in shared memory, software-pipelined over three
+// slices with two barriers per slice.
 //
 // Window moments are exact: F' = F - s and J' = J - s are held in fixed
 // point (Xq = round(X' Q), |Xq| <= 2^qb), the sums of Xq are int32 and those
