@@ -222,7 +222,7 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
     oracle.build()
     Po = _oracle_params(params)
     Fo, Mo = F.astype(np.float64), M.astype(np.float64)
-    t_or, evals, rejected = 0.0, 0, 0
+    t_or, evals, rejected, near_ties = 0.0, 0, 0, 0
     e_loss, e_trial, e_du, same_all, lam_all = [], [], [], True, True
     for _ in range(iters):
         st = P.lm_get_state(ctx)
@@ -240,9 +240,17 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
         same = acc == (act == oracle.ACCEPT)
         same_all &= same
         # lambda after the first attempt's decision (a rejected trial's
-        # retries move it further on the GPU within the same step)
+        # retries move it further on the GPU within the same step).  Its
+        # branch is the sign of L_trial - L; where that difference is below
+        # the loss's own error bound (1e-5 relative) either branch is a valid
+        # outcome of the same arithmetic: a near tie, counted, not a mismatch
         if acc:
-            lam_all &= same and abs(info.lambda_ - lam_o) <= 1e-12 * lam_o
+            tie = abs(L1 - ev["L"]) <= 1e-5 * ev["L"]
+            ok = abs(info.lambda_ - lam_o) <= 1e-12 * lam_o
+            if not ok and tie:
+                near_ties += 1
+            else:
+                lam_all &= same and ok
         else:
             rejected += 1
         e_loss.append(abs(st.loss - ev["L"]) / ev["L"])
@@ -267,6 +275,7 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
            "max_du_voxel": max(e_du) if e_du else None,
            "accepted": len(e_du), "rejected_first_trials": rejected,
            "decisions_match": bool(same_all), "lambda_match": bool(lam_all),
+           "lambda_near_ties": near_ties,
            "bars": {"rel_loss": 1e-5, "du_voxel": 1e-4}}
     return base, err
 
@@ -430,7 +439,13 @@ def run_ours(args):
     # gives the GPU's error against it
     cpu, oracle_err = None, None
     if (world == 1 and not args.no_cpu_baseline and V <= 20_000_000):
-        cpu, oracle_err = cpu_baseline(P, ctx, u, F, M, params)
+        # from the workload's start (u = 0, fresh state): the first
+        # iterations, where the steps are largest
+        with torch.cuda.stream(stream):
+            u.zero_()
+        P.lm_reset(ctx, u)
+        cpu, oracle_err = cpu_baseline(P, ctx, u, F, M, params,
+                                       what="the benched pair from u = 0")
         if shape == SHAPE:
             cpu["single_thread"] = single_thread_baseline()
 
@@ -454,11 +469,15 @@ def run_ours(args):
         # warm-up: allocations, and the coarse levels' contexts tune their
         # work split when first used
         P.lm_register(ctx2, levels, ud)
-        n_e2e = max(1, min(args.steps, 3))
+        # each registration timed on its own (host clock around the copies
+        # in, the registration and the copy out); the median of five is
+        # reported, the spread beside it
+        n_e2e = 5
+        times = []
         vox = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
         for _ in range(n_e2e):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             with torch.cuda.stream(stream):
                 Fd.copy_(Fh, non_blocking=True)
                 Md.copy_(Mh, non_blocking=True)
@@ -467,14 +486,17 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 uh.copy_(ud, non_blocking=True)
             stream.synchronize()
-            vox += rep.voxel_evals
-        dt = time.perf_counter() - t0
+            times.append(time.perf_counter() - t0)
+            vox = rep.voxel_evals
+        dt = sorted(times)[n_e2e // 2]
         e2e = {"value": vox / dt / 1e9, "unit": METRIC,
                "h2d_bytes_per_step": 2 * F.nbytes,
                "d2h_bytes_per_step": int(uh.numel() * 4),
-               "ms_per_registration": dt / n_e2e * 1e3,
+               "ms_per_registration": dt * 1e3,
+               "ms_registrations": [round(t * 1e3, 3) for t in times],
                "what": "lm_register, levels 4/2/1 x 200/100/50 iterations, "
-                       "F and M copied in, u copied out per step"}
+                       "F and M copied in, u copied out per step; median of "
+                       f"{n_e2e} registrations"}
         P.lm_destroy(ctx2)
 
     if rank != 0:
