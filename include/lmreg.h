@@ -247,7 +247,11 @@ LM_API int lm_step(lm_ctx *ctx, float *u, lm_step_info *info);
 /* n LM iterations, each exactly the iteration of lm_step (Eq. tile1 or
  * Eq. tilen, Eq. compositive, Eq. lambda-update and Eq. rejection, Sections
  * 2.1-2.2 and 3.4), replayed from a captured CUDA graph; info of the last
- * iteration (host, may be NULL).  u as for lm_step. */
+ * iteration (host, may be NULL).  u as for lm_step.  Without rejection
+ * (p.reject = 0 or max_retries = 0) the call is asynchronous when info is
+ * NULL.  With rejection each replay runs one attempt, a retry where the
+ * last trial was rejected, and the call synchronises to replay until all
+ * n iterations are done. */
 LM_API int lm_iterate(lm_ctx *ctx, float *u, int n, lm_step_info *info);
 
 /* Read / overwrite the optimiser scalars (synchronising).  lm_set_state
@@ -314,7 +318,8 @@ LM_API int lm_batch_eval(lm_batch *b, const float *const *u,
 /* As lm_reset for every pair (u[i]: device fields, in/out). */
 LM_API int lm_batch_reset(lm_batch *b, float *const *u);
 /* n LM iterations of every pair (u as given to lm_batch_reset); infos
- * (host, npairs entries, may be NULL) receive each pair's last outcome. */
+ * (host, npairs entries, may be NULL) receive each pair's last outcome.
+ * Synchronisation as for lm_iterate. */
 LM_API int lm_batch_iterate(lm_batch *b, float *const *u, int n,
                             lm_step_info *infos);
 /* Autotuner of the evaluation's tile shape and work split (the paper has

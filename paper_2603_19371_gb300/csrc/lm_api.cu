@@ -194,9 +194,7 @@ struct Core {
     std::vector<float*> gsink;     // lm_eval gradient sinks (lazy)
     bool have_reset = false;
     cudaGraphExec_t gexec = nullptr;
-    int graph_launches = 0;        // kernels of a graph launch outside any loop
-    int body_launches = 0;         // kernels of one pass of the attempt loop
-    int att_runs_seen = 0;         // attempt-loop passes already counted
+    int graph_launches = 0;        // kernels of one graph launch
     long long launches = 0;
     int num_sms = 0;
     int e1_cap = 0, e2_cap = 0;    // partial slots allocated (any plan fits)
@@ -290,9 +288,6 @@ struct Core {
         LM_CK(cudaMemcpyAsync(h_st, hpd[0].st, npairs * sizeof(DevState),
                               cudaMemcpyDeviceToHost, stream));
         LM_CK(cudaStreamSynchronize(stream));
-        // passes of the attempt loop run since the last read
-        launches += (long long)(h_st[0].att_runs - att_runs_seen) * body_launches;
-        att_runs_seen = h_st[0].att_runs;
         for (int i = 0; i < npairs; ++i)
             if (int rc = status_error(h_st[i].status, i)) return rc;
         return LM_OK;
@@ -311,66 +306,56 @@ struct Core {
         return n;
     }
 
-    // With rejection the attempts of an iteration run in a graph WHILE
-    // loop: its body (trial, evaluation, decision with the attempt read from
-    // the device state, then k_att_next) repeats only while some pair
-    // rejected its trial and has retries left, so an iteration without
-    // rejections costs one attempt.  Without rejection the graph holds the
-    // single attempt.
-    bool loop_attempts() const { return p.reject && p.max_retries > 0; }
+    // With rejection a replayed iteration is one state-driven attempt
+    // (kernels given attempt -1): the decision leaves each pair's next
+    // attempt in its device state, so a replay after a rejection retries
+    // the iteration and a replay after a decision starts the next one.  An
+    // iteration without rejections therefore costs one replay, and the
+    // graph holds no conditional node.  iterate() bounds each pair's run
+    // by iter_end and replays until every pair has finished its n
+    // iterations (or stopped), reading the states in between.
+    bool replay_retries() const { return p.reject && p.max_retries > 0; }
 
     int capture_graph(cudaGraph_t* out) {
         if (!cap_stream)
             LM_CK(cudaStreamCreateWithFlags(&cap_stream,
                                             cudaStreamNonBlocking));
-        if (!loop_attempts()) {
-            LM_CK(cudaStreamBeginCapture(cap_stream,
-                                         cudaStreamCaptureModeThreadLocal));
+        LM_CK(cudaStreamBeginCapture(cap_stream,
+                                     cudaStreamCaptureModeThreadLocal));
+        if (!replay_retries()) {
             graph_launches = enqueue_iteration(cap_stream);
-            LM_CK(cudaStreamEndCapture(cap_stream, out));
-            body_launches = 0;
-            return LM_OK;
+        } else {
+            graph_launches = batch_step(b, -1, cap_stream);
+            graph_launches += batch_eval(b, EVAL_TRIAL, -1, cap_stream,
+                                         !step_resamples(b));
+            graph_launches += batch_finalize(b, FIN_DECIDE, -1, nullptr,
+                                             cap_stream);
         }
-        // attempt 0, whose decision kernel sets the loop condition, then
-        // the loop node over the later attempts (the decision kernels keep
-        // the attempt index; it returns to 0 when the loop ends)
-        cudaGraph_t graph;
-        LM_CK(cudaGraphCreate(&graph, 0));
-        cudaGraphConditionalHandle h;
-        LM_CK(cudaGraphConditionalHandleCreate(&h, graph, 0,
-                                               cudaGraphCondAssignDefault));
-        LM_CK(cudaStreamBeginCaptureToGraph(cap_stream, graph, nullptr,
-                                            nullptr, 0,
-                                            cudaStreamCaptureModeThreadLocal));
-        int n0 = batch_step(b, 0, cap_stream);
-        n0 += batch_eval(b, EVAL_TRIAL, 0, cap_stream, !step_resamples(b));
-        n0 += batch_finalize(b, FIN_DECIDE, 0, nullptr, cap_stream, h);
-        cudaStreamCaptureStatus cs;
-        const cudaGraphNode_t* dp = nullptr;
-        size_t nd = 0;
-        LM_CK(cudaStreamGetCaptureInfo(cap_stream, &cs, nullptr, nullptr, &dp,
-                                       nullptr, &nd));
-        std::vector<cudaGraphNode_t> deps(dp, dp + nd);
-        LM_CK(cudaStreamEndCapture(cap_stream, &graph));
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t loop;
-        LM_CK(cudaGraphAddNode(&loop, graph, deps.data(), nullptr, deps.size(),
-                               &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        LM_CK(cudaStreamBeginCaptureToGraph(cap_stream, body, nullptr, nullptr,
-                                            0, cudaStreamCaptureModeThreadLocal));
-        int nb = batch_step(b, -1, cap_stream);
-        nb += batch_eval(b, EVAL_TRIAL, -1, cap_stream, !step_resamples(b));
-        nb += batch_finalize(b, FIN_DECIDE, -1, nullptr, cap_stream, h);
-        LM_CK(cudaStreamEndCapture(cap_stream, &body));
-        graph_launches = n0;
-        body_launches = nb;
-        *out = graph;
+        LM_CK(cudaStreamEndCapture(cap_stream, out));
         return LM_OK;
+    }
+
+    int replay(int n) {
+        for (int i = 0; i < n; ++i) LM_CK(cudaGraphLaunch(gexec, stream));
+        launches += (long long)n * graph_launches;
+        return LM_OK;
+    }
+
+    // Replays until every pair has reached its iter_end or stopped; the
+    // passes of one round are the largest number of iterations any pair
+    // still owes.  Each round reads the states (a synchronisation).
+    int replay_until_done() {
+        for (;;) {
+            if (int rc = read_states()) return rc;
+            int owe = 0;
+            for (int i = 0; i < npairs; ++i) {
+                const DevState& s = h_st[i];
+                if (!s.stopped && s.iter_end > 0 && s.iter_end - s.iter > owe)
+                    owe = s.iter_end - s.iter;
+            }
+            if (owe == 0) return LM_OK;
+            if (int rc = replay(owe)) return rc;
+        }
     }
 
     int iterate(int n) {
@@ -385,8 +370,17 @@ struct Core {
                 return fail(LM_ECUDA, "graph instantiate failed: %s",
                             cudaGetErrorString(e));
         }
-        for (int i = 0; i < n; ++i) LM_CK(cudaGraphLaunch(gexec, stream));
-        launches += (long long)n * graph_launches;
+        int rc = LM_OK;
+        if (!replay_retries()) {
+            rc = replay(n);
+        } else {
+            launches += batch_set_iter_end(b, n, stream);
+            rc = replay(n);
+            if (rc == LM_OK) rc = replay_until_done();
+            // the limit ends with the run, whatever its outcome
+            launches += batch_set_iter_end(b, 0, stream);
+        }
+        if (rc != LM_OK) return rc;
         launches += batch_sync_back(b, stream);
         LM_CK(cudaGetLastError());
         return LM_OK;
@@ -633,7 +627,6 @@ int core_reset(Core* c, float* const* u) {
     c->launches += batch_eval(c->b, EVAL_RESET, 0, c->stream);
     c->launches += batch_finalize(c->b, FIN_RESET, 0, nullptr, c->stream);
     LM_CK(cudaGetLastError());
-    c->att_runs_seen = 0;   // the reset decision clears the device count
     c->have_reset = true;
     return LM_OK;
 }
@@ -981,9 +974,7 @@ extern "C" int lm_state_load(lm_ctx* c, const void* buf, size_t nbytes) {
     s.cg = 0;       // the gradient is restored into slot 0
     s.done = 0;
     s.att = 0;
-    s.att_runs = 0;     // counted from this load on
-    s.fin_count = 0u;
-    k->att_runs_seen = 0;
+    s.iter_end = 0;
     k->h_st[0] = s;
     LM_CK(cudaMemcpyAsync(d.st, k->h_st, sizeof(DevState),
                           cudaMemcpyHostToDevice, k->stream));

@@ -38,10 +38,11 @@ struct DevState {
     int evals;         // loss evaluations since reset
     int log_pos;       // next log slot
     int stopped;       // reached the pair's target loss: iterations are no-ops
-    int att;           // attempt of the running iteration when the attempts
-                       // are driven by a graph loop (kernels given -1)
-    int att_runs;      // attempt-loop passes run (pair 0 of a batch counts)
-    unsigned fin_count;  // decisions written in the current pass (pair 0)
+    int att;           // the attempt the next state-driven pass runs (kernels
+                       // given -1): 0 starts an iteration, j > 0 retries it
+                       // after j rejected trials
+    int iter_end;      // > 0: passes are no-ops once iter reaches it (the
+                       // end of a replayed run of iterations); 0: no limit
 };
 
 // STATUS_TIMEOUT: a bounded device wait ran out (the evaluation's result is

@@ -101,16 +101,20 @@ __device__ __forceinline__ float* eval_g(const PairDesc& p, int mode) {
     return p.st->cg ? p.g0 : p.g1;
 }
 // Later attempts of an iteration are no-ops once the pair's iteration is
-// decided, and every attempt is once the pair has reached its target loss.
-// attempt < 0: the attempt index lives in the pair's device state (set by
-// the graph loop that repeats the attempts).
+// decided, and every attempt is once the pair has reached its target loss
+// or the end of its replayed run (iter_end).  attempt < 0: the attempt
+// index lives in the pair's device state (the decision sets it), so that
+// one captured pass runs whichever attempt each pair is at.
 __device__ __forceinline__ int attempt_of(const DevState* st, int attempt) {
     return attempt >= 0 ? attempt : st->att;
 }
+__device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
+    return st->stopped || (st->iter_end > 0 && st->iter >= st->iter_end) ||
+           (attempt_of(st, attempt) > 0 && st->done);
+}
 __device__ __forceinline__ bool trial_skip(const PairDesc& p, int mode,
                                            int attempt) {
-    return mode == EVAL_TRIAL &&
-           (p.st->stopped || (attempt_of(p.st, attempt) > 0 && p.st->done));
+    return mode == EVAL_TRIAL && attempt_skip(p.st, attempt);
 }
 
 // Pair whose block range starts at or below b (ranges ascend in pair
@@ -320,10 +324,12 @@ int launch_mi(const Batch& b, int mode, int attempt, cudaStream_t s);
 cudaError_t mi_setup();
 // Per-pair reduction and state update.
 enum FinMode { FIN_EXPLICIT = 0, FIN_RESET = 1, FIN_DECIDE = 2 };
-// attempt -1 with FIN_DECIDE: the pass of a graph attempt loop whose
-// condition handle is loop (see k_finalize).
+// attempt -1 with FIN_DECIDE: the state-driven pass (each pair's attempt
+// read from and written back to its device state).
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,
-                   cudaStream_t s, cudaGraphConditionalHandle loop = 0);
+                   cudaStream_t s);
+// Sets each pair's iter_end to its iter + n (n > 0), or clears it (n = 0).
+int batch_set_iter_end(const Batch& b, int n, cudaStream_t s);
 // Copy each pair's current field back to slot 0 when it sits in slot 1.
 int batch_sync_back(const Batch& b, cudaStream_t s);
 

@@ -20,10 +20,6 @@ namespace {
 
 constexpr int TPB = 256;
 
-__device__ __forceinline__ bool attempt_skip(const DevState* st, int attempt) {
-    return st->stopped || (attempt_of(st, attempt) > 0 && st->done);
-}
-
 // Pooled curvature of Eq. tilen (tile side k > 1).  For every
 // non-overlapping k x k x k tile T of the current gradient the kernel
 // forms H_T = |T|^-1 sum_T g g^T and stores the inverse of
@@ -571,8 +567,7 @@ __device__ __forceinline__ void finalize_pair(const PairDesc* __restrict__ pd,
         st->log_pos = 0;
         st->stopped = 0;
         st->att = 0;
-        st->att_runs = 0;
-        st->fin_count = 0u;
+        st->iter_end = 0;
         return;
     }
     // FIN_DECIDE
@@ -604,6 +599,7 @@ __device__ __forceinline__ void finalize_pair(const PairDesc* __restrict__ pd,
                 st->lambda = lam;
                 st->retries = j + 1;
                 st->done = 0;
+                st->att = j + 1;   // the next state-driven pass retries
                 return;
             }
             finished = 1;   // discard after the last retry
@@ -626,6 +622,7 @@ __device__ __forceinline__ void finalize_pair(const PairDesc* __restrict__ pd,
     }
     st->accepted = accepted;
     st->done = finished;
+    st->att = 0;   // the next state-driven pass starts an iteration
     st->iter += 1;
     if (st->L <= P.target) st->stopped = 1;   // false for a NaN target
     if (P.log) {
@@ -643,34 +640,19 @@ __device__ __forceinline__ void finalize_pair(const PairDesc* __restrict__ pd,
 }
 
 // One CTA per pair: fixed-order reduction of the pair's partials, then the
-// per-mode state update.  With a graph attempt loop (loop != 0: attempt 0
-// runs unconditionally, then a graph WHILE node repeats trial, evaluation
-// and this kernel with attempt -1 while its condition holds) the last CTA
-// to finish, once every pair's decision is written, sets the next attempt
-// and the loop condition: another pass while some pair rejected its trial
-// with retries left (its decision left done = 0; acceptance and the
-// discard after the last retry set done = 1).  Without a rejection the
-// loop's body never runs; the attempt returns to 0 when the loop ends.
+// per-mode state update.
 __global__ void k_finalize(const PairDesc* __restrict__ pd, Partials part,
                            DecideConsts d, int mode, int attempt,
-                           EvalOut* __restrict__ outs, int npairs,
-                           cudaGraphConditionalHandle loop) {
+                           EvalOut* __restrict__ outs) {
     finalize_pair(pd, part, d, mode, attempt, outs);
-    if (!loop || mode != FIN_DECIDE || threadIdx.x != 0) return;
-    DevState* st0 = pd[0].st;
-    __threadfence();   // this pair's decision before the count
-    if (atomicAdd(&st0->fin_count, 1u) != (unsigned)npairs - 1) return;
-    __threadfence();   // every pair's decision is visible
-    int any = 0;
-    for (int i = 0; i < npairs; ++i) {
-        const volatile DevState* s = pd[i].st;
-        if (!s->done && !s->stopped) any = 1;
+}
+
+// iter_end of every pair: iter + n, or 0 (no limit) for n = 0.
+__global__ void k_iter_end(const PairDesc* __restrict__ pd, int npairs, int n) {
+    for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+        DevState* st = pd[i].st;
+        st->iter_end = n > 0 ? st->iter + n : 0;
     }
-    const int next = any ? attempt_of(st0, attempt) + 1 : 0;
-    for (int i = 0; i < npairs; ++i) pd[i].st->att = next;
-    if (attempt < 0) st0->att_runs += 1;   // passes of the loop body
-    st0->fin_count = 0u;
-    cudaGraphSetConditional(loop, (any && next <= d.max_retries) ? 1u : 0u);
 }
 
 __global__ void k_copy_back(const PairDesc* __restrict__ pd, int npairs) {
@@ -720,9 +702,14 @@ int batch_step(const Batch& b, int attempt, cudaStream_t s) {
 }
 
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,
-                   cudaStream_t s, cudaGraphConditionalHandle loop) {
+                   cudaStream_t s) {
     k_finalize<<<b.npairs, 1024, 0, s>>>(b.pd, b.part, b.d, mode, attempt,
-                                         out, b.npairs, loop);
+                                         out);
+    return 1;
+}
+
+int batch_set_iter_end(const Batch& b, int n, cudaStream_t s) {
+    k_iter_end<<<1, 256, 0, s>>>(b.pd, b.npairs, n);
     return 1;
 }
 

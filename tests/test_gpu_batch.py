@@ -223,10 +223,11 @@ def test_batch_equals_single_pair_bitwise(P, mode):
 
 
 def test_batch_rejection_loop_matches_single_pairs(P):
-    """Eq. rejection in a batch: the graph's attempt loop keeps running
-    while any pair still retries, every other pair's later attempts are
-    no-ops, and each pair ends bitwise where a context of its own stepping
-    through lm_step (every attempt launched) ends."""
+    """Eq. rejection in a batch: each graph replay runs every pair's own
+    next attempt (the retry of a rejected trial or its next iteration),
+    pairs that have finished their iterations sit the replays out, and each
+    pair ends bitwise where a context of its own stepping through lm_step
+    (every attempt launched) ends."""
     import torch
     Fs, Ms = _pairs(seed0=120)
     params = P.lm_default_params(lambda0=1e-3, step=3.0, reject=1, tau=1.0,

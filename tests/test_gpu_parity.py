@@ -122,11 +122,12 @@ def test_lm_step_parity_rejection(P, oracle_mod):
 
 @pytest.mark.parametrize("warp", [0.0, 1.0])
 def test_rejection_loop_matches_unrolled_attempts(P, warp):
-    """With rejection the graph-replayed iteration runs its attempts in a
-    graph WHILE loop that stops once every decision is taken; lm_step runs
-    every attempt as launched kernels that turn into no-ops.  Both give the
-    same trajectory bit for bit (retries included), and the loop launches
-    fewer kernels."""
+    """With rejection each graph replay runs one attempt, the retry of a
+    rejected trial or the next iteration, read from the device state, and
+    lm_iterate replays until the n iterations are done; lm_step runs every
+    attempt as launched kernels that turn into no-ops.  Both give the same
+    trajectory bit for bit (retries included), and the replays launch fewer
+    kernels."""
     import torch
     import synth
     F, M, _ = synth.blob_pair((24, 24, 24), seed=9)
