@@ -84,6 +84,36 @@ LM_API int lm_unet_train_step(lm_unet *net, int n, const lm_volume *fixed,
 LM_API int lm_unet_get_weights(lm_unet *net, float *host);
 LM_API int lm_unet_get_grads(lm_unet *net, float *host);
 
+/* Tensors of the network's last pass, for inspection: the tests check
+ * every layer against the oracle on the network's own stored inputs (the
+ * paper has no network; this serves its parity checks).  Activations are
+ * those of the last lm_unet_forward, or of the last pair of the last
+ * training step; gradients are those of that pair's backward pass.  The
+ * backward pass reuses its buffers, so only these gradients survive it:
+ * DY<i>, the gradient of layer c<i>'s output after its activation mask
+ * (the operand of its weight gradient), and DX<i>, the gradient of c<i>'s
+ * input. */
+enum {
+    LM_UNET_X0, LM_UNET_E0A, LM_UNET_E0, LM_UNET_P0, LM_UNET_E1A, LM_UNET_E1,
+    LM_UNET_P1, LM_UNET_E2A, LM_UNET_E2, LM_UNET_P2, LM_UNET_E3A, LM_UNET_E3,
+    LM_UNET_CAT2, LM_UNET_D2A, LM_UNET_D2, LM_UNET_CAT1, LM_UNET_D1A,
+    LM_UNET_D1, LM_UNET_OUT,
+    LM_UNET_DY0, LM_UNET_DY1, LM_UNET_DY2, LM_UNET_DY3, LM_UNET_DY4,
+    LM_UNET_DY5, LM_UNET_DY6, LM_UNET_DY12,
+    LM_UNET_DX2, LM_UNET_DX4, LM_UNET_DX6, LM_UNET_DX8, LM_UNET_DX10,
+    LM_UNET_NTENSORS
+};
+/* which: one of the LM_UNET_* tensors.  level (host, may be NULL): the
+ * pyramid level l of the tensor (its sizes are D >> l, H >> l, W >> l);
+ * channels (host, may be NULL): its stored channel count C (the head's
+ * output and its gradient hold 16, the last 13 of them zero).  host: NULL
+ * to query only, else room for (D >> l)(H >> l)(W >> l) C floats that
+ * receive the tensor channels-last [z][y][x][c], bfloat16 values widened
+ * exactly.  Synchronises the net's stream.  LM_EINVAL on a NULL net or an
+ * unknown which. */
+LM_API int lm_unet_get_tensor(lm_unet *net, int which, float *host,
+                              int *level, int *channels);
+
 /* Single 3x3x3 convolution, zero padding 1 (the kernels the network uses).
  * Activations are channels-last bfloat16: x [D][H][W][cin],
  * y [D][H][W][cout] FP32; w bfloat16 [cout][27][cin] with tap

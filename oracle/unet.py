@@ -29,7 +29,8 @@ field; Adam (Kingma & Ba) updates FP32 master weights.
 Arrays are float64 numpy arrays with shape (C, D, H, W) (x fastest); conv
 weights are (Cout, Cin, 3, 3, 3) indexed [o, i, kz, ky, kx], biases (Cout,).
 Every function is the plain definition: explicit sums over the 27 taps, no
-blocking or fusion.
+blocking or fusion.  bf16_round() gives the bfloat16 value of a number, for
+comparisons with tensors a network stores in that format.
 """
 from __future__ import annotations
 
@@ -44,6 +45,15 @@ LAYERS = [(2, 16, True), (16, 16, True),
           (192, 64, True), (64, 64, True),
           (96, 32, True), (32, 32, True),
           (32, 3, False)]
+
+
+def bf16_round(x):
+    """x rounded to the nearest bfloat16 (ties to even), via FP32, returned
+    as float64 (finite inputs)."""
+    f = np.ascontiguousarray(np.asarray(x, np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def conv3d(x, w, b=None):

@@ -1803,6 +1803,75 @@ extern "C" int lm_unet_get_grads(lm_unet* n, float* host) {
     return fetch(n, n->grad, host);
 }
 
+extern "C" int lm_unet_get_tensor(lm_unet* n, int which, float* host,
+                                  int* level, int* channels) {
+    if (!n) return fail(LM_EINVAL, "net is NULL");
+    struct T {
+        const void* p;
+        int l, c, f32;
+    };
+    T t;
+    switch (which) {
+        case LM_UNET_X0: t = {n->x0, 0, 2, 0}; break;
+        case LM_UNET_E0A: t = {n->e0a, 0, 16, 0}; break;
+        case LM_UNET_E0: t = {n->e0, 0, 16, 0}; break;
+        case LM_UNET_P0: t = {n->p0, 1, 16, 0}; break;
+        case LM_UNET_E1A: t = {n->e1a, 1, 32, 0}; break;
+        case LM_UNET_E1: t = {n->e1, 1, 32, 0}; break;
+        case LM_UNET_P1: t = {n->p1, 2, 32, 0}; break;
+        case LM_UNET_E2A: t = {n->e2a, 2, 64, 0}; break;
+        case LM_UNET_E2: t = {n->e2, 2, 64, 0}; break;
+        case LM_UNET_P2: t = {n->p2, 3, 64, 0}; break;
+        case LM_UNET_E3A: t = {n->e3a, 3, 128, 0}; break;
+        case LM_UNET_E3: t = {n->e3, 3, 128, 0}; break;
+        case LM_UNET_CAT2: t = {n->cat2, 2, 192, 0}; break;
+        case LM_UNET_D2A: t = {n->d2a, 2, 64, 0}; break;
+        case LM_UNET_D2: t = {n->d2, 2, 64, 0}; break;
+        case LM_UNET_CAT1: t = {n->cat1, 1, 96, 0}; break;
+        case LM_UNET_D1A: t = {n->d1a, 1, 32, 0}; break;
+        case LM_UNET_D1: t = {n->d1, 1, 32, 0}; break;
+        case LM_UNET_OUT: t = {n->out, 1, 16, 1}; break;
+        // where each gradient is left by the reverse pass (see backward())
+        case LM_UNET_DY0: t = {n->gB0, 0, 16, 0}; break;
+        case LM_UNET_DY1: t = {n->gA0, 0, 16, 0}; break;
+        case LM_UNET_DY2: t = {n->gX1, 1, 32, 0}; break;
+        case LM_UNET_DY3: t = {n->ge1, 1, 32, 0}; break;
+        case LM_UNET_DY4: t = {n->gX2, 2, 64, 0}; break;
+        case LM_UNET_DY5: t = {n->ge2, 2, 64, 0}; break;
+        case LM_UNET_DY6: t = {n->gY3, 3, 128, 0}; break;
+        case LM_UNET_DY12: t = {n->gout, 1, 16, 0}; break;
+        case LM_UNET_DX2: t = {n->gY1, 1, 16, 0}; break;
+        case LM_UNET_DX4: t = {n->gY2, 2, 32, 0}; break;
+        case LM_UNET_DX6: t = {n->gX3, 3, 64, 0}; break;
+        case LM_UNET_DX8: t = {n->gcat2, 2, 192, 0}; break;
+        case LM_UNET_DX10: t = {n->gcat1, 1, 96, 0}; break;
+        default: return fail(LM_EINVAL, "unknown tensor %d", which);
+    }
+    if (level) *level = t.l;
+    if (channels) *channels = t.c;
+    if (!host) return LM_OK;
+    const size_t cnt = (size_t)n->Vl(t.l) * t.c;
+    cudaError_t e = cudaStreamSynchronize(n->stream);
+    if (e == cudaSuccess) {
+        if (t.f32) {
+            e = cudaMemcpy(host, t.p, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+        } else {
+            std::vector<uint16_t> raw(cnt);
+            e = cudaMemcpy(raw.data(), t.p, cnt * sizeof(uint16_t),
+                           cudaMemcpyDeviceToHost);
+            for (size_t i = 0; e == cudaSuccess && i < cnt; ++i) {
+                const uint32_t b = (uint32_t)raw[i] << 16;   // exact widening
+                memcpy(host + i, &b, sizeof(float));
+            }
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LM_ECUDA, "tensor copy failed: %s", cudaGetErrorString(e));
+    }
+    return LM_OK;
+}
+
 extern "C" int lm_conv3d_forward(int D, int H, int W, int cin, int cout,
                                  const void* x, const void* w, const float* bias,
                                  int act, float* y, void* stream) {

@@ -148,6 +148,7 @@ def load():
                                ctypes.c_float, ctypes.POINTER(D)],
         "lm_unet_get_weights": [V, V],
         "lm_unet_get_grads": [V, V],
+        "lm_unet_get_tensor": [V, I, V, ctypes.POINTER(I), ctypes.POINTER(I)],
         "lm_conv3d_forward": [I, I, I, I, I, V, V, V, I, V, V],
         "lm_conv3d_backward": [I, I, I, I, I, V, V, V, V, V, V, V],
         "lm_debug_check": [V],
@@ -566,7 +567,8 @@ EXPORTED = ("lm_default_params", "lm_init", "lm_destroy", "lm_eval",
             "lm_batch_debug_check",
             "lm_unet_shapes", "lm_unet_create", "lm_unet_destroy",
             "lm_unet_forward", "lm_unet_train_step", "lm_unet_get_weights",
-            "lm_unet_get_grads", "lm_conv3d_forward", "lm_conv3d_backward")
+            "lm_unet_get_grads", "lm_unet_get_tensor", "lm_conv3d_forward",
+            "lm_conv3d_backward")
 
 
 # ---------------------------------------------------------------------------
@@ -678,6 +680,30 @@ def lm_unet_get_grads(net: UNet):
                                     out.ctypes.data_as(ctypes.c_void_p)),
            "lm_unet_get_grads")
     return unpack_weights(out)
+
+
+# lm_unet_get_tensor names (include/lmunet.h), in enum order
+UNET_TENSORS = ("x0", "e0a", "e0", "p0", "e1a", "e1", "p1", "e2a", "e2", "p2",
+                "e3a", "e3", "cat2", "d2a", "d2", "cat1", "d1a", "d1", "out",
+                "dy0", "dy1", "dy2", "dy3", "dy4", "dy5", "dy6", "dy12",
+                "dx2", "dx4", "dx6", "dx8", "dx10")
+
+
+def lm_unet_get_tensor(net: UNet, name: str):
+    """A stored tensor of the network's last pass as float32
+    (D >> l, H >> l, W >> l, C), channels last."""
+    import numpy as np
+    which = UNET_TENSORS.index(name)
+    lvl, ch = ctypes.c_int(), ctypes.c_int()
+    lib = load()
+    _check(lib.lm_unet_get_tensor(net.handle, which, None, ctypes.byref(lvl),
+                                  ctypes.byref(ch)), "lm_unet_get_tensor")
+    D, H, W = (n >> lvl.value for n in net.shape)
+    out = np.empty((D, H, W, ch.value), np.float32)
+    _check(lib.lm_unet_get_tensor(net.handle, which,
+                                  out.ctypes.data_as(ctypes.c_void_p), None,
+                                  None), "lm_unet_get_tensor")
+    return out
 
 
 def lm_conv3d_forward(x, w, bias, act, y, stream=None):

@@ -198,6 +198,109 @@ def test_unet_gradients_match_oracle(P, oracle_mod):
         assert np.array_equal(a, b)
 
 
+def _ulp_bf16(v):
+    """Spacing of bfloat16 numbers at |v| (8 significant bits)."""
+    a = np.maximum(np.abs(v), 1e-30)
+    return 2.0 ** (np.floor(np.log2(a)) - 7)
+
+
+def _near_bf16(got, ref, name, floor=1e-5, frac=0.05):
+    """got and ref (bfloat16 values) at most one bfloat16 spacing apart (plus
+    an absolute floor for values that cancel to near zero), and equal for
+    all but a small fraction: only the FP32 accumulation order differs, and
+    it flips a rounding only where the exact value lies near a midpoint."""
+    d = np.abs(got - ref)
+    tol = _ulp_bf16(np.maximum(np.abs(ref), np.abs(got))) + floor * np.abs(ref).max()
+    assert (d <= tol).all(), (name, float(d.max()), float((d - tol).max()))
+    moved = float(np.mean(d > 0))
+    assert moved <= frac, (name, moved)
+    return moved
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_unet_layers_match_oracle_on_their_own_inputs(P, oracle_mod, seed):
+    """Layer-local parity of the whole network: every stage is recomputed by
+    the oracle from the tensors the network itself stored for that stage's
+    inputs (lm_unet_get_tensor), so no rounding is carried from layer to
+    layer and each stage is held to its own bar: a convolution's bfloat16
+    output within one bfloat16 spacing of the FP64 result rounded the same
+    way, pooling and concatenation exact, weight and bias gradients at the
+    1e-4 bar of a single convolution, the activation masks and the skip and
+    pooled-gradient sums between the layers bit for bit."""
+    import torch
+    from oracle import unet as U
+    init, params, F, M, tgt = _net_case(seed)
+    net = P.lm_unet_create(F.shape, init)
+    Ft, _ = _bf(F)
+    Mt, _ = _bf(M)
+    tt = torch.from_numpy(tgt).cuda()
+    L = P.lm_unet_train_step(net, [Ft], [Mt], [tt], lr=0.0)
+    grads = P.lm_unet_get_grads(net)
+    T = {n: np.moveaxis(P.lm_unet_get_tensor(net, n), -1, 0).astype(np.float64)
+         for n in P.UNET_TENSORS}
+    bf = U.bf16_round
+    cout = [co for _, co, _ in U.LAYERS]
+    moved = {}
+    # forward: each hidden convolution on its own stored input
+    convs = [("x0", "e0a", 0), ("e0a", "e0", 1), ("p0", "e1a", 2), ("e1a", "e1", 3),
+             ("p1", "e2a", 4), ("e2a", "e2", 5), ("p2", "e3a", 6), ("e3a", "e3", 7),
+             ("cat2", "d2a", 8), ("d2a", "d2", 9), ("cat1", "d1a", 10),
+             ("d1a", "d1", 11)]
+    for xin, yout, i in convs:
+        w, b = params[i]
+        ref = bf(U.leaky_relu(U.conv3d(T[xin], w, b)))
+        moved[yout] = _near_bf16(T[yout], ref, yout)
+    # the head (FP32 output, channels 3..15 are padding)
+    ref = U.conv3d(T["d1"], *params[12])
+    assert np.abs(T["out"][:3] - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert not T["out"][3:].any()
+    # the input pair, pooling (FP32 mean of 8, rounded) and concatenation
+    assert np.array_equal(T["x0"][0], U.bf16_round(F))
+    assert np.array_equal(T["x0"][1], U.bf16_round(M))
+    for src, dst in (("e0", "p0"), ("e1", "p1"), ("e2", "p2")):
+        moved[dst] = _near_bf16(T[dst], bf(U.pool(T[src])), dst, floor=0.0, frac=1e-3)
+    assert np.array_equal(T["cat2"][:128], U.up(T["e3"]))
+    assert np.array_equal(T["cat2"][128:], T["e2"])
+    assert np.array_equal(T["cat1"][:64], U.up(T["d2"]))
+    assert np.array_equal(T["cat1"][64:], T["e1"])
+    # the loss gradient at the head: 2 (out - tgt) / N, rounded
+    n_out = 3 * tgt[0].size
+    dz = bf(np.float32(2.0) * (T["out"][:3].astype(np.float32) - tgt) *
+            np.float32(1.0 / n_out))
+    assert np.abs(T["dy12"][:3] - dz).max() <= _ulp_bf16(np.abs(dz).max())
+    assert not T["dy12"][3:].any()
+    # weight and bias gradients from the layer's own input and output
+    # gradient (the layers whose gradient survives the reverse pass)
+    back = [(0, "x0", "dy0"), (1, "e0a", "dy1"), (2, "p0", "dy2"), (3, "e1a", "dy3"),
+            (4, "p1", "dy4"), (5, "e2a", "dy5"), (6, "p2", "dy6"), (12, "d1", "dy12")]
+    for i, xin, dyn in back:
+        dx, dw, db = U.conv3d_backward(T[xin], params[i][0], T[dyn][:cout[i]])
+        gw, gb = grads[i]
+        assert np.abs(gw - dw).max() <= 1e-4 * np.abs(dw).max(), (i, "w")
+        assert np.abs(gb - db).max() <= 1e-4 * np.abs(db).max(), (i, "b")
+        if dyn in ("dy2", "dy4", "dy6"):   # their data gradients survive too
+            dxn = "dx" + dyn[2:]
+            moved[dxn] = _near_bf16(T[dxn], bf(dx), dxn)
+    # between the layers, bit for bit in FP32 then bfloat16 as the network
+    # does it: the activation mask (slope 0.2f where the stored output is not
+    # positive) of the pooled gradient, alone (c1) or added to the skip
+    # connection's gradient (c3, c5)
+    s32 = np.float32(U.SLOPE)
+
+    def mask(y, g):
+        g32 = g.astype(np.float32)
+        return bf(np.where(y > 0, g32, s32 * g32))
+
+    g1 = np.float32(0.125) * U.up(T["dx2"]).astype(np.float32)
+    assert np.array_equal(T["dy1"], mask(T["e0"], bf(g1)))
+    for dyn, y, dxp, skip in (("dy3", "e1", "dx4", T["dx10"][64:]),
+                              ("dy5", "e2", "dx6", T["dx8"][128:])):
+        g = np.float32(0.125) * U.up(T[dxp]).astype(np.float32) + skip.astype(np.float32)
+        assert np.array_equal(T[dyn], mask(T[y], bf(g))), dyn
+    print("fraction of bfloat16 values one spacing off:",
+          {k: round(v, 4) for k, v in moved.items()}, "loss", L)
+
+
 def test_unet_adam_step_matches_oracle(P, oracle_mod):
     """One Adam step: the oracle applies it to the GPU's own gradients, so
     the comparison isolates the update (FP32 vs FP64 arithmetic)."""

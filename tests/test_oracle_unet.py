@@ -1,7 +1,7 @@
 """Pins of the U-Net oracle (oracle/unet.py) against facts other than
 itself: SciPy's n-D correlation, the adjoint (dot-product) identity, central
-finite differences of the training loss, and Adam's closed form under a
-constant gradient."""
+finite differences of the training loss, Adam's closed form under a
+constant gradient, and torch's float32 -> bfloat16 conversion."""
 import numpy as np
 import pytest
 from scipy import ndimage
@@ -141,3 +141,18 @@ def test_train_step_lowers_the_loss():
     for t in range(1, 6):
         _, ps, st = U.train_step(ps, st, [(F, M, tgt)], 1e-3, t)
     assert U.mse(U.forward(ps, F, M), tgt)[0] < L0
+
+
+def test_bf16_round_matches_torch():
+    # bf16_round against torch's own float32 -> bfloat16 conversion (round
+    # to nearest even), exact ties with even and odd kept bits included
+    torch = pytest.importorskip("torch")
+    r = _rng(20)
+    x = (r.standard_normal(4000) * 10.0 ** r.integers(-30, 30, 4000)).astype(np.float32)
+    hi = r.integers(0, 0x7F7F, 2000).astype(np.uint32) << 16
+    ties = (hi | np.uint32(0x8000)).view(np.float32)
+    x = np.concatenate([x, ties, -ties, np.float32([0.0, -0.0, 1.0, 3.0e38])])
+    ref = torch.from_numpy(x).to(torch.bfloat16).float().numpy().astype(np.float64)
+    got = U.bf16_round(x)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(U.bf16_round(got), got)   # idempotent
