@@ -343,8 +343,13 @@ struct Core {
 
     // Replays until every pair has reached its iter_end or stopped; the
     // passes of one round are the largest number of iterations any pair
-    // still owes.  Each round reads the states (a synchronisation).
-    int replay_until_done() {
+    // still owes.  Each round reads the states (a synchronisation).  Every
+    // pass either finishes a pair's iteration or uses one of its retries,
+    // so n iterations take at most (max_retries + 1) n passes; more means
+    // the device state is inconsistent, reported rather than looped on.
+    int replay_until_done(int n, int done) {
+        const long long cap = (long long)(p.max_retries + 1) * n;
+        long long passes = done;
         for (;;) {
             if (int rc = read_states()) return rc;
             int owe = 0;
@@ -354,7 +359,11 @@ struct Core {
                     owe = s.iter_end - s.iter;
             }
             if (owe == 0) return LM_OK;
+            if (passes + owe > cap)
+                return fail(LM_ESTATE, "%lld replays left iterations undone",
+                            passes);
             if (int rc = replay(owe)) return rc;
+            passes += owe;
         }
     }
 
@@ -376,7 +385,7 @@ struct Core {
         } else {
             launches += batch_set_iter_end(b, n, stream);
             rc = replay(n);
-            if (rc == LM_OK) rc = replay_until_done();
+            if (rc == LM_OK) rc = replay_until_done(n, n);
             // the limit ends with the run, whatever its outcome
             launches += batch_set_iter_end(b, 0, stream);
         }
