@@ -193,7 +193,12 @@ struct Core {
     LogEntry* h_log = nullptr;     // pinned, LOG_CAP
     std::vector<float*> gsink;     // lm_eval gradient sinks (lazy)
     bool have_reset = false;
+    // the captured iteration, once (gexec) and GRAPH_ITERS times in a row
+    // (gexec_n: one replay per GRAPH_ITERS iterations, so that a run of
+    // short iterations pays the launch of a graph once per group)
+    static constexpr int GRAPH_ITERS = 8;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec_n = nullptr;
     int graph_launches = 0;        // kernels of one graph launch
     long long launches = 0;
     int num_sms = 0;
@@ -204,7 +209,7 @@ struct Core {
     ~Core() {
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
-        if (gexec) cudaGraphExecDestroy(gexec);
+        drop_graphs();
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void* q : allocs) cudaFree(q);
         if (h_st) cudaFreeHost(h_st);
@@ -316,27 +321,47 @@ struct Core {
     // iterations (or stopped), reading the states in between.
     bool replay_retries() const { return p.reject && p.max_retries > 0; }
 
-    int capture_graph(cudaGraph_t* out) {
+    // Captures iters passes in a row and instantiates them.
+    int capture_graph(int iters, cudaGraphExec_t* exec) {
         if (!cap_stream)
             LM_CK(cudaStreamCreateWithFlags(&cap_stream,
                                             cudaStreamNonBlocking));
         LM_CK(cudaStreamBeginCapture(cap_stream,
                                      cudaStreamCaptureModeThreadLocal));
-        if (!replay_retries()) {
-            graph_launches = enqueue_iteration(cap_stream);
-        } else {
-            graph_launches = batch_step(b, -1, cap_stream);
-            graph_launches += batch_eval(b, EVAL_TRIAL, -1, cap_stream,
-                                         !step_resamples(b));
-            graph_launches += batch_finalize(b, FIN_DECIDE, -1, nullptr,
-                                             cap_stream);
+        for (int i = 0; i < iters; ++i) {
+            if (!replay_retries()) {
+                graph_launches = enqueue_iteration(cap_stream);
+            } else {
+                graph_launches = batch_step(b, -1, cap_stream);
+                graph_launches += batch_eval(b, EVAL_TRIAL, -1, cap_stream,
+                                             !step_resamples(b));
+                graph_launches += batch_finalize(b, FIN_DECIDE, -1, nullptr,
+                                                 cap_stream);
+            }
         }
-        LM_CK(cudaStreamEndCapture(cap_stream, out));
+        cudaGraph_t graph;
+        LM_CK(cudaStreamEndCapture(cap_stream, &graph));
+        cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return fail(LM_ECUDA, "graph instantiate failed: %s",
+                        cudaGetErrorString(e));
         return LM_OK;
     }
 
+    void drop_graphs() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (gexec_n) cudaGraphExecDestroy(gexec_n);
+        gexec = gexec_n = nullptr;
+    }
+
+    // n passes (graph_launches kernels each): whole groups from gexec_n,
+    // the rest one at a time.
     int replay(int n) {
-        for (int i = 0; i < n; ++i) LM_CK(cudaGraphLaunch(gexec, stream));
+        for (int i = 0; i < n / GRAPH_ITERS; ++i)
+            LM_CK(cudaGraphLaunch(gexec_n, stream));
+        for (int i = 0; i < n % GRAPH_ITERS; ++i)
+            LM_CK(cudaGraphLaunch(gexec, stream));
         launches += (long long)n * graph_launches;
         return LM_OK;
     }
@@ -370,14 +395,12 @@ struct Core {
     int iterate(int n) {
         if (n <= 0) return LM_OK;
         if (!gexec) {
-            cudaGraph_t graph;
-            int rc = capture_graph(&graph);
-            if (rc != LM_OK) return rc;
-            cudaError_t e = cudaGraphInstantiate(&gexec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess)
-                return fail(LM_ECUDA, "graph instantiate failed: %s",
-                            cudaGetErrorString(e));
+            int rc = capture_graph(1, &gexec);
+            if (rc == LM_OK) rc = capture_graph(GRAPH_ITERS, &gexec_n);
+            if (rc != LM_OK) {
+                drop_graphs();
+                return rc;
+            }
         }
         int rc = LM_OK;
         if (!replay_retries()) {
@@ -1211,10 +1234,7 @@ int core_replan(Core* c, int e1w, int e2w, int tile, int min_slices,
     if (plan.e1_ctas > c->e1_cap || plan.e2_ctas > c->e2_cap)
         return fail(LM_EINVAL, "plan exceeds the partial slots");
     c->b.plan = plan;
-    if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
+    c->drop_graphs();
     return c->push_table();
 }
 
