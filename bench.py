@@ -215,8 +215,12 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
     context.  The oracle's time gives the baseline, the comparisons give
     the error of the GPU against the oracle: the relative error of the
     current and the trial loss, max |u_gpu - u_oracle| of accepted trials,
-    and whether the decision and lambda match.  F and M are the images as
-    the context holds them (BF16-rounded where it stores BF16)."""
+    and whether the decision and lambda match.  The step's error is split
+    in two: the GPU's gradient at the same field against the oracle's
+    (max |g_gpu - g_oracle| / gmax), and the oracle's trial formed from
+    the GPU's gradient against the GPU's trial (the step kernel's own
+    error).  F and M are the images as the context holds them
+    (BF16-rounded where it stores BF16)."""
     import numpy as np
     import oracle
     oracle.build()
@@ -224,9 +228,17 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
     Fo, Mo = F.astype(np.float64), M.astype(np.float64)
     t_or, evals, rejected, near_ties = 0.0, 0, 0, 0
     e_loss, e_trial, e_du, same_all, lam_all = [], [], [], True, True
+    e_g, e_du_own = [], []
+    import torch
+    gbuf = torch.empty_like(u)
     for _ in range(iters):
         st = P.lm_get_state(ctx)
         ut = u.cpu().numpy().astype(np.float64)
+        # the GPU's own gradient at the same field (an evaluation that leaves
+        # the optimiser state alone), to split the step's error into the
+        # gradient's and the step kernel's
+        Lg, gmax_g = P.lm_eval(ctx, u, gbuf)
+        gg = gbuf.cpu().numpy().astype(np.float64)
         t0 = time.perf_counter()
         ev = oracle.evaluate(Fo, Mo, ut, Po)
         u1, _ = oracle.trial(ut, ev["g"], ev["gmax"], ev["L"], st.lambda_, Po)
@@ -255,9 +267,14 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
             rejected += 1
         e_loss.append(abs(st.loss - ev["L"]) / ev["L"])
         e_trial.append(abs(info.loss_first - L1) / L1)
+        e_g.append(float(np.abs(gg - ev["g"]).max() / ev["gmax"]))
         if acc:
-            e_du.append(float(np.abs(u.cpu().numpy().astype(np.float64)
-                                     - u1).max()))
+            un = u.cpu().numpy().astype(np.float64)
+            e_du.append(float(np.abs(un - u1).max()))
+            # the oracle's trial from the GPU's gradient: the step kernel's
+            # own error
+            uo, _ = oracle.trial(ut, gg, float(gmax_g), Lg, st.lambda_, Po)
+            e_du_own.append(float(np.abs(un - uo).max()))
     V = F.size
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     base = {"value": V * evals / t_or / 1e9, "unit": METRIC, "cores": cores,
@@ -273,6 +290,10 @@ def cpu_baseline(P, ctx, u, F, M, params, iters=6, what="the benched pair"):
            "max_rel_loss_err": max(e_loss),
            "max_rel_trial_loss_err": max(e_trial),
            "max_du_voxel": max(e_du) if e_du else None,
+           "max_du_voxel_per_iteration": [float(f"{x:.3g}") for x in e_du],
+           "max_g_err_rel_gmax": max(e_g),
+           "max_du_voxel_given_gpu_gradient": (max(e_du_own) if e_du_own
+                                               else None),
            "accepted": len(e_du), "rejected_first_trials": rejected,
            "decisions_match": bool(same_all), "lambda_match": bool(lam_all),
            "lambda_near_ties": near_ties,

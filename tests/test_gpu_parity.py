@@ -576,6 +576,55 @@ def test_full_size_eval_and_step(P, oracle_mod, kind):
             assert (err <= bound[None]).all(), _worst(err - bound[None])
 
 
+def test_full_size_first_step_from_identity(P, oracle_mod):
+    """The Voronoi workload's first full-resolution step from u = 0 (the
+    configuration the bench's oracle leg starts from), split into its two
+    error sources.  The step kernel given the GPU's own gradient matches
+    the oracle's Eq. tile1 + Eq. compositive to 1e-6 voxel.  The gradient
+    is held to its 1e-4 gmax bar; where |ghat|^2 << lambda the step scales
+    a gradient error d by step * r / (|ghat|^2 + lambda), so the step is
+    held per voxel to that multiple of the gradient bar plus 1e-4 voxel.
+    This is a known departure from the flat 1e-4 voxel bar at this one
+    state: at u = 0 the FP32 separable backward loses up to ~3.5e-5 gmax at
+    a few voxels where the moving image's zero band meets a saturated fixed
+    image, and the step turns that into ~2e-4 voxel; from the next
+    iteration on the flat bar holds (the oracle leg reports both)."""
+    import torch
+    import synth
+    F, M, _ = synth.voronoi_pair((160, 192, 224), seed=0)
+    shape = F.shape
+    params = P.lm_default_params()
+    Po = _oracle_params(oracle_mod, params)
+    ctx = P.lm_init(_t(F), _t(M), params)
+    u = torch.zeros((3,) + shape, device="cuda")
+    g = torch.empty_like(u)
+    Lg, gmax_g = P.lm_eval(ctx, u, g)
+    u0 = np.zeros((3,) + shape)
+    ev = oracle_mod.evaluate(F, M, u0, Po)
+    assert abs(Lg - ev["L"]) <= TOL_L * ev["L"]
+    gg = g.cpu().numpy().astype(np.float64)
+    dg = np.abs(gg - ev["g"]).max()
+    assert dg <= TOL_G * ev["gmax"], dg / ev["gmax"]
+    P.lm_reset(ctx, u)
+    st = P.lm_get_state(ctx)
+    info = P.lm_step(ctx, u)
+    assert info.accepted == 1 and info.retries == 0
+    ug = u.cpu().numpy().astype(np.float64)
+    # the step kernel alone: the oracle's trial from the GPU's gradient
+    um, _ = oracle_mod.trial(u0, gg, float(gmax_g), Lg, st.lambda_, Po)
+    assert np.abs(ug - um).max() <= 1e-6, _worst(np.abs(ug - um))
+    # against the oracle's own trial, per voxel
+    u1, _ = oracle_mod.trial(u0, ev["g"], ev["gmax"], ev["L"], st.lambda_, Po)
+    gh2 = (ev["g"] ** 2).sum(axis=0) / ev["gmax"] ** 2
+    bound = Po.step * ev["L"] * TOL_G / (gh2 + st.lambda_) + TOL_U
+    err = np.abs(ug - u1)
+    assert (err <= bound[None]).all(), _worst(err - bound[None])
+    print(f"first step from u = 0: max |du| {err.max():.2e} voxel on "
+          f"{int((err.max(axis=0) > TOL_U).sum())} voxels over 1e-4; gradient "
+          f"{dg / ev['gmax']:.2e} gmax; step kernel alone "
+          f"{np.abs(ug - um).max():.1e}")
+
+
 def test_full_size_lung_k7(P, oracle_mod):
     """Lung-CT-shaped pair at 448x448x384 (W x H x D), LNCC k = 7: the loss,
     sampled gradient entries and one LM step against the oracle, in the
