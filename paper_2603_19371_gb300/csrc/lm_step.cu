@@ -701,9 +701,14 @@ int batch_step(const Batch& b, int attempt, cudaStream_t s) {
     return 1 + launch_step<STEP_TILE>(b, attempt, s);
 }
 
+// The decision kernel's CTA: a few hundred partials per pair at most, so
+// a small CTA keeps its two reduction barriers short (the sums are exact,
+// so the result does not depend on the size).
+constexpr int FIN_THREADS = 256;
+
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,
                    cudaStream_t s) {
-    k_finalize<<<b.npairs, 1024, 0, s>>>(b.pd, b.part, b.d, mode, attempt,
+    k_finalize<<<b.npairs, FIN_THREADS, 0, s>>>(b.pd, b.part, b.d, mode, attempt,
                                          out);
     return 1;
 }
