@@ -585,10 +585,12 @@ def test_full_size_first_step_from_identity(P, oracle_mod):
     a gradient error d by step * r / (|ghat|^2 + lambda), so the step is
     held per voxel to that multiple of the gradient bar plus 1e-4 voxel.
     This is a known departure from the flat 1e-4 voxel bar at this one
-    state: at u = 0 the FP32 separable backward loses up to ~3.5e-5 gmax at
-    a few voxels where the moving image's zero band meets a saturated fixed
-    image, and the step turns that into ~2e-4 voxel; from the next
-    iteration on the flat bar holds (the oracle leg reports both)."""
+    state: at u = 0 the FP32 rounding of the backward's box sums, which the
+    combination F' Box(a) + 2 J' Box(b) + Box(c) then cancels, costs up to
+    ~3.5e-5 gmax at a few voxels where the moving image's zero band meets a
+    near-saturated fixed image, and the step turns that into ~2e-4 voxel;
+    from the next iteration on the flat bar holds (the bench's oracle leg
+    reports both)."""
     import torch
     import synth
     F, M, _ = synth.voronoi_pair((160, 192, 224), seed=0)
