@@ -157,6 +157,18 @@ def test_unet_create_validates_sizes_on_the_host(lib):
     # unsupported convolution shapes fail before any CUDA call
     assert lib.lm_conv3d_forward(4, 4, 4, 3, 16, w, w, None, 0, w, None) == lmreg.LM_EINVAL
     assert lib.lm_conv3d_forward(4, 4, 4, 16, 8, w, w, None, 0, w, None) == lmreg.LM_EINVAL
+    # tensor inspection without a network
+    assert lib.lm_unet_get_tensor(None, 0, None, None, None) == lmreg.LM_EINVAL
+
+
+def test_unet_tensor_names_follow_the_header(lib):
+    """The binding's tensor names are the header's LM_UNET_* enum, in order."""
+    from paper_2603_19371_gb300 import lmreg
+    with open(os.path.join(ROOT, "include", "lmunet.h")) as f:
+        h = f.read()
+    body = h[h.index("LM_UNET_X0"):h.index("LM_UNET_NTENSORS")]
+    names = re.findall(r"LM_UNET_(\w+)", body)
+    assert [n.lower() for n in names] == list(lmreg.UNET_TENSORS)
 
 
 def test_noalloc_validates_on_the_host(lib):
