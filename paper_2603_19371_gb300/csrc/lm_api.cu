@@ -412,8 +412,9 @@ struct Core {
             // the limit ends with the run, whatever its outcome
             launches += batch_set_iter_end(b, 0, stream);
         }
-        if (rc != LM_OK) return rc;
+        // the current field back in the caller's slot, whatever the outcome
         launches += batch_sync_back(b, stream);
+        if (rc != LM_OK) return rc;
         LM_CK(cudaGetLastError());
         return LM_OK;
     }
