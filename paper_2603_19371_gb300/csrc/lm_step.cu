@@ -708,8 +708,8 @@ constexpr int FIN_THREADS = 256;
 
 int batch_finalize(const Batch& b, int mode, int attempt, EvalOut* out,
                    cudaStream_t s) {
-    k_finalize<<<b.npairs, FIN_THREADS, 0, s>>>(b.pd, b.part, b.d, mode, attempt,
-                                         out);
+    k_finalize<<<b.npairs, FIN_THREADS, 0, s>>>(b.pd, b.part, b.d, mode,
+                                                attempt, out);
     return 1;
 }
 
