@@ -45,3 +45,28 @@ def test_replicas_aggregate_over_two_gloo_ranks():
 def test_aggregate_without_a_process_group_is_local():
     import bench
     assert bench.aggregate(7.5, 2e6) == (7.5, 2e6)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference (the FP64 oracle on the host cores) prints
+    one JSON line with the reference arm's keys; no GPU is involved."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], cwd=root,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == d["unit"] == "Gvoxel-iters/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] >= 3
+    assert d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == d["e2e"]["d2h_bytes_per_step"] == 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["value"] == d["value"]
